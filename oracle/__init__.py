@@ -1,0 +1,315 @@
+"""ctypes binding of the FP64 CPU oracle (oracle/gx_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the bench's CPU
+baseline leg use it to check and time the CUDA path.  It shares no code with
+the CUDA path and never imports it; both consume the same seeded inputs from
+``paper_2306_07552_b300.inputs``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "libgx_oracle.so")
+MAX_OBJ = 64
+BAND = 1e-4
+
+
+def build(force: bool = False) -> str:
+    src = os.path.join(_HERE, "gx_oracle.c")
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(
+            os.path.getmtime(src), os.path.getmtime(os.path.join(_HERE, "gx_oracle.h"))):
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-Wall", "-fPIC", "-shared", "-o", _SO,
+                               src, "-lm"])
+    return _SO
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        _declare(_lib)
+    return _lib
+
+
+f32p = C.POINTER(C.c_float)
+f64p = C.POINTER(C.c_double)
+i32p = C.POINTER(C.c_int32)
+u32p = C.POINTER(C.c_uint32)
+u8p = C.POINTER(C.c_uint8)
+
+
+class Robot_c(C.Structure):
+    _fields_ = [("link_offset", f32p), ("link_axis", i32p), ("q_min", f32p), ("q_max", f32p),
+                ("q_rest", f32p), ("dq_max", C.c_float), ("base_step", C.c_float),
+                ("base_turn", C.c_float), ("n_spheres", C.c_int32), ("sphere_link", i32p),
+                ("sphere_pos", f32p), ("sphere_radius", f32p), ("cam_pos", f32p),
+                ("cam_pitch", C.c_float), ("cam_near", C.c_float), ("grasp_radius", C.c_float),
+                ("rest_clearance", C.c_float)]
+
+
+class Scene_c(C.Structure):
+    _fields_ = [("n_boxes", C.c_int32), ("boxes", f32p), ("n_verts", C.c_int32), ("verts", f32p),
+                ("n_tris", C.c_int32), ("tris", i32p), ("tri_rgb", u32p),
+                ("n_supports", C.c_int32), ("supports", f32p), ("grid_origin", C.c_float * 3),
+                ("grid_h", C.c_float), ("grid_dims", C.c_int32 * 3), ("spawn", C.c_float * 4)]
+
+
+class ObjMesh_c(C.Structure):
+    _fields_ = [("n_verts", C.c_int32), ("verts", f32p), ("n_tris", C.c_int32), ("tris", i32p),
+                ("obj_rgb", u32p)]
+
+
+class State_c(C.Structure):
+    _fields_ = [("base", C.c_double * 3), ("q", C.c_double * 7), ("held", C.c_int32),
+                ("c_off", C.c_double * 3), ("p_pre", C.c_double * 3), ("n_obj", C.c_int32),
+                ("obj", (C.c_double * 4) * MAX_OBJ), ("step_count", C.c_int32),
+                ("episode", C.c_int32)]
+
+
+class StepOut_c(C.Structure):
+    _fields_ = [("contact_mask", C.c_uint32), ("flags", C.c_uint8), ("event", C.c_uint8),
+                ("reverted", C.c_uint8), ("pad", C.c_uint8), ("near_band", C.c_int32),
+                ("ee", C.c_double * 3), ("cam_R", C.c_double * 9), ("cam_t", C.c_double * 3)]
+
+
+class ResetOut_c(C.Structure):
+    _fields_ = [("near_band", C.c_int32), ("failed", C.c_int32)]
+
+
+class RenderStats_c(C.Structure):
+    _fields_ = [("tris_setup", C.c_int64), ("frags_covered", C.c_int64),
+                ("ambiguous", C.c_int64), ("overflow", C.c_int64)]
+
+
+def _declare(L):
+    P = C.POINTER
+    L.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
+    L.orc_box_sdf.argtypes = [f64p, f32p]
+    L.orc_box_sdf.restype = C.c_double
+    L.orc_grid_node.argtypes = [P(Scene_c), C.c_int, C.c_int, C.c_int]
+    L.orc_grid_node.restype = C.c_double
+    L.orc_grid_query.argtypes = [P(Scene_c), f64p, f64p, f64p]
+    L.orc_grid_query.restype = C.c_int
+    L.orc_fk.argtypes = [P(Robot_c), f64p, f64p, f64p, f64p, f64p]
+    L.orc_sphere_centres.argtypes = [P(Robot_c), f64p, f64p, f64p]
+    L.orc_step.argtypes = [P(Robot_c), P(Scene_c), P(State_c), f32p, P(StepOut_c)]
+    L.orc_reset.argtypes = [P(Robot_c), P(Scene_c), P(State_c), C.c_uint64, C.c_int32, C.c_int32,
+                            C.c_float, C.c_float, P(ResetOut_c)]
+    L.orc_snap.argtypes = [P(Scene_c), f64p, C.c_double, P(C.c_int), P(C.c_int)]
+    L.orc_snap.restype = C.c_double
+    L.orc_render.argtypes = [P(Robot_c), P(Scene_c), P(ObjMesh_c), P(State_c), C.c_int32,
+                             C.c_int32, C.c_double, C.c_double, C.c_double, f64p, u32p, u8p,
+                             i32p, P(RenderStats_c)]
+    L.orc_mlp_forward.argtypes = [f64p, C.c_int, P(f64p), P(f64p), i32p, C.c_int, f64p, f64p]
+    L.orc_mlp_forward.restype = C.c_double
+    L.orc_mlp_loss_grad.argtypes = [f64p, C.c_int, P(f64p), P(f64p), i32p, C.c_int, f64p, f64p,
+                                    C.c_int, C.c_double, C.c_double, P(f64p), P(f64p)]
+    L.orc_mlp_loss_grad.restype = C.c_double
+
+
+def _p(a, t):
+    return a.ctypes.data_as(t)
+
+
+class Oracle:
+    """FP64 oracle bound to one robot, one scene and the instanced object mesh."""
+
+    # rasteriser ambiguity band and depth tolerance ("Readings")
+    EPS_PX = 1.0 / 64.0
+    TOL_REL = 1e-5
+    COS_MIN = 0.05
+
+    def __init__(self, robot, scene, obj_mesh=None, obj_rgb=None):
+        self._keep = []
+        k = self._keep.append
+        r = robot
+        arrs = dict(link_offset=np.ascontiguousarray(r.link_offset, np.float32),
+                    link_axis=np.ascontiguousarray(r.link_axis, np.int32),
+                    q_min=np.ascontiguousarray(r.q_min, np.float32),
+                    q_max=np.ascontiguousarray(r.q_max, np.float32),
+                    q_rest=np.ascontiguousarray(r.q_rest, np.float32),
+                    sphere_link=np.ascontiguousarray(r.sphere_link, np.int32),
+                    sphere_pos=np.ascontiguousarray(r.sphere_pos, np.float32),
+                    sphere_radius=np.ascontiguousarray(r.sphere_radius, np.float32),
+                    cam_pos=np.ascontiguousarray(r.cam_pos, np.float32))
+        for v in arrs.values():
+            k(v)
+        self.robot = Robot_c(
+            _p(arrs["link_offset"], f32p), _p(arrs["link_axis"], i32p), _p(arrs["q_min"], f32p),
+            _p(arrs["q_max"], f32p), _p(arrs["q_rest"], f32p), r.dq_max, r.base_step,
+            r.base_turn, len(r.sphere_radius), _p(arrs["sphere_link"], i32p),
+            _p(arrs["sphere_pos"], f32p), _p(arrs["sphere_radius"], f32p),
+            _p(arrs["cam_pos"], f32p), r.cam_pitch, r.cam_near, r.grasp_radius, r.rest_clearance)
+        s = scene
+        sa = dict(boxes=np.ascontiguousarray(s.boxes, np.float32),
+                  verts=np.ascontiguousarray(s.verts, np.float32),
+                  tris=np.ascontiguousarray(s.tris, np.int32),
+                  tri_rgb=np.ascontiguousarray(s.tri_rgb, np.uint32),
+                  supports=np.ascontiguousarray(s.supports, np.float32))
+        for v in sa.values():
+            k(v)
+        self.scene = Scene_c(len(sa["boxes"]), _p(sa["boxes"], f32p), len(sa["verts"]),
+                             _p(sa["verts"], f32p), len(sa["tris"]), _p(sa["tris"], i32p),
+                             _p(sa["tri_rgb"], u32p), len(sa["supports"]),
+                             _p(sa["supports"], f32p),
+                             (C.c_float * 3)(*[float(x) for x in s.grid_origin]), s.grid_h,
+                             (C.c_int32 * 3)(*[int(x) for x in s.grid_dims]),
+                             (C.c_float * 4)(*[float(x) for x in s.spawn]))
+        if obj_mesh is not None:
+            mv = np.ascontiguousarray(obj_mesh[0], np.float32)
+            mt = np.ascontiguousarray(obj_mesh[1], np.int32)
+            rgb = np.zeros(MAX_OBJ, np.uint32)
+            if obj_rgb is not None:
+                rgb[:len(obj_rgb)] = obj_rgb
+            for v in (mv, mt, rgb):
+                k(v)
+            self.objmesh = ObjMesh_c(len(mv), _p(mv, f32p), len(mt), _p(mt, i32p), _p(rgb, u32p))
+        else:
+            self.objmesh = None
+        self.L = lib()
+
+    # ---------------------------------------------------------------- state
+    @staticmethod
+    def make_state(base, q, held=-1, c_off=(0, 0, 0), p_pre=(0, 0, 0), objs=None,
+                   step_count=0, episode=0):
+        st = State_c()
+        st.base[:] = [float(x) for x in base]
+        st.q[:] = [float(x) for x in q]
+        st.held = int(held)
+        st.c_off[:] = [float(x) for x in c_off]
+        st.p_pre[:] = [float(x) for x in p_pre]
+        objs = np.zeros((0, 4)) if objs is None else np.asarray(objs, np.float64)
+        st.n_obj = len(objs)
+        for j in range(len(objs)):
+            st.obj[j][:] = [float(x) for x in objs[j]]
+        st.step_count = int(step_count)
+        st.episode = int(episode)
+        return st
+
+    @staticmethod
+    def state_objs(st):
+        return np.array([[st.obj[j][a] for a in range(4)] for j in range(st.n_obj)]).reshape(-1, 4)
+
+    # ------------------------------------------------------------ functions
+    def step(self, st, action):
+        a = np.ascontiguousarray(action, np.float32)
+        out = StepOut_c()
+        self.L.orc_step(C.byref(self.robot), C.byref(self.scene), C.byref(st), _p(a, f32p),
+                        C.byref(out))
+        return out
+
+    def reset(self, st, seed, env, n_obj, rho_min, rho_max):
+        out = ResetOut_c()
+        self.L.orc_reset(C.byref(self.robot), C.byref(self.scene), C.byref(st), int(seed),
+                         int(env), int(n_obj), float(rho_min), float(rho_max), C.byref(out))
+        return out
+
+    def fk(self, base, q):
+        b = np.ascontiguousarray(base, np.float64)
+        qq = np.ascontiguousarray(q, np.float64)
+        links = np.zeros((8, 12))
+        ee = np.zeros(12)
+        cam = np.zeros(12)
+        self.L.orc_fk(C.byref(self.robot), _p(b, f64p), _p(qq, f64p), _p(links, f64p),
+                      _p(ee, f64p), _p(cam, f64p))
+        return links, ee, cam
+
+    def sphere_centres(self, base, q):
+        b = np.ascontiguousarray(base, np.float64)
+        qq = np.ascontiguousarray(q, np.float64)
+        out = np.zeros((self.robot.n_spheres, 3))
+        self.L.orc_sphere_centres(C.byref(self.robot), _p(b, f64p), _p(qq, f64p),
+                                  _p(out, f64p))
+        return out
+
+    def grid_node(self, i, j, k):
+        return self.L.orc_grid_node(C.byref(self.scene), int(i), int(j), int(k))
+
+    def grid_query(self, c):
+        cc = np.ascontiguousarray(c, np.float64)
+        d = C.c_double()
+        e = C.c_double()
+        inside = self.L.orc_grid_query(C.byref(self.scene), _p(cc, f64p), C.byref(d), C.byref(e))
+        return bool(inside), d.value, e.value
+
+    def snap(self, p, target):
+        pp = np.ascontiguousarray(p, np.float64)
+        ok = C.c_int()
+        nb = C.c_int()
+        y = self.L.orc_snap(C.byref(self.scene), _p(pp, f64p), float(target), C.byref(ok),
+                            C.byref(nb))
+        return y, bool(ok.value), nb.value
+
+    def render(self, st, W, H, eps_px=None, tol_rel=None, cos_min=None):
+        n = W * H
+        depth = np.zeros(n)
+        rgb = np.zeros(n, np.uint32)
+        amb = np.zeros(n, np.uint8)
+        win = np.zeros(n, np.int32)
+        stats = RenderStats_c()
+        self.L.orc_render(C.byref(self.robot), C.byref(self.scene), C.byref(self.objmesh),
+                          C.byref(st), W, H, self.EPS_PX if eps_px is None else eps_px,
+                          self.TOL_REL if tol_rel is None else tol_rel,
+                          self.COS_MIN if cos_min is None else cos_min, _p(depth, f64p),
+                          _p(rgb, u32p), _p(amb, u8p), _p(win, i32p), C.byref(stats))
+        return (depth.reshape(H, W), rgb.reshape(H, W), amb.reshape(H, W).astype(bool),
+                win.reshape(H, W), stats)
+
+
+def philox4x32_10(ctr, key):
+    L = lib()
+    c = np.ascontiguousarray(ctr, np.uint32)
+    k = np.ascontiguousarray(key, np.uint32)
+    o = np.zeros(4, np.uint32)
+    L.orc_philox4x32_10(_p(c, u32p), _p(k, u32p), _p(o, u32p))
+    return o
+
+
+def box_sdf(p, box):
+    L = lib()
+    pp = np.ascontiguousarray(p, np.float64)
+    b = np.ascontiguousarray(box, np.float32)
+    return L.orc_box_sdf(_p(pp, f64p), _p(b, f32p))
+
+
+class MLP64:
+    """FP64 Fourier-feature MLP used to check the neural-SDF kernels."""
+
+    def __init__(self, B, Ws, bs):
+        self.B = np.ascontiguousarray(B, np.float64)
+        self.Ws = [np.ascontiguousarray(w, np.float64) for w in Ws]
+        self.bs = [np.ascontiguousarray(b, np.float64) for b in bs]
+        self.dims = np.array([self.Ws[0].shape[1]] + [w.shape[0] for w in self.Ws], np.int32)
+        self.F = self.B.shape[0]
+        assert self.dims[0] == 2 * self.F
+        self._wp = (f64p * len(self.Ws))(*[_p(w, f64p) for w in self.Ws])
+        self._bp = (f64p * len(self.bs))(*[_p(b, f64p) for b in self.bs])
+
+    def forward(self, X):
+        X = np.ascontiguousarray(np.atleast_2d(X), np.float64)
+        L = lib()
+        out = np.zeros(len(X))
+        for i in range(len(X)):
+            out[i] = L.orc_mlp_forward(_p(self.B, f64p), self.F, self._wp, self._bp,
+                                       _p(self.dims, i32p), len(self.Ws), _p(X[i], f64p), None)
+        return out
+
+    def loss_grad(self, X, y, lo, hi):
+        X = np.ascontiguousarray(X, np.float64)
+        y = np.ascontiguousarray(y, np.float64)
+        gW = [np.zeros_like(w) for w in self.Ws]
+        gb = [np.zeros_like(b) for b in self.bs]
+        gwp = (f64p * len(gW))(*[_p(w, f64p) for w in gW])
+        gbp = (f64p * len(gb))(*[_p(b, f64p) for b in gb])
+        loss = lib().orc_mlp_loss_grad(_p(self.B, f64p), self.F, self._wp, self._bp,
+                                       _p(self.dims, i32p), len(self.Ws), _p(X, f64p),
+                                       _p(y, f64p), len(X), lo, hi, gwp, gbp)
+        return loss, gW, gb

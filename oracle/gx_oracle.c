@@ -1,0 +1,719 @@
+/*
+ * gx_oracle.c -- plain, slow, FP64 reference of the batched environment step
+ * of Galactic (arXiv 2306.07552).  TEST INFRASTRUCTURE ONLY (see the header).
+ *
+ * Every function restates a definition, in the order the method applies it:
+ *   action decoding ........ App. A (action space), Sec. 3.2 (offsets applied
+ *                            directly to the robot state)
+ *   forward kinematics ..... Sec. 3.2 (links placed by FK each step)
+ *   static collision ....... Sec. 3.2 / appendix "Collision-Detection
+ *                            Details": sphere vs static scene; here the scene
+ *                            is a signed-distance grid queried trilinearly
+ *   object collision ....... same appendix: robot spheres vs movable objects
+ *   resolution ............. Sec. 3.2: a collision disallows all robot
+ *                            movement for the step
+ *   grasp .................. Sec. 3.2: 3 cm sphere at the end-effector tip
+ *   release ................ Sec. 3.2: snap-to-surface by a downward sphere
+ *                            cast; appendix "Object Placing Heuristic":
+ *                            restore the pre-grasp pose on failure
+ *   rendering .............. Sec. 3.1: one egocentric depth + RGB image per
+ *                            environment; here the nearest front-facing
+ *                            triangle along each pixel-centre ray
+ *   reset .................. rejection sampling with Philox4x32-10
+ *                            (Salmon et al., SC'11)
+ * Nothing here is blocked, fused or reordered beyond those definitions.
+ */
+#include "gx_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw: "Parallel random numbers: as  */
+/* easy as 1, 2, 3", SC'11).  Ten rounds of the 4x32 S-box with key bumps.  */
+/* ------------------------------------------------------------------------ */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int r = 0; r < 10; ++r) {
+    uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n1 = lo1;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    uint32_t n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* uniform in [0, 1) from the top 24 bits: exact in both float and double */
+static double unit24(uint32_t w) { return (double)(w >> 8) * (1.0 / 16777216.0); }
+
+/* ------------------------------------------------------------------------ */
+/* Static scene: signed distance to a union of boxes, sampled on a lattice. */
+/* ------------------------------------------------------------------------ */
+
+/* Distance from p to an axis-aligned box: Euclidean distance to the box when
+ * outside, minus the distance to the nearest face when inside. */
+double orc_box_sdf(const double p[3], const float box[6]) {
+  double out2 = 0.0, inmax = -INFINITY;
+  for (int a = 0; a < 3; ++a) {
+    double lo = box[a], hi = box[a + 3];
+    double c = 0.5 * (lo + hi), e = 0.5 * (hi - lo);
+    double q = fabs(p[a] - c) - e;
+    if (q > 0) out2 += q * q;
+    if (q > inmax) inmax = q;
+  }
+  return sqrt(out2) + (inmax < 0 ? inmax : 0.0);
+}
+
+/* Node (i,j,k) of the distance grid: the scene SDF (min over solids) at
+ * origin + (i,j,k) * h, computed on demand. */
+double orc_grid_node(const orc_scene* s, int i, int j, int k) {
+  double p[3] = {(double)s->grid_origin[0] + i * (double)s->grid_h,
+                 (double)s->grid_origin[1] + j * (double)s->grid_h,
+                 (double)s->grid_origin[2] + k * (double)s->grid_h};
+  double d = INFINITY;
+  for (int b = 0; b < s->n_boxes; ++b) {
+    double v = orc_box_sdf(p, s->boxes + 6 * b);
+    if (v < d) d = v;
+  }
+  return d;
+}
+
+/* Trilinear interpolation of the node values at c.  Returns 0 when c lies
+ * outside the lattice box (that counts as contact); *edge receives the
+ * distance from c to the lattice boundary (negative outside). */
+int orc_grid_query(const orc_scene* s, const double c[3], double* d, double* edge) {
+  double h = s->grid_h, g[3], t[3];
+  int i[3];
+  double e = INFINITY;
+  for (int a = 0; a < 3; ++a) {
+    g[a] = (c[a] - (double)s->grid_origin[a]) / h;
+    double ea = fmin(g[a], (double)(s->grid_dims[a] - 1) - g[a]) * h;
+    if (ea < e) e = ea;
+  }
+  if (edge) *edge = e;
+  if (e < 0) return 0;
+  for (int a = 0; a < 3; ++a) {
+    i[a] = (int)floor(g[a]);
+    if (i[a] > s->grid_dims[a] - 2) i[a] = s->grid_dims[a] - 2;
+    t[a] = g[a] - i[a];
+  }
+  double v = 0.0;
+  for (int dz = 0; dz < 2; ++dz)
+    for (int dy = 0; dy < 2; ++dy)
+      for (int dx = 0; dx < 2; ++dx) {
+        double w = (dx ? t[0] : 1 - t[0]) * (dy ? t[1] : 1 - t[1]) * (dz ? t[2] : 1 - t[2]);
+        v += w * orc_grid_node(s, i[0] + dx, i[1] + dy, i[2] + dz);
+      }
+  *d = v;
+  return 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Rigid frames: R row-major 3x3 then t; x_world = R x_local + t.           */
+/* ------------------------------------------------------------------------ */
+static void fr_ident(double F[12]) {
+  memset(F, 0, 12 * sizeof(double));
+  F[0] = F[4] = F[8] = 1.0;
+}
+static void fr_mul(const double A[12], const double B[12], double O[12]) {
+  double T[12];
+  for (int r = 0; r < 3; ++r) {
+    for (int c = 0; c < 3; ++c)
+      T[3 * r + c] = A[3 * r] * B[c] + A[3 * r + 1] * B[3 + c] + A[3 * r + 2] * B[6 + c];
+    T[9 + r] = A[3 * r] * B[9] + A[3 * r + 1] * B[10] + A[3 * r + 2] * B[11] + A[9 + r];
+  }
+  memcpy(O, T, sizeof(T));
+}
+static void fr_trans(double F[12], double x, double y, double z) {
+  fr_ident(F);
+  F[9] = x; F[10] = y; F[11] = z;
+}
+static void fr_rot(double F[12], int axis, double a) {
+  double c = cos(a), s = sin(a);
+  fr_ident(F);
+  if (axis == 0) { F[4] = c; F[5] = -s; F[7] = s; F[8] = c; }
+  else if (axis == 1) { F[0] = c; F[2] = s; F[6] = -s; F[8] = c; }
+  else { F[0] = c; F[1] = -s; F[3] = s; F[4] = c; }
+}
+static void fr_apply(const double F[12], const double p[3], double o[3]) {
+  for (int r = 0; r < 3; ++r) o[r] = F[3 * r] * p[0] + F[3 * r + 1] * p[1] + F[3 * r + 2] * p[2] + F[9 + r];
+}
+
+/* Forward kinematics (Sec. 3.2).  Base frame T0 = Trans(x,0,z) Ry(yaw);
+ * T_k = T_{k-1} Trans(o_k) Rot(axis_k, q_k); tool tip = T_7 Trans(o_tip);
+ * head camera = T0 Trans(cam_pos) M where M has columns right = (0,0,-1),
+ * up = (-sin p, cos p, 0), forward = (cos p, sin p, 0) for pitch p. */
+void orc_fk(const orc_robot* rb, const double base[3], const double q[7], double links[8][12],
+            double ee[12], double cam[12]) {
+  double A[12], B[12];
+  fr_trans(A, base[0], 0.0, base[1]);
+  fr_rot(B, 1, base[2]);
+  fr_mul(A, B, links[0]);
+  for (int k = 1; k <= 7; ++k) {
+    const float* o = rb->link_offset + 3 * (k - 1);
+    fr_trans(A, o[0], o[1], o[2]);
+    fr_mul(links[k - 1], A, B);
+    fr_rot(A, rb->link_axis[k - 1], q[k - 1]);
+    fr_mul(B, A, links[k]);
+  }
+  if (ee) {
+    const float* o = rb->link_offset + 21;
+    fr_trans(A, o[0], o[1], o[2]);
+    fr_mul(links[7], A, ee);
+  }
+  if (cam) {
+    double p = rb->cam_pitch, M[12];
+    double sp = sin(p), cp = cos(p);
+    /* columns: right, up, forward */
+    M[0] = 0.0; M[1] = -sp; M[2] = cp;
+    M[3] = 0.0; M[4] = cp;  M[5] = sp;
+    M[6] = -1.0; M[7] = 0.0; M[8] = 0.0;
+    M[9] = rb->cam_pos[0]; M[10] = rb->cam_pos[1]; M[11] = rb->cam_pos[2];
+    fr_mul(links[0], M, cam);
+  }
+}
+
+void orc_sphere_centres(const orc_robot* rb, const double base[3], const double q[7],
+                        double out[][3]) {
+  double links[8][12];
+  orc_fk(rb, base, q, links, NULL, NULL);
+  for (int i = 0; i < rb->n_spheres; ++i) {
+    double p[3] = {rb->sphere_pos[3 * i], rb->sphere_pos[3 * i + 1], rb->sphere_pos[3 * i + 2]};
+    fr_apply(links[rb->sphere_link[i]], p, out[i]);
+  }
+}
+
+static double clampd(double x, double lo, double hi) { return x < lo ? lo : (x > hi ? hi : x); }
+static double dist3(const double a[3], const double b[3]) {
+  double dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
+  return sqrt(dx * dx + dy * dy + dz * dz);
+}
+
+/* Yaw kept in (-pi, pi]. */
+static double wrap_pi(double a) {
+  while (a > PI) a -= 2 * PI;
+  while (a <= -PI) a += 2 * PI;
+  return a;
+}
+
+/* Static contact of a sphere (c, r): outside the lattice, or d(c) < r. */
+static int static_contact(const orc_scene* s, const double c[3], double r, int* nb) {
+  double d, edge;
+  int inside = orc_grid_query(s, c, &d, &edge);
+  if (fabs(edge) < ORC_BAND) (*nb)++;
+  if (!inside) return 1;
+  if (fabs(d - r) < ORC_BAND) (*nb)++;
+  return d < r;
+}
+
+static int pair_contact(const double a[3], double ra, const double b[3], double rb_, int* nb) {
+  double d = dist3(a, b);
+  if (fabs(d - (ra + rb_)) < ORC_BAND) (*nb)++;
+  return d < ra + rb_;
+}
+
+/* Snap-to-surface (Sec. 3.2): cast the sphere straight down from p and
+ * return the highest y <= p.y where the interpolated distance reaches
+ * `target` (= radius + resting clearance).  At fixed (x, z) the trilinear
+ * field is linear in y inside each cell, so the landing height is the exact
+ * root of that line in the first cell (walking down) whose lower value is at
+ * or below the target.  *ok = 0 when no such height exists in the lattice. */
+double orc_snap(const orc_scene* s, const double p[3], double target, int* ok, int* nb) {
+  double h = s->grid_h;
+  double d0, edge;
+  *ok = 0;
+  if (!orc_grid_query(s, p, &d0, &edge)) {
+    if (fabs(edge) < ORC_BAND) (*nb)++;
+    return p[1];
+  }
+  if (fabs(edge) < ORC_BAND) (*nb)++;
+  if (fabs(d0 - target) < ORC_BAND) (*nb)++;
+  if (d0 <= target) { *ok = 1; return p[1]; }
+  /* level j lies at y_j = origin_y + j h; the start cell is the one the
+   * trilinear query above used for p. */
+  double gy = (p[1] - (double)s->grid_origin[1]) / h;
+  int j = (int)floor(gy);
+  if (j > s->grid_dims[1] - 2) j = s->grid_dims[1] - 2;
+  double top = p[1], dtop = d0;
+  for (; j >= 0; --j) {
+    double yj = (double)s->grid_origin[1] + j * h;
+    double q[3] = {p[0], yj, p[2]};
+    double dj, e2;
+    orc_grid_query(s, q, &dj, &e2);
+    if (fabs(dj - target) < ORC_BAND) (*nb)++;
+    if (dj <= target) {
+      /* linear root between (yj, dj) and (top, dtop) */
+      double slope = (dtop - dj) / (top - yj > 0 ? top - yj : 1.0);
+      if (slope < 0.05) (*nb)++; /* flat crossing: height sensitive to rounding */
+      double y = (top > yj) ? yj + (target - dj) / (dtop - dj) * (top - yj) : yj;
+      *ok = 1;
+      return y;
+    }
+    top = yj;
+    dtop = dj;
+  }
+  return p[1];
+}
+
+/* ------------------------------------------------------------------------ */
+/* One environment step (Sec. 3.2, App. A).                                 */
+/* ------------------------------------------------------------------------ */
+void orc_step(const orc_robot* rb, const orc_scene* sc, orc_state* st, const float act[11],
+              orc_step_out* out) {
+  double a[11];
+  for (int k = 0; k < 11; ++k) a[k] = isfinite(act[k]) ? clampd(act[k], -1.0, 1.0) : 0.0;
+  int nb = 0;
+
+  /* candidate pose: translate along the pre-step heading, then turn; +1 on
+   * the turn action is clockwise seen from above (yaw decreases). */
+  double th = st->base[2];
+  double cb[3], cq[7];
+  cb[0] = st->base[0] + (double)rb->base_step * a[0] * cos(th);
+  cb[1] = st->base[1] - (double)rb->base_step * a[0] * sin(th);
+  cb[2] = wrap_pi(th - (double)rb->base_turn * a[1]);
+  for (int k = 0; k < 7; ++k)
+    cq[k] = clampd(st->q[k] + (double)rb->dq_max * a[2 + k], rb->q_min[k], rb->q_max[k]);
+
+  /* candidate spheres */
+  double links[8][12], ee[12], cam[12];
+  double cs[ORC_MAX_SPHERES][3];
+  orc_fk(rb, cb, cq, links, ee, NULL);
+  for (int i = 0; i < rb->n_spheres; ++i) {
+    double p[3] = {rb->sphere_pos[3 * i], rb->sphere_pos[3 * i + 1], rb->sphere_pos[3 * i + 2]};
+    fr_apply(links[rb->sphere_link[i]], p, cs[i]);
+  }
+  uint32_t mask = 0;
+  uint8_t flags = 0;
+  int h = st->held;
+  for (int i = 0; i < rb->n_spheres; ++i) {
+    double r = rb->sphere_radius[i];
+    if (static_contact(sc, cs[i], r, &nb)) { mask |= 1u << i; flags |= 1; }
+    for (int j = 0; j < st->n_obj; ++j) {
+      if (j == h) continue;
+      if (pair_contact(cs[i], r, st->obj[j], st->obj[j][3], &nb)) { mask |= 1u << i; flags |= 2; }
+    }
+  }
+  if (h >= 0) {
+    double ph[3];
+    fr_apply(ee, st->c_off, ph);
+    double rho = st->obj[h][3];
+    if (static_contact(sc, ph, rho, &nb)) { mask |= 1u << 30; flags |= 1 | 4; }
+    for (int j = 0; j < st->n_obj; ++j) {
+      if (j == h) continue;
+      if (pair_contact(ph, rho, st->obj[j], st->obj[j][3], &nb)) { mask |= 1u << 30; flags |= 2 | 4; }
+    }
+  }
+  /* resolution: any contact rejects all robot motion for this step */
+  int reverted = mask != 0;
+  if (!reverted) {
+    memcpy(st->base, cb, sizeof(cb));
+    memcpy(st->q, cq, sizeof(cq));
+  }
+  orc_fk(rb, st->base, st->q, links, ee, cam);
+
+  /* grasp / release at the accepted pose */
+  uint8_t event = 0;
+  int grasp = a[9] >= 0.5;
+  if (grasp && st->held < 0) {
+    double tip[3] = {ee[9], ee[10], ee[11]};
+    double rg = rb->grasp_radius;
+    int best = -1;
+    double bests = INFINITY;
+    for (int j = 0; j < st->n_obj; ++j) {
+      double d = dist3(tip, st->obj[j]);
+      if (fabs(d - (rg + st->obj[j][3])) < ORC_BAND) nb++;
+      if (d < rg + st->obj[j][3]) {
+        double sdist = d - st->obj[j][3];
+        if (best >= 0 && fabs(sdist - bests) < ORC_BAND) nb++;
+        if (sdist < bests) { bests = sdist; best = j; }
+      }
+    }
+    if (best >= 0) {
+      /* c_off = R_ee^T (p - t_ee) */
+      double dp[3] = {st->obj[best][0] - ee[9], st->obj[best][1] - ee[10], st->obj[best][2] - ee[11]};
+      for (int r = 0; r < 3; ++r) st->c_off[r] = ee[r] * dp[0] + ee[3 + r] * dp[1] + ee[6 + r] * dp[2];
+      memcpy(st->p_pre, st->obj[best], 3 * sizeof(double));
+      st->held = best;
+      event = 1;
+    } else {
+      event = 2;
+    }
+  } else if (!grasp && st->held >= 0) {
+    int j = st->held;
+    double p[3];
+    fr_apply(ee, st->c_off, p);
+    double rho = st->obj[j][3];
+    int ok = 0;
+    double y = orc_snap(sc, p, rho + (double)rb->rest_clearance, &ok, &nb);
+    double land[3] = {p[0], y, p[2]};
+    int overlap = 0;
+    if (ok)
+      for (int k = 0; k < st->n_obj; ++k)
+        if (k != j && pair_contact(land, rho, st->obj[k], st->obj[k][3], &nb)) overlap = 1;
+    if (ok && !overlap) {
+      memcpy(st->obj[j], land, sizeof(land));
+      event = 3;
+    } else {
+      memcpy(st->obj[j], st->p_pre, 3 * sizeof(double));
+      event = 4;
+    }
+    st->held = -1;
+    memset(st->c_off, 0, sizeof(st->c_off));
+  }
+  if (st->held >= 0) fr_apply(ee, st->c_off, st->obj[st->held]);
+  st->step_count += 1;
+
+  out->contact_mask = mask;
+  out->flags = flags;
+  out->event = event;
+  out->reverted = (uint8_t)reverted;
+  out->near_band = nb;
+  out->ee[0] = ee[9]; out->ee[1] = ee[10]; out->ee[2] = ee[11];
+  memcpy(out->cam_R, cam, 9 * sizeof(double));
+  memcpy(out->cam_t, cam + 9, 3 * sizeof(double));
+}
+
+/* ------------------------------------------------------------------------ */
+/* Reset: objects on support tops, then the robot base in free space, each  */
+/* by rejection sampling with at most 64 Philox draws.  Stream (env,        */
+/* episode, j, try): j = object index, 64 = robot.                          */
+/* ------------------------------------------------------------------------ */
+void orc_reset(const orc_robot* rb, const orc_scene* sc, orc_state* st, uint64_t seed,
+               int32_t env, int32_t n_obj, float rho_min, float rho_max, orc_reset_out* out) {
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  int nb = 0, failed = 0;
+  st->episode += 1;
+  st->n_obj = n_obj;
+  double clear = rb->rest_clearance;
+  for (int j = 0; j < n_obj; ++j) {
+    double rho = 0.0;
+    int ok = 0;
+    for (uint32_t t = 0; t < 64 && !ok; ++t) {
+      uint32_t ctr[4] = {(uint32_t)env, (uint32_t)st->episode, (uint32_t)j, t}, w[4];
+      orc_philox4x32_10(ctr, key, w);
+      if (t == 0) rho = (double)rho_min + unit24(w[3]) * ((double)rho_max - (double)rho_min);
+      uint32_t si = (uint32_t)(((uint64_t)(w[0] >> 8) * (uint64_t)sc->n_supports) >> 24);
+      const float* sp = sc->supports + 5 * si;
+      double x0 = sp[0] + rho, x1 = sp[2] - rho, z0 = sp[1] + rho, z1 = sp[3] - rho;
+      double p[3] = {x0 + unit24(w[1]) * (x1 - x0), (double)sp[4] + rho + clear,
+                     z0 + unit24(w[2]) * (z1 - z0)};
+      st->obj[j][0] = p[0]; st->obj[j][1] = p[1]; st->obj[j][2] = p[2]; st->obj[j][3] = rho;
+      ok = !static_contact(sc, p, rho, &nb);
+      for (int k = 0; k < j && ok; ++k)
+        if (pair_contact(p, rho, st->obj[k], st->obj[k][3], &nb)) ok = 0;
+    }
+    if (!ok) failed++;
+  }
+  double cs[ORC_MAX_SPHERES][3];
+  int ok = 0;
+  for (int k = 0; k < 7; ++k) st->q[k] = rb->q_rest[k];
+  for (uint32_t t = 0; t < 64 && !ok; ++t) {
+    uint32_t ctr[4] = {(uint32_t)env, (uint32_t)st->episode, 64u, t}, w[4];
+    orc_philox4x32_10(ctr, key, w);
+    const float* s = sc->spawn;
+    st->base[0] = s[0] + unit24(w[0]) * ((double)s[2] - (double)s[0]);
+    st->base[1] = s[1] + unit24(w[1]) * ((double)s[3] - (double)s[1]);
+    st->base[2] = -PI + unit24(w[2]) * (2 * PI);
+    orc_sphere_centres(rb, st->base, st->q, cs);
+    ok = 1;
+    for (int i = 0; i < rb->n_spheres; ++i) {
+      double r = rb->sphere_radius[i];
+      int c = static_contact(sc, cs[i], r, &nb);
+      for (int j = 0; j < n_obj; ++j) c |= pair_contact(cs[i], r, st->obj[j], st->obj[j][3], &nb);
+      if (c) ok = 0;
+    }
+  }
+  if (!ok) failed++;
+  st->held = -1;
+  memset(st->c_off, 0, sizeof(st->c_off));
+  memset(st->p_pre, 0, sizeof(st->p_pre));
+  st->step_count = 0;
+  out->near_band = nb;
+  out->failed = failed;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Rendering (Sec. 3.1): for every pixel centre, the nearest front-facing   */
+/* triangle hit by the camera ray at planar depth z >= near.  Depth is the  */
+/* camera-space forward distance of the hit, colour that triangle's flat    */
+/* colour; no hit gives 0 / black.  The result is the minimum over          */
+/* triangles, so it does not depend on visiting order: each triangle only   */
+/* evaluates pixel centres inside its projected bounding box (grown by one  */
+/* pixel), the only ones it can cover.                                      */
+/*                                                                          */
+/* Alongside the exact answer each pixel gets an "ambiguous" bit: true when */
+/* an FP32 fixed-point rasteriser could legitimately produce a different    */
+/* visible surface there -- a pixel centre within eps_px of an edge of a    */
+/* triangle that competes for the pixel, two surfaces within tol_rel in     */
+/* depth with different colours, or a grazing hit (|cos| < cos_min).        */
+/* ------------------------------------------------------------------------ */
+#define ORC_K 16
+typedef struct { double z, s, cosv; int32_t id; uint32_t rgb; } cand;
+
+static int clip_near(const double in[3][3], double near, double out[4][3]) {
+  int n = 0;
+  for (int k = 0; k < 3; ++k) {
+    const double* a = in[k];
+    const double* b = in[(k + 1) % 3];
+    int ain = a[2] >= near, bin = b[2] >= near;
+    if (ain) { memcpy(out[n++], a, 3 * sizeof(double)); }
+    if (ain != bin) {
+      double t = (near - a[2]) / (b[2] - a[2]);
+      out[n][0] = a[0] + t * (b[0] - a[0]);
+      out[n][1] = a[1] + t * (b[1] - a[1]);
+      out[n][2] = near;
+      n++;
+    }
+  }
+  return n;
+}
+
+static void render_tri(const double P[3][3], int32_t id, uint32_t col, const double cam[12],
+                       double near, int W, int H, double eps, cand* C, int* cnt, double* dropz,
+                       orc_render_stats* stats) {
+  const double* eye = cam + 9;
+  double e1[3], e2[3], n[3];
+  for (int a = 0; a < 3; ++a) { e1[a] = P[1][a] - P[0][a]; e2[a] = P[2][a] - P[0][a]; }
+  n[0] = e1[1] * e2[2] - e1[2] * e2[1];
+  n[1] = e1[2] * e2[0] - e1[0] * e2[2];
+  n[2] = e1[0] * e2[1] - e1[1] * e2[0];
+  double hpl = n[0] * (P[0][0] - eye[0]) + n[1] * (P[0][1] - eye[1]) + n[2] * (P[0][2] - eye[2]);
+  if (!(hpl < 0)) return; /* back-facing or edge-on */
+  double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+  /* camera-space vertices: columns of R are right, up, forward */
+  double Cv[3][3];
+  for (int k = 0; k < 3; ++k) {
+    double d[3] = {P[k][0] - eye[0], P[k][1] - eye[1], P[k][2] - eye[2]};
+    for (int c = 0; c < 3; ++c) Cv[k][c] = cam[c] * d[0] + cam[3 + c] * d[1] + cam[6 + c] * d[2];
+  }
+  double poly[4][3], uv[4][2];
+  int m = clip_near(Cv, near, poly);
+  if (m < 3) return;
+  double f = 0.5 * W, cx = 0.5 * W, cy = 0.5 * H;
+  double umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
+  for (int k = 0; k < m; ++k) {
+    uv[k][0] = cx + f * poly[k][0] / poly[k][2];
+    uv[k][1] = cy - f * poly[k][1] / poly[k][2];
+    umin = fmin(umin, uv[k][0]); umax = fmax(umax, uv[k][0]);
+    vmin = fmin(vmin, uv[k][1]); vmax = fmax(vmax, uv[k][1]);
+  }
+  double area2 = 0.0;
+  for (int k = 0; k < m; ++k) {
+    int l = (k + 1) % m;
+    area2 += uv[k][0] * uv[l][1] - uv[l][0] * uv[k][1];
+  }
+  if (area2 == 0.0) return;
+  double sgn = area2 > 0 ? 1.0 : -1.0;
+  int i0 = (int)floor(umin - 1.0), i1 = (int)ceil(umax + 1.0);
+  int j0 = (int)floor(vmin - 1.0), j1 = (int)ceil(vmax + 1.0);
+  if (i0 < 0) i0 = 0;
+  if (j0 < 0) j0 = 0;
+  if (i1 > W - 1) i1 = W - 1;
+  if (j1 > H - 1) j1 = H - 1;
+  if (i0 > i1 || j0 > j1) return;
+  /* a triangle counts as set up when some pixel centre lies in its bounding box */
+  if (ceil(umin - 0.5) <= fmin(floor(umax - 0.5), W - 1.0) && ceil(umax - 0.5) >= 0.0 &&
+      ceil(vmin - 0.5) <= fmin(floor(vmax - 0.5), H - 1.0) && ceil(vmax - 0.5) >= 0.0 &&
+      floor(umax - 0.5) >= 0.0 && floor(vmax - 0.5) >= 0.0)
+    stats->tris_setup++;
+  double len[4];
+  for (int k = 0; k < m; ++k) {
+    int l = (k + 1) % m;
+    len[k] = hypot(uv[l][0] - uv[k][0], uv[l][1] - uv[k][1]);
+  }
+  for (int j = j0; j <= j1; ++j)
+    for (int i = i0; i <= i1; ++i) {
+      double u = i + 0.5, v = j + 0.5;
+      double s = INFINITY;
+      for (int k = 0; k < m; ++k) {
+        int l = (k + 1) % m;
+        if (len[k] == 0.0) continue;
+        double e = (uv[l][0] - uv[k][0]) * (v - uv[k][1]) - (uv[l][1] - uv[k][1]) * (u - uv[k][0]);
+        double sd = sgn * e / len[k];
+        if (sd < s) s = sd;
+      }
+      if (!(s > -eps)) continue;
+      double dc[3] = {(u - cx) / f, -(v - cy) / f, 1.0};
+      double D[3];
+      for (int r = 0; r < 3; ++r) D[r] = cam[3 * r] * dc[0] + cam[3 * r + 1] * dc[1] + cam[3 * r + 2] * dc[2];
+      double nd = n[0] * D[0] + n[1] * D[1] + n[2] * D[2];
+      if (!(nd < 0)) continue;
+      double z = hpl / nd;
+      double dl = sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
+      if (s > 0) stats->frags_covered++;
+      cand c = {z, s, -nd / (nn * dl), id, col};
+      cand* L = C + (size_t)(j * W + i) * ORC_K;
+      int* nc = cnt + j * W + i;
+      /* keep the ORC_K nearest, sorted by z then id */
+      int pos = *nc;
+      while (pos > 0 && (L[pos - 1].z > z || (L[pos - 1].z == z && L[pos - 1].id > id))) pos--;
+      if (pos >= ORC_K) {
+        if (z < dropz[j * W + i]) dropz[j * W + i] = z;
+        continue;
+      }
+      if (*nc == ORC_K) {
+        double zl = L[ORC_K - 1].z;
+        if (zl < dropz[j * W + i]) dropz[j * W + i] = zl;
+      } else {
+        (*nc)++;
+      }
+      for (int q = *nc - 1; q > pos; --q) L[q] = L[q - 1];
+      L[pos] = c;
+    }
+}
+
+void orc_render(const orc_robot* rb, const orc_scene* sc, const orc_objmesh* om,
+                const orc_state* st, int32_t W, int32_t H, double eps_px, double tol_rel,
+                double cos_min, double* depth, uint32_t* rgb, uint8_t* ambiguous,
+                int32_t* winner, orc_render_stats* stats) {
+  double links[8][12], cam[12];
+  orc_fk(rb, st->base, st->q, links, NULL, cam);
+  size_t np = (size_t)W * H;
+  cand* C = (cand*)malloc(np * ORC_K * sizeof(cand));
+  int* cnt = (int*)calloc(np, sizeof(int));
+  double* dropz = (double*)malloc(np * sizeof(double));
+  for (size_t p = 0; p < np; ++p) dropz[p] = INFINITY;
+  orc_render_stats local = {0, 0, 0, 0};
+  double near = rb->cam_near;
+  double P[3][3];
+  for (int t = 0; t < sc->n_tris; ++t) {
+    for (int k = 0; k < 3; ++k)
+      for (int a = 0; a < 3; ++a) P[k][a] = sc->verts[3 * sc->tris[3 * t + k] + a];
+    render_tri(P, t, sc->tri_rgb[t], cam, near, W, H, eps_px, C, cnt, dropz, &local);
+  }
+  for (int j = 0; j < st->n_obj; ++j) {
+    for (int t = 0; t < om->n_tris; ++t) {
+      for (int k = 0; k < 3; ++k)
+        for (int a = 0; a < 3; ++a)
+          P[k][a] = st->obj[j][a] + st->obj[j][3] * (double)om->verts[3 * om->tris[3 * t + k] + a];
+      render_tri(P, sc->n_tris + j * om->n_tris + t, om->obj_rgb[j], cam, near, W, H, eps_px, C,
+                 cnt, dropz, &local);
+    }
+  }
+  for (size_t p = 0; p < np; ++p) {
+    cand* L = C + p * ORC_K;
+    int nc = cnt[p];
+    int w = -1;
+    double zD = INFINITY;
+    for (int q = 0; q < nc; ++q) {
+      if (w < 0 && L[q].s > 0) w = q;
+      if (L[q].s > eps_px && L[q].z < zD) zD = L[q].z;
+    }
+    uint8_t amb = 0;
+    double zw = w >= 0 ? L[w].z : INFINITY;
+    if (dropz[p] <= zD * (1 + tol_rel)) { amb = 1; local.overflow++; }
+    for (int q = 0; q < nc; ++q) {
+      if (!(L[q].z <= zD * (1 + tol_rel))) continue; /* loses the depth test */
+      if (w < 0) { amb = 1; break; }                  /* marginal vs background */
+      if (L[q].rgb != L[w].rgb || fabs(L[q].z - zw) > tol_rel * zw) { amb = 1; break; }
+    }
+    if (w >= 0 && L[w].cosv < cos_min) amb = 1;
+    depth[p] = w >= 0 ? zw : 0.0;
+    rgb[p] = w >= 0 ? L[w].rgb : 0u;
+    if (winner) winner[p] = w >= 0 ? L[w].id : -1;
+    ambiguous[p] = amb;
+    local.ambiguous += amb;
+  }
+  if (stats) *stats = local;
+  free(C);
+  free(cnt);
+  free(dropz);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Neural SDF: d(x) = W_L relu(... relu(W_1 gamma(x) + b_1) ...) + b_L with  */
+/* Fourier features gamma(x) = [sin(2 pi B x), cos(2 pi B x)].              */
+/* dims = {2F, h1, ..., 1}; W[l] is row-major [dims[l+1]][dims[l]].         */
+/* ------------------------------------------------------------------------ */
+static void mlp_acts(const double* B, int F, const double* const* W, const double* const* b,
+                     const int* dims, int L, const double x[3], double* A) {
+  /* A holds layer inputs back to back: a_0 (2F), a_1, ..., a_L (1) */
+  for (int k = 0; k < F; ++k) {
+    double ph = 2 * PI * (B[3 * k] * x[0] + B[3 * k + 1] * x[1] + B[3 * k + 2] * x[2]);
+    A[k] = sin(ph);
+    A[F + k] = cos(ph);
+  }
+  double* in = A;
+  for (int l = 0; l < L; ++l) {
+    double* o = in + dims[l];
+    for (int r = 0; r < dims[l + 1]; ++r) {
+      double s = b[l][r];
+      for (int c = 0; c < dims[l]; ++c) s += W[l][(size_t)r * dims[l] + c] * in[c];
+      o[r] = (l < L - 1 && s < 0) ? 0.0 : s;
+    }
+    in = o;
+  }
+}
+
+double orc_mlp_forward(const double* B, int F, const double* const* W, const double* const* b,
+                       const int* dims, int L, const double x[3], double* acts) {
+  int tot = 0;
+  for (int l = 0; l <= L; ++l) tot += dims[l];
+  double* A = acts ? acts : (double*)malloc(tot * sizeof(double));
+  mlp_acts(B, F, W, b, dims, L, x, A);
+  double y = A[tot - 1];
+  if (!acts) free(A);
+  return y;
+}
+
+/* Mean L1 loss against clamped labels and its exact gradient (backprop). */
+double orc_mlp_loss_grad(const double* B, int F, const double* const* W, const double* const* b,
+                         const int* dims, int L, const double* X, const double* y, int n,
+                         double lo, double hi, double* const* gW, double* const* gb) {
+  int tot = 0, maxw = 0;
+  for (int l = 0; l <= L; ++l) { tot += dims[l]; if (dims[l] > maxw) maxw = dims[l]; }
+  for (int l = 0; l < L; ++l) {
+    memset(gW[l], 0, (size_t)dims[l] * dims[l + 1] * sizeof(double));
+    memset(gb[l], 0, (size_t)dims[l + 1] * sizeof(double));
+  }
+  double* A = (double*)malloc(tot * sizeof(double));
+  double* g = (double*)malloc(maxw * sizeof(double));
+  double* g2 = (double*)malloc(maxw * sizeof(double));
+  double loss = 0.0;
+  for (int s = 0; s < n; ++s) {
+    mlp_acts(B, F, W, b, dims, L, X + 3 * s, A);
+    double pred = A[tot - 1];
+    double t = clampd(y[s], lo, hi);
+    loss += fabs(pred - t);
+    g[0] = (pred > t ? 1.0 : (pred < t ? -1.0 : 0.0)) / n;
+    /* walk layers backwards; offsets of a_l in A */
+    int off[16];
+    off[0] = 0;
+    for (int l = 0; l < L; ++l) off[l + 1] = off[l] + dims[l];
+    for (int l = L - 1; l >= 0; --l) {
+      const double* in = A + off[l];
+      const double* outv = A + off[l + 1];
+      /* g is dLoss/d(pre-activation of layer l) once the ReLU mask is applied */
+      if (l < L - 1)
+        for (int r = 0; r < dims[l + 1]; ++r)
+          if (!(outv[r] > 0)) g[r] = 0.0;
+      for (int r = 0; r < dims[l + 1]; ++r) {
+        gb[l][r] += g[r];
+        for (int c = 0; c < dims[l]; ++c) gW[l][(size_t)r * dims[l] + c] += g[r] * in[c];
+      }
+      if (l > 0) {
+        for (int c = 0; c < dims[l]; ++c) {
+          double acc = 0.0;
+          for (int r = 0; r < dims[l + 1]; ++r) acc += W[l][(size_t)r * dims[l] + c] * g[r];
+          g2[c] = acc;
+        }
+        memcpy(g, g2, dims[l] * sizeof(double));
+      }
+    }
+  }
+  free(A);
+  free(g);
+  free(g2);
+  return loss / n;
+}

@@ -1,0 +1,124 @@
+/*
+ * gx_oracle.h -- plain, single-threaded FP64 CPU oracle for the batched
+ * environment step of Galactic (arXiv 2306.07552, Sec. 3.2 and the appendix
+ * "Additional Collision-Detection Details").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the bench's
+ * CPU-baseline leg may load this library.  It shares no code with the CUDA
+ * path: it reads the same *inputs* (robot table, scene boxes and triangles,
+ * actions) and recomputes every step of the method from its definition, in
+ * double precision, one environment at a time.
+ *
+ * Parity pins (tests/test_oracle_pins.py): every function here is checked
+ * against closed forms, hand-computed poses, published known-answer vectors
+ * or brute force on tiny inputs.  The neural-SDF MLP is pinned by central
+ * finite differences and a one-layer closed-form gradient.
+ */
+#ifndef GX_ORACLE_H
+#define GX_ORACLE_H
+#include <stdint.h>
+
+#define ORC_MAX_OBJ 64
+#define ORC_MAX_SPHERES 32
+#define ORC_BAND 1e-4 /* m: decisions this close to their threshold are "near band" */
+
+typedef struct {
+  const float* link_offset;   /* [8][3]: o_1..o_7, tool tip                 */
+  const int32_t* link_axis;   /* [7]: 0 x, 1 y, 2 z                          */
+  const float* q_min;         /* [7]                                         */
+  const float* q_max;         /* [7]                                         */
+  const float* q_rest;        /* [7]                                         */
+  float dq_max, base_step, base_turn;
+  int32_t n_spheres;
+  const int32_t* sphere_link; /* [S]                                         */
+  const float* sphere_pos;    /* [S][3] in the link frame                    */
+  const float* sphere_radius; /* [S]                                         */
+  const float* cam_pos;       /* [3] in the base frame                       */
+  float cam_pitch, cam_near, grasp_radius, rest_clearance;
+} orc_robot;
+
+typedef struct {
+  int32_t n_boxes;   const float* boxes;     /* [B][6] min xyz, max xyz     */
+  int32_t n_verts;   const float* verts;     /* [V][3]                      */
+  int32_t n_tris;    const int32_t* tris;    /* [T][3]                      */
+  const uint32_t* tri_rgb;                   /* [T]                         */
+  int32_t n_supports; const float* supports; /* [P][5] x0 z0 x1 z1 top      */
+  float grid_origin[3]; float grid_h; int32_t grid_dims[3];
+  float spawn[4];                            /* x0 z0 x1 z1                 */
+} orc_scene;
+
+typedef struct {
+  int32_t n_verts; const float* verts;       /* unit instance mesh          */
+  int32_t n_tris;  const int32_t* tris;
+  const uint32_t* obj_rgb;                   /* [ORC_MAX_OBJ] colours       */
+} orc_objmesh;
+
+typedef struct {
+  double base[3];           /* x, z, yaw                                    */
+  double q[7];
+  int32_t held;             /* -1: nothing held                             */
+  double c_off[3];          /* held object centre in the tool-tip frame     */
+  double p_pre[3];          /* held object's resting position before grasp  */
+  int32_t n_obj;
+  double obj[ORC_MAX_OBJ][4]; /* x y z rho                                  */
+  int32_t step_count;
+  int32_t episode;
+} orc_state;
+
+typedef struct {
+  uint32_t contact_mask;    /* bit i robot sphere i, bit 30 attached object */
+  uint8_t flags;            /* 1 static, 2 object, 4 attached               */
+  uint8_t event;            /* 0 none 1 grasp 2 miss 3 landed 4 restored    */
+  uint8_t reverted;
+  uint8_t pad;
+  int32_t near_band;        /* decisions within ORC_BAND of threshold       */
+  double ee[3];
+  double cam_R[9];          /* camera-to-world, columns right, up, forward  */
+  double cam_t[3];
+} orc_step_out;
+
+typedef struct {
+  int32_t near_band;
+  int32_t failed;           /* placements that used all tries               */
+} orc_reset_out;
+
+typedef struct {
+  int64_t tris_setup;       /* front-facing triangles reaching the image    */
+  int64_t frags_covered;    /* pixel centres strictly inside them           */
+  int64_t ambiguous;
+  int64_t overflow;
+} orc_render_stats;
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+double orc_box_sdf(const double p[3], const float box[6]);
+double orc_grid_node(const orc_scene* s, int i, int j, int k);
+int orc_grid_query(const orc_scene* s, const double c[3], double* d, double* edge);
+void orc_fk(const orc_robot* rb, const double base[3], const double q[7],
+            double links[8][12], double ee[12], double cam[12]);
+void orc_sphere_centres(const orc_robot* rb, const double base[3], const double q[7],
+                        double out[][3]);
+void orc_step(const orc_robot* rb, const orc_scene* sc, orc_state* st, const float act[11],
+              orc_step_out* out);
+void orc_reset(const orc_robot* rb, const orc_scene* sc, orc_state* st, uint64_t seed,
+               int32_t env, int32_t n_obj, float rho_min, float rho_max, orc_reset_out* out);
+double orc_snap(const orc_scene* s, const double p[3], double target, int* ok, int* near_band);
+void orc_render(const orc_robot* rb, const orc_scene* sc, const orc_objmesh* om,
+                const orc_state* st, int32_t W, int32_t H, double eps_px, double tol_rel,
+                double cos_min, double* depth, uint32_t* rgb, uint8_t* ambiguous,
+                int32_t* winner, orc_render_stats* stats);
+
+/* Neural SDF (Fourier-feature MLP) in FP64: forward and backward. */
+double orc_mlp_forward(const double* B /*[F][3]*/, int F, const double* const* W,
+                       const double* const* b, const int* dims, int n_layers, const double x[3],
+                       double* acts /* optional scratch: sum(dims) */);
+double orc_mlp_loss_grad(const double* B, int F, const double* const* W, const double* const* b,
+                         const int* dims, int n_layers, const double* X /*[n][3]*/,
+                         const double* y /*[n]*/, int n, double clamp_lo, double clamp_hi,
+                         double* const* gW, double* const* gb);
+#ifdef __cplusplus
+}
+#endif
+#endif
