@@ -1,0 +1,207 @@
+/*
+ * gx.h -- C ABI of the batched environment step of Galactic
+ * (arXiv 2306.07552) on one B300 GPU.
+ *
+ * One call advances every environment by one step (Sec. 3.1 "Batching": one
+ * simulator instance steps all environments and shares scene assets across
+ * them).  A step applies the action offsets to the robot state, runs forward
+ * kinematics, tests the robot's collision spheres against the static scene
+ * and the movable objects, rejects all robot motion on contact, grasps or
+ * releases objects (Sec. 3.2 "Approximate Kinematic Simulation"), and renders
+ * each environment's egocentric depth and RGB camera (Sec. 3.1; 128x128,
+ * 90-degree FOV, Sec. 4.1) into caller-owned device buffers, which is the
+ * zero-copy hand-off of Sec. 3.1.
+ *
+ * Conventions (all sides):
+ *   - world is Y-up, the floor is the XZ plane, units are metres and radians;
+ *   - robot base frame: Trans(x, 0, z) Ry(yaw); "forward" is +x of that frame;
+ *   - camera space: x right, y up, z forward; pixel (i, j) has its centre at
+ *     (i + 0.5, j + 0.5), i to the right, j downward; focal length W/2
+ *     (90-degree horizontal FOV); depth is planar camera-space z, 0 = no hit;
+ *   - images are row-major [env][row][col] (RGB: [env][row][col][3], R first).
+ *
+ * Errors: every entry point returns a gx_status.  Arguments the host can
+ * check are validated before any GPU work and return GX_EINVAL with nothing
+ * launched.  Problems only the device can see (non-finite actions, which are
+ * then treated as 0; placements that used all their tries) set a device error
+ * word; it is read without blocking on the next gx_step/gx_reset and reported
+ * as GX_EDEVICE there or by gx_sync.  The library never traps the GPU and
+ * every device loop is bounded.  gx_last_error() gives a message.
+ *
+ * Threading: one context per host thread.  Calls are asynchronous on the
+ * caller's stream (a cudaStream_t passed as void*; NULL = legacy default
+ * stream).  Scene sets are immutable after creation and may be shared by
+ * several contexts; a scene set must outlive the contexts using it.
+ */
+#ifndef GX_H
+#define GX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GX_OK = 0,
+  GX_EINVAL = 1,   /* bad argument, detected on the host; nothing launched   */
+  GX_ENOMEM = 2,   /* device or host allocation failed                        */
+  GX_ECUDA = 3,    /* a CUDA runtime call failed                              */
+  GX_EDEVICE = 4,  /* the device error word was set (see gx_last_error)       */
+  GX_ESTATE = 5    /* call not valid in the current state                     */
+} gx_status;
+
+/* device error word bits (gx_device_error) */
+#define GX_DEV_NONFINITE_ACTION 0x1u  /* some action was NaN/Inf; used 0     */
+#define GX_DEV_PLACEMENT_FAILED 0x2u  /* a reset placement used all 64 tries */
+
+#define GX_MAX_OBJECTS 64
+#define GX_MAX_SPHERES 31
+
+/* Robot description (FP32, host memory, copied at gx_create).
+ * Sec. 3.2: the robot is an articulated chain moved kinematically; each link
+ * is approximated by hand-placed spheres (appendix "Additional
+ * Collision-Detection Details").  Link k's frame sits at joint k:
+ *   T_0 = Trans(x, 0, z) Ry(yaw),  T_k = T_{k-1} Trans(o_k) Rot(axis_k, q_k),
+ *   tool tip T_ee = T_7 Trans(o_tip),  camera T_cam = T_0 Trans(cam_pos) M,
+ * M having columns right (0,0,-1), up (-sin p, cos p, 0), forward
+ * (cos p, sin p, 0) for pitch p. */
+typedef struct {
+  float link_offset[8][3];  /* o_1..o_7, then o_tip                         */
+  int32_t link_axis[7];     /* 0 = x, 1 = y, 2 = z                           */
+  float q_min[7], q_max[7]; /* joint limits (rad)                            */
+  float q_rest[7];          /* joints after a reset                          */
+  float dq_max;             /* joint offset per step at |action| = 1 (rad)   */
+  float base_step;          /* base translation at |action| = 1 (App. A: 0.10 m) */
+  float base_turn;          /* base rotation at |action| = 1 (App. A: 5 deg) */
+  int32_t n_spheres;        /* <= 30: bit 30 of contact masks is reserved    */
+  int32_t sphere_link[GX_MAX_SPHERES];   /* 0 = base, k = link k            */
+  float sphere_pos[GX_MAX_SPHERES][3];   /* centre in the link frame        */
+  float sphere_radius[GX_MAX_SPHERES];
+  float cam_pos[3];         /* head camera in the base frame                 */
+  float cam_pitch;          /* rad; negative looks down                      */
+  float cam_near;           /* near plane (m), > 0                           */
+  float grasp_radius;       /* suction sphere at the tool tip (Sec. 3.2: 0.03 m) */
+  float rest_clearance;     /* resting objects sit this far above contact (m) */
+} gx_robot;
+
+/* One static scene, host memory, read during gx_scene_set_create only.
+ * boxes: the solids the signed-distance grid is built from (union of boxes);
+ * verts/tris/tri_rgb: the triangles rendered (front face counter-clockwise
+ * seen from outside, so outward normal = (v1-v0) x (v2-v0));
+ * supports: rectangles objects are placed on at reset (x0 z0 x1 z1 top_y);
+ * grid: node (i,j,k) at origin + (i,j,k) * h, dims = (nx, ny, nz);
+ * spawn: x0 z0 x1 z1 region sampled for the robot base at reset. */
+typedef struct {
+  int32_t n_boxes;    const float* boxes;     /* [n_boxes][6] min xyz max xyz */
+  int32_t n_verts;    const float* verts;     /* [n_verts][3]                 */
+  int32_t n_tris;     const int32_t* tris;    /* [n_tris][3]                  */
+  const uint32_t* tri_rgb;                    /* [n_tris] 0x00RRGGBB          */
+  int32_t n_supports; const float* supports;  /* [n_supports][5], >= 1        */
+  float grid_origin[3];
+  float grid_h;                               /* node spacing (m)             */
+  int32_t grid_dims[3];                       /* each >= 2                    */
+  float spawn[4];
+} gx_scene_desc;
+
+/* Instance mesh for free objects (unit circumradius; scaled by each object's
+ * radius) and one colour per object index. */
+typedef struct {
+  int32_t n_verts;    const float* verts;     /* [n_verts][3], <= 32          */
+  int32_t n_tris;     const int32_t* tris;    /* [n_tris][3], <= 32           */
+  uint32_t obj_rgb[GX_MAX_OBJECTS];
+} gx_object_mesh;
+
+typedef struct gx_scene_set gx_scene_set;
+typedef struct gx_ctx gx_ctx;
+
+typedef struct {
+  int32_t n_envs;          /* >= 1                                            */
+  int32_t img_w, img_h;    /* multiples of 32, <= 256                         */
+  int32_t depth_fp16;      /* 0: depth as float32, 1: as IEEE half            */
+  int32_t render_rgb;      /* 0: skip the RGB image                           */
+  int32_t n_objects;       /* free objects per environment, <= 64             */
+  float obj_radius_min, obj_radius_max;   /* object radius drawn at reset     */
+  uint64_t seed;           /* Philox key for resets                           */
+  const int32_t* env_scene; /* host [n_envs] scene per env; NULL: env i uses
+                               scene floor(i * n_scenes / n_envs)             */
+  int32_t raster_regions;  /* horizontal bands per image (0 = library choice) */
+  int32_t small_tri_px;    /* bbox pixel count rasterised per lane (0 = default) */
+  int32_t use_graph;       /* 1: replay the step as a captured CUDA graph     */
+} gx_config;
+
+/* Outputs of one step, device memory owned by the caller (e.g. torch
+ * tensors), written in place.  NULL members are skipped, except that depth
+ * is required.  pose: [n][16] = q0..q6, holding (0/1), base x, base z, yaw,
+ * tool tip x, y, z (world), step counter, 0. */
+typedef struct {
+  void* depth;             /* [n][h][w] float32 or half                       */
+  uint8_t* rgb;            /* [n][h][w][3] (only if render_rgb)               */
+  float* pose;             /* [n][16]                                         */
+  float* obj_pos;          /* [n][n_objects][4] x y z radius                  */
+  int32_t* held;           /* [n] held object index or -1                     */
+  uint32_t* contact_mask;  /* [n] bit i robot sphere i, bit 30 held object    */
+  uint8_t* contact_flags;  /* [n] 1 static, 2 object, 4 held object           */
+  uint8_t* event;          /* [n] 0 none, 1 grasped, 2 grasp missed,
+                              3 released and landed, 4 released and restored */
+} gx_outputs;
+
+/* Builds the device copies of `n_scenes` scenes: the FP32 signed-distance
+ * grid of each (computed on the GPU in FP64 from the boxes, then rounded),
+ * the triangle clusters used by the rasteriser, supports and spawn regions,
+ * and the object instance mesh.  Blocks until done.
+ * Errors: GX_EINVAL (NULL pointers, counts out of range), GX_ENOMEM, GX_ECUDA. */
+gx_status gx_scene_set_create(const gx_scene_desc* scenes, int32_t n_scenes,
+                              const gx_object_mesh* mesh, gx_scene_set** out);
+gx_status gx_scene_set_destroy(gx_scene_set* set);
+
+/* Allocates the structure-of-arrays state for cfg->n_envs environments on
+ * the current device, borrowing `set`.  All environments start unplaced:
+ * call gx_reset (mask NULL) before the first gx_step.
+ * Errors: GX_EINVAL, GX_ENOMEM, GX_ECUDA. */
+gx_status gx_create(const gx_scene_set* set, const gx_robot* robot, const gx_config* cfg,
+                    gx_ctx** out);
+void gx_destroy(gx_ctx* ctx);
+
+/* Starts a new episode in every environment whose byte in env_mask (device,
+ * [n_envs]) is non-zero, or in all when env_mask is NULL: objects are placed
+ * on support tops and the robot base in free space by rejection sampling
+ * (at most 64 Philox4x32-10 draws each, keyed by (seed, env, episode)), the
+ * joints go to q_rest and nothing is held.  Asynchronous. */
+gx_status gx_reset(gx_ctx* ctx, const uint8_t* env_mask, void* stream);
+
+/* Advances every environment by one step.  actions: device [n_envs][11]
+ * float32 = base forward, base turn (+1 clockwise seen from above), 7 joint
+ * offsets, grasp (>= 0.5 grasps, else releases), stop (ignored); each value
+ * is clipped to [-1, 1] (App. A).  Asynchronous on `stream`. */
+gx_status gx_step(gx_ctx* ctx, const float* actions, const gx_outputs* out, void* stream);
+
+/* Same step with HOST buffers: copies the actions (pinned host memory is
+ * fastest) to the device, steps, and copies every non-NULL output back into
+ * the host buffers of `out` (same layouts as gx_outputs).  Blocks until the
+ * copies are complete. */
+gx_status gx_step_host(gx_ctx* ctx, const float* actions_host, const gx_outputs* host_out,
+                       void* stream);
+
+/* Waits for all work of ctx and reports the device error word. */
+gx_status gx_sync(gx_ctx* ctx);
+uint32_t gx_device_error(gx_ctx* ctx); /* waits, returns and clears the word */
+
+/* Environment state as one host blob (layout: see gx_state_layout). */
+size_t gx_state_bytes(const gx_ctx* ctx);
+gx_status gx_save_state(gx_ctx* ctx, void* host, size_t bytes);
+gx_status gx_load_state(gx_ctx* ctx, const void* host, size_t bytes);
+/* Byte offsets of the state arrays, in this order: base_x, base_z, yaw
+ * [n] f32; q [7][n] f32; held [n] i32; c_off [3][n] f32 (held object in the
+ * tool-tip frame); p_pre [3][n] f32 (its pre-grasp position); obj
+ * [n][n_objects][4] f32 (x, y, z, radius); step [n] i32; episode [n] i32.
+ * Each array starts on a 256-byte boundary of the blob. */
+gx_status gx_state_layout(const gx_ctx* ctx, size_t offsets[10]);
+
+const char* gx_last_error(const gx_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GX_H */

@@ -1,0 +1,534 @@
+// Host implementation of the C ABI declared in include/gx.h.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gx_internal.h"
+
+using namespace gx;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct gx_scene_set {
+  int n = 0;
+  std::vector<DScene> host;
+  DScene* d_scenes = nullptr;
+  std::vector<void*> allocs;
+  float4* omesh_v = nullptr;
+  uint32_t* omesh_t = nullptr;
+  uint32_t* obj_rgb = nullptr;
+  int omesh_nv = 0, omesh_nt = 0;
+  std::vector<int> meshlets_per_scene;
+};
+
+struct gx_ctx {
+  const gx_scene_set* set = nullptr;
+  gx_config cfg{};
+  int n = 0, M = 0, regions = 1, region_h = 0, small_px = 0;
+  float near_ = 0.05f;
+  Robot* d_robot = nullptr;
+  int* d_env_scene = nullptr;
+  void* d_state = nullptr;
+  size_t state_bytes = 0;
+  size_t off[10] = {0};
+  StateView st{};
+  float* d_cam = nullptr;
+  unsigned* d_err = nullptr;
+  unsigned* h_err = nullptr;
+  cudaEvent_t ev_err = nullptr;
+  bool err_pending = false;
+  unsigned dev_err_seen = 0;
+  std::string msg;
+  // graph replay
+  cudaGraphExec_t gexec = nullptr;
+  const float* g_actions = nullptr;
+  gx_outputs g_out{};
+  // buffers for gx_step_host
+  float* h2d_actions = nullptr;
+  gx_outputs dev_out{};
+  std::vector<void*> host_step_allocs;
+};
+
+namespace {
+
+gx_status fail(gx_ctx* c, gx_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) c->msg = buf;
+  g_last_error = buf;
+  return s;
+}
+
+#define CK(ctx, call)                                                                     \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? GX_ENOMEM : GX_ECUDA, "%s: %s", \
+                  #call, cudaGetErrorString(e_));                                         \
+  } while (0)
+
+template <class T>
+cudaError_t upload(gx_scene_set* s, T** dst, const T* src, size_t count) {
+  *dst = nullptr;
+  if (count == 0) return cudaSuccess;
+  cudaError_t e = cudaMalloc((void**)dst, count * sizeof(T));
+  if (e != cudaSuccess) return e;
+  s->allocs.push_back(*dst);
+  return cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+void free_set(gx_scene_set* s) {
+  if (!s) return;
+  for (void* p : s->allocs) cudaFree(p);
+  delete s;
+}
+
+// Reads the device error word if its asynchronous copy has landed.
+gx_status poll_device_error(gx_ctx* c, bool wait) {
+  if (!c->err_pending) return GX_OK;
+  if (wait) {
+    if (cudaEventSynchronize(c->ev_err) != cudaSuccess)
+      return fail(c, GX_ECUDA, "cudaEventSynchronize failed");
+  } else if (cudaEventQuery(c->ev_err) != cudaSuccess) {
+    return GX_OK;
+  }
+  c->err_pending = false;
+  const unsigned v = *c->h_err;
+  if (v) {
+    *c->h_err = 0;
+    c->dev_err_seen |= v;
+    cudaMemset(c->d_err, 0, sizeof(unsigned));
+    return fail(c, GX_EDEVICE, "device error word 0x%x:%s%s%s", v,
+                (v & GX_DEV_NONFINITE_ACTION) ? " non-finite action (used 0)" : "",
+                (v & GX_DEV_PLACEMENT_FAILED) ? " reset placement used all tries" : "",
+                (v & kErrWaitTimeout) ? " bounded wait gave up" : "");
+  }
+  return GX_OK;
+}
+
+gx_status post_error_copy(gx_ctx* c, cudaStream_t s) {
+  CK(c, cudaMemcpyAsync(c->h_err, c->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  CK(c, cudaEventRecord(c->ev_err, s));
+  c->err_pending = true;
+  return GX_OK;
+}
+
+bool same_outputs(const gx_outputs& a, const gx_outputs& b) {
+  return std::memcmp(&a, &b, sizeof(gx_outputs)) == 0;
+}
+
+void enqueue_step(gx_ctx* c, const float* actions, const gx_outputs& out, cudaStream_t s) {
+  PhysicsParams pp{};
+  pp.n = c->n;
+  pp.M = c->M;
+  pp.scenes = c->set->d_scenes;
+  pp.env_scene = c->d_env_scene;
+  pp.robot = c->d_robot;
+  pp.actions = actions;
+  pp.st = c->st;
+  pp.cam = c->d_cam;
+  pp.out = out;
+  pp.err = c->d_err;
+  launch_physics(pp, s);
+  RasterParams rp{};
+  rp.n = c->n;
+  rp.M = c->M;
+  rp.W = c->cfg.img_w;
+  rp.H = c->cfg.img_h;
+  rp.regions = c->regions;
+  rp.region_h = c->region_h;
+  rp.small_px = c->small_px;
+  rp.scenes = c->set->d_scenes;
+  rp.env_scene = c->d_env_scene;
+  rp.cam = c->d_cam;
+  rp.obj = c->st.obj;
+  rp.omesh_v = c->set->omesh_v;
+  rp.omesh_t = c->set->omesh_t;
+  rp.omesh_nv = c->set->omesh_nv;
+  rp.omesh_nt = c->set->omesh_nt;
+  rp.obj_rgb = c->set->obj_rgb;
+  rp.near_ = c->near_;
+  rp.depth = out.depth;
+  rp.depth_fp16 = c->cfg.depth_fp16;
+  rp.rgb = c->cfg.render_rgb ? out.rgb : nullptr;
+  rp.err = c->d_err;
+  launch_raster(rp, s);
+}
+
+}  // namespace
+
+// ===========================================================================
+// scene sets
+// ===========================================================================
+extern "C" gx_status gx_scene_set_create(const gx_scene_desc* scenes, int32_t n_scenes,
+                                         const gx_object_mesh* mesh, gx_scene_set** out) {
+  if (!out) return fail(nullptr, GX_EINVAL, "gx_scene_set_create: out is NULL");
+  *out = nullptr;
+  if (!scenes || n_scenes < 1) return fail(nullptr, GX_EINVAL, "need at least one scene");
+  if (!mesh || mesh->n_verts < 1 || mesh->n_verts > 32 || mesh->n_tris < 1 ||
+      mesh->n_tris > 32 || !mesh->verts || !mesh->tris)
+    return fail(nullptr, GX_EINVAL, "object mesh must have 1..32 vertices and triangles");
+  for (int i = 0; i < n_scenes; ++i) {
+    const gx_scene_desc& d = scenes[i];
+    if (d.n_boxes < 1 || !d.boxes || d.n_boxes > 4096)
+      return fail(nullptr, GX_EINVAL, "scene %d: need 1..4096 boxes", i);
+    if (d.n_tris < 0 || (d.n_tris > 0 && (!d.verts || !d.tris || !d.tri_rgb)) || d.n_verts < 0)
+      return fail(nullptr, GX_EINVAL, "scene %d: bad triangle arrays", i);
+    for (int t = 0; t < 3 * d.n_tris; ++t)
+      if (d.tris[t] < 0 || d.tris[t] >= d.n_verts)
+        return fail(nullptr, GX_EINVAL, "scene %d: triangle index out of range", i);
+    if (d.n_supports < 1 || !d.supports) return fail(nullptr, GX_EINVAL, "scene %d: no supports", i);
+    if (!(d.grid_h > 0.f) || d.grid_dims[0] < 2 || d.grid_dims[1] < 2 || d.grid_dims[2] < 2)
+      return fail(nullptr, GX_EINVAL, "scene %d: bad grid", i);
+    if ((double)d.grid_dims[0] * d.grid_dims[1] * d.grid_dims[2] > 2.0e9)
+      return fail(nullptr, GX_EINVAL, "scene %d: grid too large", i);
+  }
+  for (int t = 0; t < 3 * mesh->n_tris; ++t)
+    if (mesh->tris[t] < 0 || mesh->tris[t] >= mesh->n_verts)
+      return fail(nullptr, GX_EINVAL, "object mesh: index out of range");
+
+  gx_scene_set* s = new gx_scene_set();
+  s->n = n_scenes;
+  s->host.resize(n_scenes);
+  auto bail = [&](cudaError_t e, const char* what) {
+    free_set(s);
+    return fail(nullptr, e == cudaErrorMemoryAllocation ? GX_ENOMEM : GX_ECUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+  };
+  cudaError_t e;
+  for (int i = 0; i < n_scenes; ++i) {
+    const gx_scene_desc& d = scenes[i];
+    DScene& ds = s->host[i];
+    HostMeshlets hm;
+    build_meshlets(d, hm);
+    s->meshlets_per_scene.push_back((int)(hm.hdr.size() / 3));
+    if ((e = upload(s, (float4**)&ds.mhdr, hm.hdr.data(), hm.hdr.size())) != cudaSuccess)
+      return bail(e, "upload meshlets");
+    if ((e = upload(s, (float4**)&ds.mverts, hm.verts.data(), hm.verts.size())) != cudaSuccess)
+      return bail(e, "upload vertices");
+    if ((e = upload(s, (uint32_t**)&ds.mtris, hm.tris.data(), hm.tris.size())) != cudaSuccess)
+      return bail(e, "upload triangles");
+    if ((e = upload(s, (uint32_t**)&ds.tri_rgb, hm.rgb.data(), hm.rgb.size())) != cudaSuccess)
+      return bail(e, "upload colours");
+    ds.n_meshlets = (int)(hm.hdr.size() / 3);
+    ds.n_tris = (int)hm.tris.size();
+    if ((e = upload(s, (float**)&ds.supports, d.supports, (size_t)5 * d.n_supports)) != cudaSuccess)
+      return bail(e, "upload supports");
+    ds.n_supports = d.n_supports;
+    ds.ox = d.grid_origin[0];
+    ds.oy = d.grid_origin[1];
+    ds.oz = d.grid_origin[2];
+    ds.h = d.grid_h;
+    ds.inv_h = 1.0f / d.grid_h;
+    ds.nx = d.grid_dims[0];
+    ds.ny = d.grid_dims[1];
+    ds.nz = d.grid_dims[2];
+    for (int k = 0; k < 4; ++k) ds.spawn[k] = d.spawn[k];
+    const size_t nodes = (size_t)ds.nx * ds.ny * ds.nz;
+    float* grid = nullptr;
+    if ((e = cudaMalloc(&grid, nodes * sizeof(float))) != cudaSuccess) return bail(e, "grid");
+    s->allocs.push_back(grid);
+    float* dboxes = nullptr;
+    if ((e = upload(s, &dboxes, d.boxes, (size_t)6 * d.n_boxes)) != cudaSuccess)
+      return bail(e, "upload boxes");
+    launch_grid_build(grid, dboxes, d.n_boxes, ds.ox, ds.oy, ds.oz, ds.h, ds.nx, ds.ny, ds.nz, 0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "grid kernel");
+    ds.grid = grid;
+  }
+  std::vector<float4> ov(mesh->n_verts);
+  for (int k = 0; k < mesh->n_verts; ++k)
+    ov[k] = make_float4(mesh->verts[3 * k], mesh->verts[3 * k + 1], mesh->verts[3 * k + 2], 0.f);
+  std::vector<uint32_t> ot(mesh->n_tris);
+  for (int t = 0; t < mesh->n_tris; ++t)
+    ot[t] = (uint32_t)mesh->tris[3 * t] | ((uint32_t)mesh->tris[3 * t + 1] << 8) |
+            ((uint32_t)mesh->tris[3 * t + 2] << 16);
+  if ((e = upload(s, &s->omesh_v, ov.data(), ov.size())) != cudaSuccess) return bail(e, "mesh");
+  if ((e = upload(s, &s->omesh_t, ot.data(), ot.size())) != cudaSuccess) return bail(e, "mesh");
+  if ((e = upload(s, &s->obj_rgb, mesh->obj_rgb, (size_t)GX_MAX_OBJECTS)) != cudaSuccess)
+    return bail(e, "colours");
+  s->omesh_nv = mesh->n_verts;
+  s->omesh_nt = mesh->n_tris;
+  if ((e = upload(s, &s->d_scenes, s->host.data(), s->host.size())) != cudaSuccess)
+    return bail(e, "scene table");
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail(e, "scene build");
+  *out = s;
+  return GX_OK;
+}
+
+extern "C" gx_status gx_scene_set_destroy(gx_scene_set* set) {
+  free_set(set);
+  return GX_OK;
+}
+
+// ===========================================================================
+// contexts
+// ===========================================================================
+extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
+                               const gx_config* cfg, gx_ctx** out) {
+  if (!out) return fail(nullptr, GX_EINVAL, "gx_create: out is NULL");
+  *out = nullptr;
+  if (!set || !robot || !cfg) return fail(nullptr, GX_EINVAL, "gx_create: NULL argument");
+  const gx_config& c = *cfg;
+  if (c.n_envs < 1) return fail(nullptr, GX_EINVAL, "n_envs must be >= 1");
+  if (c.img_w < 32 || c.img_h < 32 || c.img_w > 256 || c.img_h > 256 || c.img_w % 32 ||
+      c.img_h % 32)
+    return fail(nullptr, GX_EINVAL, "image sides must be multiples of 32 in [32, 256]");
+  if (c.n_objects < 0 || c.n_objects > GX_MAX_OBJECTS)
+    return fail(nullptr, GX_EINVAL, "n_objects must be in [0, 64]");
+  if (!(c.obj_radius_min > 0.f) || !(c.obj_radius_max >= c.obj_radius_min))
+    return fail(nullptr, GX_EINVAL, "bad object radius range");
+  if (robot->n_spheres < 1 || robot->n_spheres > 30)
+    return fail(nullptr, GX_EINVAL, "robot needs 1..30 spheres");
+  for (int i = 0; i < robot->n_spheres; ++i)
+    if (robot->sphere_link[i] < 0 || robot->sphere_link[i] > 7 || !(robot->sphere_radius[i] > 0.f))
+      return fail(nullptr, GX_EINVAL, "robot sphere %d: bad link or radius", i);
+  for (int k = 0; k < 7; ++k)
+    if (robot->link_axis[k] < 0 || robot->link_axis[k] > 2 || !(robot->q_min[k] <= robot->q_max[k]))
+      return fail(nullptr, GX_EINVAL, "robot joint %d: bad axis or limits", k);
+  if (!(robot->cam_near > 0.f)) return fail(nullptr, GX_EINVAL, "cam_near must be > 0");
+  if (c.env_scene)
+    for (int i = 0; i < c.n_envs; ++i)
+      if (c.env_scene[i] < 0 || c.env_scene[i] >= set->n)
+        return fail(nullptr, GX_EINVAL, "env_scene[%d] out of range", i);
+  int regions = c.raster_regions;
+  if (regions <= 0) {
+    regions = 1;
+    while ((size_t)c.img_w * (c.img_h / regions) * 8 > 64 * 1024) regions *= 2;
+  }
+  if (c.img_h % regions || (c.img_h / regions) < 1)
+    return fail(nullptr, GX_EINVAL, "raster_regions must divide img_h");
+  if ((size_t)c.img_w * (c.img_h / regions) * 8 > 160 * 1024)
+    return fail(nullptr, GX_EINVAL, "image band too large for shared memory");
+
+  gx_ctx* x = new gx_ctx();
+  x->set = set;
+  x->cfg = c;
+  x->cfg.env_scene = nullptr;
+  x->n = c.n_envs;
+  x->M = c.n_objects;
+  x->regions = regions;
+  x->region_h = c.img_h / regions;
+  x->small_px = c.small_tri_px > 0 ? c.small_tri_px : 48;
+  x->near_ = robot->cam_near;
+  auto bail = [&](cudaError_t e, const char* what) {
+    gx_destroy(x);
+    return fail(nullptr, e == cudaErrorMemoryAllocation ? GX_ENOMEM : GX_ECUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+  };
+  cudaError_t e;
+  if ((e = raster_configure(c.img_w, x->region_h)) != cudaSuccess) return bail(e, "raster config");
+  Robot hr;
+  hr.r = *robot;
+  if ((e = cudaMalloc(&x->d_robot, sizeof(Robot))) != cudaSuccess) return bail(e, "robot");
+  if ((e = cudaMemcpy(x->d_robot, &hr, sizeof(Robot), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return bail(e, "robot");
+  std::vector<int> es(x->n);
+  for (int i = 0; i < x->n; ++i)
+    es[i] = c.env_scene ? c.env_scene[i] : (int)((long long)i * set->n / x->n);
+  if ((e = cudaMalloc(&x->d_env_scene, x->n * sizeof(int))) != cudaSuccess) return bail(e, "map");
+  if ((e = cudaMemcpy(x->d_env_scene, es.data(), x->n * sizeof(int), cudaMemcpyHostToDevice)) !=
+      cudaSuccess)
+    return bail(e, "map");
+  // state blob: arrays on 256-byte boundaries
+  const size_t n = x->n, M = x->M;
+  const size_t sizes[10] = {n * 4, n * 4, n * 4, 7 * n * 4, n * 4, 3 * n * 4, 3 * n * 4,
+                            n * (M ? M : 1) * 16, n * 4, n * 4};
+  size_t off = 0;
+  for (int k = 0; k < 10; ++k) {
+    x->off[k] = off;
+    off += (sizes[k] + 255) & ~(size_t)255;
+  }
+  x->state_bytes = off;
+  if ((e = cudaMalloc(&x->d_state, off)) != cudaSuccess) return bail(e, "state");
+  if ((e = cudaMemset(x->d_state, 0, off)) != cudaSuccess) return bail(e, "state");
+  char* b = (char*)x->d_state;
+  x->st.bx = (float*)(b + x->off[0]);
+  x->st.bz = (float*)(b + x->off[1]);
+  x->st.yaw = (float*)(b + x->off[2]);
+  x->st.q = (float*)(b + x->off[3]);
+  x->st.held = (int*)(b + x->off[4]);
+  x->st.coff = (float*)(b + x->off[5]);
+  x->st.ppre = (float*)(b + x->off[6]);
+  x->st.obj = (float4*)(b + x->off[7]);
+  x->st.step = (int*)(b + x->off[8]);
+  x->st.episode = (int*)(b + x->off[9]);
+  if ((e = cudaMemset(x->st.held, 0xff, n * 4)) != cudaSuccess) return bail(e, "state");
+  if ((e = cudaMalloc(&x->d_cam, n * 12 * sizeof(float))) != cudaSuccess) return bail(e, "cam");
+  if ((e = cudaMemset(x->d_cam, 0, n * 12 * sizeof(float))) != cudaSuccess) return bail(e, "cam");
+  if ((e = cudaMalloc(&x->d_err, sizeof(unsigned))) != cudaSuccess) return bail(e, "err");
+  if ((e = cudaMemset(x->d_err, 0, sizeof(unsigned))) != cudaSuccess) return bail(e, "err");
+  if ((e = cudaMallocHost(&x->h_err, sizeof(unsigned))) != cudaSuccess) return bail(e, "err");
+  *x->h_err = 0;
+  if ((e = cudaEventCreateWithFlags(&x->ev_err, cudaEventDisableTiming)) != cudaSuccess)
+    return bail(e, "event");
+  *out = x;
+  return GX_OK;
+}
+
+extern "C" void gx_destroy(gx_ctx* x) {
+  if (!x) return;
+  cudaDeviceSynchronize();
+  if (x->gexec) cudaGraphExecDestroy(x->gexec);
+  cudaFree(x->d_robot);
+  cudaFree(x->d_env_scene);
+  cudaFree(x->d_state);
+  cudaFree(x->d_cam);
+  cudaFree(x->d_err);
+  if (x->h_err) cudaFreeHost(x->h_err);
+  if (x->ev_err) cudaEventDestroy(x->ev_err);
+  for (void* p : x->host_step_allocs) cudaFree(p);
+  delete x;
+}
+
+extern "C" gx_status gx_reset(gx_ctx* x, const uint8_t* env_mask, void* stream) {
+  if (!x) return fail(nullptr, GX_EINVAL, "gx_reset: ctx is NULL");
+  gx_status st = poll_device_error(x, false);
+  if (st != GX_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  ResetParams rp{};
+  rp.n = x->n;
+  rp.M = x->M;
+  rp.scenes = x->set->d_scenes;
+  rp.env_scene = x->d_env_scene;
+  rp.robot = x->d_robot;
+  rp.mask = env_mask;
+  rp.st = x->st;
+  rp.cam = x->d_cam;
+  rp.seed = x->cfg.seed;
+  rp.rho_min = x->cfg.obj_radius_min;
+  rp.rho_max = x->cfg.obj_radius_max;
+  rp.err = x->d_err;
+  launch_reset(rp, s);
+  CK(x, cudaGetLastError());
+  return post_error_copy(x, s);
+}
+
+extern "C" gx_status gx_step(gx_ctx* x, const float* actions, const gx_outputs* out,
+                             void* stream) {
+  if (!x) return fail(nullptr, GX_EINVAL, "gx_step: ctx is NULL");
+  if (!actions || !out || !out->depth) return fail(x, GX_EINVAL, "gx_step: actions and depth required");
+  if (x->cfg.render_rgb && !out->rgb) return fail(x, GX_EINVAL, "gx_step: render_rgb needs rgb");
+  gx_status st = poll_device_error(x, false);
+  if (st != GX_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (x->cfg.use_graph && s != nullptr) {
+    if (!x->gexec || x->g_actions != actions || !same_outputs(x->g_out, *out)) {
+      if (x->gexec) {
+        cudaGraphExecDestroy(x->gexec);
+        x->gexec = nullptr;
+      }
+      cudaGraph_t g;
+      CK(x, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      enqueue_step(x, actions, *out, s);
+      CK(x, cudaStreamEndCapture(s, &g));
+      cudaError_t e = cudaGraphInstantiate(&x->gexec, g, 0);
+      cudaGraphDestroy(g);
+      CK(x, e);
+      x->g_actions = actions;
+      x->g_out = *out;
+    }
+    CK(x, cudaGraphLaunch(x->gexec, s));
+  } else {
+    enqueue_step(x, actions, *out, s);
+    CK(x, cudaGetLastError());
+  }
+  return post_error_copy(x, s);
+}
+
+extern "C" gx_status gx_step_host(gx_ctx* x, const float* actions_host, const gx_outputs* host_out,
+                                  void* stream) {
+  if (!x) return fail(nullptr, GX_EINVAL, "gx_step_host: ctx is NULL");
+  if (!actions_host || !host_out || !host_out->depth)
+    return fail(x, GX_EINVAL, "gx_step_host: actions and depth required");
+  if (x->cfg.render_rgb && !host_out->rgb)
+    return fail(x, GX_EINVAL, "gx_step_host: render_rgb needs rgb");
+  const size_t n = x->n, M = x->M, px = (size_t)x->cfg.img_w * x->cfg.img_h;
+  const size_t dbytes = n * px * (x->cfg.depth_fp16 ? 2 : 4);
+  if (!x->h2d_actions) {
+    auto alloc = [&](void** p, size_t bytes) {
+      cudaError_t e = cudaMalloc(p, bytes);
+      if (e == cudaSuccess) x->host_step_allocs.push_back(*p);
+      return e;
+    };
+    CK(x, alloc((void**)&x->h2d_actions, n * 11 * 4));
+    CK(x, alloc(&x->dev_out.depth, dbytes));
+    if (x->cfg.render_rgb) CK(x, alloc((void**)&x->dev_out.rgb, n * px * 3));
+    CK(x, alloc((void**)&x->dev_out.pose, n * 16 * 4));
+    CK(x, alloc((void**)&x->dev_out.obj_pos, n * (M ? M : 1) * 16));
+    CK(x, alloc((void**)&x->dev_out.held, n * 4));
+    CK(x, alloc((void**)&x->dev_out.contact_mask, n * 4));
+    CK(x, alloc((void**)&x->dev_out.contact_flags, n));
+    CK(x, alloc((void**)&x->dev_out.event, n));
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(x, cudaMemcpyAsync(x->h2d_actions, actions_host, n * 11 * 4, cudaMemcpyHostToDevice, s));
+  gx_status st = gx_step(x, x->h2d_actions, &x->dev_out, stream);
+  if (st != GX_OK) return st;
+  const gx_outputs& d = x->dev_out;
+  const gx_outputs& h = *host_out;
+  CK(x, cudaMemcpyAsync(h.depth, d.depth, dbytes, cudaMemcpyDeviceToHost, s));
+  if (h.rgb && d.rgb) CK(x, cudaMemcpyAsync(h.rgb, d.rgb, n * px * 3, cudaMemcpyDeviceToHost, s));
+  if (h.pose) CK(x, cudaMemcpyAsync(h.pose, d.pose, n * 64, cudaMemcpyDeviceToHost, s));
+  if (h.obj_pos && M) CK(x, cudaMemcpyAsync(h.obj_pos, d.obj_pos, n * M * 16, cudaMemcpyDeviceToHost, s));
+  if (h.held) CK(x, cudaMemcpyAsync(h.held, d.held, n * 4, cudaMemcpyDeviceToHost, s));
+  if (h.contact_mask) CK(x, cudaMemcpyAsync(h.contact_mask, d.contact_mask, n * 4, cudaMemcpyDeviceToHost, s));
+  if (h.contact_flags) CK(x, cudaMemcpyAsync(h.contact_flags, d.contact_flags, n, cudaMemcpyDeviceToHost, s));
+  if (h.event) CK(x, cudaMemcpyAsync(h.event, d.event, n, cudaMemcpyDeviceToHost, s));
+  CK(x, cudaStreamSynchronize(s));
+  return poll_device_error(x, true);
+}
+
+extern "C" gx_status gx_sync(gx_ctx* x) {
+  if (!x) return fail(nullptr, GX_EINVAL, "gx_sync: ctx is NULL");
+  CK(x, cudaDeviceSynchronize());
+  return poll_device_error(x, true);
+}
+
+extern "C" uint32_t gx_device_error(gx_ctx* x) {
+  if (!x) return 0;
+  cudaDeviceSynchronize();
+  poll_device_error(x, true);
+  unsigned v = x->dev_err_seen;
+  x->dev_err_seen = 0;
+  return v;
+}
+
+extern "C" size_t gx_state_bytes(const gx_ctx* x) { return x ? x->state_bytes : 0; }
+
+extern "C" gx_status gx_save_state(gx_ctx* x, void* host, size_t bytes) {
+  if (!x || !host || bytes != x->state_bytes) return fail(x, GX_EINVAL, "gx_save_state: bad size");
+  CK(x, cudaDeviceSynchronize());
+  CK(x, cudaMemcpy(host, x->d_state, bytes, cudaMemcpyDeviceToHost));
+  return GX_OK;
+}
+
+extern "C" gx_status gx_load_state(gx_ctx* x, const void* host, size_t bytes) {
+  if (!x || !host || bytes != x->state_bytes) return fail(x, GX_EINVAL, "gx_load_state: bad size");
+  CK(x, cudaDeviceSynchronize());
+  CK(x, cudaMemcpy(x->d_state, host, bytes, cudaMemcpyHostToDevice));
+  return GX_OK;
+}
+
+extern "C" gx_status gx_state_layout(const gx_ctx* x, size_t offsets[10]) {
+  if (!x || !offsets) return fail(nullptr, GX_EINVAL, "gx_state_layout: NULL argument");
+  for (int k = 0; k < 10; ++k) offsets[k] = x->off[k];
+  return GX_OK;
+}
+
+extern "C" const char* gx_last_error(const gx_ctx* x) {
+  return x ? x->msg.c_str() : g_last_error.c_str();
+}

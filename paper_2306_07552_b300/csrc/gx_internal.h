@@ -1,0 +1,128 @@
+// Internal declarations of the gx library (device data layouts, kernel
+// parameter blocks, launchers).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/gx.h"
+
+namespace gx {
+
+// ---------------------------------------------------------------------------
+// Scene data on the device.  Triangles are regrouped into clusters of at most
+// 64 triangles and 64 vertices ("meshlets") with a bounding sphere and a cone
+// that bounds the face normals, so a camera can reject whole clusters that are
+// outside its view or entirely back-facing before touching their triangles.
+// ---------------------------------------------------------------------------
+constexpr int kMeshletMaxVerts = 64;
+constexpr int kMeshletMaxTris = 64;
+
+// Three float4 per meshlet:
+//   [0] bounding sphere centre xyz, radius
+//   [1] normal-cone axis xyz, sin(half angle)   (cos < -0.5 disables the test)
+//   [2] cos(half angle), vertex offset (float4 units, as bits),
+//       triangle offset (as bits), n_verts | n_tris << 8 (as bits)
+struct DScene {
+  const float4* mhdr;
+  const float4* mverts;     // world positions, w unused
+  const uint32_t* mtris;    // i0 | i1 << 8 | i2 << 16 (meshlet-local)
+  const uint32_t* tri_rgb;  // colour per triangle, meshlet order
+  int n_meshlets;
+  int n_tris;
+  const float* grid;        // [nz][ny][nx]
+  float ox, oy, oz, h, inv_h;
+  int nx, ny, nz;
+  const float* supports;    // [P][5]
+  int n_supports;
+  float spawn[4];
+};
+
+struct HostMeshlets {
+  std::vector<float4> hdr, verts;
+  std::vector<uint32_t> tris, rgb;
+};
+
+// Builds the meshlet arrays of one scene (host, deterministic).
+void build_meshlets(const gx_scene_desc& s, HostMeshlets& out);
+
+// Device robot table: gx_robot as given.
+struct Robot {
+  gx_robot r;
+};
+
+// ---------------------------------------------------------------------------
+// State: one device allocation, structure of arrays per field.
+// ---------------------------------------------------------------------------
+struct StateView {
+  float* bx;      // [n]
+  float* bz;      // [n]
+  float* yaw;     // [n]
+  float* q;       // [7][n]
+  int* held;      // [n]
+  float* coff;    // [3][n]
+  float* ppre;    // [3][n]
+  float4* obj;    // [n][M]
+  int* step;      // [n]
+  int* episode;   // [n]
+};
+
+struct PhysicsParams {
+  int n, M;
+  const DScene* scenes;
+  const int* env_scene;
+  const Robot* robot;
+  const float* actions;   // [n][11]
+  StateView st;
+  float* cam;             // [n][12] camera R (row-major, columns right/up/fwd) + eye
+  gx_outputs out;
+  unsigned* err;
+};
+
+struct ResetParams {
+  int n, M;
+  const DScene* scenes;
+  const int* env_scene;
+  const Robot* robot;
+  const uint8_t* mask;    // [n] or NULL
+  StateView st;
+  float* cam;
+  uint64_t seed;
+  float rho_min, rho_max;
+  unsigned* err;
+};
+
+struct RasterParams {
+  int n, M, W, H;
+  int regions, region_h;
+  int small_px;
+  const DScene* scenes;
+  const int* env_scene;
+  const float* cam;        // [n][12]
+  const float4* obj;       // [n][M]
+  const float4* omesh_v;   // [nv] unit instance mesh
+  const uint32_t* omesh_t; // [nt] packed
+  int omesh_nv, omesh_nt;
+  const uint32_t* obj_rgb; // [64]
+  float near_;
+  void* depth;
+  int depth_fp16;
+  uint8_t* rgb;
+  unsigned* err;
+};
+
+void launch_physics(const PhysicsParams& p, cudaStream_t s);
+void launch_reset(const ResetParams& p, cudaStream_t s);
+void launch_raster(const RasterParams& p, cudaStream_t s);
+size_t raster_smem_bytes(int W, int region_h);
+cudaError_t raster_configure(int W, int region_h);
+void launch_grid_build(float* grid, const float* boxes, int n_boxes, float ox, float oy, float oz,
+                       float h, int nx, int ny, int nz, cudaStream_t s);
+
+// device error bits beyond the public ones
+constexpr unsigned kErrWaitTimeout = 0x100u;  // a bounded mbarrier wait gave up
+
+}  // namespace gx

@@ -1,0 +1,154 @@
+// Host-side clustering of a scene's triangles into meshlets: at most 64
+// triangles and 64 distinct vertices per cluster, each with a bounding sphere
+// and a cone bounding its face normals.  A camera rejects a whole cluster when
+// the sphere is outside its view or every face in the cone faces away, so the
+// rasteriser only stages and sets up triangles that can be visible.
+//
+// Clusters are formed greedily over triangles sorted by (dominant normal
+// direction, Morton code of the centroid), which keeps each cluster compact
+// and nearly planar.  Deterministic for a given input.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <unordered_map>
+
+#include "gx_internal.h"
+
+namespace gx {
+
+namespace {
+
+uint32_t part1by2(uint32_t x) {
+  x &= 0x3ff;
+  x = (x | (x << 16)) & 0x030000ff;
+  x = (x | (x << 8)) & 0x0300f00f;
+  x = (x | (x << 4)) & 0x030c30c3;
+  x = (x | (x << 2)) & 0x09249249;
+  return x;
+}
+
+struct V3 {
+  double x, y, z;
+};
+V3 sub(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+V3 cross(V3 a, V3 b) { return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x}; }
+double dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+double norm(V3 a) { return std::sqrt(dot(a, a)); }
+
+}  // namespace
+
+void build_meshlets(const gx_scene_desc& s, HostMeshlets& out) {
+  const int T = s.n_tris;
+  auto vert = [&](int v) { return V3{s.verts[3 * v], s.verts[3 * v + 1], s.verts[3 * v + 2]}; };
+  std::vector<V3> nrm(T);
+  V3 lo{1e30, 1e30, 1e30}, hi{-1e30, -1e30, -1e30};
+  for (int v = 0; v < s.n_verts; ++v) {
+    V3 p = vert(v);
+    lo = {std::min(lo.x, p.x), std::min(lo.y, p.y), std::min(lo.z, p.z)};
+    hi = {std::max(hi.x, p.x), std::max(hi.y, p.y), std::max(hi.z, p.z)};
+  }
+  std::vector<uint64_t> key(T);
+  for (int t = 0; t < T; ++t) {
+    V3 a = vert(s.tris[3 * t]), b = vert(s.tris[3 * t + 1]), c = vert(s.tris[3 * t + 2]);
+    V3 n = cross(sub(b, a), sub(c, a));
+    double l = norm(n);
+    nrm[t] = l > 0 ? V3{n.x / l, n.y / l, n.z / l} : V3{0, 0, 0};
+    double ax = std::fabs(nrm[t].x), ay = std::fabs(nrm[t].y), az = std::fabs(nrm[t].z);
+    uint32_t dir = ax >= ay && ax >= az ? (nrm[t].x >= 0 ? 0 : 1)
+                   : ay >= az          ? (nrm[t].y >= 0 ? 2 : 3)
+                                       : (nrm[t].z >= 0 ? 4 : 5);
+    V3 cen{(a.x + b.x + c.x) / 3, (a.y + b.y + c.y) / 3, (a.z + b.z + c.z) / 3};
+    auto q = [](double v, double l0, double h0) {
+      double f = (h0 > l0) ? (v - l0) / (h0 - l0) : 0.0;
+      return (uint32_t)std::min(1023.0, std::max(0.0, f * 1023.0));
+    };
+    uint32_t m = part1by2(q(cen.x, lo.x, hi.x)) | (part1by2(q(cen.y, lo.y, hi.y)) << 1) |
+                 (part1by2(q(cen.z, lo.z, hi.z)) << 2);
+    key[t] = ((uint64_t)dir << 32) | m;
+  }
+  std::vector<int> order(T);
+  for (int t = 0; t < T; ++t) order[t] = t;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return key[a] < key[b]; });
+
+  out.hdr.clear();
+  out.verts.clear();
+  out.tris.clear();
+  out.rgb.clear();
+  std::unordered_map<int, int> local;
+  std::vector<int> cur_tris, cur_verts;
+  auto flush = [&]() {
+    if (cur_tris.empty()) return;
+    const uint32_t voff = (uint32_t)out.verts.size();
+    const uint32_t toff = (uint32_t)out.tris.size();
+    V3 bl{1e30, 1e30, 1e30}, bh{-1e30, -1e30, -1e30};
+    for (int gv : cur_verts) {
+      V3 p = vert(gv);
+      out.verts.push_back(make_float4((float)p.x, (float)p.y, (float)p.z, 0.f));
+      bl = {std::min(bl.x, p.x), std::min(bl.y, p.y), std::min(bl.z, p.z)};
+      bh = {std::max(bh.x, p.x), std::max(bh.y, p.y), std::max(bh.z, p.z)};
+    }
+    V3 c{0.5 * (bl.x + bh.x), 0.5 * (bl.y + bh.y), 0.5 * (bl.z + bh.z)};
+    double r = 0;
+    for (int gv : cur_verts) r = std::max(r, norm(sub(vert(gv), c)));
+    V3 ax{0, 0, 0};
+    for (int t : cur_tris) ax = {ax.x + nrm[t].x, ax.y + nrm[t].y, ax.z + nrm[t].z};
+    double al = norm(ax);
+    double cosang = -1.0, sinang = 1.0;
+    if (al > 1e-12) {
+      ax = {ax.x / al, ax.y / al, ax.z / al};
+      double mn = 1.0;
+      for (int t : cur_tris) mn = std::min(mn, dot(ax, nrm[t]));
+      if (mn > 0.2) {  // cone narrower than ~78 degrees: usable for culling
+        double ang = std::acos(std::min(1.0, mn)) + 1e-3;
+        cosang = std::cos(ang);
+        sinang = std::sin(ang);
+      }
+    }
+    if (cosang < -0.5) ax = {0, 0, 1};
+    for (int t : cur_tris) {
+      uint32_t packed = 0;
+      for (int k = 0; k < 3; ++k) packed |= (uint32_t)local[s.tris[3 * t + k]] << (8 * k);
+      out.tris.push_back(packed);
+      out.rgb.push_back(s.tri_rgb[t]);
+    }
+    while (out.tris.size() % 4) {  // 16-byte blocks for bulk copies
+      out.tris.push_back(0);
+      out.rgb.push_back(0);
+    }
+    const uint32_t counts = (uint32_t)cur_verts.size() | ((uint32_t)cur_tris.size() << 8);
+    // radius padded by a relative epsilon: float rounding of the centre
+    float4 h0 = make_float4((float)c.x, (float)c.y, (float)c.z, (float)(r * (1 + 1e-6) + 1e-6));
+    float4 h1 = make_float4((float)ax.x, (float)ax.y, (float)ax.z, (float)sinang);
+    float4 h2;
+    h2.x = (float)cosang;
+    std::memcpy(&h2.y, &voff, 4);
+    std::memcpy(&h2.z, &toff, 4);
+    std::memcpy(&h2.w, &counts, 4);
+    out.hdr.push_back(h0);
+    out.hdr.push_back(h1);
+    out.hdr.push_back(h2);
+    cur_tris.clear();
+    cur_verts.clear();
+    local.clear();
+  };
+  for (int t : order) {
+    int need = 0;
+    for (int k = 0; k < 3; ++k) need += local.count(s.tris[3 * t + k]) ? 0 : 1;
+    // keep vertex, triangle and direction-bucket limits per cluster
+    bool dir_change = !cur_tris.empty() && (key[cur_tris[0]] >> 32) != (key[t] >> 32);
+    if ((int)cur_tris.size() == kMeshletMaxTris ||
+        (int)cur_verts.size() + need > kMeshletMaxVerts || dir_change)
+      flush();
+    for (int k = 0; k < 3; ++k) {
+      int gv = s.tris[3 * t + k];
+      if (!local.count(gv)) {
+        local[gv] = (int)cur_verts.size();
+        cur_verts.push_back(gv);
+      }
+    }
+    cur_tris.push_back(t);
+  }
+  flush();
+}
+
+}  // namespace gx

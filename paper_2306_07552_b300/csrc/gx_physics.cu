@@ -1,0 +1,538 @@
+// Physics part of the batched step: one warp per environment.
+//
+// Sec. 3.2 ("Approximate Kinematic Simulation"): action offsets are applied
+// directly to the robot state, forward kinematics places the links, the
+// candidate pose is tested for overlap with the static scene and the movable
+// objects, and any overlap rejects all robot motion for the step.  Grasping
+// attaches the object overlapping a small sphere at the end-effector tip; a
+// release snaps the object down onto the surface below it and, when that
+// fails, restores the object's pre-grasp position (appendix "Object Placing
+// Heuristic").  Here the static scene is a signed-distance grid queried by
+// trilinear interpolation and free objects are spheres.
+//
+// Lane layout: lane i < n_spheres carries robot sphere i, lane 30 the held
+// object; contact masks are warp ballots, so bit i is lane i.  Every lane
+// runs the (cheap) FK chain and keeps only its own link's frame.
+#include <math_constants.h>
+
+#include "gx_internal.h"
+
+namespace gx {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kEnvsPerBlock = 4;
+
+__device__ __forceinline__ float clampf(float x, float lo, float hi) {
+  return fminf(fmaxf(x, lo), hi);
+}
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of the
+// multiply-xor S-box with a Weyl key schedule.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+__device__ __forceinline__ float unit24(uint32_t w) {
+  return (float)(w >> 8) * (1.0f / 16777216.0f);
+}
+
+__device__ __forceinline__ float gnode(const DScene& s, int i, int j, int k) {
+  return __ldg(s.grid + ((size_t)k * s.ny + j) * s.nx + i);
+}
+
+// Trilinear interpolation of the distance grid.  false when c lies outside
+// the lattice box (or is not finite): that counts as contact.
+__device__ bool grid_query(const DScene& s, float cx, float cy, float cz, float& d) {
+  const float gx = (cx - s.ox) * s.inv_h, gy = (cy - s.oy) * s.inv_h, gz = (cz - s.oz) * s.inv_h;
+  if (!(gx >= 0.f && gx <= (float)(s.nx - 1) && gy >= 0.f && gy <= (float)(s.ny - 1) &&
+        gz >= 0.f && gz <= (float)(s.nz - 1)))
+    return false;
+  const int i = min((int)floorf(gx), s.nx - 2);
+  const int j = min((int)floorf(gy), s.ny - 2);
+  const int k = min((int)floorf(gz), s.nz - 2);
+  const float tx = gx - i, ty = gy - j, tz = gz - k;
+  const float* g = s.grid + ((size_t)k * s.ny + j) * s.nx + i;
+  const size_t sy = s.nx, sz = (size_t)s.nx * s.ny;
+  const float c000 = __ldg(g), c100 = __ldg(g + 1);
+  const float c010 = __ldg(g + sy), c110 = __ldg(g + sy + 1);
+  const float c001 = __ldg(g + sz), c101 = __ldg(g + sz + 1);
+  const float c011 = __ldg(g + sz + sy), c111 = __ldg(g + sz + sy + 1);
+  const float c00 = c000 + tx * (c100 - c000), c10 = c010 + tx * (c110 - c010);
+  const float c01 = c001 + tx * (c101 - c001), c11 = c011 + tx * (c111 - c011);
+  const float c0 = c00 + ty * (c10 - c00), c1 = c01 + ty * (c11 - c01);
+  d = c0 + tz * (c1 - c0);
+  return true;
+}
+
+// Right-multiplies the row-major rotation R by a rotation of `axis` by the
+// angle with sine s, cosine c (columns mix pairwise).
+__device__ __forceinline__ void rmul_axis(float R[9], int axis, float s, float c) {
+  const int a = axis == 0 ? 1 : 0;  // the two columns that mix
+  const int b = axis == 2 ? 1 : 2;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const float ca = R[3 * r + a], cb = R[3 * r + b];
+    if (axis == 1) {  // Ry: col0' = c col0 - s col2, col2' = s col0 + c col2
+      R[3 * r + a] = c * ca - s * cb;
+      R[3 * r + b] = s * ca + c * cb;
+    } else {          // Rx (cols 1,2), Rz (cols 0,1): colA' = c A + s B, colB' = -s A + c B
+      R[3 * r + a] = c * ca + s * cb;
+      R[3 * r + b] = -s * ca + c * cb;
+    }
+  }
+}
+
+__device__ __forceinline__ void apply(const float R[9], const float t[3], float x, float y, float z,
+                                      float o[3]) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r) o[r] = R[3 * r] * x + R[3 * r + 1] * y + R[3 * r + 2] * z + t[r];
+}
+
+// Forward kinematics of the chain (Sec. 3.2).  Returns the frame of link
+// `mylink` (0 = base) and the tool-tip frame.
+__device__ void fk(const gx_robot& rb, float x, float z, float yaw, const float q[7], int mylink,
+                   float myR[9], float myt[3], float eR[9], float et[3]) {
+  float s, c;
+  sincosf(yaw, &s, &c);
+  float R[9] = {c, 0.f, s, 0.f, 1.f, 0.f, -s, 0.f, c};
+  float t[3] = {x, 0.f, z};
+  if (mylink == 0) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) myR[i] = R[i];
+    myt[0] = t[0]; myt[1] = t[1]; myt[2] = t[2];
+  }
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    const float ox = rb.link_offset[k][0], oy = rb.link_offset[k][1], oz = rb.link_offset[k][2];
+    float nt[3];
+    apply(R, t, ox, oy, oz, nt);
+    t[0] = nt[0]; t[1] = nt[1]; t[2] = nt[2];
+    float sk, ck;
+    sincosf(q[k], &sk, &ck);
+    rmul_axis(R, rb.link_axis[k], sk, ck);
+    if (mylink == k + 1) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) myR[i] = R[i];
+      myt[0] = t[0]; myt[1] = t[1]; myt[2] = t[2];
+    }
+  }
+  apply(R, t, rb.link_offset[7][0], rb.link_offset[7][1], rb.link_offset[7][2], et);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) eR[i] = R[i];
+}
+
+// Head camera of base pose (x, z, yaw): R (row-major, columns right, up,
+// forward) re-orthonormalised by Gram-Schmidt on forward then up, and eye.
+__device__ void camera(const gx_robot& rb, float x, float z, float yaw, float out[12]) {
+  float s, c, sp, cp;
+  sincosf(yaw, &s, &c);
+  sincosf(rb.cam_pitch, &sp, &cp);
+  const float R0[9] = {c, 0.f, s, 0.f, 1.f, 0.f, -s, 0.f, c};
+  // mount columns in the base frame
+  const float Mr[3] = {0.f, 0.f, -1.f}, Mu[3] = {-sp, cp, 0.f}, Mf[3] = {cp, sp, 0.f};
+  float r[3], u[3], f[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    r[i] = R0[3 * i] * Mr[0] + R0[3 * i + 1] * Mr[1] + R0[3 * i + 2] * Mr[2];
+    u[i] = R0[3 * i] * Mu[0] + R0[3 * i + 1] * Mu[1] + R0[3 * i + 2] * Mu[2];
+    f[i] = R0[3 * i] * Mf[0] + R0[3 * i + 1] * Mf[1] + R0[3 * i + 2] * Mf[2];
+  }
+  float nf = rsqrtf(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+  f[0] *= nf; f[1] *= nf; f[2] *= nf;
+  const float d = u[0] * f[0] + u[1] * f[1] + u[2] * f[2];
+  u[0] -= d * f[0]; u[1] -= d * f[1]; u[2] -= d * f[2];
+  const float nu = rsqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  u[0] *= nu; u[1] *= nu; u[2] *= nu;
+  // right = up x forward
+  r[0] = u[1] * f[2] - u[2] * f[1];
+  r[1] = u[2] * f[0] - u[0] * f[2];
+  r[2] = u[0] * f[1] - u[1] * f[0];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    out[3 * i + 0] = r[i];
+    out[3 * i + 1] = u[i];
+    out[3 * i + 2] = f[i];
+  }
+  float e[3];
+  const float t0[3] = {x, 0.f, z};
+  apply(R0, t0, rb.cam_pos[0], rb.cam_pos[1], rb.cam_pos[2], e);
+  out[9] = e[0]; out[10] = e[1]; out[11] = e[2];
+}
+
+// Snap-to-surface: cast a sphere straight down from p; the landing height is
+// the highest y <= p.y where the interpolated distance reaches `target`.  At
+// fixed (x, z) the field is linear in y between lattice levels, so each
+// lane examines one level (32 levels per pass, top down) and the first level
+// at or below the target fixes the cell holding the exact root.
+__device__ bool snap_down(const DScene& s, const float p[3], float target, float& y, int lane) {
+  float d0;
+  if (!grid_query(s, p[0], p[1], p[2], d0)) return false;
+  if (d0 <= target) {
+    y = p[1];
+    return true;
+  }
+  const float gx = (p[0] - s.ox) * s.inv_h, gz = (p[2] - s.oz) * s.inv_h;
+  const float gy = (p[1] - s.oy) * s.inv_h;
+  const int i = min((int)floorf(gx), s.nx - 2), k = min((int)floorf(gz), s.nz - 2);
+  const float tx = gx - i, tz = gz - k;
+  const int jstart = min((int)floorf(gy), s.ny - 2);
+  float top = p[1], dtop = d0;
+  for (int base = jstart; base >= 0; base -= 32) {
+    const int j = base - lane;
+    float dj = CUDART_INF_F;
+    if (j >= 0) {
+      const float a0 = gnode(s, i, j, k), a1 = gnode(s, i + 1, j, k);
+      const float b0 = gnode(s, i, j, k + 1), b1 = gnode(s, i + 1, j, k + 1);
+      const float c0 = a0 + tx * (a1 - a0), c1 = b0 + tx * (b1 - b0);
+      dj = c0 + tz * (c1 - c0);
+    }
+    const unsigned hit = __ballot_sync(kFull, j >= 0 && dj <= target);
+    if (hit) {
+      const int L = __ffs(hit) - 1;
+      const float dl = __shfl_sync(kFull, dj, L);
+      const float dprev = __shfl_sync(kFull, dj, L > 0 ? L - 1 : 0);
+      const int jr = base - L;
+      const float yj = s.oy + (float)jr * s.h;
+      const float yt = (L == 0) ? top : s.oy + (float)(jr + 1) * s.h;
+      const float dt = (L == 0) ? dtop : dprev;
+      y = (yt > yj) ? yj + (target - dl) / (dt - dl) * (yt - yj) : yj;
+      return true;
+    }
+    dtop = __shfl_sync(kFull, dj, 31);
+    top = s.oy + (float)(base - 31) * s.h;
+  }
+  return false;
+}
+
+__global__ void __launch_bounds__(32 * kEnvsPerBlock) physics_kernel(const PhysicsParams P) {
+  __shared__ float4 s_obj[kEnvsPerBlock][GX_MAX_OBJECTS];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int env = blockIdx.x * kEnvsPerBlock + w;
+  if (env >= P.n) return;
+  const int n = P.n, M = P.M;
+  const DScene& S = P.scenes[P.env_scene[env]];
+  const gx_robot& rb = P.robot->r;
+  float4* so = s_obj[w];
+  for (int j = lane; j < M; j += 32) so[j] = P.st.obj[(size_t)env * M + j];
+
+  // (a1) actions, clipped to [-1, 1]; non-finite values count as 0
+  float a = lane < 11 ? P.actions[(size_t)env * 11 + lane] : 0.f;
+  const bool bad = lane < 11 && !isfinite(a);
+  if (__any_sync(kFull, bad) && lane == 0) atomicOr(P.err, GX_DEV_NONFINITE_ACTION);
+  a = bad ? 0.f : clampf(a, -1.f, 1.f);
+  float act[11];
+#pragma unroll
+  for (int k = 0; k < 11; ++k) act[k] = __shfl_sync(kFull, a, k);
+
+  // (a2) candidate pose: translate along the pre-step heading, then turn
+  // (+1 = clockwise seen from above, so yaw decreases); joints clamped
+  const float x0 = P.st.bx[env], z0 = P.st.bz[env], th0 = P.st.yaw[env];
+  float q0[7], cq[7];
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    q0[k] = P.st.q[(size_t)k * n + env];
+    cq[k] = clampf(q0[k] + rb.dq_max * act[2 + k], rb.q_min[k], rb.q_max[k]);
+  }
+  float sth, cth;
+  sincosf(th0, &sth, &cth);
+  const float cx = x0 + rb.base_step * act[0] * cth;
+  const float cz = z0 - rb.base_step * act[0] * sth;
+  float cyaw = th0 - rb.base_turn * act[1];
+  if (cyaw > CUDART_PI_F) cyaw -= 2.f * CUDART_PI_F;
+  if (cyaw <= -CUDART_PI_F) cyaw += 2.f * CUDART_PI_F;
+  int held = P.st.held[env];
+  if (held >= M) held = -1;  // a loaded state cannot index past the objects
+  const int stepc = P.st.step[env] + 1;
+  float coff[3] = {P.st.coff[env], P.st.coff[(size_t)n + env], P.st.coff[2 * (size_t)n + env]};
+
+  // (a3, a4) FK and sphere centres of the candidate
+  const int mylink = lane < rb.n_spheres ? rb.sphere_link[lane] : -1;
+  float myR[9], myt[3], eR[9], et[3];
+  fk(rb, cx, cz, cyaw, cq, mylink, myR, myt, eR, et);
+  __syncwarp();
+  bool active = false;
+  float c[3] = {0.f, 0.f, 0.f}, r = 0.f;
+  if (lane < rb.n_spheres) {
+    apply(myR, myt, rb.sphere_pos[lane][0], rb.sphere_pos[lane][1], rb.sphere_pos[lane][2], c);
+    r = rb.sphere_radius[lane];
+    active = true;
+  } else if (lane == 30 && held >= 0) {
+    apply(eR, et, coff[0], coff[1], coff[2], c);
+    r = so[held].w;
+    active = true;
+  }
+  // (a5, a6) static grid and free objects (the held object is not tested)
+  bool cs = false, co = false;
+  if (active) {
+    float d;
+    cs = !grid_query(S, c[0], c[1], c[2], d) || d < r;
+    for (int j = 0; j < M; ++j) {
+      if (j == held) continue;
+      const float4 o = so[j];
+      const float dx = c[0] - o.x, dy = c[1] - o.y, dz = c[2] - o.z, rr = r + o.w;
+      co |= dx * dx + dy * dy + dz * dz < rr * rr;
+    }
+  }
+  const unsigned mask = __ballot_sync(kFull, active && (cs || co));
+  const unsigned ms = __ballot_sync(kFull, active && cs);
+  const unsigned mo = __ballot_sync(kFull, active && co);
+  const uint8_t flags = (ms ? 1 : 0) | (mo ? 2 : 0) | ((mask >> 30) & 1u ? 4 : 0);
+
+  // (a7) any contact rejects all robot motion this step
+  const bool rev = mask != 0;
+  float ax = cx, az = cz, ayaw = cyaw, aq[7];
+#pragma unroll
+  for (int k = 0; k < 7; ++k) aq[k] = cq[k];
+  if (rev) {
+    ax = x0; az = z0; ayaw = th0;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) aq[k] = q0[k];
+    fk(rb, ax, az, ayaw, aq, -1, myR, myt, eR, et);
+  }
+
+  // (a8) grasp / release at the accepted pose
+  int nheld = held;
+  uint8_t event = 0;
+  float ppre[3] = {P.st.ppre[env], P.st.ppre[(size_t)n + env], P.st.ppre[2 * (size_t)n + env]};
+  const bool grasp = act[9] >= 0.5f;
+  if (grasp && held < 0) {
+    float bs = CUDART_INF_F;
+    int bj = -1;
+    const float rg = rb.grasp_radius;
+    for (int j = lane; j < M; j += 32) {
+      const float4 o = so[j];
+      const float dx = et[0] - o.x, dy = et[1] - o.y, dz = et[2] - o.z;
+      const float d = sqrtf(dx * dx + dy * dy + dz * dz);
+      if (d < rg + o.w) {
+        const float sd = d - o.w;
+        if (sd < bs) { bs = sd; bj = j; }
+      }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const float os = __shfl_xor_sync(kFull, bs, off);
+      const int oj = __shfl_xor_sync(kFull, bj, off);
+      if (oj >= 0 && (bj < 0 || os < bs || (os == bs && oj < bj))) { bs = os; bj = oj; }
+    }
+    if (bj >= 0) {
+      const float4 o = so[bj];
+      const float dp[3] = {o.x - et[0], o.y - et[1], o.z - et[2]};
+#pragma unroll
+      for (int k = 0; k < 3; ++k) coff[k] = eR[k] * dp[0] + eR[3 + k] * dp[1] + eR[6 + k] * dp[2];
+      ppre[0] = o.x; ppre[1] = o.y; ppre[2] = o.z;
+      nheld = bj;
+      event = 1;
+    } else {
+      event = 2;
+    }
+  } else if (!grasp && held >= 0) {
+    float p[3];
+    apply(eR, et, coff[0], coff[1], coff[2], p);
+    const float rho = so[held].w;
+    float y = p[1];
+    const bool ok = snap_down(S, p, rho + rb.rest_clearance, y, lane);
+    bool ov = false;
+    if (ok) {
+      for (int j = lane; j < M; j += 32) {
+        if (j == held) continue;
+        const float4 o = so[j];
+        const float dx = p[0] - o.x, dy = y - o.y, dz = p[2] - o.z, rr = rho + o.w;
+        ov |= dx * dx + dy * dy + dz * dz < rr * rr;
+      }
+    }
+    ov = __any_sync(kFull, ov);
+    __syncwarp();
+    if (lane == 0) so[held] = (ok && !ov) ? make_float4(p[0], y, p[2], rho)
+                                          : make_float4(ppre[0], ppre[1], ppre[2], rho);
+    event = (ok && !ov) ? 3 : 4;
+    nheld = -1;
+    coff[0] = coff[1] = coff[2] = 0.f;
+  }
+  __syncwarp();
+  if (nheld >= 0 && lane == 0) {
+    float p[3];
+    apply(eR, et, coff[0], coff[1], coff[2], p);
+    so[nheld] = make_float4(p[0], p[1], p[2], so[nheld].w);
+  }
+  __syncwarp();
+
+  // state write-back
+  if (lane == 0) {
+    P.st.bx[env] = ax; P.st.bz[env] = az; P.st.yaw[env] = ayaw;
+    P.st.held[env] = nheld;
+    P.st.step[env] = stepc;
+  }
+  if (lane < 7) P.st.q[(size_t)lane * n + env] = aq[lane];
+  if (lane < 3) {
+    P.st.coff[(size_t)lane * n + env] = coff[lane];
+    P.st.ppre[(size_t)lane * n + env] = ppre[lane];
+  }
+  for (int j = lane; j < M; j += 32) {
+    P.st.obj[(size_t)env * M + j] = so[j];
+    if (P.out.obj_pos) reinterpret_cast<float4*>(P.out.obj_pos)[(size_t)env * M + j] = so[j];
+  }
+  // (a9) camera for the rasteriser
+  float cam[12];
+  camera(rb, ax, az, ayaw, cam);
+  if (lane < 12) {
+    float v = cam[0];
+#pragma unroll
+    for (int k = 1; k < 12; ++k) v = lane == k ? cam[k] : v;
+    P.cam[(size_t)env * 12 + lane] = v;
+  }
+  // (a11) observations other than images
+  if (P.out.pose && lane < 16) {
+    float v = 0.f;
+    if (lane < 7) {
+#pragma unroll
+      for (int k = 0; k < 7; ++k) v = lane == k ? aq[k] : v;
+    } else if (lane == 7) v = nheld >= 0 ? 1.f : 0.f;
+    else if (lane == 8) v = ax;
+    else if (lane == 9) v = az;
+    else if (lane == 10) v = ayaw;
+    else if (lane == 11) v = et[0];
+    else if (lane == 12) v = et[1];
+    else if (lane == 13) v = et[2];
+    else if (lane == 14) v = (float)stepc;
+    P.out.pose[(size_t)env * 16 + lane] = v;
+  }
+  if (lane == 0) {
+    if (P.out.held) P.out.held[env] = nheld;
+    if (P.out.contact_mask) P.out.contact_mask[env] = mask;
+    if (P.out.contact_flags) P.out.contact_flags[env] = flags;
+    if (P.out.event) P.out.event[env] = event;
+  }
+}
+
+// (a12) masked reset: objects on support tops, then the robot base in free
+// space, by rejection sampling with at most 64 Philox draws each.  Lane t
+// evaluates try t (two passes of 32); the lowest accepted try wins, which is
+// the same choice as trying them in order.
+__global__ void __launch_bounds__(32 * kEnvsPerBlock) reset_kernel(const ResetParams P) {
+  __shared__ float4 s_obj[kEnvsPerBlock][GX_MAX_OBJECTS];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int env = blockIdx.x * kEnvsPerBlock + w;
+  if (env >= P.n) return;
+  if (P.mask && !P.mask[env]) return;
+  const int n = P.n, M = P.M;
+  const DScene& S = P.scenes[P.env_scene[env]];
+  const gx_robot& rb = P.robot->r;
+  float4* so = s_obj[w];
+  const uint32_t ep = (uint32_t)P.st.episode[env] + 1u;
+  const uint2 key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
+  const float clear = rb.rest_clearance;
+  bool failed = false;
+  for (int j = 0; j < M; ++j) {
+    float rho = 0.f;
+    float4 pick = make_float4(0.f, 0.f, 0.f, 0.f);
+    bool placed = false;
+    for (int tb = 0; tb < 64 && !placed; tb += 32) {
+      const uint4 wv = philox4x32_10(make_uint4((uint32_t)env, ep, (uint32_t)j, (uint32_t)(tb + lane)), key);
+      if (tb == 0) rho = __shfl_sync(kFull, P.rho_min + unit24(wv.w) * (P.rho_max - P.rho_min), 0);
+      const uint32_t si = (uint32_t)(((uint64_t)(wv.x >> 8) * (uint64_t)S.n_supports) >> 24);
+      const float* sp = S.supports + 5 * si;
+      const float x0 = sp[0] + rho, x1 = sp[2] - rho, z0 = sp[1] + rho, z1 = sp[3] - rho;
+      const float px = x0 + unit24(wv.y) * (x1 - x0);
+      const float py = sp[4] + rho + clear;
+      const float pz = z0 + unit24(wv.z) * (z1 - z0);
+      float d;
+      bool ok = grid_query(S, px, py, pz, d) && !(d < rho);
+      for (int k = 0; k < j && ok; ++k) {
+        const float4 o = so[k];
+        const float dx = px - o.x, dy = py - o.y, dz = pz - o.z, rr = rho + o.w;
+        ok = !(dx * dx + dy * dy + dz * dz < rr * rr);
+      }
+      const unsigned b = __ballot_sync(kFull, ok);
+      const int L = b ? __ffs(b) - 1 : 31;
+      pick = make_float4(__shfl_sync(kFull, px, L), __shfl_sync(kFull, py, L),
+                         __shfl_sync(kFull, pz, L), rho);
+      placed = b != 0;
+    }
+    failed |= !placed;
+    __syncwarp();
+    if (lane == 0) so[j] = pick;
+    __syncwarp();
+  }
+  // robot base: every lane evaluates one try of the spawn rectangle
+  float q[7];
+#pragma unroll
+  for (int k = 0; k < 7; ++k) q[k] = rb.q_rest[k];
+  float bx = 0.f, bz = 0.f, byaw = 0.f;
+  bool placed = false;
+  for (int tb = 0; tb < 64 && !placed; tb += 32) {
+    const uint4 wv = philox4x32_10(make_uint4((uint32_t)env, ep, 64u, (uint32_t)(tb + lane)), key);
+    const float x = S.spawn[0] + unit24(wv.x) * (S.spawn[2] - S.spawn[0]);
+    const float z = S.spawn[1] + unit24(wv.y) * (S.spawn[3] - S.spawn[1]);
+    const float yaw = -CUDART_PI_F + unit24(wv.z) * (2.f * CUDART_PI_F);
+    bool ok = true;
+    for (int link = 0; link <= 7 && ok; ++link) {
+      float R[9], t[3], eR[9], et[3];
+      fk(rb, x, z, yaw, q, link, R, t, eR, et);
+      for (int i = 0; i < rb.n_spheres && ok; ++i) {
+        if (rb.sphere_link[i] != link) continue;
+        float c[3];
+        apply(R, t, rb.sphere_pos[i][0], rb.sphere_pos[i][1], rb.sphere_pos[i][2], c);
+        const float r = rb.sphere_radius[i];
+        float d;
+        ok = grid_query(S, c[0], c[1], c[2], d) && !(d < r);
+        for (int j = 0; j < M && ok; ++j) {
+          const float4 o = so[j];
+          const float dx = c[0] - o.x, dy = c[1] - o.y, dz = c[2] - o.z, rr = r + o.w;
+          ok = !(dx * dx + dy * dy + dz * dz < rr * rr);
+        }
+      }
+    }
+    const unsigned b = __ballot_sync(kFull, ok);
+    const int L = b ? __ffs(b) - 1 : 31;
+    bx = __shfl_sync(kFull, x, L);
+    bz = __shfl_sync(kFull, z, L);
+    byaw = __shfl_sync(kFull, yaw, L);
+    placed = b != 0;
+  }
+  failed |= !placed;
+  if (failed && lane == 0) atomicOr(P.err, GX_DEV_PLACEMENT_FAILED);
+  if (lane == 0) {
+    P.st.bx[env] = bx; P.st.bz[env] = bz; P.st.yaw[env] = byaw;
+    P.st.held[env] = -1;
+    P.st.step[env] = 0;
+    P.st.episode[env] = (int)ep;
+  }
+  if (lane < 7) P.st.q[(size_t)lane * n + env] = rb.q_rest[lane];
+  if (lane < 3) {
+    P.st.coff[(size_t)lane * n + env] = 0.f;
+    P.st.ppre[(size_t)lane * n + env] = 0.f;
+  }
+  for (int j = lane; j < M; j += 32) P.st.obj[(size_t)env * M + j] = so[j];
+  float cam[12];
+  camera(rb, bx, bz, byaw, cam);
+  if (lane < 12) {
+    float v = cam[0];
+#pragma unroll
+    for (int k = 1; k < 12; ++k) v = lane == k ? cam[k] : v;
+    P.cam[(size_t)env * 12 + lane] = v;
+  }
+}
+
+}  // namespace
+
+void launch_physics(const PhysicsParams& p, cudaStream_t s) {
+  const int blocks = (p.n + kEnvsPerBlock - 1) / kEnvsPerBlock;
+  physics_kernel<<<blocks, 32 * kEnvsPerBlock, 0, s>>>(p);
+}
+
+void launch_reset(const ResetParams& p, cudaStream_t s) {
+  const int blocks = (p.n + kEnvsPerBlock - 1) / kEnvsPerBlock;
+  reset_kernel<<<blocks, 32 * kEnvsPerBlock, 0, s>>>(p);
+}
+
+}  // namespace gx

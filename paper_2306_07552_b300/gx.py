@@ -1,0 +1,325 @@
+"""Python binding of the gx C ABI (include/gx.h): argument marshalling only.
+
+Every step of the environment update runs in the CUDA kernels of libgx.so;
+this module builds the C structs, allocates caller-owned output tensors with
+PyTorch (device memory and streams are all PyTorch is used for) and forwards
+calls.  There is no CPU fallback: without the library or a CUDA device the
+constructors raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import inputs as _inputs
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+SO_PATH = os.path.join(_HERE, "libgx.so")
+
+GX_OK, GX_EINVAL, GX_ENOMEM, GX_ECUDA, GX_EDEVICE, GX_ESTATE = range(6)
+GX_DEV_NONFINITE_ACTION = 0x1
+GX_DEV_PLACEMENT_FAILED = 0x2
+MAX_OBJECTS = 64
+MAX_SPHERES = 31
+
+SYMBOLS = ["gx_scene_set_create", "gx_scene_set_destroy", "gx_create", "gx_destroy", "gx_reset",
+           "gx_step", "gx_step_host", "gx_sync", "gx_device_error", "gx_state_bytes",
+           "gx_save_state", "gx_load_state", "gx_state_layout", "gx_last_error"]
+
+f32p = C.POINTER(C.c_float)
+i32p = C.POINTER(C.c_int32)
+u32p = C.POINTER(C.c_uint32)
+u8p = C.POINTER(C.c_uint8)
+
+
+class GxRobot(C.Structure):
+    _fields_ = [("link_offset", (C.c_float * 3) * 8), ("link_axis", C.c_int32 * 7),
+                ("q_min", C.c_float * 7), ("q_max", C.c_float * 7), ("q_rest", C.c_float * 7),
+                ("dq_max", C.c_float), ("base_step", C.c_float), ("base_turn", C.c_float),
+                ("n_spheres", C.c_int32), ("sphere_link", C.c_int32 * MAX_SPHERES),
+                ("sphere_pos", (C.c_float * 3) * MAX_SPHERES),
+                ("sphere_radius", C.c_float * MAX_SPHERES), ("cam_pos", C.c_float * 3),
+                ("cam_pitch", C.c_float), ("cam_near", C.c_float), ("grasp_radius", C.c_float),
+                ("rest_clearance", C.c_float)]
+
+
+class GxSceneDesc(C.Structure):
+    _fields_ = [("n_boxes", C.c_int32), ("boxes", f32p), ("n_verts", C.c_int32), ("verts", f32p),
+                ("n_tris", C.c_int32), ("tris", i32p), ("tri_rgb", u32p),
+                ("n_supports", C.c_int32), ("supports", f32p), ("grid_origin", C.c_float * 3),
+                ("grid_h", C.c_float), ("grid_dims", C.c_int32 * 3), ("spawn", C.c_float * 4)]
+
+
+class GxObjectMesh(C.Structure):
+    _fields_ = [("n_verts", C.c_int32), ("verts", f32p), ("n_tris", C.c_int32), ("tris", i32p),
+                ("obj_rgb", C.c_uint32 * MAX_OBJECTS)]
+
+
+class GxConfig(C.Structure):
+    _fields_ = [("n_envs", C.c_int32), ("img_w", C.c_int32), ("img_h", C.c_int32),
+                ("depth_fp16", C.c_int32), ("render_rgb", C.c_int32), ("n_objects", C.c_int32),
+                ("obj_radius_min", C.c_float), ("obj_radius_max", C.c_float),
+                ("seed", C.c_uint64), ("env_scene", i32p), ("raster_regions", C.c_int32),
+                ("small_tri_px", C.c_int32), ("use_graph", C.c_int32)]
+
+
+class GxOutputs(C.Structure):
+    _fields_ = [("depth", C.c_void_p), ("rgb", C.c_void_p), ("pose", C.c_void_p),
+                ("obj_pos", C.c_void_p), ("held", C.c_void_p), ("contact_mask", C.c_void_p),
+                ("contact_flags", C.c_void_p), ("event", C.c_void_p)]
+
+
+class GxError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"gx status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Loads libgx.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(SO_PATH):
+            raise RuntimeError(f"{SO_PATH} is missing: run paper_2306_07552_b300.build.build()")
+        L = C.CDLL(SO_PATH)
+        P = C.POINTER
+        vp = C.c_void_p
+        L.gx_scene_set_create.argtypes = [P(GxSceneDesc), C.c_int32, P(GxObjectMesh), P(vp)]
+        L.gx_scene_set_destroy.argtypes = [vp]
+        L.gx_create.argtypes = [vp, P(GxRobot), P(GxConfig), P(vp)]
+        L.gx_destroy.argtypes = [vp]
+        L.gx_destroy.restype = None
+        L.gx_reset.argtypes = [vp, vp, vp]
+        L.gx_step.argtypes = [vp, vp, P(GxOutputs), vp]
+        L.gx_step_host.argtypes = [vp, vp, P(GxOutputs), vp]
+        L.gx_sync.argtypes = [vp]
+        L.gx_device_error.argtypes = [vp]
+        L.gx_device_error.restype = C.c_uint32
+        L.gx_state_bytes.argtypes = [vp]
+        L.gx_state_bytes.restype = C.c_size_t
+        L.gx_save_state.argtypes = [vp, vp, C.c_size_t]
+        L.gx_load_state.argtypes = [vp, vp, C.c_size_t]
+        L.gx_state_layout.argtypes = [vp, P(C.c_size_t)]
+        L.gx_last_error.argtypes = [vp]
+        L.gx_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(status, ctx=None):
+    if status != GX_OK:
+        msg = lib().gx_last_error(ctx).decode(errors="replace")
+        raise GxError(status, msg)
+
+
+def robot_struct(r: _inputs.Robot) -> GxRobot:
+    g = GxRobot()
+    for k in range(8):
+        g.link_offset[k][:] = [float(x) for x in r.link_offset[k]]
+    g.link_axis[:] = [int(x) for x in r.link_axis]
+    g.q_min[:] = [float(x) for x in r.q_min]
+    g.q_max[:] = [float(x) for x in r.q_max]
+    g.q_rest[:] = [float(x) for x in r.q_rest]
+    g.dq_max, g.base_step, g.base_turn = r.dq_max, r.base_step, r.base_turn
+    S = len(r.sphere_radius)
+    g.n_spheres = S
+    for i in range(S):
+        g.sphere_link[i] = int(r.sphere_link[i])
+        g.sphere_pos[i][:] = [float(x) for x in r.sphere_pos[i]]
+        g.sphere_radius[i] = float(r.sphere_radius[i])
+    g.cam_pos[:] = [float(x) for x in r.cam_pos]
+    g.cam_pitch, g.cam_near = r.cam_pitch, r.cam_near
+    g.grasp_radius, g.rest_clearance = r.grasp_radius, r.rest_clearance
+    return g
+
+
+class SceneSet:
+    """Device copies of a list of scenes (grid, clusters, supports)."""
+
+    def __init__(self, scenes, obj_mesh=None, obj_rgb=None):
+        self._keep = []
+        n = len(scenes)
+        descs = (GxSceneDesc * n)()
+        for i, s in enumerate(scenes):
+            arrs = [np.ascontiguousarray(s.boxes, np.float32), np.ascontiguousarray(s.verts, np.float32),
+                    np.ascontiguousarray(s.tris, np.int32), np.ascontiguousarray(s.tri_rgb, np.uint32),
+                    np.ascontiguousarray(s.supports, np.float32)]
+            self._keep += arrs
+            b, v, t, c, sp = arrs
+            d = descs[i]
+            d.n_boxes, d.boxes = len(b), b.ctypes.data_as(f32p)
+            d.n_verts, d.verts = len(v), v.ctypes.data_as(f32p)
+            d.n_tris, d.tris, d.tri_rgb = len(t), t.ctypes.data_as(i32p), c.ctypes.data_as(u32p)
+            d.n_supports, d.supports = len(sp), sp.ctypes.data_as(f32p)
+            d.grid_origin[:] = [float(x) for x in s.grid_origin]
+            d.grid_h = float(s.grid_h)
+            d.grid_dims[:] = [int(x) for x in s.grid_dims]
+            d.spawn[:] = [float(x) for x in s.spawn]
+        mv, mt = obj_mesh if obj_mesh is not None else _inputs.icosahedron()
+        mv = np.ascontiguousarray(mv, np.float32)
+        mt = np.ascontiguousarray(mt, np.int32)
+        self._keep += [mv, mt]
+        m = GxObjectMesh()
+        m.n_verts, m.verts = len(mv), mv.ctypes.data_as(f32p)
+        m.n_tris, m.tris = len(mt), mt.ctypes.data_as(i32p)
+        rgb = _inputs.object_colors(MAX_OBJECTS) if obj_rgb is None else obj_rgb
+        m.obj_rgb[:] = [int(x) for x in np.asarray(rgb, np.uint32)[:MAX_OBJECTS]]
+        self.n_obj_tris = len(mt)
+        self.handle = C.c_void_p()
+        _check(lib().gx_scene_set_create(descs, n, C.byref(m), C.byref(self.handle)))
+        self._keep = []   # the library copied everything
+        self.n = n
+
+    def close(self):
+        if self.handle:
+            lib().gx_scene_set_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+STATE_FIELDS = ["base_x", "base_z", "yaw", "q", "held", "c_off", "p_pre", "obj", "step", "episode"]
+
+
+class Sim:
+    """A batch of environments stepped by libgx on the current CUDA device."""
+
+    def __init__(self, scene_set: SceneSet, robot: _inputs.Robot, n_envs: int, img=(128, 128),
+                 depth_fp16=False, render_rgb=True, n_objects=40, obj_radius=(0.03, 0.06),
+                 seed=1, env_scene=None, raster_regions=0, small_tri_px=0, use_graph=False):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("gx needs a CUDA device; there is no CPU fallback")
+        self.torch = torch
+        self.scene_set = scene_set
+        self.n, self.W, self.H, self.M = n_envs, img[0], img[1], n_objects
+        self.depth_fp16, self.render_rgb = bool(depth_fp16), bool(render_rgb)
+        cfg = GxConfig()
+        cfg.n_envs, cfg.img_w, cfg.img_h = n_envs, img[0], img[1]
+        cfg.depth_fp16, cfg.render_rgb, cfg.n_objects = int(depth_fp16), int(render_rgb), n_objects
+        cfg.obj_radius_min, cfg.obj_radius_max = obj_radius
+        cfg.seed = seed
+        es = None
+        if env_scene is not None:
+            es = np.ascontiguousarray(env_scene, np.int32)
+            cfg.env_scene = es.ctypes.data_as(i32p)
+        cfg.raster_regions, cfg.small_tri_px, cfg.use_graph = raster_regions, small_tri_px, int(use_graph)
+        self.robot_c = robot_struct(robot)
+        self.handle = C.c_void_p()
+        _check(lib().gx_create(scene_set.handle, C.byref(self.robot_c), C.byref(cfg),
+                               C.byref(self.handle)))
+        dev = torch.device("cuda")
+        self.out = dict(
+            depth=torch.zeros((n_envs, img[1], img[0]),
+                              dtype=torch.float16 if depth_fp16 else torch.float32, device=dev),
+            rgb=torch.zeros((n_envs, img[1], img[0], 3), dtype=torch.uint8, device=dev)
+            if render_rgb else None,
+            pose=torch.zeros((n_envs, 16), dtype=torch.float32, device=dev),
+            obj_pos=torch.zeros((n_envs, max(n_objects, 1), 4), dtype=torch.float32, device=dev),
+            held=torch.zeros(n_envs, dtype=torch.int32, device=dev),
+            contact_mask=torch.zeros(n_envs, dtype=torch.int32, device=dev),
+            contact_flags=torch.zeros(n_envs, dtype=torch.uint8, device=dev),
+            event=torch.zeros(n_envs, dtype=torch.uint8, device=dev),
+        )
+        self._outs = self._outputs_struct(self.out)
+
+    @staticmethod
+    def _outputs_struct(d):
+        o = GxOutputs()
+        for k in ["depth", "rgb", "pose", "obj_pos", "held", "contact_mask", "contact_flags", "event"]:
+            v = d.get(k)
+            setattr(o, k, None if v is None else (v.data_ptr() if hasattr(v, "data_ptr")
+                                                  else v.ctypes.data))
+        return o
+
+    def _stream(self, stream):
+        s = stream if stream is not None else self.torch.cuda.current_stream()
+        return C.c_void_p(s.cuda_stream)
+
+    def reset(self, mask=None, stream=None):
+        ptr = None if mask is None else C.c_void_p(mask.data_ptr())
+        _check(lib().gx_reset(self.handle, ptr, self._stream(stream)), self.handle)
+
+    def step(self, actions, stream=None):
+        """actions: CUDA float32 tensor [n][11]; returns the output tensors."""
+        assert actions.is_cuda and actions.dtype == self.torch.float32 and actions.is_contiguous()
+        assert tuple(actions.shape) == (self.n, 11)
+        _check(lib().gx_step(self.handle, C.c_void_p(actions.data_ptr()), C.byref(self._outs),
+                             self._stream(stream)), self.handle)
+        return self.out
+
+    def host_outputs(self, pinned=True):
+        """Host buffers (pinned torch tensors) matching the outputs of step()."""
+        t = self.torch
+        d = {k: (None if v is None else t.empty(v.shape, dtype=v.dtype, pin_memory=pinned))
+             for k, v in self.out.items()}
+        return d
+
+    def step_host(self, actions_host, host_out, stream=None):
+        """Same step through host buffers: copies in, steps, copies every
+        output back; returns when the host buffers hold the results."""
+        o = self._outputs_struct(host_out)
+        ptr = actions_host.data_ptr() if hasattr(actions_host, "data_ptr") else actions_host.ctypes.data
+        _check(lib().gx_step_host(self.handle, C.c_void_p(ptr), C.byref(o), self._stream(stream)),
+               self.handle)
+        return host_out
+
+    def sync(self):
+        _check(lib().gx_sync(self.handle), self.handle)
+
+    def device_error(self):
+        return int(lib().gx_device_error(self.handle))
+
+    # ------------------------------------------------------------- state
+    def state_bytes(self):
+        return int(lib().gx_state_bytes(self.handle))
+
+    def save_state(self) -> np.ndarray:
+        buf = np.zeros(self.state_bytes(), np.uint8)
+        _check(lib().gx_save_state(self.handle, buf.ctypes.data, buf.nbytes), self.handle)
+        return buf
+
+    def load_state(self, buf: np.ndarray):
+        buf = np.ascontiguousarray(buf, np.uint8)
+        _check(lib().gx_load_state(self.handle, buf.ctypes.data, buf.nbytes), self.handle)
+
+    def layout(self):
+        offs = (C.c_size_t * 10)()
+        _check(lib().gx_state_layout(self.handle, offs), self.handle)
+        return list(offs)
+
+    def state_arrays(self, buf=None):
+        """Views of a saved state blob as named numpy arrays."""
+        buf = self.save_state() if buf is None else buf
+        o = self.layout()
+        n, M = self.n, max(self.M, 1)
+
+        def arr(k, dt, shape):
+            cnt = int(np.prod(shape))
+            return np.frombuffer(buf, dt, cnt, o[k]).reshape(shape)
+
+        return dict(base_x=arr(0, np.float32, (n,)), base_z=arr(1, np.float32, (n,)),
+                    yaw=arr(2, np.float32, (n,)), q=arr(3, np.float32, (7, n)),
+                    held=arr(4, np.int32, (n,)), c_off=arr(5, np.float32, (3, n)),
+                    p_pre=arr(6, np.float32, (3, n)), obj=arr(7, np.float32, (n, M, 4)),
+                    step=arr(8, np.int32, (n,)), episode=arr(9, np.int32, (n,)))
+
+    def close(self):
+        if self.handle:
+            lib().gx_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,114 @@
+"""Helpers comparing the CUDA path (through the C ABI) with the FP64 oracle.
+
+Protocol (lockstep): for every checked environment the oracle starts from the
+GPU's FP32 state before the step, widened to FP64, applies the same actions
+and must reproduce the GPU's state after the step.  Discrete results (contact
+masks, flags, grasp events, held index) must match bit for bit unless the
+oracle reports a decision within 1e-4 m of its threshold ("near band"; such
+environments are counted and skipped).  Continuous results must agree within
+1e-5 m / rad.  Images are rendered by the oracle from the GPU's state after
+the step; on pixels the oracle does not flag as ambiguous, coverage and RGB
+must match exactly and depth within 1e-5 relative.
+"""
+import math
+
+import numpy as np
+
+import oracle as O
+
+POSE_TOL = 1e-5
+DEPTH_REL = 1e-5
+
+
+def oracle_state(arrs, e, M):
+    return O.Oracle.make_state((float(arrs["base_x"][e]), float(arrs["base_z"][e]),
+                                float(arrs["yaw"][e])), arrs["q"][:, e], int(arrs["held"][e]),
+                               arrs["c_off"][:, e], arrs["p_pre"][:, e], arrs["obj"][e, :M],
+                               int(arrs["step"][e]), int(arrs["episode"][e]))
+
+
+def ang_diff(a, b):
+    d = (a - b) % (2 * math.pi)
+    return min(d, 2 * math.pi - d)
+
+
+class Tally:
+    def __init__(self):
+        self.envs = 0
+        self.near_band = 0
+        self.events = {}
+        self.contacts = 0
+        self.pixels = 0
+        self.ambiguous = 0
+        self.max_pose_err = 0.0
+        self.max_depth_rel = 0.0
+
+    def __repr__(self):
+        return (f"envs={self.envs} near_band={self.near_band} contacts={self.contacts} "
+                f"events={self.events} pixels={self.pixels} ambiguous={self.ambiguous} "
+                f"max_pose_err={self.max_pose_err:.2e} max_depth_rel={self.max_depth_rel:.2e}")
+
+
+def check_step(orc, before, after, out, acts, envs, M, tally):
+    """Physics parity of one step for the listed environments."""
+    mask = out["contact_mask"].cpu().numpy().view(np.uint32)
+    flags = out["contact_flags"].cpu().numpy()
+    event = out["event"].cpu().numpy()
+    held = out["held"].cpu().numpy()
+    pose = out["pose"].cpu().numpy()
+    objo = out["obj_pos"].cpu().numpy()
+    for e in envs:
+        st = oracle_state(before, e, M)
+        o = orc.step(st, acts[e])
+        tally.envs += 1
+        if o.near_band:
+            tally.near_band += 1
+            continue
+        assert mask[e] == o.contact_mask, (e, hex(mask[e]), hex(o.contact_mask))
+        assert flags[e] == o.flags, (e, flags[e], o.flags)
+        assert event[e] == o.event, (e, event[e], o.event)
+        assert held[e] == st.held == after["held"][e], (e, held[e], st.held)
+        tally.contacts += int(o.contact_mask != 0)
+        tally.events[int(o.event)] = tally.events.get(int(o.event), 0) + 1
+        errs = [abs(after["base_x"][e] - st.base[0]), abs(after["base_z"][e] - st.base[1]),
+                ang_diff(after["yaw"][e], st.base[2])]
+        errs += list(np.abs(after["q"][:, e] - np.array(list(st.q))))
+        errs += list(np.abs(pose[e, 11:14] - np.array(list(o.ee))))
+        so = O.Oracle.state_objs(st)
+        errs += list(np.abs(after["obj"][e, :M, :4] - so).ravel())
+        errs += list(np.abs(objo[e, :M] - so).ravel())
+        if st.held >= 0:
+            errs += list(np.abs(after["c_off"][:, e] - np.array(list(st.c_off))))
+            errs += list(np.abs(after["p_pre"][:, e] - np.array(list(st.p_pre))))
+        m = float(max(errs))
+        tally.max_pose_err = max(tally.max_pose_err, m)
+        assert m <= POSE_TOL, (e, m)
+        assert pose[e, 7] == (1.0 if st.held >= 0 else 0.0)
+        assert pose[e, 14] == st.step_count
+
+
+def check_image(orc, after, out, e, W, H, M, tally, fp16=False):
+    st = oracle_state(after, e, M)
+    depth, rgb, amb, win, stats = orc.render(st, W, H)
+    gd = out["depth"][e].float().cpu().numpy().astype(np.float64)
+    ok = ~amb
+    tally.pixels += int(ok.sum())
+    tally.ambiguous += int(amb.sum())
+    assert np.array_equal(gd[ok] > 0, depth[ok] > 0), (e, int(((gd > 0) != (depth > 0))[ok].sum()))
+    if out.get("rgb") is not None:
+        g = out["rgb"][e].cpu().numpy().astype(np.uint32)
+        grgb = (g[..., 0] << 16) | (g[..., 1] << 8) | g[..., 2]
+        bad = ok & (grgb != rgb)
+        assert not bad.any(), (e, int(bad.sum()))
+    cov = ok & (depth > 0)
+    if fp16:
+        ulp = np.spacing(depth[cov].astype(np.float16)).astype(np.float64)
+        lim = 0.5 * ulp + DEPTH_REL * depth[cov]
+        err = np.abs(gd[cov] - depth[cov])
+        assert np.all(err <= lim), (e, float((err - lim).max()))
+    else:
+        rel = np.abs(gd[cov] - depth[cov]) / depth[cov]
+        if rel.size:
+            tally.max_depth_rel = max(tally.max_depth_rel, float(rel.max()))
+        assert np.all(rel <= DEPTH_REL), (e, float(rel.max()))
+    return stats

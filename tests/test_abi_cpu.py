@@ -1,0 +1,60 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads,
+exports every entry point include/gx.h declares, and rejects bad arguments
+with GX_EINVAL before touching the device."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2306_07552_b300 import build as B
+from paper_2306_07552_b300 import gx
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    B.build()
+    return gx.lib()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "gx.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gx_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(L):
+    names = declared_functions()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(L, n), n
+    assert sorted(gx.SYMBOLS) == names
+
+
+def test_struct_sizes_match_header():
+    # all-4-byte robot table: no padding anywhere
+    assert C.sizeof(gx.GxRobot) == 4 * (24 + 7 + 21 + 3 + 1 + 31 + 93 + 31 + 3 + 4)
+    assert C.sizeof(gx.GxOutputs) == 8 * 8
+    assert gx.GxConfig.seed.offset == 32
+
+
+def test_null_arguments_are_rejected(L):
+    out = C.c_void_p()
+    assert L.gx_create(None, None, None, C.byref(out)) == gx.GX_EINVAL
+    assert L.gx_scene_set_create(None, 0, None, C.byref(out)) == gx.GX_EINVAL
+    assert L.gx_step(None, None, None, None) == gx.GX_EINVAL
+    assert L.gx_reset(None, None, None) == gx.GX_EINVAL
+    assert b"NULL" in L.gx_last_error(None) or L.gx_last_error(None)
+
+
+def test_bad_scene_is_rejected_before_device_work(L):
+    import numpy as np
+    from paper_2306_07552_b300 import inputs as I
+    s = I.room_scene(3, 300, n_furniture=2)
+    s.tris = s.tris.copy()
+    s.tris[0, 0] = 10 ** 6          # index out of range
+    with pytest.raises(gx.GxError) as e:
+        gx.SceneSet([s])
+    assert e.value.status == gx.GX_EINVAL

@@ -1,0 +1,293 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the FP64
+oracle (lockstep protocol described in tests/parity.py)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2306_07552_b300 import inputs as I
+from tests.parity import Tally, check_image, check_step, oracle_state
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+ROBOT = I.fetch_like_robot()
+
+
+def _gx():
+    from paper_2306_07552_b300 import build, gx
+    build.build()
+    return gx
+
+
+@pytest.fixture(scope="module")
+def room():
+    gx = _gx()
+    scene = I.room_scene(1000, 2000)
+    ss = gx.SceneSet([scene])
+    orc = O.Oracle(ROBOT, scene, I.icosahedron(), I.object_colors(64))
+    yield gx, scene, ss, orc
+    ss.close()
+
+
+def _run_lockstep(sim, orc, acts, M, W, H, img_envs, tally, fp16=False):
+    """Steps the GPU batch and checks every env's physics and the listed
+    envs' images against the oracle at every step."""
+    n = sim.n
+    for t in range(len(acts)):
+        before = {k: v.copy() for k, v in sim.state_arrays().items()}
+        out = sim.step(torch.from_numpy(acts[t]).cuda())
+        torch.cuda.synchronize()
+        after = sim.state_arrays()
+        check_step(orc, before, after, out, acts[t], range(n), M, tally)
+        for e in img_envs(t):
+            check_image(orc, after, out, e, W, H, M, tally, fp16=fp16)
+
+
+def test_reset_matches_oracle(room):
+    gx, scene, ss, orc = room
+    n, M = 16, 10
+    sim = gx.Sim(ss, ROBOT, n, img=(64, 64), n_objects=M, obj_radius=(0.03, 0.06), seed=1)
+    sim.reset()
+    sim.sync()
+    s = sim.state_arrays()
+    nb = 0
+    for e in range(n):
+        st = O.Oracle.make_state((0, 0, 0), np.zeros(7))
+        r = orc.reset(st, 1, e, M, 0.03, 0.06)
+        assert r.failed == 0
+        if r.near_band:
+            nb += 1
+            continue
+        assert s["episode"][e] == st.episode == 1
+        assert s["held"][e] == -1 and s["step"][e] == 0
+        assert np.allclose(s["obj"][e, :M], O.Oracle.state_objs(st), atol=1e-5)
+        assert abs(s["base_x"][e] - st.base[0]) < 1e-5 and abs(s["base_z"][e] - st.base[1]) < 1e-5
+        d = (s["yaw"][e] - st.base[2]) % (2 * math.pi)
+        assert min(d, 2 * math.pi - d) < 1e-5
+        assert np.allclose(s["q"][:, e], ROBOT.q_rest, atol=0)
+    assert nb <= 2
+    # a second reset starts episode 2 with a new placement
+    sim.reset()
+    s2 = sim.state_arrays()
+    assert (s2["episode"] == 2).all()
+    assert not np.array_equal(s2["obj"], s["obj"])
+    assert sim.device_error() == 0
+    sim.close()
+
+
+def test_room16_trajectory_lockstep(room):
+    """16 envs sharing one room, 64x64 camera, 10 objects, 20 uniform-random
+    steps: every env's physics and every image at every step."""
+    gx, scene, ss, orc = room
+    n, M, W = 16, 10, 64
+    sim = gx.Sim(ss, ROBOT, n, img=(W, W), n_objects=M, obj_radius=(0.03, 0.06), seed=1)
+    sim.reset()
+    acts = I.make_actions(20, n, "uniform", seed=0)
+    tally = Tally()
+    _run_lockstep(sim, orc, acts, M, W, W, lambda t: range(n), tally)
+    print(tally)
+    assert tally.envs == 320 and tally.near_band <= 8
+    assert tally.ambiguous < 0.03 * (tally.pixels + tally.ambiguous)
+    assert sim.device_error() == 0
+    sim.close()
+
+
+def _grasp_states(sim, orc, M):
+    """Puts object 0 of every env just in front of the suction tip."""
+    s = sim.state_arrays()
+    buf = sim.save_state()
+    o = sim.layout()
+    obj = np.frombuffer(buf, np.float32, sim.n * max(M, 1) * 4, o[7]).reshape(sim.n, max(M, 1), 4)
+    obj = obj.copy()
+    for e in range(sim.n):
+        _, ee, _ = orc.fk((s["base_x"][e], s["base_z"][e], s["yaw"][e]), s["q"][:, e])
+        R, t = ee[:9].reshape(3, 3), ee[9:]
+        p = t + R @ np.array([0.05, 0.0, 0.0])
+        obj[e, 0, :3] = p
+        obj[e, 0, 3] = 0.035
+    buf = buf.copy()
+    buf[o[7]:o[7] + obj.nbytes] = obj.view(np.uint8).ravel()
+    sim.load_state(buf)
+
+
+def test_grasp_carry_release(room):
+    gx, scene, ss, orc = room
+    n, M, W = 16, 10, 64
+    sim = gx.Sim(ss, ROBOT, n, img=(W, W), n_objects=M, obj_radius=(0.03, 0.06), seed=3)
+    sim.reset()
+    _grasp_states(sim, orc, M)
+    rng = np.random.default_rng(1)
+    acts = np.zeros((8, n, 11), np.float32)
+    acts[:, :, 2:9] = rng.uniform(-1, 1, (8, n, 7)) * 0.5
+    acts[:, :, 0] = rng.uniform(-1, 1, (8, n)) * 0.3
+    acts[:5, :, 9] = 1.0    # grasp and carry for 5 steps, then release
+    tally = Tally()
+    _run_lockstep(sim, orc, acts, M, W, W, lambda t: [0, 5] if t in (0, 5) else [], tally)
+    print(tally)
+    assert tally.events.get(1, 0) >= 12
+    assert tally.events.get(3, 0) + tally.events.get(4, 0) >= 10
+    sim.close()
+
+
+def test_edge_sizes_and_no_objects(room):
+    gx, scene, ss, orc = room
+    for n, M in [(1, 0), (13, 1), (5, 64)]:
+        sim = gx.Sim(ss, ROBOT, n, img=(32, 64), n_objects=M, obj_radius=(0.03, 0.04), seed=7)
+        sim.reset()
+        acts = I.make_actions(3, n, "uniform", seed=n)
+        tally = Tally()
+        for t in range(3):
+            before = {k: v.copy() for k, v in sim.state_arrays().items()}
+            out = sim.step(torch.from_numpy(acts[t]).cuda())
+            torch.cuda.synchronize()
+            after = sim.state_arrays()
+            check_step(orc, before, after, out, acts[t], range(n), M, tally)
+            check_image(orc, after, out, n - 1, 32, 64, M, tally)
+        sim.close()
+
+
+def test_graph_replay_and_determinism(room):
+    gx, scene, ss, orc = room
+    n, M, W = 16, 10, 64
+    res = []
+    for use_graph in (False, True, True):
+        sim = gx.Sim(ss, ROBOT, n, img=(W, W), n_objects=M, seed=11, use_graph=use_graph)
+        sim.reset()
+        acts = torch.from_numpy(I.make_actions(6, n, "uniform", seed=4)).cuda()
+        abuf = torch.empty_like(acts[0])     # one action buffer: the graph is replayed
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            for t in range(6):
+                abuf.copy_(acts[t])
+                out = sim.step(abuf)
+        torch.cuda.synchronize()
+        res.append((out["depth"].cpu().numpy().tobytes(), out["rgb"].cpu().numpy().tobytes(),
+                    sim.save_state().tobytes()))
+        sim.close()
+    assert res[0] == res[1] == res[2]
+
+
+def test_nonfinite_actions_report_and_count_as_zero(room):
+    gx, scene, ss, orc = room
+    n, M = 4, 10
+    sim = gx.Sim(ss, ROBOT, n, img=(64, 64), n_objects=M, seed=5)
+    sim.reset()
+    before = {k: v.copy() for k, v in sim.state_arrays().items()}
+    a = I.make_actions(1, n, "uniform", seed=2)[0]
+    a[1, 0] = np.nan
+    a[2, 3] = np.inf
+    out = sim.step(torch.from_numpy(a).cuda())
+    with pytest.raises(gx.GxError) as err:
+        sim.sync()
+    assert err.value.status == gx.GX_EDEVICE
+    after = sim.state_arrays()
+    clean = a.copy()
+    clean[~np.isfinite(clean)] = 0.0
+    tally = Tally()
+    check_step(orc, before, after, out, clean, range(n), M, tally)
+    sim.sync()   # the word was cleared
+    sim.close()
+
+
+def test_save_load_and_host_step(room):
+    gx, scene, ss, orc = room
+    n, M = 8, 10
+    sim = gx.Sim(ss, ROBOT, n, img=(64, 64), n_objects=M, seed=9)
+    sim.reset()
+    snap = sim.save_state()
+    acts = I.make_actions(3, n, "uniform", seed=8)
+    for t in range(3):
+        out = sim.step(torch.from_numpy(acts[t]).cuda())
+    torch.cuda.synchronize()
+    ref = {k: (None if v is None else v.cpu().clone()) for k, v in out.items()}
+    ref_state = sim.save_state()
+    sim.load_state(snap)
+    host = sim.host_outputs()
+    for t in range(3):
+        sim.step_host(torch.from_numpy(acts[t]).pin_memory(), host)
+    for k, v in ref.items():
+        if v is not None:
+            assert torch.equal(v, host[k]), k
+    assert np.array_equal(ref_state, sim.save_state())
+    sim.close()
+
+
+@pytest.fixture(scope="module")
+def apartments():
+    gx = _gx()
+    w = I.WORKLOADS["apartments4096"]
+    scenes = I.make_scenes(w)
+    ss = gx.SceneSet(scenes)
+    yield gx, w, scenes, ss
+    ss.close()
+
+
+def test_apartments_full_size_sampled(apartments):
+    """The bench workload (4096 envs, 16 apartments of 20k-60k triangles,
+    2 cm grid, 40 objects, 128x128 FP32 depth + RGB8) in the bench's launch
+    configuration; physics checked on 256 sampled envs per step, images on
+    8 envs."""
+    gx, w, scenes, ss = apartments
+    n, M, W = w.n_envs, w.n_objects, w.img
+    sim = gx.Sim(ss, ROBOT, n, img=(W, W), n_objects=M, obj_radius=w.obj_radius,
+                 seed=w.reset_seed, use_graph=True)
+    sim.reset()
+    assert sim.device_error() == 0
+    env_scene = I.env_scene_map(n, w.n_scenes)
+    orcs = {s: O.Oracle(ROBOT, scenes[s], I.icosahedron(), I.object_colors(64))
+            for s in range(w.n_scenes)}
+    rng = np.random.default_rng(0)
+    acts = I.make_actions(3, n, w.action_dist, seed=w.action_seed)
+    tally = Tally()
+    stream = torch.cuda.Stream()
+    for t in range(3):
+        before = {k: v.copy() for k, v in sim.state_arrays().items()}
+        with torch.cuda.stream(stream):
+            out = sim.step(torch.from_numpy(acts[t]).cuda())
+        torch.cuda.synchronize()
+        after = sim.state_arrays()
+        envs = sorted(rng.choice(n, 256, replace=False))
+        for e in envs:
+            check_step(orcs[int(env_scene[e])], before, after, out, acts[t], [e], M, tally)
+        if t == 2:
+            for e in envs[:8]:
+                check_image(orcs[int(env_scene[e])], after, out, e, W, W, M, tally)
+    print(tally)
+    assert tally.near_band <= 0.05 * tally.envs
+    assert tally.ambiguous < 0.05 * (tally.pixels + tally.ambiguous)
+    sim.close()
+
+
+def test_uneven_fp16_sampled():
+    """64 scenes with log-uniform 5k-150k triangles, FP16 depth: physics on
+    sampled envs, images of the largest and smallest scenes."""
+    gx = _gx()
+    w = I.WORKLOADS["uneven8192"]
+    scenes = I.make_scenes(w)
+    ss = gx.SceneSet(scenes)
+    n, M, W = w.n_envs, w.n_objects, w.img
+    sim = gx.Sim(ss, ROBOT, n, img=(W, W), depth_fp16=True, render_rgb=False, n_objects=M,
+                 obj_radius=w.obj_radius, seed=w.reset_seed, use_graph=True)
+    sim.reset()
+    env_scene = I.env_scene_map(n, w.n_scenes)
+    tris = [s.n_tris for s in scenes]
+    big, small = int(np.argmax(tris)), int(np.argmin(tris))
+    acts = I.make_actions(1, n, w.action_dist, seed=w.action_seed)
+    before = {k: v.copy() for k, v in sim.state_arrays().items()}
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        out = sim.step(torch.from_numpy(acts[0]).cuda())
+    torch.cuda.synchronize()
+    after = sim.state_arrays()
+    tally = Tally()
+    for s in (big, small):
+        orc = O.Oracle(ROBOT, scenes[s], I.icosahedron(), I.object_colors(64))
+        envs = np.nonzero(env_scene == s)[0][:32]
+        check_step(orc, before, after, out, acts[0], envs, M, tally)
+        for e in envs[:3]:
+            check_image(orc, after, out, int(e), W, W, M, tally, fp16=True)
+    print(tally, tris[big], tris[small])
+    sim.close()
+    ss.close()
