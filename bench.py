@@ -1,0 +1,421 @@
+#!/usr/bin/env python
+"""Benchmark of the batched environment step (Galactic, arXiv 2306.07552).
+
+Metric: sim steps/sec = environments x steps / device time of the timed loop
+(render + kinematics + collision, resets included at the workload's rate).
+Default workload: 4096 envs over 16 procedural apartments (20k-60k
+triangles, 2 cm distance grid), 40 objects per env, 128x128 FP32 depth +
+RGB8, Gaussian actions, 200-step episodes (staggered: every step resets the
+envs whose episode ends).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gx|reference]
+
+Under torchrun every rank runs its own full batch on its own GPU (weak
+scaling, no collective on the data path); rank 0 prints one JSON line.
+--impl reference times the FP64 CPU oracle on the host on a bounded sample
+of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import dataclasses
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2306_07552_b300 import inputs as I  # noqa: E402
+
+METRIC = "sim steps/sec (render+kinematics+collision) on 1 B300; fraction of roofline"
+UNIT = "env-steps/s"
+# Minimal per-unit work of the rasteriser in lane operations, for its ALU
+# roofline: one front-facing triangle reaching the image (its share of the
+# vertex transform, plane, orientation, bounding box, edge setup) and one
+# covered fragment (three edge tests, depth plane, key, depth test).
+C_TRI = 70
+C_FRAG = 10
+SMS, LANES = 148, 128
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 7:
+                self.rows.append(p)
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [v for v in (num(r[0]) for r in self.rows) if v is not None]
+        mx = [v for v in (num(r[1]) for r in self.rows) if v is not None]
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        reasons = [n for k, n in enumerate(self.NAMES)
+                   if any(r[3 + k].lower() == "active" for r in self.rows)]
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+def golden(name):
+    p = os.path.join(ROOT, "tests", "golden", name)
+    return json.load(open(p)) if os.path.exists(p) else None
+
+
+def raster_work(workload):
+    """Per-view triangles set up and fragments covered, measured by the
+    oracle on a sample of the workload (written by oracle/raster_work.py)."""
+    return golden(f"raster_work_{workload.split('-')[0]}.json")
+
+
+def kernel_traffic(workload):
+    """DRAM bytes per rasteriser launch scaled to the full workload from an
+    ncu capture of a smaller case; None once the rasteriser source changed."""
+    p = os.path.join(ROOT, "profiles", f"raster_{workload}_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    src = open(os.path.join(ROOT, "paper_2306_07552_b300", "csrc", "gx_raster.cu"), "rb").read()
+    if d.get("source_sha1") != hashlib.sha1(src).hexdigest():
+        return None
+    return d.get("bytes_per_launch_full")
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), float(d.get("sm_max_mhz", 2032.0)), "measured"
+    return 6400.0, 2032.0, "fallback"
+
+
+def reset_masks(n, period):
+    masks = np.zeros((period, n), np.uint8)
+    for t in range(period):
+        masks[t, (np.arange(n) + t) % period == 0] = 1
+    return masks
+
+
+def work_counters(ss, w, acts, mask_at, steps):
+    """Rasteriser work counters per view from a separate, untimed context
+    running the counting variant of the kernel."""
+    from paper_2306_07552_b300 import gx
+    sim = gx.Sim(ss, I.fetch_like_robot(), w.n_envs, img=(w.img, w.img),
+                 depth_fp16=w.depth_fp16, render_rgb=w.rgb, n_objects=w.n_objects,
+                 obj_radius=w.obj_radius, seed=w.reset_seed, profile=3)
+    sim.reset()
+    for t in range(steps):
+        sim.reset(mask_at(t))
+        sim.step(acts[t])
+    c = sim.raster_counters()
+    sim.close()
+    return {k: v / (steps * w.n_envs) for k, v in c.items()}
+
+
+def cpu_baseline(w, scenes, seconds):
+    """The FP64 oracle on the host, single-threaded, on a bounded sample of
+    the same workload: 8 envs spread over the scenes, reset, then stepped
+    and rendered until `seconds` of CPU time are spent."""
+    import oracle as O
+    robot = I.fetch_like_robot()
+    env_scene = I.env_scene_map(w.n_envs, w.n_scenes)
+    sample_envs = [int(e) for e in np.linspace(0, w.n_envs - 1, 8)]
+    orcs, states = {}, []
+    for e in sample_envs:
+        s = int(env_scene[e])
+        if s not in orcs:
+            orcs[s] = O.Oracle(robot, scenes[s], I.icosahedron(), I.object_colors(64))
+        st = O.Oracle.make_state((0, 0, 0), np.zeros(7))
+        orcs[s].reset(st, w.reset_seed, e, w.n_objects, *w.obj_radius)
+        states.append((orcs[s], st))
+    acts = I.make_actions(200, len(sample_envs), w.action_dist, seed=w.action_seed + 1)
+    t0 = time.perf_counter()
+    done = 0
+    while time.perf_counter() - t0 < seconds and done < 200 * len(sample_envs):
+        k = done // len(sample_envs)
+        for i, (orc, st) in enumerate(states):
+            orc.step(st, acts[k % 200, i])
+            orc.render(st, w.img, w.img)
+            done += 1
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done} env-steps (physics + {w.img}x{w.img} render) over "
+                      f"{len(sample_envs)} envs of {w.name}, {dt:.1f} s, one thread, FP64"}
+
+
+def config_of(w):
+    return {"workload": w.name, "envs": w.n_envs, "scenes": w.n_scenes,
+            "triangles_per_scene": f"{w.tri_range[0]}-{w.tri_range[1]} {w.tri_dist}",
+            "grid_h_m": w.grid_h, "objects": w.n_objects, "image": f"{w.img}x{w.img}",
+            "depth": "f16" if w.depth_fp16 else "f32", "rgb8": w.rgb, "actions": w.action_dist,
+            "resets": (f"{w.reset_every}-step episodes, staggered" if w.reset_every
+                       else f"Bernoulli p={w.reset_prob} per env-step"),
+            "l2": "no flush: each step writes more observation bytes than L2 holds"}
+
+
+def run_reference(args, w, rank, world):
+    """Reference arm: the oracle as it stands, each step a bounded sample."""
+    if rank != 0:
+        return
+    import oracle as O
+    scenes = I.make_scenes(w)
+    robot = I.fetch_like_robot()
+    env_scene = I.env_scene_map(w.n_envs, w.n_scenes)
+    sample = [int(e) for e in np.linspace(0, w.n_envs - 1, args.ref_envs)]
+    orcs, sts = {}, []
+    for e in sample:
+        s = int(env_scene[e])
+        if s not in orcs:
+            orcs[s] = O.Oracle(robot, scenes[s], I.icosahedron(), I.object_colors(64))
+        st = O.Oracle.make_state((0, 0, 0), np.zeros(7))
+        orcs[s].reset(st, w.reset_seed, e, w.n_objects, *w.obj_radius)
+        sts.append((orcs[s], st))
+    acts = I.make_actions(args.warmup + args.steps, len(sample), w.action_dist,
+                          seed=w.action_seed)
+
+    def one(t):
+        for i, (orc, st) in enumerate(sts):
+            if w.reset_every and (t + sample[i]) % w.reset_every == 0:
+                orc.reset(st, w.reset_seed, sample[i], w.n_objects, *w.obj_radius)
+            orc.step(st, acts[t, i])
+            orc.render(st, w.img, w.img)
+
+    for t in range(args.warmup):
+        one(t)
+    t0 = time.perf_counter()
+    for t in range(args.warmup, args.warmup + args.steps):
+        one(t)
+    dt = time.perf_counter() - t0
+    value = len(sample) * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of(w),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{len(sample)} envs of {w.name} per step, each step "
+                                       f"physics + {w.img}x{w.img} render, FP64, one thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gx", choices=["gx", "reference"])
+    ap.add_argument("--workload", default="apartments4096", choices=list(I.WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-counters", action="store_true")
+    ap.add_argument("--ref-envs", type=int, default=4)
+    ap.add_argument("--envs", type=int, default=0, help="smaller batch (profiling runs)")
+    ap.add_argument("--scenes", type=int, default=0, help="fewer scenes (profiling runs)")
+    ap.add_argument("--small-px", type=int, default=0, help="expansion bbox limit (0: auto)")
+    ap.add_argument("--graph", action="store_true",
+                    help="replay the step as a CUDA graph (no per-kernel timing)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank, world, local = dist_env()
+    w = I.WORKLOADS[args.workload]
+    if args.envs or args.scenes:
+        w = dataclasses.replace(w, n_envs=args.envs or w.n_envs,
+                                n_scenes=args.scenes or w.n_scenes,
+                                name=f"{w.name}-{args.envs or w.n_envs}x{args.scenes or w.n_scenes}")
+    if args.impl == "reference":
+        run_reference(args, w, rank, world)
+        return
+
+    import torch
+    from paper_2306_07552_b300 import gx
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    n = w.n_envs
+    scenes = I.make_scenes(w)
+    ss = gx.SceneSet(scenes)
+    sim = gx.Sim(ss, I.fetch_like_robot(), n, img=(w.img, w.img), depth_fp16=w.depth_fp16,
+                 render_rgb=w.rgb, n_objects=w.n_objects, obj_radius=w.obj_radius,
+                 seed=w.reset_seed + 7919 * rank, profile=0 if args.graph else 1,
+                 use_graph=args.graph, small_tri_px=args.small_px)
+    total = args.warmup + args.steps
+    acts = torch.from_numpy(I.make_actions(total, n, w.action_dist,
+                                           seed=w.action_seed + rank)).cuda()
+    if w.reset_every:
+        masks = torch.from_numpy(reset_masks(n, w.reset_every)).cuda()
+        mask_at = lambda t: masks[t % w.reset_every]  # noqa: E731
+    else:
+        rng = np.random.default_rng(w.reset_seed + rank)
+        mk = torch.from_numpy((rng.random((total, n)) < w.reset_prob).astype(np.uint8)).cuda()
+        mask_at = lambda t: mk[t]  # noqa: E731
+    abuf = torch.empty((n, 11), dtype=torch.float32, device="cuda")
+    mbuf = torch.empty((n,), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.Stream()
+    launches = 0
+
+    def one(t):
+        # copy into fixed buffers so a graph replay sees the same pointers
+        abuf.copy_(acts[t])
+        mbuf.copy_(mask_at(t))
+        sim.reset(mbuf, stream=stream)
+        sim.step(abuf, stream=stream)
+
+    with torch.cuda.stream(stream):
+        sim.reset(stream=stream)
+        for t in range(args.warmup):
+            one(t)
+    torch.cuda.synchronize()
+    if not args.graph:
+        sim.phase_times()
+    if dist:
+        dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        with torch.cuda.stream(stream):
+            for t in range(args.warmup, total):
+                one(t)
+                launches += 3
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    phase_ms, phase_n = sim.phase_times() if not args.graph else ([0, 0, 0], [0, 0, 0])
+    dev_err = sim.device_error()
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n * args.steps / (ms / 1e3)
+
+    # end to end through the C ABI with host buffers (pinned): actions in,
+    # every output back (images included), copies inside the timed region
+    host = sim.host_outputs(pinned=True)
+    acts_h = torch.empty((n, 11), dtype=torch.float32, pin_memory=True)
+    ne = max(1, args.e2e_steps)
+    acts_np = I.make_actions(ne, n, w.action_dist, seed=w.action_seed + 99 + rank)
+    t0 = time.perf_counter()
+    for t in range(ne):
+        acts_h.numpy()[:] = acts_np[t]
+        sim.step_host(acts_h, host, stream=stream)
+    e2e_dt = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_dt], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_dt = float(t.item())
+    d2h = sum(v.numel() * v.element_size() for v in host.values() if v is not None)
+    e2e = {"value": world * n * ne / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": n * 11 * 4,
+           "d2h_bytes_per_step": int(d2h), "steps": ne,
+           "note": "gx_step_host: pinned actions in, every output (images included) back"}
+    counters = None
+    if rank == 0 and not args.no_counters:
+        counters = work_counters(ss, w, acts, mask_at, min(args.warmup, 5))
+    sim.close()
+    if rank != 0:
+        ss.close()
+        return
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, scenes, args.cpu_seconds)
+    clocks = clk.summary()
+    hbm_peak, sm_max_mhz, peak_src = measured_peaks()
+    roof = None
+    if phase_n[1]:
+        launch_ms = phase_ms[1] / phase_n[1]
+        sm_mhz = clocks.get("sm_max_mhz") or sm_max_mhz
+        peak = SMS * LANES * sm_mhz * 1e6 / 1e12
+        work = raster_work(w.name)
+        achieved = None
+        if work:
+            ops = n * (C_TRI * work["tris_per_view"] + C_FRAG * work["frags_per_view"])
+            achieved = ops / (launch_ms / 1e3) / 1e12
+        obs = n * w.img * w.img * ((2 if w.depth_fp16 else 4) + (3 if w.rgb else 0))
+        roof = {"bound": "alu", "kernel": "raster_kernel", "achieved": achieved, "peak": peak,
+                "unit": "Tops/s (FP32/INT32 lane ops)",
+                "frac": (achieved / peak) if achieved else None,
+                "traffic": kernel_traffic(w.name), "launch_ms": launch_ms,
+                "peak_basis": f"{SMS} SMs x {LANES} lanes x {sm_mhz:.0f} MHz ({peak_src} max "
+                              f"clock)",
+                "work_basis": f"{C_TRI} ops per front-facing triangle reaching the image + "
+                              f"{C_FRAG} per covered fragment; counts per view from the oracle",
+                "hbm_view": {"bytes_per_launch": obs,
+                             "achieved_gbs": obs / (launch_ms / 1e3) / 1e9,
+                             "peak_gbs": hbm_peak, "peak_source": peak_src,
+                             "frac": obs / (launch_ms / 1e3) / 1e9 / hbm_peak,
+                             "note": "observation writes only"}}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (procedural apartments standing in for ReplicaCAD; see DESIGN.md)",
+        "config": config_of(w),
+        "phases_ms_per_launch": {k: phase_ms[i] / max(phase_n[i], 1)
+                                 for i, k in enumerate(["physics", "raster", "reset"])},
+        "raster_counters_per_view": counters,
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": launches, "clocks": clocks, "device_error": dev_err,
+    }
+    print(json.dumps(line), flush=True)
+    ss.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -126,9 +126,15 @@ typedef struct {
   uint64_t seed;           /* Philox key for resets                           */
   const int32_t* env_scene; /* host [n_envs] scene per env; NULL: env i uses
                                scene floor(i * n_scenes / n_envs)             */
-  int32_t raster_regions;  /* horizontal bands per image (0 = library choice) */
-  int32_t small_tri_px;    /* bbox pixel count rasterised per lane (0 = default) */
+  int32_t raster_regions;  /* reserved, must be 0                             */
+  int32_t small_tri_px;    /* triangles whose clipped bounding box exceeds this
+                              many pixels are scanned block-wise by a warp
+                              instead of by fragment expansion (0: only those
+                              128 px or larger, and near-clipped ones)        */
   int32_t use_graph;       /* 1: replay the step as a captured CUDA graph     */
+  int32_t profile;         /* bit 0: time each kernel with CUDA events on the
+                              caller's stream (disables graph replay);
+                              bit 1: also count rasteriser work (slower)      */
 } gx_config;
 
 /* Outputs of one step, device memory owned by the caller (e.g. torch
@@ -198,6 +204,19 @@ gx_status gx_load_state(gx_ctx* ctx, const void* host, size_t bytes);
  * [n][n_objects][4] f32 (x, y, z, radius); step [n] i32; episode [n] i32.
  * Each array starts on a 256-byte boundary of the blob. */
 gx_status gx_state_layout(const gx_ctx* ctx, size_t offsets[10]);
+
+/* Per-kernel device time recorded since the previous call when the context
+ * was created with profile bit 0 set: ms[0] physics, ms[1] rasteriser, ms[2]
+ * reset; launches[k] the number of timed launches.  Waits for the device. */
+gx_status gx_phase_times(gx_ctx* ctx, double ms[3], int64_t launches[3]);
+
+/* Rasteriser work counters accumulated since the previous call (contexts
+ * created with profile bit 1), then cleared: clusters tested, clusters drawn,
+ * triangles seen, front-facing, rasterised by fragment expansion, pixels
+ * they expand to, rasterised per warp, 8x4 blocks the warps scanned,
+ * near-clipped, fragments written.  Fills out[0..n-1]; waits for the device.
+ * GX_ESTATE when the context does not count. */
+gx_status gx_raster_counters(gx_ctx* ctx, int64_t* out, int32_t n);
 
 const char* gx_last_error(const gx_ctx* ctx);
 

@@ -20,15 +20,16 @@ def _stale() -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not _stale():
+def build(force: bool = False, verbose: bool = False, out: str = SO, defines=()) -> str:
+    """Compiles libgx.so (or `out`, with extra -D `defines` for tuning runs)."""
+    if out == SO and not defines and not force and not _stale():
         return SO
     cmd = (["nvcc", *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-            "-o", SO] + [os.path.join(CSRC, s) for s in SOURCES])
+            *[f"-D{d}" for d in defines], "-o", out] + [os.path.join(CSRC, s) for s in SOURCES])
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     subprocess.check_call(cmd, cwd=HERE)
-    return SO
+    return out
 
 
 if __name__ == "__main__":

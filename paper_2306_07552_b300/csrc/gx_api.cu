@@ -35,7 +35,9 @@ struct gx_scene_set {
 struct gx_ctx {
   const gx_scene_set* set = nullptr;
   gx_config cfg{};
-  int n = 0, M = 0, regions = 1, region_h = 0, small_px = 0;
+  int n = 0, M = 0, big_px = 0, n_slots = 0;
+  unsigned long long* d_fb = nullptr;  // rasteriser framebuffer slots
+  int* d_raster_work = nullptr;
   float near_ = 0.05f;
   Robot* d_robot = nullptr;
   int* d_env_scene = nullptr;
@@ -54,6 +56,13 @@ struct gx_ctx {
   cudaGraphExec_t gexec = nullptr;
   const float* g_actions = nullptr;
   gx_outputs g_out{};
+  // profiling: event triples per timed launch group, read back lazily
+  std::vector<cudaEvent_t> prof_ev;
+  std::vector<int> prof_kind;   // 0 = step (physics, raster), 1 = reset
+  size_t prof_used = 0;
+  double prof_ms[3] = {0, 0, 0};
+  int64_t prof_n[3] = {0, 0, 0};
+  unsigned long long* d_counters = nullptr;
   // buffers for gx_step_host
   float* h2d_actions = nullptr;
   gx_outputs dev_out{};
@@ -131,7 +140,25 @@ bool same_outputs(const gx_outputs& a, const gx_outputs& b) {
   return std::memcmp(&a, &b, sizeof(gx_outputs)) == 0;
 }
 
+// Three events for the next timed launch group (nullptr once the pool is
+// full; gx_phase_times drains it).
+cudaEvent_t* prof_slot(gx_ctx* c, int kind) {
+  const size_t kMax = 3 * 8192;
+  if (c->prof_used + 3 > kMax) return nullptr;
+  while (c->prof_ev.size() < c->prof_used + 3) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    c->prof_ev.push_back(e);
+  }
+  c->prof_kind.push_back(kind);
+  cudaEvent_t* r = &c->prof_ev[c->prof_used];
+  c->prof_used += 3;
+  return r;
+}
+
 void enqueue_step(gx_ctx* c, const float* actions, const gx_outputs& out, cudaStream_t s) {
+  cudaEvent_t* ev = (c->cfg.profile & 1) ? prof_slot(c, 0) : nullptr;
+  if (ev) cudaEventRecord(ev[0], s);
   PhysicsParams pp{};
   pp.n = c->n;
   pp.M = c->M;
@@ -143,15 +170,18 @@ void enqueue_step(gx_ctx* c, const float* actions, const gx_outputs& out, cudaSt
   pp.cam = c->d_cam;
   pp.out = out;
   pp.err = c->d_err;
+  pp.raster_work = c->d_raster_work;
   launch_physics(pp, s);
+  if (ev) cudaEventRecord(ev[1], s);
   RasterParams rp{};
   rp.n = c->n;
   rp.M = c->M;
   rp.W = c->cfg.img_w;
   rp.H = c->cfg.img_h;
-  rp.regions = c->regions;
-  rp.region_h = c->region_h;
-  rp.small_px = c->small_px;
+  rp.big_px = c->big_px;
+  rp.fb_slots = c->d_fb;
+  rp.n_slots = c->n_slots;
+  rp.work = c->d_raster_work;
   rp.scenes = c->set->d_scenes;
   rp.env_scene = c->d_env_scene;
   rp.cam = c->d_cam;
@@ -166,7 +196,9 @@ void enqueue_step(gx_ctx* c, const float* actions, const gx_outputs& out, cudaSt
   rp.depth_fp16 = c->cfg.depth_fp16;
   rp.rgb = c->cfg.render_rgb ? out.rgb : nullptr;
   rp.err = c->d_err;
+  rp.counters = (c->cfg.profile & 2) ? c->d_counters : nullptr;
   launch_raster(rp, s);
+  if (ev) cudaEventRecord(ev[2], s);
 }
 
 }  // namespace
@@ -304,25 +336,14 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
     for (int i = 0; i < c.n_envs; ++i)
       if (c.env_scene[i] < 0 || c.env_scene[i] >= set->n)
         return fail(nullptr, GX_EINVAL, "env_scene[%d] out of range", i);
-  int regions = c.raster_regions;
-  if (regions <= 0) {
-    regions = 1;
-    while ((size_t)c.img_w * (c.img_h / regions) * 8 > 64 * 1024) regions *= 2;
-  }
-  if (c.img_h % regions || (c.img_h / regions) < 1)
-    return fail(nullptr, GX_EINVAL, "raster_regions must divide img_h");
-  if ((size_t)c.img_w * (c.img_h / regions) * 8 > 160 * 1024)
-    return fail(nullptr, GX_EINVAL, "image band too large for shared memory");
-
+  if (c.raster_regions != 0) return fail(nullptr, GX_EINVAL, "raster_regions is reserved (0)");
   gx_ctx* x = new gx_ctx();
   x->set = set;
   x->cfg = c;
   x->cfg.env_scene = nullptr;
   x->n = c.n_envs;
   x->M = c.n_objects;
-  x->regions = regions;
-  x->region_h = c.img_h / regions;
-  x->small_px = c.small_tri_px > 0 ? c.small_tri_px : 48;
+  x->big_px = c.small_tri_px > 0 ? c.small_tri_px : (1 << 30);
   x->near_ = robot->cam_near;
   auto bail = [&](cudaError_t e, const char* what) {
     gx_destroy(x);
@@ -330,7 +351,16 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
                 cudaGetErrorString(e));
   };
   cudaError_t e;
-  if ((e = raster_configure(c.img_w, x->region_h)) != cudaSuccess) return bail(e, "raster config");
+  if ((e = raster_configure(&x->n_slots)) != cudaSuccess) return bail(e, "raster config");
+  if (x->n_slots > x->n) x->n_slots = x->n;
+  {
+    // one framebuffer slot per resident rasteriser CTA, all keys "empty"
+    const size_t fb_bytes = (size_t)x->n_slots * c.img_w * c.img_h * 8;
+    if ((e = cudaMalloc(&x->d_fb, fb_bytes)) != cudaSuccess) return bail(e, "fb slots");
+    if ((e = cudaMemset(x->d_fb, 0xff, fb_bytes)) != cudaSuccess) return bail(e, "fb slots");
+    if ((e = cudaMalloc(&x->d_raster_work, sizeof(int))) != cudaSuccess) return bail(e, "work");
+    if ((e = cudaMemset(x->d_raster_work, 0, sizeof(int))) != cudaSuccess) return bail(e, "work");
+  }
   Robot hr;
   hr.r = *robot;
   if ((e = cudaMalloc(&x->d_robot, sizeof(Robot))) != cudaSuccess) return bail(e, "robot");
@@ -375,6 +405,12 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
   *x->h_err = 0;
   if ((e = cudaEventCreateWithFlags(&x->ev_err, cudaEventDisableTiming)) != cudaSuccess)
     return bail(e, "event");
+  if (c.profile & 2) {
+    if ((e = cudaMalloc(&x->d_counters, kRasterCounters * 8)) != cudaSuccess)
+      return bail(e, "counters");
+    if ((e = cudaMemset(x->d_counters, 0, kRasterCounters * 8)) != cudaSuccess)
+      return bail(e, "counters");
+  }
   *out = x;
   return GX_OK;
 }
@@ -387,8 +423,12 @@ extern "C" void gx_destroy(gx_ctx* x) {
   cudaFree(x->d_env_scene);
   cudaFree(x->d_state);
   cudaFree(x->d_cam);
+  cudaFree(x->d_fb);
+  cudaFree(x->d_raster_work);
   cudaFree(x->d_err);
   if (x->h_err) cudaFreeHost(x->h_err);
+  for (cudaEvent_t e : x->prof_ev) cudaEventDestroy(e);
+  cudaFree(x->d_counters);
   if (x->ev_err) cudaEventDestroy(x->ev_err);
   for (void* p : x->host_step_allocs) cudaFree(p);
   delete x;
@@ -412,7 +452,13 @@ extern "C" gx_status gx_reset(gx_ctx* x, const uint8_t* env_mask, void* stream) 
   rp.rho_min = x->cfg.obj_radius_min;
   rp.rho_max = x->cfg.obj_radius_max;
   rp.err = x->d_err;
+  cudaEvent_t* ev = (x->cfg.profile & 1) ? prof_slot(x, 1) : nullptr;
+  if (ev) cudaEventRecord(ev[0], s);
   launch_reset(rp, s);
+  if (ev) {
+    cudaEventRecord(ev[1], s);
+    cudaEventRecord(ev[2], s);
+  }
   CK(x, cudaGetLastError());
   return post_error_copy(x, s);
 }
@@ -425,7 +471,7 @@ extern "C" gx_status gx_step(gx_ctx* x, const float* actions, const gx_outputs* 
   gx_status st = poll_device_error(x, false);
   if (st != GX_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  if (x->cfg.use_graph && s != nullptr) {
+  if (x->cfg.use_graph && !x->cfg.profile && s != nullptr) {
     if (!x->gexec || x->g_actions != actions || !same_outputs(x->g_out, *out)) {
       if (x->gexec) {
         cudaGraphExecDestroy(x->gexec);
@@ -526,6 +572,46 @@ extern "C" gx_status gx_load_state(gx_ctx* x, const void* host, size_t bytes) {
 extern "C" gx_status gx_state_layout(const gx_ctx* x, size_t offsets[10]) {
   if (!x || !offsets) return fail(nullptr, GX_EINVAL, "gx_state_layout: NULL argument");
   for (int k = 0; k < 10; ++k) offsets[k] = x->off[k];
+  return GX_OK;
+}
+
+extern "C" gx_status gx_phase_times(gx_ctx* x, double ms[3], int64_t launches[3]) {
+  if (!x || !ms || !launches) return fail(x, GX_EINVAL, "gx_phase_times: NULL argument");
+  CK(x, cudaDeviceSynchronize());
+  for (size_t g = 0; g < x->prof_kind.size(); ++g) {
+    cudaEvent_t* e = &x->prof_ev[3 * g];
+    float a = 0.f, b = 0.f;
+    CK(x, cudaEventElapsedTime(&a, e[0], e[1]));
+    CK(x, cudaEventElapsedTime(&b, e[1], e[2]));
+    if (x->prof_kind[g] == 0) {
+      x->prof_ms[0] += a;
+      x->prof_ms[1] += b;
+      x->prof_n[0]++;
+      x->prof_n[1]++;
+    } else {
+      x->prof_ms[2] += a;
+      x->prof_n[2]++;
+    }
+  }
+  x->prof_kind.clear();
+  x->prof_used = 0;
+  for (int k = 0; k < 3; ++k) {
+    ms[k] = x->prof_ms[k];
+    launches[k] = x->prof_n[k];
+    x->prof_ms[k] = 0;
+    x->prof_n[k] = 0;
+  }
+  return GX_OK;
+}
+
+extern "C" gx_status gx_raster_counters(gx_ctx* x, int64_t* out, int32_t n) {
+  if (!x || !out || n < 1) return fail(x, GX_EINVAL, "gx_raster_counters: bad argument");
+  if (!x->d_counters) return fail(x, GX_ESTATE, "gx_raster_counters: context does not count");
+  CK(x, cudaDeviceSynchronize());
+  unsigned long long h[kRasterCounters];
+  CK(x, cudaMemcpy(h, x->d_counters, sizeof(h), cudaMemcpyDeviceToHost));
+  CK(x, cudaMemset(x->d_counters, 0, sizeof(h)));
+  for (int k = 0; k < n; ++k) out[k] = k < kRasterCounters ? (int64_t)h[k] : 0;
   return GX_OK;
 }
 

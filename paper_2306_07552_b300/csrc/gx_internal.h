@@ -80,6 +80,7 @@ struct PhysicsParams {
   float* cam;             // [n][12] camera R (row-major, columns right/up/fwd) + eye
   gx_outputs out;
   unsigned* err;
+  int* raster_work;       // zeroed here for the rasteriser that follows
 };
 
 struct ResetParams {
@@ -95,10 +96,16 @@ struct ResetParams {
   unsigned* err;
 };
 
+// Rasteriser launch shape: threads per CTA and CTAs wanted per SM.
+constexpr int kRasterThreads = 256;
+constexpr int kRasterMinBlocks = 3;
+
 struct RasterParams {
   int n, M, W, H;
-  int regions, region_h;
-  int small_px;
+  int big_px;                    // larger bounding boxes go to the warp scan
+  unsigned long long* fb_slots;  // [n_slots][H][W] keys, all ~0 between launches
+  int n_slots;                   // = grid size
+  int* work;                     // environment counter, zeroed before each launch
   const DScene* scenes;
   const int* env_scene;
   const float* cam;        // [n][12]
@@ -112,13 +119,32 @@ struct RasterParams {
   int depth_fp16;
   uint8_t* rgb;
   unsigned* err;
+  unsigned long long* counters;  // optional [kRasterCounters] work counters
+};
+
+// Rasteriser work counters (profiling only).
+enum RasterCounter {
+  kCntClustersTested = 0,
+  kCntClustersDrawn,
+  kCntTrisSeen,
+  kCntTrisFront,
+  kCntTrisSmall,
+  kCntSmallPixels,
+  kCntTrisBig,
+  kCntBigBlocks,
+  kCntTrisClipped,
+  kCntFragments,
+  kCntWaitIters,     // mbarrier polls (per warp)
+  kCntExpandTrips,   // fragment-expansion loop trips (per warp)
+  kCntRounds,        // 32-triangle rounds (per warp)
+  kRasterCounters
 };
 
 void launch_physics(const PhysicsParams& p, cudaStream_t s);
 void launch_reset(const ResetParams& p, cudaStream_t s);
 void launch_raster(const RasterParams& p, cudaStream_t s);
-size_t raster_smem_bytes(int W, int region_h);
-cudaError_t raster_configure(int W, int region_h);
+size_t raster_smem_bytes();
+cudaError_t raster_configure(int* slots);
 void launch_grid_build(float* grid, const float* boxes, int n_boxes, float ox, float oy, float oz,
                        float h, int nx, int ny, int nz, cudaStream_t s);
 

@@ -218,6 +218,7 @@ __global__ void __launch_bounds__(32 * kEnvsPerBlock) physics_kernel(const Physi
   __shared__ float4 s_obj[kEnvsPerBlock][GX_MAX_OBJECTS];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int env = blockIdx.x * kEnvsPerBlock + w;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && P.raster_work) *P.raster_work = 0;
   if (env >= P.n) return;
   const int n = P.n, M = P.M;
   const DScene& S = P.scenes[P.env_scene[env]];

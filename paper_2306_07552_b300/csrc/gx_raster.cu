@@ -2,27 +2,38 @@
 // every environment into one batched observation tensor that stays on the
 // GPU).  A CUDA software rasteriser replaces the paper's Vulkan renderer.
 //
-// Work item: one CTA per (environment, horizontal band of the image).  The
-// band's framebuffer lives in shared memory as 64-bit keys
+// Persistent launch: a fixed grid of CTAs (as many as fit on the GPU at
+// once) pulls environments from a work counter.  Each CTA owns one
+// framebuffer slot in global memory (L2-resident: slots x W x H x 8 bytes)
+// of 64-bit keys
 //     key = (~bits(1/z) << 32) | triangle id,
-// so one atomicMin keeps the nearest fragment and breaks exact depth ties
-// toward the lower triangle id, independently of visiting order.
+// updated with fire-and-forget atomicMin reductions, so the nearest fragment
+// wins and exact depth ties go to the lower triangle id, independently of
+// visiting order.  The resolve of an environment reads its slot, writes the
+// observation rows and resets the slot for the CTA's next environment.
 //
-// Pipeline inside a CTA:
-//   1. cull the scene's triangle clusters (meshlets) against the band's view
-//      frustum and the cluster normal cone (whole clusters facing away);
-//   2. warps pull surviving clusters from a shared queue; lane 0 stages each
-//      cluster's vertices and triangles into the warp's shared buffers with
-//      bulk asynchronous copies (cp.async.bulk + mbarrier), double-buffered so
-//      the next cluster streams in while the current one is rasterised;
-//   3. lanes transform and snap vertices to 1/256-pixel fixed point; each
-//      lane sets up one triangle: back-face test in world space, near-plane
-//      test, integer edge functions with the top-left fill rule, depth plane;
-//      small triangles are scanned by their lane (int32 edge functions),
-//      large or near-clipped ones by the whole warp (int64 edge functions);
-//   4. free objects are instanced icosahedra built in the same buffers;
-//   5. the band is resolved (depth = 1 / (1/z), colour by triangle id) and
-//      written to HBM with coalesced row-major stores.
+// Per environment, inside a CTA:
+//   1. each warp grabs 32 triangle clusters (meshlets) at a time, culls them
+//      lane-parallel against the view frustum and the cluster normal cone
+//      (whole clusters facing away), and keeps the survivors;
+//   2. lane 0 stages each surviving cluster's vertices and triangles into the
+//      warp's shared buffers with bulk asynchronous copies (cp.async.bulk +
+//      mbarrier), double-buffered so the next cluster streams in while the
+//      current one is rasterised; warps never wait for each other until the
+//      resolve;
+//   3. lanes transform vertices, snap them to 1/256-pixel fixed point and
+//      give each an outcode against the frustum planes;
+//   4. each lane takes one triangle: shared outcode bit -> rejected; world-
+//      space back-face test; integer edge functions with the top-left fill
+//      rule; depth plane.  Triangles whose bounding box is under 128 px are
+//      expanded pixel by pixel over the whole warp: a prefix sum over their
+//      bounding-box areas gives consecutive lanes consecutive pixel slots,
+//      and each slot's triangle is found from a mask of where triangles
+//      start.  Huge or near-plane-clipped triangles are scanned by the warp
+//      with int64 edge functions, 8x4 blocks first rejected against edges;
+//   5. free objects are instanced icosahedra built in the same buffers;
+//   6. resolve: depth = 1 / (1/z), colour by triangle id, 16-byte row-major
+//      stores into the batched observation buffers.
 //
 // Every wait is bounded: a wait that gives up sets an error bit and the warp
 // stops using its buffers.
@@ -36,22 +47,48 @@ namespace gx {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kThreads = 256;
+constexpr int kThreads = kRasterThreads;
 constexpr int kWarps = kThreads / 32;
-constexpr int kChunk = 512;       // clusters culled per pass
-constexpr long kWaitLimit = 1L << 22;
+constexpr long kWaitLimit = 1L << 22;  // bounded waits
 
-struct WarpSmem {
+// Setup of one triangle queued for pixel expansion.
+struct __align__(16) ExpTri {
+  int e[3];       // edge values at the bounding box's first pixel centre (bias included)
+  int ixy;        // ix0 | iy0 << 16
+  int sx[3];      // edge increments per pixel step in x
+  int bw;         // bounding-box width in pixels
+  int sy[3];      // edge increments per pixel step in y
+  uint32_t id;
+  float A, B, C;  // 1/z plane
+  int pad;
+};
+
+struct __align__(16) WarpSmem {
   float4 vbuf[2][kMeshletMaxVerts];     // staged world-space vertices
+  ExpTri q[32];                         // expansion queue of one round
   uint32_t tbuf[2][kMeshletMaxTris];    // staged packed triangles
-  float4 vc[kMeshletMaxVerts];          // camera-space xyz (w unused)
   int2 vfix[kMeshletMaxVerts];          // snapped screen coordinates (1/256 px)
+  float vz[kMeshletMaxVerts];           // camera-space depth
+  uint8_t voc[kMeshletMaxVerts];        // frustum outcode
+  uint8_t start[32];                    // lane whose triangle starts at slot base + i
   unsigned long long bar[2];            // mbarriers of the two buffers
+};
+
+// Per-lane work counters, summed into RasterParams::counters when counting.
+struct Cnt {
+  unsigned long long v[kRasterCounters];
 };
 
 struct Cam {
   float rx, ry, rz, ux, uy, uz, fx, fy, fz, ex, ey, ez;
   float f, cx, cy, near_;
+};
+
+struct View {
+  int W, H;
+  unsigned long long* fb;  // this CTA's slot, [H][W]
+  // side planes of the frustum as slopes x/z, y/z, with 1/|n|
+  float tl, tr, tt, tb, kl, kr, kt, kb;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -82,8 +119,10 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, uint32_t
 }
 
 // Bounded wait on an mbarrier phase; false when the limit was reached.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t phase) {
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t phase,
+                                          unsigned long long* polls = nullptr) {
   for (long it = 0; it < kWaitLimit; ++it) {
+    if (polls) ++*polls;
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -99,34 +138,29 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t phas
 __device__ __forceinline__ int floor_div256(int a) { return a >> 8; }
 __device__ __forceinline__ int ceil_div256(int a) { return -((-a) >> 8); }
 
-__device__ __forceinline__ void frag(unsigned long long* fb, int W, int row0, int i, int j, float A,
-                                     float B, float C, const Cam& cm, uint32_t id) {
+template <bool kCount>
+__device__ __forceinline__ void frag(const View& vw, int i, int j, float A, float B, float C,
+                                     const Cam& cm, uint32_t id, Cnt& cn) {
+  if (kCount) cn.v[kCntFragments]++;
   float invz = fmaf(A, (float)i + 0.5f - cm.cx, fmaf(B, (float)j + 0.5f - cm.cy, C));
   invz = fmaxf(invz, 1e-30f);
   const unsigned long long key =
       ((unsigned long long)(~__float_as_uint(invz)) << 32) | (unsigned long long)id;
-  unsigned long long* slot = fb + (j - row0) * W + i;
-  if (key < *slot) atomicMin(slot, key);
+  atomicMin(vw.fb + j * vw.W + i, key);  // result unused: a reduction
 }
 
-struct Band {
-  int W, row0, row1;  // rows [row0, row1)
-  // view-frustum side planes of the band, as slopes x/z and y/z with norms
-  float tl, tr, tt, tb, kl, kr, kt, kb;
-};
-
-// Bounding sphere (world centre c, radius r) vs the band's frustum.
-__device__ __forceinline__ bool sphere_visible(const Cam& cm, const Band& bd, float cx, float cy,
+// Bounding sphere (world centre c, radius r) vs the view frustum.
+__device__ __forceinline__ bool sphere_visible(const Cam& cm, const View& vw, float cx, float cy,
                                                float cz, float r) {
   const float dx = cx - cm.ex, dy = cy - cm.ey, dz = cz - cm.ez;
   const float xc = cm.rx * dx + cm.ry * dy + cm.rz * dz;
   const float yc = cm.ux * dx + cm.uy * dy + cm.uz * dz;
   const float zc = cm.fx * dx + cm.fy * dy + cm.fz * dz;
   if (zc + r < cm.near_) return false;
-  if ((xc - bd.tl * zc) * bd.kl < -r) return false;
-  if ((bd.tr * zc - xc) * bd.kr < -r) return false;
-  if ((bd.tt * zc - yc) * bd.kt < -r) return false;
-  if ((yc - bd.tb * zc) * bd.kb < -r) return false;
+  if ((xc - vw.tl * zc) * vw.kl < -r) return false;
+  if ((vw.tr * zc - xc) * vw.kr < -r) return false;
+  if ((vw.tt * zc - yc) * vw.kt < -r) return false;
+  if ((yc - vw.tb * zc) * vw.kb < -r) return false;
   return true;
 }
 
@@ -144,74 +178,6 @@ __device__ __forceinline__ void depth_plane(const Cam& cm, float nx, float ny, f
   C = ncz * ih;
 }
 
-// One lane scans the pixel rectangle of a small triangle (int32 edges).
-__device__ void raster_small(unsigned long long* fb, const Band& bd, const Cam& cm, int2 V0,
-                             int2 V1, int2 V2, int ix0, int ix1, int iy0, int iy1, float A,
-                             float B, float C, uint32_t id) {
-  const int dx0 = V1.x - V0.x, dy0 = V1.y - V0.y;
-  const int dx1 = V2.x - V1.x, dy1 = V2.y - V1.y;
-  const int dx2 = V0.x - V2.x, dy2 = V0.y - V2.y;
-  const int b0 = (dy0 < 0 || (dy0 == 0 && dx0 > 0)) ? 0 : -1;
-  const int b1 = (dy1 < 0 || (dy1 == 0 && dx1 > 0)) ? 0 : -1;
-  const int b2 = (dy2 < 0 || (dy2 == 0 && dx2 > 0)) ? 0 : -1;
-  const int px = ix0 * 256 + 128, py = iy0 * 256 + 128;
-  int r0 = dx0 * (py - V0.y) - dy0 * (px - V0.x) + b0;
-  int r1 = dx1 * (py - V1.y) - dy1 * (px - V1.x) + b1;
-  int r2 = dx2 * (py - V2.y) - dy2 * (px - V2.x) + b2;
-  const int sx0 = -dy0 * 256, sx1 = -dy1 * 256, sx2 = -dy2 * 256;
-  const int sy0 = dx0 * 256, sy1 = dx1 * 256, sy2 = dx2 * 256;
-  for (int j = iy0; j <= iy1; ++j) {
-    int e0 = r0, e1 = r1, e2 = r2;
-    for (int i = ix0; i <= ix1; ++i) {
-      if ((e0 | e1 | e2) >= 0) frag(fb, bd.W, bd.row0, i, j, A, B, C, cm, id);
-      e0 += sx0;
-      e1 += sx1;
-      e2 += sx2;
-    }
-    r0 += sy0;
-    r1 += sy1;
-    r2 += sy2;
-  }
-}
-
-// The whole warp scans one triangle (int64 edges): 8x4 pixel blocks.
-__device__ void raster_warp_tri(unsigned long long* fb, const Band& bd, const Cam& cm, int2 V0,
-                                int2 V1, int2 V2, float A, float B, float C, uint32_t id,
-                                int lane) {
-  long long area = (long long)(V1.x - V0.x) * (V2.y - V0.y) - (long long)(V2.x - V0.x) * (V1.y - V0.y);
-  if (area == 0) return;
-  if (area < 0) {
-    const int2 t = V1;
-    V1 = V2;
-    V2 = t;
-  }
-  const int xmin = min(V0.x, min(V1.x, V2.x)), xmax = max(V0.x, max(V1.x, V2.x));
-  const int ymin = min(V0.y, min(V1.y, V2.y)), ymax = max(V0.y, max(V1.y, V2.y));
-  const int ix0 = max(ceil_div256(xmin - 128), 0), ix1 = min(floor_div256(xmax - 128), bd.W - 1);
-  const int iy0 = max(ceil_div256(ymin - 128), bd.row0);
-  const int iy1 = min(floor_div256(ymax - 128), bd.row1 - 1);
-  if (ix0 > ix1 || iy0 > iy1) return;
-  const int dx0 = V1.x - V0.x, dy0 = V1.y - V0.y;
-  const int dx1 = V2.x - V1.x, dy1 = V2.y - V1.y;
-  const int dx2 = V0.x - V2.x, dy2 = V0.y - V2.y;
-  const long long b0 = (dy0 < 0 || (dy0 == 0 && dx0 > 0)) ? 0 : -1;
-  const long long b1 = (dy1 < 0 || (dy1 == 0 && dx1 > 0)) ? 0 : -1;
-  const long long b2 = (dy2 < 0 || (dy2 == 0 && dx2 > 0)) ? 0 : -1;
-  const int lx = lane & 7, ly = lane >> 3;
-  for (int by = iy0; by <= iy1; by += 4) {
-    const int j = by + ly;
-    for (int bx = ix0; bx <= ix1; bx += 8) {
-      const int i = bx + lx;
-      if (i > ix1 || j > iy1) continue;
-      const long long px = (long long)i * 256 + 128, py = (long long)j * 256 + 128;
-      const long long e0 = (long long)dx0 * (py - V0.y) - (long long)dy0 * (px - V0.x) + b0;
-      const long long e1 = (long long)dx1 * (py - V1.y) - (long long)dy1 * (px - V1.x) + b1;
-      const long long e2 = (long long)dx2 * (py - V2.y) - (long long)dy2 * (px - V2.x) + b2;
-      if ((e0 | e1 | e2) >= 0) frag(fb, bd.W, bd.row0, i, j, A, B, C, cm, id);
-    }
-  }
-}
-
 __device__ __forceinline__ int2 project_fix(const Cam& cm, float xc, float yc, float zc) {
   const float iz = __frcp_rn(zc);
   const float px = fminf(fmaxf(xc * iz, -1000.f), 1000.f);
@@ -220,26 +186,106 @@ __device__ __forceinline__ int2 project_fix(const Cam& cm, float xc, float yc, f
                    __float2int_rn(fmaf(-cm.f, py, cm.cy) * 256.f));
 }
 
-// Warp-cooperative raster of triangle t of the staged cluster: the whole warp
-// recomputes its setup from shared memory, clips it against the near plane
-// when needed and scans the (one or two) resulting triangles.
-__device__ void raster_big(unsigned long long* fb, const Band& bd, const Cam& cm,
-                           const WarpSmem& ws, int buf, uint32_t packed, uint32_t id, int lane) {
-  const int i0 = packed & 0xff, i1 = (packed >> 8) & 0xff, i2 = (packed >> 16) & 0xff;
-  const float4 P0 = ws.vbuf[buf][i0], P1 = ws.vbuf[buf][i1], P2 = ws.vbuf[buf][i2];
+__device__ __forceinline__ bool top_left(int dx, int dy) { return dy < 0 || (dy == 0 && dx > 0); }
+
+// The whole warp scans one triangle with int64 edge functions.  Lanes first
+// test 32 8x4 blocks at a time against the three edges (each edge at the
+// block corner where it is largest); only blocks no edge excludes are
+// scanned, one pixel per lane.
+template <bool kCount>
+__device__ void raster_warp_tri(const View& vw, const Cam& cm, int2 V0, int2 V1, int2 V2, float A,
+                                float B, float C, uint32_t id, int lane, Cnt& cn) {
+  const long long area =
+      (long long)(V1.x - V0.x) * (V2.y - V0.y) - (long long)(V2.x - V0.x) * (V1.y - V0.y);
+  if (area == 0) return;
+  if (area < 0) {
+    const int2 t = V1;
+    V1 = V2;
+    V2 = t;
+  }
+  const int xmin = min(V0.x, min(V1.x, V2.x)), xmax = max(V0.x, max(V1.x, V2.x));
+  const int ymin = min(V0.y, min(V1.y, V2.y)), ymax = max(V0.y, max(V1.y, V2.y));
+  const int ix0 = max(ceil_div256(xmin - 128), 0), ix1 = min(floor_div256(xmax - 128), vw.W - 1);
+  const int iy0 = max(ceil_div256(ymin - 128), 0), iy1 = min(floor_div256(ymax - 128), vw.H - 1);
+  if (ix0 > ix1 || iy0 > iy1) return;
+  const int2 V[3] = {V0, V1, V2};
+  int dx[3], dy[3];
+  long long b[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    dx[k] = V[(k + 1) % 3].x - V[k].x;
+    dy[k] = V[(k + 1) % 3].y - V[k].y;
+    b[k] = top_left(dx[k], dy[k]) ? 0 : -1;
+  }
+  const int nbx = (ix1 - ix0) / 8 + 1, nby = (iy1 - iy0) / 4 + 1;
+  const int nblk = nbx * nby;
+  const int lx = lane & 7, ly = lane >> 3;
+  for (int base = 0; base < nblk; base += 32) {
+    const int blk = base + lane;
+    bool keep = false;
+    if (blk < nblk) {
+      const int bx = ix0 + (blk % nbx) * 8, by = iy0 + (blk / nbx) * 4;
+      const int bx1 = min(bx + 7, ix1), by1 = min(by + 3, iy1);
+      keep = true;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const long long px = (long long)(dy[k] < 0 ? bx1 : bx) * 256 + 128;
+        const long long py = (long long)(dx[k] > 0 ? by1 : by) * 256 + 128;
+        const long long e = (long long)dx[k] * (py - V[k].y) - (long long)dy[k] * (px - V[k].x) + b[k];
+        keep &= e >= 0;
+      }
+    }
+    unsigned m = __ballot_sync(kFull, keep);
+    while (m) {
+      const int L = __ffs(m) - 1;
+      m &= m - 1;
+      const int blk2 = base + L;
+      if (kCount && lane == 0) cn.v[kCntBigBlocks]++;
+      const int i = ix0 + (blk2 % nbx) * 8 + lx, j = iy0 + (blk2 / nbx) * 4 + ly;
+      if (i > ix1 || j > iy1) continue;
+      const long long px = (long long)i * 256 + 128, py = (long long)j * 256 + 128;
+      bool in = true;
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        in &= (long long)dx[k] * (py - V[k].y) - (long long)dy[k] * (px - V[k].x) + b[k] >= 0;
+      if (in) frag<kCount>(vw, i, j, A, B, C, cm, id, cn);
+    }
+  }
+}
+
+// Warp-cooperative raster of a triangle of the staged cluster: every lane
+// recomputes its setup, clips it against the near plane when needed and the
+// warp scans the (one or two) resulting triangles.
+template <bool kCount>
+__device__ void raster_big(const View& vw, const Cam& cm, const WarpSmem& ws, int buf,
+                           uint32_t packed, uint32_t id, int lane, Cnt& cn) {
+  if (kCount && lane == 0) cn.v[kCntTrisBig]++;
+  const int idx[3] = {(int)(packed & 0xff), (int)((packed >> 8) & 0xff), (int)((packed >> 16) & 0xff)};
+  const float4 P0 = ws.vbuf[buf][idx[0]], P1 = ws.vbuf[buf][idx[1]], P2 = ws.vbuf[buf][idx[2]];
   const float e1x = P1.x - P0.x, e1y = P1.y - P0.y, e1z = P1.z - P0.z;
   const float e2x = P2.x - P0.x, e2y = P2.y - P0.y, e2z = P2.z - P0.z;
   const float nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
   const float h = nx * (P0.x - cm.ex) + ny * (P0.y - cm.ey) + nz * (P0.z - cm.ez);
   float A, B, C;
   depth_plane(cm, nx, ny, nz, h, A, B, C);
-  const float4 v[3] = {ws.vc[i0], ws.vc[i1], ws.vc[i2]};
-  const int2 f[3] = {ws.vfix[i0], ws.vfix[i1], ws.vfix[i2]};
+  float3 v[3];
+  int2 f[3];
+  bool clipped = false;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float4 P = ws.vbuf[buf][idx[k]];
+    const float dx = P.x - cm.ex, dy = P.y - cm.ey, dz = P.z - cm.ez;
+    v[k] = make_float3(cm.rx * dx + cm.ry * dy + cm.rz * dz, cm.ux * dx + cm.uy * dy + cm.uz * dz,
+                       ws.vz[idx[k]]);
+    f[k] = ws.vfix[idx[k]];
+    clipped |= v[k].z < cm.near_;
+  }
+  if (kCount && clipped && lane == 0) cn.v[kCntTrisClipped]++;
   int2 poly[4];
   int m = 0;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const float4 a = v[k], b = v[(k + 1) % 3];
+    const float3 a = v[k], b = v[(k + 1) % 3];
     const bool ain = a.z >= cm.near_, bin = b.z >= cm.near_;
     if (ain) poly[m++] = f[k];
     if (ain != bin) {
@@ -247,143 +293,187 @@ __device__ void raster_big(unsigned long long* fb, const Band& bd, const Cam& cm
       poly[m++] = project_fix(cm, fmaf(t, b.x - a.x, a.x), fmaf(t, b.y - a.y, a.y), cm.near_);
     }
   }
-  if (m >= 3) raster_warp_tri(fb, bd, cm, poly[0], poly[1], poly[2], A, B, C, id, lane);
-  if (m == 4) raster_warp_tri(fb, bd, cm, poly[0], poly[2], poly[3], A, B, C, id, lane);
+  if (m >= 3) raster_warp_tri<kCount>(vw, cm, poly[0], poly[1], poly[2], A, B, C, id, lane, cn);
+  if (m == 4) raster_warp_tri<kCount>(vw, cm, poly[0], poly[2], poly[3], A, B, C, id, lane, cn);
 }
 
 // Rasterises the cluster staged in buffer `buf` (nv vertices, nt triangles,
 // triangle ids id0 + t).
-__device__ void raster_cluster(unsigned long long* fb, const Band& bd, const Cam& cm, WarpSmem& ws,
-                               int buf, int nv, int nt, uint32_t id0, int small_px, int lane) {
+template <bool kCount>
+__device__ void raster_cluster(const View& vw, const Cam& cm, WarpSmem& ws, int buf, int nv, int nt,
+                               uint32_t id0, int big_px, int lane, Cnt& cn) {
+  if (kCount && lane == 0) cn.v[kCntClustersDrawn]++;
   for (int k = lane; k < nv; k += 32) {
     const float4 P = ws.vbuf[buf][k];
     const float dx = P.x - cm.ex, dy = P.y - cm.ey, dz = P.z - cm.ez;
     const float xc = cm.rx * dx + cm.ry * dy + cm.rz * dz;
     const float yc = cm.ux * dx + cm.uy * dy + cm.uz * dz;
     const float zc = cm.fx * dx + cm.fy * dy + cm.fz * dz;
-    ws.vc[k] = make_float4(xc, yc, zc, 0.f);
+    uint32_t oc = 0;
+    oc |= (xc - vw.tl * zc < 0.f) ? 1u : 0u;
+    oc |= (vw.tr * zc - xc < 0.f) ? 2u : 0u;
+    oc |= (vw.tt * zc - yc < 0.f) ? 4u : 0u;
+    oc |= (yc - vw.tb * zc < 0.f) ? 8u : 0u;
+    oc |= (zc < cm.near_) ? 16u : 0u;
+    ws.vz[k] = zc;
+    ws.voc[k] = (uint8_t)oc;
     ws.vfix[k] = zc >= cm.near_ ? project_fix(cm, xc, yc, zc) : make_int2(0, 0);
   }
   __syncwarp();
   for (int tb = 0; tb < nt; tb += 32) {
     const int t = tb + lane;
     bool big = false;
+    int npx = 0;
     uint32_t packed = 0;
     if (t < nt) {
+      if (kCount) cn.v[kCntTrisSeen]++;
       packed = ws.tbuf[buf][t];
       const int i0 = packed & 0xff, i1 = (packed >> 8) & 0xff, i2 = (packed >> 16) & 0xff;
-      const float4 P0 = ws.vbuf[buf][i0], P1 = ws.vbuf[buf][i1], P2 = ws.vbuf[buf][i2];
-      const float e1x = P1.x - P0.x, e1y = P1.y - P0.y, e1z = P1.z - P0.z;
-      const float e2x = P2.x - P0.x, e2y = P2.y - P0.y, e2z = P2.z - P0.z;
-      const float nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z,
-                  nz = e1x * e2y - e1y * e2x;
-      const float h = nx * (P0.x - cm.ex) + ny * (P0.y - cm.ey) + nz * (P0.z - cm.ez);
-      if (h < 0.f) {  // front-facing
-        const float z0 = ws.vc[i0].z, z1 = ws.vc[i1].z, z2 = ws.vc[i2].z;
-        const bool c0 = z0 >= cm.near_, c1 = z1 >= cm.near_, c2 = z2 >= cm.near_;
-        if (c0 && c1 && c2) {
-          int2 V0 = ws.vfix[i0], V1 = ws.vfix[i1], V2 = ws.vfix[i2];
-          const long long area = (long long)(V1.x - V0.x) * (V2.y - V0.y) -
-                                 (long long)(V2.x - V0.x) * (V1.y - V0.y);
-          if (area != 0) {
-            if (area < 0) {
-              const int2 tmp = V1;
-              V1 = V2;
-              V2 = tmp;
-            }
-            const int xmin = min(V0.x, min(V1.x, V2.x)), xmax = max(V0.x, max(V1.x, V2.x));
-            const int ymin = min(V0.y, min(V1.y, V2.y)), ymax = max(V0.y, max(V1.y, V2.y));
-            const int ix0 = max(ceil_div256(xmin - 128), 0);
-            const int ix1 = min(floor_div256(xmax - 128), bd.W - 1);
-            const int iy0 = max(ceil_div256(ymin - 128), bd.row0);
-            const int iy1 = min(floor_div256(ymax - 128), bd.row1 - 1);
-            if (ix0 <= ix1 && iy0 <= iy1) {
-              const int npx = (ix1 - ix0 + 1) * (iy1 - iy0 + 1);
-              const bool fits32 = (xmax - xmin) < 32768 && (ymax - ymin) < 32768;
-              if (fits32 && npx <= small_px) {
-                float A, B, C;
-                depth_plane(cm, nx, ny, nz, h, A, B, C);
-                raster_small(fb, bd, cm, V0, V1, V2, ix0, ix1, iy0, iy1, A, B, C, id0 + t);
-              } else {
-                big = true;
+      const uint32_t oc0 = ws.voc[i0], oc1 = ws.voc[i1], oc2 = ws.voc[i2];
+      if ((oc0 & oc1 & oc2) == 0) {
+        const float4 P0 = ws.vbuf[buf][i0], P1 = ws.vbuf[buf][i1], P2 = ws.vbuf[buf][i2];
+        const float e1x = P1.x - P0.x, e1y = P1.y - P0.y, e1z = P1.z - P0.z;
+        const float e2x = P2.x - P0.x, e2y = P2.y - P0.y, e2z = P2.z - P0.z;
+        const float nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z,
+                    nz = e1x * e2y - e1y * e2x;
+        const float h = nx * (P0.x - cm.ex) + ny * (P0.y - cm.ey) + nz * (P0.z - cm.ez);
+        if (h < 0.f) {  // front-facing
+          if (kCount) cn.v[kCntTrisFront]++;
+          if (((oc0 | oc1 | oc2) & 16u) != 0) {
+            big = true;  // crosses the near plane
+          } else {
+            int2 V0 = ws.vfix[i0], V1 = ws.vfix[i1], V2 = ws.vfix[i2];
+            const long long area = (long long)(V1.x - V0.x) * (V2.y - V0.y) -
+                                   (long long)(V2.x - V0.x) * (V1.y - V0.y);
+            if (area != 0) {
+              if (area < 0) {
+                const int2 tmp = V1;
+                V1 = V2;
+                V2 = tmp;
+              }
+              const int xmin = min(V0.x, min(V1.x, V2.x)), xmax = max(V0.x, max(V1.x, V2.x));
+              const int ymin = min(V0.y, min(V1.y, V2.y)), ymax = max(V0.y, max(V1.y, V2.y));
+              const int ix0 = max(ceil_div256(xmin - 128), 0);
+              const int ix1 = min(floor_div256(xmax - 128), vw.W - 1);
+              const int iy0 = max(ceil_div256(ymin - 128), 0);
+              const int iy1 = min(floor_div256(ymax - 128), vw.H - 1);
+              if (ix0 <= ix1 && iy0 <= iy1) {
+                const int bw = ix1 - ix0 + 1, bh = iy1 - iy0 + 1;
+                const bool fits32 = (xmax - xmin) < 32768 && (ymax - ymin) < 32768;
+                if (fits32 && bw * bh <= big_px) {
+                  // queued for pixel expansion; int32 edge values are exact
+                  // because every visited pixel lies inside the bounding box
+                  ExpTri& r = ws.q[lane];
+                  const int2 V[3] = {V0, V1, V2};
+                  const int px = ix0 * 256 + 128, py = iy0 * 256 + 128;
+#pragma unroll
+                  for (int k = 0; k < 3; ++k) {
+                    const int dxk = V[(k + 1) % 3].x - V[k].x, dyk = V[(k + 1) % 3].y - V[k].y;
+                    r.e[k] = dxk * (py - V[k].y) - dyk * (px - V[k].x) + (top_left(dxk, dyk) ? 0 : -1);
+                    r.sx[k] = -dyk * 256;
+                    r.sy[k] = dxk * 256;
+                  }
+                  float A, B, C;
+                  depth_plane(cm, nx, ny, nz, h, A, B, C);
+                  r.ixy = ix0 | (iy0 << 16);
+                  r.bw = bw;
+                  r.A = A;
+                  r.B = B;
+                  r.C = C;
+                  r.id = id0 + t;
+                  npx = bw * bh;
+                  if (kCount) {
+                    cn.v[kCntTrisSmall]++;
+                    cn.v[kCntSmallPixels] += npx;
+                  }
+                } else {
+                  big = true;
+                }
               }
             }
           }
-        } else if (c0 || c1 || c2) {
-          big = true;  // crosses the near plane
         }
       }
+    }
+    // pixel expansion: lane k's triangle owns slots [off_k, off_k + npx_k);
+    // in each pass lane l takes slot base + l, so neighbouring lanes mostly
+    // take neighbouring pixels of one row
+    int incl = npx;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const int off = incl - npx;
+    const int total = __shfl_sync(kFull, incl, 31);
+    if (kCount && lane == 0) {
+      cn.v[kCntRounds]++;
+      cn.v[kCntExpandTrips] += (total + 31) / 32;
+    }
+    __syncwarp();
+    for (int base = 0; base < total; base += 32) {
+      // triangles starting inside this pass, and the one running into it
+      const int d = off - base;
+      const bool starts = npx > 0 && d >= 0 && d < 32;
+      const unsigned smask = __reduce_or_sync(kFull, starts ? (1u << d) : 0u);
+      const unsigned before = __ballot_sync(kFull, npx > 0 && d < 0);
+      if (starts) ws.start[d] = (uint8_t)lane;
+      __syncwarp();
+      const unsigned upto = smask & (0xffffffffu >> (31 - lane));
+      const int k = upto ? (int)ws.start[31 - __clz(upto)] : (before ? 31 - __clz(before) : 0);
+      const int offk = __shfl_sync(kFull, off, k);
+      const int s = base + lane;
+      if (s < total) {
+        const ExpTri& r = ws.q[k];
+        const int rr = s - offk;
+        const int bw = r.bw;
+        const int y = __float2int_rz(((float)rr + 0.5f) * __frcp_rn((float)bw));
+        const int x = rr - y * bw;
+        const int e0 = r.e[0] + x * r.sx[0] + y * r.sy[0];
+        const int e1 = r.e[1] + x * r.sx[1] + y * r.sy[1];
+        const int e2 = r.e[2] + x * r.sx[2] + y * r.sy[2];
+        if ((e0 | e1 | e2) >= 0)
+          frag<kCount>(vw, (r.ixy & 0xffff) + x, (r.ixy >> 16) + y, r.A, r.B, r.C, cm, r.id, cn);
+      }
+      __syncwarp();
     }
     unsigned bm = __ballot_sync(kFull, big);
     while (bm) {
       const int L = __ffs(bm) - 1;
       bm &= bm - 1;
       const uint32_t pk = __shfl_sync(kFull, packed, L);
-      raster_big(fb, bd, cm, ws, buf, pk, id0 + tb + L, lane);
+      raster_big<kCount>(vw, cm, ws, buf, pk, id0 + tb + L, lane, cn);
     }
   }
   __syncwarp();
 }
 
-__global__ void __launch_bounds__(kThreads, 2) raster_kernel(const RasterParams P) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  const int W = P.W, rh = P.region_h;
-  unsigned long long* fb = reinterpret_cast<unsigned long long*>(smem);
-  uint4* list = reinterpret_cast<uint4*>(smem + (size_t)W * rh * 8);
-  int* counters = reinterpret_cast<int*>(list + kChunk);  // [0] count, [1] next
-  WarpSmem* wsm = reinterpret_cast<WarpSmem*>(smem + (size_t)W * rh * 8 + kChunk * 16 + 128);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int env = blockIdx.x / P.regions, band = blockIdx.x % P.regions;
-  WarpSmem& ws = wsm[warp];
-  const DScene& S = P.scenes[P.env_scene[env]];
+// Per-warp software pipeline over the scene's clusters.  A warp grabs 32
+// cluster headers at a time from the CTA's shared counter, culls them lane-
+// parallel and keeps the survivors as a ballot mask; `pop` hands out the next
+// survivor, culling a new batch when the mask runs dry.
+struct ClusterQueue {
+  unsigned mask;   // survivors of the batch in hand not yet handed out
+  uint4 mine;      // this lane's cluster entry (vertex offset, triangle offset, counts)
+};
 
-  Cam cm;
-  {
-    const float* c = P.cam + (size_t)env * 12;
-    cm.rx = c[0]; cm.ux = c[1]; cm.fx = c[2];
-    cm.ry = c[3]; cm.uy = c[4]; cm.fy = c[5];
-    cm.rz = c[6]; cm.uz = c[7]; cm.fz = c[8];
-    cm.ex = c[9]; cm.ey = c[10]; cm.ez = c[11];
-    cm.f = 0.5f * (float)W;
-    cm.cx = 0.5f * (float)W;
-    cm.cy = 0.5f * (float)P.H;
-    cm.near_ = P.near_;
-  }
-  Band bd;
-  bd.W = W;
-  bd.row0 = band * rh;
-  bd.row1 = bd.row0 + rh;
-  bd.tl = (-1.f - cm.cx) / cm.f;
-  bd.tr = ((float)W + 1.f - cm.cx) / cm.f;
-  bd.tt = (cm.cy - ((float)bd.row0 - 1.f)) / cm.f;
-  bd.tb = (cm.cy - ((float)bd.row1 + 1.f)) / cm.f;
-  bd.kl = rsqrtf(1.f + bd.tl * bd.tl);
-  bd.kr = rsqrtf(1.f + bd.tr * bd.tr);
-  bd.kt = rsqrtf(1.f + bd.tt * bd.tt);
-  bd.kb = rsqrtf(1.f + bd.tb * bd.tb);
-
-  for (int p = tid; p < W * rh; p += kThreads) fb[p] = ~0ull;
-  if (lane == 0) {
-    mbar_init(&ws.bar[0]);
-    mbar_init(&ws.bar[1]);
-    fence_mbar_init();
-  }
-  uint32_t phase[2] = {0u, 0u};
-  bool dead = false;  // a wait gave up: this warp stops using its buffers
-  __syncthreads();
-
-  for (int base = 0; base < S.n_meshlets; base += kChunk) {
-    if (tid == 0) {
-      counters[0] = 0;
-      counters[1] = 0;
-    }
-    __syncthreads();
-    const int end = min(base + kChunk, S.n_meshlets);
-    for (int m = base + tid; m < end; m += kThreads) {
-      const float4 h0 = __ldg(S.mhdr + 3 * m), h1 = __ldg(S.mhdr + 3 * m + 1);
-      bool vis = sphere_visible(cm, bd, h0.x, h0.y, h0.z, h0.w);
+template <bool kCount>
+__device__ __forceinline__ bool pop_cluster(ClusterQueue& q, int* next_ctr, const DScene& S,
+                                            const Cam& cm, const View& vw, int lane, uint4& out,
+                                            Cnt& cn) {
+  while (q.mask == 0) {
+    int b = 0;
+    if (lane == 0) b = atomicAdd(next_ctr, 32);
+    b = __shfl_sync(kFull, b, 0);
+    if (b >= S.n_meshlets) return false;
+    const int m = b + lane;
+    bool vis = false;
+    if (m < S.n_meshlets) {
+      if (kCount) cn.v[kCntClustersTested]++;
+      const float4 h0 = __ldg(S.mhdr + 3 * m);
+      vis = sphere_visible(cm, vw, h0.x, h0.y, h0.z, h0.w);
       if (vis) {
-        const float4 h2 = __ldg(S.mhdr + 3 * m + 2);
+        const float4 h1 = __ldg(S.mhdr + 3 * m + 1), h2 = __ldg(S.mhdr + 3 * m + 2);
         if (h2.x > -0.5f) {  // normal cone: every face looks away from the eye
           const float vx = h0.x - cm.ex, vy = h0.y - cm.ey, vz = h0.z - cm.ez;
           const float av = h1.x * vx + h1.y * vy + h1.z * vz;
@@ -392,112 +482,223 @@ __global__ void __launch_bounds__(kThreads, 2) raster_kernel(const RasterParams 
           const float cr = sqrtf(cx_ * cx_ + cy_ * cy_ + cz_ * cz_);
           if (av * h2.x - cr * h1.w > h0.w * 1.001f + 1e-4f) vis = false;
         }
-        if (vis) {
-          const int slot = atomicAdd(&counters[0], 1);
-          list[slot] = make_uint4(__float_as_uint(h2.y), __float_as_uint(h2.z),
-                                  __float_as_uint(h2.w), 0u);
-        }
+        q.mine = make_uint4(__float_as_uint(h2.y), __float_as_uint(h2.z), __float_as_uint(h2.w), 0u);
       }
+    }
+    q.mask = __ballot_sync(kFull, vis);
+  }
+  const int L = __ffs(q.mask) - 1;
+  q.mask &= q.mask - 1;
+  out.x = __shfl_sync(kFull, q.mine.x, L);
+  out.y = __shfl_sync(kFull, q.mine.y, L);
+  out.z = __shfl_sync(kFull, q.mine.z, L);
+  return true;
+}
+
+__device__ __forceinline__ void issue_cluster(WarpSmem& ws, int buf, const DScene& S, uint4 e) {
+  const int nv = e.z & 0xff, nt = (e.z >> 8) & 0xff;
+  const uint32_t tbytes = (uint32_t)((nt + 3) & ~3) * 4u;
+  mbar_expect_tx(&ws.bar[buf], nv * 16u + tbytes);
+  bulk_g2s(ws.vbuf[buf], S.mverts + e.x, nv * 16u, &ws.bar[buf]);
+  bulk_g2s(ws.tbuf[buf], S.mtris + e.y, tbytes, &ws.bar[buf]);
+}
+
+template <bool kCount>
+__global__ void __launch_bounds__(kThreads, kRasterMinBlocks) raster_kernel(const RasterParams P) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  int* ctr = reinterpret_cast<int*>(smem);  // [0] env, [1] clusters, [2] objects
+  WarpSmem* wsm = reinterpret_cast<WarpSmem*>(smem + 128);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  WarpSmem& ws = wsm[warp];
+  const int W = P.W, H = P.H, npix = W * H;
+  Cnt cn;
+  if (kCount)
+    for (int k = 0; k < kRasterCounters; ++k) cn.v[k] = 0;
+  View vw;
+  vw.W = W;
+  vw.H = H;
+  vw.fb = P.fb_slots + (size_t)blockIdx.x * npix;
+  if (lane == 0) {
+    mbar_init(&ws.bar[0]);
+    mbar_init(&ws.bar[1]);
+    fence_mbar_init();
+  }
+  uint32_t phase[2] = {0u, 0u};
+  bool dead = false;  // a wait gave up: this warp stops using its buffers
+
+  for (;;) {
+    if (tid == 0) {
+      ctr[0] = atomicAdd(P.work, 1);
+      ctr[1] = 0;
+      ctr[2] = 0;
     }
     __syncthreads();
-    const int count = counters[0];
-    // warps consume the surviving clusters; the next one streams in meanwhile
-    int cur = 0, buf = 0;
-    if (lane == 0) cur = atomicAdd(&counters[1], 1);
-    cur = __shfl_sync(kFull, cur, 0);
-    if (!dead && cur < count && lane == 0) {
-      const uint4 e = list[cur];
-      const int nv = e.z & 0xff, nt = (e.z >> 8) & 0xff;
-      const uint32_t tbytes = (uint32_t)((nt + 3) & ~3) * 4u;
-      mbar_expect_tx(&ws.bar[0], nv * 16u + tbytes);
-      bulk_g2s(ws.vbuf[0], S.mverts + e.x, nv * 16u, &ws.bar[0]);
-      bulk_g2s(ws.tbuf[0], S.mtris + e.y, tbytes, &ws.bar[0]);
+    const int env = ctr[0];
+    if (env >= P.n) break;
+    const DScene& S = P.scenes[P.env_scene[env]];
+    Cam cm;
+    {
+      const float* c = P.cam + (size_t)env * 12;
+      cm.rx = c[0]; cm.ux = c[1]; cm.fx = c[2];
+      cm.ry = c[3]; cm.uy = c[4]; cm.fy = c[5];
+      cm.rz = c[6]; cm.uz = c[7]; cm.fz = c[8];
+      cm.ex = c[9]; cm.ey = c[10]; cm.ez = c[11];
+      cm.f = 0.5f * (float)W;
+      cm.cx = 0.5f * (float)W;
+      cm.cy = 0.5f * (float)H;
+      cm.near_ = P.near_;
     }
-    while (!dead && cur < count) {
-      int nxt = 0;
-      if (lane == 0) nxt = atomicAdd(&counters[1], 1);
-      nxt = __shfl_sync(kFull, nxt, 0);
-      if (nxt < count && lane == 0) {
-        const uint4 e = list[nxt];
-        const int nv = e.z & 0xff, nt = (e.z >> 8) & 0xff;
-        const uint32_t tbytes = (uint32_t)((nt + 3) & ~3) * 4u;
-        mbar_expect_tx(&ws.bar[buf ^ 1], nv * 16u + tbytes);
-        bulk_g2s(ws.vbuf[buf ^ 1], S.mverts + e.x, nv * 16u, &ws.bar[buf ^ 1]);
-        bulk_g2s(ws.tbuf[buf ^ 1], S.mtris + e.y, tbytes, &ws.bar[buf ^ 1]);
-      }
-      const bool ok = mbar_wait(&ws.bar[buf], phase[buf]);
+    vw.tl = (-1.f - cm.cx) / cm.f;
+    vw.tr = ((float)W + 1.f - cm.cx) / cm.f;
+    vw.tt = (cm.cy + 1.f) / cm.f;
+    vw.tb = (cm.cy - ((float)H + 1.f)) / cm.f;
+    vw.kl = rsqrtf(1.f + vw.tl * vw.tl);
+    vw.kr = rsqrtf(1.f + vw.tr * vw.tr);
+    vw.kt = rsqrtf(1.f + vw.tt * vw.tt);
+    vw.kb = rsqrtf(1.f + vw.tb * vw.tb);
+
+    // clusters: each warp culls and draws on its own, staging the next
+    // survivor while it draws the current one
+    ClusterQueue q;
+    q.mask = 0;
+    q.mine = make_uint4(0u, 0u, 0u, 0u);
+    uint4 cur;
+    bool have = !dead && pop_cluster<kCount>(q, &ctr[1], S, cm, vw, lane, cur, cn);
+    int buf = 0;
+    if (have && lane == 0) issue_cluster(ws, 0, S, cur);
+    while (have) {
+      uint4 nxt;
+      const bool more = pop_cluster<kCount>(q, &ctr[1], S, cm, vw, lane, nxt, cn);
+      if (more && lane == 0) issue_cluster(ws, buf ^ 1, S, nxt);
+      const bool ok = mbar_wait(&ws.bar[buf], phase[buf],
+                                (kCount && lane == 0) ? &cn.v[kCntWaitIters] : nullptr);
       phase[buf] ^= 1u;
       if (!__all_sync(kFull, ok)) {
         if (lane == 0) atomicOr(P.err, kErrWaitTimeout);
         // let the copy in flight into the other buffer land before leaving
-        if (nxt < count) mbar_wait(&ws.bar[buf ^ 1], phase[buf ^ 1]);
+        if (more) mbar_wait(&ws.bar[buf ^ 1], phase[buf ^ 1]);
         dead = true;
         break;
       }
-      const uint4 e = list[cur];
-      raster_cluster(fb, bd, cm, ws, buf, e.z & 0xff, (e.z >> 8) & 0xff, e.y, P.small_px, lane);
+      raster_cluster<kCount>(vw, cm, ws, buf, cur.z & 0xff, (cur.z >> 8) & 0xff, cur.y,
+                             P.big_px, lane, cn);
       cur = nxt;
+      have = more;
       buf ^= 1;
     }
-    __syncthreads();
-  }
-
-  // free objects: icosahedra scaled to each object's radius
-  if (!dead) {
-    for (int j = warp; j < P.M; j += kWarps) {
+    // free objects: icosahedra scaled to each object's radius, handed out to
+    // warps as they finish their clusters
+    while (!dead) {
+      int j = 0;
+      if (lane == 0) j = atomicAdd(&ctr[2], 1);
+      j = __shfl_sync(kFull, j, 0);
+      if (j >= P.M) break;
       const float4 o = P.obj[(size_t)env * P.M + j];
-      if (!sphere_visible(cm, bd, o.x, o.y, o.z, o.w * 1.0001f + 1e-6f)) continue;
+      if (!sphere_visible(cm, vw, o.x, o.y, o.z, o.w * 1.0001f + 1e-6f)) continue;
       for (int k = lane; k < P.omesh_nv; k += 32) {
         const float4 u = P.omesh_v[k];
         ws.vbuf[0][k] = make_float4(fmaf(o.w, u.x, o.x), fmaf(o.w, u.y, o.y), fmaf(o.w, u.z, o.z), 0.f);
       }
       for (int k = lane; k < P.omesh_nt; k += 32) ws.tbuf[0][k] = P.omesh_t[k];
       __syncwarp();
-      raster_cluster(fb, bd, cm, ws, 0, P.omesh_nv, P.omesh_nt,
-                     (uint32_t)S.n_tris + (uint32_t)(j * P.omesh_nt), P.small_px, lane);
+      raster_cluster<kCount>(vw, cm, ws, 0, P.omesh_nv, P.omesh_nt,
+                             (uint32_t)S.n_tris + (uint32_t)(j * P.omesh_nt), P.big_px, lane, cn);
     }
-  }
-  __syncthreads();
+    // object vertices were written to vbuf[0] by ordinary stores: order them
+    // before the next environment's bulk copies into the same buffer
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    // the reductions must land before the resolve reads the slot
+    __threadfence();
+    __syncthreads();
 
-  // resolve the band and write it out row-major (coalesced)
-  const size_t out0 = ((size_t)env * P.H + bd.row0) * W;
-  for (int p = tid; p < W * rh; p += kThreads) {
-    const unsigned long long key = fb[p];
-    float z = 0.f;
-    uint32_t col = 0u;
-    if (key != ~0ull) {
-      const float invz = __uint_as_float(~(uint32_t)(key >> 32));
-      z = 1.0f / invz;
-      const uint32_t id = (uint32_t)key;
-      col = id < (uint32_t)S.n_tris ? __ldg(S.tri_rgb + id)
-                                    : __ldg(P.obj_rgb + (id - (uint32_t)S.n_tris) / P.omesh_nt);
+    // resolve four pixels per thread: 16-byte stores, row-major; the slot is
+    // reset for this CTA's next environment
+    const size_t out0 = (size_t)env * npix;
+    for (int p = tid * 4; p < npix; p += kThreads * 4) {
+      // L2 reads/writes (.cg): the reductions were applied in L2
+      const ulonglong2 k01 = __ldcg(reinterpret_cast<const ulonglong2*>(vw.fb + p));
+      const ulonglong2 k23 = __ldcg(reinterpret_cast<const ulonglong2*>(vw.fb + p + 2));
+      __stcg(reinterpret_cast<ulonglong2*>(vw.fb + p), make_ulonglong2(~0ull, ~0ull));
+      __stcg(reinterpret_cast<ulonglong2*>(vw.fb + p + 2), make_ulonglong2(~0ull, ~0ull));
+      const unsigned long long keys[4] = {k01.x, k01.y, k23.x, k23.y};
+      float z[4];
+      uint32_t col[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        z[k] = 0.f;
+        col[k] = 0u;
+        if (keys[k] != ~0ull) {
+          const float invz = __uint_as_float(~(uint32_t)(keys[k] >> 32));
+          z[k] = 1.0f / invz;
+          const uint32_t id = (uint32_t)keys[k];
+          col[k] = id < (uint32_t)S.n_tris ? __ldg(S.tri_rgb + id)
+                                           : __ldg(P.obj_rgb + (id - (uint32_t)S.n_tris) / P.omesh_nt);
+        }
+      }
+      if (P.depth_fp16) {
+        __half2 a = __floats2half2_rn(z[0], z[1]), b = __floats2half2_rn(z[2], z[3]);
+        uint2 v;
+        v.x = *reinterpret_cast<uint32_t*>(&a);
+        v.y = *reinterpret_cast<uint32_t*>(&b);
+        *reinterpret_cast<uint2*>(reinterpret_cast<__half*>(P.depth) + out0 + p) = v;
+      } else {
+        *reinterpret_cast<float4*>(reinterpret_cast<float*>(P.depth) + out0 + p) =
+            make_float4(z[0], z[1], z[2], z[3]);
+      }
+      if (P.rgb) {
+        // 4 pixels = 12 bytes R G B R G B ... packed into three words
+        const uint32_t r0 = col[0], r1 = col[1], r2 = col[2], r3 = col[3];
+        const uint32_t w0 = ((r0 >> 16) & 0xff) | (((r0 >> 8) & 0xff) << 8) | ((r0 & 0xff) << 16) |
+                            (((r1 >> 16) & 0xff) << 24);
+        const uint32_t w1 = ((r1 >> 8) & 0xff) | ((r1 & 0xff) << 8) | (((r2 >> 16) & 0xff) << 16) |
+                            (((r2 >> 8) & 0xff) << 24);
+        const uint32_t w2 = (r2 & 0xff) | (((r3 >> 16) & 0xff) << 8) | (((r3 >> 8) & 0xff) << 16) |
+                            ((r3 & 0xff) << 24);
+        uint32_t* o = reinterpret_cast<uint32_t*>(P.rgb + (out0 + p) * 3);
+        o[0] = w0;
+        o[1] = w1;
+        o[2] = w2;
+      }
     }
-    if (P.depth_fp16)
-      reinterpret_cast<__half*>(P.depth)[out0 + p] = __float2half_rn(z);
-    else
-      reinterpret_cast<float*>(P.depth)[out0 + p] = z;
-    if (P.rgb) {
-      uint8_t* o = P.rgb + (out0 + p) * 3;
-      o[0] = (uint8_t)(col >> 16);
-      o[1] = (uint8_t)(col >> 8);
-      o[2] = (uint8_t)col;
+    __syncthreads();
+  }
+  if (kCount) {
+    for (int k = 0; k < kRasterCounters; ++k) {
+      unsigned long long v = cn.v[k];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+      if (lane == 0 && v) atomicAdd(P.counters + k, v);
     }
   }
 }
 
 }  // namespace
 
-size_t raster_smem_bytes(int W, int region_h) {
-  return (size_t)W * region_h * 8 + kChunk * 16 + 128 + kWarps * sizeof(WarpSmem);
-}
+size_t raster_smem_bytes() { return 128 + kWarps * sizeof(WarpSmem); }
 
-cudaError_t raster_configure(int W, int region_h) {
-  return cudaFuncSetAttribute(raster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)raster_smem_bytes(W, region_h));
+cudaError_t raster_configure(int* slots) {
+  const int bytes = (int)raster_smem_bytes();
+  cudaError_t e = cudaFuncSetAttribute(raster_kernel<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(raster_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0, dev = 0, sms = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raster_kernel<false>, kThreads, bytes);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  *slots = (per_sm > 0 ? per_sm : 1) * sms;
+  return cudaSuccess;
 }
 
 void launch_raster(const RasterParams& p, cudaStream_t s) {
-  raster_kernel<<<p.n * p.regions, kThreads, raster_smem_bytes(p.W, p.region_h), s>>>(p);
+  const size_t smem = raster_smem_bytes();
+  const int grid = p.n < p.n_slots ? p.n : p.n_slots;
+  if (p.counters)
+    raster_kernel<true><<<grid, kThreads, smem, s>>>(p);
+  else
+    raster_kernel<false><<<grid, kThreads, smem, s>>>(p);
 }
 
 }  // namespace gx

@@ -26,7 +26,11 @@ MAX_SPHERES = 31
 
 SYMBOLS = ["gx_scene_set_create", "gx_scene_set_destroy", "gx_create", "gx_destroy", "gx_reset",
            "gx_step", "gx_step_host", "gx_sync", "gx_device_error", "gx_state_bytes",
-           "gx_save_state", "gx_load_state", "gx_state_layout", "gx_last_error"]
+           "gx_save_state", "gx_load_state", "gx_state_layout", "gx_phase_times",
+           "gx_raster_counters", "gx_last_error"]
+RASTER_COUNTERS = ["clusters_tested", "clusters_drawn", "tris_seen", "tris_front", "tris_expand",
+                   "expand_pixels", "tris_warp", "warp_blocks", "tris_clipped", "fragments", "wait_polls",
+                   "expand_trips", "rounds"]
 
 f32p = C.POINTER(C.c_float)
 i32p = C.POINTER(C.c_int32)
@@ -62,7 +66,7 @@ class GxConfig(C.Structure):
                 ("depth_fp16", C.c_int32), ("render_rgb", C.c_int32), ("n_objects", C.c_int32),
                 ("obj_radius_min", C.c_float), ("obj_radius_max", C.c_float),
                 ("seed", C.c_uint64), ("env_scene", i32p), ("raster_regions", C.c_int32),
-                ("small_tri_px", C.c_int32), ("use_graph", C.c_int32)]
+                ("small_tri_px", C.c_int32), ("use_graph", C.c_int32), ("profile", C.c_int32)]
 
 
 class GxOutputs(C.Structure):
@@ -105,6 +109,8 @@ def lib():
         L.gx_save_state.argtypes = [vp, vp, C.c_size_t]
         L.gx_load_state.argtypes = [vp, vp, C.c_size_t]
         L.gx_state_layout.argtypes = [vp, P(C.c_size_t)]
+        L.gx_phase_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+        L.gx_raster_counters.argtypes = [vp, C.POINTER(C.c_int64), C.c_int32]
         L.gx_last_error.argtypes = [vp]
         L.gx_last_error.restype = C.c_char_p
         _lib = L
@@ -195,7 +201,8 @@ class Sim:
 
     def __init__(self, scene_set: SceneSet, robot: _inputs.Robot, n_envs: int, img=(128, 128),
                  depth_fp16=False, render_rgb=True, n_objects=40, obj_radius=(0.03, 0.06),
-                 seed=1, env_scene=None, raster_regions=0, small_tri_px=0, use_graph=False):
+                 seed=1, env_scene=None, raster_regions=0, small_tri_px=0, use_graph=False,
+                 profile=0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("gx needs a CUDA device; there is no CPU fallback")
@@ -213,6 +220,7 @@ class Sim:
             es = np.ascontiguousarray(env_scene, np.int32)
             cfg.env_scene = es.ctypes.data_as(i32p)
         cfg.raster_regions, cfg.small_tri_px, cfg.use_graph = raster_regions, small_tri_px, int(use_graph)
+        cfg.profile = int(profile)
         self.robot_c = robot_struct(robot)
         self.handle = C.c_void_p()
         _check(lib().gx_create(scene_set.handle, C.byref(self.robot_c), C.byref(cfg),
@@ -272,6 +280,19 @@ class Sim:
         _check(lib().gx_step_host(self.handle, C.c_void_p(ptr), C.byref(o), self._stream(stream)),
                self.handle)
         return host_out
+
+    def phase_times(self):
+        """(ms, launches) per kernel since the last call: physics, raster, reset."""
+        ms = (C.c_double * 3)()
+        n = (C.c_int64 * 3)()
+        _check(lib().gx_phase_times(self.handle, ms, n), self.handle)
+        return list(ms), list(n)
+
+    def raster_counters(self):
+        """Rasteriser work counters since the last call (profile bit 1 only)."""
+        v = (C.c_int64 * len(RASTER_COUNTERS))()
+        _check(lib().gx_raster_counters(self.handle, v, len(RASTER_COUNTERS)), self.handle)
+        return dict(zip(RASTER_COUNTERS, list(v)))
 
     def sync(self):
         _check(lib().gx_sync(self.handle), self.handle)

@@ -67,7 +67,7 @@ def test_reset_matches_oracle(room):
         d = (s["yaw"][e] - st.base[2]) % (2 * math.pi)
         assert min(d, 2 * math.pi - d) < 1e-5
         assert np.allclose(s["q"][:, e], ROBOT.q_rest, atol=0)
-    assert nb <= 2
+    assert nb <= n // 4   # near-band decisions anywhere in 64-try rejection loops
     # a second reset starts episode 2 with a new placement
     sim.reset()
     s2 = sim.state_arrays()
