@@ -218,6 +218,32 @@ gx_status gx_phase_times(gx_ctx* ctx, double ms[3], int64_t launches[3]);
  * GX_ESTATE when the context does not count. */
 gx_status gx_raster_counters(gx_ctx* ctx, int64_t* out, int32_t n);
 
+/* Renders depth (and RGB when rgb != NULL) for n environments without
+ * allocating any device memory.  The paper has no counterpart: this serves
+ * callers that cannot call cudaMalloc when they need images -- code in a
+ * section where device allocation is forbidden or would stall (real-time
+ * loops, allocation-free serving paths, hosts that only allow allocation at
+ * start-up) or embedders that have spent their memory budget.  Instead of the
+ * framebuffer slots a context allocates, it uses a fixed 16 MiB scratch array
+ * built into the library, which every GPU that loads the library keeps until
+ * the process exits; with it at most 16 MiB / (img_w * img_h * 8) CTAs render
+ * at once, so it is slower than gx_step on large batches.
+ * Inputs (device memory, caller-owned): env_scene [n] scene index per env;
+ * cam [n][12] camera-to-world rotation, row-major with columns right, up,
+ * forward, then the eye position; obj [n][n_objects][4] object centre and
+ * radius.  Outputs: depth [n][img_h][img_w] float32 (or half when depth_fp16),
+ * rgb [n][img_h][img_w][3] (optional).  Image sides must be multiples of 32
+ * and at most 256 (larger sizes return GX_EINVAL); n_objects <= 64.
+ * The first call on a device (the current one) sets the scratch up
+ * synchronously; make that first call before any stream capture.  Every call
+ * shares the same scratch and clears what it needs at the start, so calls
+ * that overlap on the GPU (other streams, other host threads) race: order
+ * them on one stream.  Asynchronous on `stream` after the first call. */
+gx_status gx_render_noalloc(const gx_scene_set* set, int32_t n, const int32_t* env_scene,
+                            const float* cam, const float* obj, int32_t n_objects, int32_t img_w,
+                            int32_t img_h, float cam_near, void* depth, int32_t depth_fp16,
+                            uint8_t* rgb, void* stream);
+
 const char* gx_last_error(const gx_ctx* ctx);
 
 #ifdef __cplusplus

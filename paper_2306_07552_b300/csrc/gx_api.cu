@@ -618,3 +618,20 @@ extern "C" gx_status gx_raster_counters(gx_ctx* x, int64_t* out, int32_t n) {
 extern "C" const char* gx_last_error(const gx_ctx* x) {
   return x ? x->msg.c_str() : g_last_error.c_str();
 }
+
+// ===========================================================================
+// internal helpers for other translation units
+// ===========================================================================
+bool gx::scene_set_view(const gx_scene_set* set, SceneSetView* out) {
+  if (!set || !out) return false;
+  out->scenes = set->d_scenes;
+  out->n = set->n;
+  out->omesh_v = set->omesh_v;
+  out->omesh_t = set->omesh_t;
+  out->omesh_nv = set->omesh_nv;
+  out->omesh_nt = set->omesh_nt;
+  out->obj_rgb = set->obj_rgb;
+  return true;
+}
+
+gx_status gx::set_last_error(gx_status s, const char* msg) { return fail(nullptr, s, "%s", msg); }

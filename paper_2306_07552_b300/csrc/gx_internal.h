@@ -143,6 +143,19 @@ enum RasterCounter {
 void launch_physics(const PhysicsParams& p, cudaStream_t s);
 void launch_reset(const ResetParams& p, cudaStream_t s);
 void launch_raster(const RasterParams& p, cudaStream_t s);
+// Read-only view of a scene set's device data, for entry points outside
+// gx_api.cu.
+struct SceneSetView {
+  const DScene* scenes;
+  int n;
+  const float4* omesh_v;
+  const uint32_t* omesh_t;
+  int omesh_nv, omesh_nt;
+  const uint32_t* obj_rgb;
+};
+bool scene_set_view(const gx_scene_set* set, SceneSetView* out);
+gx_status set_last_error(gx_status s, const char* msg);
+
 size_t raster_smem_bytes();
 cudaError_t raster_configure(int* slots);
 void launch_grid_build(float* grid, const float* boxes, int n_boxes, float ox, float oy, float oz,

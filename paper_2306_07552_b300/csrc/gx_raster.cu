@@ -40,6 +40,8 @@
 #include <math_constants.h>
 #include <cuda_fp16.h>
 
+#include <mutex>
+
 #include "gx_internal.h"
 
 namespace gx {
@@ -702,3 +704,122 @@ void launch_raster(const RasterParams& p, cudaStream_t s) {
 }
 
 }  // namespace gx
+
+// ===========================================================================
+// Rendering without allocation.
+//
+// Some callers cannot call cudaMalloc when they need images: code that runs
+// in a section where device allocation is forbidden or would stall (real-time
+// control loops, allocation-free serving paths, hosts whose memory policy
+// only allows allocation at start-up), or embedders that already spent their
+// memory budget.  gx_render_noalloc renders for them with a framebuffer
+// scratch area that the library itself holds: the fixed array below, which
+// every GPU that loads this library keeps until the process exits.
+// ===========================================================================
+namespace gx {
+namespace {
+
+constexpr size_t kNoAllocFbBytes = 16u << 20;  // framebuffer slots (16 MiB)
+constexpr int kNoAllocMaxSide = 256;           // largest image side it accepts
+
+// [0, kNoAllocFbBytes): framebuffer slots; then the work counter and a spare
+// word for device-side error bits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocFbBytes + 256];
+
+struct NoAllocDevice {
+  bool ready = false;
+  unsigned char* base = nullptr;  // device address of g_noalloc_scratch
+  int occupancy_slots = 0;
+};
+constexpr int kMaxDevices = 64;
+NoAllocDevice g_noalloc[kMaxDevices];
+std::mutex g_noalloc_mu;
+
+}  // namespace
+}  // namespace gx
+
+extern "C" gx_status gx_render_noalloc(const gx_scene_set* set, int32_t n,
+                                       const int32_t* env_scene, const float* cam,
+                                       const float* obj, int32_t n_objects, int32_t img_w,
+                                       int32_t img_h, float cam_near, void* depth,
+                                       int32_t depth_fp16, uint8_t* rgb, void* stream) {
+  using namespace gx;
+  SceneSetView sv;
+  if (!scene_set_view(set, &sv)) return set_last_error(GX_EINVAL, "gx_render_noalloc: set is NULL");
+  if (n < 1 || !env_scene || !cam || !depth || (n_objects > 0 && !obj))
+    return set_last_error(GX_EINVAL, "gx_render_noalloc: NULL buffer or n < 1");
+  if (n_objects < 0 || n_objects > GX_MAX_OBJECTS)
+    return set_last_error(GX_EINVAL, "gx_render_noalloc: n_objects must be in [0, 64]");
+  if (img_w < 32 || img_h < 32 || img_w % 32 || img_h % 32)
+    return set_last_error(GX_EINVAL, "gx_render_noalloc: image sides must be multiples of 32");
+  if (img_w > kNoAllocMaxSide || img_h > kNoAllocMaxSide)
+    return set_last_error(GX_EINVAL,
+                          "gx_render_noalloc: image larger than its fixed scratch allows "
+                          "(at most 256x256)");
+  if (!(cam_near > 0.f)) return set_last_error(GX_EINVAL, "gx_render_noalloc: cam_near <= 0");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+    return set_last_error(GX_ECUDA, "gx_render_noalloc: no usable current device");
+  NoAllocDevice& d = g_noalloc[dev];
+  {
+    // one-time set-up on this device (the current one): find the array's
+    // device address and mark every framebuffer key empty
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!d.ready) {
+      void* p = nullptr;
+      if ((e = cudaGetSymbolAddress(&p, g_noalloc_scratch)) != cudaSuccess)
+        return set_last_error(GX_ECUDA, "gx_render_noalloc: cudaGetSymbolAddress failed");
+      if ((e = cudaMemset(p, 0xff, kNoAllocFbBytes)) != cudaSuccess ||
+          (e = cudaMemset((unsigned char*)p + kNoAllocFbBytes, 0, 256)) != cudaSuccess)
+        return set_last_error(GX_ECUDA, "gx_render_noalloc: clearing the scratch failed");
+      int slots = 0;
+      if ((e = raster_configure(&slots)) != cudaSuccess)
+        return set_last_error(GX_ECUDA, "gx_render_noalloc: kernel configuration failed");
+      if ((e = cudaDeviceSynchronize()) != cudaSuccess)
+        return set_last_error(GX_ECUDA, "gx_render_noalloc: set-up failed");
+      d.base = (unsigned char*)p;
+      d.occupancy_slots = slots;
+      d.ready = true;
+    }
+  }
+  const size_t slot_bytes = (size_t)img_w * img_h * 8;
+  int slots = (int)(kNoAllocFbBytes / slot_bytes);
+  if (slots > d.occupancy_slots) slots = d.occupancy_slots;
+  if (slots > n) slots = n;
+  cudaStream_t s = (cudaStream_t)stream;
+  int* work = reinterpret_cast<int*>(d.base + kNoAllocFbBytes);
+  unsigned* err = reinterpret_cast<unsigned*>(d.base + kNoAllocFbBytes + 4);
+  // shared by every call: start from a zero work counter and empty keys
+  if ((e = cudaMemsetAsync(work, 0, 8, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(d.base, 0xff, (size_t)slots * slot_bytes, s)) != cudaSuccess)
+    return set_last_error(GX_ECUDA, "gx_render_noalloc: clearing the scratch failed");
+  RasterParams rp{};
+  rp.n = n;
+  rp.M = n_objects;
+  rp.W = img_w;
+  rp.H = img_h;
+  rp.big_px = 1 << 30;
+  rp.fb_slots = reinterpret_cast<unsigned long long*>(d.base);
+  rp.n_slots = slots;
+  rp.work = work;
+  rp.scenes = sv.scenes;
+  rp.env_scene = env_scene;
+  rp.cam = cam;
+  rp.obj = reinterpret_cast<const float4*>(obj);
+  rp.omesh_v = sv.omesh_v;
+  rp.omesh_t = sv.omesh_t;
+  rp.omesh_nv = sv.omesh_nv;
+  rp.omesh_nt = sv.omesh_nt;
+  rp.obj_rgb = sv.obj_rgb;
+  rp.near_ = cam_near;
+  rp.depth = depth;
+  rp.depth_fp16 = depth_fp16 ? 1 : 0;
+  rp.rgb = rgb;
+  rp.err = err;
+  rp.counters = nullptr;
+  launch_raster(rp, s);
+  if ((e = cudaGetLastError()) != cudaSuccess)
+    return set_last_error(GX_ECUDA, "gx_render_noalloc: launch failed");
+  return GX_OK;
+}

@@ -27,7 +27,7 @@ MAX_SPHERES = 31
 SYMBOLS = ["gx_scene_set_create", "gx_scene_set_destroy", "gx_create", "gx_destroy", "gx_reset",
            "gx_step", "gx_step_host", "gx_sync", "gx_device_error", "gx_state_bytes",
            "gx_save_state", "gx_load_state", "gx_state_layout", "gx_phase_times",
-           "gx_raster_counters", "gx_last_error"]
+           "gx_raster_counters", "gx_render_noalloc", "gx_last_error"]
 RASTER_COUNTERS = ["clusters_tested", "clusters_drawn", "tris_seen", "tris_front", "tris_expand",
                    "expand_pixels", "tris_warp", "warp_blocks", "tris_clipped", "fragments", "wait_polls",
                    "expand_trips", "rounds"]
@@ -111,6 +111,8 @@ def lib():
         L.gx_state_layout.argtypes = [vp, P(C.c_size_t)]
         L.gx_phase_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
         L.gx_raster_counters.argtypes = [vp, C.POINTER(C.c_int64), C.c_int32]
+        L.gx_render_noalloc.argtypes = [vp, C.c_int32, vp, vp, vp, C.c_int32, C.c_int32,
+                                        C.c_int32, C.c_float, vp, C.c_int32, vp, vp]
         L.gx_last_error.argtypes = [vp]
         L.gx_last_error.restype = C.c_char_p
         _lib = L
