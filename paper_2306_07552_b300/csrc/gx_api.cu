@@ -248,6 +248,10 @@ extern "C" gx_status gx_scene_set_create(const gx_scene_desc* scenes, int32_t n_
     HostMeshlets hm;
     build_meshlets(d, hm);
     s->meshlets_per_scene.push_back((int)(hm.hdr.size() / 3));
+    if (hm.verts.size() >= (1u << 24) || hm.tris.size() >= (1u << 24)) {
+      free_set(s);
+      return fail(nullptr, GX_EINVAL, "scene %d: more than 2^24 cluster vertices or triangles", i);
+    }
     if ((e = upload(s, (float4**)&ds.mhdr, hm.hdr.data(), hm.hdr.size())) != cudaSuccess)
       return bail(e, "upload meshlets");
     if ((e = upload(s, (float4**)&ds.mverts, hm.verts.data(), hm.verts.size())) != cudaSuccess)

@@ -52,6 +52,7 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kThreads = kRasterThreads;
 constexpr int kWarps = kThreads / 32;
 constexpr long kWaitLimit = 1L << 22;  // bounded waits
+constexpr int kListCap = 2048;          // clusters culled per pass
 
 // Setup of one triangle queued for pixel expansion.
 struct __align__(16) ExpTri {
@@ -89,6 +90,7 @@ struct Cam {
 struct View {
   int W, H;
   unsigned long long* fb;  // this CTA's slot, [H][W]
+  uint64_t pol;            // L2 policy keeping the slot resident
   // side planes of the frustum as slopes x/z, y/z, with 1/|n|
   float tl, tr, tt, tb, kl, kr, kt, kb;
 };
@@ -148,7 +150,11 @@ __device__ __forceinline__ void frag(const View& vw, int i, int j, float A, floa
   invz = fmaxf(invz, 1e-30f);
   const unsigned long long key =
       ((unsigned long long)(~__float_as_uint(invz)) << 32) | (unsigned long long)id;
-  atomicMin(vw.fb + j * vw.W + i, key);  // result unused: a reduction
+  // fire-and-forget reduction in L2, the slot marked to stay resident there
+  asm volatile("red.relaxed.gpu.global.min.L2::cache_hint.u64 [%0], %1, %2;" ::"l"(
+                   vw.fb + j * vw.W + i),
+               "l"(key), "l"(vw.pol)
+               : "memory");
 }
 
 // Bounding sphere (world centre c, radius r) vs the view frustum.
@@ -450,66 +456,28 @@ __device__ void raster_cluster(const View& vw, const Cam& cm, WarpSmem& ws, int 
   __syncwarp();
 }
 
-// Per-warp software pipeline over the scene's clusters.  A warp grabs 32
-// cluster headers at a time from the CTA's shared counter, culls them lane-
-// parallel and keeps the survivors as a ballot mask; `pop` hands out the next
-// survivor, culling a new batch when the mask runs dry.
-struct ClusterQueue {
-  unsigned mask;   // survivors of the batch in hand not yet handed out
-  uint4 mine;      // this lane's cluster entry (vertex offset, triangle offset, counts)
-};
-
-template <bool kCount>
-__device__ __forceinline__ bool pop_cluster(ClusterQueue& q, int* next_ctr, const DScene& S,
-                                            const Cam& cm, const View& vw, int lane, uint4& out,
-                                            Cnt& cn) {
-  while (q.mask == 0) {
-    int b = 0;
-    if (lane == 0) b = atomicAdd(next_ctr, 32);
-    b = __shfl_sync(kFull, b, 0);
-    if (b >= S.n_meshlets) return false;
-    const int m = b + lane;
-    bool vis = false;
-    if (m < S.n_meshlets) {
-      if (kCount) cn.v[kCntClustersTested]++;
-      const float4 h0 = __ldg(S.mhdr + 3 * m);
-      vis = sphere_visible(cm, vw, h0.x, h0.y, h0.z, h0.w);
-      if (vis) {
-        const float4 h1 = __ldg(S.mhdr + 3 * m + 1), h2 = __ldg(S.mhdr + 3 * m + 2);
-        if (h2.x > -0.5f) {  // normal cone: every face looks away from the eye
-          const float vx = h0.x - cm.ex, vy = h0.y - cm.ey, vz = h0.z - cm.ez;
-          const float av = h1.x * vx + h1.y * vy + h1.z * vz;
-          const float cx_ = h1.y * vz - h1.z * vy, cy_ = h1.z * vx - h1.x * vz,
-                      cz_ = h1.x * vy - h1.y * vx;
-          const float cr = sqrtf(cx_ * cx_ + cy_ * cy_ + cz_ * cz_);
-          if (av * h2.x - cr * h1.w > h0.w * 1.001f + 1e-4f) vis = false;
-        }
-        q.mine = make_uint4(__float_as_uint(h2.y), __float_as_uint(h2.z), __float_as_uint(h2.w), 0u);
-      }
-    }
-    q.mask = __ballot_sync(kFull, vis);
-  }
-  const int L = __ffs(q.mask) - 1;
-  q.mask &= q.mask - 1;
-  out.x = __shfl_sync(kFull, q.mine.x, L);
-  out.y = __shfl_sync(kFull, q.mine.y, L);
-  out.z = __shfl_sync(kFull, q.mine.z, L);
-  return true;
+__device__ __forceinline__ void issue_cluster(WarpSmem& ws, int buf, const DScene& S, uint2 e) {
+  const uint32_t voff = e.x & 0xffffffu, nv = e.x >> 24;
+  const uint32_t toff = e.y & 0xffffffu, nt = e.y >> 24;
+  const uint32_t tbytes = ((nt + 3u) & ~3u) * 4u;
+  mbar_expect_tx(&ws.bar[buf], nv * 16u + tbytes);
+  bulk_g2s(ws.vbuf[buf], S.mverts + voff, nv * 16u, &ws.bar[buf]);
+  bulk_g2s(ws.tbuf[buf], S.mtris + toff, tbytes, &ws.bar[buf]);
 }
 
-__device__ __forceinline__ void issue_cluster(WarpSmem& ws, int buf, const DScene& S, uint4 e) {
-  const int nv = e.z & 0xff, nt = (e.z >> 8) & 0xff;
-  const uint32_t tbytes = (uint32_t)((nt + 3) & ~3) * 4u;
-  mbar_expect_tx(&ws.bar[buf], nv * 16u + tbytes);
-  bulk_g2s(ws.vbuf[buf], S.mverts + e.x, nv * 16u, &ws.bar[buf]);
-  bulk_g2s(ws.tbuf[buf], S.mtris + e.y, tbytes, &ws.bar[buf]);
+__device__ __forceinline__ int pop_item(int* ctr, int lane) {
+  int i = 0;
+  if (lane == 0) i = atomicAdd(ctr, 1);
+  return __shfl_sync(kFull, i, 0);
 }
 
 template <bool kCount>
 __global__ void __launch_bounds__(kThreads, kRasterMinBlocks) raster_kernel(const RasterParams P) {
   extern __shared__ __align__(128) unsigned char smem[];
-  int* ctr = reinterpret_cast<int*>(smem);  // [0] env, [1] clusters, [2] objects
-  WarpSmem* wsm = reinterpret_cast<WarpSmem*>(smem + 128);
+  // [0] environment, [1] clusters listed, [2] clusters handed out, [3] objects handed out
+  int* ctr = reinterpret_cast<int*>(smem);
+  uint2* list = reinterpret_cast<uint2*>(smem + 128);
+  WarpSmem* wsm = reinterpret_cast<WarpSmem*>(smem + 128 + kListCap * sizeof(uint2));
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   WarpSmem& ws = wsm[warp];
   const int W = P.W, H = P.H, npix = W * H;
@@ -520,6 +488,8 @@ __global__ void __launch_bounds__(kThreads, kRasterMinBlocks) raster_kernel(cons
   vw.W = W;
   vw.H = H;
   vw.fb = P.fb_slots + (size_t)blockIdx.x * npix;
+  // the slot stays in L2 while observations stream through it
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(vw.pol));
   if (lane == 0) {
     mbar_init(&ws.bar[0]);
     mbar_init(&ws.bar[1]);
@@ -529,11 +499,7 @@ __global__ void __launch_bounds__(kThreads, kRasterMinBlocks) raster_kernel(cons
   bool dead = false;  // a wait gave up: this warp stops using its buffers
 
   for (;;) {
-    if (tid == 0) {
-      ctr[0] = atomicAdd(P.work, 1);
-      ctr[1] = 0;
-      ctr[2] = 0;
-    }
+    if (tid == 0) ctr[0] = atomicAdd(P.work, 1);
     __syncthreads();
     const int env = ctr[0];
     if (env >= P.n) break;
@@ -559,70 +525,103 @@ __global__ void __launch_bounds__(kThreads, kRasterMinBlocks) raster_kernel(cons
     vw.kt = rsqrtf(1.f + vw.tt * vw.tt);
     vw.kb = rsqrtf(1.f + vw.tb * vw.tb);
 
-    // clusters: each warp culls and draws on its own, staging the next
-    // survivor while it draws the current one
-    ClusterQueue q;
-    q.mask = 0;
-    q.mine = make_uint4(0u, 0u, 0u, 0u);
-    uint4 cur;
-    bool have = !dead && pop_cluster<kCount>(q, &ctr[1], S, cm, vw, lane, cur, cn);
-    int buf = 0;
-    if (have && lane == 0) issue_cluster(ws, 0, S, cur);
-    while (have) {
-      uint4 nxt;
-      const bool more = pop_cluster<kCount>(q, &ctr[1], S, cm, vw, lane, nxt, cn);
-      if (more && lane == 0) issue_cluster(ws, buf ^ 1, S, nxt);
-      const bool ok = mbar_wait(&ws.bar[buf], phase[buf],
-                                (kCount && lane == 0) ? &cn.v[kCntWaitIters] : nullptr);
-      phase[buf] ^= 1u;
-      if (!__all_sync(kFull, ok)) {
-        if (lane == 0) atomicOr(P.err, kErrWaitTimeout);
-        // let the copy in flight into the other buffer land before leaving
-        if (more) mbar_wait(&ws.bar[buf ^ 1], phase[buf ^ 1]);
-        dead = true;
-        break;
+    for (int base = 0; base < S.n_meshlets || base == 0; base += kListCap) {
+      if (tid == 0) {
+        ctr[1] = 0;
+        ctr[2] = 0;
+        ctr[3] = 0;
       }
-      raster_cluster<kCount>(vw, cm, ws, buf, cur.z & 0xff, (cur.z >> 8) & 0xff, cur.y,
-                             P.big_px, lane, cn);
-      cur = nxt;
-      have = more;
-      buf ^= 1;
-    }
-    // free objects: icosahedra scaled to each object's radius, handed out to
-    // warps as they finish their clusters
-    while (!dead) {
-      int j = 0;
-      if (lane == 0) j = atomicAdd(&ctr[2], 1);
-      j = __shfl_sync(kFull, j, 0);
-      if (j >= P.M) break;
-      const float4 o = P.obj[(size_t)env * P.M + j];
-      if (!sphere_visible(cm, vw, o.x, o.y, o.z, o.w * 1.0001f + 1e-6f)) continue;
-      for (int k = lane; k < P.omesh_nv; k += 32) {
-        const float4 u = P.omesh_v[k];
-        ws.vbuf[0][k] = make_float4(fmaf(o.w, u.x, o.x), fmaf(o.w, u.y, o.y), fmaf(o.w, u.z, o.z), 0.f);
+      __syncthreads();
+      // 1. the whole CTA culls the clusters of this pass into the list
+      const int end = min(base + kListCap, S.n_meshlets);
+      for (int m = base + tid; m < end; m += kThreads) {
+        if (kCount) cn.v[kCntClustersTested]++;
+        const float4 h0 = __ldg(S.mhdr + 3 * m);
+        bool vis = sphere_visible(cm, vw, h0.x, h0.y, h0.z, h0.w);
+        if (vis) {
+          const float4 h1 = __ldg(S.mhdr + 3 * m + 1), h2 = __ldg(S.mhdr + 3 * m + 2);
+          if (h2.x > -0.5f) {  // normal cone: every face looks away from the eye
+            const float vx = h0.x - cm.ex, vy = h0.y - cm.ey, vz = h0.z - cm.ez;
+            const float av = h1.x * vx + h1.y * vy + h1.z * vz;
+            const float cx_ = h1.y * vz - h1.z * vy, cy_ = h1.z * vx - h1.x * vz,
+                        cz_ = h1.x * vy - h1.y * vx;
+            const float cr = sqrtf(cx_ * cx_ + cy_ * cy_ + cz_ * cz_);
+            if (av * h2.x - cr * h1.w > h0.w * 1.001f + 1e-4f) vis = false;
+          }
+          if (vis) {
+            const uint32_t cnt = __float_as_uint(h2.w);
+            list[atomicAdd(&ctr[1], 1)] =
+                make_uint2(__float_as_uint(h2.y) | ((cnt & 0xffu) << 24),
+                           __float_as_uint(h2.z) | (((cnt >> 8) & 0xffu) << 24));
+          }
+        }
       }
-      for (int k = lane; k < P.omesh_nt; k += 32) ws.tbuf[0][k] = P.omesh_t[k];
-      __syncwarp();
-      raster_cluster<kCount>(vw, cm, ws, 0, P.omesh_nv, P.omesh_nt,
-                             (uint32_t)S.n_tris + (uint32_t)(j * P.omesh_nt), P.big_px, lane, cn);
+      __syncthreads();
+      const int count = ctr[1];
+      // 2. warps take one cluster at a time; the next streams in meanwhile
+      int cur = dead ? count : pop_item(&ctr[2], lane);
+      int buf = 0;
+      if (cur < count && lane == 0) issue_cluster(ws, 0, S, list[cur]);
+      while (cur < count) {
+        const int nxt = pop_item(&ctr[2], lane);
+        if (nxt < count && lane == 0) issue_cluster(ws, buf ^ 1, S, list[nxt]);
+        const bool ok = mbar_wait(&ws.bar[buf], phase[buf],
+                                  (kCount && lane == 0) ? &cn.v[kCntWaitIters] : nullptr);
+        phase[buf] ^= 1u;
+        if (!__all_sync(kFull, ok)) {
+          if (lane == 0) atomicOr(P.err, kErrWaitTimeout);
+          // let the copy in flight into the other buffer land before leaving
+          if (nxt < count) mbar_wait(&ws.bar[buf ^ 1], phase[buf ^ 1]);
+          dead = true;
+          break;
+        }
+        const uint2 e = list[cur];
+        raster_cluster<kCount>(vw, cm, ws, buf, (int)(e.x >> 24), (int)(e.y >> 24),
+                               e.y & 0xffffffu, P.big_px, lane, cn);
+        cur = nxt;
+        buf ^= 1;
+      }
+      // 3. free objects (last pass): icosahedra scaled to each object's radius
+      if (base + kListCap >= S.n_meshlets) {
+        while (!dead) {
+          const int j = pop_item(&ctr[3], lane);
+          if (j >= P.M) break;
+          const float4 o = P.obj[(size_t)env * P.M + j];
+          if (!sphere_visible(cm, vw, o.x, o.y, o.z, o.w * 1.0001f + 1e-6f)) continue;
+          for (int k = lane; k < P.omesh_nv; k += 32) {
+            const float4 u = P.omesh_v[k];
+            ws.vbuf[0][k] = make_float4(fmaf(o.w, u.x, o.x), fmaf(o.w, u.y, o.y),
+                                        fmaf(o.w, u.z, o.z), 0.f);
+          }
+          for (int k = lane; k < P.omesh_nt; k += 32) ws.tbuf[0][k] = P.omesh_t[k];
+          __syncwarp();
+          raster_cluster<kCount>(vw, cm, ws, 0, P.omesh_nv, P.omesh_nt,
+                                 (uint32_t)S.n_tris + (uint32_t)(j * P.omesh_nt), P.big_px, lane,
+                                 cn);
+        }
+        // object vertices were written to vbuf[0] by ordinary stores: order
+        // them before later bulk copies into the same buffer
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      }
+      __syncthreads();  // the list is reused by the next pass
     }
-    // object vertices were written to vbuf[0] by ordinary stores: order them
-    // before the next environment's bulk copies into the same buffer
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     // the reductions must land before the resolve reads the slot
     __threadfence();
     __syncthreads();
 
-    // resolve four pixels per thread: 16-byte stores, row-major; the slot is
-    // reset for this CTA's next environment
+    // resolve four pixels per thread: 16-byte streaming stores, row-major; the
+    // slot is read from L2 and reset for this CTA's next environment
     const size_t out0 = (size_t)env * npix;
     for (int p = tid * 4; p < npix; p += kThreads * 4) {
-      // L2 reads/writes (.cg): the reductions were applied in L2
-      const ulonglong2 k01 = __ldcg(reinterpret_cast<const ulonglong2*>(vw.fb + p));
-      const ulonglong2 k23 = __ldcg(reinterpret_cast<const ulonglong2*>(vw.fb + p + 2));
-      __stcg(reinterpret_cast<ulonglong2*>(vw.fb + p), make_ulonglong2(~0ull, ~0ull));
-      __stcg(reinterpret_cast<ulonglong2*>(vw.fb + p + 2), make_ulonglong2(~0ull, ~0ull));
-      const unsigned long long keys[4] = {k01.x, k01.y, k23.x, k23.y};
+      unsigned long long keys[4];
+      asm volatile("ld.global.cg.L2::cache_hint.v2.u64 {%0, %1}, [%2], %3;"
+                   : "=l"(keys[0]), "=l"(keys[1]) : "l"(vw.fb + p), "l"(vw.pol));
+      asm volatile("ld.global.cg.L2::cache_hint.v2.u64 {%0, %1}, [%2], %3;"
+                   : "=l"(keys[2]), "=l"(keys[3]) : "l"(vw.fb + p + 2), "l"(vw.pol));
+      asm volatile("st.global.cg.L2::cache_hint.v2.u64 [%0], {%1, %1}, %2;"
+                   :: "l"(vw.fb + p), "l"(~0ull), "l"(vw.pol) : "memory");
+      asm volatile("st.global.cg.L2::cache_hint.v2.u64 [%0], {%1, %1}, %2;"
+                   :: "l"(vw.fb + p + 2), "l"(~0ull), "l"(vw.pol) : "memory");
       float z[4];
       uint32_t col[4];
 #pragma unroll
@@ -642,10 +641,10 @@ __global__ void __launch_bounds__(kThreads, kRasterMinBlocks) raster_kernel(cons
         uint2 v;
         v.x = *reinterpret_cast<uint32_t*>(&a);
         v.y = *reinterpret_cast<uint32_t*>(&b);
-        *reinterpret_cast<uint2*>(reinterpret_cast<__half*>(P.depth) + out0 + p) = v;
+        __stcs(reinterpret_cast<uint2*>(reinterpret_cast<__half*>(P.depth) + out0 + p), v);
       } else {
-        *reinterpret_cast<float4*>(reinterpret_cast<float*>(P.depth) + out0 + p) =
-            make_float4(z[0], z[1], z[2], z[3]);
+        __stcs(reinterpret_cast<float4*>(reinterpret_cast<float*>(P.depth) + out0 + p),
+               make_float4(z[0], z[1], z[2], z[3]));
       }
       if (P.rgb) {
         // 4 pixels = 12 bytes R G B R G B ... packed into three words
@@ -656,10 +655,10 @@ __global__ void __launch_bounds__(kThreads, kRasterMinBlocks) raster_kernel(cons
                             (((r2 >> 8) & 0xff) << 24);
         const uint32_t w2 = (r2 & 0xff) | (((r3 >> 16) & 0xff) << 8) | (((r3 >> 8) & 0xff) << 16) |
                             ((r3 & 0xff) << 24);
-        uint32_t* o = reinterpret_cast<uint32_t*>(P.rgb + (out0 + p) * 3);
-        o[0] = w0;
-        o[1] = w1;
-        o[2] = w2;
+        unsigned int* o = reinterpret_cast<unsigned int*>(P.rgb + (out0 + p) * 3);
+        __stcs(o, w0);
+        __stcs(o + 1, w1);
+        __stcs(o + 2, w2);
       }
     }
     __syncthreads();
@@ -676,7 +675,7 @@ __global__ void __launch_bounds__(kThreads, kRasterMinBlocks) raster_kernel(cons
 
 }  // namespace
 
-size_t raster_smem_bytes() { return 128 + kWarps * sizeof(WarpSmem); }
+size_t raster_smem_bytes() { return 128 + kListCap * sizeof(uint2) + kWarps * sizeof(WarpSmem); }
 
 cudaError_t raster_configure(int* slots) {
   const int bytes = (int)raster_smem_bytes();
