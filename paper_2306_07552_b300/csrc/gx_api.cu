@@ -356,6 +356,7 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
   };
   cudaError_t e;
   if ((e = raster_configure(&x->n_slots)) != cudaSuccess) return bail(e, "raster config");
+  if ((e = reset_configure()) != cudaSuccess) return bail(e, "reset config");
   if (x->n_slots > x->n) x->n_slots = x->n;
   {
     // one framebuffer slot per resident rasteriser CTA, all keys "empty"

@@ -142,6 +142,7 @@ enum RasterCounter {
 
 void launch_physics(const PhysicsParams& p, cudaStream_t s);
 void launch_reset(const ResetParams& p, cudaStream_t s);
+cudaError_t reset_configure();
 void launch_raster(const RasterParams& p, cudaStream_t s);
 // Read-only view of a scene set's device data, for entry points outside
 // gx_api.cu.

@@ -75,19 +75,21 @@ __device__ bool grid_query(const DScene& s, float cx, float cy, float cz, float&
 }
 
 // Right-multiplies the row-major rotation R by a rotation of `axis` by the
-// angle with sine s, cosine c (columns mix pairwise).
+// angle with sine s, cosine c (columns mix pairwise).  Each case names its
+// columns at compile time so R stays in registers.
 __device__ __forceinline__ void rmul_axis(float R[9], int axis, float s, float c) {
-  const int a = axis == 0 ? 1 : 0;  // the two columns that mix
-  const int b = axis == 2 ? 1 : 2;
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
-    const float ca = R[3 * r + a], cb = R[3 * r + b];
-    if (axis == 1) {  // Ry: col0' = c col0 - s col2, col2' = s col0 + c col2
-      R[3 * r + a] = c * ca - s * cb;
-      R[3 * r + b] = s * ca + c * cb;
-    } else {          // Rx (cols 1,2), Rz (cols 0,1): colA' = c A + s B, colB' = -s A + c B
-      R[3 * r + a] = c * ca + s * cb;
-      R[3 * r + b] = -s * ca + c * cb;
+    const float c0 = R[3 * r], c1 = R[3 * r + 1], c2 = R[3 * r + 2];
+    if (axis == 0) {         // Rx: col1' = c col1 + s col2, col2' = -s col1 + c col2
+      R[3 * r + 1] = c * c1 + s * c2;
+      R[3 * r + 2] = -s * c1 + c * c2;
+    } else if (axis == 1) {  // Ry: col0' = c col0 - s col2, col2' = s col0 + c col2
+      R[3 * r + 0] = c * c0 - s * c2;
+      R[3 * r + 2] = s * c0 + c * c2;
+    } else {                 // Rz: col0' = c col0 + s col1, col1' = -s col0 + c col1
+      R[3 * r + 0] = c * c0 + s * c1;
+      R[3 * r + 1] = -s * c0 + c * c1;
     }
   }
 }
@@ -415,92 +417,174 @@ __global__ void __launch_bounds__(32 * kEnvsPerBlock) physics_kernel(const Physi
   }
 }
 
-// (a12) masked reset: objects on support tops, then the robot base in free
-// space, by rejection sampling with at most 64 Philox draws each.  Lane t
-// evaluates try t (two passes of 32); the lowest accepted try wins, which is
-// the same choice as trying them in order.
-__global__ void __launch_bounds__(32 * kEnvsPerBlock) reset_kernel(const ResetParams P) {
-  __shared__ float4 s_obj[kEnvsPerBlock][GX_MAX_OBJECTS];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int env = blockIdx.x * kEnvsPerBlock + w;
-  if (env >= P.n) return;
+// Candidate placement of object j at try t (the same Philox draws the
+// sequential definition uses): support by the top 24 bits, uniform on the
+// support top shrunk by the radius, resting 1 clearance above it.
+__device__ __forceinline__ float3 object_candidate(const DScene& S, uint4 wv, float rho,
+                                                   float clear) {
+  const uint32_t si = (uint32_t)(((uint64_t)(wv.x >> 8) * (uint64_t)S.n_supports) >> 24);
+  const float* sp = S.supports + 5 * si;
+  const float x0 = sp[0] + rho, x1 = sp[2] - rho, z0 = sp[1] + rho, z1 = sp[3] - rho;
+  return make_float3(x0 + unit24(wv.y) * (x1 - x0), sp[4] + rho + clear, z0 + unit24(wv.z) * (z1 - z0));
+}
+
+__device__ __forceinline__ void robot_try(const DScene& S, uint4 wv, float& x, float& z,
+                                          float& yaw) {
+  x = S.spawn[0] + unit24(wv.x) * (S.spawn[2] - S.spawn[0]);
+  z = S.spawn[1] + unit24(wv.y) * (S.spawn[3] - S.spawn[1]);
+  yaw = -CUDART_PI_F + unit24(wv.z) * (2.f * CUDART_PI_F);
+}
+
+// World centre of robot sphere i with the base at (x, z, yaw) and joints q:
+// the FK chain walked up to the sphere's link.
+__device__ void sphere_world(const gx_robot& rb, int i, float x, float z, float yaw,
+                             const float q[7], float out[3]) {
+  float sn, cs;
+  sincosf(yaw, &sn, &cs);
+  float R[9] = {cs, 0.f, sn, 0.f, 1.f, 0.f, -sn, 0.f, cs};
+  float t[3] = {x, 0.f, z};
+  const int link = rb.sphere_link[i];
+  for (int k = 0; k < link; ++k) {
+    float nt[3];
+    apply(R, t, rb.link_offset[k][0], rb.link_offset[k][1], rb.link_offset[k][2], nt);
+    t[0] = nt[0]; t[1] = nt[1]; t[2] = nt[2];
+    float sk, ck;
+    sincosf(q[k], &sk, &ck);
+    rmul_axis(R, rb.link_axis[k], sk, ck);
+  }
+  apply(R, t, rb.sphere_pos[i][0], rb.sphere_pos[i][1], rb.sphere_pos[i][2], out);
+}
+
+constexpr int kResetThreads = 256;
+constexpr int kTryWindow = 8;  // tries evaluated together before looking further
+
+// (a12) masked reset, one CTA per environment: objects on support tops, then
+// the robot base in free space, by rejection sampling with at most 64
+// Philox draws each; the lowest accepted try wins, the same choice as trying
+// them in order.  Tries are evaluated in windows of 8 so that the scene-grid
+// gathers of a window are in flight together (random gathers into a
+// multi-gigabyte grid have long latency, and a reset is latency-bound):
+//   1. the static-scene test of tries 0..7 of every object, all at once;
+//   2. objects in order (one warp): the first try that passed step 1 and
+//      clears the objects already placed; when all 8 fail, the warp tests
+//      the following tries itself, 32 at a time;
+//   3. every (robot try, sphere) pair of a window at once; the first window
+//      with a contact-free try decides.
+__global__ void __launch_bounds__(kResetThreads) reset_kernel(const ResetParams P) {
+  __shared__ float4 s_cand[GX_MAX_OBJECTS][kTryWindow];  // x, y, z, static test passed
+  __shared__ float4 so[GX_MAX_OBJECTS];
+  __shared__ float s_rho[GX_MAX_OBJECTS];
+  __shared__ unsigned s_bad;
+  __shared__ int s_robot_try;
+  const int env = blockIdx.x;
   if (P.mask && !P.mask[env]) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = P.n, M = P.M;
   const DScene& S = P.scenes[P.env_scene[env]];
   const gx_robot& rb = P.robot->r;
-  float4* so = s_obj[w];
   const uint32_t ep = (uint32_t)P.st.episode[env] + 1u;
   const uint2 key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
   const float clear = rb.rest_clearance;
+  // 1. radii (from each object's try 0) and the first window's static tests
+  for (int jt = tid; jt < M * kTryWindow; jt += kResetThreads) {
+    const int j = jt / kTryWindow, t = jt % kTryWindow;
+    const uint4 w0 = philox4x32_10(make_uint4((uint32_t)env, ep, (uint32_t)j, 0u), key);
+    const float rho = P.rho_min + unit24(w0.w) * (P.rho_max - P.rho_min);
+    if (t == 0) s_rho[j] = rho;
+    const uint4 wv = t == 0 ? w0 : philox4x32_10(make_uint4((uint32_t)env, ep, (uint32_t)j, (uint32_t)t), key);
+    const float3 p = object_candidate(S, wv, rho, clear);
+    float d;
+    const bool ok = grid_query(S, p.x, p.y, p.z, d) && !(d < rho);
+    s_cand[j][t] = make_float4(p.x, p.y, p.z, ok ? 1.f : 0.f);
+  }
+  if (tid == 0) s_robot_try = -1;
+  __syncthreads();
+  // 2. objects in order
   bool failed = false;
-  for (int j = 0; j < M; ++j) {
-    float rho = 0.f;
-    float4 pick = make_float4(0.f, 0.f, 0.f, 0.f);
-    bool placed = false;
-    for (int tb = 0; tb < 64 && !placed; tb += 32) {
-      const uint4 wv = philox4x32_10(make_uint4((uint32_t)env, ep, (uint32_t)j, (uint32_t)(tb + lane)), key);
-      if (tb == 0) rho = __shfl_sync(kFull, P.rho_min + unit24(wv.w) * (P.rho_max - P.rho_min), 0);
-      const uint32_t si = (uint32_t)(((uint64_t)(wv.x >> 8) * (uint64_t)S.n_supports) >> 24);
-      const float* sp = S.supports + 5 * si;
-      const float x0 = sp[0] + rho, x1 = sp[2] - rho, z0 = sp[1] + rho, z1 = sp[3] - rho;
-      const float px = x0 + unit24(wv.y) * (x1 - x0);
-      const float py = sp[4] + rho + clear;
-      const float pz = z0 + unit24(wv.z) * (z1 - z0);
-      float d;
-      bool ok = grid_query(S, px, py, pz, d) && !(d < rho);
+  if (warp == 0) {
+    for (int j = 0; j < M; ++j) {
+      const float rho = s_rho[j];
+      float4 c = lane < kTryWindow ? s_cand[j][lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+      bool ok = c.w > 0.5f;
       for (int k = 0; k < j && ok; ++k) {
         const float4 o = so[k];
-        const float dx = px - o.x, dy = py - o.y, dz = pz - o.z, rr = rho + o.w;
+        const float dx = c.x - o.x, dy = c.y - o.y, dz = c.z - o.z, rr = rho + o.w;
         ok = !(dx * dx + dy * dy + dz * dz < rr * rr);
       }
-      const unsigned b = __ballot_sync(kFull, ok);
-      const int L = b ? __ffs(b) - 1 : 31;
-      pick = make_float4(__shfl_sync(kFull, px, L), __shfl_sync(kFull, py, L),
-                         __shfl_sync(kFull, pz, L), rho);
-      placed = b != 0;
+      unsigned b = __ballot_sync(kFull, ok);
+      int L = b ? __ffs(b) - 1 : -1;
+      float4 pick = make_float4(__shfl_sync(kFull, c.x, L < 0 ? 0 : L),
+                                __shfl_sync(kFull, c.y, L < 0 ? 0 : L),
+                                __shfl_sync(kFull, c.z, L < 0 ? 0 : L), rho);
+      for (int tb = kTryWindow; tb < 64 && L < 0; tb += 32) {
+        const int t = tb + lane;
+        float3 p = make_float3(0.f, 0.f, 0.f);
+        bool ok2 = false;
+        if (t < 64) {
+          const uint4 wv = philox4x32_10(make_uint4((uint32_t)env, ep, (uint32_t)j, (uint32_t)t), key);
+          p = object_candidate(S, wv, rho, clear);
+          float d;
+          ok2 = grid_query(S, p.x, p.y, p.z, d) && !(d < rho);
+          for (int k = 0; k < j && ok2; ++k) {
+            const float4 o = so[k];
+            const float dx = p.x - o.x, dy = p.y - o.y, dz = p.z - o.z, rr = rho + o.w;
+            ok2 = !(dx * dx + dy * dy + dz * dz < rr * rr);
+          }
+        }
+        b = __ballot_sync(kFull, ok2);
+        // the last try (63) stands when every try failed
+        const int last = 63 - tb;
+        L = b ? __ffs(b) - 1 : -1;
+        const int src = L >= 0 ? L : (last < 32 ? last : 31);
+        pick = make_float4(__shfl_sync(kFull, p.x, src), __shfl_sync(kFull, p.y, src),
+                           __shfl_sync(kFull, p.z, src), rho);
+      }
+      failed |= L < 0;
+      if (lane == 0) so[j] = pick;
+      __syncwarp();
     }
-    failed |= !placed;
-    __syncwarp();
-    if (lane == 0) so[j] = pick;
-    __syncwarp();
   }
-  // robot base: every lane evaluates one try of the spawn rectangle
+  __syncthreads();
+  // 3. robot base, a window of tries at a time
   float q[7];
 #pragma unroll
   for (int k = 0; k < 7; ++k) q[k] = rb.q_rest[k];
-  float bx = 0.f, bz = 0.f, byaw = 0.f;
-  bool placed = false;
-  for (int tb = 0; tb < 64 && !placed; tb += 32) {
-    const uint4 wv = philox4x32_10(make_uint4((uint32_t)env, ep, 64u, (uint32_t)(tb + lane)), key);
-    const float x = S.spawn[0] + unit24(wv.x) * (S.spawn[2] - S.spawn[0]);
-    const float z = S.spawn[1] + unit24(wv.y) * (S.spawn[3] - S.spawn[1]);
-    const float yaw = -CUDART_PI_F + unit24(wv.z) * (2.f * CUDART_PI_F);
-    bool ok = true;
-    for (int link = 0; link <= 7 && ok; ++link) {
-      float R[9], t[3], eR[9], et[3];
-      fk(rb, x, z, yaw, q, link, R, t, eR, et);
-      for (int i = 0; i < rb.n_spheres && ok; ++i) {
-        if (rb.sphere_link[i] != link) continue;
-        float c[3];
-        apply(R, t, rb.sphere_pos[i][0], rb.sphere_pos[i][1], rb.sphere_pos[i][2], c);
-        const float r = rb.sphere_radius[i];
-        float d;
-        ok = grid_query(S, c[0], c[1], c[2], d) && !(d < r);
-        for (int j = 0; j < M && ok; ++j) {
-          const float4 o = so[j];
-          const float dx = c[0] - o.x, dy = c[1] - o.y, dz = c[2] - o.z, rr = r + o.w;
-          ok = !(dx * dx + dy * dy + dz * dz < rr * rr);
-        }
+  const int ns = rb.n_spheres;
+  for (int t0 = 0; t0 < 64; t0 += kTryWindow) {
+    if (tid == 0) s_bad = 0u;
+    __syncthreads();
+    for (int p = tid; p < kTryWindow * ns; p += kResetThreads) {
+      const int tw = p / ns, i = p - tw * ns;
+      const uint4 wv = philox4x32_10(make_uint4((uint32_t)env, ep, 64u, (uint32_t)(t0 + tw)), key);
+      float x, z, yaw;
+      robot_try(S, wv, x, z, yaw);
+      float cc[3];
+      sphere_world(rb, i, x, z, yaw, q, cc);
+      const float r = rb.sphere_radius[i];
+      float d;
+      bool hit = !grid_query(S, cc[0], cc[1], cc[2], d) || d < r;
+      for (int j = 0; j < M && !hit; ++j) {
+        const float4 o = so[j];
+        const float dx = cc[0] - o.x, dy = cc[1] - o.y, dz = cc[2] - o.z, rr = r + o.w;
+        hit = dx * dx + dy * dy + dz * dz < rr * rr;
       }
+      if (hit) atomicOr(&s_bad, 1u << tw);
     }
-    const unsigned b = __ballot_sync(kFull, ok);
-    const int L = b ? __ffs(b) - 1 : 31;
-    bx = __shfl_sync(kFull, x, L);
-    bz = __shfl_sync(kFull, z, L);
-    byaw = __shfl_sync(kFull, yaw, L);
-    placed = b != 0;
+    __syncthreads();
+    const unsigned freew = ~s_bad & ((1u << kTryWindow) - 1u);
+    if (freew) {
+      if (tid == 0) s_robot_try = t0 + __ffs(freew) - 1;
+      break;
+    }
   }
-  failed |= !placed;
+  __syncthreads();
+  if (warp != 0) return;
+  int t = s_robot_try;
+  failed |= t < 0;
+  if (t < 0) t = 63;
+  const uint4 wv = philox4x32_10(make_uint4((uint32_t)env, ep, 64u, (uint32_t)t), key);
+  float bx, bz, byaw;
+  robot_try(S, wv, bx, bz, byaw);
   if (failed && lane == 0) atomicOr(P.err, GX_DEV_PLACEMENT_FAILED);
   if (lane == 0) {
     P.st.bx[env] = bx; P.st.bz[env] = bz; P.st.yaw[env] = byaw;
@@ -531,9 +615,10 @@ void launch_physics(const PhysicsParams& p, cudaStream_t s) {
   physics_kernel<<<blocks, 32 * kEnvsPerBlock, 0, s>>>(p);
 }
 
+cudaError_t reset_configure() { return cudaSuccess; }
+
 void launch_reset(const ResetParams& p, cudaStream_t s) {
-  const int blocks = (p.n + kEnvsPerBlock - 1) / kEnvsPerBlock;
-  reset_kernel<<<blocks, 32 * kEnvsPerBlock, 0, s>>>(p);
+  reset_kernel<<<p.n, kResetThreads, 0, s>>>(p);
 }
 
 }  // namespace gx
