@@ -139,6 +139,26 @@ def measured_peaks():
     return 6400.0, 2032.0, "fallback"
 
 
+def rank_seeds(w, rank):
+    """Reset and action seeds of one rank: every rank runs its own batch of
+    independent environments (weak scaling), so their streams must differ."""
+    return w.reset_seed + 7919 * rank, w.action_seed + rank
+
+
+def job_value(dist, n_envs, steps, ms_local):
+    """Whole-job env-steps/s: all ranks' environments over the slowest rank's
+    time (max over ranks)."""
+    import torch
+    world = dist.get_world_size() if dist else 1
+    ms = ms_local
+    if dist:
+        t = torch.tensor([ms_local], dtype=torch.float64,
+                         device="cuda" if dist.get_backend() == "nccl" else "cpu")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return world * n_envs * steps / (ms / 1e3), ms
+
+
 def reset_masks(n, period):
     masks = np.zeros((period, n), np.uint8)
     for t in range(period):
@@ -290,11 +310,11 @@ def main():
     ss = gx.SceneSet(scenes)
     sim = gx.Sim(ss, I.fetch_like_robot(), n, img=(w.img, w.img), depth_fp16=w.depth_fp16,
                  render_rgb=w.rgb, n_objects=w.n_objects, obj_radius=w.obj_radius,
-                 seed=w.reset_seed + 7919 * rank, profile=0 if args.graph else 1,
+                 seed=rank_seeds(w, rank)[0], profile=0 if args.graph else 1,
                  use_graph=args.graph, small_tri_px=args.small_px)
     total = args.warmup + args.steps
     acts = torch.from_numpy(I.make_actions(total, n, w.action_dist,
-                                           seed=w.action_seed + rank)).cuda()
+                                           seed=rank_seeds(w, rank)[1])).cuda()
     if w.reset_every:
         masks = torch.from_numpy(reset_masks(n, w.reset_every)).cuda()
         mask_at = lambda t: masks[t % w.reset_every]  # noqa: E731
@@ -339,11 +359,7 @@ def main():
     ms = e0.elapsed_time(e1)
     phase_ms, phase_n = sim.phase_times() if not args.graph else ([0, 0, 0], [0, 0, 0])
     dev_err = sim.device_error()
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * n * args.steps / (ms / 1e3)
+    value, ms = job_value(dist, n, args.steps, ms)
 
     # end to end through the C ABI with host buffers (pinned): actions in,
     # every output back (images included), copies inside the timed region
@@ -355,13 +371,9 @@ def main():
     for t in range(ne):
         acts_h.numpy()[:] = acts_np[t]
         sim.step_host(acts_h, host, stream=stream)
-    e2e_dt = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_dt], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_dt = float(t.item())
+    e2e_value, _ = job_value(dist, n, ne, (time.perf_counter() - t0) * 1e3)
     d2h = sum(v.numel() * v.element_size() for v in host.values() if v is not None)
-    e2e = {"value": world * n * ne / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": n * 11 * 4,
+    e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * 11 * 4,
            "d2h_bytes_per_step": int(d2h), "steps": ne,
            "note": "gx_step_host: pinned actions in, every output (images included) back"}
     counters = None
