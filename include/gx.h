@@ -218,6 +218,35 @@ gx_status gx_phase_times(gx_ctx* ctx, double ms[3], int64_t launches[3]);
  * GX_ESTATE when the context does not count. */
 gx_status gx_raster_counters(gx_ctx* ctx, int64_t* out, int32_t n);
 
+/* ----------------------------------------------------------------------------
+ * Neural SDF (not in the paper; the learned stand-in for the distance grid).
+ * Per scene, a Fourier-feature MLP
+ *   d(x) = W5 relu(W4 relu(W3 relu(W2 relu(W1 g(x) + b1) + b2) + b3) + b4) + b5,
+ *   g(x) = [sin(2 pi B (x - c)), cos(2 pi B (x - c))],
+ * B [32][3], c the centre of the scene's grid box, hidden width 128.  W1..W4
+ * are stored and multiplied in BF16 on the tensor cores with FP32
+ * accumulation; features and hidden activations are rounded to BF16 where
+ * they enter a product; biases, W5 and b5 are FP32.
+ * params layout (GX_NSDF_PARAMS floats): W1 [128][64], b1 [128], W2 [128][128],
+ * b2, W3, b3, W4, b4, W5 [128], b5 [1] (row-major, rows = outputs).
+ * Setting or training weights mutates the scene set: do it while no context
+ * using the set is stepping. */
+#define GX_NSDF_PARAMS 57985
+
+/* Loads weights (host FP32; W1..W4 are rounded to BF16) for one scene.
+ * Allocates the scene's device copy on first use. */
+gx_status gx_nsdf_set_weights(gx_scene_set* set, int32_t scene, const float* fourier_B,
+                              const float* params);
+/* The weights as the kernels use them (BF16 values widened to FP32), the
+ * Fourier matrix and the feature centre c (each output may be NULL except
+ * params).  GX_ESTATE when the scene has no neural SDF. */
+gx_status gx_nsdf_get_weights(const gx_scene_set* set, int32_t scene, float* fourier_B,
+                              float* params, float* centre);
+/* d(x) for n points (device [n][3] world coordinates) into dist (device [n]).
+ * Asynchronous on `stream`. */
+gx_status gx_nsdf_query(const gx_scene_set* set, int32_t scene, const float* pts, int32_t n,
+                        float* dist, void* stream);
+
 /* Renders depth (and RGB when rgb != NULL) for n environments without
  * allocating any device memory.  The paper has no counterpart: this serves
  * callers that cannot call cudaMalloc when they need images -- code in a

@@ -108,6 +108,7 @@ def _declare(L):
     L.orc_render.argtypes = [P(Robot_c), P(Scene_c), P(ObjMesh_c), P(State_c), C.c_int32,
                              C.c_int32, C.c_double, C.c_double, C.c_double, f64p, u32p, u8p,
                              i32p, P(RenderStats_c)]
+    L.orc_mlp_set_bf16_operands.argtypes = [C.c_int]
     L.orc_mlp_forward.argtypes = [f64p, C.c_int, P(f64p), P(f64p), i32p, C.c_int, f64p, f64p]
     L.orc_mlp_forward.restype = C.c_double
     L.orc_mlp_loss_grad.argtypes = [f64p, C.c_int, P(f64p), P(f64p), i32p, C.c_int, f64p, f64p,
@@ -281,9 +282,11 @@ def box_sdf(p, box):
 
 
 class MLP64:
-    """FP64 Fourier-feature MLP used to check the neural-SDF kernels."""
+    """FP64 Fourier-feature MLP used to check the neural-SDF kernels.
+    bf16_operands=True rounds what the tensor cores consume to BF16."""
 
-    def __init__(self, B, Ws, bs):
+    def __init__(self, B, Ws, bs, bf16_operands=False):
+        self.bf16 = bool(bf16_operands)
         self.B = np.ascontiguousarray(B, np.float64)
         self.Ws = [np.ascontiguousarray(w, np.float64) for w in Ws]
         self.bs = [np.ascontiguousarray(b, np.float64) for b in bs]
@@ -296,6 +299,7 @@ class MLP64:
     def forward(self, X):
         X = np.ascontiguousarray(np.atleast_2d(X), np.float64)
         L = lib()
+        L.orc_mlp_set_bf16_operands(int(self.bf16))
         out = np.zeros(len(X))
         for i in range(len(X)):
             out[i] = L.orc_mlp_forward(_p(self.B, f64p), self.F, self._wp, self._bp,
@@ -309,6 +313,7 @@ class MLP64:
         gb = [np.zeros_like(b) for b in self.bs]
         gwp = (f64p * len(gW))(*[_p(w, f64p) for w in gW])
         gbp = (f64p * len(gb))(*[_p(b, f64p) for b in gb])
+        lib().orc_mlp_set_bf16_operands(int(self.bf16))
         loss = lib().orc_mlp_loss_grad(_p(self.B, f64p), self.F, self._wp, self._bp,
                                        _p(self.dims, i32p), len(self.Ws), _p(X, f64p),
                                        _p(y, f64p), len(X), lo, hi, gwp, gbp)

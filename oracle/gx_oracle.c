@@ -636,13 +636,29 @@ void orc_render(const orc_robot* rb, const orc_scene* sc, const orc_objmesh* om,
 /* Fourier features gamma(x) = [sin(2 pi B x), cos(2 pi B x)].              */
 /* dims = {2F, h1, ..., 1}; W[l] is row-major [dims[l+1]][dims[l]].         */
 /* ------------------------------------------------------------------------ */
+/* Optional rounding of every GEMM operand the tensor-core kernels feed in
+ * BF16 (features, hidden activations, back-propagated gradients), to the
+ * nearest BF16 (ties to even) through float; the arithmetic stays FP64. */
+static int g_mlp_bf16 = 0;
+void orc_mlp_set_bf16_operands(int on) { g_mlp_bf16 = on; }
+static double bf16r(double x) {
+  if (!g_mlp_bf16) return x;
+  float f = (float)x;
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  if ((u & 0x7f800000u) != 0x7f800000u) u += 0x7fffu + ((u >> 16) & 1u);
+  u &= 0xffff0000u;
+  memcpy(&f, &u, 4);
+  return (double)f;
+}
+
 static void mlp_acts(const double* B, int F, const double* const* W, const double* const* b,
                      const int* dims, int L, const double x[3], double* A) {
   /* A holds layer inputs back to back: a_0 (2F), a_1, ..., a_L (1) */
   for (int k = 0; k < F; ++k) {
     double ph = 2 * PI * (B[3 * k] * x[0] + B[3 * k + 1] * x[1] + B[3 * k + 2] * x[2]);
-    A[k] = sin(ph);
-    A[F + k] = cos(ph);
+    A[k] = bf16r(sin(ph));
+    A[F + k] = bf16r(cos(ph));
   }
   double* in = A;
   for (int l = 0; l < L; ++l) {
@@ -651,6 +667,7 @@ static void mlp_acts(const double* B, int F, const double* const* W, const doubl
       double s = b[l][r];
       for (int c = 0; c < dims[l]; ++c) s += W[l][(size_t)r * dims[l] + c] * in[c];
       o[r] = (l < L - 1 && s < 0) ? 0.0 : s;
+      if (l < L - 1) o[r] = bf16r(o[r]);
     }
     in = o;
   }
@@ -696,8 +713,7 @@ double orc_mlp_loss_grad(const double* B, int F, const double* const* W, const d
       const double* outv = A + off[l + 1];
       /* g is dLoss/d(pre-activation of layer l) once the ReLU mask is applied */
       if (l < L - 1)
-        for (int r = 0; r < dims[l + 1]; ++r)
-          if (!(outv[r] > 0)) g[r] = 0.0;
+        for (int r = 0; r < dims[l + 1]; ++r) g[r] = (outv[r] > 0) ? bf16r(g[r]) : 0.0;
       for (int r = 0; r < dims[l + 1]; ++r) {
         gb[l][r] += g[r];
         for (int c = 0; c < dims[l]; ++c) gW[l][(size_t)r * dims[l] + c] += g[r] * in[c];

@@ -110,7 +110,11 @@ void orc_render(const orc_robot* rb, const orc_scene* sc, const orc_objmesh* om,
                 double cos_min, double* depth, uint32_t* rgb, uint8_t* ambiguous,
                 int32_t* winner, orc_render_stats* stats);
 
-/* Neural SDF (Fourier-feature MLP) in FP64: forward and backward. */
+/* Neural SDF (Fourier-feature MLP) in FP64: forward and backward.  With
+ * orc_mlp_set_bf16_operands(1) every value fed to a BF16 matrix product
+ * (features, hidden activations, hidden-layer gradients) is rounded to the
+ * nearest BF16 first, as the tensor-core kernels do; sums stay FP64. */
+void orc_mlp_set_bf16_operands(int on);
 double orc_mlp_forward(const double* B /*[F][3]*/, int F, const double* const* W,
                        const double* const* b, const int* dims, int n_layers, const double x[3],
                        double* acts /* optional scratch: sum(dims) */);

@@ -20,17 +20,6 @@ struct DevBuf {
 
 }  // namespace
 
-struct gx_scene_set {
-  int n = 0;
-  std::vector<DScene> host;
-  DScene* d_scenes = nullptr;
-  std::vector<void*> allocs;
-  float4* omesh_v = nullptr;
-  uint32_t* omesh_t = nullptr;
-  uint32_t* obj_rgb = nullptr;
-  int omesh_nv = 0, omesh_nt = 0;
-  std::vector<int> meshlets_per_scene;
-};
 
 struct gx_ctx {
   const gx_scene_set* set = nullptr;
@@ -103,6 +92,7 @@ cudaError_t upload(gx_scene_set* s, T** dst, const T* src, size_t count) {
 void free_set(gx_scene_set* s) {
   if (!s) return;
   for (void* p : s->allocs) cudaFree(p);
+  nsdf_free(s);
   delete s;
 }
 

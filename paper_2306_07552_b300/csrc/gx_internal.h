@@ -144,6 +144,52 @@ void launch_physics(const PhysicsParams& p, cudaStream_t s);
 void launch_reset(const ResetParams& p, cudaStream_t s);
 cudaError_t reset_configure();
 void launch_raster(const RasterParams& p, cudaStream_t s);
+// ---------------------------------------------------------------------------
+// Neural SDF of one scene (Fourier-feature MLP 64 -> 128 x4 -> 1).
+// ---------------------------------------------------------------------------
+constexpr int kNsdfFreq = 32;    // Fourier frequencies (64 features)
+constexpr int kNsdfWidth = 128;  // hidden width
+constexpr int kNsdfParams = 128 * 64 + 128 + 3 * (128 * 128 + 128) + 128 + 1;  // 57,985
+// Device blob read by the kernels: BF16 weight images laid out exactly as
+// the tensor cores read them from shared memory (K-major, 128-byte swizzle),
+// then FP32 biases, the FP32 output row and the Fourier matrix.
+constexpr int kNsdfW1Bytes = 128 * 64 * 2;    // 16 KB
+constexpr int kNsdfWhBytes = 128 * 128 * 2;   // 32 KB each for layers 2..4
+constexpr int kNsdfImgBytes = kNsdfW1Bytes + 3 * kNsdfWhBytes;  // 112 KB
+struct NsdfTail {            // follows the weight images in the blob
+  float b[4][128];           // hidden biases
+  float w5[128];             // output row
+  float b5;
+  float centre[3];           // features use x - centre
+  float B[kNsdfFreq][3];     // Fourier matrix
+  float pad[4];
+};
+constexpr int kNsdfBlobBytes = kNsdfImgBytes + (int)sizeof(NsdfTail);
+struct NsdfScene {
+  unsigned char* blob = nullptr;  // device, kNsdfBlobBytes
+  float* master = nullptr;        // device FP32 parameters (kNsdfParams), training only
+  bool ready = false;
+};
+
+}  // namespace gx
+
+struct gx_scene_set {
+  int n = 0;
+  std::vector<gx::DScene> host;
+  gx::DScene* d_scenes = nullptr;
+  std::vector<void*> allocs;
+  float4* omesh_v = nullptr;
+  uint32_t* omesh_t = nullptr;
+  uint32_t* obj_rgb = nullptr;
+  int omesh_nv = 0, omesh_nt = 0;
+  std::vector<int> meshlets_per_scene;
+  std::vector<gx::NsdfScene> nsdf;
+};
+
+namespace gx {
+
+void nsdf_free(gx_scene_set* s);
+
 // Read-only view of a scene set's device data, for entry points outside
 // gx_api.cu.
 struct SceneSetView {

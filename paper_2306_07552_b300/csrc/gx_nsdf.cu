@@ -1,0 +1,420 @@
+// Neural SDF: a per-scene Fourier-feature MLP that stands in for the static
+// distance grid (not in the paper; the workload's learned part).
+//
+//   d(x) = W5 relu(W4 relu(W3 relu(W2 relu(W1 g(x) + b1) + b2) + b3) + b4) + b5
+//   g(x) = [sin(2 pi B (x - c)), cos(2 pi B (x - c))],  B in R^{32x3}
+//
+// W1..W4 are BF16 and every hidden product runs on the 5th-generation tensor
+// cores (tcgen05.mma, kind::f16, FP32 accumulation in tensor memory); the
+// 128 -> 1 output row and the biases are FP32.  Features and hidden
+// activations are rounded to BF16 where they enter a product.
+//
+// Tensor-core operands live in shared memory in the K-major, 128-byte
+// swizzled layout: a K-block of 64 BF16 values per row, rows of 128 bytes,
+// 8-row atoms of 1024 bytes, the 16-byte chunk c of row r stored at chunk
+// c ^ (r % 8).  Weights are kept on the device already in that layout, so a
+// CTA stages them with one bulk copy.
+#include <math_constants.h>
+#include <cuda_bf16.h>
+
+#include <cstring>
+#include <mutex>
+
+#include "gx_internal.h"
+
+namespace gx {
+
+namespace {
+
+constexpr long kWaitLimit = 1L << 22;
+constexpr int kTile = 128;            // rows (queries) per MMA tile
+constexpr int kQueryThreads = 128;    // one warpgroup: TMEM lanes 0..127
+
+// ------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// Bounded wait on an mbarrier phase; false when the limit was reached.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t phase) {
+  for (long it = 0; it < kWaitLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// Tensor-memory allocation by one full warp; the column base lands in *slot.
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(slot)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+// D[tmem] (+)= A[smem] . B[smem]^T, one 128 x N x 16 step, BF16 in, FP32 out.
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// Arrives on the mbarrier once every MMA this thread issued has completed.
+__device__ __forceinline__ void mma_commit(unsigned long long* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+// 32 consecutive FP32 columns of this warp's 32 tensor-memory lanes.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+      "%30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms
+// 1024 bytes apart.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                    // leading byte offset (unused here)
+  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset between 8-row atoms
+  d |= (uint64_t)1 << 46;                    // descriptor version
+  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+  return d;
+}
+// Instruction descriptor, kind::f16: BF16 A and B (both K-major), FP32 D.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+// Byte offset of element (row, k) of a K-major swizzled operand whose
+// K-blocks of 64 values are `rows * 128` bytes apart.
+__host__ __device__ __forceinline__ uint32_t sw128_offset(int row, int k, int rows) {
+  const int kb = k >> 6, kk = k & 63;
+  return (uint32_t)(kb * rows * 128 + row * 128 + ((((kk >> 3) ^ (row & 7))) << 4) + (kk & 7) * 2);
+}
+// One row's 8 consecutive K values (a 16-byte chunk) into the swizzled tile.
+__device__ __forceinline__ void store_chunk(unsigned char* tile, int row, int k8, int rows,
+                                            const float (&v)[8]) {
+  __nv_bfloat162 p[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) p[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+  *reinterpret_cast<uint4*>(tile + sw128_offset(row, k8, rows)) = *reinterpret_cast<uint4*>(p);
+}
+
+__device__ __forceinline__ float bf16_round(float x) {
+  return __bfloat162float(__float2bfloat16_rn(x));
+}
+
+// Issues the K steps of one layer: D = A . W^T over K = 64 * kblocks.
+__device__ __forceinline__ void layer_mma(uint32_t tmem, uint32_t a_base, uint32_t w_base,
+                                          int kblocks) {
+  const uint32_t idesc = idesc_bf16(kTile, kNsdfWidth);
+  for (int kb = 0; kb < kblocks; ++kb)
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const uint64_t a = desc_sw128(a_base + kb * kTile * 128 + s * 32);
+      const uint64_t b = desc_sw128(w_base + kb * kNsdfWidth * 128 + s * 32);
+      mma_bf16(tmem, a, b, idesc, (kb | s) != 0);
+    }
+}
+
+struct QuerySmem {
+  unsigned char w[kNsdfImgBytes];        // W1 | W2 | W3 | W4 images
+  unsigned char a[kTile * 128 * 2];      // activation operand (K <= 128)
+  NsdfTail tail;
+  unsigned long long bar_w, bar_mma;
+  uint32_t tmem_slot;
+};
+
+// Persistent: each CTA stages the scene's weights once, then runs 128-query
+// tiles through the network.
+__global__ void __launch_bounds__(kQueryThreads, 1)
+    nsdf_query_kernel(const unsigned char* __restrict__ blob, const float* __restrict__ pts,
+                      int n, float* __restrict__ out, unsigned* err) {
+  extern __shared__ unsigned char smem_raw[];
+  QuerySmem& sm = *reinterpret_cast<QuerySmem*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    mbar_init(&sm.bar_w, 1);
+    mbar_init(&sm.bar_mma, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) tmem_alloc(&sm.tmem_slot, kNsdfWidth);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = sm.tmem_slot;
+  if (tid == 0) {
+    mbar_expect_tx(&sm.bar_w, kNsdfBlobBytes);
+    bulk_g2s(sm.w, blob, kNsdfW1Bytes, &sm.bar_w);
+    for (int l = 0; l < 3; ++l)
+      bulk_g2s(sm.w + kNsdfW1Bytes + l * kNsdfWhBytes, blob + kNsdfW1Bytes + l * kNsdfWhBytes,
+               kNsdfWhBytes, &sm.bar_w);
+    bulk_g2s(&sm.tail, blob + kNsdfImgBytes, sizeof(NsdfTail), &sm.bar_w);
+  }
+  bool ok = mbar_wait(&sm.bar_w, 0);
+  if (!ok) mbar_wait(&sm.bar_w, 0);  // give the copy in flight one more bounded wait
+  uint32_t mma_phase = 0;
+  const uint32_t a_base = smem_u32(sm.a);
+  const uint32_t w_base[4] = {smem_u32(sm.w), smem_u32(sm.w + kNsdfW1Bytes),
+                              smem_u32(sm.w + kNsdfW1Bytes + kNsdfWhBytes),
+                              smem_u32(sm.w + kNsdfW1Bytes + 2 * kNsdfWhBytes)};
+  const int tiles = (n + kTile - 1) / kTile;
+  for (int tile = blockIdx.x; ok && tile < tiles; tile += gridDim.x) {
+    const int row = tid;
+    const int i = tile * kTile + row;
+    // Fourier features of this row's point, rounded to BF16 into the operand
+    float px = 0.f, py = 0.f, pz = 0.f;
+    if (i < n) {
+      px = pts[3 * (size_t)i] - sm.tail.centre[0];
+      py = pts[3 * (size_t)i + 1] - sm.tail.centre[1];
+      pz = pts[3 * (size_t)i + 2] - sm.tail.centre[2];
+    }
+#pragma unroll
+    for (int f8 = 0; f8 < kNsdfFreq; f8 += 8) {
+      float sv[8], cv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float* Bf = sm.tail.B[f8 + u];
+        const float ph = 2.f * CUDART_PI_F * (Bf[0] * px + Bf[1] * py + Bf[2] * pz);
+        sincosf(ph, &sv[u], &cv[u]);
+      }
+      store_chunk(sm.a, row, f8, kTile, sv);
+      store_chunk(sm.a, row, kNsdfFreq + f8, kTile, cv);
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    float dot = 0.f;
+    for (int layer = 0; layer < 4 && ok; ++layer) {
+      if (tid == 0) {
+        tc_fence_after();
+        layer_mma(tmem, a_base, w_base[layer], layer == 0 ? 1 : 2);
+        mma_commit(&sm.bar_mma);
+      }
+      ok = __syncthreads_and(mbar_wait(&sm.bar_mma, mma_phase));
+      mma_phase ^= 1u;
+      tc_fence_after();
+      // epilogue: this warp's 32 rows, 32 columns at a time
+#pragma unroll 1
+      for (int c = 0; c < kNsdfWidth / 32; ++c) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
+#pragma unroll
+        for (int u = 0; u < 32; ++u) v[u] = bf16_round(fmaxf(v[u] + sm.tail.b[layer][c * 32 + u], 0.f));
+        if (layer < 3) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            float ch[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) ch[u] = v[q * 8 + u];
+            store_chunk(sm.a, warp * 32 + lane, c * 32 + q * 8, kTile, ch);
+          }
+        } else {
+#pragma unroll
+          for (int u = 0; u < 32; ++u) dot = fmaf(v[u], sm.tail.w5[c * 32 + u], dot);
+        }
+      }
+      fence_proxy_async();
+      tc_fence_before();
+      __syncthreads();
+    }
+    if (ok && i < n) out[i] = dot + sm.tail.b5;
+  }
+  if (!ok && tid == 0 && err) atomicOr(err, kErrWaitTimeout);
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, kNsdfWidth);
+}
+
+// Host-side packing: FP32 parameters (W1 [128][64], b1, W2 [128][128], b2,
+// W3, b3, W4, b4, W5 [128], b5) into the device blob layout.
+void pack_blob(const float* params, const float* B, const float centre[3], unsigned char* blob) {
+  std::memset(blob, 0, kNsdfBlobBytes);
+  const float* p = params;
+  const int in_dims[4] = {64, 128, 128, 128};
+  size_t img = 0;
+  NsdfTail tail;
+  std::memset(&tail, 0, sizeof(tail));
+  for (int l = 0; l < 4; ++l) {
+    const int K = in_dims[l];
+    for (int r = 0; r < kNsdfWidth; ++r)
+      for (int k = 0; k < K; ++k) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(p[(size_t)r * K + k]);
+        std::memcpy(blob + img + sw128_offset(r, k, kNsdfWidth), &h, 2);
+      }
+    p += (size_t)kNsdfWidth * K;
+    for (int r = 0; r < kNsdfWidth; ++r) tail.b[l][r] = p[r];
+    p += kNsdfWidth;
+    img += (size_t)kNsdfWidth * K * 2;
+  }
+  for (int r = 0; r < kNsdfWidth; ++r) tail.w5[r] = p[r];
+  tail.b5 = p[kNsdfWidth];
+  for (int a = 0; a < 3; ++a) tail.centre[a] = centre[a];
+  std::memcpy(tail.B, B, sizeof(tail.B));
+  std::memcpy(blob + kNsdfImgBytes, &tail, sizeof(tail));
+}
+
+// Inverse of pack_blob: the parameters the kernels actually use (BF16 values
+// of W1..W4 widened to FP32).
+void unpack_blob(const unsigned char* blob, float* params, float* B, float* centre) {
+  float* p = params;
+  const int in_dims[4] = {64, 128, 128, 128};
+  size_t img = 0;
+  NsdfTail tail;
+  std::memcpy(&tail, blob + kNsdfImgBytes, sizeof(tail));
+  for (int l = 0; l < 4; ++l) {
+    const int K = in_dims[l];
+    for (int r = 0; r < kNsdfWidth; ++r)
+      for (int k = 0; k < K; ++k) {
+        __nv_bfloat16 h;
+        std::memcpy(&h, blob + img + sw128_offset(r, k, kNsdfWidth), 2);
+        p[(size_t)r * K + k] = __bfloat162float(h);
+      }
+    p += (size_t)kNsdfWidth * K;
+    for (int r = 0; r < kNsdfWidth; ++r) p[r] = tail.b[l][r];
+    p += kNsdfWidth;
+    img += (size_t)kNsdfWidth * K * 2;
+  }
+  for (int r = 0; r < kNsdfWidth; ++r) p[r] = tail.w5[r];
+  p[kNsdfWidth] = tail.b5;
+  if (B) std::memcpy(B, tail.B, sizeof(tail.B));
+  if (centre) std::memcpy(centre, tail.centre, sizeof(tail.centre));
+}
+
+size_t query_smem_bytes() { return sizeof(QuerySmem) + 1024; }
+
+}  // namespace
+
+void nsdf_free(gx_scene_set* s) {
+  for (NsdfScene& ns : s->nsdf) {
+    cudaFree(ns.blob);
+    cudaFree(ns.master);
+    ns = NsdfScene();
+  }
+}
+
+void nsdf_scene_centre(const gx_scene_set* s, int scene, float c[3]) {
+  const DScene& d = s->host[scene];
+  c[0] = d.ox + 0.5f * (d.nx - 1) * d.h;
+  c[1] = d.oy + 0.5f * (d.ny - 1) * d.h;
+  c[2] = d.oz + 0.5f * (d.nz - 1) * d.h;
+}
+
+cudaError_t nsdf_launch_query(const unsigned char* blob, const float* pts, int n, float* out,
+                              unsigned* err, cudaStream_t s) {
+  static std::once_flag once;
+  static cudaError_t cfg = cudaSuccess;
+  std::call_once(once, [] {
+    cfg = cudaFuncSetAttribute(nsdf_query_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)query_smem_bytes());
+  });
+  if (cfg != cudaSuccess) return cfg;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int tiles = (n + kTile - 1) / kTile;
+  const int grid = tiles < sms ? tiles : sms;
+  if (grid > 0)
+    nsdf_query_kernel<<<grid, kQueryThreads, query_smem_bytes(), s>>>(blob, pts, n, out, err);
+  return cudaGetLastError();
+}
+
+}  // namespace gx
+
+using namespace gx;
+
+extern "C" gx_status gx_nsdf_set_weights(gx_scene_set* set, int32_t scene, const float* fourier_B,
+                                         const float* params) {
+  if (!set || !fourier_B || !params) return set_last_error(GX_EINVAL, "gx_nsdf_set_weights: NULL");
+  if (scene < 0 || scene >= set->n) return set_last_error(GX_EINVAL, "gx_nsdf_set_weights: scene");
+  if ((int)set->nsdf.size() != set->n) set->nsdf.resize(set->n);
+  NsdfScene& ns = set->nsdf[scene];
+  if (!ns.blob && cudaMalloc(&ns.blob, kNsdfBlobBytes) != cudaSuccess)
+    return set_last_error(GX_ENOMEM, "gx_nsdf_set_weights: allocation failed");
+  std::vector<unsigned char> host(kNsdfBlobBytes);
+  float c[3];
+  nsdf_scene_centre(set, scene, c);
+  pack_blob(params, fourier_B, c, host.data());
+  if (cudaMemcpy(ns.blob, host.data(), kNsdfBlobBytes, cudaMemcpyHostToDevice) != cudaSuccess)
+    return set_last_error(GX_ECUDA, "gx_nsdf_set_weights: copy failed");
+  ns.ready = true;
+  return GX_OK;
+}
+
+extern "C" gx_status gx_nsdf_get_weights(const gx_scene_set* set, int32_t scene, float* fourier_B,
+                                         float* params, float* centre) {
+  if (!set || !params) return set_last_error(GX_EINVAL, "gx_nsdf_get_weights: NULL");
+  if (scene < 0 || scene >= set->n || (int)set->nsdf.size() != set->n || !set->nsdf[scene].ready)
+    return set_last_error(GX_ESTATE, "gx_nsdf_get_weights: scene has no neural SDF");
+  std::vector<unsigned char> host(kNsdfBlobBytes);
+  if (cudaMemcpy(host.data(), set->nsdf[scene].blob, kNsdfBlobBytes, cudaMemcpyDeviceToHost) !=
+      cudaSuccess)
+    return set_last_error(GX_ECUDA, "gx_nsdf_get_weights: copy failed");
+  unpack_blob(host.data(), params, fourier_B, centre);
+  return GX_OK;
+}
+
+extern "C" gx_status gx_nsdf_query(const gx_scene_set* set, int32_t scene, const float* pts,
+                                   int32_t n, float* dist, void* stream) {
+  if (!set || (n > 0 && (!pts || !dist)) || n < 0)
+    return set_last_error(GX_EINVAL, "gx_nsdf_query: bad arguments");
+  if (scene < 0 || scene >= set->n || (int)set->nsdf.size() != set->n || !set->nsdf[scene].ready)
+    return set_last_error(GX_ESTATE, "gx_nsdf_query: scene has no neural SDF");
+  if (nsdf_launch_query(set->nsdf[scene].blob, pts, n, dist, nullptr, (cudaStream_t)stream) !=
+      cudaSuccess)
+    return set_last_error(GX_ECUDA, "gx_nsdf_query: launch failed");
+  return GX_OK;
+}

@@ -27,7 +27,10 @@ MAX_SPHERES = 31
 SYMBOLS = ["gx_scene_set_create", "gx_scene_set_destroy", "gx_create", "gx_destroy", "gx_reset",
            "gx_step", "gx_step_host", "gx_sync", "gx_device_error", "gx_state_bytes",
            "gx_save_state", "gx_load_state", "gx_state_layout", "gx_phase_times",
-           "gx_raster_counters", "gx_render_noalloc", "gx_last_error"]
+           "gx_raster_counters", "gx_render_noalloc", "gx_nsdf_set_weights",
+           "gx_nsdf_get_weights", "gx_nsdf_query", "gx_last_error"]
+NSDF_PARAMS = 57985
+NSDF_FREQ = 32
 RASTER_COUNTERS = ["clusters_tested", "clusters_drawn", "tris_seen", "tris_front", "tris_expand",
                    "expand_pixels", "tris_warp", "warp_blocks", "tris_clipped", "fragments", "wait_polls",
                    "expand_trips", "rounds"]
@@ -113,6 +116,9 @@ def lib():
         L.gx_raster_counters.argtypes = [vp, C.POINTER(C.c_int64), C.c_int32]
         L.gx_render_noalloc.argtypes = [vp, C.c_int32, vp, vp, vp, C.c_int32, C.c_int32,
                                         C.c_int32, C.c_float, vp, C.c_int32, vp, vp]
+        L.gx_nsdf_set_weights.argtypes = [vp, C.c_int32, vp, vp]
+        L.gx_nsdf_get_weights.argtypes = [vp, C.c_int32, vp, vp, vp]
+        L.gx_nsdf_query.argtypes = [vp, C.c_int32, vp, C.c_int32, vp, vp]
         L.gx_last_error.argtypes = [vp]
         L.gx_last_error.restype = C.c_char_p
         _lib = L
@@ -182,6 +188,31 @@ class SceneSet:
         _check(lib().gx_scene_set_create(descs, n, C.byref(m), C.byref(self.handle)))
         self._keep = []   # the library copied everything
         self.n = n
+
+    # -------------------------------------------------------- neural SDF
+    def nsdf_set_weights(self, scene, fourier_B, params):
+        B = np.ascontiguousarray(fourier_B, np.float32)
+        P = np.ascontiguousarray(params, np.float32)
+        assert B.shape == (NSDF_FREQ, 3) and P.shape == (NSDF_PARAMS,)
+        _check(lib().gx_nsdf_set_weights(self.handle, scene, B.ctypes.data, P.ctypes.data))
+
+    def nsdf_get_weights(self, scene):
+        """(B, params, centre) as the kernels use them."""
+        B = np.zeros((NSDF_FREQ, 3), np.float32)
+        P = np.zeros(NSDF_PARAMS, np.float32)
+        c = np.zeros(3, np.float32)
+        _check(lib().gx_nsdf_get_weights(self.handle, scene, B.ctypes.data, P.ctypes.data,
+                                         c.ctypes.data))
+        return B, P, c
+
+    def nsdf_query(self, scene, pts, out, stream=None):
+        """pts: CUDA float32 [n][3]; out: CUDA float32 [n]."""
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        _check(lib().gx_nsdf_query(self.handle, scene, C.c_void_p(pts.data_ptr()),
+                                   int(pts.shape[0]), C.c_void_p(out.data_ptr()),
+                                   C.c_void_p(s.cuda_stream)))
+        return out
 
     def close(self):
         if self.handle:

@@ -566,6 +566,27 @@ def make_actions(n_steps: int, n_envs: int, dist: str, seed: int = 0) -> np.ndar
     return a.astype(np.float32)
 
 
+def fourier_matrix(seed: int = 7, n_freq: int = 32, sigma: float = 2.0) -> np.ndarray:
+    """Fourier feature frequencies B [n_freq][3] ~ N(0, sigma^2) per metre
+    (sigma = 1 / (2 * 0.25 m)), for the neural SDF's features."""
+    rng = np.random.default_rng(seed)
+    return rng.normal(0.0, sigma, (n_freq, 3)).astype(np.float32)
+
+
+def nsdf_init(seed: int = 7) -> np.ndarray:
+    """Initial neural-SDF parameters (He-normal weights, zero biases) in the
+    C ABI's flat layout: W1 [128][64], b1, W2..W4 [128][128] with biases,
+    W5 [128], b5."""
+    rng = np.random.default_rng(seed + 1)
+    parts = []
+    for fan_in, fan_out in [(64, 128), (128, 128), (128, 128), (128, 128)]:
+        parts.append(rng.normal(0.0, math.sqrt(2.0 / fan_in), fan_out * fan_in))
+        parts.append(np.zeros(fan_out))
+    parts.append(rng.normal(0.0, math.sqrt(1.0 / 128), 128))
+    parts.append(np.zeros(1))
+    return np.concatenate(parts).astype(np.float32)
+
+
 def env_scene_map(n_envs: int, n_scenes: int) -> np.ndarray:
     """Contiguous blocks: env i uses scene floor(i * S / N)."""
     return (np.arange(n_envs, dtype=np.int64) * n_scenes // n_envs).astype(np.int32)
