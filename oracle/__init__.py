@@ -108,6 +108,9 @@ def _declare(L):
     L.orc_render.argtypes = [P(Robot_c), P(Scene_c), P(ObjMesh_c), P(State_c), C.c_int32,
                              C.c_int32, C.c_double, C.c_double, C.c_double, f64p, u32p, u8p,
                              i32p, P(RenderStats_c)]
+    L.orc_nsdf_sample.argtypes = [P(Scene_c), C.c_uint64, C.c_uint32, C.c_uint32, C.c_double,
+                                  f64p, f64p, P(C.c_int)]
+    L.orc_nsdf_sample.restype = C.c_int
     L.orc_mlp_set_bf16_operands.argtypes = [C.c_int]
     L.orc_mlp_forward.argtypes = [f64p, C.c_int, P(f64p), P(f64p), i32p, C.c_int, f64p, f64p]
     L.orc_mlp_forward.restype = C.c_double
@@ -249,6 +252,24 @@ class Oracle:
                             C.byref(nb))
         return y, bool(ok.value), nb.value
 
+    def nsdf_samples(self, seed, scene, idx, band=0.1):
+        """Training samples idx (neural SDF): points [n][3], labels, draw used, near-band draws."""
+        idx = np.atleast_1d(np.asarray(idx, np.int64))
+        P = np.zeros((len(idx), 3))
+        d = np.zeros(len(idx))
+        t = np.zeros(len(idx), np.int32)
+        nb = np.zeros(len(idx), np.int32)
+        p3 = np.zeros(3)
+        dd = C.c_double()
+        nbb = C.c_int()
+        for k, i in enumerate(idx):
+            t[k] = self.L.orc_nsdf_sample(C.byref(self.scene), int(seed), int(scene), int(i),
+                                          float(band), _p(p3, f64p), C.byref(dd), C.byref(nbb))
+            P[k] = p3
+            d[k] = dd.value
+            nb[k] = nbb.value
+        return P, d, t, nb
+
     def render(self, st, W, H, eps_px=None, tol_rel=None, cos_min=None):
         n = W * H
         depth = np.zeros(n)
@@ -318,3 +339,22 @@ class MLP64:
                                        _p(self.dims, i32p), len(self.Ws), _p(X, f64p),
                                        _p(y, f64p), len(X), lo, hi, gwp, gbp)
         return loss, gW, gb
+
+
+# ------------------------------------------------------------------ training
+# Adam (Kingma and Ba, ICLR 2015, Algorithm 1) and a cosine learning-rate
+# decay, in FP64, for checking the neural-SDF optimiser step.
+
+def cosine_lr(lr0, t, T):
+    """Learning rate of step t (0-based) of T: lr0 (1 + cos(pi t / T)) / 2."""
+    return lr0 * 0.5 * (1.0 + np.cos(np.pi * t / T))
+
+
+def adam_step(p, m, v, g, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update at step t (1-based): returns new (p, m, v)."""
+    g = np.asarray(g, np.float64)
+    m = beta1 * np.asarray(m, np.float64) + (1.0 - beta1) * g
+    v = beta2 * np.asarray(v, np.float64) + (1.0 - beta2) * g * g
+    mhat = m / (1.0 - beta1 ** t)
+    vhat = v / (1.0 - beta2 ** t)
+    return np.asarray(p, np.float64) - lr * mhat / (np.sqrt(vhat) + eps), m, v

@@ -632,6 +632,38 @@ void orc_render(const orc_robot* rb, const orc_scene* sc, const orc_objmesh* om,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Neural-SDF training sample i (the workload's learned part; not in the     */
+/* paper).  Even i: one uniform draw over the lattice box.  Odd i: the first */
+/* of at most 64 uniform draws whose interpolated distance has |d| < band,   */
+/* or the last draw when none has.  Draw t of sample i takes Philox4x32-10  */
+/* on counter (i, scene, t, 0x4E534446) with key (seed low, seed high);     */
+/* coordinate a = origin_a + u_a (dims_a - 1) h with u_a = (word_a >> 8) /  */
+/* 2^24.  The label is the trilinear grid distance at the drawn point.       */
+/* Returns the index of the draw used; *near_band counts draws whose |d|    */
+/* lay within ORC_BAND of band.                                              */
+/* ------------------------------------------------------------------------ */
+int orc_nsdf_sample(const orc_scene* s, uint64_t seed, uint32_t scene, uint32_t i, double band,
+                    double p[3], double* d, int* near_band) {
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  const int tries = (i & 1u) ? 64 : 1;
+  int nb = 0, t = 0;
+  for (t = 0; t < tries; ++t) {
+    uint32_t ctr[4] = {i, scene, (uint32_t)t, 0x4E534446u}, w[4];
+    orc_philox4x32_10(ctr, key, w);
+    for (int a = 0; a < 3; ++a)
+      p[a] = (double)s->grid_origin[a] +
+             unit24(w[a]) * ((double)(s->grid_dims[a] - 1) * (double)s->grid_h);
+    double edge;
+    orc_grid_query(s, p, d, &edge);
+    if (tries == 1) break;
+    if (fabs(fabs(*d) - band) < ORC_BAND) nb++;
+    if (fabs(*d) < band) break;
+  }
+  if (near_band) *near_band = nb;
+  return t < tries ? t : tries - 1;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Neural SDF: d(x) = W_L relu(... relu(W_1 gamma(x) + b_1) ...) + b_L with  */
 /* Fourier features gamma(x) = [sin(2 pi B x), cos(2 pi B x)].              */
 /* dims = {2F, h1, ..., 1}; W[l] is row-major [dims[l+1]][dims[l]].         */

@@ -110,6 +110,12 @@ void orc_render(const orc_robot* rb, const orc_scene* sc, const orc_objmesh* om,
                 double cos_min, double* depth, uint32_t* rgb, uint8_t* ambiguous,
                 int32_t* winner, orc_render_stats* stats);
 
+/* Neural-SDF training sample i: even i uniform over the lattice box, odd i
+ * the first of at most 64 uniform draws with |d| < band; label = grid d.
+ * Returns the draw index used. */
+int orc_nsdf_sample(const orc_scene* s, uint64_t seed, uint32_t scene, uint32_t i, double band,
+                    double p[3], double* d, int* near_band);
+
 /* Neural SDF (Fourier-feature MLP) in FP64: forward and backward.  With
  * orc_mlp_set_bf16_operands(1) every value fed to a BF16 matrix product
  * (features, hidden activations, hidden-layer gradients) is rounded to the

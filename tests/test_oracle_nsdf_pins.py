@@ -1,0 +1,158 @@
+"""Pins the oracle's neural-SDF training pieces (the workload's learned part,
+not in the paper) to facts that do not come from the oracle: a planar field
+whose distance is known in closed form, acceptance rates that follow from the
+geometry, Adam's published invariances (Kingma and Ba, ICLR 2015, Sec. 2.1)
+and PyTorch's own BF16 rounding and autograd for the BF16-operand mode."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2306_07552_b300 import inputs as I
+
+from test_oracle_pins import FLOOR, oracle_for, scene_from_boxes
+
+BAND = 0.1
+
+
+@pytest.fixture(scope="module")
+def floor_oracle():
+    # a floor slab (top y = 0) under a 2 x 2 x 2 m lattice from y = -0.5
+    sc = scene_from_boxes([FLOOR], (-1, -0.5, -1), (1, 1.5, 1), h=0.05)
+    return sc, oracle_for(sc)
+
+
+def test_samples_lie_in_the_lattice_box_with_planar_labels(floor_oracle):
+    sc, orc = floor_oracle
+    P, d, t, nb = orc.nsdf_samples(seed=11, scene=3, idx=np.arange(400), band=BAND)
+    lo = sc.grid_origin.astype(np.float64)
+    hi = lo + (sc.grid_dims - 1) * np.float64(sc.grid_h)
+    assert np.all(P >= lo) and np.all(P < hi)
+    # the floor's distance field is d = y in this box (nearest face is the top)
+    assert np.allclose(d, P[:, 1], atol=1e-12)
+    assert np.all(t[0::2] == 0)                    # even samples: one uniform draw
+
+
+def test_near_surface_half_accepts_inside_the_band(floor_oracle):
+    _, orc = floor_oracle
+    idx = np.arange(1, 1601, 2)
+    P, d, t, nb = orc.nsdf_samples(seed=5, scene=0, idx=idx, band=BAND)
+    acc = t < 63
+    assert np.all(np.abs(d[acc]) < BAND)
+    # P(|y| < 0.1) over a 2 m tall box is 0.1: draws until acceptance are
+    # geometric with mean 10
+    assert 8.5 < (t + 1).mean() < 11.5
+    # accepted heights are uniform in (-0.1, 0.1)
+    assert abs(P[acc, 1].mean()) < 0.01
+
+
+def test_uniform_half_is_uniform(floor_oracle):
+    _, orc = floor_oracle
+    P, d, t, nb = orc.nsdf_samples(seed=7, scene=1, idx=np.arange(0, 4000, 2), band=BAND)
+    # box y in [-0.5, 1.5): mean 0.5, a quarter below the floor
+    assert abs(P[:, 1].mean() - 0.5) < 0.04
+    assert abs((P[:, 1] < 0).mean() - 0.25) < 0.03
+    assert abs(P[:, 0].mean()) < 0.04 and abs(P[:, 2].mean()) < 0.04
+
+
+def test_samples_are_counter_based(floor_oracle):
+    _, orc = floor_oracle
+    a = orc.nsdf_samples(seed=9, scene=2, idx=[10, 11, 12])[0]
+    b = orc.nsdf_samples(seed=9, scene=2, idx=[12, 11, 10])[0]
+    assert np.array_equal(a, b[::-1])
+    c = orc.nsdf_samples(seed=10, scene=2, idx=[10, 11, 12])[0]
+    e = orc.nsdf_samples(seed=9, scene=4, idx=[10, 11, 12])[0]
+    assert not np.allclose(a, c) and not np.allclose(a, e)
+
+
+# ------------------------------------------------------------------ Adam
+
+def test_adam_first_step_has_size_lr():
+    g = np.array([3.0, -1e-3, 250.0, -7.0])
+    p, m, v = O.adam_step(np.zeros(4), np.zeros(4), np.zeros(4), g, t=1, lr=0.01)
+    assert np.allclose(p, -0.01 * np.sign(g), rtol=1e-4)
+
+
+def test_adam_is_invariant_to_gradient_scale():
+    rng = np.random.default_rng(0)
+    p0 = rng.normal(size=8)
+    state_a = (p0, np.zeros(8), np.zeros(8))
+    state_b = (p0, np.zeros(8), np.zeros(8))
+    for t in range(1, 20):
+        g = rng.normal(size=8)
+        state_a = O.adam_step(*state_a, g, t, 1e-3)
+        state_b = O.adam_step(*state_b, 1000.0 * g, t, 1e-3)
+    assert np.allclose(state_a[0], state_b[0], rtol=0, atol=1e-9)
+
+
+def test_adam_constant_gradient_moves_lr_per_step():
+    s = (np.zeros(3), np.zeros(3), np.zeros(3))
+    g = np.array([0.5, -2.0, 1e-2])
+    for t in range(1, 51):
+        s = O.adam_step(*s, g, t, 1e-3)
+    assert np.allclose(s[0], -50 * 1e-3 * np.sign(g), rtol=1e-5)
+
+
+def test_adam_minimises_a_quadratic():
+    a = np.array([1.0, 10.0, 0.1])
+    s = (np.array([1.0, -1.0, 2.0]), np.zeros(3), np.zeros(3))
+    for t in range(1, 3001):
+        s = O.adam_step(*s, a * s[0], t, O.cosine_lr(0.05, t - 1, 3000))
+    assert np.all(np.abs(s[0]) < 1e-2)
+
+
+def test_cosine_schedule_end_points():
+    assert O.cosine_lr(1e-3, 0, 100) == pytest.approx(1e-3)
+    assert O.cosine_lr(1e-3, 50, 100) == pytest.approx(5e-4)
+    assert O.cosine_lr(1e-3, 100, 100) == pytest.approx(0.0, abs=1e-18)
+    lrs = [O.cosine_lr(1e-3, t, 100) for t in range(101)]
+    assert all(b <= a for a, b in zip(lrs, lrs[1:]))
+
+
+# ------------------------------------------------------ BF16 operand mode
+
+def _bf16(x):
+    return torch.as_tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float64)
+
+
+def test_bf16_operand_mode_matches_torch_rounding_and_autograd():
+    """Forward and gradients of the BF16-operand mode against PyTorch: FP64
+    arithmetic, PyTorch's BF16 rounding of features and hidden activations
+    (straight-through in backward) and of each hidden layer's gradient."""
+    rng = np.random.default_rng(3)
+    F, widths = 6, (24, 20, 16)
+    dims = [2 * F, *widths, 1]
+    Ws = [rng.normal(0, 0.4, (dims[i + 1], dims[i])) for i in range(len(dims) - 1)]
+    bs = [rng.normal(0, 0.1, dims[i + 1]) for i in range(len(dims) - 1)]
+    B = rng.normal(0, 1, (F, 3))
+    X = rng.uniform(-1, 1, (9, 3))
+    y = rng.uniform(-0.3, 1.2, 9)
+    m = O.MLP64(B, Ws, bs, bf16_operands=True)
+
+    Wt = [torch.tensor(w, requires_grad=True) for w in Ws]
+    bt = [torch.tensor(b, requires_grad=True) for b in bs]
+    ph = 2 * math.pi * torch.tensor(X) @ torch.tensor(B).T
+    h = torch.cat([torch.sin(ph), torch.cos(ph)], 1)
+    h = h + (_bf16(h.detach()) - h).detach()
+    for l in range(len(Ws)):
+        z = h @ Wt[l].T + bt[l]
+        if l == len(Ws) - 1:
+            h = z
+            break
+        z.register_hook(lambda g: _bf16(g))
+        a = torch.relu(z)
+        h = a + (_bf16(a.detach()) - a).detach()
+    pred = h[:, 0]
+    assert np.allclose(m.forward(X), pred.detach().numpy(), rtol=0, atol=1e-12)
+    t = torch.clamp(torch.tensor(y), -0.2, 1.0)
+    loss_t = torch.abs(pred - t).mean()
+    loss_t.backward()
+    loss, gW, gb = m.loss_grad(X, y, -0.2, 1.0)
+    assert loss == pytest.approx(loss_t.item(), abs=1e-13)
+    for l in range(len(Ws)):
+        assert np.allclose(gW[l], Wt[l].grad.numpy(), rtol=0, atol=1e-12)
+        assert np.allclose(gb[l], bt[l].grad.numpy(), rtol=0, atol=1e-12)
+    # rounding is really applied: the FP64 mode differs
+    assert not np.allclose(O.MLP64(B, Ws, bs).forward(X), m.forward(X), rtol=0, atol=1e-9)
