@@ -233,8 +233,9 @@ gx_status gx_raster_counters(gx_ctx* ctx, int64_t* out, int32_t n);
  * using the set is stepping. */
 #define GX_NSDF_PARAMS 57985
 
-/* Loads weights (host FP32; W1..W4 are rounded to BF16) for one scene.
- * Allocates the scene's device copy on first use. */
+/* Loads weights (host FP32; W1..W4 are rounded to BF16 for the kernels, the
+ * FP32 values are kept as training's master copy) for one scene.  Allocates
+ * the scene's device copies on first use. */
 gx_status gx_nsdf_set_weights(gx_scene_set* set, int32_t scene, const float* fourier_B,
                               const float* params);
 /* The weights as the kernels use them (BF16 values widened to FP32), the
@@ -242,10 +243,60 @@ gx_status gx_nsdf_set_weights(gx_scene_set* set, int32_t scene, const float* fou
  * params).  GX_ESTATE when the scene has no neural SDF. */
 gx_status gx_nsdf_get_weights(const gx_scene_set* set, int32_t scene, float* fourier_B,
                               float* params, float* centre);
+/* The FP32 master parameters (training's copy; equal to the values last
+ * passed to gx_nsdf_set_weights until gx_nsdf_train changes them) into
+ * params (host, GX_NSDF_PARAMS).  Waits for the device. */
+gx_status gx_nsdf_get_master(const gx_scene_set* set, int32_t scene, float* params);
 /* d(x) for n points (device [n][3] world coordinates) into dist (device [n]).
  * Asynchronous on `stream`. */
 gx_status gx_nsdf_query(const gx_scene_set* set, int32_t scene, const float* pts, int32_t n,
                         float* dist, void* stream);
+
+/* Training-sample stream of one scene (workload definition): sample i (0 <=
+ * i < 2^32) is, for even i, a uniform point of the scene's grid box and, for
+ * odd i, the first of at most 64 such points whose grid distance has
+ * |d| < near_band (the last one when none has); point t of sample i comes from
+ * Philox4x32-10 on counter (i, scene, t, 0x4E534446) with key (seed low 32
+ * bits, seed high 32 bits), coordinate = origin + ((word >> 8) / 2^24) *
+ * (dims - 1) * h.  Label = trilinear grid distance.  Writes samples
+ * [first, first + n) to pts (device [n][3]) and dist (device [n]);
+ * asynchronous on `stream`. */
+gx_status gx_nsdf_samples(const gx_scene_set* set, int32_t scene, uint64_t seed, int64_t first,
+                          int64_t n, float near_band, float* pts, float* dist, void* stream);
+
+/* Gradient of the mean L1 loss (1/n) sum |d(x_i) - clamp(y_i, lo, hi)| with
+ * respect to the GX_NSDF_PARAMS parameters (layout as above), evaluated with
+ * the scene's current weights on n points (device pts [n][3], labels [n]),
+ * into grad (device [GX_NSDF_PARAMS]) and the loss into *loss (device, may be
+ * NULL).  BF16 operands as in the forward; the gradients of hidden
+ * pre-activations are rounded to BF16 where they enter a product.  Allocates
+ * its workspace, waits for the stream; GX_EDEVICE when a bounded wait inside
+ * a kernel gave up. */
+gx_status gx_nsdf_grad(gx_scene_set* set, int32_t scene, const float* pts, const float* labels,
+                       int32_t n, float clamp_lo, float clamp_hi, float* grad, float* loss,
+                       void* stream);
+
+typedef struct {
+  int64_t n_samples;   /* training set size (samples 0 .. n_samples-1), <= 2^32 */
+  int32_t batch;       /* samples per Adam step; batch t = samples t*batch ..   */
+                       /* (t+1)*batch-1, indices modulo n_samples              */
+  int32_t steps;       /* Adam steps                                            */
+  float lr;            /* peak rate; step t uses lr (1 + cos(pi t / steps)) / 2 */
+  float beta1, beta2, eps;   /* Adam (Kingma and Ba 2015)                       */
+  float clamp_lo, clamp_hi;  /* labels clamped to [lo, hi] (m)                  */
+  float near_band;     /* sample stream parameter (m), as gx_nsdf_samples       */
+  uint64_t seed;       /* sample stream seed                                    */
+} gx_train_params;
+
+/* Trains the scene's network from its current weights (gx_nsdf_set_weights
+ * must have been called): draws the sample set, then `steps` Adam steps with
+ * fresh moments.  FP32 master parameters; the BF16 copy the kernels read is
+ * rewritten after every step.  loss_host (host, [steps], may be NULL)
+ * receives each step's loss.  Allocates n_samples * 16 bytes plus the batch's
+ * workspace (245,760 bytes per 128 samples) and frees them; waits for the
+ * stream. */
+gx_status gx_nsdf_train(gx_scene_set* set, int32_t scene, const gx_train_params* params,
+                        float* loss_host, void* stream);
 
 /* Renders depth (and RGB when rgb != NULL) for n environments without
  * allocating any device memory.  The paper has no counterpart: this serves

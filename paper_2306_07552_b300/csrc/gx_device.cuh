@@ -1,0 +1,96 @@
+// Device functions shared by the step kernels and the neural-SDF kernels:
+// the counter-based random generator and the distance-grid query.
+#pragma once
+
+#include "gx_internal.h"
+
+namespace gx {
+namespace {
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of the
+// multiply-xor S-box with a Weyl key schedule.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+__device__ __forceinline__ float unit24(uint32_t w) {
+  return (float)(w >> 8) * (1.0f / 16777216.0f);
+}
+
+__device__ __forceinline__ float gnode(const DScene& s, int i, int j, int k) {
+  return __ldg(s.grid + ((size_t)k * s.ny + j) * s.nx + i);
+}
+
+// Trilinear interpolation at lattice coordinates g (0 <= g <= n - 1 per axis).
+__device__ __forceinline__ float grid_lerp(const DScene& s, float gx, float gy, float gz) {
+  const int i = min((int)floorf(gx), s.nx - 2);
+  const int j = min((int)floorf(gy), s.ny - 2);
+  const int k = min((int)floorf(gz), s.nz - 2);
+  const float tx = gx - i, ty = gy - j, tz = gz - k;
+  const float* g = s.grid + ((size_t)k * s.ny + j) * s.nx + i;
+  const size_t sy = s.nx, sz = (size_t)s.nx * s.ny;
+  const float c000 = __ldg(g), c100 = __ldg(g + 1);
+  const float c010 = __ldg(g + sy), c110 = __ldg(g + sy + 1);
+  const float c001 = __ldg(g + sz), c101 = __ldg(g + sz + 1);
+  const float c011 = __ldg(g + sz + sy), c111 = __ldg(g + sz + sy + 1);
+  const float c00 = c000 + tx * (c100 - c000), c10 = c010 + tx * (c110 - c010);
+  const float c01 = c001 + tx * (c101 - c001), c11 = c011 + tx * (c111 - c011);
+  const float c0 = c00 + ty * (c10 - c00), c1 = c01 + ty * (c11 - c01);
+  return c0 + tz * (c1 - c0);
+}
+
+// Trilinear interpolation of the distance grid.  false when c lies outside
+// the lattice box (or is not finite): that counts as contact.
+__device__ bool grid_query(const DScene& s, float cx, float cy, float cz, float& d) {
+  const float gx = (cx - s.ox) * s.inv_h, gy = (cy - s.oy) * s.inv_h, gz = (cz - s.oz) * s.inv_h;
+  if (!(gx >= 0.f && gx <= (float)(s.nx - 1) && gy >= 0.f && gy <= (float)(s.ny - 1) &&
+        gz >= 0.f && gz <= (float)(s.nz - 1)))
+    return false;
+  d = grid_lerp(s, gx, gy, gz);
+  return true;
+}
+
+// Fourier-feature phase b . (p - c) in turns, reduced to about [-1/2, 1/2].
+// FP32 alone loses the phase of a point metres from c (|b . (p - c)| reaches
+// tens of turns, ~1e-5 rad of rounding); the difference p - c (Knuth's
+// TwoSum) and the products (FMA TwoProduct) are carried as unevaluated
+// hi + lo pairs, the integer part of hi is removed exactly, and only the
+// final fraction is rounded, so the phase is good to ~1e-7 rad.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+struct Centred {
+  float h[3], l[3];
+};
+__device__ __forceinline__ Centred centre_point(float x, float y, float z, const float c[3]) {
+  Centred d;
+  two_sum(x, -c[0], d.h[0], d.l[0]);
+  two_sum(y, -c[1], d.h[1], d.l[1]);
+  two_sum(z, -c[2], d.h[2], d.l[2]);
+  return d;
+}
+__device__ __forceinline__ float phase_turns(const float b[3], const Centred& d) {
+  float hi = 0.f, lo = 0.f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float p = b[a] * d.h[a];
+    const float pe = fmaf(b[a], d.h[a], -p);
+    float e;
+    two_sum(hi, p, hi, e);
+    lo += e + pe + b[a] * d.l[a];
+  }
+  return (hi - rintf(hi)) + lo;
+}
+
+}  // namespace
+}  // namespace gx

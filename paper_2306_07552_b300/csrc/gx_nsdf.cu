@@ -3,6 +3,8 @@
 //
 //   d(x) = W5 relu(W4 relu(W3 relu(W2 relu(W1 g(x) + b1) + b2) + b3) + b4) + b5
 //   g(x) = [sin(2 pi B (x - c)), cos(2 pi B (x - c))],  B in R^{32x3}
+//   (phases formed in turns with error-free transformations, reduced, then
+//   sincospi)
 //
 // W1..W4 are BF16 and every hidden product runs on the 5th-generation tensor
 // cores (tcgen05.mma, kind::f16, FP32 accumulation in tensor memory); the
@@ -15,147 +17,20 @@
 // c ^ (r % 8).  Weights are kept on the device already in that layout, so a
 // CTA stages them with one bulk copy.
 #include <math_constants.h>
-#include <cuda_bf16.h>
 
 #include <cstring>
 #include <mutex>
 
+#include "gx_device.cuh"
 #include "gx_internal.h"
+#include "gx_tc.cuh"
 
 namespace gx {
 
 namespace {
 
-constexpr long kWaitLimit = 1L << 22;
 constexpr int kTile = 128;            // rows (queries) per MMA tile
 constexpr int kQueryThreads = 128;    // one warpgroup: TMEM lanes 0..127
-
-// ------------------------------------------------------------ PTX helpers
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
-                                         unsigned long long* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-// Bounded wait on an mbarrier phase; false when the limit was reached.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t phase) {
-  for (long it = 0; it < kWaitLimit; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(phase)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-// Tensor-memory allocation by one full warp; the column base lands in *slot.
-__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                   smem_u32(slot)),
-               "r"(ncols)
-               : "memory");
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
-               : "memory");
-}
-// D[tmem] (+)= A[smem] . B[smem]^T, one 128 x N x 16 step, BF16 in, FP32 out.
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
-                                         uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-// Arrives on the mbarrier once every MMA this thread issued has completed.
-__device__ __forceinline__ void mma_commit(unsigned long long* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(bar))
-      : "memory");
-}
-// 32 consecutive FP32 columns of this warp's 32 tensor-memory lanes.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
-      "%30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
-        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
-        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms
-// 1024 bytes apart.
-__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
-  d |= (uint64_t)1 << 16;                    // leading byte offset (unused here)
-  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset between 8-row atoms
-  d |= (uint64_t)1 << 46;                    // descriptor version
-  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
-  return d;
-}
-// Instruction descriptor, kind::f16: BF16 A and B (both K-major), FP32 D.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
-}
-// Byte offset of element (row, k) of a K-major swizzled operand whose
-// K-blocks of 64 values are `rows * 128` bytes apart.
-__host__ __device__ __forceinline__ uint32_t sw128_offset(int row, int k, int rows) {
-  const int kb = k >> 6, kk = k & 63;
-  return (uint32_t)(kb * rows * 128 + row * 128 + ((((kk >> 3) ^ (row & 7))) << 4) + (kk & 7) * 2);
-}
-// One row's 8 consecutive K values (a 16-byte chunk) into the swizzled tile.
-__device__ __forceinline__ void store_chunk(unsigned char* tile, int row, int k8, int rows,
-                                            const float (&v)[8]) {
-  __nv_bfloat162 p[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) p[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-  *reinterpret_cast<uint4*>(tile + sw128_offset(row, k8, rows)) = *reinterpret_cast<uint4*>(p);
-}
-
-__device__ __forceinline__ float bf16_round(float x) {
-  return __bfloat162float(__float2bfloat16_rn(x));
-}
 
 // Issues the K steps of one layer: D = A . W^T over K = 64 * kblocks.
 __device__ __forceinline__ void layer_mma(uint32_t tmem, uint32_t a_base, uint32_t w_base,
@@ -217,21 +92,16 @@ __global__ void __launch_bounds__(kQueryThreads, 1)
     const int row = tid;
     const int i = tile * kTile + row;
     // Fourier features of this row's point, rounded to BF16 into the operand
-    float px = 0.f, py = 0.f, pz = 0.f;
-    if (i < n) {
-      px = pts[3 * (size_t)i] - sm.tail.centre[0];
-      py = pts[3 * (size_t)i + 1] - sm.tail.centre[1];
-      pz = pts[3 * (size_t)i + 2] - sm.tail.centre[2];
-    }
+    Centred d = centre_point(sm.tail.centre[0], sm.tail.centre[1], sm.tail.centre[2],
+                             sm.tail.centre);
+    if (i < n) d = centre_point(pts[3 * (size_t)i], pts[3 * (size_t)i + 1], pts[3 * (size_t)i + 2],
+                                sm.tail.centre);
 #pragma unroll
     for (int f8 = 0; f8 < kNsdfFreq; f8 += 8) {
       float sv[8], cv[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const float* Bf = sm.tail.B[f8 + u];
-        const float ph = 2.f * CUDART_PI_F * (Bf[0] * px + Bf[1] * py + Bf[2] * pz);
-        sincosf(ph, &sv[u], &cv[u]);
-      }
+      for (int u = 0; u < 8; ++u)
+        sincospif(2.f * phase_turns(sm.tail.B[f8 + u], d), &sv[u], &cv[u]);
       store_chunk(sm.a, row, f8, kTile, sv);
       store_chunk(sm.a, row, kNsdfFreq + f8, kTile, cv);
     }
@@ -384,6 +254,10 @@ extern "C" gx_status gx_nsdf_set_weights(gx_scene_set* set, int32_t scene, const
   NsdfScene& ns = set->nsdf[scene];
   if (!ns.blob && cudaMalloc(&ns.blob, kNsdfBlobBytes) != cudaSuccess)
     return set_last_error(GX_ENOMEM, "gx_nsdf_set_weights: allocation failed");
+  if (!ns.master && cudaMalloc(&ns.master, (size_t)kNsdfParams * 4) != cudaSuccess)
+    return set_last_error(GX_ENOMEM, "gx_nsdf_set_weights: allocation failed");
+  if (cudaMemcpy(ns.master, params, (size_t)kNsdfParams * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+    return set_last_error(GX_ECUDA, "gx_nsdf_set_weights: copy failed");
   std::vector<unsigned char> host(kNsdfBlobBytes);
   float c[3];
   nsdf_scene_centre(set, scene, c);
@@ -404,6 +278,16 @@ extern "C" gx_status gx_nsdf_get_weights(const gx_scene_set* set, int32_t scene,
       cudaSuccess)
     return set_last_error(GX_ECUDA, "gx_nsdf_get_weights: copy failed");
   unpack_blob(host.data(), params, fourier_B, centre);
+  return GX_OK;
+}
+
+extern "C" gx_status gx_nsdf_get_master(const gx_scene_set* set, int32_t scene, float* params) {
+  if (!set || !params) return set_last_error(GX_EINVAL, "gx_nsdf_get_master: NULL");
+  if (scene < 0 || scene >= set->n || (int)set->nsdf.size() != set->n || !set->nsdf[scene].master)
+    return set_last_error(GX_ESTATE, "gx_nsdf_get_master: scene has no neural SDF");
+  if (cudaMemcpy(params, set->nsdf[scene].master, (size_t)kNsdfParams * 4,
+                 cudaMemcpyDeviceToHost) != cudaSuccess)
+    return set_last_error(GX_ECUDA, "gx_nsdf_get_master: copy failed");
   return GX_OK;
 }
 

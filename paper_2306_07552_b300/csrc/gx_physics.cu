@@ -16,6 +16,7 @@
 #include <math_constants.h>
 
 #include "gx_internal.h"
+#include "gx_device.cuh"
 
 namespace gx {
 
@@ -26,52 +27,6 @@ constexpr int kEnvsPerBlock = 4;
 
 __device__ __forceinline__ float clampf(float x, float lo, float hi) {
   return fminf(fmaxf(x, lo), hi);
-}
-
-// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of the
-// multiply-xor S-box with a Weyl key schedule.
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
-    k.x += 0x9E3779B9u;
-    k.y += 0xBB67AE85u;
-  }
-  return c;
-}
-
-__device__ __forceinline__ float unit24(uint32_t w) {
-  return (float)(w >> 8) * (1.0f / 16777216.0f);
-}
-
-__device__ __forceinline__ float gnode(const DScene& s, int i, int j, int k) {
-  return __ldg(s.grid + ((size_t)k * s.ny + j) * s.nx + i);
-}
-
-// Trilinear interpolation of the distance grid.  false when c lies outside
-// the lattice box (or is not finite): that counts as contact.
-__device__ bool grid_query(const DScene& s, float cx, float cy, float cz, float& d) {
-  const float gx = (cx - s.ox) * s.inv_h, gy = (cy - s.oy) * s.inv_h, gz = (cz - s.oz) * s.inv_h;
-  if (!(gx >= 0.f && gx <= (float)(s.nx - 1) && gy >= 0.f && gy <= (float)(s.ny - 1) &&
-        gz >= 0.f && gz <= (float)(s.nz - 1)))
-    return false;
-  const int i = min((int)floorf(gx), s.nx - 2);
-  const int j = min((int)floorf(gy), s.ny - 2);
-  const int k = min((int)floorf(gz), s.nz - 2);
-  const float tx = gx - i, ty = gy - j, tz = gz - k;
-  const float* g = s.grid + ((size_t)k * s.ny + j) * s.nx + i;
-  const size_t sy = s.nx, sz = (size_t)s.nx * s.ny;
-  const float c000 = __ldg(g), c100 = __ldg(g + 1);
-  const float c010 = __ldg(g + sy), c110 = __ldg(g + sy + 1);
-  const float c001 = __ldg(g + sz), c101 = __ldg(g + sz + 1);
-  const float c011 = __ldg(g + sz + sy), c111 = __ldg(g + sz + sy + 1);
-  const float c00 = c000 + tx * (c100 - c000), c10 = c010 + tx * (c110 - c010);
-  const float c01 = c001 + tx * (c101 - c001), c11 = c011 + tx * (c111 - c011);
-  const float c0 = c00 + ty * (c10 - c00), c1 = c01 + ty * (c11 - c01);
-  d = c0 + tz * (c1 - c0);
-  return true;
 }
 
 // Right-multiplies the row-major rotation R by a rotation of `axis` by the

@@ -28,7 +28,8 @@ SYMBOLS = ["gx_scene_set_create", "gx_scene_set_destroy", "gx_create", "gx_destr
            "gx_step", "gx_step_host", "gx_sync", "gx_device_error", "gx_state_bytes",
            "gx_save_state", "gx_load_state", "gx_state_layout", "gx_phase_times",
            "gx_raster_counters", "gx_render_noalloc", "gx_nsdf_set_weights",
-           "gx_nsdf_get_weights", "gx_nsdf_query", "gx_last_error"]
+           "gx_nsdf_get_weights", "gx_nsdf_query", "gx_nsdf_get_master", "gx_nsdf_samples", "gx_nsdf_grad",
+           "gx_nsdf_train", "gx_last_error"]
 NSDF_PARAMS = 57985
 NSDF_FREQ = 32
 RASTER_COUNTERS = ["clusters_tested", "clusters_drawn", "tris_seen", "tris_front", "tris_expand",
@@ -78,6 +79,13 @@ class GxOutputs(C.Structure):
                 ("contact_flags", C.c_void_p), ("event", C.c_void_p)]
 
 
+class GxTrainParams(C.Structure):
+    _fields_ = [("n_samples", C.c_int64), ("batch", C.c_int32), ("steps", C.c_int32),
+                ("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
+                ("eps", C.c_float), ("clamp_lo", C.c_float), ("clamp_hi", C.c_float),
+                ("near_band", C.c_float), ("seed", C.c_uint64)]
+
+
 class GxError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"gx status {status}: {msg}")
@@ -119,6 +127,12 @@ def lib():
         L.gx_nsdf_set_weights.argtypes = [vp, C.c_int32, vp, vp]
         L.gx_nsdf_get_weights.argtypes = [vp, C.c_int32, vp, vp, vp]
         L.gx_nsdf_query.argtypes = [vp, C.c_int32, vp, C.c_int32, vp, vp]
+        L.gx_nsdf_get_master.argtypes = [vp, C.c_int32, vp]
+        L.gx_nsdf_samples.argtypes = [vp, C.c_int32, C.c_uint64, C.c_int64, C.c_int64, C.c_float,
+                                      vp, vp, vp]
+        L.gx_nsdf_grad.argtypes = [vp, C.c_int32, vp, vp, C.c_int32, C.c_float, C.c_float, vp, vp,
+                                   vp]
+        L.gx_nsdf_train.argtypes = [vp, C.c_int32, C.POINTER(GxTrainParams), vp, vp]
         L.gx_last_error.argtypes = [vp]
         L.gx_last_error.restype = C.c_char_p
         _lib = L
@@ -205,6 +219,12 @@ class SceneSet:
                                          c.ctypes.data))
         return B, P, c
 
+    def nsdf_get_master(self, scene):
+        """FP32 master parameters (training's copy)."""
+        P = np.zeros(NSDF_PARAMS, np.float32)
+        _check(lib().gx_nsdf_get_master(self.handle, scene, P.ctypes.data))
+        return P
+
     def nsdf_query(self, scene, pts, out, stream=None):
         """pts: CUDA float32 [n][3]; out: CUDA float32 [n]."""
         import torch
@@ -213,6 +233,42 @@ class SceneSet:
                                    int(pts.shape[0]), C.c_void_p(out.data_ptr()),
                                    C.c_void_p(s.cuda_stream)))
         return out
+
+    def nsdf_samples(self, scene, seed, first, n, near_band=0.1, stream=None):
+        """Training samples [first, first + n): (CUDA [n][3] points, CUDA [n] labels)."""
+        import torch
+        pts = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+        d = torch.empty(n, dtype=torch.float32, device="cuda")
+        s = stream if stream is not None else torch.cuda.current_stream()
+        _check(lib().gx_nsdf_samples(self.handle, scene, int(seed), int(first), int(n),
+                                     float(near_band), C.c_void_p(pts.data_ptr()),
+                                     C.c_void_p(d.data_ptr()), C.c_void_p(s.cuda_stream)))
+        return pts, d
+
+    def nsdf_grad(self, scene, pts, labels, clamp_lo=-0.2, clamp_hi=1.0, stream=None):
+        """(gradient CUDA [NSDF_PARAMS], loss) of the mean clamped L1 loss."""
+        import torch
+        g = torch.empty(NSDF_PARAMS, dtype=torch.float32, device="cuda")
+        loss = torch.empty(1, dtype=torch.float32, device="cuda")
+        s = stream if stream is not None else torch.cuda.current_stream()
+        _check(lib().gx_nsdf_grad(self.handle, scene, C.c_void_p(pts.data_ptr()),
+                                  C.c_void_p(labels.data_ptr()), int(pts.shape[0]),
+                                  float(clamp_lo), float(clamp_hi), C.c_void_p(g.data_ptr()),
+                                  C.c_void_p(loss.data_ptr()), C.c_void_p(s.cuda_stream)))
+        return g, float(loss.item())
+
+    def nsdf_train(self, scene, n_samples=10_000_000, batch=65536, steps=1000, lr=1e-3,
+                   beta1=0.9, beta2=0.999, eps=1e-8, clamp_lo=-0.2, clamp_hi=1.0,
+                   near_band=0.1, seed=7, stream=None):
+        """Adam training from the current weights; returns the per-step losses."""
+        import torch
+        tp = GxTrainParams(n_samples, batch, steps, lr, beta1, beta2, eps, clamp_lo, clamp_hi,
+                           near_band, seed)
+        losses = np.zeros(max(steps, 1), np.float32)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        _check(lib().gx_nsdf_train(self.handle, scene, C.byref(tp), losses.ctypes.data,
+                                   C.c_void_p(s.cuda_stream)))
+        return losses[:steps]
 
     def close(self):
         if self.handle:

