@@ -101,6 +101,9 @@ def _declare(L):
     L.orc_fk.argtypes = [P(Robot_c), f64p, f64p, f64p, f64p, f64p]
     L.orc_sphere_centres.argtypes = [P(Robot_c), f64p, f64p, f64p]
     L.orc_step.argtypes = [P(Robot_c), P(Scene_c), P(State_c), f32p, P(StepOut_c)]
+    L.orc_step_nsdf.argtypes = [P(Robot_c), P(Scene_c), P(State_c), f32p, f64p, C.c_double,
+                                C.c_double, P(StepOut_c)]
+    L.orc_candidate_spheres.argtypes = [P(Robot_c), P(State_c), f32p, f64p, f64p, i32p]
     L.orc_reset.argtypes = [P(Robot_c), P(Scene_c), P(State_c), C.c_uint64, C.c_int32, C.c_int32,
                             C.c_float, C.c_float, P(ResetOut_c)]
     L.orc_snap.argtypes = [P(Scene_c), f64p, C.c_double, P(C.c_int), P(C.c_int)]
@@ -208,6 +211,25 @@ class Oracle:
         out = StepOut_c()
         self.L.orc_step(C.byref(self.robot), C.byref(self.scene), C.byref(st), _p(a, f32p),
                         C.byref(out))
+        return out
+
+    def candidate_spheres(self, st, action):
+        """Centres [31][3], radii [31] and the active mask of the proposed pose."""
+        a = np.ascontiguousarray(action, np.float32)
+        c = np.zeros((31, 3))
+        r = np.zeros(31)
+        act = np.zeros(31, np.int32)
+        self.L.orc_candidate_spheres(C.byref(self.robot), C.byref(st), _p(a, f32p), _p(c, f64p),
+                                     _p(r, f64p), _p(act, i32p))
+        return c, r, act.astype(bool)
+
+    def step_nsdf(self, st, action, dhat, margin, band):
+        """One step with the neural-SDF static test (dhat [31] predictions)."""
+        a = np.ascontiguousarray(action, np.float32)
+        d = np.ascontiguousarray(dhat, np.float64)
+        out = StepOut_c()
+        self.L.orc_step_nsdf(C.byref(self.robot), C.byref(self.scene), C.byref(st), _p(a, f32p),
+                             _p(d, f64p), float(margin), float(band), C.byref(out))
         return out
 
     def reset(self, st, seed, env, n_obj, rho_min, rho_max):

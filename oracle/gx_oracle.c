@@ -269,21 +269,71 @@ double orc_snap(const orc_scene* s, const double p[3], double target, int* ok, i
 /* ------------------------------------------------------------------------ */
 /* One environment step (Sec. 3.2, App. A).                                 */
 /* ------------------------------------------------------------------------ */
-void orc_step(const orc_robot* rb, const orc_scene* sc, orc_state* st, const float act[11],
-              orc_step_out* out) {
-  double a[11];
-  for (int k = 0; k < 11; ++k) a[k] = isfinite(act[k]) ? clampd(act[k], -1.0, 1.0) : 0.0;
-  int nb = 0;
+/* Static test with a learned distance (the workload's neural SDF): a centre
+ * outside the lattice box is in contact; a predicted clearance dhat - r of at
+ * least `margin` is free without consulting the grid; otherwise the grid
+ * decides.  Predictions within `band` of the margin count as near band. */
+static int neural_static_contact(const orc_scene* s, const double c[3], double r, double dhat,
+                                 double margin, double band, int* nb) {
+  double d, edge;
+  int inside = orc_grid_query(s, c, &d, &edge);
+  if (fabs(edge) < ORC_BAND) (*nb)++;
+  if (!inside) return 1;
+  if (fabs(dhat - r - margin) < band) (*nb)++;
+  if (dhat - r >= margin) return 0;
+  if (fabs(d - r) < ORC_BAND) (*nb)++;
+  return d < r;
+}
 
-  /* candidate pose: translate along the pre-step heading, then turn; +1 on
-   * the turn action is clockwise seen from above (yaw decreases). */
+static void candidate_pose(const orc_robot* rb, const orc_state* st, const double a[11],
+                           double cb[3], double cq[7]) {
+  /* translate along the pre-step heading, then turn; +1 on the turn action
+   * is clockwise seen from above (yaw decreases). */
   double th = st->base[2];
-  double cb[3], cq[7];
   cb[0] = st->base[0] + (double)rb->base_step * a[0] * cos(th);
   cb[1] = st->base[1] - (double)rb->base_step * a[0] * sin(th);
   cb[2] = wrap_pi(th - (double)rb->base_turn * a[1]);
   for (int k = 0; k < 7; ++k)
     cq[k] = clampd(st->q[k] + (double)rb->dq_max * a[2 + k], rb->q_min[k], rb->q_max[k]);
+}
+
+static void clip_actions(const float act[11], double a[11]) {
+  for (int k = 0; k < 11; ++k) a[k] = isfinite(act[k]) ? clampd(act[k], -1.0, 1.0) : 0.0;
+}
+
+void orc_candidate_spheres(const orc_robot* rb, const orc_state* st, const float act[11],
+                           double c[31][3], double r[31], int32_t active[31]) {
+  double a[11], cb[3], cq[7], links[8][12], ee[12];
+  clip_actions(act, a);
+  candidate_pose(rb, st, a, cb, cq);
+  orc_fk(rb, cb, cq, links, ee, NULL);
+  for (int i = 0; i < 31; ++i) { active[i] = 0; r[i] = 0; c[i][0] = c[i][1] = c[i][2] = 0; }
+  for (int i = 0; i < rb->n_spheres; ++i) {
+    double p[3] = {rb->sphere_pos[3 * i], rb->sphere_pos[3 * i + 1], rb->sphere_pos[3 * i + 2]};
+    fr_apply(links[rb->sphere_link[i]], p, c[i]);
+    r[i] = rb->sphere_radius[i];
+    active[i] = 1;
+  }
+  if (st->held >= 0) {
+    fr_apply(ee, st->c_off, c[30]);
+    r[30] = st->obj[st->held][3];
+    active[30] = 1;
+  }
+}
+
+void orc_step(const orc_robot* rb, const orc_scene* sc, orc_state* st, const float act[11],
+              orc_step_out* out) {
+  orc_step_nsdf(rb, sc, st, act, NULL, 0.0, 0.0, out);
+}
+
+void orc_step_nsdf(const orc_robot* rb, const orc_scene* sc, orc_state* st, const float act[11],
+                   const double* dhat, double margin, double band, orc_step_out* out) {
+  double a[11];
+  clip_actions(act, a);
+  int nb = 0;
+
+  double cb[3], cq[7];
+  candidate_pose(rb, st, a, cb, cq);
 
   /* candidate spheres */
   double links[8][12], ee[12], cam[12];
@@ -298,7 +348,9 @@ void orc_step(const orc_robot* rb, const orc_scene* sc, orc_state* st, const flo
   int h = st->held;
   for (int i = 0; i < rb->n_spheres; ++i) {
     double r = rb->sphere_radius[i];
-    if (static_contact(sc, cs[i], r, &nb)) { mask |= 1u << i; flags |= 1; }
+    int hit = dhat ? neural_static_contact(sc, cs[i], r, dhat[i], margin, band, &nb)
+                   : static_contact(sc, cs[i], r, &nb);
+    if (hit) { mask |= 1u << i; flags |= 1; }
     for (int j = 0; j < st->n_obj; ++j) {
       if (j == h) continue;
       if (pair_contact(cs[i], r, st->obj[j], st->obj[j][3], &nb)) { mask |= 1u << i; flags |= 2; }
@@ -308,7 +360,9 @@ void orc_step(const orc_robot* rb, const orc_scene* sc, orc_state* st, const flo
     double ph[3];
     fr_apply(ee, st->c_off, ph);
     double rho = st->obj[h][3];
-    if (static_contact(sc, ph, rho, &nb)) { mask |= 1u << 30; flags |= 1 | 4; }
+    int hit = dhat ? neural_static_contact(sc, ph, rho, dhat[30], margin, band, &nb)
+                   : static_contact(sc, ph, rho, &nb);
+    if (hit) { mask |= 1u << 30; flags |= 1 | 4; }
     for (int j = 0; j < st->n_obj; ++j) {
       if (j == h) continue;
       if (pair_contact(ph, rho, st->obj[j], st->obj[j][3], &nb)) { mask |= 1u << 30; flags |= 2 | 4; }

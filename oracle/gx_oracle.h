@@ -102,6 +102,16 @@ void orc_sphere_centres(const orc_robot* rb, const double base[3], const double 
                         double out[][3]);
 void orc_step(const orc_robot* rb, const orc_scene* sc, orc_state* st, const float act[11],
               orc_step_out* out);
+/* The step with the neural-SDF static test: dhat[i] is the predicted
+ * distance at candidate sphere i (i < n_spheres; 30 = held object).  Outside
+ * the lattice box is contact; dhat - r >= margin is free; else the grid
+ * decides.  Predictions within `band` of the margin count as near band. */
+void orc_step_nsdf(const orc_robot* rb, const orc_scene* sc, orc_state* st, const float act[11],
+                   const double* dhat, double margin, double band, orc_step_out* out);
+/* Candidate sphere centres and radii of the step that `act` proposes (robot
+ * spheres 0..n_spheres-1, held object at 30); active[i] marks the used ones. */
+void orc_candidate_spheres(const orc_robot* rb, const orc_state* st, const float act[11],
+                           double c[31][3], double r[31], int32_t active[31]);
 void orc_reset(const orc_robot* rb, const orc_scene* sc, orc_state* st, uint64_t seed,
                int32_t env, int32_t n_obj, float rho_min, float rho_max, orc_reset_out* out);
 double orc_snap(const orc_scene* s, const double p[3], double target, int* ok, int* near_band);

@@ -156,3 +156,71 @@ def test_bf16_operand_mode_matches_torch_rounding_and_autograd():
         assert np.allclose(gb[l], bt[l].grad.numpy(), rtol=0, atol=1e-12)
     # rounding is really applied: the FP64 mode differs
     assert not np.allclose(O.MLP64(B, Ws, bs).forward(X), m.forward(X), rtol=0, atol=1e-9)
+
+
+# ------------------------------------------- neural static test in the step
+
+from test_oracle_pins import _act, _state  # noqa: E402
+
+POST = [-0.5, 0.0, -0.1, -0.3, 1.0, 0.1]
+
+
+def _post_oracle():
+    sc = scene_from_boxes([FLOOR, POST], (-2, -0.3, -2), (2, 2.5, 2), h=0.02)
+    return oracle_for(sc)
+
+
+def test_candidate_spheres_are_the_proposed_pose():
+    orc = _post_oracle()
+    st = _state(orc, base=(0.2, 0.1, 0.3))
+    c, r, act = orc.candidate_spheres(st, np.zeros(11, np.float32))
+    n = len(I.fetch_like_robot().sphere_radius)
+    assert np.allclose(c[:n], orc.sphere_centres([0.2, 0.1, 0.3], I.fetch_like_robot().q_rest),
+                       atol=1e-12)
+    assert np.array_equal(act[:n], np.ones(n, bool)) and not act[30]
+    # a held object rides at T_ee c_off
+    st = _state(orc, objs=[[0.5, 0.5, 0.0, 0.04]], held=0, c_off=(0.01, 0.02, 0.03))
+    c, r, act = orc.candidate_spheres(st, np.zeros(11, np.float32))
+    _, ee, _ = orc.fk((0, 0, 0), I.fetch_like_robot().q_rest)
+    assert act[30] and r[30] == pytest.approx(0.04)
+    R, t = ee[:9].reshape(3, 3), ee[9:]
+    assert np.allclose(c[30], R @ [0.01, 0.02, 0.03] + t, atol=1e-12)
+
+
+def test_neural_rule_reduces_to_grid_when_every_prediction_is_close():
+    orc = _post_oracle()
+    acts = I.make_actions(40, 1, "uniform", seed=4)[:, 0]
+    sa, sb = _state(orc), _state(orc)
+    for t in range(40):
+        oa = orc.step(sa, acts[t])
+        ob = orc.step_nsdf(sb, acts[t], np.full(31, -1e9), 0.02, 1e-3)
+        assert (oa.contact_mask, oa.flags, oa.event) == (ob.contact_mask, ob.flags, ob.event)
+        assert list(sa.base) == list(sb.base) and list(sa.q) == list(sb.q)
+
+
+def test_neural_rule_trusts_a_large_clearance_but_not_the_box_edge():
+    orc = _post_oracle()
+    st = _state(orc)
+    back = _act(fwd=-1.0, q1=0.5)           # drives a base sphere into the post
+    assert orc.step(_state(orc), back).flags & 1
+    out = orc.step_nsdf(st, back, np.full(31, 1e9), 0.02, 1e-3)
+    assert out.contact_mask == 0 and not out.reverted
+    # outside the lattice box stays contact whatever the prediction
+    sc = scene_from_boxes([FLOOR], (-1, -0.3, -1), (1.0, 2.5, 1.0), h=0.05)
+    o2 = oracle_for(sc)
+    out = o2.step_nsdf(_state(o2, base=(0.45, 0, 0)), _act(fwd=1.0), np.full(31, 1e9), 0.02, 1e-3)
+    assert out.reverted and out.flags & 1
+
+
+def test_neural_rule_margin_is_inclusive_and_banded():
+    orc = _post_oracle()
+    back = _act(fwd=-1.0, q1=0.5)
+    c, r, act = orc.candidate_spheres(_state(orc), back)
+    hit = orc.step(_state(orc), back).contact_mask
+    i = int(np.flatnonzero([(hit >> k) & 1 for k in range(31)])[0])
+    d = np.full(31, 1e9)
+    d[i] = r[i] + 0.02                       # clearance exactly the margin: trusted
+    assert orc.step_nsdf(_state(orc), back, d, 0.02, 1e-3).contact_mask & (1 << i) == 0
+    d[i] = np.nextafter(r[i] + 0.02, 0)      # just below: the grid decides
+    out = orc.step_nsdf(_state(orc), back, d, 0.02, 1e-3)
+    assert out.contact_mask & (1 << i) and out.near_band >= 1
