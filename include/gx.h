@@ -134,7 +134,16 @@ typedef struct {
   int32_t use_graph;       /* 1: replay the step as a captured CUDA graph     */
   int32_t profile;         /* bit 0: time each kernel with CUDA events on the
                               caller's stream (disables graph replay);
-                              bit 1: also count rasteriser work (slower)      */
+                              bit 1: also count rasteriser work (slower);
+                              bit 2: count neural-SDF decisions against the
+                              grid-only rule (evaluates both; slower)         */
+  int32_t sdf_mode;        /* 0: static test on the distance grid;
+                              1: neural SDF (every scene an environment uses
+                              needs weights, gx_nsdf_set_weights): the grid is
+                              consulted only where the predicted clearance
+                              d - r is below sdf_margin, or not finite; a
+                              centre outside the grid box is contact          */
+  float sdf_margin;        /* metres, >= 0 (e.g. 0.02)                        */
 } gx_config;
 
 /* Outputs of one step, device memory owned by the caller (e.g. torch
@@ -217,6 +226,14 @@ gx_status gx_phase_times(gx_ctx* ctx, double ms[3], int64_t launches[3]);
  * near-clipped, fragments written.  Fills out[0..n-1]; waits for the device.
  * GX_ESTATE when the context does not count. */
 gx_status gx_raster_counters(gx_ctx* ctx, int64_t* out, int32_t n);
+
+/* Neural-SDF decision counters accumulated since the previous call (profile
+ * bit 2):
+ * out[0] static tests made, out[1] of which the grid decided, out[2]
+ * decisions that differ from the grid-only rule, out[3] env-steps whose
+ * contact mask differs from it.  Waits for the device.  GX_ESTATE when the
+ * context does not count. */
+gx_status gx_nsdf_counters(gx_ctx* ctx, int64_t out[4]);
 
 /* ----------------------------------------------------------------------------
  * Neural SDF (not in the paper; the learned stand-in for the distance grid).

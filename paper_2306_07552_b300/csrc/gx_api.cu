@@ -2,6 +2,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -52,6 +53,14 @@ struct gx_ctx {
   double prof_ms[3] = {0, 0, 0};
   int64_t prof_n[3] = {0, 0, 0};
   unsigned long long* d_counters = nullptr;
+  // neural SDF in the static test
+  float4* d_nsdf_pts = nullptr;
+  float* d_nsdf_d = nullptr;
+  int4* d_nsdf_tiles = nullptr;
+  int n_nsdf_tiles = 0;
+  int* d_nsdf_perm = nullptr;
+  const unsigned char** d_nsdf_blobs = nullptr;
+  unsigned long long* d_nsdf_counters = nullptr;
   // buffers for gx_step_host
   float* h2d_actions = nullptr;
   gx_outputs dev_out{};
@@ -161,6 +170,24 @@ void enqueue_step(gx_ctx* c, const float* actions, const gx_outputs& out, cudaSt
   pp.out = out;
   pp.err = c->d_err;
   pp.raster_work = c->d_raster_work;
+  if (c->cfg.sdf_mode == 1) {
+    pp.nsdf_pts = c->d_nsdf_pts;
+    pp.nsdf_d = c->d_nsdf_d;
+    pp.nsdf_margin = c->cfg.sdf_margin;
+    pp.nsdf_counters = c->d_nsdf_counters;
+    pp.nsdf_pass = 1;
+    launch_physics(pp, s);
+    NsdfStepParams np{};
+    np.blobs = c->d_nsdf_blobs;
+    np.tiles = c->d_nsdf_tiles;
+    np.n_tiles = c->n_nsdf_tiles;
+    np.perm = c->d_nsdf_perm;
+    np.pts = c->d_nsdf_pts;
+    np.out = c->d_nsdf_d;
+    np.err = c->d_err;
+    nsdf_launch_step(np, s);
+    pp.nsdf_pass = 2;
+  }
   launch_physics(pp, s);
   if (ev) cudaEventRecord(ev[1], s);
   RasterParams rp{};
@@ -331,6 +358,9 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
       if (c.env_scene[i] < 0 || c.env_scene[i] >= set->n)
         return fail(nullptr, GX_EINVAL, "env_scene[%d] out of range", i);
   if (c.raster_regions != 0) return fail(nullptr, GX_EINVAL, "raster_regions is reserved (0)");
+  if (c.sdf_mode != 0 && c.sdf_mode != 1) return fail(nullptr, GX_EINVAL, "sdf_mode must be 0 or 1");
+  if (c.sdf_mode == 1 && !(c.sdf_margin >= 0.f && c.sdf_margin < 1e30f))
+    return fail(nullptr, GX_EINVAL, "sdf_margin must be finite and >= 0");
   gx_ctx* x = new gx_ctx();
   x->set = set;
   x->cfg = c;
@@ -400,6 +430,44 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
   *x->h_err = 0;
   if ((e = cudaEventCreateWithFlags(&x->ev_err, cudaEventDisableTiming)) != cudaSuccess)
     return bail(e, "event");
+  if (c.sdf_mode == 1) {
+    // environments grouped by scene; tiles of up to 4 that share a scene
+    std::vector<int> perm(x->n);
+    for (int i = 0; i < x->n; ++i) perm[i] = i;
+    std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return es[a] < es[b]; });
+    std::vector<int4> tiles;
+    for (int i = 0; i < x->n;) {
+      const int sc = es[perm[i]];
+      if ((int)set->nsdf.size() != set->n || !set->nsdf[sc].ready) {
+        gx_destroy(x);
+        return fail(nullptr, GX_ESTATE, "sdf_mode 1: scene %d has no neural SDF weights", sc);
+      }
+      int k = 0;
+      while (k < 4 && i + k < x->n && es[perm[i + k]] == sc) ++k;
+      tiles.push_back(make_int4(sc, i, k, 0));
+      i += k;
+    }
+    std::vector<const unsigned char*> blobs(set->n, nullptr);
+    for (int sc = 0; sc < set->n && sc < (int)set->nsdf.size(); ++sc) blobs[sc] = set->nsdf[sc].blob;
+    x->n_nsdf_tiles = (int)tiles.size();
+    if ((e = cudaMalloc(&x->d_nsdf_pts, n * 32 * sizeof(float4))) != cudaSuccess ||
+        (e = cudaMalloc(&x->d_nsdf_d, n * 32 * sizeof(float))) != cudaSuccess ||
+        (e = cudaMalloc(&x->d_nsdf_tiles, tiles.size() * sizeof(int4))) != cudaSuccess ||
+        (e = cudaMalloc(&x->d_nsdf_perm, n * sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc(&x->d_nsdf_blobs, set->n * sizeof(void*))) != cudaSuccess ||
+        (e = cudaMemcpy(x->d_nsdf_tiles, tiles.data(), tiles.size() * sizeof(int4),
+                        cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(x->d_nsdf_perm, perm.data(), n * sizeof(int), cudaMemcpyHostToDevice)) !=
+            cudaSuccess ||
+        (e = cudaMemcpy(x->d_nsdf_blobs, blobs.data(), set->n * sizeof(void*),
+                        cudaMemcpyHostToDevice)) != cudaSuccess)
+      return bail(e, "neural SDF buffers");
+    if (c.profile & 4) {
+      if ((e = cudaMalloc(&x->d_nsdf_counters, kNsdfCounters * 8)) != cudaSuccess ||
+          (e = cudaMemset(x->d_nsdf_counters, 0, kNsdfCounters * 8)) != cudaSuccess)
+        return bail(e, "neural SDF counters");
+    }
+  }
   if (c.profile & 2) {
     if ((e = cudaMalloc(&x->d_counters, kRasterCounters * 8)) != cudaSuccess)
       return bail(e, "counters");
@@ -424,6 +492,12 @@ extern "C" void gx_destroy(gx_ctx* x) {
   if (x->h_err) cudaFreeHost(x->h_err);
   for (cudaEvent_t e : x->prof_ev) cudaEventDestroy(e);
   cudaFree(x->d_counters);
+  cudaFree(x->d_nsdf_pts);
+  cudaFree(x->d_nsdf_d);
+  cudaFree(x->d_nsdf_tiles);
+  cudaFree(x->d_nsdf_perm);
+  cudaFree((void*)x->d_nsdf_blobs);
+  cudaFree(x->d_nsdf_counters);
   if (x->ev_err) cudaEventDestroy(x->ev_err);
   for (void* p : x->host_step_allocs) cudaFree(p);
   delete x;
@@ -607,6 +681,17 @@ extern "C" gx_status gx_raster_counters(gx_ctx* x, int64_t* out, int32_t n) {
   CK(x, cudaMemcpy(h, x->d_counters, sizeof(h), cudaMemcpyDeviceToHost));
   CK(x, cudaMemset(x->d_counters, 0, sizeof(h)));
   for (int k = 0; k < n; ++k) out[k] = k < kRasterCounters ? (int64_t)h[k] : 0;
+  return GX_OK;
+}
+
+extern "C" gx_status gx_nsdf_counters(gx_ctx* x, int64_t out[4]) {
+  if (!x || !out) return fail(x, GX_EINVAL, "gx_nsdf_counters: bad argument");
+  if (!x->d_nsdf_counters) return fail(x, GX_ESTATE, "gx_nsdf_counters: context does not count");
+  CK(x, cudaDeviceSynchronize());
+  unsigned long long h[kNsdfCounters];
+  CK(x, cudaMemcpy(h, x->d_nsdf_counters, sizeof(h), cudaMemcpyDeviceToHost));
+  CK(x, cudaMemset(x->d_nsdf_counters, 0, sizeof(h)));
+  for (int k = 0; k < kNsdfCounters; ++k) out[k] = (int64_t)h[k];
   return GX_OK;
 }
 

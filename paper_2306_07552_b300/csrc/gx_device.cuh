@@ -47,6 +47,13 @@ __device__ __forceinline__ float grid_lerp(const DScene& s, float gx, float gy, 
   return c0 + tz * (c1 - c0);
 }
 
+// true when c lies inside the lattice box (and is finite).
+__device__ __forceinline__ bool grid_contains(const DScene& s, float cx, float cy, float cz) {
+  const float gx = (cx - s.ox) * s.inv_h, gy = (cy - s.oy) * s.inv_h, gz = (cz - s.oz) * s.inv_h;
+  return gx >= 0.f && gx <= (float)(s.nx - 1) && gy >= 0.f && gy <= (float)(s.ny - 1) &&
+         gz >= 0.f && gz <= (float)(s.nz - 1);
+}
+
 // Trilinear interpolation of the distance grid.  false when c lies outside
 // the lattice box (or is not finite): that counts as contact.
 __device__ bool grid_query(const DScene& s, float cx, float cy, float cz, float& d) {

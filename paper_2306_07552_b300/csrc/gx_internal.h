@@ -81,6 +81,23 @@ struct PhysicsParams {
   gx_outputs out;
   unsigned* err;
   int* raster_work;       // zeroed here for the rasteriser that follows
+  // neural-SDF static test: pass 1 writes the candidate sphere centres
+  // (x, y, z, radius or -1 when unused) and stops; pass 2 reads the
+  // predicted distances and consults the grid only below the margin.
+  int nsdf_pass;                        // 0: grid only, 1: emit, 2: consume
+  float4* nsdf_pts;                     // [n][32]
+  const float* nsdf_d;                  // [n][32]
+  float nsdf_margin;
+  unsigned long long* nsdf_counters;    // optional [kNsdfCounters]
+};
+
+// Neural-SDF decision counters (profiling only).
+enum NsdfCounter {
+  kNsdfSpheres = 0,   // static tests made
+  kNsdfFallbacks,     // of which the grid decided (predicted clearance < margin)
+  kNsdfDisagree,      // decisions that differ from the grid-only rule
+  kNsdfEnvDisagree,   // env-steps whose contact mask differs from the grid-only rule
+  kNsdfCounters
 };
 
 struct ResetParams {
@@ -189,6 +206,19 @@ struct gx_scene_set {
 namespace gx {
 
 void nsdf_free(gx_scene_set* s);
+
+// Neural-SDF queries of a step: tiles of up to 4 environments (128 rows of
+// 32 sphere slots) that share a scene.
+struct NsdfStepParams {
+  const unsigned char* const* blobs;  // [n_scenes] device blob per scene
+  const int4* tiles;                  // (scene, first index into perm, count, 0)
+  int n_tiles;
+  const int* perm;                    // environments grouped by scene
+  const float4* pts;                  // [n][32]
+  float* out;                         // [n][32]
+  unsigned* err;
+};
+cudaError_t nsdf_launch_step(const NsdfStepParams& p, cudaStream_t s);
 
 // Read-only view of a scene set's device data, for entry points outside
 // gx_api.cu.

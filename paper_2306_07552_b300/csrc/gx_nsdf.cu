@@ -53,26 +53,10 @@ struct QuerySmem {
   uint32_t tmem_slot;
 };
 
-// Persistent: each CTA stages the scene's weights once, then runs 128-query
-// tiles through the network.
-__global__ void __launch_bounds__(kQueryThreads, 1)
-    nsdf_query_kernel(const unsigned char* __restrict__ blob, const float* __restrict__ pts,
-                      int n, float* __restrict__ out, unsigned* err) {
-  extern __shared__ unsigned char smem_raw[];
-  QuerySmem& sm = *reinterpret_cast<QuerySmem*>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (tid == 0) {
-    mbar_init(&sm.bar_w, 1);
-    mbar_init(&sm.bar_mma, 1);
-    fence_mbar_init();
-  }
-  if (warp == 0) tmem_alloc(&sm.tmem_slot, kNsdfWidth);
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = sm.tmem_slot;
-  if (tid == 0) {
+// Stages a scene's weights (BF16 images and the FP32 tail) into shared
+// memory: thread 0 issues the bulk copies, every thread waits (bounded).
+__device__ bool load_weights(QuerySmem& sm, const unsigned char* blob, uint32_t& w_phase) {
+  if (threadIdx.x == 0) {
     mbar_expect_tx(&sm.bar_w, kNsdfBlobBytes);
     bulk_g2s(sm.w, blob, kNsdfW1Bytes, &sm.bar_w);
     for (int l = 0; l < 3; ++l)
@@ -80,73 +64,154 @@ __global__ void __launch_bounds__(kQueryThreads, 1)
                kNsdfWhBytes, &sm.bar_w);
     bulk_g2s(&sm.tail, blob + kNsdfImgBytes, sizeof(NsdfTail), &sm.bar_w);
   }
-  bool ok = mbar_wait(&sm.bar_w, 0);
-  if (!ok) mbar_wait(&sm.bar_w, 0);  // give the copy in flight one more bounded wait
-  uint32_t mma_phase = 0;
+  bool ok = mbar_wait(&sm.bar_w, w_phase);
+  if (!ok) ok = mbar_wait(&sm.bar_w, w_phase);  // one more bounded wait for the copy in flight
+  w_phase ^= 1u;
+  return ok;
+}
+
+// One 128-row tile through the network; d is this thread's point relative
+// to the feature centre.  Returns this row's output (valid when ok).
+__device__ float run_tile(QuerySmem& sm, uint32_t tmem, const Centred& d, uint32_t& mma_phase,
+                          bool& ok) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t a_base = smem_u32(sm.a);
   const uint32_t w_base[4] = {smem_u32(sm.w), smem_u32(sm.w + kNsdfW1Bytes),
                               smem_u32(sm.w + kNsdfW1Bytes + kNsdfWhBytes),
                               smem_u32(sm.w + kNsdfW1Bytes + 2 * kNsdfWhBytes)};
-  const int tiles = (n + kTile - 1) / kTile;
-  for (int tile = blockIdx.x; ok && tile < tiles; tile += gridDim.x) {
-    const int row = tid;
-    const int i = tile * kTile + row;
-    // Fourier features of this row's point, rounded to BF16 into the operand
-    Centred d = centre_point(sm.tail.centre[0], sm.tail.centre[1], sm.tail.centre[2],
-                             sm.tail.centre);
-    if (i < n) d = centre_point(pts[3 * (size_t)i], pts[3 * (size_t)i + 1], pts[3 * (size_t)i + 2],
-                                sm.tail.centre);
+  // Fourier features of this row's point, rounded to BF16 into the operand
 #pragma unroll
-    for (int f8 = 0; f8 < kNsdfFreq; f8 += 8) {
-      float sv[8], cv[8];
+  for (int f8 = 0; f8 < kNsdfFreq; f8 += 8) {
+    float sv[8], cv[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u)
-        sincospif(2.f * phase_turns(sm.tail.B[f8 + u], d), &sv[u], &cv[u]);
-      store_chunk(sm.a, row, f8, kTile, sv);
-      store_chunk(sm.a, row, kNsdfFreq + f8, kTile, cv);
+    for (int u = 0; u < 8; ++u)
+      sincospif(2.f * phase_turns(sm.tail.B[f8 + u], d), &sv[u], &cv[u]);
+    store_chunk(sm.a, tid, f8, kTile, sv);
+    store_chunk(sm.a, tid, kNsdfFreq + f8, kTile, cv);
+  }
+  fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  float dot = 0.f;
+  for (int layer = 0; layer < 4 && ok; ++layer) {
+    if (tid == 0) {
+      tc_fence_after();
+      layer_mma(tmem, a_base, w_base[layer], layer == 0 ? 1 : 2);
+      mma_commit(&sm.bar_mma);
+    }
+    ok = __syncthreads_and(mbar_wait(&sm.bar_mma, mma_phase));
+    mma_phase ^= 1u;
+    tc_fence_after();
+    // epilogue: this warp's 32 rows, 32 columns at a time
+#pragma unroll 1
+    for (int c = 0; c < kNsdfWidth / 32; ++c) {
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
+#pragma unroll
+      for (int u = 0; u < 32; ++u)
+        v[u] = bf16_round(fmaxf(v[u] + sm.tail.b[layer][c * 32 + u], 0.f));
+      if (layer < 3) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          float ch[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) ch[u] = v[q * 8 + u];
+          store_chunk(sm.a, warp * 32 + lane, c * 32 + q * 8, kTile, ch);
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < 32; ++u) dot = fmaf(v[u], sm.tail.w5[c * 32 + u], dot);
+      }
     }
     fence_proxy_async();
     tc_fence_before();
     __syncthreads();
-    float dot = 0.f;
-    for (int layer = 0; layer < 4 && ok; ++layer) {
-      if (tid == 0) {
-        tc_fence_after();
-        layer_mma(tmem, a_base, w_base[layer], layer == 0 ? 1 : 2);
-        mma_commit(&sm.bar_mma);
-      }
-      ok = __syncthreads_and(mbar_wait(&sm.bar_mma, mma_phase));
-      mma_phase ^= 1u;
-      tc_fence_after();
-      // epilogue: this warp's 32 rows, 32 columns at a time
-#pragma unroll 1
-      for (int c = 0; c < kNsdfWidth / 32; ++c) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
-#pragma unroll
-        for (int u = 0; u < 32; ++u) v[u] = bf16_round(fmaxf(v[u] + sm.tail.b[layer][c * 32 + u], 0.f));
-        if (layer < 3) {
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            float ch[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) ch[u] = v[q * 8 + u];
-            store_chunk(sm.a, warp * 32 + lane, c * 32 + q * 8, kTile, ch);
-          }
-        } else {
-#pragma unroll
-          for (int u = 0; u < 32; ++u) dot = fmaf(v[u], sm.tail.w5[c * 32 + u], dot);
-        }
-      }
-      fence_proxy_async();
-      tc_fence_before();
-      __syncthreads();
-    }
-    if (ok && i < n) out[i] = dot + sm.tail.b5;
   }
-  if (!ok && tid == 0 && err) atomicOr(err, kErrWaitTimeout);
+  return dot + sm.tail.b5;
+}
+
+__device__ void query_setup(QuerySmem& sm) {
+  if (threadIdx.x == 0) {
+    mbar_init(&sm.bar_w, 1);
+    mbar_init(&sm.bar_mma, 1);
+    fence_mbar_init();
+  }
+  if (threadIdx.x < 32) tmem_alloc(&sm.tmem_slot, kNsdfWidth);
+  tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, kNsdfWidth);
+  tc_fence_after();
+}
+
+__device__ void query_teardown(QuerySmem& sm, bool ok, unsigned* err) {
+  if (!ok && threadIdx.x == 0 && err) atomicOr(err, kErrWaitTimeout);
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x < 32) tmem_dealloc(sm.tmem_slot, kNsdfWidth);
+}
+
+__device__ __forceinline__ QuerySmem& query_smem(unsigned char* raw) {
+  return *reinterpret_cast<QuerySmem*>((reinterpret_cast<uintptr_t>(raw) + 1023) &
+                                       ~(uintptr_t)1023);
+}
+
+// Persistent: each CTA stages the scene's weights once, then runs 128-query
+// tiles through the network.
+__global__ void __launch_bounds__(kQueryThreads, 1)
+    nsdf_query_kernel(const unsigned char* __restrict__ blob, const float* __restrict__ pts,
+                      int n, float* __restrict__ out, unsigned* err) {
+  extern __shared__ unsigned char smem_raw[];
+  QuerySmem& sm = query_smem(smem_raw);
+  query_setup(sm);
+  uint32_t w_phase = 0, mma_phase = 0;
+  bool ok = __syncthreads_and(load_weights(sm, blob, w_phase));
+  const int tiles = (n + kTile - 1) / kTile;
+  for (int tile = blockIdx.x; ok && tile < tiles; tile += gridDim.x) {
+    const int i = tile * kTile + threadIdx.x;
+    Centred d = centre_point(sm.tail.centre[0], sm.tail.centre[1], sm.tail.centre[2],
+                             sm.tail.centre);
+    if (i < n)
+      d = centre_point(pts[3 * (size_t)i], pts[3 * (size_t)i + 1], pts[3 * (size_t)i + 2],
+                       sm.tail.centre);
+    const float v = run_tile(sm, sm.tmem_slot, d, mma_phase, ok);
+    if (ok && i < n) out[i] = v;
+  }
+  query_teardown(sm, ok, err);
+}
+
+// The step's queries: each CTA takes a contiguous run of tiles (grouped by
+// scene, so it reloads weights only where the scene changes); a tile's 128
+// rows are 4 environments x 32 sphere slots.
+__global__ void __launch_bounds__(kQueryThreads, 1) nsdf_step_kernel(const NsdfStepParams p) {
+  extern __shared__ unsigned char smem_raw[];
+  QuerySmem& sm = query_smem(smem_raw);
+  query_setup(sm);
+  uint32_t w_phase = 0, mma_phase = 0;
+  bool ok = true;
+  int loaded = -1;
+  const int t0 = (int)((long long)blockIdx.x * p.n_tiles / gridDim.x);
+  const int t1 = (int)((long long)(blockIdx.x + 1) * p.n_tiles / gridDim.x);
+  const int slot = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int t = t0; ok && t < t1; ++t) {
+    const int4 tile = p.tiles[t];
+    if (tile.x != loaded) {
+      fence_proxy_async();  // this CTA's reads of the old weights come first
+      __syncthreads();
+      ok = __syncthreads_and(load_weights(sm, p.blobs[tile.x], w_phase));
+      if (!ok) break;
+      loaded = tile.x;
+    }
+    int env = -1;
+    Centred d = centre_point(sm.tail.centre[0], sm.tail.centre[1], sm.tail.centre[2],
+                             sm.tail.centre);
+    if (slot < tile.z) {
+      env = p.perm[tile.y + slot];
+      const float4 q = p.pts[(size_t)env * 32 + lane];
+      d = centre_point(q.x, q.y, q.z, sm.tail.centre);
+    }
+    const float v = run_tile(sm, sm.tmem_slot, d, mma_phase, ok);
+    if (ok && env >= 0) p.out[(size_t)env * 32 + lane] = v;
+  }
+  query_teardown(sm, ok, p.err);
 }
 
 // Host-side packing: FP32 parameters (W1 [128][64], b1, W2 [128][128], b2,
@@ -239,6 +304,22 @@ cudaError_t nsdf_launch_query(const unsigned char* blob, const float* pts, int n
   const int grid = tiles < sms ? tiles : sms;
   if (grid > 0)
     nsdf_query_kernel<<<grid, kQueryThreads, query_smem_bytes(), s>>>(blob, pts, n, out, err);
+  return cudaGetLastError();
+}
+
+cudaError_t nsdf_launch_step(const NsdfStepParams& p, cudaStream_t s) {
+  static std::once_flag once;
+  static cudaError_t cfg = cudaSuccess;
+  std::call_once(once, [] {
+    cfg = cudaFuncSetAttribute(nsdf_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)query_smem_bytes());
+  });
+  if (cfg != cudaSuccess) return cfg;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = p.n_tiles < sms ? p.n_tiles : sms;
+  if (grid > 0) nsdf_step_kernel<<<grid, kQueryThreads, query_smem_bytes(), s>>>(p);
   return cudaGetLastError();
 }
 

@@ -175,7 +175,8 @@ __global__ void __launch_bounds__(32 * kEnvsPerBlock) physics_kernel(const Physi
   __shared__ float4 s_obj[kEnvsPerBlock][GX_MAX_OBJECTS];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int env = blockIdx.x * kEnvsPerBlock + w;
-  if (blockIdx.x == 0 && threadIdx.x == 0 && P.raster_work) *P.raster_work = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && P.raster_work && P.nsdf_pass != 1)
+    *P.raster_work = 0;
   if (env >= P.n) return;
   const int n = P.n, M = P.M;
   const DScene& S = P.scenes[P.env_scene[env]];
@@ -229,11 +230,30 @@ __global__ void __launch_bounds__(32 * kEnvsPerBlock) physics_kernel(const Physi
     r = so[held].w;
     active = true;
   }
+  if (P.nsdf_pass == 1) {  // the neural SDF is queried between the passes
+    P.nsdf_pts[(size_t)env * 32 + lane] = make_float4(c[0], c[1], c[2], active ? r : -1.f);
+    return;
+  }
   // (a5, a6) static grid and free objects (the held object is not tested)
-  bool cs = false, co = false;
+  bool cs = false, co = false, cs_grid = false;
   if (active) {
     float d;
-    cs = !grid_query(S, c[0], c[1], c[2], d) || d < r;
+    if (P.nsdf_pass == 2) {
+      // learned distance: outside the box is contact; a predicted clearance
+      // of at least the margin is free; otherwise (NaN too) the grid decides
+      const float dn = P.nsdf_d[(size_t)env * 32 + lane];
+      const bool inside = grid_contains(S, c[0], c[1], c[2]);
+      const bool trust = inside && dn - r >= P.nsdf_margin;
+      cs = !inside || (!trust && (!grid_query(S, c[0], c[1], c[2], d) || d < r));
+      if (P.nsdf_counters) {
+        cs_grid = !grid_query(S, c[0], c[1], c[2], d) || d < r;
+        atomicAdd(P.nsdf_counters + kNsdfSpheres, 1ull);
+        if (inside && !trust) atomicAdd(P.nsdf_counters + kNsdfFallbacks, 1ull);
+        if (cs != cs_grid) atomicAdd(P.nsdf_counters + kNsdfDisagree, 1ull);
+      }
+    } else {
+      cs = !grid_query(S, c[0], c[1], c[2], d) || d < r;
+    }
     for (int j = 0; j < M; ++j) {
       if (j == held) continue;
       const float4 o = so[j];
@@ -242,6 +262,10 @@ __global__ void __launch_bounds__(32 * kEnvsPerBlock) physics_kernel(const Physi
     }
   }
   const unsigned mask = __ballot_sync(kFull, active && (cs || co));
+  if (P.nsdf_pass == 2 && P.nsdf_counters) {
+    const unsigned mask_grid = __ballot_sync(kFull, active && (cs_grid || co));
+    if (lane == 0 && mask_grid != mask) atomicAdd(P.nsdf_counters + kNsdfEnvDisagree, 1ull);
+  }
   const unsigned ms = __ballot_sync(kFull, active && cs);
   const unsigned mo = __ballot_sync(kFull, active && co);
   const uint8_t flags = (ms ? 1 : 0) | (mo ? 2 : 0) | ((mask >> 30) & 1u ? 4 : 0);

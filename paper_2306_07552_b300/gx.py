@@ -29,7 +29,7 @@ SYMBOLS = ["gx_scene_set_create", "gx_scene_set_destroy", "gx_create", "gx_destr
            "gx_save_state", "gx_load_state", "gx_state_layout", "gx_phase_times",
            "gx_raster_counters", "gx_render_noalloc", "gx_nsdf_set_weights",
            "gx_nsdf_get_weights", "gx_nsdf_query", "gx_nsdf_get_master", "gx_nsdf_samples", "gx_nsdf_grad",
-           "gx_nsdf_train", "gx_last_error"]
+           "gx_nsdf_train", "gx_nsdf_counters", "gx_last_error"]
 NSDF_PARAMS = 57985
 NSDF_FREQ = 32
 RASTER_COUNTERS = ["clusters_tested", "clusters_drawn", "tris_seen", "tris_front", "tris_expand",
@@ -70,7 +70,8 @@ class GxConfig(C.Structure):
                 ("depth_fp16", C.c_int32), ("render_rgb", C.c_int32), ("n_objects", C.c_int32),
                 ("obj_radius_min", C.c_float), ("obj_radius_max", C.c_float),
                 ("seed", C.c_uint64), ("env_scene", i32p), ("raster_regions", C.c_int32),
-                ("small_tri_px", C.c_int32), ("use_graph", C.c_int32), ("profile", C.c_int32)]
+                ("small_tri_px", C.c_int32), ("use_graph", C.c_int32), ("profile", C.c_int32),
+                ("sdf_mode", C.c_int32), ("sdf_margin", C.c_float)]
 
 
 class GxOutputs(C.Structure):
@@ -132,6 +133,7 @@ def lib():
                                       vp, vp, vp]
         L.gx_nsdf_grad.argtypes = [vp, C.c_int32, vp, vp, C.c_int32, C.c_float, C.c_float, vp, vp,
                                    vp]
+        L.gx_nsdf_counters.argtypes = [vp, C.POINTER(C.c_int64)]
         L.gx_nsdf_train.argtypes = [vp, C.c_int32, C.POINTER(GxTrainParams), vp, vp]
         L.gx_last_error.argtypes = [vp]
         L.gx_last_error.restype = C.c_char_p
@@ -291,7 +293,7 @@ class Sim:
     def __init__(self, scene_set: SceneSet, robot: _inputs.Robot, n_envs: int, img=(128, 128),
                  depth_fp16=False, render_rgb=True, n_objects=40, obj_radius=(0.03, 0.06),
                  seed=1, env_scene=None, raster_regions=0, small_tri_px=0, use_graph=False,
-                 profile=0):
+                 profile=0, sdf_mode=0, sdf_margin=0.02):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("gx needs a CUDA device; there is no CPU fallback")
@@ -310,6 +312,7 @@ class Sim:
             cfg.env_scene = es.ctypes.data_as(i32p)
         cfg.raster_regions, cfg.small_tri_px, cfg.use_graph = raster_regions, small_tri_px, int(use_graph)
         cfg.profile = int(profile)
+        cfg.sdf_mode, cfg.sdf_margin = int(sdf_mode), float(sdf_margin)
         self.robot_c = robot_struct(robot)
         self.handle = C.c_void_p()
         _check(lib().gx_create(scene_set.handle, C.byref(self.robot_c), C.byref(cfg),
@@ -382,6 +385,12 @@ class Sim:
         v = (C.c_int64 * len(RASTER_COUNTERS))()
         _check(lib().gx_raster_counters(self.handle, v, len(RASTER_COUNTERS)), self.handle)
         return dict(zip(RASTER_COUNTERS, list(v)))
+
+    def nsdf_counters(self):
+        """Neural-SDF decision counters since the last call (profile bit 2 only)."""
+        v = (C.c_int64 * 4)()
+        _check(lib().gx_nsdf_counters(self.handle, v), self.handle)
+        return dict(zip(["tests", "grid_fallbacks", "disagree", "env_disagree"], list(v)))
 
     def sync(self):
         _check(lib().gx_sync(self.handle), self.handle)

@@ -49,8 +49,9 @@ class Tally:
                 f"max_pose_err={self.max_pose_err:.2e} max_depth_rel={self.max_depth_rel:.2e}")
 
 
-def check_step(orc, before, after, out, acts, envs, M, tally):
-    """Physics parity of one step for the listed environments."""
+def check_step(orc, before, after, out, acts, envs, M, tally, step_fn=None):
+    """Physics parity of one step for the listed environments.  step_fn(st,
+    action) replaces the oracle's grid step (e.g. with its neural-SDF rule)."""
     mask = out["contact_mask"].cpu().numpy().view(np.uint32)
     flags = out["contact_flags"].cpu().numpy()
     event = out["event"].cpu().numpy()
@@ -59,7 +60,7 @@ def check_step(orc, before, after, out, acts, envs, M, tally):
     objo = out["obj_pos"].cpu().numpy()
     for e in envs:
         st = oracle_state(before, e, M)
-        o = orc.step(st, acts[e])
+        o = step_fn(st, acts[e]) if step_fn else orc.step(st, acts[e])
         tally.envs += 1
         if o.near_band:
             tally.near_band += 1
