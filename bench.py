@@ -112,16 +112,22 @@ def golden(name):
     return json.load(open(p)) if os.path.exists(p) else None
 
 
+# Workloads whose views are drawn from another workload's scenes and camera
+# statistics (the static test differs, the rendering work per view does not).
+SAME_VIEWS = {"apartments4096_nsdf": "apartments4096", "uneven16384_nsdf": "uneven8192"}
+
+
 def raster_work(workload):
     """Per-view triangles set up and fragments covered, measured by the
     oracle on a sample of the workload (written by oracle/raster_work.py)."""
-    return golden(f"raster_work_{workload.split('-')[0]}.json")
+    base = workload.split('-')[0]
+    return golden(f"raster_work_{SAME_VIEWS.get(base, base)}.json")
 
 
 def kernel_traffic(workload):
     """DRAM bytes per rasteriser launch scaled to the full workload from an
     ncu capture of a smaller case; None once the rasteriser source changed."""
-    p = os.path.join(ROOT, "profiles", f"raster_{workload}_traffic.json")
+    p = os.path.join(ROOT, "profiles", f"raster_{SAME_VIEWS.get(workload, workload)}_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
@@ -213,6 +219,50 @@ def cpu_baseline(w, scenes, seconds):
                       f"{len(sample_envs)} envs of {w.name}, {dt:.1f} s, one thread, FP64"}
 
 
+# Neural SDF: algorithmic FLOPs per training sample (forward 64x128 +
+# 3 x 128x128 + 128 MACs, backward-data 3 x 128x128, weight gradient 64x128 +
+# 3 x 128x128; 2 FLOPs per MAC) and per query (forward only).
+NSDF_TRAIN_FLOP = 2 * ((64 * 128 + 3 * 128 * 128 + 128) + 3 * 128 * 128 + (64 * 128 + 3 * 128 * 128))
+NSDF_QUERY_FLOP = 2 * (64 * 128 + 3 * 128 * 128 + 128)
+NSDF_BATCH = 65536
+NSDF_BLOB_BYTES = 114688 + 2976
+
+
+def train_scenes(ss, w, scenes_used):
+    """Trains every used scene's network (untimed for the step metric);
+    returns the training measurement.  The per-step time is the difference
+    of a full and a short run on the first scene, so sample generation and
+    workspace allocation cancel out."""
+    B = I.fourier_matrix(w.nsdf_seed)
+    P0 = I.nsdf_init(w.nsdf_seed)
+    first = scenes_used[0]
+    ss.nsdf_set_weights(first, B, P0)
+    short = max(w.nsdf_steps // 4, 1)
+    t0 = time.perf_counter()
+    ss.nsdf_train(first, n_samples=w.nsdf_samples, batch=NSDF_BATCH, steps=short,
+                  seed=w.nsdf_seed + first)
+    t_short = time.perf_counter() - t0
+    losses, total = [], 0.0
+    for s in scenes_used:
+        ss.nsdf_set_weights(s, B, P0)
+        t0 = time.perf_counter()
+        lo = ss.nsdf_train(s, n_samples=w.nsdf_samples, batch=NSDF_BATCH, steps=w.nsdf_steps,
+                           seed=w.nsdf_seed + s)
+        dt = time.perf_counter() - t0
+        total += dt
+        if s == first:
+            t_full = dt
+        losses.append(float(np.mean(lo[-20:])))
+    step_ms = (t_full - t_short) / (w.nsdf_steps - short) * 1e3
+    tflops = NSDF_BATCH * NSDF_TRAIN_FLOP / (step_ms / 1e3) / 1e12
+    return {"scenes": len(scenes_used), "samples_per_scene": w.nsdf_samples,
+            "batch": NSDF_BATCH, "adam_steps": w.nsdf_steps, "train_s_total": total,
+            "step_ms": step_ms, "tflops": tflops,
+            "final_loss_mean_m": float(np.mean(losses)),
+            "flop_basis": f"{NSDF_TRAIN_FLOP} FLOP per sample (forward, backward-data, "
+                          f"weight gradient)"}
+
+
 def config_of(w):
     return {"workload": w.name, "envs": w.n_envs, "scenes": w.n_scenes,
             "triangles_per_scene": f"{w.tri_range[0]}-{w.tri_range[1]} {w.tri_dist}",
@@ -220,7 +270,9 @@ def config_of(w):
             "depth": "f16" if w.depth_fp16 else "f32", "rgb8": w.rgb, "actions": w.action_dist,
             "resets": (f"{w.reset_every}-step episodes, staggered" if w.reset_every
                        else f"Bernoulli p={w.reset_prob} per env-step"),
-            "l2": "no flush: each step writes more observation bytes than L2 holds"}
+            "l2": "no flush: each step writes more observation bytes than L2 holds",
+            "static_test": (f"neural SDF, grid below {w.sdf_margin} m predicted clearance"
+                            if w.sdf == "neural" else "distance grid")}
 
 
 def run_reference(args, w, rank, world):
@@ -308,10 +360,16 @@ def main():
     n = w.n_envs
     scenes = I.make_scenes(w)
     ss = gx.SceneSet(scenes)
-    sim = gx.Sim(ss, I.fetch_like_robot(), n, img=(w.img, w.img), depth_fp16=w.depth_fp16,
-                 render_rgb=w.rgb, n_objects=w.n_objects, obj_radius=w.obj_radius,
-                 seed=rank_seeds(w, rank)[0], profile=0 if args.graph else 1,
-                 use_graph=args.graph, small_tri_px=args.small_px)
+    neural = w.sdf == "neural"
+    nsdf = None
+    if neural:
+        nsdf = train_scenes(ss, w, sorted(set(int(x) for x in I.env_scene_map(n, w.n_scenes))))
+    sim_kw = dict(img=(w.img, w.img), depth_fp16=w.depth_fp16, render_rgb=w.rgb,
+                  n_objects=w.n_objects, obj_radius=w.obj_radius, seed=rank_seeds(w, rank)[0],
+                  small_tri_px=args.small_px)
+    sim = gx.Sim(ss, I.fetch_like_robot(), n, profile=0 if args.graph else 1,
+                 use_graph=args.graph, sdf_mode=1 if neural else 0, sdf_margin=w.sdf_margin,
+                 **sim_kw)
     total = args.warmup + args.steps
     acts = torch.from_numpy(I.make_actions(total, n, w.action_dist,
                                            seed=rank_seeds(w, rank)[1])).cuda()
@@ -351,15 +409,63 @@ def main():
         with torch.cuda.stream(stream):
             for t in range(args.warmup, total):
                 one(t)
-                launches += 3
+                launches += 5 if neural else 3
         e1.record(stream)
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
     ms = e0.elapsed_time(e1)
-    phase_ms, phase_n = sim.phase_times() if not args.graph else ([0, 0, 0], [0, 0, 0])
+    phase_ms, phase_n = sim.phase_times() if not args.graph else ([0] * 4, [0] * 4)
     dev_err = sim.device_error()
     value, ms = job_value(dist, n, args.steps, ms)
+    if neural:
+        # the grid form of the same workload, timed the same way, and the
+        # neural form's decisions counted against the grid-only rule
+        g = gx.Sim(ss, I.fetch_like_robot(), n, profile=1, **sim_kw)
+        with torch.cuda.stream(stream):
+            g.reset(stream=stream)
+            for t in range(args.warmup):
+                abuf.copy_(acts[t])
+                mbuf.copy_(mask_at(t))
+                g.reset(mbuf, stream=stream)
+                g.step(abuf, stream=stream)
+        torch.cuda.synchronize()
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        with torch.cuda.stream(stream):
+            for t in range(args.warmup, total):
+                abuf.copy_(acts[t])
+                mbuf.copy_(mask_at(t))
+                g.reset(mbuf, stream=stream)
+                g.step(abuf, stream=stream)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        grid_value, _ = job_value(dist, n, args.steps, g0.elapsed_time(g1))
+        g.close()
+        c = gx.Sim(ss, I.fetch_like_robot(), n, profile=4, sdf_mode=1, sdf_margin=w.sdf_margin,
+                   **sim_kw)
+        c.reset()
+        for t in range(min(args.steps, 50)):
+            c.reset(mask_at(t))
+            c.step(acts[t])
+        cnt = c.nsdf_counters()
+        c.close()
+        grid_bytes = [int(np.prod(sc.grid_dims)) * 4 for sc in scenes]
+        q_ms = phase_ms[3] / max(phase_n[3], 1)
+        nsdf.update({
+            "grid_form_value": grid_value, "neural_over_grid": value / grid_value,
+            "query_ms_per_step": q_ms,
+            "query_tflops": n * 32 * NSDF_QUERY_FLOP / (q_ms / 1e3) / 1e12 if q_ms else None,
+            "query_flop_basis": f"{NSDF_QUERY_FLOP} FLOP per query, 32 query rows per env "
+                                f"(31 used)",
+            "decisions": cnt,
+            "decisions_differing_from_grid": cnt["disagree"] / max(cnt["tests"], 1),
+            "grid_consulted": cnt["grid_fallbacks"] / max(cnt["tests"], 1),
+            "env_steps_differing": cnt["env_disagree"] / max(min(args.steps, 50) * n, 1),
+            "bytes_per_scene": {"grid_mean": float(np.mean(grid_bytes)),
+                                "network": NSDF_BLOB_BYTES},
+            "note": "the grid stays resident: it decides every test below the margin"})
 
     # end to end through the C ABI with host buffers (pinned): actions in,
     # every output back (images included), copies inside the timed region
@@ -420,7 +526,9 @@ def main():
         "data": "synthetic (procedural apartments standing in for ReplicaCAD; see DESIGN.md)",
         "config": config_of(w),
         "phases_ms_per_launch": {k: phase_ms[i] / max(phase_n[i], 1)
-                                 for i, k in enumerate(["physics", "raster", "reset"])},
+                                 for i, k in enumerate(["physics", "raster", "reset",
+                                                        "nsdf_query"])},
+        "nsdf": nsdf,
         "raster_counters_per_view": counters,
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches, "clocks": clocks, "device_error": dev_err,

@@ -215,9 +215,10 @@ gx_status gx_load_state(gx_ctx* ctx, const void* host, size_t bytes);
 gx_status gx_state_layout(const gx_ctx* ctx, size_t offsets[10]);
 
 /* Per-kernel device time recorded since the previous call when the context
- * was created with profile bit 0 set: ms[0] physics, ms[1] rasteriser, ms[2]
- * reset; launches[k] the number of timed launches.  Waits for the device. */
-gx_status gx_phase_times(gx_ctx* ctx, double ms[3], int64_t launches[3]);
+ * was created with profile bit 0 set: ms[0] physics (both passes when
+ * sdf_mode is 1), ms[1] rasteriser, ms[2] reset, ms[3] neural-SDF queries;
+ * launches[k] the number of timed launches.  Waits for the device. */
+gx_status gx_phase_times(gx_ctx* ctx, double ms[4], int64_t launches[4]);
 
 /* Rasteriser work counters accumulated since the previous call (contexts
  * created with profile bit 1), then cleared: clusters tested, clusters drawn,

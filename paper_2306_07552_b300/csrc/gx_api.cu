@@ -48,10 +48,11 @@ struct gx_ctx {
   gx_outputs g_out{};
   // profiling: event triples per timed launch group, read back lazily
   std::vector<cudaEvent_t> prof_ev;
-  std::vector<int> prof_kind;   // 0 = step (physics, raster), 1 = reset
+  std::vector<int> prof_kind;   // 0 = step, 1 = reset, 2 = step with neural-SDF queries
+  std::vector<size_t> prof_at;  // first event of each group
   size_t prof_used = 0;
-  double prof_ms[3] = {0, 0, 0};
-  int64_t prof_n[3] = {0, 0, 0};
+  double prof_ms[4] = {0, 0, 0, 0};
+  int64_t prof_n[4] = {0, 0, 0, 0};
   unsigned long long* d_counters = nullptr;
   // neural SDF in the static test
   float4* d_nsdf_pts = nullptr;
@@ -139,24 +140,28 @@ bool same_outputs(const gx_outputs& a, const gx_outputs& b) {
   return std::memcmp(&a, &b, sizeof(gx_outputs)) == 0;
 }
 
-// Three events for the next timed launch group (nullptr once the pool is
-// full; gx_phase_times drains it).
+// Events for the next timed launch group: 5 for a step (start, after
+// physics pass 1, after the neural-SDF queries, after physics, after the
+// rasteriser), 2 for a reset.  nullptr once the pool is full;
+// gx_phase_times drains it.
 cudaEvent_t* prof_slot(gx_ctx* c, int kind) {
-  const size_t kMax = 3 * 8192;
-  if (c->prof_used + 3 > kMax) return nullptr;
-  while (c->prof_ev.size() < c->prof_used + 3) {
+  const size_t kMax = 5 * 8192, k = kind == 1 ? 2 : 5;
+  if (c->prof_used + k > kMax) return nullptr;
+  while (c->prof_ev.size() < c->prof_used + k) {
     cudaEvent_t e;
     if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
     c->prof_ev.push_back(e);
   }
   c->prof_kind.push_back(kind);
+  c->prof_at.push_back(c->prof_used);
   cudaEvent_t* r = &c->prof_ev[c->prof_used];
-  c->prof_used += 3;
+  c->prof_used += k;
   return r;
 }
 
 void enqueue_step(gx_ctx* c, const float* actions, const gx_outputs& out, cudaStream_t s) {
-  cudaEvent_t* ev = (c->cfg.profile & 1) ? prof_slot(c, 0) : nullptr;
+  const bool neural = c->cfg.sdf_mode == 1;
+  cudaEvent_t* ev = (c->cfg.profile & 1) ? prof_slot(c, neural ? 2 : 0) : nullptr;
   if (ev) cudaEventRecord(ev[0], s);
   PhysicsParams pp{};
   pp.n = c->n;
@@ -177,6 +182,7 @@ void enqueue_step(gx_ctx* c, const float* actions, const gx_outputs& out, cudaSt
     pp.nsdf_counters = c->d_nsdf_counters;
     pp.nsdf_pass = 1;
     launch_physics(pp, s);
+    if (ev) cudaEventRecord(ev[1], s);
     NsdfStepParams np{};
     np.blobs = c->d_nsdf_blobs;
     np.tiles = c->d_nsdf_tiles;
@@ -186,10 +192,11 @@ void enqueue_step(gx_ctx* c, const float* actions, const gx_outputs& out, cudaSt
     np.out = c->d_nsdf_d;
     np.err = c->d_err;
     nsdf_launch_step(np, s);
+    if (ev) cudaEventRecord(ev[2], s);
     pp.nsdf_pass = 2;
   }
   launch_physics(pp, s);
-  if (ev) cudaEventRecord(ev[1], s);
+  if (ev) cudaEventRecord(ev[3], s);
   RasterParams rp{};
   rp.n = c->n;
   rp.M = c->M;
@@ -215,7 +222,7 @@ void enqueue_step(gx_ctx* c, const float* actions, const gx_outputs& out, cudaSt
   rp.err = c->d_err;
   rp.counters = (c->cfg.profile & 2) ? c->d_counters : nullptr;
   launch_raster(rp, s);
-  if (ev) cudaEventRecord(ev[2], s);
+  if (ev) cudaEventRecord(ev[4], s);
 }
 
 }  // namespace
@@ -524,10 +531,7 @@ extern "C" gx_status gx_reset(gx_ctx* x, const uint8_t* env_mask, void* stream) 
   cudaEvent_t* ev = (x->cfg.profile & 1) ? prof_slot(x, 1) : nullptr;
   if (ev) cudaEventRecord(ev[0], s);
   launch_reset(rp, s);
-  if (ev) {
-    cudaEventRecord(ev[1], s);
-    cudaEventRecord(ev[2], s);
-  }
+  if (ev) cudaEventRecord(ev[1], s);
   CK(x, cudaGetLastError());
   return post_error_copy(x, s);
 }
@@ -644,27 +648,39 @@ extern "C" gx_status gx_state_layout(const gx_ctx* x, size_t offsets[10]) {
   return GX_OK;
 }
 
-extern "C" gx_status gx_phase_times(gx_ctx* x, double ms[3], int64_t launches[3]) {
+extern "C" gx_status gx_phase_times(gx_ctx* x, double ms[4], int64_t launches[4]) {
   if (!x || !ms || !launches) return fail(x, GX_EINVAL, "gx_phase_times: NULL argument");
   CK(x, cudaDeviceSynchronize());
+  auto el = [&](cudaEvent_t a, cudaEvent_t b, float* out) { return cudaEventElapsedTime(out, a, b); };
   for (size_t g = 0; g < x->prof_kind.size(); ++g) {
-    cudaEvent_t* e = &x->prof_ev[3 * g];
-    float a = 0.f, b = 0.f;
-    CK(x, cudaEventElapsedTime(&a, e[0], e[1]));
-    CK(x, cudaEventElapsedTime(&b, e[1], e[2]));
-    if (x->prof_kind[g] == 0) {
-      x->prof_ms[0] += a;
-      x->prof_ms[1] += b;
-      x->prof_n[0]++;
-      x->prof_n[1]++;
-    } else {
+    cudaEvent_t* e = &x->prof_ev[x->prof_at[g]];
+    float a = 0.f, b = 0.f, q = 0.f, r = 0.f;
+    if (x->prof_kind[g] == 1) {
+      CK(x, el(e[0], e[1], &a));
       x->prof_ms[2] += a;
       x->prof_n[2]++;
+      continue;
     }
+    if (x->prof_kind[g] == 2) {     // physics = both passes, queries separately
+      CK(x, el(e[0], e[1], &a));
+      CK(x, el(e[1], e[2], &q));
+      CK(x, el(e[2], e[3], &b));
+      a += b;
+      x->prof_ms[3] += q;
+      x->prof_n[3]++;
+    } else {
+      CK(x, el(e[0], e[3], &a));
+    }
+    CK(x, el(e[3], e[4], &r));
+    x->prof_ms[0] += a;
+    x->prof_ms[1] += r;
+    x->prof_n[0]++;
+    x->prof_n[1]++;
   }
   x->prof_kind.clear();
+  x->prof_at.clear();
   x->prof_used = 0;
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < 4; ++k) {
     ms[k] = x->prof_ms[k];
     launches[k] = x->prof_n[k];
     x->prof_ms[k] = 0;

@@ -374,9 +374,10 @@ class Sim:
         return host_out
 
     def phase_times(self):
-        """(ms, launches) per kernel since the last call: physics, raster, reset."""
-        ms = (C.c_double * 3)()
-        n = (C.c_int64 * 3)()
+        """(ms, launches) per kernel since the last call: physics, raster, reset,
+        neural-SDF queries."""
+        ms = (C.c_double * 4)()
+        n = (C.c_int64 * 4)()
         _check(lib().gx_phase_times(self.handle, ms, n), self.handle)
         return list(ms), list(n)
 
