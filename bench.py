@@ -336,6 +336,8 @@ def main():
     ap.add_argument("--envs", type=int, default=0, help="smaller batch (profiling runs)")
     ap.add_argument("--scenes", type=int, default=0, help="fewer scenes (profiling runs)")
     ap.add_argument("--small-px", type=int, default=0, help="expansion bbox limit (0: auto)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default rasteriser setting instead of timing candidates")
     ap.add_argument("--graph", action="store_true",
                     help="replay the step as a CUDA graph (no per-kernel timing)")
     args = ap.parse_args()
@@ -392,10 +394,15 @@ def main():
         sim.reset(mbuf, stream=stream)
         sim.step(abuf, stream=stream)
 
+    tune = None
     with torch.cuda.stream(stream):
         sim.reset(stream=stream)
         for t in range(args.warmup):
             one(t)
+        if not args.no_autotune:
+            # rasteriser setting timed on this batch's own state (restored)
+            abuf.copy_(acts[args.warmup - 1])
+            tune = sim.autotune(abuf, steps=3, stream=stream)
     torch.cuda.synchronize()
     if not args.graph:
         sim.phase_times()
@@ -529,6 +536,7 @@ def main():
                                  for i, k in enumerate(["physics", "raster", "reset",
                                                         "nsdf_query"])},
         "nsdf": nsdf,
+        "autotune": tune,
         "raster_counters_per_view": counters,
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches, "clocks": clocks, "device_error": dev_err,

@@ -228,6 +228,28 @@ gx_status gx_phase_times(gx_ctx* ctx, double ms[4], int64_t launches[4]);
  * GX_ESTATE when the context does not count. */
 gx_status gx_raster_counters(gx_ctx* ctx, int64_t* out, int32_t n);
 
+/* Rasteriser settings chosen by gx_autotune. */
+typedef struct {
+  int32_t small_tri_px;           /* as gx_config.small_tri_px (0: default)      */
+  int32_t order_costliest_first;  /* 1: environments of the scenes with the most
+                                     triangle clusters are rendered first       */
+  int32_t raster_ctas;            /* persistent CTAs launched                    */
+  float ms_per_step;              /* measured step time with these settings      */
+} gx_tune_result;
+
+/* Times the step on this context's own state under each candidate rasteriser
+ * setting -- expansion limit small_tri_px in {0, 256, 96, 48}, work order
+ * {index, costliest scene first}, resident CTAs per SM {occupancy,
+ * occupancy - 1} -- for `steps` steps each (plus one warm-up), restoring the
+ * state after every candidate, and keeps the fastest (written to *best when
+ * not NULL).  The outputs are overwritten; the state is left as before the
+ * call.  actions: device [n][11], reused for every step.  Allocates one copy
+ * of the state; waits for the stream.  The context starts with the index
+ * order, or the costliest-first order when its scenes' cluster counts differ
+ * by more than 1.5x. */
+gx_status gx_autotune(gx_ctx* ctx, const float* actions, const gx_outputs* out, int32_t steps,
+                      gx_tune_result* best, void* stream);
+
 /* Neural-SDF decision counters accumulated since the previous call (profile
  * bit 2):
  * out[0] static tests made, out[1] of which the grid decided, out[2]

@@ -26,6 +26,10 @@ struct gx_ctx {
   const gx_scene_set* set = nullptr;
   gx_config cfg{};
   int n = 0, M = 0, big_px = 0, n_slots = 0;
+  int raster_ctas = 0;                 // CTAs launched (<= n_slots), set by the autotuner
+  int order_mode = 0;                  // 0: index order, 1: costliest scene first
+  int* d_order = nullptr;              // environments, costliest scene first
+  int sms = 0;
   unsigned long long* d_fb = nullptr;  // rasteriser framebuffer slots
   int* d_raster_work = nullptr;
   float near_ = 0.05f;
@@ -179,7 +183,7 @@ void enqueue_step(gx_ctx* c, const float* actions, const gx_outputs& out, cudaSt
     pp.nsdf_pts = c->d_nsdf_pts;
     pp.nsdf_d = c->d_nsdf_d;
     pp.nsdf_margin = c->cfg.sdf_margin;
-    pp.nsdf_counters = c->d_nsdf_counters;
+    pp.nsdf_counters = (c->cfg.profile & 4) ? c->d_nsdf_counters : nullptr;
     pp.nsdf_pass = 1;
     launch_physics(pp, s);
     if (ev) cudaEventRecord(ev[1], s);
@@ -204,7 +208,8 @@ void enqueue_step(gx_ctx* c, const float* actions, const gx_outputs& out, cudaSt
   rp.H = c->cfg.img_h;
   rp.big_px = c->big_px;
   rp.fb_slots = c->d_fb;
-  rp.n_slots = c->n_slots;
+  rp.n_slots = c->raster_ctas;
+  rp.order = c->order_mode ? c->d_order : nullptr;
   rp.work = c->d_raster_work;
   rp.scenes = c->set->d_scenes;
   rp.env_scene = c->d_env_scene;
@@ -385,6 +390,12 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
   if ((e = raster_configure(&x->n_slots)) != cudaSuccess) return bail(e, "raster config");
   if ((e = reset_configure()) != cudaSuccess) return bail(e, "reset config");
   if (x->n_slots > x->n) x->n_slots = x->n;
+  x->raster_ctas = x->n_slots;
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&x->sms, cudaDevAttrMultiProcessorCount, dev);
+  }
   {
     // one framebuffer slot per resident rasteriser CTA, all keys "empty"
     const size_t fb_bytes = (size_t)x->n_slots * c.img_w * c.img_h * 8;
@@ -437,6 +448,25 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
   *x->h_err = 0;
   if ((e = cudaEventCreateWithFlags(&x->ev_err, cudaEventDisableTiming)) != cudaSuccess)
     return bail(e, "event");
+  {
+    // rasteriser work order: environments of the costliest scenes (most
+    // triangle clusters) first, so the last CTAs to finish hold small items;
+    // on by default when scene sizes differ by more than 1.5x
+    std::vector<int> ord(x->n);
+    for (int i = 0; i < x->n; ++i) ord[i] = i;
+    const std::vector<int>& ms = set->meshlets_per_scene;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return ms[es[a]] > ms[es[b]]; });
+    int lo = 1 << 30, hi = 0;
+    for (int i = 0; i < x->n; ++i) {
+      lo = std::min(lo, ms[es[i]]);
+      hi = std::max(hi, ms[es[i]]);
+    }
+    x->order_mode = hi > 1.5 * lo ? 1 : 0;
+    if ((e = cudaMalloc(&x->d_order, n * sizeof(int))) != cudaSuccess ||
+        (e = cudaMemcpy(x->d_order, ord.data(), n * sizeof(int), cudaMemcpyHostToDevice)) !=
+            cudaSuccess)
+      return bail(e, "work order");
+  }
   if (c.sdf_mode == 1) {
     // environments grouped by scene; tiles of up to 4 that share a scene
     std::vector<int> perm(x->n);
@@ -499,6 +529,7 @@ extern "C" void gx_destroy(gx_ctx* x) {
   if (x->h_err) cudaFreeHost(x->h_err);
   for (cudaEvent_t e : x->prof_ev) cudaEventDestroy(e);
   cudaFree(x->d_counters);
+  cudaFree(x->d_order);
   cudaFree(x->d_nsdf_pts);
   cudaFree(x->d_nsdf_d);
   cudaFree(x->d_nsdf_tiles);
@@ -698,6 +729,74 @@ extern "C" gx_status gx_raster_counters(gx_ctx* x, int64_t* out, int32_t n) {
   CK(x, cudaMemset(x->d_counters, 0, sizeof(h)));
   for (int k = 0; k < n; ++k) out[k] = k < kRasterCounters ? (int64_t)h[k] : 0;
   return GX_OK;
+}
+
+extern "C" gx_status gx_autotune(gx_ctx* x, const float* actions, const gx_outputs* out,
+                                 int32_t steps, gx_tune_result* best, void* stream) {
+  if (!x || !actions || !out || !out->depth || steps < 1)
+    return fail(x, GX_EINVAL, "gx_autotune: bad argument");
+  if (x->cfg.render_rgb && !out->rgb) return fail(x, GX_EINVAL, "gx_autotune: render_rgb needs rgb");
+  gx_status st = poll_device_error(x, false);
+  if (st != GX_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  // the candidates run from the same state, restored after each one
+  void* saved = nullptr;
+  CK(x, cudaMalloc(&saved, x->state_bytes));
+  auto release = [&] { cudaFree(saved); };
+  if (cudaMemcpyAsync(saved, x->d_state, x->state_bytes, cudaMemcpyDeviceToDevice, s) !=
+      cudaSuccess) {
+    release();
+    return fail(x, GX_ECUDA, "gx_autotune: state copy failed");
+  }
+  const int per_sm = std::max(1, x->n_slots / std::max(1, x->sms));
+  const int px[4] = {0, 256, 96, 48};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int saved_profile = x->cfg.profile;
+  x->cfg.profile = 0;  // no per-kernel events inside the candidates
+  gx_tune_result b{};
+  b.ms_per_step = 1e30f;
+  cudaError_t err = cudaSuccess;
+  for (int ci = 0; ci < 4 && err == cudaSuccess; ++ci)
+    for (int order = 0; order < 2 && err == cudaSuccess; ++order)
+      for (int k = 0; k < 2 && err == cudaSuccess; ++k) {
+        const int ctas = std::min(x->n, std::max(1, per_sm - k) * x->sms);
+        if (k == 1 && per_sm == 1) continue;
+        x->big_px = px[ci] > 0 ? px[ci] : (1 << 30);
+        x->order_mode = order;
+        x->raster_ctas = std::min(ctas, x->n_slots);
+        enqueue_step(x, actions, *out, s);  // warm-up
+        cudaEventRecord(e0, s);
+        for (int t = 0; t < steps; ++t) enqueue_step(x, actions, *out, s);
+        cudaEventRecord(e1, s);
+        err = cudaMemcpyAsync(x->d_state, saved, x->state_bytes, cudaMemcpyDeviceToDevice, s);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        if (err == cudaSuccess && ms / steps < b.ms_per_step) {
+          b.ms_per_step = ms / steps;
+          b.small_tri_px = px[ci];
+          b.order_costliest_first = order;
+          b.raster_ctas = x->raster_ctas;
+        }
+      }
+  x->cfg.profile = saved_profile;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  release();
+  if (err != cudaSuccess) return fail(x, GX_ECUDA, "gx_autotune: %s", cudaGetErrorString(err));
+  x->big_px = b.small_tri_px > 0 ? b.small_tri_px : (1 << 30);
+  x->order_mode = b.order_costliest_first;
+  x->raster_ctas = b.raster_ctas;
+  x->cfg.small_tri_px = b.small_tri_px;
+  if (x->gexec) {  // a captured step holds the old settings
+    cudaGraphExecDestroy(x->gexec);
+    x->gexec = nullptr;
+  }
+  if (best) *best = b;
+  return poll_device_error(x, true);
 }
 
 extern "C" gx_status gx_nsdf_counters(gx_ctx* x, int64_t out[4]) {

@@ -123,6 +123,7 @@ struct RasterParams {
   unsigned long long* fb_slots;  // [n_slots][H][W] keys, all ~0 between launches
   int n_slots;                   // = grid size
   int* work;                     // environment counter, zeroed before each launch
+  const int* order;              // optional: k-th environment to render (costliest first)
   const DScene* scenes;
   const int* env_scene;
   const float* cam;        // [n][12]

@@ -499,7 +499,10 @@ __global__ void __launch_bounds__(kThreads, kRasterMinBlocks) raster_kernel(cons
   bool dead = false;  // a wait gave up: this warp stops using its buffers
 
   for (;;) {
-    if (tid == 0) ctr[0] = atomicAdd(P.work, 1);
+    if (tid == 0) {
+      const int k = atomicAdd(P.work, 1);
+      ctr[0] = (k < P.n && P.order) ? P.order[k] : k;
+    }
     __syncthreads();
     const int env = ctr[0];
     if (env >= P.n) break;
@@ -695,7 +698,7 @@ cudaError_t raster_configure(int* slots) {
 
 void launch_raster(const RasterParams& p, cudaStream_t s) {
   const size_t smem = raster_smem_bytes();
-  const int grid = p.n < p.n_slots ? p.n : p.n_slots;
+  const int grid = p.n < p.n_slots ? p.n : p.n_slots;  // n_slots: CTAs to launch
   if (p.counters)
     raster_kernel<true><<<grid, kThreads, smem, s>>>(p);
   else

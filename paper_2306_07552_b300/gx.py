@@ -29,7 +29,7 @@ SYMBOLS = ["gx_scene_set_create", "gx_scene_set_destroy", "gx_create", "gx_destr
            "gx_save_state", "gx_load_state", "gx_state_layout", "gx_phase_times",
            "gx_raster_counters", "gx_render_noalloc", "gx_nsdf_set_weights",
            "gx_nsdf_get_weights", "gx_nsdf_query", "gx_nsdf_get_master", "gx_nsdf_samples", "gx_nsdf_grad",
-           "gx_nsdf_train", "gx_nsdf_counters", "gx_last_error"]
+           "gx_nsdf_train", "gx_nsdf_counters", "gx_autotune", "gx_last_error"]
 NSDF_PARAMS = 57985
 NSDF_FREQ = 32
 RASTER_COUNTERS = ["clusters_tested", "clusters_drawn", "tris_seen", "tris_front", "tris_expand",
@@ -87,6 +87,11 @@ class GxTrainParams(C.Structure):
                 ("near_band", C.c_float), ("seed", C.c_uint64)]
 
 
+class GxTuneResult(C.Structure):
+    _fields_ = [("small_tri_px", C.c_int32), ("order_costliest_first", C.c_int32),
+                ("raster_ctas", C.c_int32), ("ms_per_step", C.c_float)]
+
+
 class GxError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"gx status {status}: {msg}")
@@ -134,6 +139,7 @@ def lib():
         L.gx_nsdf_grad.argtypes = [vp, C.c_int32, vp, vp, C.c_int32, C.c_float, C.c_float, vp, vp,
                                    vp]
         L.gx_nsdf_counters.argtypes = [vp, C.POINTER(C.c_int64)]
+        L.gx_autotune.argtypes = [vp, vp, P(GxOutputs), C.c_int32, P(GxTuneResult), vp]
         L.gx_nsdf_train.argtypes = [vp, C.c_int32, C.POINTER(GxTrainParams), vp, vp]
         L.gx_last_error.argtypes = [vp]
         L.gx_last_error.restype = C.c_char_p
@@ -386,6 +392,16 @@ class Sim:
         v = (C.c_int64 * len(RASTER_COUNTERS))()
         _check(lib().gx_raster_counters(self.handle, v, len(RASTER_COUNTERS)), self.handle)
         return dict(zip(RASTER_COUNTERS, list(v)))
+
+    def autotune(self, actions, steps=5, stream=None):
+        """Picks the fastest rasteriser setting on this batch's own state
+        (state restored afterwards); returns the chosen setting."""
+        r = GxTuneResult()
+        _check(lib().gx_autotune(self.handle, C.c_void_p(actions.data_ptr()),
+                                 C.byref(self._outs), int(steps), C.byref(r),
+                                 self._stream(stream)), self.handle)
+        return {"small_tri_px": r.small_tri_px, "order_costliest_first": r.order_costliest_first,
+                "raster_ctas": r.raster_ctas, "ms_per_step": r.ms_per_step}
 
     def nsdf_counters(self):
         """Neural-SDF decision counters since the last call (profile bit 2 only)."""
