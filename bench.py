@@ -188,6 +188,65 @@ def work_counters(ss, w, acts, mask_at, steps):
     return {k: v / (steps * w.n_envs) for k, v in c.items()}
 
 
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def _oracle_worker(args):
+    """One host process: the oracle on its own disjoint set of environments
+    for `seconds` of wall time; returns env-steps done."""
+    wname, sample_envs, seconds = args
+    w = I.WORKLOADS[wname]
+    scenes = {}
+    env_scene = I.env_scene_map(w.n_envs, w.n_scenes)
+    targets = I.scene_tri_targets(w)
+    import oracle as O
+    robot = I.fetch_like_robot()
+    states = []
+    for e in sample_envs:
+        s = int(env_scene[e])
+        if s not in scenes:
+            sc = (I.room_scene(w.scene_seed + s, targets[s], grid_h=w.grid_h)
+                  if w.scene_kind == "room" else
+                  I.apartment_scene(w.scene_seed + s, targets[s], grid_h=w.grid_h))
+            scenes[s] = O.Oracle(robot, sc, I.icosahedron(), I.object_colors(64))
+        st = O.Oracle.make_state((0, 0, 0), np.zeros(7))
+        scenes[s].reset(st, w.reset_seed, e, w.n_objects, *w.obj_radius)
+        states.append((scenes[s], st))
+    acts = I.make_actions(200, len(sample_envs), w.action_dist, seed=w.action_seed + 1)
+    t0 = time.perf_counter()
+    done = 0
+    while time.perf_counter() - t0 < seconds:
+        k = done // len(sample_envs)
+        for i, (orc, st) in enumerate(states):
+            orc.step(st, acts[k % 200, i])
+            orc.render(st, w.img, w.img)
+            done += 1
+    return done, time.perf_counter() - t0
+
+
+def cpu_all_cores(w, seconds):
+    """One oracle process per host core over disjoint environments (the
+    environments are independent), started with spawn; aggregate rate."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    envs = np.linspace(0, w.n_envs - 1, 2 * cores).astype(int)
+    jobs = [(w.name.split("-")[0], [int(envs[2 * c]), int(envs[2 * c + 1])], seconds)
+            for c in range(cores)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_worker, jobs)
+    rate = sum(d / t for d, t in res)
+    return {"value": rate, "unit": UNIT, "cores": cores,
+            "sample": f"{cores} processes x 2 envs each (disjoint), {seconds:.0f} s each, "
+                      f"{sum(d for d, _ in res)} env-steps in all"}
+
+
 def cpu_baseline(w, scenes, seconds):
     """The FP64 oracle on the host, single-threaded, on a bounded sample of
     the same workload: 8 envs spread over the scenes, reset, then stepped
@@ -216,7 +275,8 @@ def cpu_baseline(w, scenes, seconds):
     dt = time.perf_counter() - t0
     return {"value": done / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{done} env-steps (physics + {w.img}x{w.img} render) over "
-                      f"{len(sample_envs)} envs of {w.name}, {dt:.1f} s, one thread, FP64"}
+                      f"{len(sample_envs)} envs of {w.name}, {dt:.1f} s, one thread, FP64",
+            "cpu_model": cpu_model(), "nproc": os.cpu_count()}
 
 
 # Neural SDF: algorithmic FLOPs per training sample (forward 64x128 +
@@ -331,6 +391,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-all-cores", type=float, default=8.0,
+                    help="seconds of the all-cores oracle run (0: skip)")
     ap.add_argument("--no-counters", action="store_true")
     ap.add_argument("--ref-envs", type=int, default=4)
     ap.add_argument("--envs", type=int, default=0, help="smaller batch (profiling runs)")
@@ -500,6 +562,8 @@ def main():
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, scenes, args.cpu_seconds)
+        if args.cpu_all_cores > 0 and not (args.envs or args.scenes):
+            cpu["all_cores"] = cpu_all_cores(w, args.cpu_all_cores)
     clocks = clk.summary()
     hbm_peak, sm_max_mhz, peak_src = measured_peaks()
     roof = None

@@ -42,11 +42,17 @@ class Tally:
         self.ambiguous = 0
         self.max_pose_err = 0.0
         self.max_depth_rel = 0.0
+        self.fp16_max_err = 0.0        # FP16 depth: largest |gpu - oracle| (m)
+        self.fp16_max_frac = 0.0       # ... as a fraction of its bound
 
     def __repr__(self):
-        return (f"envs={self.envs} near_band={self.near_band} contacts={self.contacts} "
-                f"events={self.events} pixels={self.pixels} ambiguous={self.ambiguous} "
-                f"max_pose_err={self.max_pose_err:.2e} max_depth_rel={self.max_depth_rel:.2e}")
+        r = (f"envs={self.envs} near_band={self.near_band} contacts={self.contacts} "
+             f"events={self.events} pixels={self.pixels} ambiguous={self.ambiguous} "
+             f"max_pose_err={self.max_pose_err:.2e} max_depth_rel={self.max_depth_rel:.2e}")
+        if self.fp16_max_frac:
+            r += (f" fp16_max_err={self.fp16_max_err:.2e} m "
+                  f"fp16_max_of_bound={self.fp16_max_frac:.3f}")
+        return r
 
 
 def check_step(orc, before, after, out, acts, envs, M, tally, step_fn=None):
@@ -106,6 +112,9 @@ def check_image(orc, after, out, e, W, H, M, tally, fp16=False):
         ulp = np.spacing(depth[cov].astype(np.float16)).astype(np.float64)
         lim = 0.5 * ulp + DEPTH_REL * depth[cov]
         err = np.abs(gd[cov] - depth[cov])
+        if err.size:
+            tally.fp16_max_err = max(tally.fp16_max_err, float(err.max()))
+            tally.fp16_max_frac = max(tally.fp16_max_frac, float((err / lim).max()))
         assert np.all(err <= lim), (e, float((err - lim).max()))
     else:
         rel = np.abs(gd[cov] - depth[cov]) / depth[cov]
