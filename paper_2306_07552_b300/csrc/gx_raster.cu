@@ -63,7 +63,9 @@ struct __align__(16) ExpTri {
   int sy[3];      // edge increments per pixel step in y
   uint32_t id;
   float A, B, C;  // 1/z plane
-  int pad;
+  int off;        // first expansion slot of this round
+  float inv_bw;   // 1 / bw
+  int pad[3];
 };
 
 struct __align__(16) WarpSmem {
@@ -73,7 +75,7 @@ struct __align__(16) WarpSmem {
   int2 vfix[kMeshletMaxVerts];          // snapped screen coordinates (1/256 px)
   float vz[kMeshletMaxVerts];           // camera-space depth
   uint8_t voc[kMeshletMaxVerts];        // frustum outcode
-  uint8_t start[32];                    // lane whose triangle starts at slot base + i
+  uint8_t qlane[32];                    // lanes whose triangles have pixels, in order
   unsigned long long bar[2];            // mbarriers of the two buffers
 };
 
@@ -385,6 +387,7 @@ __device__ void raster_cluster(const View& vw, const Cam& cm, WarpSmem& ws, int 
                   depth_plane(cm, nx, ny, nz, h, A, B, C);
                   r.ixy = ix0 | (iy0 << 16);
                   r.bw = bw;
+                  r.inv_bw = __frcp_rn((float)bw);
                   r.A = A;
                   r.B = B;
                   r.C = C;
@@ -403,9 +406,12 @@ __device__ void raster_cluster(const View& vw, const Cam& cm, WarpSmem& ws, int 
         }
       }
     }
-    // pixel expansion: lane k's triangle owns slots [off_k, off_k + npx_k);
-    // in each pass lane l takes slot base + l, so neighbouring lanes mostly
-    // take neighbouring pixels of one row
+    // pixel expansion: the lanes whose triangles have pixels are listed in
+    // order (qlane); the c-th listed triangle owns slots [off, off + npx).  In
+    // each pass lane l takes slot base + l (neighbouring lanes mostly take
+    // neighbouring pixels of one row); its triangle is the last one started at
+    // or before that slot: the ones started in earlier passes plus the start
+    // bits of this pass up to lane l.
     int incl = npx;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -414,37 +420,38 @@ __device__ void raster_cluster(const View& vw, const Cam& cm, WarpSmem& ws, int 
     }
     const int off = incl - npx;
     const int total = __shfl_sync(kFull, incl, 31);
+    const unsigned has = __ballot_sync(kFull, npx > 0);
+    if (npx > 0) {
+      ws.q[lane].off = off;
+      ws.qlane[__popc(has & ((1u << lane) - 1u))] = (uint8_t)lane;
+    }
     if (kCount && lane == 0) {
       cn.v[kCntRounds]++;
       cn.v[kCntExpandTrips] += (total + 31) / 32;
     }
     __syncwarp();
+    int started = 0;
     for (int base = 0; base < total; base += 32) {
-      // triangles starting inside this pass, and the one running into it
       const int d = off - base;
       const bool starts = npx > 0 && d >= 0 && d < 32;
       const unsigned smask = __reduce_or_sync(kFull, starts ? (1u << d) : 0u);
-      const unsigned before = __ballot_sync(kFull, npx > 0 && d < 0);
-      if (starts) ws.start[d] = (uint8_t)lane;
-      __syncwarp();
-      const unsigned upto = smask & (0xffffffffu >> (31 - lane));
-      const int k = upto ? (int)ws.start[31 - __clz(upto)] : (before ? 31 - __clz(before) : 0);
-      const int offk = __shfl_sync(kFull, off, k);
+      const int k = started + __popc(smask & (0xffffffffu >> (31 - lane))) - 1;
+      started += __popc(smask);
       const int s = base + lane;
       if (s < total) {
-        const ExpTri& r = ws.q[k];
-        const int rr = s - offk;
-        const int bw = r.bw;
-        const int y = __float2int_rz(((float)rr + 0.5f) * __frcp_rn((float)bw));
+        const ExpTri& q = ws.q[ws.qlane[k]];
+        const int rr = s - q.off;
+        const int bw = q.bw;
+        const int y = __float2int_rz(((float)rr + 0.5f) * q.inv_bw);
         const int x = rr - y * bw;
-        const int e0 = r.e[0] + x * r.sx[0] + y * r.sy[0];
-        const int e1 = r.e[1] + x * r.sx[1] + y * r.sy[1];
-        const int e2 = r.e[2] + x * r.sx[2] + y * r.sy[2];
+        const int e0 = q.e[0] + x * q.sx[0] + y * q.sy[0];
+        const int e1 = q.e[1] + x * q.sx[1] + y * q.sy[1];
+        const int e2 = q.e[2] + x * q.sx[2] + y * q.sy[2];
         if ((e0 | e1 | e2) >= 0)
-          frag<kCount>(vw, (r.ixy & 0xffff) + x, (r.ixy >> 16) + y, r.A, r.B, r.C, cm, r.id, cn);
+          frag<kCount>(vw, (q.ixy & 0xffff) + x, (q.ixy >> 16) + y, q.A, q.B, q.C, cm, q.id, cn);
       }
-      __syncwarp();
     }
+    __syncwarp();
     unsigned bm = __ballot_sync(kFull, big);
     while (bm) {
       const int L = __ffs(bm) - 1;
