@@ -64,7 +64,7 @@ struct __align__(16) ExpTri {
   uint32_t id;
   float A, B, C;  // 1/z plane
   int off;        // first expansion slot of this round
-  float inv_bw;   // 1 / bw
+  float inv_bp;   // 1 / pairs per row
   int pad[3];
 };
 
@@ -387,15 +387,15 @@ __device__ void raster_cluster(const View& vw, const Cam& cm, WarpSmem& ws, int 
                   depth_plane(cm, nx, ny, nz, h, A, B, C);
                   r.ixy = ix0 | (iy0 << 16);
                   r.bw = bw;
-                  r.inv_bw = __frcp_rn((float)bw);
+                  r.inv_bp = __frcp_rn((float)((bw + 1) >> 1));
                   r.A = A;
                   r.B = B;
                   r.C = C;
                   r.id = id0 + t;
-                  npx = bw * bh;
+                  npx = ((bw + 1) >> 1) * bh;  // expansion slots: pixel pairs
                   if (kCount) {
                     cn.v[kCntTrisSmall]++;
-                    cn.v[kCntSmallPixels] += npx;
+                    cn.v[kCntSmallPixels] += bw * bh;
                   }
                 } else {
                   big = true;
@@ -407,9 +407,10 @@ __device__ void raster_cluster(const View& vw, const Cam& cm, WarpSmem& ws, int 
       }
     }
     // pixel expansion: the lanes whose triangles have pixels are listed in
-    // order (qlane); the c-th listed triangle owns slots [off, off + npx).  In
+    // order (qlane); the c-th listed triangle owns slots [off, off + npx), one
+    // slot per pair of horizontally adjacent pixels of its bounding box.  In
     // each pass lane l takes slot base + l (neighbouring lanes mostly take
-    // neighbouring pixels of one row); its triangle is the last one started at
+    // neighbouring pairs of one row); its triangle is the last one started at
     // or before that slot: the ones started in earlier passes plus the start
     // bits of this pass up to lane l.
     int incl = npx;
@@ -442,13 +443,15 @@ __device__ void raster_cluster(const View& vw, const Cam& cm, WarpSmem& ws, int 
         const ExpTri& q = ws.q[ws.qlane[k]];
         const int rr = s - q.off;
         const int bw = q.bw;
-        const int y = __float2int_rz(((float)rr + 0.5f) * q.inv_bw);
-        const int x = rr - y * bw;
+        const int y = __float2int_rz(((float)rr + 0.5f) * q.inv_bp);
+        const int x = 2 * (rr - y * ((bw + 1) >> 1));
         const int e0 = q.e[0] + x * q.sx[0] + y * q.sy[0];
         const int e1 = q.e[1] + x * q.sx[1] + y * q.sy[1];
         const int e2 = q.e[2] + x * q.sx[2] + y * q.sy[2];
-        if ((e0 | e1 | e2) >= 0)
-          frag<kCount>(vw, (q.ixy & 0xffff) + x, (q.ixy >> 16) + y, q.A, q.B, q.C, cm, q.id, cn);
+        const int i = (q.ixy & 0xffff) + x, j = (q.ixy >> 16) + y;
+        if ((e0 | e1 | e2) >= 0) frag<kCount>(vw, i, j, q.A, q.B, q.C, cm, q.id, cn);
+        if (x + 1 < bw && ((e0 + q.sx[0]) | (e1 + q.sx[1]) | (e2 + q.sx[2])) >= 0)
+          frag<kCount>(vw, i + 1, j, q.A, q.B, q.C, cm, q.id, cn);
       }
     }
     __syncwarp();
