@@ -53,6 +53,7 @@ constexpr int kThreads = kRasterThreads;
 constexpr int kWarps = kThreads / 32;
 constexpr long kWaitLimit = 1L << 22;  // bounded waits
 constexpr int kListCap = 2048;          // clusters culled per pass
+constexpr int kSpan = 4;                // adjacent pixels of a row per expansion slot
 
 // Setup of one triangle queued for pixel expansion.
 struct __align__(16) ExpTri {
@@ -387,12 +388,12 @@ __device__ void raster_cluster(const View& vw, const Cam& cm, WarpSmem& ws, int 
                   depth_plane(cm, nx, ny, nz, h, A, B, C);
                   r.ixy = ix0 | (iy0 << 16);
                   r.bw = bw;
-                  r.inv_bp = __frcp_rn((float)((bw + 1) >> 1));
+                  r.inv_bp = __frcp_rn((float)((bw + kSpan - 1) / kSpan));
                   r.A = A;
                   r.B = B;
                   r.C = C;
                   r.id = id0 + t;
-                  npx = ((bw + 1) >> 1) * bh;  // expansion slots: pixel pairs
+                  npx = ((bw + kSpan - 1) / kSpan) * bh;  // expansion slots: pixel runs
                   if (kCount) {
                     cn.v[kCntTrisSmall]++;
                     cn.v[kCntSmallPixels] += bw * bh;
@@ -444,14 +445,15 @@ __device__ void raster_cluster(const View& vw, const Cam& cm, WarpSmem& ws, int 
         const int rr = s - q.off;
         const int bw = q.bw;
         const int y = __float2int_rz(((float)rr + 0.5f) * q.inv_bp);
-        const int x = 2 * (rr - y * ((bw + 1) >> 1));
+        const int x = kSpan * (rr - y * ((bw + kSpan - 1) / kSpan));
         const int e0 = q.e[0] + x * q.sx[0] + y * q.sy[0];
         const int e1 = q.e[1] + x * q.sx[1] + y * q.sy[1];
         const int e2 = q.e[2] + x * q.sx[2] + y * q.sy[2];
         const int i = (q.ixy & 0xffff) + x, j = (q.ixy >> 16) + y;
-        if ((e0 | e1 | e2) >= 0) frag<kCount>(vw, i, j, q.A, q.B, q.C, cm, q.id, cn);
-        if (x + 1 < bw && ((e0 + q.sx[0]) | (e1 + q.sx[1]) | (e2 + q.sx[2])) >= 0)
-          frag<kCount>(vw, i + 1, j, q.A, q.B, q.C, cm, q.id, cn);
+#pragma unroll
+        for (int u = 0; u < kSpan; ++u)
+          if (x + u < bw && ((e0 + u * q.sx[0]) | (e1 + u * q.sx[1]) | (e2 + u * q.sx[2])) >= 0)
+            frag<kCount>(vw, i + u, j, q.A, q.B, q.C, cm, q.id, cn);
       }
     }
     __syncwarp();
