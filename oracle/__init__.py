@@ -89,6 +89,12 @@ class RenderStats_c(C.Structure):
                 ("ambiguous", C.c_int64), ("overflow", C.c_int64)]
 
 
+class StepOpts_c(C.Structure):
+    _fields_ = [("dhat", f64p), ("margin", C.c_double), ("band", C.c_double),
+                ("slide", C.c_int32), ("place_jitter", C.c_int32), ("seed", C.c_uint64),
+                ("env", C.c_int32)]
+
+
 def _declare(L):
     P = C.POINTER
     L.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
@@ -101,6 +107,9 @@ def _declare(L):
     L.orc_fk.argtypes = [P(Robot_c), f64p, f64p, f64p, f64p, f64p]
     L.orc_sphere_centres.argtypes = [P(Robot_c), f64p, f64p, f64p]
     L.orc_step.argtypes = [P(Robot_c), P(Scene_c), P(State_c), f32p, P(StepOut_c)]
+    L.orc_step_ex.argtypes = [P(Robot_c), P(Scene_c), P(State_c), f32p, P(StepOpts_c), P(StepOut_c)]
+    L.orc_grid_gradient.argtypes = [P(Scene_c), f64p, f64p]
+    L.orc_grid_gradient.restype = C.c_int
     L.orc_step_nsdf.argtypes = [P(Robot_c), P(Scene_c), P(State_c), f32p, f64p, C.c_double,
                                 C.c_double, P(StepOut_c)]
     L.orc_candidate_spheres.argtypes = [P(Robot_c), P(State_c), f32p, f64p, f64p, i32p]
@@ -212,6 +221,29 @@ class Oracle:
         self.L.orc_step(C.byref(self.robot), C.byref(self.scene), C.byref(st), _p(a, f32p),
                         C.byref(out))
         return out
+
+    def step_ex(self, st, action, slide=False, place_jitter=False, seed=0, env=0, dhat=None,
+                margin=0.0, band=0.0):
+        """One step with the paper's heuristics switched on as asked."""
+        a = np.ascontiguousarray(action, np.float32)
+        o = StepOpts_c()
+        d = None
+        if dhat is not None:
+            d = np.ascontiguousarray(dhat, np.float64)
+            o.dhat = _p(d, f64p)
+        o.margin, o.band = float(margin), float(band)
+        o.slide, o.place_jitter = int(slide), int(place_jitter)
+        o.seed, o.env = int(seed), int(env)
+        out = StepOut_c()
+        self.L.orc_step_ex(C.byref(self.robot), C.byref(self.scene), C.byref(st), _p(a, f32p),
+                           C.byref(o), C.byref(out))
+        return out
+
+    def grid_gradient(self, c):
+        cc = np.ascontiguousarray(c, np.float64)
+        g = np.zeros(3)
+        inside = self.L.orc_grid_gradient(C.byref(self.scene), _p(cc, f64p), _p(g, f64p))
+        return bool(inside), g
 
     def candidate_spheres(self, st, action):
         """Centres [31][3], radii [31] and the active mask of the proposed pose."""

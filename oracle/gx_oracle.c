@@ -119,6 +119,32 @@ int orc_grid_query(const orc_scene* s, const double c[3], double* d, double* edg
   return 1;
 }
 
+/* Gradient of the trilinear interpolant at c (the cell the query above
+ * uses), per metre; 0 outside the lattice box. */
+int orc_grid_gradient(const orc_scene* s, const double c[3], double g[3]) {
+  double h = s->grid_h, gl[3], t[3];
+  int i[3];
+  g[0] = g[1] = g[2] = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    gl[a] = (c[a] - (double)s->grid_origin[a]) / h;
+    if (gl[a] < 0 || gl[a] > s->grid_dims[a] - 1) return 0;
+    i[a] = (int)floor(gl[a]);
+    if (i[a] > s->grid_dims[a] - 2) i[a] = s->grid_dims[a] - 2;
+    t[a] = gl[a] - i[a];
+  }
+  for (int dz = 0; dz < 2; ++dz)
+    for (int dy = 0; dy < 2; ++dy)
+      for (int dx = 0; dx < 2; ++dx) {
+        double v = orc_grid_node(s, i[0] + dx, i[1] + dy, i[2] + dz);
+        double wx = dx ? t[0] : 1 - t[0], wy = dy ? t[1] : 1 - t[1], wz = dz ? t[2] : 1 - t[2];
+        double sx = dx ? 1.0 : -1.0, sy = dy ? 1.0 : -1.0, sz = dz ? 1.0 : -1.0;
+        g[0] += sx * wy * wz * v / h;
+        g[1] += wx * sy * wz * v / h;
+        g[2] += wx * wy * sz * v / h;
+      }
+  return 1;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Rigid frames: R row-major 3x3 then t; x_world = R x_local + t.           */
 /* ------------------------------------------------------------------------ */
@@ -323,11 +349,95 @@ void orc_candidate_spheres(const orc_robot* rb, const orc_state* st, const float
 
 void orc_step(const orc_robot* rb, const orc_scene* sc, orc_state* st, const float act[11],
               orc_step_out* out) {
-  orc_step_nsdf(rb, sc, st, act, NULL, 0.0, 0.0, out);
+  orc_step_opts o;
+  memset(&o, 0, sizeof(o));
+  orc_step_ex(rb, sc, st, act, &o, out);
 }
 
 void orc_step_nsdf(const orc_robot* rb, const orc_scene* sc, orc_state* st, const float act[11],
                    const double* dhat, double margin, double band, orc_step_out* out) {
+  orc_step_opts o;
+  memset(&o, 0, sizeof(o));
+  o.dhat = dhat;
+  o.margin = margin;
+  o.band = band;
+  orc_step_ex(rb, sc, st, act, &o, out);
+}
+
+/* Contacts of the robot spheres cs[0..n) and the held object ph (when h >=
+ * 0) shifted by (ox, 0, oz), grid rule, counting near-band decisions. */
+static uint32_t shifted_contacts(const orc_robot* rb, const orc_scene* sc, const orc_state* st,
+                                 double cs[][3], const double ph[3], double ox, double oz, int* nb) {
+  uint32_t m = 0;
+  int h = st->held;
+  for (int i = 0; i <= 30; ++i) {
+    if (i >= rb->n_spheres && !(i == 30 && h >= 0)) continue;
+    const double* c0 = i == 30 ? ph : cs[i];
+    double c[3] = {c0[0] + ox, c0[1], c0[2] + oz};
+    double r = i == 30 ? st->obj[h][3] : rb->sphere_radius[i];
+    int hit = static_contact(sc, c, r, nb);
+    for (int j = 0; j < st->n_obj && !hit; ++j)
+      if (j != h && pair_contact(c, r, st->obj[j], st->obj[j][3], nb)) hit = 1;
+    if (hit) m |= 1u << i;
+  }
+  return m;
+}
+
+/* Sliding heuristic (appendix "Sliding Heuristic"): from the candidate pose,
+ * at most three jitters of the base in the ground plane.  Direction: the sum
+ * over penetrating spheres of penetration x outward ground-plane normal (the
+ * horizontal gradient of the distance field for the static scene, away from
+ * the object's centre for objects), normalised; length: the deepest
+ * penetration + 1 mm.  A zero direction (|sum| < 1e-5 m) ends the search.
+ * Returns 1 and the base shift when a contact-free pose was found. */
+static int slide_search(const orc_robot* rb, const orc_scene* sc, const orc_state* st,
+                        double cs[][3], const double ph[3], double off[2], int* nb) {
+  int h = st->held;
+  off[0] = off[1] = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    double D[2] = {0.0, 0.0}, pen = 0.0;
+    for (int i = 0; i <= 30; ++i) {
+      if (i >= rb->n_spheres && !(i == 30 && h >= 0)) continue;
+      const double* c0 = i == 30 ? ph : cs[i];
+      double c[3] = {c0[0] + off[0], c0[1], c0[2] + off[1]};
+      double r = i == 30 ? st->obj[h][3] : rb->sphere_radius[i];
+      double d, edge, g[3];
+      if (orc_grid_query(sc, c, &d, &edge) && d < r) {
+        orc_grid_gradient(sc, c, g);
+        double gl = sqrt(g[0] * g[0] + g[2] * g[2]);
+        if (gl > 1e-9) {
+          D[0] += (r - d) * g[0] / gl;
+          D[1] += (r - d) * g[2] / gl;
+        }
+        if (r - d > pen) pen = r - d;
+      }
+      for (int j = 0; j < st->n_obj; ++j) {
+        if (j == h) continue;
+        double dist = dist3(c, st->obj[j]), rr = r + st->obj[j][3];
+        if (dist < rr) {
+          double vx = c[0] - st->obj[j][0], vz = c[2] - st->obj[j][2], vl = sqrt(vx * vx + vz * vz);
+          if (vl > 1e-9) {
+            D[0] += (rr - dist) * vx / vl;
+            D[1] += (rr - dist) * vz / vl;
+          }
+          if (rr - dist > pen) pen = rr - dist;
+        }
+      }
+    }
+    double dl = sqrt(D[0] * D[0] + D[1] * D[1]);
+    if (dl < 1e-4) (*nb)++;
+    if (dl < 1e-5) return 0;
+    off[0] += (pen + 0.001) * D[0] / dl;
+    off[1] += (pen + 0.001) * D[1] / dl;
+    if (shifted_contacts(rb, sc, st, cs, ph, off[0], off[1], nb) == 0) return 1;
+  }
+  return 0;
+}
+
+void orc_step_ex(const orc_robot* rb, const orc_scene* sc, orc_state* st, const float act[11],
+                 const orc_step_opts* opt, orc_step_out* out) {
+  const double* dhat = opt->dhat;
+  const double margin = opt->margin, band = opt->band;
   double a[11];
   clip_actions(act, a);
   int nb = 0;
@@ -368,8 +478,19 @@ void orc_step_nsdf(const orc_robot* rb, const orc_scene* sc, orc_state* st, cons
       if (pair_contact(ph, rho, st->obj[j], st->obj[j][3], &nb)) { mask |= 1u << 30; flags |= 2 | 4; }
     }
   }
-  /* resolution: any contact rejects all robot motion for this step */
+  /* resolution: any contact rejects all robot motion for this step, unless
+   * sliding finds a contact-free base position nearby */
   int reverted = mask != 0;
+  if (reverted && opt->slide) {
+    double ph[3] = {0, 0, 0}, off[2];
+    if (h >= 0) fr_apply(ee, st->c_off, ph);
+    if (slide_search(rb, sc, st, cs, ph, off, &nb)) {
+      cb[0] += off[0];
+      cb[1] += off[1];
+      reverted = 0;
+      flags |= 8;
+    }
+  }
   if (!reverted) {
     memcpy(st->base, cb, sizeof(cb));
     memcpy(st->q, cq, sizeof(cq));
@@ -415,9 +536,61 @@ void orc_step_nsdf(const orc_robot* rb, const orc_scene* sc, orc_state* st, cons
     if (ok)
       for (int k = 0; k < st->n_obj; ++k)
         if (k != j && pair_contact(land, rho, st->obj[k], st->obj[k][3], &nb)) overlap = 1;
+    int jittered = 0;
+    if (!(ok && !overlap) && opt->place_jitter) {
+      /* Object placing heuristic (appendix "Object Placing Heuristic"): at
+       * most six jitters of 2 rho in the ground plane, each followed by a new
+       * cast down from the release height.  Direction: away from the
+       * objects the landing overlaps (sum of unit ground-plane vectors),
+       * turned by a uniform angle in [-pi/4, pi/4); a uniform direction when
+       * nothing overlaps.  Draw k: Philox4x32-10 on (env, step, k,
+       * 0x4A495454) with the reset key. */
+      const uint32_t key[2] = {(uint32_t)opt->seed, (uint32_t)(opt->seed >> 32)};
+      double q[3] = {land[0], land[1], land[2]};
+      int landed = ok;  /* the current trial position rests on a surface */
+      for (uint32_t k = 0; k < 6 && !jittered; ++k) {
+        double Dx = 0.0, Dz = 0.0;
+        if (landed)
+          for (int m = 0; m < st->n_obj; ++m) {
+            if (m == j) continue;
+            if (dist3(q, st->obj[m]) < rho + st->obj[m][3]) {
+              double vx = q[0] - st->obj[m][0], vz = q[2] - st->obj[m][2];
+              double vl = sqrt(vx * vx + vz * vz);
+              if (vl > 1e-9) { Dx += vx / vl; Dz += vz / vl; }
+            }
+          }
+        uint32_t ctr[4] = {(uint32_t)opt->env, (uint32_t)st->step_count, k, 0x4A495454u}, w[4];
+        orc_philox4x32_10(ctr, key, w);
+        double u = unit24(w[0]), dl = sqrt(Dx * Dx + Dz * Dz), phi;
+        if (dl > 1e-6) {
+          if (dl < 1e-4) nb++;
+          phi = atan2(Dz, Dx) + (u - 0.5) * (PI / 2);
+        } else {
+          phi = 2 * PI * u;
+        }
+        q[0] += 2 * rho * cos(phi);
+        q[2] += 2 * rho * sin(phi);
+        double cast[3] = {q[0], p[1], q[2]};
+        int ok2 = 0;
+        double y2 = orc_snap(sc, cast, rho + (double)rb->rest_clearance, &ok2, &nb);
+        q[1] = ok2 ? y2 : p[1];
+        landed = ok2;
+        int ov2 = 0;
+        if (ok2)
+          for (int m = 0; m < st->n_obj; ++m)
+            if (m != j && pair_contact(q, rho, st->obj[m], st->obj[m][3], &nb)) ov2 = 1;
+        if (ok2 && !ov2) {
+          memcpy(land, q, sizeof(land));
+          jittered = 1;
+        }
+      }
+    }
     if (ok && !overlap) {
       memcpy(st->obj[j], land, sizeof(land));
       event = 3;
+    } else if (jittered) {
+      memcpy(st->obj[j], land, sizeof(land));
+      event = 5;
     } else {
       memcpy(st->obj[j], st->p_pre, 3 * sizeof(double));
       event = 4;

@@ -102,6 +102,21 @@ void orc_sphere_centres(const orc_robot* rb, const double base[3], const double 
                         double out[][3]);
 void orc_step(const orc_robot* rb, const orc_scene* sc, orc_state* st, const float act[11],
               orc_step_out* out);
+/* Options of the general step.  dhat != NULL: the neural-SDF static test
+ * (see orc_step_nsdf); slide: the sliding heuristic (contact_flags bit 8 when
+ * it moved the base); place_jitter: the object placing heuristic on release
+ * (event 5 when a jittered landing was found), drawing from Philox with key
+ * `seed` and counter (env, step, k, 0x4A495454). */
+typedef struct {
+  const double* dhat;
+  double margin, band;
+  int32_t slide, place_jitter;
+  uint64_t seed;
+  int32_t env;
+} orc_step_opts;
+void orc_step_ex(const orc_robot* rb, const orc_scene* sc, orc_state* st, const float act[11],
+                 const orc_step_opts* opt, orc_step_out* out);
+int orc_grid_gradient(const orc_scene* s, const double c[3], double g[3]);
 /* The step with the neural-SDF static test: dhat[i] is the predicted
  * distance at candidate sphere i (i < n_spheres; 30 = held object).  Outside
  * the lattice box is contact; dhat - r >= margin is free; else the grid
