@@ -398,6 +398,8 @@ def main():
     ap.add_argument("--envs", type=int, default=0, help="smaller batch (profiling runs)")
     ap.add_argument("--scenes", type=int, default=0, help="fewer scenes (profiling runs)")
     ap.add_argument("--small-px", type=int, default=0, help="expansion bbox limit (0: auto)")
+    ap.add_argument("--heuristics", type=int, default=0,
+                    help="the paper's heuristics: bit 0 sliding, bit 1 object placing")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default rasteriser setting instead of timing candidates")
     ap.add_argument("--graph", action="store_true",
@@ -430,7 +432,7 @@ def main():
         nsdf = train_scenes(ss, w, sorted(set(int(x) for x in I.env_scene_map(n, w.n_scenes))))
     sim_kw = dict(img=(w.img, w.img), depth_fp16=w.depth_fp16, render_rgb=w.rgb,
                   n_objects=w.n_objects, obj_radius=w.obj_radius, seed=rank_seeds(w, rank)[0],
-                  small_tri_px=args.small_px)
+                  small_tri_px=args.small_px, heuristics=args.heuristics)
     sim = gx.Sim(ss, I.fetch_like_robot(), n, profile=0 if args.graph else 1,
                  use_graph=args.graph, sdf_mode=1 if neural else 0, sdf_margin=w.sdf_margin,
                  **sim_kw)
@@ -595,7 +597,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (procedural apartments standing in for ReplicaCAD; see DESIGN.md)",
-        "config": config_of(w),
+        "config": {**config_of(w), "heuristics": {"sliding": bool(args.heuristics & 1),
+                                                  "object_placing": bool(args.heuristics & 2)}},
         "phases_ms_per_launch": {k: phase_ms[i] / max(phase_n[i], 1)
                                  for i, k in enumerate(["physics", "raster", "reset",
                                                         "nsdf_query"])},

@@ -144,6 +144,17 @@ typedef struct {
                               d - r is below sdf_margin, or not finite; a
                               centre outside the grid box is contact          */
   float sdf_margin;        /* metres, >= 0 (e.g. 0.02)                        */
+  int32_t heuristics;      /* the paper's heuristics (appendix "Description of
+                              Heuristics"), bit 0: sliding -- a colliding
+                              candidate base is jittered in the ground plane
+                              at most 3 times, along the penetration-weighted
+                              outward normals by the deepest penetration + 1 mm
+                              (contact_flags bit 3 = 8 when it moved); bit 1:
+                              object placing -- a failed release is jittered
+                              at most 6 times by 2 rho away from overlapped
+                              objects (random turn in [-pi/4, pi/4), Philox on
+                              env, step, k, 0x4A495454 with the reset seed) and
+                              re-cast down (event 5 when that lands)          */
 } gx_config;
 
 /* Outputs of one step, device memory owned by the caller (e.g. torch

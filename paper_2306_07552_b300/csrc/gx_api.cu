@@ -179,6 +179,9 @@ void enqueue_step(gx_ctx* c, const float* actions, const gx_outputs& out, cudaSt
   pp.out = out;
   pp.err = c->d_err;
   pp.raster_work = c->d_raster_work;
+  pp.slide = c->cfg.heuristics & 1;
+  pp.place_jitter = (c->cfg.heuristics >> 1) & 1;
+  pp.seed = c->cfg.seed;
   if (c->cfg.sdf_mode == 1) {
     pp.nsdf_pts = c->d_nsdf_pts;
     pp.nsdf_d = c->d_nsdf_d;
@@ -371,6 +374,7 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
         return fail(nullptr, GX_EINVAL, "env_scene[%d] out of range", i);
   if (c.raster_regions != 0) return fail(nullptr, GX_EINVAL, "raster_regions is reserved (0)");
   if (c.sdf_mode != 0 && c.sdf_mode != 1) return fail(nullptr, GX_EINVAL, "sdf_mode must be 0 or 1");
+  if (c.heuristics & ~3) return fail(nullptr, GX_EINVAL, "heuristics: only bits 0 and 1 are defined");
   if (c.sdf_mode == 1 && !(c.sdf_margin >= 0.f && c.sdf_margin < 1e30f))
     return fail(nullptr, GX_EINVAL, "sdf_margin must be finite and >= 0");
   gx_ctx* x = new gx_ctx();

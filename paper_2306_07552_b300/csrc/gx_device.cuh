@@ -47,6 +47,32 @@ __device__ __forceinline__ float grid_lerp(const DScene& s, float gx, float gy, 
   return c0 + tz * (c1 - c0);
 }
 
+// Trilinear distance and its horizontal gradient (x and z, per metre) at c;
+// false outside the lattice box.  d equals grid_query's value.
+__device__ bool grid_query_grad(const DScene& s, float cx, float cy, float cz, float& d,
+                                float& gxo, float& gzo) {
+  const float gx = (cx - s.ox) * s.inv_h, gy = (cy - s.oy) * s.inv_h, gz = (cz - s.oz) * s.inv_h;
+  if (!(gx >= 0.f && gx <= (float)(s.nx - 1) && gy >= 0.f && gy <= (float)(s.ny - 1) &&
+        gz >= 0.f && gz <= (float)(s.nz - 1)))
+    return false;
+  d = grid_lerp(s, gx, gy, gz);
+  const int i = min((int)floorf(gx), s.nx - 2);
+  const int j = min((int)floorf(gy), s.ny - 2);
+  const int k = min((int)floorf(gz), s.nz - 2);
+  const float tx = gx - i, ty = gy - j, tz = gz - k;
+  const float* g = s.grid + ((size_t)k * s.ny + j) * s.nx + i;
+  const size_t sy = s.nx, sz = (size_t)s.nx * s.ny;
+  const float c000 = __ldg(g), c100 = __ldg(g + 1);
+  const float c010 = __ldg(g + sy), c110 = __ldg(g + sy + 1);
+  const float c001 = __ldg(g + sz), c101 = __ldg(g + sz + 1);
+  const float c011 = __ldg(g + sz + sy), c111 = __ldg(g + sz + sy + 1);
+  gxo = ((c100 - c000) * (1.f - ty) * (1.f - tz) + (c110 - c010) * ty * (1.f - tz) +
+         (c101 - c001) * (1.f - ty) * tz + (c111 - c011) * ty * tz) * s.inv_h;
+  gzo = ((c001 - c000) * (1.f - tx) * (1.f - ty) + (c101 - c100) * tx * (1.f - ty) +
+         (c011 - c010) * (1.f - tx) * ty + (c111 - c110) * tx * ty) * s.inv_h;
+  return true;
+}
+
 // true when c lies inside the lattice box (and is finite).
 __device__ __forceinline__ bool grid_contains(const DScene& s, float cx, float cy, float cz) {
   const float gx = (cx - s.ox) * s.inv_h, gy = (cy - s.oy) * s.inv_h, gz = (cz - s.oz) * s.inv_h;

@@ -84,6 +84,9 @@ struct PhysicsParams {
   // neural-SDF static test: pass 1 writes the candidate sphere centres
   // (x, y, z, radius or -1 when unused) and stops; pass 2 reads the
   // predicted distances and consults the grid only below the margin.
+  int slide;                            // sliding heuristic on
+  int place_jitter;                     // object placing heuristic on
+  uint64_t seed;                        // Philox key (the reset key)
   int nsdf_pass;                        // 0: grid only, 1: emit, 2: consume
   float4* nsdf_pts;                     // [n][32]
   const float* nsdf_d;                  // [n][32]

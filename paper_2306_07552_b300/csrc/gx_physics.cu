@@ -268,11 +268,81 @@ __global__ void __launch_bounds__(32 * kEnvsPerBlock) physics_kernel(const Physi
   }
   const unsigned ms = __ballot_sync(kFull, active && cs);
   const unsigned mo = __ballot_sync(kFull, active && co);
-  const uint8_t flags = (ms ? 1 : 0) | (mo ? 2 : 0) | ((mask >> 30) & 1u ? 4 : 0);
+  uint8_t flags = (ms ? 1 : 0) | (mo ? 2 : 0) | ((mask >> 30) & 1u ? 4 : 0);
 
-  // (a7) any contact rejects all robot motion this step
-  const bool rev = mask != 0;
-  float ax = cx, az = cz, ayaw = cyaw, aq[7];
+  // (a7) any contact rejects all robot motion this step, unless sliding
+  // (appendix "Sliding Heuristic") finds a contact-free base nearby: at most
+  // three ground-plane jitters along the penetration-weighted outward
+  // normals (horizontal grid gradient; away from object centres), each by
+  // the deepest penetration + 1 mm.  Only the base moves, so every sphere
+  // translates with it and no new FK is needed.
+  bool rev = mask != 0;
+  float offx = 0.f, offz = 0.f;
+  if (rev && P.slide) {
+    bool found = false;
+    for (int k = 0; k < 3; ++k) {
+      float Dx = 0.f, Dz = 0.f, pen = 0.f;
+      const float sx = c[0] + offx, sy = c[1], sz = c[2] + offz;
+      if (active) {
+        float d, gxx, gzz;
+        if (grid_query_grad(S, sx, sy, sz, d, gxx, gzz) && d < r) {
+          const float gl = sqrtf(gxx * gxx + gzz * gzz);
+          if (gl > 1e-9f) {
+            Dx += (r - d) * gxx / gl;
+            Dz += (r - d) * gzz / gl;
+          }
+          pen = fmaxf(pen, r - d);
+        }
+        for (int j = 0; j < M; ++j) {
+          if (j == held) continue;
+          const float4 o = so[j];
+          const float dx = sx - o.x, dy = sy - o.y, dz = sz - o.z, rr = r + o.w;
+          const float dist = sqrtf(dx * dx + dy * dy + dz * dz);
+          if (dist < rr) {
+            const float vl = sqrtf(dx * dx + dz * dz);
+            if (vl > 1e-9f) {
+              Dx += (rr - dist) * dx / vl;
+              Dz += (rr - dist) * dz / vl;
+            }
+            pen = fmaxf(pen, rr - dist);
+          }
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        Dx += __shfl_xor_sync(kFull, Dx, o);
+        Dz += __shfl_xor_sync(kFull, Dz, o);
+        pen = fmaxf(pen, __shfl_xor_sync(kFull, pen, o));
+      }
+      const float dl = sqrtf(Dx * Dx + Dz * Dz);
+      if (dl < 1e-5f) break;
+      offx += (pen + 0.001f) * Dx / dl;
+      offz += (pen + 0.001f) * Dz / dl;
+      bool hit = false;
+      if (active) {
+        const float tx = c[0] + offx, ty = c[1], tz = c[2] + offz;
+        float d;
+        hit = !grid_query(S, tx, ty, tz, d) || d < r;
+        for (int j = 0; j < M && !hit; ++j) {
+          if (j == held) continue;
+          const float4 o = so[j];
+          const float dx = tx - o.x, dy = ty - o.y, dz = tz - o.z, rr = r + o.w;
+          hit = dx * dx + dy * dy + dz * dz < rr * rr;
+        }
+      }
+      if (!__any_sync(kFull, hit)) {
+        found = true;
+        break;
+      }
+    }
+    if (found) {
+      rev = false;
+      flags |= 8;
+    } else {
+      offx = offz = 0.f;
+    }
+  }
+  float ax = cx + offx, az = cz + offz, ayaw = cyaw, aq[7];
 #pragma unroll
   for (int k = 0; k < 7; ++k) aq[k] = cq[k];
   if (rev) {
@@ -280,6 +350,9 @@ __global__ void __launch_bounds__(32 * kEnvsPerBlock) physics_kernel(const Physi
 #pragma unroll
     for (int k = 0; k < 7; ++k) aq[k] = q0[k];
     fk(rb, ax, az, ayaw, aq, -1, myR, myt, eR, et);
+  } else {
+    et[0] += offx;  // a slid base carries the tool frame along
+    et[2] += offz;
   }
 
   // (a8) grasp / release at the accepted pose
@@ -321,8 +394,9 @@ __global__ void __launch_bounds__(32 * kEnvsPerBlock) physics_kernel(const Physi
     float p[3];
     apply(eR, et, coff[0], coff[1], coff[2], p);
     const float rho = so[held].w;
+    const float target = rho + rb.rest_clearance;
     float y = p[1];
-    const bool ok = snap_down(S, p, rho + rb.rest_clearance, y, lane);
+    const bool ok = snap_down(S, p, target, y, lane);
     bool ov = false;
     if (ok) {
       for (int j = lane; j < M; j += 32) {
@@ -333,10 +407,73 @@ __global__ void __launch_bounds__(32 * kEnvsPerBlock) physics_kernel(const Physi
       }
     }
     ov = __any_sync(kFull, ov);
-    __syncwarp();
-    if (lane == 0) so[held] = (ok && !ov) ? make_float4(p[0], y, p[2], rho)
-                                          : make_float4(ppre[0], ppre[1], ppre[2], rho);
+    float lx = p[0], ly = y, lz = p[2];
     event = (ok && !ov) ? 3 : 4;
+    if (event == 4 && P.place_jitter) {
+      // object placing heuristic (appendix): at most six ground-plane jitters
+      // of 2 rho away from the overlapped objects, turned by a uniform angle
+      // in [-pi/4, pi/4) (uniform when nothing overlaps), each re-cast down
+      // from the release height; Philox on (env, step, k, 0x4A495454)
+      const uint2 key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
+      float qx = p[0], qy = y, qz = p[2];
+      bool landed = ok;
+      for (int k = 0; k < 6; ++k) {
+        float Dx = 0.f, Dz = 0.f;
+        if (landed) {
+          for (int j = lane; j < M; j += 32) {
+            if (j == held) continue;
+            const float4 o = so[j];
+            const float dx = qx - o.x, dy = qy - o.y, dz = qz - o.z;
+            if (sqrtf(dx * dx + dy * dy + dz * dz) < rho + o.w) {
+              const float vl = sqrtf(dx * dx + dz * dz);
+              if (vl > 1e-9f) {
+                Dx += dx / vl;
+                Dz += dz / vl;
+              }
+            }
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            Dx += __shfl_xor_sync(kFull, Dx, o);
+            Dz += __shfl_xor_sync(kFull, Dz, o);
+          }
+        }
+        const uint4 w = philox4x32_10(
+            make_uint4((uint32_t)env, (uint32_t)(stepc - 1), (uint32_t)k, 0x4A495454u), key);
+        const float u = unit24(w.x);
+        const float dl = sqrtf(Dx * Dx + Dz * Dz);
+        const float phi = dl > 1e-6f ? atan2f(Dz, Dx) + (u - 0.5f) * (0.5f * CUDART_PI_F)
+                                     : 2.f * CUDART_PI_F * u;
+        float sp, cp;
+        sincosf(phi, &sp, &cp);
+        qx += 2.f * rho * cp;
+        qz += 2.f * rho * sp;
+        const float cast[3] = {qx, p[1], qz};
+        float y2 = p[1];
+        const bool ok2 = snap_down(S, cast, target, y2, lane);
+        qy = ok2 ? y2 : p[1];
+        landed = ok2;
+        bool ov2 = false;
+        if (ok2) {
+          for (int j = lane; j < M; j += 32) {
+            if (j == held) continue;
+            const float4 o = so[j];
+            const float dx = qx - o.x, dy = qy - o.y, dz = qz - o.z, rr = rho + o.w;
+            ov2 |= dx * dx + dy * dy + dz * dz < rr * rr;
+          }
+        }
+        if (ok2 && !__any_sync(kFull, ov2)) {
+          lx = qx;
+          ly = qy;
+          lz = qz;
+          event = 5;
+          break;
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0) so[held] = event != 4 ? make_float4(lx, ly, lz, rho)
+                                         : make_float4(ppre[0], ppre[1], ppre[2], rho);
     nheld = -1;
     coff[0] = coff[1] = coff[2] = 0.f;
   }

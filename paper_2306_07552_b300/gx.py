@@ -71,7 +71,7 @@ class GxConfig(C.Structure):
                 ("obj_radius_min", C.c_float), ("obj_radius_max", C.c_float),
                 ("seed", C.c_uint64), ("env_scene", i32p), ("raster_regions", C.c_int32),
                 ("small_tri_px", C.c_int32), ("use_graph", C.c_int32), ("profile", C.c_int32),
-                ("sdf_mode", C.c_int32), ("sdf_margin", C.c_float)]
+                ("sdf_mode", C.c_int32), ("sdf_margin", C.c_float), ("heuristics", C.c_int32)]
 
 
 class GxOutputs(C.Structure):
@@ -299,7 +299,7 @@ class Sim:
     def __init__(self, scene_set: SceneSet, robot: _inputs.Robot, n_envs: int, img=(128, 128),
                  depth_fp16=False, render_rgb=True, n_objects=40, obj_radius=(0.03, 0.06),
                  seed=1, env_scene=None, raster_regions=0, small_tri_px=0, use_graph=False,
-                 profile=0, sdf_mode=0, sdf_margin=0.02):
+                 profile=0, sdf_mode=0, sdf_margin=0.02, heuristics=0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("gx needs a CUDA device; there is no CPU fallback")
@@ -319,6 +319,7 @@ class Sim:
         cfg.raster_regions, cfg.small_tri_px, cfg.use_graph = raster_regions, small_tri_px, int(use_graph)
         cfg.profile = int(profile)
         cfg.sdf_mode, cfg.sdf_margin = int(sdf_mode), float(sdf_margin)
+        cfg.heuristics = int(heuristics)
         self.robot_c = robot_struct(robot)
         self.handle = C.c_void_p()
         _check(lib().gx_create(scene_set.handle, C.byref(self.robot_c), C.byref(cfg),

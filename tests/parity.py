@@ -57,7 +57,8 @@ class Tally:
 
 def check_step(orc, before, after, out, acts, envs, M, tally, step_fn=None):
     """Physics parity of one step for the listed environments.  step_fn(st,
-    action) replaces the oracle's grid step (e.g. with its neural-SDF rule)."""
+    action, env) replaces the oracle's plain step (e.g. with its neural-SDF
+    rule or the paper's heuristics)."""
     mask = out["contact_mask"].cpu().numpy().view(np.uint32)
     flags = out["contact_flags"].cpu().numpy()
     event = out["event"].cpu().numpy()
@@ -66,7 +67,7 @@ def check_step(orc, before, after, out, acts, envs, M, tally, step_fn=None):
     objo = out["obj_pos"].cpu().numpy()
     for e in envs:
         st = oracle_state(before, e, M)
-        o = step_fn(st, acts[e]) if step_fn else orc.step(st, acts[e])
+        o = step_fn(st, acts[e], e) if step_fn else orc.step(st, acts[e])
         tally.envs += 1
         if o.near_band:
             tally.near_band += 1

@@ -102,7 +102,7 @@ def test_neural_rule_matches_oracle(two_rooms):
     trusted = 0
 
     def step_fn_for(k):
-        def f(st, action):
+        def f(st, action, env):
             nonlocal trusted
             c, r, act = orcs[k].candidate_spheres(st, action)
             d = np.full(31, -1e9)
