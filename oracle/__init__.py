@@ -92,7 +92,7 @@ class RenderStats_c(C.Structure):
 class StepOpts_c(C.Structure):
     _fields_ = [("dhat", f64p), ("margin", C.c_double), ("band", C.c_double),
                 ("slide", C.c_int32), ("place_jitter", C.c_int32), ("seed", C.c_uint64),
-                ("env", C.c_int32)]
+                ("env", C.c_int32), ("column", C.c_int32)]
 
 
 def _declare(L):
@@ -109,6 +109,13 @@ def _declare(L):
     L.orc_step.argtypes = [P(Robot_c), P(Scene_c), P(State_c), f32p, P(StepOut_c)]
     L.orc_step_ex.argtypes = [P(Robot_c), P(Scene_c), P(State_c), f32p, P(StepOpts_c), P(StepOut_c)]
     L.orc_grid_gradient.argtypes = [P(Scene_c), f64p, f64p]
+    L.orc_column_radius_index.argtypes = [C.c_double]
+    L.orc_column_radius_index.restype = C.c_int
+    L.orc_column_dims.argtypes = [P(Scene_c), i32p]
+    L.orc_column_spans.argtypes = [P(Scene_c), C.c_int, C.c_int, C.c_int, f64p, C.c_int]
+    L.orc_column_spans.restype = C.c_int
+    L.orc_column_contact.argtypes = [P(Scene_c), f64p, C.c_double, P(C.c_int)]
+    L.orc_column_contact.restype = C.c_int
     L.orc_grid_gradient.restype = C.c_int
     L.orc_step_nsdf.argtypes = [P(Robot_c), P(Scene_c), P(State_c), f32p, f64p, C.c_double,
                                 C.c_double, P(StepOut_c)]
@@ -223,7 +230,7 @@ class Oracle:
         return out
 
     def step_ex(self, st, action, slide=False, place_jitter=False, seed=0, env=0, dhat=None,
-                margin=0.0, band=0.0):
+                margin=0.0, band=0.0, column=False):
         """One step with the paper's heuristics switched on as asked."""
         a = np.ascontiguousarray(action, np.float32)
         o = StepOpts_c()
@@ -234,10 +241,27 @@ class Oracle:
         o.margin, o.band = float(margin), float(band)
         o.slide, o.place_jitter = int(slide), int(place_jitter)
         o.seed, o.env = int(seed), int(env)
+        o.column = int(column)
         out = StepOut_c()
         self.L.orc_step_ex(C.byref(self.robot), C.byref(self.scene), C.byref(st), _p(a, f32p),
                            C.byref(o), C.byref(out))
         return out
+
+    def column_spans(self, ri, i, k):
+        sp = np.zeros((64, 2))
+        n = self.L.orc_column_spans(C.byref(self.scene), int(ri), int(i), int(k), _p(sp, f64p), 64)
+        return sp[:n]
+
+    def column_dims(self):
+        d = np.zeros(2, np.int32)
+        self.L.orc_column_dims(C.byref(self.scene), _p(d, i32p))
+        return tuple(int(x) for x in d)
+
+    def column_contact(self, c, r):
+        cc = np.ascontiguousarray(c, np.float64)
+        nb = C.c_int()
+        hit = self.L.orc_column_contact(C.byref(self.scene), _p(cc, f64p), float(r), C.byref(nb))
+        return bool(hit), nb.value
 
     def grid_gradient(self, c):
         cc = np.ascontiguousarray(c, np.float64)

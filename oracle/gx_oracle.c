@@ -119,6 +119,97 @@ int orc_grid_query(const orc_scene* s, const double c[3], double* d, double* edg
   return 1;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Column grid (appendix "Additional Collision-Detection Details"): for each */
+/* radius R of the working set {1.5, 5, 12} cm, a lattice of vertical       */
+/* columns 3 cm apart in XZ over the grid box (column (i, k) at origin +    */
+/* (i, k) * 3 cm); each column holds the free spans of the centre height y  */
+/* of a sphere of radius R: [oy, oy + (ny-1) h] minus, for every box whose  */
+/* XZ rectangle lies closer than R to the column, the open interval         */
+/* (y0 - e, y1 + e) with e = sqrt(R^2 - dxz^2).  A sphere of radius r is    */
+/* tested with the smallest R >= r (1e-5 relative tolerance) at the nearest */
+/* column: contact unless its centre height lies in a free span; a centre   */
+/* outside the columns' extent is contact.                                  */
+/* ------------------------------------------------------------------------ */
+static const double ORC_COL_R[3] = {0.015, 0.05, 0.12};
+#define ORC_COL_S 0.03
+#define ORC_COL_CAP 64
+
+int orc_column_radius_index(double r) {
+  for (int k = 0; k < 3; ++k)
+    if (r <= ORC_COL_R[k] * (1.0 + 1e-5)) return k;
+  return 2;
+}
+
+void orc_column_dims(const orc_scene* s, int32_t dims[2]) {
+  dims[0] = (int)floor((s->grid_dims[0] - 1) * (double)s->grid_h / ORC_COL_S + 1e-6) + 1;
+  dims[1] = (int)floor((s->grid_dims[2] - 1) * (double)s->grid_h / ORC_COL_S + 1e-6) + 1;
+}
+
+int orc_column_spans(const orc_scene* s, int ri, int i, int k, double spans[][2], int cap) {
+  const double R = ORC_COL_R[ri];
+  const double x = (double)s->grid_origin[0] + i * ORC_COL_S;
+  const double z = (double)s->grid_origin[2] + k * ORC_COL_S;
+  const double ylo = (double)s->grid_origin[1];
+  const double yhi = ylo + (s->grid_dims[1] - 1) * (double)s->grid_h;
+  double iv[ORC_COL_CAP][2];
+  int n = 0;
+  for (int b = 0; b < s->n_boxes && n < ORC_COL_CAP; ++b) {
+    const float* bx = s->boxes + 6 * b;
+    double dx = fmax(fmax((double)bx[0] - x, 0.0), x - (double)bx[3]);
+    double dz = fmax(fmax((double)bx[2] - z, 0.0), z - (double)bx[5]);
+    double d2 = dx * dx + dz * dz;
+    if (d2 >= R * R) continue;
+    double e = sqrt(R * R - d2);
+    double lo = (double)bx[1] - e, hi = (double)bx[4] + e;
+    if (hi <= ylo || lo >= yhi) continue;
+    /* insertion by lower end */
+    int m = n++;
+    while (m > 0 && iv[m - 1][0] > lo) {
+      iv[m][0] = iv[m - 1][0];
+      iv[m][1] = iv[m - 1][1];
+      --m;
+    }
+    iv[m][0] = lo;
+    iv[m][1] = hi;
+  }
+  int ns = 0;
+  double cur = ylo;
+  for (int t = 0; t < n; ++t) {
+    if (iv[t][0] > cur && ns < cap) {
+      spans[ns][0] = cur;
+      spans[ns][1] = iv[t][0];
+      ns++;
+    }
+    if (iv[t][1] > cur) cur = iv[t][1];
+  }
+  if (cur <= yhi && ns < cap) {
+    spans[ns][0] = cur;
+    spans[ns][1] = yhi;
+    ns++;
+  }
+  return ns;
+}
+
+int orc_column_contact(const orc_scene* s, const double c[3], double r, int* nb) {
+  int32_t dims[2];
+  orc_column_dims(s, dims);
+  const double fi = (c[0] - (double)s->grid_origin[0]) / ORC_COL_S;
+  const double fk = (c[2] - (double)s->grid_origin[2]) / ORC_COL_S;
+  if (fabs(fi - floor(fi) - 0.5) < ORC_BAND / ORC_COL_S) (*nb)++;
+  if (fabs(fk - floor(fk) - 0.5) < ORC_BAND / ORC_COL_S) (*nb)++;
+  const int i = (int)floor(fi + 0.5), k = (int)floor(fk + 0.5);
+  if (i < 0 || i >= dims[0] || k < 0 || k >= dims[1]) return 1;
+  double sp[ORC_COL_CAP][2];
+  const int n = orc_column_spans(s, orc_column_radius_index(r), i, k, sp, ORC_COL_CAP);
+  int free_ = 0;
+  for (int t = 0; t < n; ++t) {
+    if (fabs(c[1] - sp[t][0]) < ORC_BAND || fabs(c[1] - sp[t][1]) < ORC_BAND) (*nb)++;
+    if (c[1] >= sp[t][0] && c[1] <= sp[t][1]) free_ = 1;
+  }
+  return !free_;
+}
+
 /* Gradient of the trilinear interpolant at c (the cell the query above
  * uses), per metre; 0 outside the lattice box. */
 int orc_grid_gradient(const orc_scene* s, const double c[3], double g[3]) {
@@ -458,8 +549,9 @@ void orc_step_ex(const orc_robot* rb, const orc_scene* sc, orc_state* st, const 
   int h = st->held;
   for (int i = 0; i < rb->n_spheres; ++i) {
     double r = rb->sphere_radius[i];
-    int hit = dhat ? neural_static_contact(sc, cs[i], r, dhat[i], margin, band, &nb)
-                   : static_contact(sc, cs[i], r, &nb);
+    int hit = opt->column ? orc_column_contact(sc, cs[i], r, &nb)
+              : dhat      ? neural_static_contact(sc, cs[i], r, dhat[i], margin, band, &nb)
+                          : static_contact(sc, cs[i], r, &nb);
     if (hit) { mask |= 1u << i; flags |= 1; }
     for (int j = 0; j < st->n_obj; ++j) {
       if (j == h) continue;
@@ -470,8 +562,9 @@ void orc_step_ex(const orc_robot* rb, const orc_scene* sc, orc_state* st, const 
     double ph[3];
     fr_apply(ee, st->c_off, ph);
     double rho = st->obj[h][3];
-    int hit = dhat ? neural_static_contact(sc, ph, rho, dhat[30], margin, band, &nb)
-                   : static_contact(sc, ph, rho, &nb);
+    int hit = opt->column ? orc_column_contact(sc, ph, rho, &nb)
+              : dhat      ? neural_static_contact(sc, ph, rho, dhat[30], margin, band, &nb)
+                          : static_contact(sc, ph, rho, &nb);
     if (hit) { mask |= 1u << 30; flags |= 1 | 4; }
     for (int j = 0; j < st->n_obj; ++j) {
       if (j == h) continue;

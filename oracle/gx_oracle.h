@@ -113,7 +113,15 @@ typedef struct {
   int32_t slide, place_jitter;
   uint64_t seed;
   int32_t env;
+  int32_t column;          /* 1: static test on the column grid             */
 } orc_step_opts;
+/* Column grid (see gx_oracle.c): working-set radius index for r, columns
+ * per axis, free spans of column (i, k) at radius index ri, and the sphere
+ * test. */
+int orc_column_radius_index(double r);
+void orc_column_dims(const orc_scene* s, int32_t dims[2]);
+int orc_column_spans(const orc_scene* s, int ri, int i, int k, double spans[][2], int cap);
+int orc_column_contact(const orc_scene* s, const double c[3], double r, int* nb);
 void orc_step_ex(const orc_robot* rb, const orc_scene* sc, orc_state* st, const float act[11],
                  const orc_step_opts* opt, orc_step_out* out);
 int orc_grid_gradient(const orc_scene* s, const double c[3], double g[3]);
