@@ -114,7 +114,8 @@ def golden(name):
 
 # Workloads whose views are drawn from another workload's scenes and camera
 # statistics (the static test differs, the rendering work per view does not).
-SAME_VIEWS = {"apartments4096_nsdf": "apartments4096", "uneven16384_nsdf": "uneven8192"}
+SAME_VIEWS = {"apartments4096_nsdf": "apartments4096", "uneven16384_nsdf": "uneven8192",
+              "apartments4096_column": "apartments4096"}
 
 
 def raster_work(workload):
@@ -331,8 +332,10 @@ def config_of(w):
             "resets": (f"{w.reset_every}-step episodes, staggered" if w.reset_every
                        else f"Bernoulli p={w.reset_prob} per env-step"),
             "l2": "no flush: each step writes more observation bytes than L2 holds",
-            "static_test": (f"neural SDF, grid below {w.sdf_margin} m predicted clearance"
-                            if w.sdf == "neural" else "distance grid")}
+            "static_test": {"neural": f"neural SDF, grid below {w.sdf_margin} m predicted "
+                                      f"clearance",
+                            "column": "column grid (radii 1.5/5/12 cm, 3 cm columns)"}.get(
+                                w.sdf, "distance grid")}
 
 
 def run_reference(args, w, rank, world):
@@ -433,8 +436,10 @@ def main():
     sim_kw = dict(img=(w.img, w.img), depth_fp16=w.depth_fp16, render_rgb=w.rgb,
                   n_objects=w.n_objects, obj_radius=w.obj_radius, seed=rank_seeds(w, rank)[0],
                   small_tri_px=args.small_px, heuristics=args.heuristics)
+    column = w.sdf == "column"
+    sdf_mode = 1 if neural else (2 if column else 0)
     sim = gx.Sim(ss, I.fetch_like_robot(), n, profile=0 if args.graph else 1,
-                 use_graph=args.graph, sdf_mode=1 if neural else 0, sdf_margin=w.sdf_margin,
+                 use_graph=args.graph, sdf_mode=sdf_mode, sdf_margin=w.sdf_margin,
                  **sim_kw)
     total = args.warmup + args.steps
     acts = torch.from_numpy(I.make_actions(total, n, w.action_dist,
@@ -489,9 +494,9 @@ def main():
     phase_ms, phase_n = sim.phase_times() if not args.graph else ([0] * 4, [0] * 4)
     dev_err = sim.device_error()
     value, ms = job_value(dist, n, args.steps, ms)
-    if neural:
-        # the grid form of the same workload, timed the same way, and the
-        # neural form's decisions counted against the grid-only rule
+    static_form = None
+    if neural or column:
+        # the grid form of the same workload, timed the same way
         g = gx.Sim(ss, I.fetch_like_robot(), n, profile=1, **sim_kw)
         with torch.cuda.stream(stream):
             g.reset(stream=stream)
@@ -513,7 +518,20 @@ def main():
         g1.record(stream)
         torch.cuda.synchronize()
         grid_value, _ = job_value(dist, n, args.steps, g0.elapsed_time(g1))
+        g_ms, g_n = g.phase_times()
+        grid_physics_ms = g_ms[0] / max(g_n[0], 1)
         g.close()
+        grid_bytes = [int(np.prod(sc.grid_dims)) * 4 for sc in scenes]
+        if column:
+            cb = [ss.column_info(s)[1] for s in range(len(scenes))]
+            static_form = {"grid_form_value": grid_value, "column_over_grid": value / grid_value,
+                           "physics_ms": {"column": phase_ms[0] / max(phase_n[0], 1),
+                                          "grid": grid_physics_ms},
+                           "bytes_per_scene": {"grid_mean": float(np.mean(grid_bytes)),
+                                               "column_mean": float(np.mean(cb))},
+                           "note": "release, reset and the heuristics still read the grid"}
+    if neural:
+        # the neural form's decisions counted against the grid-only rule
         c = gx.Sim(ss, I.fetch_like_robot(), n, profile=4, sdf_mode=1, sdf_margin=w.sdf_margin,
                    **sim_kw)
         c.reset()
@@ -522,7 +540,6 @@ def main():
             c.step(acts[t])
         cnt = c.nsdf_counters()
         c.close()
-        grid_bytes = [int(np.prod(sc.grid_dims)) * 4 for sc in scenes]
         q_ms = phase_ms[3] / max(phase_n[3], 1)
         nsdf.update({
             "grid_form_value": grid_value, "neural_over_grid": value / grid_value,
@@ -603,6 +620,7 @@ def main():
                                  for i, k in enumerate(["physics", "raster", "reset",
                                                         "nsdf_query"])},
         "nsdf": nsdf,
+        "column_grid": static_form,
         "autotune": tune,
         "raster_counters_per_view": counters,
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,

@@ -138,6 +138,15 @@ typedef struct {
                               bit 2: count neural-SDF decisions against the
                               grid-only rule (evaluates both; slower)         */
   int32_t sdf_mode;        /* 0: static test on the distance grid;
+                              2: on the column grid (appendix "Additional
+                              Collision-Detection Details"): per working-set
+                              radius {1.5, 5, 12} cm, columns 3 cm apart in XZ
+                              over the grid box holding the free spans of a
+                              sphere centre's height; a sphere uses the
+                              smallest working radius R not below its own r at
+                              the nearest column, the spans widened by R - r
+                              at both ends (release, reset and the sliding
+                              heuristic keep the distance grid);
                               1: neural SDF (every scene an environment uses
                               needs weights, gx_nsdf_set_weights): the grid is
                               consulted only where the predicted clearance
@@ -348,6 +357,17 @@ typedef struct {
  * stream. */
 gx_status gx_nsdf_train(gx_scene_set* set, int32_t scene, const gx_train_params* params,
                         float* loss_host, void* stream);
+
+/* Column grid of a scene (built with the scene set; see sdf_mode 2): columns
+ * per axis (dims[0] along x, dims[1] along z) and its size in device bytes
+ * (bytes may be NULL). */
+gx_status gx_column_info(const gx_scene_set* set, int32_t scene, int32_t dims[2], uint64_t* bytes);
+/* Free spans (lo, hi pairs, host float [cap][2]) of column (i, k) at
+ * working-set radius index 0, 1, 2 (1.5, 5, 12 cm); returns the number of
+ * spans (only the first cap are copied), -1 on a bad argument.  Waits for
+ * the device. */
+int32_t gx_column_spans(const gx_scene_set* set, int32_t scene, int32_t radius_index, int32_t i,
+                        int32_t k, float* spans, int32_t cap);
 
 /* Renders depth (and RGB when rgb != NULL) for n environments without
  * allocating any device memory.  The paper has no counterpart: this serves

@@ -128,8 +128,8 @@ int orc_grid_query(const orc_scene* s, const double c[3], double* d, double* edg
 /* XZ rectangle lies closer than R to the column, the open interval         */
 /* (y0 - e, y1 + e) with e = sqrt(R^2 - dxz^2).  A sphere of radius r is    */
 /* tested with the smallest R >= r (1e-5 relative tolerance) at the nearest */
-/* column: contact unless its centre height lies in a free span; a centre   */
-/* outside the columns' extent is contact.                                  */
+/* column: contact unless its centre height lies in a free span widened by  */
+/* R - r at both ends; a centre outside the columns' extent is contact.     */
 /* ------------------------------------------------------------------------ */
 static const double ORC_COL_R[3] = {0.015, 0.05, 0.12};
 #define ORC_COL_S 0.03
@@ -196,16 +196,24 @@ int orc_column_contact(const orc_scene* s, const double c[3], double r, int* nb)
   orc_column_dims(s, dims);
   const double fi = (c[0] - (double)s->grid_origin[0]) / ORC_COL_S;
   const double fk = (c[2] - (double)s->grid_origin[2]) / ORC_COL_S;
-  if (fabs(fi - floor(fi) - 0.5) < ORC_BAND / ORC_COL_S) (*nb)++;
-  if (fabs(fk - floor(fk) - 0.5) < ORC_BAND / ORC_COL_S) (*nb)++;
+  /* nearest-column choice: near band within 1e-5 m of a column boundary
+   * (FP32 and FP64 sphere centres agree to a few 1e-6 m) */
+  if (fabs(fi - floor(fi) - 0.5) < 1e-5 / ORC_COL_S) (*nb)++;
+  if (fabs(fk - floor(fk) - 0.5) < 1e-5 / ORC_COL_S) (*nb)++;
   const int i = (int)floor(fi + 0.5), k = (int)floor(fk + 0.5);
   if (i < 0 || i >= dims[0] || k < 0 || k >= dims[1]) return 1;
   double sp[ORC_COL_CAP][2];
-  const int n = orc_column_spans(s, orc_column_radius_index(r), i, k, sp, ORC_COL_CAP);
+  const int ri = orc_column_radius_index(r);
+  const int n = orc_column_spans(s, ri, i, k, sp, ORC_COL_CAP);
+  /* the spans are for radius R >= r: widened by R - r at both ends (exact
+   * for surfaces directly above or below the column, conservative beside
+   * walls, which block the whole column within R) */
+  const double w = ORC_COL_R[ri] > r ? ORC_COL_R[ri] - r : 0.0;
   int free_ = 0;
   for (int t = 0; t < n; ++t) {
-    if (fabs(c[1] - sp[t][0]) < ORC_BAND || fabs(c[1] - sp[t][1]) < ORC_BAND) (*nb)++;
-    if (c[1] >= sp[t][0] && c[1] <= sp[t][1]) free_ = 1;
+    const double lo = sp[t][0] - w, hi = sp[t][1] + w;
+    if (fabs(c[1] - lo) < ORC_BAND || fabs(c[1] - hi) < ORC_BAND) (*nb)++;
+    if (c[1] >= lo && c[1] <= hi) free_ = 1;
   }
   return !free_;
 }

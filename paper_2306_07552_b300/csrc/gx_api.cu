@@ -1,4 +1,5 @@
 // Host implementation of the C ABI declared in include/gx.h.
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -182,6 +183,7 @@ void enqueue_step(gx_ctx* c, const float* actions, const gx_outputs& out, cudaSt
   pp.slide = c->cfg.heuristics & 1;
   pp.place_jitter = (c->cfg.heuristics >> 1) & 1;
   pp.seed = c->cfg.seed;
+  pp.column = c->cfg.sdf_mode == 2;
   if (c->cfg.sdf_mode == 1) {
     pp.nsdf_pts = c->d_nsdf_pts;
     pp.nsdf_d = c->d_nsdf_d;
@@ -316,6 +318,55 @@ extern "C" gx_status gx_scene_set_create(const gx_scene_desc* scenes, int32_t n_
     launch_grid_build(grid, dboxes, d.n_boxes, ds.ox, ds.oy, ds.oz, ds.h, ds.nx, ds.ny, ds.nz, 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "grid kernel");
     ds.grid = grid;
+    {
+      // column grid over the same box: count, prefix sum on the host, fill
+      const double h = (double)ds.h;
+      ds.ncx = (int)std::floor((ds.nx - 1) * h / kColumnSpacing + 1e-6) + 1;
+      ds.ncz = (int)std::floor((ds.nz - 1) * h / kColumnSpacing + 1e-6) + 1;
+      const size_t ncol = (size_t)3 * ds.ncx * ds.ncz;
+      const double ylo = (double)ds.oy, yhi = ylo + (ds.ny - 1) * h;
+      uint32_t *cnt = nullptr, *off = nullptr;
+      unsigned* ovf = nullptr;
+      float2* spans = nullptr;
+      if ((e = cudaMalloc(&cnt, ncol * 4)) != cudaSuccess) return bail(e, "columns");
+      s->allocs.push_back(cnt);
+      if ((e = cudaMalloc(&ovf, 4)) != cudaSuccess) return bail(e, "columns");
+      s->allocs.push_back(ovf);
+      cudaMemset(ovf, 0, 4);
+      launch_column_build(dboxes, d.n_boxes, (double)ds.ox, (double)ds.oz, ylo, yhi, ds.ncx, ds.ncz,
+                          nullptr, cnt, nullptr, ovf, 0);
+      std::vector<uint32_t> hc(ncol);
+      if ((e = cudaMemcpy(hc.data(), cnt, ncol * 4, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return bail(e, "column counts");
+      std::vector<uint32_t> ho(ncol + 1);
+      uint64_t acc = 0;
+      for (size_t c = 0; c < ncol; ++c) {
+        ho[c] = (uint32_t)acc;
+        acc += hc[c];
+      }
+      ho[ncol] = (uint32_t)acc;
+      if (acc >= ((uint64_t)1 << 32)) {
+        free_set(s);
+        return fail(nullptr, GX_EINVAL, "scene %d: too many column spans", i);
+      }
+      if ((e = upload(s, &off, ho.data(), ho.size())) != cudaSuccess) return bail(e, "columns");
+      if ((e = cudaMalloc(&spans, (acc ? acc : 1) * sizeof(float2))) != cudaSuccess)
+        return bail(e, "column spans");
+      s->allocs.push_back(spans);
+      launch_column_build(dboxes, d.n_boxes, (double)ds.ox, (double)ds.oz, ylo, yhi, ds.ncx, ds.ncz,
+                          off, cnt, spans, ovf, 0);
+      unsigned hovf = 0;
+      if ((e = cudaMemcpy(&hovf, ovf, 4, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return bail(e, "column build");
+      if (hovf) {
+        free_set(s);
+        return fail(nullptr, GX_EINVAL, "scene %d: a column meets more than %d boxes", i,
+                    kColumnCap);
+      }
+      ds.col_off = off;
+      ds.col_spans = spans;
+      s->column_bytes.push_back((ncol + 1) * 4 + acc * sizeof(float2));
+    }
   }
   std::vector<float4> ov(mesh->n_verts);
   for (int k = 0; k < mesh->n_verts; ++k)
@@ -373,7 +424,7 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
       if (c.env_scene[i] < 0 || c.env_scene[i] >= set->n)
         return fail(nullptr, GX_EINVAL, "env_scene[%d] out of range", i);
   if (c.raster_regions != 0) return fail(nullptr, GX_EINVAL, "raster_regions is reserved (0)");
-  if (c.sdf_mode != 0 && c.sdf_mode != 1) return fail(nullptr, GX_EINVAL, "sdf_mode must be 0 or 1");
+  if (c.sdf_mode < 0 || c.sdf_mode > 2) return fail(nullptr, GX_EINVAL, "sdf_mode must be 0, 1 or 2");
   if (c.heuristics & ~3) return fail(nullptr, GX_EINVAL, "heuristics: only bits 0 and 1 are defined");
   if (c.sdf_mode == 1 && !(c.sdf_margin >= 0.f && c.sdf_margin < 1e30f))
     return fail(nullptr, GX_EINVAL, "sdf_margin must be finite and >= 0");
@@ -812,6 +863,35 @@ extern "C" gx_status gx_nsdf_counters(gx_ctx* x, int64_t out[4]) {
   CK(x, cudaMemset(x->d_nsdf_counters, 0, sizeof(h)));
   for (int k = 0; k < kNsdfCounters; ++k) out[k] = (int64_t)h[k];
   return GX_OK;
+}
+
+extern "C" gx_status gx_column_info(const gx_scene_set* set, int32_t scene, int32_t dims[2],
+                                   uint64_t* bytes) {
+  if (!set || scene < 0 || scene >= set->n || !dims)
+    return fail(nullptr, GX_EINVAL, "gx_column_info: bad argument");
+  dims[0] = set->host[scene].ncx;
+  dims[1] = set->host[scene].ncz;
+  if (bytes) *bytes = set->column_bytes[scene];
+  return GX_OK;
+}
+
+extern "C" int32_t gx_column_spans(const gx_scene_set* set, int32_t scene, int32_t radius_index,
+                                   int32_t i, int32_t k, float* spans, int32_t cap) {
+  if (!set || scene < 0 || scene >= set->n || radius_index < 0 || radius_index > 2 || !spans ||
+      cap < 0)
+    return -1;
+  const DScene& d = set->host[scene];
+  if (i < 0 || i >= d.ncx || k < 0 || k >= d.ncz) return -1;
+  const size_t idx = ((size_t)radius_index * d.ncz + k) * d.ncx + i;
+  uint32_t ab[2];
+  if (cudaMemcpy(ab, d.col_off + idx, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+  const int n = (int)(ab[1] - ab[0]);
+  const int m = n < cap ? n : cap;
+  if (m > 0 &&
+      cudaMemcpy(spans, d.col_spans + ab[0], (size_t)m * sizeof(float2), cudaMemcpyDeviceToHost) !=
+          cudaSuccess)
+    return -1;
+  return n;
 }
 
 extern "C" const char* gx_last_error(const gx_ctx* x) {

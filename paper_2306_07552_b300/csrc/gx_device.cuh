@@ -73,6 +73,28 @@ __device__ bool grid_query_grad(const DScene& s, float cx, float cy, float cz, f
   return true;
 }
 
+// Column-grid test of a sphere (c, r): the smallest working-set radius R not
+// below r (1e-5 relative tolerance), the nearest column (floor(f + 0.5)),
+// contact unless the centre height lies in one of the column's free spans
+// widened by R - r at both ends; outside the columns' extent is contact.
+__device__ bool column_contact(const DScene& s, float cx, float cy, float cz, float r) {
+  const int ri = r <= 0.015f * 1.00001f ? 0 : (r <= 0.05f * 1.00001f ? 1 : 2);
+  // spans are for radius R >= r: widened by R - r at both ends
+  const float w = fmaxf((ri == 0 ? 0.015f : (ri == 1 ? 0.05f : 0.12f)) - r, 0.f);
+  const float fi = (cx - s.ox) * (float)(1.0 / kColumnSpacing);
+  const float fk = (cz - s.oz) * (float)(1.0 / kColumnSpacing);
+  if (!(fi > -0.5f && fk > -0.5f)) return true;  // also catches NaN
+  const int i = (int)floorf(fi + 0.5f), k = (int)floorf(fk + 0.5f);
+  if (i >= s.ncx || k >= s.ncz) return true;
+  const int idx = (ri * s.ncz + k) * s.ncx + i;
+  const uint32_t a = __ldg(s.col_off + idx), b = __ldg(s.col_off + idx + 1);
+  for (uint32_t t = a; t < b; ++t) {
+    const float2 sp = __ldg(s.col_spans + t);
+    if (cy >= sp.x - w && cy <= sp.y + w) return false;
+  }
+  return true;
+}
+
 // true when c lies inside the lattice box (and is finite).
 __device__ __forceinline__ bool grid_contains(const DScene& s, float cx, float cy, float cz) {
   const float gx = (cx - s.ox) * s.inv_h, gy = (cy - s.oy) * s.inv_h, gz = (cz - s.oz) * s.inv_h;

@@ -44,7 +44,77 @@ __global__ void grid_kernel(float* __restrict__ grid, const float* __restrict__ 
   }
 }
 
+// Column grid (appendix "Additional Collision-Detection Details"): one
+// thread per (radius, column), FP64 like the distance grid: the free spans
+// of a sphere centre's height, [ylo, yhi] minus the open interval
+// (y0 - e, y1 + e), e = sqrt(R^2 - dxz^2), of every box closer than R in XZ.
+// Count pass (offsets == nullptr) then fill pass.
+__global__ void column_kernel(const float* __restrict__ boxes, int n_boxes, double ox, double oz,
+                              double ylo, double yhi, int ncx, int ncz,
+                              const uint32_t* __restrict__ offsets, uint32_t* __restrict__ counts,
+                              float2* __restrict__ spans, unsigned* overflow) {
+  extern __shared__ double cb[];  // [n_boxes][6]
+  for (int b = threadIdx.x; b < n_boxes; b += blockDim.x)
+    for (int a = 0; a < 6; ++a) cb[6 * b + a] = boxes[6 * b + a];
+  __syncthreads();
+  const int total = 3 * ncx * ncz;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    const int i = idx % ncx, k = (idx / ncx) % ncz, ri = idx / (ncx * ncz);
+    const double R = kColumnRadius[ri];
+    const double x = ox + i * kColumnSpacing, z = oz + k * kColumnSpacing;
+    double lo[kColumnCap], hi[kColumnCap];
+    int n = 0;
+    for (int b = 0; b < n_boxes; ++b) {
+      const double* bx = cb + 6 * b;
+      const double dx = fmax(fmax(bx[0] - x, 0.0), x - bx[3]);
+      const double dz = fmax(fmax(bx[2] - z, 0.0), z - bx[5]);
+      const double d2 = dx * dx + dz * dz;
+      if (d2 >= R * R) continue;
+      const double e = sqrt(R * R - d2);
+      const double l = bx[1] - e, h = bx[4] + e;
+      if (h <= ylo || l >= yhi) continue;
+      if (n == kColumnCap) {
+        atomicOr(overflow, 1u);
+        break;
+      }
+      int m = n++;
+      while (m > 0 && lo[m - 1] > l) {
+        lo[m] = lo[m - 1];
+        hi[m] = hi[m - 1];
+        --m;
+      }
+      lo[m] = l;
+      hi[m] = h;
+    }
+    uint32_t ns = 0;
+    const uint32_t o = offsets ? offsets[idx] : 0u;
+    double cur = ylo;
+    for (int t = 0; t < n; ++t) {
+      if (lo[t] > cur) {
+        if (offsets) spans[o + ns] = make_float2((float)cur, (float)lo[t]);
+        ++ns;
+      }
+      if (hi[t] > cur) cur = hi[t];
+    }
+    if (cur <= yhi) {
+      if (offsets) spans[o + ns] = make_float2((float)cur, (float)yhi);
+      ++ns;
+    }
+    if (!offsets) counts[idx] = ns;
+  }
+}
+
 }  // namespace
+
+void launch_column_build(const float* boxes, int n_boxes, double ox, double oz, double ylo,
+                         double yhi, int ncx, int ncz, const uint32_t* offsets, uint32_t* counts,
+                         float2* spans, unsigned* overflow, cudaStream_t s) {
+  const int total = 3 * ncx * ncz;
+  int blocks = (total + 127) / 128;
+  if (blocks > 148 * 16) blocks = 148 * 16;
+  column_kernel<<<blocks, 128, (size_t)n_boxes * 6 * sizeof(double), s>>>(
+      boxes, n_boxes, ox, oz, ylo, yhi, ncx, ncz, offsets, counts, spans, overflow);
+}
 
 void launch_grid_build(float* grid, const float* boxes, int n_boxes, float ox, float oy, float oz,
                        float h, int nx, int ny, int nz, cudaStream_t s) {

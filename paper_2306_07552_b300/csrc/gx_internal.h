@@ -36,6 +36,11 @@ struct DScene {
   const float* grid;        // [nz][ny][nx]
   float ox, oy, oz, h, inv_h;
   int nx, ny, nz;
+  // column grid: 3 working-set radii x ncz x ncx columns, CSR offsets into
+  // the free spans (lo, hi) of a sphere centre's height
+  const uint32_t* col_off;  // [3 * ncz * ncx + 1]
+  const float2* col_spans;
+  int ncx, ncz;
   const float* supports;    // [P][5]
   int n_supports;
   float spawn[4];
@@ -87,6 +92,7 @@ struct PhysicsParams {
   int slide;                            // sliding heuristic on
   int place_jitter;                     // object placing heuristic on
   uint64_t seed;                        // Philox key (the reset key)
+  int column;                           // static test on the column grid
   int nsdf_pass;                        // 0: grid only, 1: emit, 2: consume
   float4* nsdf_pts;                     // [n][32]
   const float* nsdf_d;                  // [n][32]
@@ -205,6 +211,7 @@ struct gx_scene_set {
   int omesh_nv = 0, omesh_nt = 0;
   std::vector<int> meshlets_per_scene;
   std::vector<gx::NsdfScene> nsdf;
+  std::vector<size_t> column_bytes;  // column grid size per scene
 };
 
 namespace gx {
@@ -236,6 +243,14 @@ struct SceneSetView {
 };
 bool scene_set_view(const gx_scene_set* set, SceneSetView* out);
 gx_status set_last_error(gx_status s, const char* msg);
+
+// Column grid constants (working-set radii, spacing, per-column interval cap).
+constexpr double kColumnSpacing = 0.03;
+constexpr int kColumnCap = 64;
+__device__ constexpr double kColumnRadius[3] = {0.015, 0.05, 0.12};
+void launch_column_build(const float* boxes, int n_boxes, double ox, double oz, double ylo,
+                         double yhi, int ncx, int ncz, const uint32_t* offsets, uint32_t* counts,
+                         float2* spans, unsigned* overflow, cudaStream_t s);
 
 size_t raster_smem_bytes();
 cudaError_t raster_configure(int* slots);

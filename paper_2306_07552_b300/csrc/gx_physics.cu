@@ -251,6 +251,8 @@ __global__ void __launch_bounds__(32 * kEnvsPerBlock) physics_kernel(const Physi
         if (inside && !trust) atomicAdd(P.nsdf_counters + kNsdfFallbacks, 1ull);
         if (cs != cs_grid) atomicAdd(P.nsdf_counters + kNsdfDisagree, 1ull);
       }
+    } else if (P.column) {
+      cs = column_contact(S, c[0], c[1], c[2], r);
     } else {
       cs = !grid_query(S, c[0], c[1], c[2], d) || d < r;
     }

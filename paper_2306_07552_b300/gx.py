@@ -29,7 +29,8 @@ SYMBOLS = ["gx_scene_set_create", "gx_scene_set_destroy", "gx_create", "gx_destr
            "gx_save_state", "gx_load_state", "gx_state_layout", "gx_phase_times",
            "gx_raster_counters", "gx_render_noalloc", "gx_nsdf_set_weights",
            "gx_nsdf_get_weights", "gx_nsdf_query", "gx_nsdf_get_master", "gx_nsdf_samples", "gx_nsdf_grad",
-           "gx_nsdf_train", "gx_nsdf_counters", "gx_autotune", "gx_last_error"]
+           "gx_nsdf_train", "gx_nsdf_counters", "gx_autotune", "gx_column_info", "gx_column_spans",
+           "gx_last_error"]
 NSDF_PARAMS = 57985
 NSDF_FREQ = 32
 RASTER_COUNTERS = ["clusters_tested", "clusters_drawn", "tris_seen", "tris_front", "tris_expand",
@@ -139,6 +140,9 @@ def lib():
         L.gx_nsdf_grad.argtypes = [vp, C.c_int32, vp, vp, C.c_int32, C.c_float, C.c_float, vp, vp,
                                    vp]
         L.gx_nsdf_counters.argtypes = [vp, C.POINTER(C.c_int64)]
+        L.gx_column_info.argtypes = [vp, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_uint64)]
+        L.gx_column_spans.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, vp, C.c_int32]
+        L.gx_column_spans.restype = C.c_int32
         L.gx_autotune.argtypes = [vp, vp, P(GxOutputs), C.c_int32, P(GxTuneResult), vp]
         L.gx_nsdf_train.argtypes = [vp, C.c_int32, C.POINTER(GxTrainParams), vp, vp]
         L.gx_last_error.argtypes = [vp]
@@ -241,6 +245,20 @@ class SceneSet:
                                    int(pts.shape[0]), C.c_void_p(out.data_ptr()),
                                    C.c_void_p(s.cuda_stream)))
         return out
+
+    def column_info(self, scene):
+        """(columns along x, columns along z), device bytes of a scene's column grid."""
+        d = (C.c_int32 * 2)()
+        b = C.c_uint64()
+        _check(lib().gx_column_info(self.handle, scene, d, C.byref(b)))
+        return (d[0], d[1]), b.value
+
+    def column_spans(self, scene, ri, i, k):
+        sp = np.zeros((64, 2), np.float32)
+        n = lib().gx_column_spans(self.handle, scene, ri, i, k, sp.ctypes.data, 64)
+        if n < 0:
+            raise ValueError("bad column")
+        return sp[:min(n, 64)]
 
     def nsdf_samples(self, scene, seed, first, n, near_band=0.1, stream=None):
         """Training samples [first, first + n): (CUDA [n][3] points, CUDA [n] labels)."""

@@ -522,6 +522,7 @@ class Workload:
     reset_seed: int = 1
     action_seed: int = 0
     sdf: str = "grid"        # static test: "grid" | "neural" (neural SDF, grid below margin)
+                             # | "column" (the paper's column grid)
     sdf_margin: float = 0.02
     nsdf_samples: int = 10_000_000
     nsdf_steps: int = 2000   # Adam steps per scene, batch 65,536
@@ -540,6 +541,9 @@ WORKLOADS = {
     "apartments4096_nsdf": Workload("apartments4096_nsdf", 4096, 16, "apartment", (20000, 60000),
                                     "uniform", 0.02, 40, (0.03, 0.06), 128, False, True, 500,
                                     "gauss0.5", 200, 0.0, 1000, sdf="neural"),
+    "apartments4096_column": Workload("apartments4096_column", 4096, 16, "apartment",
+                                      (20000, 60000), "uniform", 0.02, 40, (0.03, 0.06), 128,
+                                      False, True, 500, "gauss0.5", 200, 0.0, 1000, sdf="column"),
     "uneven16384_nsdf": Workload("uneven16384_nsdf", 16384, 64, "apartment", (5000, 150000),
                                  "loguniform", 0.02, 40, (0.03, 0.06), 128, True, True, 1000,
                                  "gauss0.5", 0, 0.005, 2000, sdf="neural"),

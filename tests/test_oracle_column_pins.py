@@ -105,6 +105,16 @@ def test_query_uses_the_nearest_column_and_inflated_radius():
     assert orc.column_contact([sc.grid_origin[0] - 0.05, 1.0, 0.0], 0.05)[0]
 
 
+def test_smaller_sphere_rests_on_the_floor_as_with_its_own_radius():
+    sc, orc = _room()
+    x = sc.grid_origin[0] + 40 * 0.03
+    for r in (0.03, 0.1, f32(0.1)):
+        # spans for R >= r widened by R - r: a sphere resting above the floor
+        # is free exactly when its centre is at least r high
+        assert not orc.column_contact([x, r + 1e-3, x], r)[0]
+        assert orc.column_contact([x, r - 1e-3, x], r)[0]
+
+
 def test_step_on_the_column_grid():
     wall = [0.45, -1.0, -5.0, 3.0, 3.0, 5.0]
     sc = scene_from_boxes([FLOOR, wall], (-2, -0.3, -2), (1.5, 2.5, 2), h=0.05)
