@@ -71,13 +71,16 @@ class State_c(C.Structure):
     _fields_ = [("base", C.c_double * 3), ("q", C.c_double * 7), ("held", C.c_int32),
                 ("c_off", C.c_double * 3), ("p_pre", C.c_double * 3), ("n_obj", C.c_int32),
                 ("obj", (C.c_double * 4) * MAX_OBJ), ("step_count", C.c_int32),
-                ("episode", C.c_int32)]
+                ("episode", C.c_int32), ("goal", C.c_double * 3), ("obj_start", C.c_double * 3),
+                ("prev_a", C.c_double * 7), ("prev_d", C.c_double), ("prev_e", C.c_double)]
 
 
 class StepOut_c(C.Structure):
     _fields_ = [("contact_mask", C.c_uint32), ("flags", C.c_uint8), ("event", C.c_uint8),
                 ("reverted", C.c_uint8), ("pad", C.c_uint8), ("near_band", C.c_int32),
-                ("ee", C.c_double * 3), ("cam_R", C.c_double * 9), ("cam_t", C.c_double * 3)]
+                ("ee", C.c_double * 3), ("cam_R", C.c_double * 9), ("cam_t", C.c_double * 3),
+                ("reward", C.c_double), ("task_obs", C.c_double * 12), ("success", C.c_uint8),
+                ("pad2", C.c_uint8 * 7)]
 
 
 class ResetOut_c(C.Structure):
@@ -202,7 +205,9 @@ class Oracle:
     # ---------------------------------------------------------------- state
     @staticmethod
     def make_state(base, q, held=-1, c_off=(0, 0, 0), p_pre=(0, 0, 0), objs=None,
-                   step_count=0, episode=0):
+                   step_count=0, episode=0, task=None):
+        """task: [16] goal xyz, target start xyz, previous joint actions [7],
+        previous tip-target and target-goal distances (the GPU's layout)."""
         st = State_c()
         st.base[:] = [float(x) for x in base]
         st.q[:] = [float(x) for x in q]
@@ -215,6 +220,12 @@ class Oracle:
             st.obj[j][:] = [float(x) for x in objs[j]]
         st.step_count = int(step_count)
         st.episode = int(episode)
+        if task is not None:
+            t = [float(x) for x in task]
+            st.goal[:] = t[0:3]
+            st.obj_start[:] = t[3:6]
+            st.prev_a[:] = t[6:13]
+            st.prev_d, st.prev_e = t[13], t[14]
         return st
 
     @staticmethod

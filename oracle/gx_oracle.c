@@ -702,6 +702,45 @@ void orc_step_ex(const orc_robot* rb, const orc_scene* sc, orc_state* st, const 
   if (st->held >= 0) fr_apply(ee, st->c_off, st->obj[st->held]);
   st->step_count += 1;
 
+  /* reward of the rearrangement task (App. "Additional Task Details"):
+   *   r = 10 I_success + 5 I_pick + (d_{t-1} - d_t) + (e_{t-1} - e_t) - 0.001 C_t
+   * with d the tip-target distance, e the target-goal distance, C_t the
+   * squared change of the 7 joint actions; success = stop called while the
+   * target rests within 15 cm of the goal; pick = the target just grasped.
+   * Egomotion observations (Sec. 4.1): the target's start and the goal
+   * relative to the base and to the tool tip, in the base frame. */
+  {
+    const double tip[3] = {ee[9], ee[10], ee[11]};
+    double C = 0.0;
+    for (int k = 0; k < 7; ++k) C += (a[2 + k] - st->prev_a[k]) * (a[2 + k] - st->prev_a[k]);
+    double r = -0.001 * C;
+    uint8_t success = 0;
+    if (st->n_obj > 0) {
+      const double d = dist3(tip, st->obj[0]), e = dist3(st->obj[0], st->goal);
+      const int pick = event == 1 && st->held == 0;
+      if (a[10] >= 0.5 && st->held != 0) {
+        if (fabs(e - 0.15) < ORC_BAND) nb++;
+        success = e < 0.15;
+      }
+      r += 10.0 * success + 5.0 * pick + (st->prev_d - d) + (st->prev_e - e);
+      st->prev_d = d;
+      st->prev_e = e;
+    }
+    for (int k = 0; k < 7; ++k) st->prev_a[k] = a[2 + k];
+    const double c = cos(st->base[2]), sn = sin(st->base[2]);
+    const double pb[3] = {st->base[0], 0.0, st->base[1]};
+    const double* from[4] = {pb, pb, tip, tip};
+    const double* to[4] = {st->obj_start, st->goal, st->obj_start, st->goal};
+    for (int v = 0; v < 4; ++v) {
+      const double w[3] = {to[v][0] - from[v][0], to[v][1] - from[v][1], to[v][2] - from[v][2]};
+      out->task_obs[3 * v] = c * w[0] - sn * w[2];
+      out->task_obs[3 * v + 1] = w[1];
+      out->task_obs[3 * v + 2] = sn * w[0] + c * w[2];
+    }
+    out->reward = r;
+    out->success = success;
+  }
+
   out->contact_mask = mask;
   out->flags = flags;
   out->event = event;
@@ -767,6 +806,31 @@ void orc_reset(const orc_robot* rb, const orc_scene* sc, orc_state* st, uint64_t
   memset(st->c_off, 0, sizeof(st->c_off));
   memset(st->p_pre, 0, sizeof(st->p_pre));
   st->step_count = 0;
+  /* task: object 0 is the target; its goal lies on a support top, drawn
+   * like an object placement from stream 65 (first draw, not tested for
+   * collisions); the previous distances start at the episode's first pose
+   * and the previous joint actions at 0. */
+  memset(st->goal, 0, sizeof(st->goal));
+  memset(st->obj_start, 0, sizeof(st->obj_start));
+  memset(st->prev_a, 0, sizeof(st->prev_a));
+  st->prev_d = st->prev_e = 0.0;
+  if (n_obj > 0 && sc->n_supports > 0) {
+    uint32_t ctr[4] = {(uint32_t)env, (uint32_t)st->episode, 65u, 0u}, w[4];
+    orc_philox4x32_10(ctr, key, w);
+    const double rho = st->obj[0][3];
+    uint32_t si = (uint32_t)(((uint64_t)(w[0] >> 8) * (uint64_t)sc->n_supports) >> 24);
+    const float* sp = sc->supports + 5 * si;
+    double x0 = sp[0] + rho, x1 = sp[2] - rho, z0 = sp[1] + rho, z1 = sp[3] - rho;
+    st->goal[0] = x0 + unit24(w[1]) * (x1 - x0);
+    st->goal[1] = (double)sp[4] + rho + clear;
+    st->goal[2] = z0 + unit24(w[2]) * (z1 - z0);
+    memcpy(st->obj_start, st->obj[0], 3 * sizeof(double));
+    double links[8][12], ee[12];
+    orc_fk(rb, st->base, st->q, links, ee, NULL);
+    const double tip[3] = {ee[9], ee[10], ee[11]};
+    st->prev_d = dist3(tip, st->obj[0]);
+    st->prev_e = dist3(st->obj[0], st->goal);
+  }
   out->near_band = nb;
   out->failed = failed;
 }

@@ -63,6 +63,11 @@ typedef struct {
   double obj[ORC_MAX_OBJ][4]; /* x y z rho                                  */
   int32_t step_count;
   int32_t episode;
+  /* rearrangement task (object 0 is the target) */
+  double goal[3];           /* goal position of the target                  */
+  double obj_start[3];      /* the target's position at the episode start   */
+  double prev_a[7];         /* previous step's joint actions (clipped)      */
+  double prev_d, prev_e;    /* previous tip-target, target-goal distances   */
 } orc_state;
 
 typedef struct {
@@ -75,6 +80,11 @@ typedef struct {
   double ee[3];
   double cam_R[9];          /* camera-to-world, columns right, up, forward  */
   double cam_t[3];
+  double reward;            /* App. "Additional Task Details", r_t          */
+  double task_obs[12];      /* base frame: start - base, goal - base,
+                               start - tip, goal - tip                      */
+  uint8_t success;
+  uint8_t pad2[7];
 } orc_step_out;
 
 typedef struct {
