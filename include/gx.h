@@ -179,7 +179,20 @@ typedef struct {
   uint32_t* contact_mask;  /* [n] bit i robot sphere i, bit 30 held object    */
   uint8_t* contact_flags;  /* [n] 1 static, 2 object, 4 held object           */
   uint8_t* event;          /* [n] 0 none, 1 grasped, 2 grasp missed,
-                              3 released and landed, 4 released and restored */
+                              3 released and landed, 4 released and restored,
+                              5 released and landed after placing jitters    */
+  /* rearrangement task (object 0 is the target; its goal is drawn at reset
+   * on a support top): */
+  float* reward;           /* [n] 10 success + 5 pick + (d_{t-1} - d_t)
+                              + (e_{t-1} - e_t) - 0.001 sum_k (a_k - a'_k)^2,
+                              d tip-target, e target-goal distance, a / a' this
+                              and the previous step's clipped joint actions;
+                              success: stop >= 0.5 with the target released
+                              within 0.15 m of the goal; pick: the target was
+                              just grasped (App. "Additional Task Details")  */
+  float* task_obs;         /* [n][12] in the base frame: target start - base,
+                              goal - base, target start - tip, goal - tip      */
+  uint8_t* success;        /* [n]                                              */
 } gx_outputs;
 
 /* Builds the device copies of `n_scenes` scenes: the FP32 signed-distance
@@ -230,9 +243,11 @@ gx_status gx_load_state(gx_ctx* ctx, const void* host, size_t bytes);
 /* Byte offsets of the state arrays, in this order: base_x, base_z, yaw
  * [n] f32; q [7][n] f32; held [n] i32; c_off [3][n] f32 (held object in the
  * tool-tip frame); p_pre [3][n] f32 (its pre-grasp position); obj
- * [n][n_objects][4] f32 (x, y, z, radius); step [n] i32; episode [n] i32.
+ * [n][n_objects][4] f32 (x, y, z, radius); step [n] i32; episode [n] i32;
+ * task [n][16] f32 (goal xyz, target start xyz, previous joint actions [7],
+ * previous tip-target and target-goal distances, unused).
  * Each array starts on a 256-byte boundary of the blob. */
-gx_status gx_state_layout(const gx_ctx* ctx, size_t offsets[10]);
+gx_status gx_state_layout(const gx_ctx* ctx, size_t offsets[11]);
 
 /* Per-kernel device time recorded since the previous call when the context
  * was created with profile bit 0 set: ms[0] physics (both passes when

@@ -38,7 +38,7 @@ struct gx_ctx {
   int* d_env_scene = nullptr;
   void* d_state = nullptr;
   size_t state_bytes = 0;
-  size_t off[10] = {0};
+  size_t off[11] = {0};
   StateView st{};
   float* d_cam = nullptr;
   unsigned* d_err = nullptr;
@@ -473,10 +473,10 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
     return bail(e, "map");
   // state blob: arrays on 256-byte boundaries
   const size_t n = x->n, M = x->M;
-  const size_t sizes[10] = {n * 4, n * 4, n * 4, 7 * n * 4, n * 4, 3 * n * 4, 3 * n * 4,
-                            n * (M ? M : 1) * 16, n * 4, n * 4};
+  const size_t sizes[11] = {n * 4, n * 4, n * 4, 7 * n * 4, n * 4, 3 * n * 4, 3 * n * 4,
+                            n * (M ? M : 1) * 16, n * 4, n * 4, n * 64};
   size_t off = 0;
-  for (int k = 0; k < 10; ++k) {
+  for (int k = 0; k < 11; ++k) {
     x->off[k] = off;
     off += (sizes[k] + 255) & ~(size_t)255;
   }
@@ -494,6 +494,7 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
   x->st.obj = (float4*)(b + x->off[7]);
   x->st.step = (int*)(b + x->off[8]);
   x->st.episode = (int*)(b + x->off[9]);
+  x->st.task = (float*)(b + x->off[10]);
   if ((e = cudaMemset(x->st.held, 0xff, n * 4)) != cudaSuccess) return bail(e, "state");
   if ((e = cudaMalloc(&x->d_cam, n * 12 * sizeof(float))) != cudaSuccess) return bail(e, "cam");
   if ((e = cudaMemset(x->d_cam, 0, n * 12 * sizeof(float))) != cudaSuccess) return bail(e, "cam");
@@ -678,6 +679,9 @@ extern "C" gx_status gx_step_host(gx_ctx* x, const float* actions_host, const gx
     CK(x, alloc((void**)&x->dev_out.contact_mask, n * 4));
     CK(x, alloc((void**)&x->dev_out.contact_flags, n));
     CK(x, alloc((void**)&x->dev_out.event, n));
+    CK(x, alloc((void**)&x->dev_out.reward, n * 4));
+    CK(x, alloc((void**)&x->dev_out.task_obs, n * 48));
+    CK(x, alloc((void**)&x->dev_out.success, n));
   }
   cudaStream_t s = (cudaStream_t)stream;
   CK(x, cudaMemcpyAsync(x->h2d_actions, actions_host, n * 11 * 4, cudaMemcpyHostToDevice, s));
@@ -693,6 +697,9 @@ extern "C" gx_status gx_step_host(gx_ctx* x, const float* actions_host, const gx
   if (h.contact_mask) CK(x, cudaMemcpyAsync(h.contact_mask, d.contact_mask, n * 4, cudaMemcpyDeviceToHost, s));
   if (h.contact_flags) CK(x, cudaMemcpyAsync(h.contact_flags, d.contact_flags, n, cudaMemcpyDeviceToHost, s));
   if (h.event) CK(x, cudaMemcpyAsync(h.event, d.event, n, cudaMemcpyDeviceToHost, s));
+  if (h.reward) CK(x, cudaMemcpyAsync(h.reward, d.reward, n * 4, cudaMemcpyDeviceToHost, s));
+  if (h.task_obs) CK(x, cudaMemcpyAsync(h.task_obs, d.task_obs, n * 48, cudaMemcpyDeviceToHost, s));
+  if (h.success) CK(x, cudaMemcpyAsync(h.success, d.success, n, cudaMemcpyDeviceToHost, s));
   CK(x, cudaStreamSynchronize(s));
   return poll_device_error(x, true);
 }
@@ -728,9 +735,9 @@ extern "C" gx_status gx_load_state(gx_ctx* x, const void* host, size_t bytes) {
   return GX_OK;
 }
 
-extern "C" gx_status gx_state_layout(const gx_ctx* x, size_t offsets[10]) {
+extern "C" gx_status gx_state_layout(const gx_ctx* x, size_t offsets[11]) {
   if (!x || !offsets) return fail(nullptr, GX_EINVAL, "gx_state_layout: NULL argument");
-  for (int k = 0; k < 10; ++k) offsets[k] = x->off[k];
+  for (int k = 0; k < 11; ++k) offsets[k] = x->off[k];
   return GX_OK;
 }
 

@@ -73,6 +73,8 @@ struct StateView {
   float4* obj;    // [n][M]
   int* step;      // [n]
   int* episode;   // [n]
+  float* task;    // [n][16]: goal xyz, target start xyz, previous joint actions [7],
+                  // previous tip-target and target-goal distances, unused
 };
 
 struct PhysicsParams {

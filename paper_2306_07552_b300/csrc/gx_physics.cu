@@ -533,6 +533,52 @@ __global__ void __launch_bounds__(32 * kEnvsPerBlock) physics_kernel(const Physi
     if (P.out.contact_flags) P.out.contact_flags[env] = flags;
     if (P.out.event) P.out.event[env] = event;
   }
+  // rearrangement task (App. "Additional Task Details"): object 0 is the
+  // target; r = 10 success + 5 pick + (d' - d) + (e' - e) - 0.001 C, d the
+  // tip-target and e the target-goal distance (primes: previous step), C the
+  // squared change of the 7 joint actions.  Egomotion observations (Sec.
+  // 4.1): target start and goal relative to base and tip, base frame.
+  {
+    float* tk = P.st.task + (size_t)env * 16;
+    const float tv = lane < 16 ? tk[lane] : 0.f;
+    float t16[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) t16[k] = __shfl_sync(kFull, tv, k);
+    float C = 0.f;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) C += (act[2 + k] - t16[6 + k]) * (act[2 + k] - t16[6 + k]);
+    float r = -0.001f * C;
+    bool success = false;
+    float nd = t16[13], ne = t16[14];
+    if (M > 0) {
+      const float4 o = so[0];
+      const float dx = et[0] - o.x, dy = et[1] - o.y, dz = et[2] - o.z;
+      const float gx = o.x - t16[0], gy = o.y - t16[1], gz = o.z - t16[2];
+      nd = sqrtf(dx * dx + dy * dy + dz * dz);
+      ne = sqrtf(gx * gx + gy * gy + gz * gz);
+      const bool pick = event == 1 && nheld == 0;
+      success = act[10] >= 0.5f && nheld != 0 && ne < 0.15f;
+      r += (success ? 10.f : 0.f) + (pick ? 5.f : 0.f) + (t16[13] - nd) + (t16[14] - ne);
+    }
+    if (lane < 7) tk[6 + lane] = act[2 + lane];
+    if (lane == 0) {
+      tk[13] = nd;
+      tk[14] = ne;
+      if (P.out.reward) P.out.reward[env] = r;
+      if (P.out.success) P.out.success[env] = success ? 1 : 0;
+    }
+    if (P.out.task_obs && lane < 12) {
+      float syw, cyw;
+      sincosf(ayaw, &syw, &cyw);
+      const int v = lane / 3, a = lane % 3;
+      const float fx = v < 2 ? ax : et[0], fy = v < 2 ? 0.f : et[1], fz = v < 2 ? az : et[2];
+      const float tx = (v & 1) ? t16[0] : t16[3], ty = (v & 1) ? t16[1] : t16[4],
+                  tz = (v & 1) ? t16[2] : t16[5];
+      const float wx = tx - fx, wy = ty - fy, wz = tz - fz;
+      P.out.task_obs[(size_t)env * 12 + lane] =
+          a == 0 ? cyw * wx - syw * wz : (a == 1 ? wy : syw * wx + cyw * wz);
+    }
+  }
 }
 
 // Candidate placement of object j at try t (the same Philox draws the
@@ -716,6 +762,39 @@ __global__ void __launch_bounds__(kResetThreads) reset_kernel(const ResetParams 
     P.st.ppre[(size_t)lane * n + env] = 0.f;
   }
   for (int j = lane; j < M; j += 32) P.st.obj[(size_t)env * M + j] = so[j];
+  // task: object 0 is the target; its goal lies on a support top, drawn like
+  // an object placement from stream 65 (first draw); previous distances from
+  // the episode's first pose, previous joint actions 0
+  {
+    float task[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) task[k] = 0.f;
+    if (M > 0 && S.n_supports > 0) {
+      const uint4 wg = philox4x32_10(make_uint4((uint32_t)env, ep, 65u, 0u), key);
+      const float4 o = so[0];
+      const float3 g = object_candidate(S, wg, o.w, rb.rest_clearance);
+      task[0] = g.x;
+      task[1] = g.y;
+      task[2] = g.z;
+      task[3] = o.x;
+      task[4] = o.y;
+      task[5] = o.z;
+      float q0[7], mR[9], mt[3], eR[9], et[3];
+#pragma unroll
+      for (int k = 0; k < 7; ++k) q0[k] = rb.q_rest[k];
+      fk(rb, bx, bz, byaw, q0, -1, mR, mt, eR, et);
+      const float dx = et[0] - o.x, dy = et[1] - o.y, dz = et[2] - o.z;
+      const float gx = o.x - task[0], gy = o.y - task[1], gz = o.z - task[2];
+      task[13] = sqrtf(dx * dx + dy * dy + dz * dz);
+      task[14] = sqrtf(gx * gx + gy * gy + gz * gz);
+    }
+    if (lane < 16) {
+      float v = task[0];
+#pragma unroll
+      for (int k = 1; k < 16; ++k) v = lane == k ? task[k] : v;
+      P.st.task[(size_t)env * 16 + lane] = v;
+    }
+  }
   float cam[12];
   camera(rb, bx, bz, byaw, cam);
   if (lane < 12) {

@@ -75,10 +75,12 @@ class GxConfig(C.Structure):
                 ("sdf_mode", C.c_int32), ("sdf_margin", C.c_float), ("heuristics", C.c_int32)]
 
 
+OUTPUT_KEYS = ["depth", "rgb", "pose", "obj_pos", "held", "contact_mask", "contact_flags", "event",
+               "reward", "task_obs", "success"]
+
+
 class GxOutputs(C.Structure):
-    _fields_ = [("depth", C.c_void_p), ("rgb", C.c_void_p), ("pose", C.c_void_p),
-                ("obj_pos", C.c_void_p), ("held", C.c_void_p), ("contact_mask", C.c_void_p),
-                ("contact_flags", C.c_void_p), ("event", C.c_void_p)]
+    _fields_ = [(k, C.c_void_p) for k in OUTPUT_KEYS]
 
 
 class GxTrainParams(C.Structure):
@@ -354,13 +356,16 @@ class Sim:
             contact_mask=torch.zeros(n_envs, dtype=torch.int32, device=dev),
             contact_flags=torch.zeros(n_envs, dtype=torch.uint8, device=dev),
             event=torch.zeros(n_envs, dtype=torch.uint8, device=dev),
+            reward=torch.zeros(n_envs, dtype=torch.float32, device=dev),
+            task_obs=torch.zeros((n_envs, 12), dtype=torch.float32, device=dev),
+            success=torch.zeros(n_envs, dtype=torch.uint8, device=dev),
         )
         self._outs = self._outputs_struct(self.out)
 
     @staticmethod
     def _outputs_struct(d):
         o = GxOutputs()
-        for k in ["depth", "rgb", "pose", "obj_pos", "held", "contact_mask", "contact_flags", "event"]:
+        for k in OUTPUT_KEYS:
             v = d.get(k)
             setattr(o, k, None if v is None else (v.data_ptr() if hasattr(v, "data_ptr")
                                                   else v.ctypes.data))
@@ -448,7 +453,7 @@ class Sim:
         _check(lib().gx_load_state(self.handle, buf.ctypes.data, buf.nbytes), self.handle)
 
     def layout(self):
-        offs = (C.c_size_t * 10)()
+        offs = (C.c_size_t * 11)()
         _check(lib().gx_state_layout(self.handle, offs), self.handle)
         return list(offs)
 
@@ -466,7 +471,8 @@ class Sim:
                     yaw=arr(2, np.float32, (n,)), q=arr(3, np.float32, (7, n)),
                     held=arr(4, np.int32, (n,)), c_off=arr(5, np.float32, (3, n)),
                     p_pre=arr(6, np.float32, (3, n)), obj=arr(7, np.float32, (n, M, 4)),
-                    step=arr(8, np.int32, (n,)), episode=arr(9, np.int32, (n,)))
+                    step=arr(8, np.int32, (n,)), episode=arr(9, np.int32, (n,)),
+                    task=arr(10, np.float32, (n, 16)))
 
     def close(self):
         if self.handle:

@@ -24,7 +24,8 @@ def oracle_state(arrs, e, M):
     return O.Oracle.make_state((float(arrs["base_x"][e]), float(arrs["base_z"][e]),
                                 float(arrs["yaw"][e])), arrs["q"][:, e], int(arrs["held"][e]),
                                arrs["c_off"][:, e], arrs["p_pre"][:, e], arrs["obj"][e, :M],
-                               int(arrs["step"][e]), int(arrs["episode"][e]))
+                               int(arrs["step"][e]), int(arrs["episode"][e]),
+                               task=arrs["task"][e] if "task" in arrs else None)
 
 
 def ang_diff(a, b):
@@ -42,13 +43,15 @@ class Tally:
         self.ambiguous = 0
         self.max_pose_err = 0.0
         self.max_depth_rel = 0.0
+        self.max_task_err = 0.0        # reward, task observations and task state
         self.fp16_max_err = 0.0        # FP16 depth: largest |gpu - oracle| (m)
         self.fp16_max_frac = 0.0       # ... as a fraction of its bound
 
     def __repr__(self):
         r = (f"envs={self.envs} near_band={self.near_band} contacts={self.contacts} "
              f"events={self.events} pixels={self.pixels} ambiguous={self.ambiguous} "
-             f"max_pose_err={self.max_pose_err:.2e} max_depth_rel={self.max_depth_rel:.2e}")
+             f"max_pose_err={self.max_pose_err:.2e} max_depth_rel={self.max_depth_rel:.2e} "
+             f"max_task_err={self.max_task_err:.2e}")
         if self.fp16_max_frac:
             r += (f" fp16_max_err={self.fp16_max_err:.2e} m "
                   f"fp16_max_of_bound={self.fp16_max_frac:.3f}")
@@ -65,6 +68,9 @@ def check_step(orc, before, after, out, acts, envs, M, tally, step_fn=None):
     held = out["held"].cpu().numpy()
     pose = out["pose"].cpu().numpy()
     objo = out["obj_pos"].cpu().numpy()
+    reward = out["reward"].cpu().numpy() if out.get("reward") is not None else None
+    tobs = out["task_obs"].cpu().numpy() if out.get("task_obs") is not None else None
+    succ = out["success"].cpu().numpy() if out.get("success") is not None else None
     for e in envs:
         st = oracle_state(before, e, M)
         o = step_fn(st, acts[e], e) if step_fn else orc.step(st, acts[e])
@@ -93,6 +99,15 @@ def check_step(orc, before, after, out, acts, envs, M, tally, step_fn=None):
         assert m <= POSE_TOL, (e, m)
         assert pose[e, 7] == (1.0 if st.held >= 0 else 0.0)
         assert pose[e, 14] == st.step_count
+        if reward is not None:
+            # the task epilogue: reward, success and egomotion observations
+            assert succ[e] == o.success, (e, succ[e], o.success)
+            terr = [abs(float(reward[e]) - o.reward)] + list(np.abs(tobs[e] - np.array(list(o.task_obs))))
+            terr += list(np.abs(after["task"][e, :15] - np.array(
+                [*st.goal, *st.obj_start, *st.prev_a, st.prev_d, st.prev_e])))
+            m2 = float(max(terr))
+            tally.max_task_err = max(tally.max_task_err, m2)
+            assert m2 <= POSE_TOL, (e, m2)
 
 
 def check_image(orc, after, out, e, W, H, M, tally, fp16=False):

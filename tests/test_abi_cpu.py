@@ -33,11 +33,33 @@ def test_exports_every_declared_symbol(L):
     assert sorted(gx.SYMBOLS) == names
 
 
-def test_struct_sizes_match_header():
-    # all-4-byte robot table: no padding anywhere
-    assert C.sizeof(gx.GxRobot) == 4 * (24 + 7 + 21 + 3 + 1 + 31 + 93 + 31 + 3 + 4)
-    assert C.sizeof(gx.GxOutputs) == 8 * 8
-    assert gx.GxConfig.seed.offset == 32
+def test_struct_sizes_match_header(tmp_path):
+    """The ctypes mirrors against the C compiler's layout of include/gx.h."""
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    structs = {"gx_robot": gx.GxRobot, "gx_scene_desc": gx.GxSceneDesc,
+               "gx_object_mesh": gx.GxObjectMesh, "gx_config": gx.GxConfig,
+               "gx_outputs": gx.GxOutputs, "gx_train_params": gx.GxTrainParams,
+               "gx_tune_result": gx.GxTuneResult}
+    fields = {"gx_config": ["seed", "env_scene", "profile", "sdf_mode", "sdf_margin",
+                            "heuristics"],
+              "gx_outputs": ["event", "reward", "task_obs", "success"],
+              "gx_train_params": ["batch", "lr", "seed"]}
+    src = ["#include <stdio.h>", "#include <stddef.h>", '#include "gx.h"', "int main(void) {"]
+    for name in structs:
+        src.append(f'  printf("{name} %zu\\n", sizeof({name}));')
+        for f in fields.get(name, []):
+            src.append(f'  printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    src.append("  return 0;\n}")
+    c = tmp_path / "sizes.c"
+    c.write_text("\n".join(src))
+    exe = tmp_path / "sizes"
+    subprocess.check_call(["gcc", "-I", os.path.join(root, "include"), "-o", str(exe), str(c)])
+    got = dict(line.split() for line in subprocess.check_output([str(exe)], text=True).splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == C.sizeof(cls), name
+        for f in fields.get(name, []):
+            assert int(got[f"{name}.{f}"]) == getattr(cls, f).offset, (name, f)
 
 
 def test_null_arguments_are_rejected(L):

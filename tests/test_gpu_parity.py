@@ -67,6 +67,9 @@ def test_reset_matches_oracle(room):
         d = (s["yaw"][e] - st.base[2]) % (2 * math.pi)
         assert min(d, 2 * math.pi - d) < 1e-5
         assert np.allclose(s["q"][:, e], ROBOT.q_rest, atol=0)
+        # the task: goal on a support top, target start, first distances
+        want = [*st.goal, *st.obj_start, *st.prev_a, st.prev_d, st.prev_e]
+        assert np.allclose(s["task"][e, :15], want, atol=1e-5), (e, s["task"][e], want)
     assert nb <= n // 4   # near-band decisions anywhere in 64-try rejection loops
     # a second reset starts episode 2 with a new placement
     sim.reset()
