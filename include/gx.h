@@ -225,12 +225,19 @@ gx_status gx_reset(gx_ctx* ctx, const uint8_t* env_mask, void* stream);
  * is clipped to [-1, 1] (App. A).  Asynchronous on `stream`. */
 gx_status gx_step(gx_ctx* ctx, const float* actions, const gx_outputs* out, void* stream);
 
-/* Same step with HOST buffers: copies the actions (pinned host memory is
- * fastest) to the device, steps, and copies every non-NULL output back into
- * the host buffers of `out` (same layouts as gx_outputs).  Blocks until the
- * copies are complete. */
+/* Same step with HOST actions: copies the actions (pinned host memory is
+ * fastest) to the device, steps into the context's own device output
+ * buffers, and copies back every non-NULL member of `host_out` (host
+ * buffers, same layouts as gx_outputs; depth may be NULL too).  The outputs
+ * not copied stay on the device, where gx_device_outputs finds them (the
+ * paper's zero-copy hand-off of observations to a policy on the GPU).
+ * Blocks until the copies are complete. */
 gx_status gx_step_host(gx_ctx* ctx, const float* actions_host, const gx_outputs* host_out,
                        void* stream);
+
+/* Device pointers of the context's own output buffers that gx_step_host
+ * writes (all members set once gx_step_host has run; GX_ESTATE before). */
+gx_status gx_device_outputs(gx_ctx* ctx, gx_outputs* out);
 
 /* Waits for all work of ctx and reports the device error word. */
 gx_status gx_sync(gx_ctx* ctx);

@@ -658,10 +658,7 @@ extern "C" gx_status gx_step(gx_ctx* x, const float* actions, const gx_outputs* 
 extern "C" gx_status gx_step_host(gx_ctx* x, const float* actions_host, const gx_outputs* host_out,
                                   void* stream) {
   if (!x) return fail(nullptr, GX_EINVAL, "gx_step_host: ctx is NULL");
-  if (!actions_host || !host_out || !host_out->depth)
-    return fail(x, GX_EINVAL, "gx_step_host: actions and depth required");
-  if (x->cfg.render_rgb && !host_out->rgb)
-    return fail(x, GX_EINVAL, "gx_step_host: render_rgb needs rgb");
+  if (!actions_host || !host_out) return fail(x, GX_EINVAL, "gx_step_host: NULL argument");
   const size_t n = x->n, M = x->M, px = (size_t)x->cfg.img_w * x->cfg.img_h;
   const size_t dbytes = n * px * (x->cfg.depth_fp16 ? 2 : 4);
   if (!x->h2d_actions) {
@@ -689,7 +686,7 @@ extern "C" gx_status gx_step_host(gx_ctx* x, const float* actions_host, const gx
   if (st != GX_OK) return st;
   const gx_outputs& d = x->dev_out;
   const gx_outputs& h = *host_out;
-  CK(x, cudaMemcpyAsync(h.depth, d.depth, dbytes, cudaMemcpyDeviceToHost, s));
+  if (h.depth) CK(x, cudaMemcpyAsync(h.depth, d.depth, dbytes, cudaMemcpyDeviceToHost, s));
   if (h.rgb && d.rgb) CK(x, cudaMemcpyAsync(h.rgb, d.rgb, n * px * 3, cudaMemcpyDeviceToHost, s));
   if (h.pose) CK(x, cudaMemcpyAsync(h.pose, d.pose, n * 64, cudaMemcpyDeviceToHost, s));
   if (h.obj_pos && M) CK(x, cudaMemcpyAsync(h.obj_pos, d.obj_pos, n * M * 16, cudaMemcpyDeviceToHost, s));
@@ -702,6 +699,13 @@ extern "C" gx_status gx_step_host(gx_ctx* x, const float* actions_host, const gx
   if (h.success) CK(x, cudaMemcpyAsync(h.success, d.success, n, cudaMemcpyDeviceToHost, s));
   CK(x, cudaStreamSynchronize(s));
   return poll_device_error(x, true);
+}
+
+extern "C" gx_status gx_device_outputs(gx_ctx* x, gx_outputs* out) {
+  if (!x || !out) return fail(x, GX_EINVAL, "gx_device_outputs: NULL argument");
+  if (!x->h2d_actions) return fail(x, GX_ESTATE, "gx_device_outputs: gx_step_host has not run");
+  *out = x->dev_out;
+  return GX_OK;
 }
 
 extern "C" gx_status gx_sync(gx_ctx* x) {

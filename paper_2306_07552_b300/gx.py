@@ -29,7 +29,7 @@ SYMBOLS = ["gx_scene_set_create", "gx_scene_set_destroy", "gx_create", "gx_destr
            "gx_save_state", "gx_load_state", "gx_state_layout", "gx_phase_times",
            "gx_raster_counters", "gx_render_noalloc", "gx_nsdf_set_weights",
            "gx_nsdf_get_weights", "gx_nsdf_query", "gx_nsdf_get_master", "gx_nsdf_samples", "gx_nsdf_grad",
-           "gx_nsdf_train", "gx_nsdf_counters", "gx_autotune", "gx_column_info", "gx_column_spans",
+           "gx_nsdf_train", "gx_nsdf_counters", "gx_autotune", "gx_column_info", "gx_column_spans", "gx_device_outputs",
            "gx_last_error"]
 NSDF_PARAMS = 57985
 NSDF_FREQ = 32
@@ -142,6 +142,7 @@ def lib():
         L.gx_nsdf_grad.argtypes = [vp, C.c_int32, vp, vp, C.c_int32, C.c_float, C.c_float, vp, vp,
                                    vp]
         L.gx_nsdf_counters.argtypes = [vp, C.POINTER(C.c_int64)]
+        L.gx_device_outputs.argtypes = [vp, P(GxOutputs)]
         L.gx_column_info.argtypes = [vp, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_uint64)]
         L.gx_column_spans.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, vp, C.c_int32]
         L.gx_column_spans.restype = C.c_int32
@@ -395,13 +396,20 @@ class Sim:
         return d
 
     def step_host(self, actions_host, host_out, stream=None):
-        """Same step through host buffers: copies in, steps, copies every
-        output back; returns when the host buffers hold the results."""
+        """Same step with host actions: copies them in, steps, copies back the
+        host buffers given (None entries stay on the device, see
+        device_outputs); returns when the host buffers hold the results."""
         o = self._outputs_struct(host_out)
         ptr = actions_host.data_ptr() if hasattr(actions_host, "data_ptr") else actions_host.ctypes.data
         _check(lib().gx_step_host(self.handle, C.c_void_p(ptr), C.byref(o), self._stream(stream)),
                self.handle)
         return host_out
+
+    def device_outputs(self):
+        """Device pointers of the outputs step_host left on the device."""
+        o = GxOutputs()
+        _check(lib().gx_device_outputs(self.handle, C.byref(o)), self.handle)
+        return {k: getattr(o, k) for k in OUTPUT_KEYS}
 
     def phase_times(self):
         """(ms, launches) per kernel since the last call: physics, raster, reset,

@@ -214,6 +214,23 @@ def test_save_load_and_host_step(room):
         if v is not None:
             assert torch.equal(v, host[k]), k
     assert np.array_equal(ref_state, sim.save_state())
+    # only the step's result back to the host; the images stay on the device
+    sim.load_state(snap)
+    result = {k: (v if k in ("reward", "success", "event") else None) for k, v in host.items()}
+    for k in result:
+        if result[k] is not None:
+            result[k].zero_()
+    for t in range(3):
+        sim.step_host(torch.from_numpy(acts[t]).pin_memory(), result)
+    for k in ("reward", "success", "event"):
+        assert torch.equal(ref[k], result[k]), k
+    from cuda.bindings import runtime as rt
+    dev = sim.device_outputs()
+    depth = torch.empty_like(ref["depth"]).cuda()
+    err, = rt.cudaMemcpy(depth.data_ptr(), dev["depth"], depth.numel() * depth.element_size(),
+                         rt.cudaMemcpyKind.cudaMemcpyDeviceToDevice)
+    assert err == rt.cudaError_t.cudaSuccess
+    assert torch.equal(depth.cpu(), ref["depth"])
     sim.close()
 
 
