@@ -3,8 +3,8 @@
 //
 //   d(x) = W5 relu(W4 relu(W3 relu(W2 relu(W1 g(x) + b1) + b2) + b3) + b4) + b5
 //   g(x) = [sin(2 pi B (x - c)), cos(2 pi B (x - c))],  B in R^{32x3}
-//   (phases formed in turns with error-free transformations, reduced, then
-//   sincospi)
+//   (phases formed in turns with error-free transformations and reduced to
+//   a fraction of a turn; sin and cos by the hardware approximations)
 //
 // W1..W4 are BF16 and every hidden product runs on the 5th-generation tensor
 // cores (tcgen05.mma, kind::f16, FP32 accumulation in tensor memory); the
@@ -30,7 +30,8 @@ namespace gx {
 namespace {
 
 constexpr int kTile = 128;            // rows (queries) per MMA tile
-constexpr int kQueryThreads = 128;    // one warpgroup: TMEM lanes 0..127
+constexpr int kGroups = 2;            // warpgroups per CTA, each with a tile in flight
+constexpr int kQueryThreads = 128 * kGroups;
 
 // Issues the K steps of one layer: D = A . W^T over K = 64 * kblocks.
 __device__ __forceinline__ void layer_mma(uint32_t tmem, uint32_t a_base, uint32_t w_base,
@@ -45,13 +46,32 @@ __device__ __forceinline__ void layer_mma(uint32_t tmem, uint32_t a_base, uint32
     }
 }
 
+// Two warpgroups share the weights; each owns an activation operand, 128
+// tensor-memory columns and an mbarrier, and runs its own tiles, so one
+// group's products overlap the other's epilogue.
 struct QuerySmem {
-  unsigned char w[kNsdfImgBytes];        // W1 | W2 | W3 | W4 images
-  unsigned char a[kTile * 128 * 2];      // activation operand (K <= 128)
+  unsigned char w[kNsdfImgBytes];           // W1 | W2 | W3 | W4 images
+  unsigned char a[kGroups][kTile * 128 * 2];  // activation operand per group (K <= 128)
   NsdfTail tail;
-  unsigned long long bar_w, bar_mma;
+  unsigned long long bar_w, bar_mma[kGroups];
   uint32_t tmem_slot;
 };
+
+// Barrier of one warpgroup (named barrier 1 + g, 128 threads).
+__device__ __forceinline__ void group_sync(int g) {
+  asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory");
+}
+// The same barrier, returning the AND of v over the group.
+__device__ __forceinline__ bool group_and(int g, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, %2, 128, p;\n"
+      " selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(1 + g)
+      : "memory");
+  return r != 0;
+}
 
 // Stages a scene's weights (BF16 images and the FP32 tail) into shared
 // memory: thread 0 issues the bulk copies, every thread waits (bounded).
@@ -70,12 +90,14 @@ __device__ bool load_weights(QuerySmem& sm, const unsigned char* blob, uint32_t&
   return ok;
 }
 
-// One 128-row tile through the network; d is this thread's point relative
-// to the feature centre.  Returns this row's output (valid when ok).
-__device__ float run_tile(QuerySmem& sm, uint32_t tmem, const Centred& d, uint32_t& mma_phase,
-                          bool& ok) {
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t a_base = smem_u32(sm.a);
+// One 128-row tile through the network by warpgroup g; d is this thread's
+// point relative to the feature centre.  Returns this row's output (valid
+// when ok).  Only the group's own threads synchronise.
+__device__ float run_tile(QuerySmem& sm, int g, const Centred& d, uint32_t& mma_phase, bool& ok) {
+  const int gt = threadIdx.x & 127, warp = gt >> 5, lane = gt & 31;
+  unsigned char* act = sm.a[g];
+  const uint32_t tmem = sm.tmem_slot + (uint32_t)(g * kNsdfWidth);
+  const uint32_t a_base = smem_u32(act);
   const uint32_t w_base[4] = {smem_u32(sm.w), smem_u32(sm.w + kNsdfW1Bytes),
                               smem_u32(sm.w + kNsdfW1Bytes + kNsdfWhBytes),
                               smem_u32(sm.w + kNsdfW1Bytes + 2 * kNsdfWhBytes)};
@@ -85,22 +107,23 @@ __device__ float run_tile(QuerySmem& sm, uint32_t tmem, const Centred& d, uint32
     float sv[8], cv[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u)
-      sincospif(2.f * phase_turns(sm.tail.B[f8 + u], d), &sv[u], &cv[u]);
-    store_chunk(sm.a, tid, f8, kTile, sv);
-    store_chunk(sm.a, tid, kNsdfFreq + f8, kTile, cv);
+      sincos_turns(phase_turns(sm.tail.B[f8 + u], d), &sv[u], &cv[u]);
+    store_chunk(act, gt, f8, kTile, sv);
+    store_chunk(act, gt, kNsdfFreq + f8, kTile, cv);
   }
   fence_proxy_async();
   tc_fence_before();
-  __syncthreads();
+  group_sync(g);
   float dot = 0.f;
-  for (int layer = 0; layer < 4 && ok; ++layer) {
-    if (tid == 0) {
+  for (int layer = 0; layer < 4; ++layer) {
+    if (gt == 0) {
       tc_fence_after();
       layer_mma(tmem, a_base, w_base[layer], layer == 0 ? 1 : 2);
-      mma_commit(&sm.bar_mma);
+      mma_commit(&sm.bar_mma[g]);
     }
-    ok = __syncthreads_and(mbar_wait(&sm.bar_mma, mma_phase));
+    const bool good = mbar_wait(&sm.bar_mma[g], mma_phase);
     mma_phase ^= 1u;
+    ok = group_and(g, ok && good);  // uniform over the group
     tc_fence_after();
     // epilogue: this warp's 32 rows, 32 columns at a time
 #pragma unroll 1
@@ -108,24 +131,24 @@ __device__ float run_tile(QuerySmem& sm, uint32_t tmem, const Centred& d, uint32
       float v[32];
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
 #pragma unroll
-      for (int u = 0; u < 32; ++u)
-        v[u] = bf16_round(fmaxf(v[u] + sm.tail.b[layer][c * 32 + u], 0.f));
+      for (int u = 0; u < 32; ++u) v[u] = fmaxf(v[u] + sm.tail.b[layer][c * 32 + u], 0.f);
       if (layer < 3) {
+        // store_chunk rounds to BF16 on the way into the next operand
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           float ch[8];
 #pragma unroll
           for (int u = 0; u < 8; ++u) ch[u] = v[q * 8 + u];
-          store_chunk(sm.a, warp * 32 + lane, c * 32 + q * 8, kTile, ch);
+          store_chunk(act, warp * 32 + lane, c * 32 + q * 8, kTile, ch);
         }
       } else {
 #pragma unroll
-        for (int u = 0; u < 32; ++u) dot = fmaf(v[u], sm.tail.w5[c * 32 + u], dot);
+        for (int u = 0; u < 32; ++u) dot = fmaf(bf16_round(v[u]), sm.tail.w5[c * 32 + u], dot);
       }
     }
     fence_proxy_async();
     tc_fence_before();
-    __syncthreads();
+    group_sync(g);
   }
   return dot + sm.tail.b5;
 }
@@ -133,10 +156,10 @@ __device__ float run_tile(QuerySmem& sm, uint32_t tmem, const Centred& d, uint32
 __device__ void query_setup(QuerySmem& sm) {
   if (threadIdx.x == 0) {
     mbar_init(&sm.bar_w, 1);
-    mbar_init(&sm.bar_mma, 1);
+    for (int g = 0; g < kGroups; ++g) mbar_init(&sm.bar_mma[g], 1);
     fence_mbar_init();
   }
-  if (threadIdx.x < 32) tmem_alloc(&sm.tmem_slot, kNsdfWidth);
+  if (threadIdx.x < 32) tmem_alloc(&sm.tmem_slot, kGroups * kNsdfWidth);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -146,7 +169,7 @@ __device__ void query_teardown(QuerySmem& sm, bool ok, unsigned* err) {
   if (!ok && threadIdx.x == 0 && err) atomicOr(err, kErrWaitTimeout);
   tc_fence_before();
   __syncthreads();
-  if (threadIdx.x < 32) tmem_dealloc(sm.tmem_slot, kNsdfWidth);
+  if (threadIdx.x < 32) tmem_dealloc(sm.tmem_slot, kGroups * kNsdfWidth);
 }
 
 __device__ __forceinline__ QuerySmem& query_smem(unsigned char* raw) {
@@ -164,23 +187,27 @@ __global__ void __launch_bounds__(kQueryThreads, 1)
   query_setup(sm);
   uint32_t w_phase = 0, mma_phase = 0;
   bool ok = __syncthreads_and(load_weights(sm, blob, w_phase));
+  const int g = threadIdx.x >> 7, gt = threadIdx.x & 127;
   const int tiles = (n + kTile - 1) / kTile;
-  for (int tile = blockIdx.x; ok && tile < tiles; tile += gridDim.x) {
-    const int i = tile * kTile + threadIdx.x;
+  // warpgroup g of CTA b takes tiles kGroups * b + g, then strides by the grid
+  for (int tile = kGroups * blockIdx.x + g; ok && tile < tiles; tile += kGroups * gridDim.x) {
+    const int i = tile * kTile + gt;
     Centred d = centre_point(sm.tail.centre[0], sm.tail.centre[1], sm.tail.centre[2],
                              sm.tail.centre);
     if (i < n)
       d = centre_point(pts[3 * (size_t)i], pts[3 * (size_t)i + 1], pts[3 * (size_t)i + 2],
                        sm.tail.centre);
-    const float v = run_tile(sm, sm.tmem_slot, d, mma_phase, ok);
+    const float v = run_tile(sm, g, d, mma_phase, ok);
     if (ok && i < n) out[i] = v;
   }
+  ok = __syncthreads_and(ok);
   query_teardown(sm, ok, err);
 }
 
 // The step's queries: each CTA takes a contiguous run of tiles (grouped by
 // scene, so it reloads weights only where the scene changes); a tile's 128
-// rows are 4 environments x 32 sphere slots.
+// rows are 4 environments x 32 sphere slots.  In each round the two
+// warpgroups take up to two consecutive tiles of the loaded scene.
 __global__ void __launch_bounds__(kQueryThreads, 1) nsdf_step_kernel(const NsdfStepParams p) {
   extern __shared__ unsigned char smem_raw[];
   QuerySmem& sm = query_smem(smem_raw);
@@ -190,26 +217,33 @@ __global__ void __launch_bounds__(kQueryThreads, 1) nsdf_step_kernel(const NsdfS
   int loaded = -1;
   const int t0 = (int)((long long)blockIdx.x * p.n_tiles / gridDim.x);
   const int t1 = (int)((long long)(blockIdx.x + 1) * p.n_tiles / gridDim.x);
-  const int slot = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int t = t0; ok && t < t1; ++t) {
-    const int4 tile = p.tiles[t];
-    if (tile.x != loaded) {
+  const int g = threadIdx.x >> 7, gt = threadIdx.x & 127;
+  const int slot = gt >> 5, lane = gt & 31;
+  for (int t = t0; ok && t < t1;) {
+    const int4 first = p.tiles[t];
+    if (first.x != loaded) {
       fence_proxy_async();  // this CTA's reads of the old weights come first
       __syncthreads();
-      ok = __syncthreads_and(load_weights(sm, p.blobs[tile.x], w_phase));
+      ok = __syncthreads_and(load_weights(sm, p.blobs[first.x], w_phase));
       if (!ok) break;
-      loaded = tile.x;
+      loaded = first.x;
     }
-    int env = -1;
-    Centred d = centre_point(sm.tail.centre[0], sm.tail.centre[1], sm.tail.centre[2],
-                             sm.tail.centre);
-    if (slot < tile.z) {
-      env = p.perm[tile.y + slot];
-      const float4 q = p.pts[(size_t)env * 32 + lane];
-      d = centre_point(q.x, q.y, q.z, sm.tail.centre);
+    const int in_round = (t + 1 < t1 && p.tiles[t + 1].x == first.x) ? 2 : 1;
+    if (g < in_round) {
+      const int4 tile = p.tiles[t + g];
+      int env = -1;
+      Centred d = centre_point(sm.tail.centre[0], sm.tail.centre[1], sm.tail.centre[2],
+                               sm.tail.centre);
+      if (slot < tile.z) {
+        env = p.perm[tile.y + slot];
+        const float4 q = p.pts[(size_t)env * 32 + lane];
+        d = centre_point(q.x, q.y, q.z, sm.tail.centre);
+      }
+      const float v = run_tile(sm, g, d, mma_phase, ok);
+      if (ok && env >= 0) p.out[(size_t)env * 32 + lane] = v;
     }
-    const float v = run_tile(sm, sm.tmem_slot, d, mma_phase, ok);
-    if (ok && env >= 0) p.out[(size_t)env * 32 + lane] = v;
+    ok = __syncthreads_and(ok);  // the round is over for both groups
+    t += in_round;
   }
   query_teardown(sm, ok, p.err);
 }

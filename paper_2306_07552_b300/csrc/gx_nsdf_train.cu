@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) nsdf_fwd_bwd_kernel(const Fw
       float sv[8], cv[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u)
-        sincospif(2.f * phase_turns(sm.tail.B[hf * 16 + f8 + u], d), &sv[u], &cv[u]);
+        sincos_turns(phase_turns(sm.tail.B[hf * 16 + f8 + u], d), &sv[u], &cv[u]);
       store_chunk(sm.f, row, hf * 16 + f8, kTile, sv);
       store_chunk(sm.f, row, kNsdfFreq + hf * 16 + f8, kTile, cv);
     }

@@ -4,10 +4,11 @@ kernels), the Adam update, and a short training run judged by the grid.
 
 Gradient tolerance.  Both sides round the same operands to BF16 (features,
 hidden activations, hidden-layer gradients); the kernels sum in FP32 where
-the oracle sums in FP64, and their Fourier phases are good to ~1e-7 rad.  A
-value within that distance of a BF16 rounding boundary can round the other
-way: with BF16 steps of 2^-8 relative this happens to ~1e-4 of the features
-and ~3e-5 of the hidden values, each time moving that operand by one step.
+the oracle sums in FP64, and their features (hardware sin and cos of a phase
+reduced exactly to a fraction of a turn) are good to 4e-7.  A value within
+that distance of a BF16 rounding boundary can round the other way: with BF16
+steps of 2^-8 relative this happens to ~2e-4 of the features and ~3e-5 of the
+hidden values, each time moving that operand by one step.
 Over the ~5e5 rounded operands of a 1000-sample batch a few tens flip; the
 per-layer gradient then differs by well under 1e-3 relative (L2), and the
 loss (a mean of |prediction - label|) by ~1e-5 relative.  Asserted: 2e-3
