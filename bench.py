@@ -401,6 +401,8 @@ def main():
     ap.add_argument("--envs", type=int, default=0, help="smaller batch (profiling runs)")
     ap.add_argument("--scenes", type=int, default=0, help="fewer scenes (profiling runs)")
     ap.add_argument("--small-px", type=int, default=0, help="expansion bbox limit (0: auto)")
+    ap.add_argument("--render-robot", action="store_true",
+                    help="render the robot's collision spheres into every image")
     ap.add_argument("--heuristics", type=int, default=0,
                     help="the paper's heuristics: bit 0 sliding, bit 1 object placing")
     ap.add_argument("--no-autotune", action="store_true",
@@ -435,7 +437,8 @@ def main():
         nsdf = train_scenes(ss, w, sorted(set(int(x) for x in I.env_scene_map(n, w.n_scenes))))
     sim_kw = dict(img=(w.img, w.img), depth_fp16=w.depth_fp16, render_rgb=w.rgb,
                   n_objects=w.n_objects, obj_radius=w.obj_radius, seed=rank_seeds(w, rank)[0],
-                  small_tri_px=args.small_px, heuristics=args.heuristics)
+                  small_tri_px=args.small_px, heuristics=args.heuristics,
+                  render_robot=args.render_robot)
     column = w.sdf == "column"
     sdf_mode = 1 if neural else (2 if column else 0)
     sim = gx.Sim(ss, I.fetch_like_robot(), n, profile=0 if args.graph else 1,
@@ -639,7 +642,8 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (procedural apartments standing in for ReplicaCAD; see DESIGN.md)",
         "config": {**config_of(w), "heuristics": {"sliding": bool(args.heuristics & 1),
-                                                  "object_placing": bool(args.heuristics & 2)}},
+                                                  "object_placing": bool(args.heuristics & 2)},
+                   "robot_body_rendered": bool(args.render_robot)},
         "phases_ms_per_launch": {k: phase_ms[i] / max(phase_n[i], 1)
                                  for i, k in enumerate(["physics", "raster", "reset",
                                                         "nsdf_query"])},

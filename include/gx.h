@@ -106,11 +106,14 @@ typedef struct {
 } gx_scene_desc;
 
 /* Instance mesh for free objects (unit circumradius; scaled by each object's
- * radius) and one colour per object index. */
+ * radius) and one colour per object index; robot_rgb colours the robot's
+ * collision spheres when a context renders the robot body (the same mesh,
+ * instance slots GX_MAX_OBJECTS + sphere index). */
 typedef struct {
   int32_t n_verts;    const float* verts;     /* [n_verts][3], <= 32          */
   int32_t n_tris;     const int32_t* tris;    /* [n_tris][3], <= 32           */
   uint32_t obj_rgb[GX_MAX_OBJECTS];
+  uint32_t robot_rgb[32];
 } gx_object_mesh;
 
 typedef struct gx_scene_set gx_scene_set;
@@ -153,6 +156,8 @@ typedef struct {
                               d - r is below sdf_margin, or not finite; a
                               centre outside the grid box is contact          */
   float sdf_margin;        /* metres, >= 0 (e.g. 0.02)                        */
+  int32_t render_robot;    /* 1: the robot's collision spheres are rendered
+                              (instanced like the objects, robot_rgb)        */
   int32_t heuristics;      /* the paper's heuristics (appendix "Description of
                               Heuristics"), bit 0: sliding -- a colliding
                               candidate base is jittered in the ground plane

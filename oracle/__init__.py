@@ -64,7 +64,7 @@ class Scene_c(C.Structure):
 
 class ObjMesh_c(C.Structure):
     _fields_ = [("n_verts", C.c_int32), ("verts", f32p), ("n_tris", C.c_int32), ("tris", i32p),
-                ("obj_rgb", u32p)]
+                ("obj_rgb", u32p), ("robot_rgb", u32p)]
 
 
 class State_c(C.Structure):
@@ -153,7 +153,7 @@ class Oracle:
     TOL_REL = 1e-5
     COS_MIN = 0.05
 
-    def __init__(self, robot, scene, obj_mesh=None, obj_rgb=None):
+    def __init__(self, robot, scene, obj_mesh=None, obj_rgb=None, robot_rgb=None):
         self._keep = []
         k = self._keep.append
         r = robot
@@ -197,7 +197,13 @@ class Oracle:
                 rgb[:len(obj_rgb)] = obj_rgb
             for v in (mv, mt, rgb):
                 k(v)
-            self.objmesh = ObjMesh_c(len(mv), _p(mv, f32p), len(mt), _p(mt, i32p), _p(rgb, u32p))
+            rr = None
+            if robot_rgb is not None:
+                rr = np.zeros(32, np.uint32)
+                rr[:len(robot_rgb)] = robot_rgb
+                k(rr)
+            self.objmesh = ObjMesh_c(len(mv), _p(mv, f32p), len(mt), _p(mt, i32p), _p(rgb, u32p),
+                                     _p(rr, u32p) if rr is not None else None)
         else:
             self.objmesh = None
         self.L = lib()

@@ -993,6 +993,22 @@ void orc_render(const orc_robot* rb, const orc_scene* sc, const orc_objmesh* om,
                  cnt, dropz, &local);
     }
   }
+  /* the robot body: its collision spheres as the same instanced mesh, in
+   * instance slots ORC_MAX_OBJ + i */
+  if (om->robot_rgb) {
+    double cs[ORC_MAX_SPHERES][3];
+    orc_sphere_centres(rb, st->base, st->q, cs);
+    for (int i = 0; i < rb->n_spheres; ++i) {
+      const double r = rb->sphere_radius[i];
+      for (int t = 0; t < om->n_tris; ++t) {
+        for (int k = 0; k < 3; ++k)
+          for (int a = 0; a < 3; ++a)
+            P[k][a] = cs[i][a] + r * (double)om->verts[3 * om->tris[3 * t + k] + a];
+        render_tri(P, sc->n_tris + (ORC_MAX_OBJ + i) * om->n_tris + t, om->robot_rgb[i], cam,
+                   near, W, H, eps_px, C, cnt, dropz, &local);
+      }
+    }
+  }
   for (size_t p = 0; p < np; ++p) {
     cand* L = C + p * ORC_K;
     int nc = cnt[p];

@@ -51,6 +51,9 @@ typedef struct {
   int32_t n_verts; const float* verts;       /* unit instance mesh          */
   int32_t n_tris;  const int32_t* tris;
   const uint32_t* obj_rgb;                   /* [ORC_MAX_OBJ] colours       */
+  const uint32_t* robot_rgb;                 /* [ORC_MAX_SPHERES] colours of the
+                                                robot's spheres; NULL: the
+                                                robot body is not rendered   */
 } orc_objmesh;
 
 typedef struct {

@@ -41,6 +41,7 @@ struct gx_ctx {
   size_t off[11] = {0};
   StateView st{};
   float* d_cam = nullptr;
+  float4* d_robot_sph = nullptr;       // robot spheres for rendering the robot body
   unsigned* d_err = nullptr;
   unsigned* h_err = nullptr;
   cudaEvent_t ev_err = nullptr;
@@ -177,6 +178,7 @@ void enqueue_step(gx_ctx* c, const float* actions, const gx_outputs& out, cudaSt
   pp.actions = actions;
   pp.st = c->st;
   pp.cam = c->d_cam;
+  pp.robot_sph = c->d_robot_sph;
   pp.out = out;
   pp.err = c->d_err;
   pp.raster_work = c->d_raster_work;
@@ -225,6 +227,7 @@ void enqueue_step(gx_ctx* c, const float* actions, const gx_outputs& out, cudaSt
   rp.omesh_nv = c->set->omesh_nv;
   rp.omesh_nt = c->set->omesh_nt;
   rp.obj_rgb = c->set->obj_rgb;
+  rp.robot_sph = c->d_robot_sph;
   rp.near_ = c->near_;
   rp.depth = out.depth;
   rp.depth_fp16 = c->cfg.depth_fp16;
@@ -377,7 +380,10 @@ extern "C" gx_status gx_scene_set_create(const gx_scene_desc* scenes, int32_t n_
             ((uint32_t)mesh->tris[3 * t + 2] << 16);
   if ((e = upload(s, &s->omesh_v, ov.data(), ov.size())) != cudaSuccess) return bail(e, "mesh");
   if ((e = upload(s, &s->omesh_t, ot.data(), ot.size())) != cudaSuccess) return bail(e, "mesh");
-  if ((e = upload(s, &s->obj_rgb, mesh->obj_rgb, (size_t)GX_MAX_OBJECTS)) != cudaSuccess)
+  std::vector<uint32_t> rgb96(GX_MAX_OBJECTS + 32);
+  std::memcpy(rgb96.data(), mesh->obj_rgb, GX_MAX_OBJECTS * 4);
+  std::memcpy(rgb96.data() + GX_MAX_OBJECTS, mesh->robot_rgb, 32 * 4);
+  if ((e = upload(s, &s->obj_rgb, rgb96.data(), rgb96.size())) != cudaSuccess)
     return bail(e, "colours");
   s->omesh_nv = mesh->n_verts;
   s->omesh_nt = mesh->n_tris;
@@ -498,6 +504,11 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
   if ((e = cudaMemset(x->st.held, 0xff, n * 4)) != cudaSuccess) return bail(e, "state");
   if ((e = cudaMalloc(&x->d_cam, n * 12 * sizeof(float))) != cudaSuccess) return bail(e, "cam");
   if ((e = cudaMemset(x->d_cam, 0, n * 12 * sizeof(float))) != cudaSuccess) return bail(e, "cam");
+  if (c.render_robot) {
+    if ((e = cudaMalloc(&x->d_robot_sph, n * 32 * sizeof(float4))) != cudaSuccess ||
+        (e = cudaMemset(x->d_robot_sph, 0, n * 32 * sizeof(float4))) != cudaSuccess)
+      return bail(e, "robot spheres");
+  }
   if ((e = cudaMalloc(&x->d_err, sizeof(unsigned))) != cudaSuccess) return bail(e, "err");
   if ((e = cudaMemset(x->d_err, 0, sizeof(unsigned))) != cudaSuccess) return bail(e, "err");
   if ((e = cudaMallocHost(&x->h_err, sizeof(unsigned))) != cudaSuccess) return bail(e, "err");
@@ -586,6 +597,7 @@ extern "C" void gx_destroy(gx_ctx* x) {
   for (cudaEvent_t e : x->prof_ev) cudaEventDestroy(e);
   cudaFree(x->d_counters);
   cudaFree(x->d_order);
+  cudaFree(x->d_robot_sph);
   cudaFree(x->d_nsdf_pts);
   cudaFree(x->d_nsdf_d);
   cudaFree(x->d_nsdf_tiles);

@@ -91,6 +91,7 @@ struct PhysicsParams {
   // neural-SDF static test: pass 1 writes the candidate sphere centres
   // (x, y, z, radius or -1 when unused) and stops; pass 2 reads the
   // predicted distances and consults the grid only below the margin.
+  float4* robot_sph;                    // optional [n][32]: spheres at the accepted pose
   int slide;                            // sliding heuristic on
   int place_jitter;                     // object placing heuristic on
   uint64_t seed;                        // Philox key (the reset key)
@@ -142,7 +143,8 @@ struct RasterParams {
   const float4* omesh_v;   // [nv] unit instance mesh
   const uint32_t* omesh_t; // [nt] packed
   int omesh_nv, omesh_nt;
-  const uint32_t* obj_rgb; // [64]
+  const uint32_t* obj_rgb; // [64 objects + 32 robot spheres]
+  const float4* robot_sph; // optional [n][32] robot sphere centre, radius (0: unused)
   float near_;
   void* depth;
   int depth_fp16;

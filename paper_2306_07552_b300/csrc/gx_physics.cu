@@ -351,10 +351,19 @@ __global__ void __launch_bounds__(32 * kEnvsPerBlock) physics_kernel(const Physi
     ax = x0; az = z0; ayaw = th0;
 #pragma unroll
     for (int k = 0; k < 7; ++k) aq[k] = q0[k];
-    fk(rb, ax, az, ayaw, aq, -1, myR, myt, eR, et);
+    fk(rb, ax, az, ayaw, aq, P.robot_sph ? mylink : -1, myR, myt, eR, et);
   } else {
     et[0] += offx;  // a slid base carries the tool frame along
     et[2] += offz;
+  }
+  if (P.robot_sph) {  // the robot body for the rasteriser: spheres at the accepted pose
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (lane < rb.n_spheres) {
+      float cc[3];
+      apply(myR, myt, rb.sphere_pos[lane][0], rb.sphere_pos[lane][1], rb.sphere_pos[lane][2], cc);
+      v = make_float4(cc[0] + offx, cc[1], cc[2] + offz, rb.sphere_radius[lane]);
+    }
+    P.robot_sph[(size_t)env * 32 + lane] = v;
   }
 
   // (a8) grasp / release at the accepted pose

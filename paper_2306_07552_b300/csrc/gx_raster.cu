@@ -598,10 +598,16 @@ __global__ void __launch_bounds__(kThreads, kRasterMinBlocks) raster_kernel(cons
       }
       // 3. free objects (last pass): icosahedra scaled to each object's radius
       if (base + kListCap >= S.n_meshlets) {
+        // objects, then (when rendered) the robot's 32 sphere slots, which
+        // take instance slots 64.. so their colours follow the objects'
+        const int n_inst = P.M + (P.robot_sph ? 32 : 0);
         while (!dead) {
           const int j = pop_item(&ctr[3], lane);
-          if (j >= P.M) break;
-          const float4 o = P.obj[(size_t)env * P.M + j];
+          if (j >= n_inst) break;
+          const float4 o = j < P.M ? P.obj[(size_t)env * P.M + j]
+                                   : P.robot_sph[(size_t)env * 32 + (j - P.M)];
+          if (!(o.w > 0.f)) continue;
+          const int slot = j < P.M ? j : GX_MAX_OBJECTS + (j - P.M);
           if (!sphere_visible(cm, vw, o.x, o.y, o.z, o.w * 1.0001f + 1e-6f)) continue;
           for (int k = lane; k < P.omesh_nv; k += 32) {
             const float4 u = P.omesh_v[k];
@@ -611,7 +617,7 @@ __global__ void __launch_bounds__(kThreads, kRasterMinBlocks) raster_kernel(cons
           for (int k = lane; k < P.omesh_nt; k += 32) ws.tbuf[0][k] = P.omesh_t[k];
           __syncwarp();
           raster_cluster<kCount>(vw, cm, ws, 0, P.omesh_nv, P.omesh_nt,
-                                 (uint32_t)S.n_tris + (uint32_t)(j * P.omesh_nt), P.big_px, lane,
+                                 (uint32_t)S.n_tris + (uint32_t)(slot * P.omesh_nt), P.big_px, lane,
                                  cn);
         }
         // object vertices were written to vbuf[0] by ordinary stores: order

@@ -63,7 +63,7 @@ class GxSceneDesc(C.Structure):
 
 class GxObjectMesh(C.Structure):
     _fields_ = [("n_verts", C.c_int32), ("verts", f32p), ("n_tris", C.c_int32), ("tris", i32p),
-                ("obj_rgb", C.c_uint32 * MAX_OBJECTS)]
+                ("obj_rgb", C.c_uint32 * MAX_OBJECTS), ("robot_rgb", C.c_uint32 * 32)]
 
 
 class GxConfig(C.Structure):
@@ -72,7 +72,8 @@ class GxConfig(C.Structure):
                 ("obj_radius_min", C.c_float), ("obj_radius_max", C.c_float),
                 ("seed", C.c_uint64), ("env_scene", i32p), ("raster_regions", C.c_int32),
                 ("small_tri_px", C.c_int32), ("use_graph", C.c_int32), ("profile", C.c_int32),
-                ("sdf_mode", C.c_int32), ("sdf_margin", C.c_float), ("heuristics", C.c_int32)]
+                ("sdf_mode", C.c_int32), ("sdf_margin", C.c_float), ("render_robot", C.c_int32),
+                ("heuristics", C.c_int32)]
 
 
 OUTPUT_KEYS = ["depth", "rgb", "pose", "obj_pos", "held", "contact_mask", "contact_flags", "event",
@@ -184,7 +185,7 @@ def robot_struct(r: _inputs.Robot) -> GxRobot:
 class SceneSet:
     """Device copies of a list of scenes (grid, clusters, supports)."""
 
-    def __init__(self, scenes, obj_mesh=None, obj_rgb=None):
+    def __init__(self, scenes, obj_mesh=None, obj_rgb=None, robot_rgb=None):
         self._keep = []
         n = len(scenes)
         descs = (GxSceneDesc * n)()
@@ -212,6 +213,10 @@ class SceneSet:
         m.n_tris, m.tris = len(mt), mt.ctypes.data_as(i32p)
         rgb = _inputs.object_colors(MAX_OBJECTS) if obj_rgb is None else obj_rgb
         m.obj_rgb[:] = [int(x) for x in np.asarray(rgb, np.uint32)[:MAX_OBJECTS]]
+        rr = np.zeros(32, np.uint32)
+        rc = _inputs.robot_colors(_inputs.fetch_like_robot()) if robot_rgb is None else robot_rgb
+        rr[:len(rc)] = np.asarray(rc, np.uint32)[:32]
+        m.robot_rgb[:] = [int(x) for x in rr]
         self.n_obj_tris = len(mt)
         self.handle = C.c_void_p()
         _check(lib().gx_scene_set_create(descs, n, C.byref(m), C.byref(self.handle)))
@@ -320,7 +325,7 @@ class Sim:
     def __init__(self, scene_set: SceneSet, robot: _inputs.Robot, n_envs: int, img=(128, 128),
                  depth_fp16=False, render_rgb=True, n_objects=40, obj_radius=(0.03, 0.06),
                  seed=1, env_scene=None, raster_regions=0, small_tri_px=0, use_graph=False,
-                 profile=0, sdf_mode=0, sdf_margin=0.02, heuristics=0):
+                 profile=0, sdf_mode=0, sdf_margin=0.02, heuristics=0, render_robot=False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("gx needs a CUDA device; there is no CPU fallback")
@@ -341,6 +346,7 @@ class Sim:
         cfg.profile = int(profile)
         cfg.sdf_mode, cfg.sdf_margin = int(sdf_mode), float(sdf_margin)
         cfg.heuristics = int(heuristics)
+        cfg.render_robot = int(render_robot)
         self.robot_c = robot_struct(robot)
         self.handle = C.c_void_p()
         _check(lib().gx_create(scene_set.handle, C.byref(self.robot_c), C.byref(cfg),

@@ -146,6 +146,14 @@ def icosahedron() -> tuple[np.ndarray, np.ndarray]:
     return v.astype(np.float32), f
 
 
+def robot_colors(robot: "Robot") -> np.ndarray:
+    """Flat colour of each robot collision sphere when the robot body is
+    rendered: grey shades by link (base darkest)."""
+    link = np.asarray(robot.sphere_link, np.int64)
+    g = (0x50 + 0x12 * link).astype(np.uint32)
+    return ((g << 16) | (g << 8) | (g + 0x10)).astype(np.uint32)
+
+
 def object_colors(m: int, seed: int = 77) -> np.ndarray:
     rng = np.random.default_rng(seed)
     hues = (np.arange(m) * 0.61803398875 + rng.random()) % 1.0

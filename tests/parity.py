@@ -8,7 +8,7 @@ oracle reports a decision within 1e-4 m of its threshold ("near band"; such
 environments are counted and skipped).  Continuous results must agree within
 1e-5 m / rad.  Images are rendered by the oracle from the GPU's state after
 the step; on pixels the oracle does not flag as ambiguous, coverage and RGB
-must match exactly and depth within 1e-5 relative.
+must match exactly and depth within 1e-5 relative + 5e-6 m.
 """
 import math
 
@@ -18,6 +18,11 @@ import oracle as O
 
 POSE_TOL = 1e-5
 DEPTH_REL = 1e-5
+# FP32 forward kinematics places the camera and the robot's own spheres
+# within the pose error measured in lockstep (<= 2.5e-6 m); a depth can carry
+# both errors, which at the few-centimetre depths of the robot body exceeds
+# 1e-5 relative, so depth also gets an absolute 5e-6 m
+DEPTH_ABS = 5e-6
 
 
 def oracle_state(arrs, e, M):
@@ -133,8 +138,10 @@ def check_image(orc, after, out, e, W, H, M, tally, fp16=False):
             tally.fp16_max_frac = max(tally.fp16_max_frac, float((err / lim).max()))
         assert np.all(err <= lim), (e, float((err - lim).max()))
     else:
-        rel = np.abs(gd[cov] - depth[cov]) / depth[cov]
+        err = np.abs(gd[cov] - depth[cov])
+        rel = err / depth[cov]
         if rel.size:
             tally.max_depth_rel = max(tally.max_depth_rel, float(rel.max()))
-        assert np.all(rel <= DEPTH_REL), (e, float(rel.max()))
+        assert np.all(err <= DEPTH_REL * depth[cov] + DEPTH_ABS), (
+            e, float((err - DEPTH_REL * depth[cov]).max()))
     return stats

@@ -311,3 +311,33 @@ def test_uneven_fp16_sampled():
     print(tally, tris[big], tris[small])
     sim.close()
     ss.close()
+
+
+def test_robot_body_rendering_lockstep(room):
+    """render_robot: the robot's spheres in every image, against the oracle
+    rendering the same spheres from the state after the step."""
+    gx, scene, ss, orc = room
+    n, M, W = 16, 10, 64
+    orc_b = O.Oracle(ROBOT, scene, I.icosahedron(), I.object_colors(64),
+                     robot_rgb=I.robot_colors(ROBOT))
+    sim = gx.Sim(ss, ROBOT, n, img=(W, W), n_objects=M, obj_radius=(0.03, 0.06), seed=1,
+                 render_robot=True)
+    sim.reset()
+    acts = I.make_actions(10, n, "uniform", seed=0)
+    tally = Tally()
+    robot_px = 0
+    n_tris, nt = len(scene.tris), len(I.icosahedron()[1])
+    for t in range(10):
+        before = {k: v.copy() for k, v in sim.state_arrays().items()}
+        out = sim.step(torch.from_numpy(acts[t]).cuda())
+        torch.cuda.synchronize()
+        after = sim.state_arrays()
+        check_step(orc_b, before, after, out, acts[t], range(n), M, tally)
+        for e in range(n):
+            check_image(orc_b, after, out, e, W, W, M, tally)
+            st = oracle_state(after, e, M)
+            robot_px += int((orc_b.render(st, W, W)[3] >= n_tris + 64 * nt).sum())
+    print(tally, f"robot pixels {robot_px}")
+    assert robot_px > 1000
+    assert tally.ambiguous < 0.03 * (tally.pixels + tally.ambiguous)
+    sim.close()

@@ -656,3 +656,24 @@ def test_invariants_over_random_rollouts():
         if t % 20 == 0:
             depth, _, _, _, _ = orc.render(st, 32, 32)
             assert np.all((depth == 0) | (depth >= ROBOT.cam_near))
+
+
+def test_robot_body_renders_as_instanced_spheres():
+    """With robot colours given, the robot's collision spheres render like
+    the objects: every pixel they win carries its sphere's colour, pixels
+    elsewhere are unchanged, and the arm in front of the head camera shows."""
+    sc = scene_from_boxes([FLOOR], (-3, -0.3, -3), (3, 2.5, 3), h=0.05)
+    rc = I.robot_colors(ROBOT)
+    plain = O.Oracle(ROBOT, sc, I.icosahedron(), I.object_colors(64))
+    body = O.Oracle(ROBOT, sc, I.icosahedron(), I.object_colors(64), robot_rgb=rc)
+    st = O.Oracle.make_state((0, 0, 0), ROBOT.q_rest)
+    d0, c0, a0, w0, _ = plain.render(st, 64, 64)
+    d1, c1, a1, w1, _ = body.render(st, 64, 64)
+    n_tris, nt = len(sc.tris), len(I.icosahedron()[1])
+    rob = w1 >= n_tris + 64 * nt
+    assert rob.sum() > 20                                  # the arm is in view
+    sphere = (w1[rob] - n_tris) // nt - 64
+    assert np.array_equal(c1[rob], rc[sphere])
+    assert np.all(d1[rob] <= np.where(d0[rob] > 0, d0[rob], np.inf) + 1e-12)
+    same = ~rob & ~a0 & ~a1
+    assert np.array_equal(c1[same], c0[same]) and np.allclose(d1[same], d0[same])
