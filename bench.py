@@ -115,7 +115,7 @@ def golden(name):
 # Workloads whose views are drawn from another workload's scenes and camera
 # statistics (the static test differs, the rendering work per view does not).
 SAME_VIEWS = {"apartments4096_nsdf": "apartments4096", "uneven16384_nsdf": "uneven8192",
-              "apartments4096_column": "apartments4096"}
+              "apartments4096_column": "apartments4096"}  # same scenes and cameras
 
 
 def raster_work(workload):
@@ -216,7 +216,7 @@ def _oracle_worker(args):
             sc = (I.room_scene(w.scene_seed + s, targets[s], grid_h=w.grid_h)
                   if w.scene_kind == "room" else
                   I.apartment_scene(w.scene_seed + s, targets[s], grid_h=w.grid_h))
-            scenes[s] = O.Oracle(robot, sc, I.icosahedron(), I.object_colors(64))
+            scenes[s] = O.Oracle(robot, sc, I.icosahedron(), I.object_colors(256))
         st = O.Oracle.make_state((0, 0, 0), np.zeros(7))
         scenes[s].reset(st, w.reset_seed, e, w.n_objects, *w.obj_radius)
         states.append((scenes[s], st))
@@ -260,7 +260,7 @@ def cpu_baseline(w, scenes, seconds):
     for e in sample_envs:
         s = int(env_scene[e])
         if s not in orcs:
-            orcs[s] = O.Oracle(robot, scenes[s], I.icosahedron(), I.object_colors(64))
+            orcs[s] = O.Oracle(robot, scenes[s], I.icosahedron(), I.object_colors(256))
         st = O.Oracle.make_state((0, 0, 0), np.zeros(7))
         orcs[s].reset(st, w.reset_seed, e, w.n_objects, *w.obj_radius)
         states.append((orcs[s], st))
@@ -351,7 +351,7 @@ def run_reference(args, w, rank, world):
     for e in sample:
         s = int(env_scene[e])
         if s not in orcs:
-            orcs[s] = O.Oracle(robot, scenes[s], I.icosahedron(), I.object_colors(64))
+            orcs[s] = O.Oracle(robot, scenes[s], I.icosahedron(), I.object_colors(256))
         st = O.Oracle.make_state((0, 0, 0), np.zeros(7))
         orcs[s].reset(st, w.reset_seed, e, w.n_objects, *w.obj_radius)
         sts.append((orcs[s], st))
@@ -401,6 +401,8 @@ def main():
     ap.add_argument("--envs", type=int, default=0, help="smaller batch (profiling runs)")
     ap.add_argument("--scenes", type=int, default=0, help="fewer scenes (profiling runs)")
     ap.add_argument("--small-px", type=int, default=0, help="expansion bbox limit (0: auto)")
+    ap.add_argument("--broadphase", action="store_true",
+                    help="object broad-phase (four offset regular grids per environment)")
     ap.add_argument("--render-robot", action="store_true",
                     help="render the robot's collision spheres into every image")
     ap.add_argument("--heuristics", type=int, default=0,
@@ -438,7 +440,7 @@ def main():
     sim_kw = dict(img=(w.img, w.img), depth_fp16=w.depth_fp16, render_rgb=w.rgb,
                   n_objects=w.n_objects, obj_radius=w.obj_radius, seed=rank_seeds(w, rank)[0],
                   small_tri_px=args.small_px, heuristics=args.heuristics,
-                  render_robot=args.render_robot)
+                  render_robot=args.render_robot, broadphase=args.broadphase)
     column = w.sdf == "column"
     sdf_mode = 1 if neural else (2 if column else 0)
     sim = gx.Sim(ss, I.fetch_like_robot(), n, profile=0 if args.graph else 1,
@@ -476,6 +478,9 @@ def main():
         sim.reset(stream=stream)
         for t in range(args.warmup):
             one(t)
+        # device error bits of the warm-up (e.g. 0x2: a crowded reset kept an
+        # object's last placement try), recorded and cleared
+        warmup_err = sim.device_error()
         if not args.no_autotune:
             # rasteriser setting timed on this batch's own state (restored)
             abuf.copy_(acts[args.warmup - 1])
@@ -643,7 +648,8 @@ def main():
         "data": "synthetic (procedural apartments standing in for ReplicaCAD; see DESIGN.md)",
         "config": {**config_of(w), "heuristics": {"sliding": bool(args.heuristics & 1),
                                                   "object_placing": bool(args.heuristics & 2)},
-                   "robot_body_rendered": bool(args.render_robot)},
+                   "robot_body_rendered": bool(args.render_robot),
+                   "object_broadphase": bool(args.broadphase)},
         "phases_ms_per_launch": {k: phase_ms[i] / max(phase_n[i], 1)
                                  for i, k in enumerate(["physics", "raster", "reset",
                                                         "nsdf_query"])},
@@ -653,6 +659,7 @@ def main():
         "raster_counters_per_view": counters,
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches, "clocks": clocks, "device_error": dev_err,
+        "device_error_warmup": warmup_err,
     }
     print(json.dumps(line), flush=True)
     ss.close()

@@ -54,9 +54,11 @@ typedef enum {
 
 /* device error word bits (gx_device_error) */
 #define GX_DEV_NONFINITE_ACTION 0x1u  /* some action was NaN/Inf; used 0     */
-#define GX_DEV_PLACEMENT_FAILED 0x2u  /* a reset placement used all 64 tries */
+#define GX_DEV_PLACEMENT_FAILED 0x2u  /* a reset placement used all 64 tries
+                                         and kept the last one; reported by
+                                         gx_device_error only (no GX_EDEVICE) */
 
-#define GX_MAX_OBJECTS 64
+#define GX_MAX_OBJECTS 256
 #define GX_MAX_SPHERES 31
 
 /* Robot description (FP32, host memory, copied at gx_create).
@@ -124,7 +126,7 @@ typedef struct {
   int32_t img_w, img_h;    /* multiples of 32, <= 256                         */
   int32_t depth_fp16;      /* 0: depth as float32, 1: as IEEE half            */
   int32_t render_rgb;      /* 0: skip the RGB image                           */
-  int32_t n_objects;       /* free objects per environment, <= 64             */
+  int32_t n_objects;       /* free objects per environment, <= 256            */
   float obj_radius_min, obj_radius_max;   /* object radius drawn at reset     */
   uint64_t seed;           /* Philox key for resets                           */
   const int32_t* env_scene; /* host [n_envs] scene per env; NULL: env i uses
@@ -156,6 +158,11 @@ typedef struct {
                               d - r is below sdf_margin, or not finite; a
                               centre outside the grid box is contact          */
   float sdf_margin;        /* metres, >= 0 (e.g. 0.02)                        */
+  int32_t broadphase;      /* 1: robot spheres meet only the objects listed in
+                              one cell of four offset regular grids per env
+                              (appendix "Additional Collision-Detection
+                              Details"; cells 0.5 m, 12 objects each, fuller
+                              cells brute force); results are unchanged       */
   int32_t render_robot;    /* 1: the robot's collision spheres are rendered
                               (instanced like the objects, robot_rgb)        */
   int32_t heuristics;      /* the paper's heuristics (appendix "Description of
@@ -411,7 +418,7 @@ int32_t gx_column_spans(const gx_scene_set* set, int32_t scene, int32_t radius_i
  * forward, then the eye position; obj [n][n_objects][4] object centre and
  * radius.  Outputs: depth [n][img_h][img_w] float32 (or half when depth_fp16),
  * rgb [n][img_h][img_w][3] (optional).  Image sides must be multiples of 32
- * and at most 256 (larger sizes return GX_EINVAL); n_objects <= 64.
+ * and at most 256 (larger sizes return GX_EINVAL); n_objects <= 256.
  * The first call on a device (the current one) sets the scratch up
  * synchronously; make that first call before any stream capture.  Every call
  * shares the same scratch and clears what it needs at the start, so calls

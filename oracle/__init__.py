@@ -15,7 +15,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "libgx_oracle.so")
-MAX_OBJ = 64
+MAX_OBJ = 256
 BAND = 1e-4
 
 
@@ -130,6 +130,7 @@ def _declare(L):
     L.orc_render.argtypes = [P(Robot_c), P(Scene_c), P(ObjMesh_c), P(State_c), C.c_int32,
                              C.c_int32, C.c_double, C.c_double, C.c_double, f64p, u32p, u8p,
                              i32p, P(RenderStats_c)]
+    L.orc_render_cos.argtypes = L.orc_render.argtypes + [f64p]
     L.orc_nsdf_sample.argtypes = [P(Scene_c), C.c_uint64, C.c_uint32, C.c_uint32, C.c_double,
                                   f64p, f64p, P(C.c_int)]
     L.orc_nsdf_sample.restype = C.c_int
@@ -365,18 +366,22 @@ class Oracle:
             nb[k] = nbb.value
         return P, d, t, nb
 
-    def render(self, st, W, H, eps_px=None, tol_rel=None, cos_min=None):
+    def render(self, st, W, H, eps_px=None, tol_rel=None, cos_min=None, cos_out=None):
         n = W * H
         depth = np.zeros(n)
         rgb = np.zeros(n, np.uint32)
         amb = np.zeros(n, np.uint8)
         win = np.zeros(n, np.int32)
         stats = RenderStats_c()
-        self.L.orc_render(C.byref(self.robot), C.byref(self.scene), C.byref(self.objmesh),
-                          C.byref(st), W, H, self.EPS_PX if eps_px is None else eps_px,
-                          self.TOL_REL if tol_rel is None else tol_rel,
-                          self.COS_MIN if cos_min is None else cos_min, _p(depth, f64p),
-                          _p(rgb, u32p), _p(amb, u8p), _p(win, i32p), C.byref(stats))
+        cs = np.ones(n)
+        self.L.orc_render_cos(C.byref(self.robot), C.byref(self.scene), C.byref(self.objmesh),
+                              C.byref(st), W, H, self.EPS_PX if eps_px is None else eps_px,
+                              self.TOL_REL if tol_rel is None else tol_rel,
+                              self.COS_MIN if cos_min is None else cos_min, _p(depth, f64p),
+                              _p(rgb, u32p), _p(amb, u8p), _p(win, i32p), C.byref(stats),
+                              _p(cs, f64p))
+        if cos_out is not None:
+            cos_out[...] = cs.reshape(H, W)
         return (depth.reshape(H, W), rgb.reshape(H, W), amb.reshape(H, W).astype(bool),
                 win.reshape(H, W), stats)
 

@@ -754,7 +754,8 @@ void orc_step_ex(const orc_robot* rb, const orc_scene* sc, orc_state* st, const 
 /* ------------------------------------------------------------------------ */
 /* Reset: objects on support tops, then the robot base in free space, each  */
 /* by rejection sampling with at most 64 Philox draws.  Stream (env,        */
-/* episode, j, try): j = object index, 64 = robot.                          */
+/* episode, j, try): j = object index, ORC_MAX_OBJ = robot, ORC_MAX_OBJ + 1 */
+/* = the task's goal.                                                       */
 /* ------------------------------------------------------------------------ */
 void orc_reset(const orc_robot* rb, const orc_scene* sc, orc_state* st, uint64_t seed,
                int32_t env, int32_t n_obj, float rho_min, float rho_max, orc_reset_out* out) {
@@ -786,7 +787,7 @@ void orc_reset(const orc_robot* rb, const orc_scene* sc, orc_state* st, uint64_t
   int ok = 0;
   for (int k = 0; k < 7; ++k) st->q[k] = rb->q_rest[k];
   for (uint32_t t = 0; t < 64 && !ok; ++t) {
-    uint32_t ctr[4] = {(uint32_t)env, (uint32_t)st->episode, 64u, t}, w[4];
+    uint32_t ctr[4] = {(uint32_t)env, (uint32_t)st->episode, ORC_MAX_OBJ, t}, w[4];
     orc_philox4x32_10(ctr, key, w);
     const float* s = sc->spawn;
     st->base[0] = s[0] + unit24(w[0]) * ((double)s[2] - (double)s[0]);
@@ -807,7 +808,7 @@ void orc_reset(const orc_robot* rb, const orc_scene* sc, orc_state* st, uint64_t
   memset(st->p_pre, 0, sizeof(st->p_pre));
   st->step_count = 0;
   /* task: object 0 is the target; its goal lies on a support top, drawn
-   * like an object placement from stream 65 (first draw, not tested for
+   * like an object placement from stream ORC_MAX_OBJ + 1 (first draw, not tested for
    * collisions); the previous distances start at the episode's first pose
    * and the previous joint actions at 0. */
   memset(st->goal, 0, sizeof(st->goal));
@@ -815,7 +816,7 @@ void orc_reset(const orc_robot* rb, const orc_scene* sc, orc_state* st, uint64_t
   memset(st->prev_a, 0, sizeof(st->prev_a));
   st->prev_d = st->prev_e = 0.0;
   if (n_obj > 0 && sc->n_supports > 0) {
-    uint32_t ctr[4] = {(uint32_t)env, (uint32_t)st->episode, 65u, 0u}, w[4];
+    uint32_t ctr[4] = {(uint32_t)env, (uint32_t)st->episode, ORC_MAX_OBJ + 1, 0u}, w[4];
     orc_philox4x32_10(ctr, key, w);
     const double rho = st->obj[0][3];
     uint32_t si = (uint32_t)(((uint64_t)(w[0] >> 8) * (uint64_t)sc->n_supports) >> 24);
@@ -969,6 +970,14 @@ void orc_render(const orc_robot* rb, const orc_scene* sc, const orc_objmesh* om,
                 const orc_state* st, int32_t W, int32_t H, double eps_px, double tol_rel,
                 double cos_min, double* depth, uint32_t* rgb, uint8_t* ambiguous,
                 int32_t* winner, orc_render_stats* stats) {
+  orc_render_cos(rb, sc, om, st, W, H, eps_px, tol_rel, cos_min, depth, rgb, ambiguous, winner,
+                 stats, NULL);
+}
+
+void orc_render_cos(const orc_robot* rb, const orc_scene* sc, const orc_objmesh* om,
+                    const orc_state* st, int32_t W, int32_t H, double eps_px, double tol_rel,
+                    double cos_min, double* depth, uint32_t* rgb, uint8_t* ambiguous,
+                    int32_t* winner, orc_render_stats* stats, double* cos_out) {
   double links[8][12], cam[12];
   orc_fk(rb, st->base, st->q, links, NULL, cam);
   size_t np = (size_t)W * H;
@@ -1030,6 +1039,7 @@ void orc_render(const orc_robot* rb, const orc_scene* sc, const orc_objmesh* om,
     depth[p] = w >= 0 ? zw : 0.0;
     rgb[p] = w >= 0 ? L[w].rgb : 0u;
     if (winner) winner[p] = w >= 0 ? L[w].id : -1;
+    if (cos_out) cos_out[p] = w >= 0 ? L[w].cosv : 1.0;
     ambiguous[p] = amb;
     local.ambiguous += amb;
   }

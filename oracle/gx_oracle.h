@@ -18,7 +18,7 @@
 #define GX_ORACLE_H
 #include <stdint.h>
 
-#define ORC_MAX_OBJ 64
+#define ORC_MAX_OBJ 256
 #define ORC_MAX_SPHERES 32
 #define ORC_BAND 1e-4 /* m: decisions this close to their threshold are "near band" */
 
@@ -155,6 +155,12 @@ void orc_render(const orc_robot* rb, const orc_scene* sc, const orc_objmesh* om,
                 const orc_state* st, int32_t W, int32_t H, double eps_px, double tol_rel,
                 double cos_min, double* depth, uint32_t* rgb, uint8_t* ambiguous,
                 int32_t* winner, orc_render_stats* stats);
+/* orc_render that also reports, per pixel, |cos| between the view ray and
+ * the winning surface's normal (1 where nothing is hit). */
+void orc_render_cos(const orc_robot* rb, const orc_scene* sc, const orc_objmesh* om,
+                    const orc_state* st, int32_t W, int32_t H, double eps_px, double tol_rel,
+                    double cos_min, double* depth, uint32_t* rgb, uint8_t* ambiguous,
+                    int32_t* winner, orc_render_stats* stats, double* cos_out);
 
 /* Neural-SDF training sample i: even i uniform over the lattice box, odd i
  * the first of at most 64 uniform draws with |d| < band; label = grid d.

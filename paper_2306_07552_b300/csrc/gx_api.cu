@@ -42,6 +42,8 @@ struct gx_ctx {
   StateView st{};
   float* d_cam = nullptr;
   float4* d_robot_sph = nullptr;       // robot spheres for rendering the robot body
+  BpCell* d_bp = nullptr;              // object broad-phase cells
+  int bp_cells = 0;
   unsigned* d_err = nullptr;
   unsigned* h_err = nullptr;
   cudaEvent_t ev_err = nullptr;
@@ -127,6 +129,9 @@ gx_status poll_device_error(gx_ctx* c, bool wait) {
     *c->h_err = 0;
     c->dev_err_seen |= v;
     cudaMemset(c->d_err, 0, sizeof(unsigned));
+    // a crowded reset keeping an object's last try is reported by
+    // gx_device_error but does not fail the call
+    if ((v & ~GX_DEV_PLACEMENT_FAILED) == 0) return GX_OK;
     return fail(c, GX_EDEVICE, "device error word 0x%x:%s%s%s", v,
                 (v & GX_DEV_NONFINITE_ACTION) ? " non-finite action (used 0)" : "",
                 (v & GX_DEV_PLACEMENT_FAILED) ? " reset placement used all tries" : "",
@@ -179,6 +184,8 @@ void enqueue_step(gx_ctx* c, const float* actions, const gx_outputs& out, cudaSt
   pp.st = c->st;
   pp.cam = c->d_cam;
   pp.robot_sph = c->d_robot_sph;
+  pp.bp = c->d_bp;
+  pp.bp_cells = c->bp_cells;
   pp.out = out;
   pp.err = c->d_err;
   pp.raster_work = c->d_raster_work;
@@ -321,6 +328,11 @@ extern "C" gx_status gx_scene_set_create(const gx_scene_desc* scenes, int32_t n_
     launch_grid_build(grid, dboxes, d.n_boxes, ds.ox, ds.oy, ds.oz, ds.h, ds.nx, ds.ny, ds.nz, 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "grid kernel");
     ds.grid = grid;
+    // object broad-phase lattice: the grid box with a cell of margin
+    ds.bp_x0 = ds.ox - kBpCell;
+    ds.bp_z0 = ds.oz - kBpCell;
+    ds.bp_nx = (int)std::ceil(((ds.nx - 1) * (double)ds.h + 2 * kBpCell) / kBpCell) + 1;
+    ds.bp_nz = (int)std::ceil(((ds.nz - 1) * (double)ds.h + 2 * kBpCell) / kBpCell) + 1;
     {
       // column grid over the same box: count, prefix sum on the host, fill
       const double h = (double)ds.h;
@@ -413,7 +425,7 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
       c.img_h % 32)
     return fail(nullptr, GX_EINVAL, "image sides must be multiples of 32 in [32, 256]");
   if (c.n_objects < 0 || c.n_objects > GX_MAX_OBJECTS)
-    return fail(nullptr, GX_EINVAL, "n_objects must be in [0, 64]");
+    return fail(nullptr, GX_EINVAL, "n_objects must be in [0, 256]");
   if (!(c.obj_radius_min > 0.f) || !(c.obj_radius_max >= c.obj_radius_min))
     return fail(nullptr, GX_EINVAL, "bad object radius range");
   if (robot->n_spheres < 1 || robot->n_spheres > 30)
@@ -504,6 +516,14 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
   if ((e = cudaMemset(x->st.held, 0xff, n * 4)) != cudaSuccess) return bail(e, "state");
   if ((e = cudaMalloc(&x->d_cam, n * 12 * sizeof(float))) != cudaSuccess) return bail(e, "cam");
   if ((e = cudaMemset(x->d_cam, 0, n * 12 * sizeof(float))) != cudaSuccess) return bail(e, "cam");
+  if (c.broadphase) {
+    for (int sc = 0; sc < set->n; ++sc)
+      x->bp_cells = std::max(x->bp_cells, set->host[sc].bp_nx * set->host[sc].bp_nz);
+    const size_t bytes = n * 4 * (size_t)x->bp_cells * sizeof(BpCell);
+    if ((e = cudaMalloc(&x->d_bp, bytes)) != cudaSuccess ||
+        (e = cudaMemset(x->d_bp, 0, bytes)) != cudaSuccess)
+      return bail(e, "broad-phase");
+  }
   if (c.render_robot) {
     if ((e = cudaMalloc(&x->d_robot_sph, n * 32 * sizeof(float4))) != cudaSuccess ||
         (e = cudaMemset(x->d_robot_sph, 0, n * 32 * sizeof(float4))) != cudaSuccess)
@@ -598,6 +618,7 @@ extern "C" void gx_destroy(gx_ctx* x) {
   cudaFree(x->d_counters);
   cudaFree(x->d_order);
   cudaFree(x->d_robot_sph);
+  cudaFree(x->d_bp);
   cudaFree(x->d_nsdf_pts);
   cudaFree(x->d_nsdf_d);
   cudaFree(x->d_nsdf_tiles);
@@ -627,6 +648,8 @@ extern "C" gx_status gx_reset(gx_ctx* x, const uint8_t* env_mask, void* stream) 
   rp.rho_min = x->cfg.obj_radius_min;
   rp.rho_max = x->cfg.obj_radius_max;
   rp.err = x->d_err;
+  rp.bp = x->d_bp;
+  rp.bp_cells = x->bp_cells;
   cudaEvent_t* ev = (x->cfg.profile & 1) ? prof_slot(x, 1) : nullptr;
   if (ev) cudaEventRecord(ev[0], s);
   launch_reset(rp, s);
@@ -748,6 +771,10 @@ extern "C" gx_status gx_load_state(gx_ctx* x, const void* host, size_t bytes) {
   if (!x || !host || bytes != x->state_bytes) return fail(x, GX_EINVAL, "gx_load_state: bad size");
   CK(x, cudaDeviceSynchronize());
   CK(x, cudaMemcpy(x->d_state, host, bytes, cudaMemcpyHostToDevice));
+  if (x->d_bp) {  // the object broad-phase follows the loaded objects
+    launch_bp_rebuild(x->set->d_scenes, x->d_env_scene, x->st, x->n, x->M, x->d_bp, x->bp_cells, 0);
+    CK(x, cudaDeviceSynchronize());
+  }
   return GX_OK;
 }
 
@@ -849,6 +876,11 @@ extern "C" gx_status gx_autotune(gx_ctx* x, const float* actions, const gx_outpu
         for (int t = 0; t < steps; ++t) enqueue_step(x, actions, *out, s);
         cudaEventRecord(e1, s);
         err = cudaMemcpyAsync(x->d_state, saved, x->state_bytes, cudaMemcpyDeviceToDevice, s);
+        if (err == cudaSuccess && x->d_bp) {
+          launch_bp_rebuild(x->set->d_scenes, x->d_env_scene, x->st, x->n, x->M, x->d_bp,
+                            x->bp_cells, s);
+          err = cudaGetLastError();
+        }
         if (err == cudaSuccess) err = cudaEventSynchronize(e1);
         float ms = 0.f;
         if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);

@@ -95,6 +95,83 @@ __device__ bool column_contact(const DScene& s, float cx, float cy, float cz, fl
   return true;
 }
 
+// Broad-phase cell range of an object (x, z, radius rho) in grid g, padded
+// by 0.1 mm so rounding can only add cells; false outside the lattice.
+__device__ __forceinline__ void bp_range(const DScene& s, int g, float x, float z, float rho,
+                                         int& i0, int& i1, int& k0, int& k1) {
+  const float sx = (g & 1) ? 0.5f * kBpCell : 0.f, sz = (g & 2) ? 0.5f * kBpCell : 0.f;
+  const float inv = 1.f / kBpCell, pad = rho + 1e-4f;
+  i0 = max((int)floorf((x - pad - s.bp_x0 - sx) * inv), 0);
+  i1 = min((int)floorf((x + pad - s.bp_x0 - sx) * inv), s.bp_nx - 1);
+  k0 = max((int)floorf((z - pad - s.bp_z0 - sz) * inv), 0);
+  k1 = min((int)floorf((z + pad - s.bp_z0 - sz) * inv), s.bp_nz - 1);
+}
+__device__ __forceinline__ void bp_insert(BpCell* grids, int cells, const DScene& s, int j,
+                                          float x, float z, float rho) {
+  for (int g = 0; g < 4; ++g) {
+    int i0, i1, k0, k1;
+    bp_range(s, g, x, z, rho, i0, i1, k0, k1);
+    for (int k = k0; k <= k1; ++k)
+      for (int i = i0; i <= i1; ++i) {
+        BpCell& c = grids[(size_t)g * cells + (size_t)k * s.bp_nx + i];
+        const uint32_t slot = atomicAdd(&c.count, 1u);
+        if (slot < (uint32_t)kBpCap) c.id[slot] = (uint8_t)j;
+      }
+  }
+}
+// Removes object j from its cells (single thread per environment); a cell
+// that ever overflowed stays in brute-force mode until the next rebuild.
+__device__ __forceinline__ void bp_remove(BpCell* grids, int cells, const DScene& s, int j,
+                                          float x, float z, float rho) {
+  for (int g = 0; g < 4; ++g) {
+    int i0, i1, k0, k1;
+    bp_range(s, g, x, z, rho, i0, i1, k0, k1);
+    for (int k = k0; k <= k1; ++k)
+      for (int i = i0; i <= i1; ++i) {
+        BpCell& c = grids[(size_t)g * cells + (size_t)k * s.bp_nx + i];
+        if (c.count > (uint32_t)kBpCap) continue;
+        for (uint32_t t = 0; t < c.count; ++t)
+          if (c.id[t] == (uint8_t)j) {
+            c.id[t] = c.id[c.count - 1];
+            c.count -= 1;
+            break;
+          }
+      }
+  }
+}
+// The cell of the grid that holds the whole XZ disk of a query sphere;
+// nullptr when there is none in range (the caller tests every object).
+__device__ __forceinline__ const BpCell* bp_cell(const BpCell* grids, int cells, const DScene& s,
+                                                 float x, float z, float r) {
+  const float inv = 1.f / kBpCell, h = 0.5f * kBpCell;
+  int g = 0, ci = 0, ck = 0;
+  {
+    const float a = (x - s.bp_x0) * inv;
+    const int lo = (int)floorf(a - r * inv), hi = (int)floorf(a + r * inv);
+    if (lo == hi) {
+      ci = lo;
+    } else {
+      g |= 1;
+      ci = (int)floorf((x - r - s.bp_x0 - h) * inv);
+      if ((int)floorf((x + r - s.bp_x0 - h) * inv) != ci) return nullptr;
+    }
+  }
+  {
+    const float a = (z - s.bp_z0) * inv;
+    const int lo = (int)floorf(a - r * inv), hi = (int)floorf(a + r * inv);
+    if (lo == hi) {
+      ck = lo;
+    } else {
+      g |= 2;
+      ck = (int)floorf((z - r - s.bp_z0 - h) * inv);
+      if ((int)floorf((z + r - s.bp_z0 - h) * inv) != ck) return nullptr;
+    }
+  }
+  if (ci < 0 || ci >= s.bp_nx || ck < 0 || ck >= s.bp_nz) return nullptr;
+  const BpCell* c = grids + (size_t)g * cells + (size_t)ck * s.bp_nx + ci;
+  return c->count > (uint32_t)kBpCap ? nullptr : c;
+}
+
 // true when c lies inside the lattice box (and is finite).
 __device__ __forceinline__ bool grid_contains(const DScene& s, float cx, float cy, float cz) {
   const float gx = (cx - s.ox) * s.inv_h, gy = (cy - s.oy) * s.inv_h, gz = (cz - s.oz) * s.inv_h;

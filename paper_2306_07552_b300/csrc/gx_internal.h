@@ -38,6 +38,9 @@ struct DScene {
   int nx, ny, nz;
   // column grid: 3 working-set radii x ncz x ncx columns, CSR offsets into
   // the free spans (lo, hi) of a sphere centre's height
+  // object broad-phase lattice (four copies offset by half a cell)
+  float bp_x0, bp_z0;       // corner of the unshifted grid
+  int bp_nx, bp_nz;         // cells per axis of each grid
   const uint32_t* col_off;  // [3 * ncz * ncx + 1]
   const float2* col_spans;
   int ncx, ncz;
@@ -58,6 +61,19 @@ void build_meshlets(const gx_scene_desc& s, HostMeshlets& out);
 struct Robot {
   gx_robot r;
 };
+
+// Object broad-phase (appendix "Additional Collision-Detection Details"):
+// per environment four regular XZ grids, cells kBpCell metres (at least
+// four times the largest query radius), shifted by half a cell in x and/or
+// z; a query sphere lies wholly inside one cell of one of them.  A cell
+// lists up to kBpCap object indices; a fuller cell is tested by brute force.
+constexpr float kBpCell = 0.5f;
+constexpr int kBpCap = 12;
+struct BpCell {
+  uint32_t count;
+  uint8_t id[kBpCap];
+};
+static_assert(sizeof(BpCell) == 16, "broad-phase cell");
 
 // ---------------------------------------------------------------------------
 // State: one device allocation, structure of arrays per field.
@@ -92,6 +108,8 @@ struct PhysicsParams {
   // (x, y, z, radius or -1 when unused) and stops; pass 2 reads the
   // predicted distances and consults the grid only below the margin.
   float4* robot_sph;                    // optional [n][32]: spheres at the accepted pose
+  BpCell* bp;                           // optional [n][4][bp_cells] object broad-phase
+  int bp_cells;                         // cells per grid (the largest scene's)
   int slide;                            // sliding heuristic on
   int place_jitter;                     // object placing heuristic on
   uint64_t seed;                        // Philox key (the reset key)
@@ -113,6 +131,8 @@ enum NsdfCounter {
 };
 
 struct ResetParams {
+  BpCell* bp;          // optional broad-phase, rebuilt for each reset env
+  int bp_cells;
   int n, M;
   const DScene* scenes;
   const int* env_scene;
@@ -172,6 +192,8 @@ enum RasterCounter {
 };
 
 void launch_physics(const PhysicsParams& p, cudaStream_t s);
+void launch_bp_rebuild(const DScene* scenes, const int* env_scene, const StateView& st, int n,
+                       int M, BpCell* bp, int cells, cudaStream_t s);
 void launch_reset(const ResetParams& p, cudaStream_t s);
 cudaError_t reset_configure();
 void launch_raster(const RasterParams& p, cudaStream_t s);

@@ -24,6 +24,9 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kEnvsPerBlock = 4;
+// Philox streams of a reset beyond the objects' 0..GX_MAX_OBJECTS-1
+constexpr uint32_t kRobotStream = GX_MAX_OBJECTS;
+constexpr uint32_t kGoalStream = GX_MAX_OBJECTS + 1;
 
 __device__ __forceinline__ float clampf(float x, float lo, float hi) {
   return fminf(fmaxf(x, lo), hi);
@@ -256,8 +259,15 @@ __global__ void __launch_bounds__(32 * kEnvsPerBlock) physics_kernel(const Physi
     } else {
       cs = !grid_query(S, c[0], c[1], c[2], d) || d < r;
     }
-    for (int j = 0; j < M; ++j) {
-      if (j == held) continue;
+    // free objects: with the broad-phase, only those listed in the cell that
+    // holds this sphere's XZ disk (held objects stay listed and are skipped)
+    const BpCell* cell = P.bp ? bp_cell(P.bp + (size_t)env * 4 * P.bp_cells, P.bp_cells, S, c[0],
+                                        c[2], r)
+                              : nullptr;
+    const int nj = cell ? (int)cell->count : M;
+    for (int t = 0; t < nj; ++t) {
+      const int j = cell ? (int)cell->id[t] : t;
+      if (j == held || j >= M) continue;
       const float4 o = so[j];
       const float dx = c[0] - o.x, dy = c[1] - o.y, dz = c[2] - o.z, rr = r + o.w;
       co |= dx * dx + dy * dy + dz * dz < rr * rr;
@@ -485,6 +495,12 @@ __global__ void __launch_bounds__(32 * kEnvsPerBlock) physics_kernel(const Physi
     __syncwarp();
     if (lane == 0) so[held] = event != 4 ? make_float4(lx, ly, lz, rho)
                                          : make_float4(ppre[0], ppre[1], ppre[2], rho);
+    if (P.bp && event != 4 && lane == 0) {
+      // the object was listed where it rested before the grasp
+      BpCell* grids = P.bp + (size_t)env * 4 * P.bp_cells;
+      bp_remove(grids, P.bp_cells, S, held, ppre[0], ppre[2], rho);
+      bp_insert(grids, P.bp_cells, S, held, lx, lz, rho);
+    }
     nheld = -1;
     coff[0] = coff[1] = coff[2] = 0.f;
   }
@@ -630,6 +646,7 @@ __device__ void sphere_world(const gx_robot& rb, int i, float x, float z, float 
 
 constexpr int kResetThreads = 256;
 constexpr int kTryWindow = 8;  // tries evaluated together before looking further
+static_assert(kResetThreads / 32 == kTryWindow, "one warp per try of a window");
 
 // (a12) masked reset, one CTA per environment: objects on support tops, then
 // the robot base in free space, by rejection sampling with at most 64
@@ -672,52 +689,58 @@ __global__ void __launch_bounds__(kResetThreads) reset_kernel(const ResetParams 
   }
   if (tid == 0) s_robot_try = -1;
   __syncthreads();
-  // 2. objects in order
+  // 2. objects in order; in each window of tries warp w takes try t0 + w and
+  // its lanes split the test against the objects already placed; the lowest
+  // accepted try wins (the same choice as trying them in order); after 64
+  // failed tries the last one stands
   bool failed = false;
-  if (warp == 0) {
-    for (int j = 0; j < M; ++j) {
-      const float rho = s_rho[j];
-      float4 c = lane < kTryWindow ? s_cand[j][lane] : make_float4(0.f, 0.f, 0.f, 0.f);
-      bool ok = c.w > 0.5f;
-      for (int k = 0; k < j && ok; ++k) {
-        const float4 o = so[k];
-        const float dx = c.x - o.x, dy = c.y - o.y, dz = c.z - o.z, rr = rho + o.w;
-        ok = !(dx * dx + dy * dy + dz * dz < rr * rr);
+  for (int j = 0; j < M; ++j) {
+    const float rho = s_rho[j];
+    int pick_t = -1;
+    for (int t0 = 0; t0 < 64 && pick_t < 0; t0 += kTryWindow) {
+      const int t = t0 + warp;
+      float4 c;
+      if (t0 == 0) {
+        c = s_cand[j][warp];
+      } else {
+        const uint4 wv = philox4x32_10(make_uint4((uint32_t)env, ep, (uint32_t)j, (uint32_t)t), key);
+        const float3 p = object_candidate(S, wv, rho, clear);
+        float d;
+        const bool sok = grid_query(S, p.x, p.y, p.z, d) && !(d < rho);
+        c = make_float4(p.x, p.y, p.z, sok ? 1.f : 0.f);
       }
-      unsigned b = __ballot_sync(kFull, ok);
-      int L = b ? __ffs(b) - 1 : -1;
-      float4 pick = make_float4(__shfl_sync(kFull, c.x, L < 0 ? 0 : L),
-                                __shfl_sync(kFull, c.y, L < 0 ? 0 : L),
-                                __shfl_sync(kFull, c.z, L < 0 ? 0 : L), rho);
-      for (int tb = kTryWindow; tb < 64 && L < 0; tb += 32) {
-        const int t = tb + lane;
-        float3 p = make_float3(0.f, 0.f, 0.f);
-        bool ok2 = false;
-        if (t < 64) {
-          const uint4 wv = philox4x32_10(make_uint4((uint32_t)env, ep, (uint32_t)j, (uint32_t)t), key);
-          p = object_candidate(S, wv, rho, clear);
-          float d;
-          ok2 = grid_query(S, p.x, p.y, p.z, d) && !(d < rho);
-          for (int k = 0; k < j && ok2; ++k) {
-            const float4 o = so[k];
-            const float dx = p.x - o.x, dy = p.y - o.y, dz = p.z - o.z, rr = rho + o.w;
-            ok2 = !(dx * dx + dy * dy + dz * dz < rr * rr);
-          }
+      bool hit = false;
+      if (c.w > 0.5f)
+        for (int k = lane; k < j && !hit; k += 32) {
+          const float4 o = so[k];
+          const float dx = c.x - o.x, dy = c.y - o.y, dz = c.z - o.z, rr = rho + o.w;
+          hit = dx * dx + dy * dy + dz * dz < rr * rr;
         }
-        b = __ballot_sync(kFull, ok2);
-        // the last try (63) stands when every try failed
-        const int last = 63 - tb;
-        L = b ? __ffs(b) - 1 : -1;
-        const int src = L >= 0 ? L : (last < 32 ? last : 31);
-        pick = make_float4(__shfl_sync(kFull, p.x, src), __shfl_sync(kFull, p.y, src),
-                           __shfl_sync(kFull, p.z, src), rho);
+      const bool ok = c.w > 0.5f && !__any_sync(kFull, hit);
+      if (lane == 0) s_cand[j][warp] = c;  // this window's candidates, for the pick below
+      if (tid == 0) s_bad = 0u;
+      __syncthreads();
+      if (lane == 0 && ok) atomicOr(&s_bad, 1u << warp);
+      __syncthreads();
+      const unsigned okw = s_bad;
+      if (okw) pick_t = t0 + __ffs(okw) - 1;
+      if (pick_t >= 0 || t0 + kTryWindow >= 64) {
+        const int w = pick_t >= 0 ? pick_t - t0 : kTryWindow - 1;
+        const float4 cc = s_cand[j][w];
+        if (tid == 0) so[j] = make_float4(cc.x, cc.y, cc.z, rho);
       }
-      failed |= L < 0;
-      if (lane == 0) so[j] = pick;
-      __syncwarp();
+      __syncthreads();
     }
+    failed |= pick_t < 0;
   }
   __syncthreads();
+  if (P.bp) {  // the object broad-phase of this environment, rebuilt
+    BpCell* grids = P.bp + (size_t)env * 4 * P.bp_cells;
+    uint4* raw = reinterpret_cast<uint4*>(grids);
+    for (int i = tid; i < 4 * P.bp_cells; i += kResetThreads) raw[i] = make_uint4(0, 0, 0, 0);
+    __syncthreads();
+    for (int j = tid; j < M; j += kResetThreads) bp_insert(grids, P.bp_cells, S, j, so[j].x, so[j].z, so[j].w);
+  }
   // 3. robot base, a window of tries at a time
   float q[7];
 #pragma unroll
@@ -728,7 +751,7 @@ __global__ void __launch_bounds__(kResetThreads) reset_kernel(const ResetParams 
     __syncthreads();
     for (int p = tid; p < kTryWindow * ns; p += kResetThreads) {
       const int tw = p / ns, i = p - tw * ns;
-      const uint4 wv = philox4x32_10(make_uint4((uint32_t)env, ep, 64u, (uint32_t)(t0 + tw)), key);
+      const uint4 wv = philox4x32_10(make_uint4((uint32_t)env, ep, kRobotStream, (uint32_t)(t0 + tw)), key);
       float x, z, yaw;
       robot_try(S, wv, x, z, yaw);
       float cc[3];
@@ -755,7 +778,7 @@ __global__ void __launch_bounds__(kResetThreads) reset_kernel(const ResetParams 
   int t = s_robot_try;
   failed |= t < 0;
   if (t < 0) t = 63;
-  const uint4 wv = philox4x32_10(make_uint4((uint32_t)env, ep, 64u, (uint32_t)t), key);
+  const uint4 wv = philox4x32_10(make_uint4((uint32_t)env, ep, kRobotStream, (uint32_t)t), key);
   float bx, bz, byaw;
   robot_try(S, wv, bx, bz, byaw);
   if (failed && lane == 0) atomicOr(P.err, GX_DEV_PLACEMENT_FAILED);
@@ -772,14 +795,14 @@ __global__ void __launch_bounds__(kResetThreads) reset_kernel(const ResetParams 
   }
   for (int j = lane; j < M; j += 32) P.st.obj[(size_t)env * M + j] = so[j];
   // task: object 0 is the target; its goal lies on a support top, drawn like
-  // an object placement from stream 65 (first draw); previous distances from
+  // an object placement from stream kGoalStream (first draw); previous distances from
   // the episode's first pose, previous joint actions 0
   {
     float task[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) task[k] = 0.f;
     if (M > 0 && S.n_supports > 0) {
-      const uint4 wg = philox4x32_10(make_uint4((uint32_t)env, ep, 65u, 0u), key);
+      const uint4 wg = philox4x32_10(make_uint4((uint32_t)env, ep, kGoalStream, 0u), key);
       const float4 o = so[0];
       const float3 g = object_candidate(S, wg, o.w, rb.rest_clearance);
       task[0] = g.x;
@@ -814,7 +837,36 @@ __global__ void __launch_bounds__(kResetThreads) reset_kernel(const ResetParams 
   }
 }
 
+// Rebuilds every environment's object broad-phase from the state (after a
+// state load): resting objects where they are, a held object where it
+// rested before the grasp.
+__global__ void bp_rebuild_kernel(const DScene* scenes, const int* env_scene, StateView st, int n,
+                                  int M, BpCell* bp, int cells) {
+  const int env = blockIdx.x;
+  if (env >= n) return;
+  const DScene& S = scenes[env_scene[env]];
+  BpCell* grids = bp + (size_t)env * 4 * cells;
+  uint4* raw = reinterpret_cast<uint4*>(grids);
+  for (int i = threadIdx.x; i < 4 * cells; i += blockDim.x) raw[i] = make_uint4(0, 0, 0, 0);
+  __syncthreads();
+  const int held = st.held[env];
+  for (int j = threadIdx.x; j < M; j += blockDim.x) {
+    const float4 o = st.obj[(size_t)env * M + j];
+    float x = o.x, z = o.z;
+    if (j == held) {
+      x = st.ppre[env];
+      z = st.ppre[2 * (size_t)n + env];
+    }
+    bp_insert(grids, cells, S, j, x, z, o.w);
+  }
+}
+
 }  // namespace
+
+void launch_bp_rebuild(const DScene* scenes, const int* env_scene, const StateView& st, int n,
+                       int M, BpCell* bp, int cells, cudaStream_t s) {
+  if (n > 0) bp_rebuild_kernel<<<n, 256, 0, s>>>(scenes, env_scene, st, n, M, bp, cells);
+}
 
 void launch_physics(const PhysicsParams& p, cudaStream_t s) {
   const int blocks = (p.n + kEnvsPerBlock - 1) / kEnvsPerBlock;

@@ -769,7 +769,7 @@ extern "C" gx_status gx_render_noalloc(const gx_scene_set* set, int32_t n,
   if (n < 1 || !env_scene || !cam || !depth || (n_objects > 0 && !obj))
     return set_last_error(GX_EINVAL, "gx_render_noalloc: NULL buffer or n < 1");
   if (n_objects < 0 || n_objects > GX_MAX_OBJECTS)
-    return set_last_error(GX_EINVAL, "gx_render_noalloc: n_objects must be in [0, 64]");
+    return set_last_error(GX_EINVAL, "gx_render_noalloc: n_objects must be in [0, 256]");
   if (img_w < 32 || img_h < 32 || img_w % 32 || img_h % 32)
     return set_last_error(GX_EINVAL, "gx_render_noalloc: image sides must be multiples of 32");
   if (img_w > kNoAllocMaxSide || img_h > kNoAllocMaxSide)

@@ -21,7 +21,7 @@ SO_PATH = os.path.join(_HERE, "libgx.so")
 GX_OK, GX_EINVAL, GX_ENOMEM, GX_ECUDA, GX_EDEVICE, GX_ESTATE = range(6)
 GX_DEV_NONFINITE_ACTION = 0x1
 GX_DEV_PLACEMENT_FAILED = 0x2
-MAX_OBJECTS = 64
+MAX_OBJECTS = 256
 MAX_SPHERES = 31
 
 SYMBOLS = ["gx_scene_set_create", "gx_scene_set_destroy", "gx_create", "gx_destroy", "gx_reset",
@@ -72,8 +72,8 @@ class GxConfig(C.Structure):
                 ("obj_radius_min", C.c_float), ("obj_radius_max", C.c_float),
                 ("seed", C.c_uint64), ("env_scene", i32p), ("raster_regions", C.c_int32),
                 ("small_tri_px", C.c_int32), ("use_graph", C.c_int32), ("profile", C.c_int32),
-                ("sdf_mode", C.c_int32), ("sdf_margin", C.c_float), ("render_robot", C.c_int32),
-                ("heuristics", C.c_int32)]
+                ("sdf_mode", C.c_int32), ("sdf_margin", C.c_float), ("broadphase", C.c_int32),
+                ("render_robot", C.c_int32), ("heuristics", C.c_int32)]
 
 
 OUTPUT_KEYS = ["depth", "rgb", "pose", "obj_pos", "held", "contact_mask", "contact_flags", "event",
@@ -325,7 +325,8 @@ class Sim:
     def __init__(self, scene_set: SceneSet, robot: _inputs.Robot, n_envs: int, img=(128, 128),
                  depth_fp16=False, render_rgb=True, n_objects=40, obj_radius=(0.03, 0.06),
                  seed=1, env_scene=None, raster_regions=0, small_tri_px=0, use_graph=False,
-                 profile=0, sdf_mode=0, sdf_margin=0.02, heuristics=0, render_robot=False):
+                 profile=0, sdf_mode=0, sdf_margin=0.02, heuristics=0, render_robot=False,
+                 broadphase=False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("gx needs a CUDA device; there is no CPU fallback")
@@ -347,6 +348,7 @@ class Sim:
         cfg.sdf_mode, cfg.sdf_margin = int(sdf_mode), float(sdf_margin)
         cfg.heuristics = int(heuristics)
         cfg.render_robot = int(render_robot)
+        cfg.broadphase = int(broadphase)
         self.robot_c = robot_struct(robot)
         self.handle = C.c_void_p()
         _check(lib().gx_create(scene_set.handle, C.byref(self.robot_c), C.byref(cfg),

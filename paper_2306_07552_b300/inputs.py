@@ -549,6 +549,9 @@ WORKLOADS = {
     "apartments4096_nsdf": Workload("apartments4096_nsdf", 4096, 16, "apartment", (20000, 60000),
                                     "uniform", 0.02, 40, (0.03, 0.06), 128, False, True, 500,
                                     "gauss0.5", 200, 0.0, 1000, sdf="neural"),
+    "apartments4096_obj200": Workload("apartments4096_obj200", 4096, 16, "apartment",
+                                      (20000, 60000), "uniform", 0.02, 200, (0.03, 0.06), 128,
+                                      False, True, 500, "gauss0.5", 200, 0.0, 1000),
     "apartments4096_column": Workload("apartments4096_column", 4096, 16, "apartment",
                                       (20000, 60000), "uniform", 0.02, 40, (0.03, 0.06), 128,
                                       False, True, 500, "gauss0.5", 200, 0.0, 1000, sdf="column"),

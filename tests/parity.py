@@ -8,7 +8,7 @@ oracle reports a decision within 1e-4 m of its threshold ("near band"; such
 environments are counted and skipped).  Continuous results must agree within
 1e-5 m / rad.  Images are rendered by the oracle from the GPU's state after
 the step; on pixels the oracle does not flag as ambiguous, coverage and RGB
-must match exactly and depth within 1e-5 relative + 5e-6 m.
+must match exactly and depth within 1e-5 relative + 5e-6 m / |cos|.
 """
 import math
 
@@ -20,8 +20,10 @@ POSE_TOL = 1e-5
 DEPTH_REL = 1e-5
 # FP32 forward kinematics places the camera and the robot's own spheres
 # within the pose error measured in lockstep (<= 2.5e-6 m); a depth can carry
-# both errors, which at the few-centimetre depths of the robot body exceeds
-# 1e-5 relative, so depth also gets an absolute 5e-6 m
+# both, divided by |cos| of the surface it lands on (a shift across a
+# slanted face moves the hit along the ray by shift / |cos|).  At the
+# few-centimetre depths of the robot body that exceeds 1e-5 relative, so
+# depth also gets 5e-6 m / |cos| (|cos| >= 0.05 outside the ambiguous band).
 DEPTH_ABS = 5e-6
 
 
@@ -117,7 +119,8 @@ def check_step(orc, before, after, out, acts, envs, M, tally, step_fn=None):
 
 def check_image(orc, after, out, e, W, H, M, tally, fp16=False):
     st = oracle_state(after, e, M)
-    depth, rgb, amb, win, stats = orc.render(st, W, H)
+    cosv = np.ones((H, W))
+    depth, rgb, amb, win, stats = orc.render(st, W, H, cos_out=cosv)
     gd = out["depth"][e].float().cpu().numpy().astype(np.float64)
     ok = ~amb
     tally.pixels += int(ok.sum())
@@ -142,6 +145,6 @@ def check_image(orc, after, out, e, W, H, M, tally, fp16=False):
         rel = err / depth[cov]
         if rel.size:
             tally.max_depth_rel = max(tally.max_depth_rel, float(rel.max()))
-        assert np.all(err <= DEPTH_REL * depth[cov] + DEPTH_ABS), (
-            e, float((err - DEPTH_REL * depth[cov]).max()))
+        lim = DEPTH_REL * depth[cov] + DEPTH_ABS / np.maximum(cosv[cov], 0.05)
+        assert np.all(err <= lim), (e, float((err - lim).max()))
     return stats

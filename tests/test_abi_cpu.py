@@ -42,7 +42,7 @@ def test_struct_sizes_match_header(tmp_path):
                "gx_outputs": gx.GxOutputs, "gx_train_params": gx.GxTrainParams,
                "gx_tune_result": gx.GxTuneResult}
     fields = {"gx_config": ["seed", "env_scene", "profile", "sdf_mode", "sdf_margin",
-                            "heuristics"],
+                            "broadphase", "render_robot", "heuristics"],
               "gx_outputs": ["event", "reward", "task_obs", "success"],
               "gx_train_params": ["batch", "lr", "seed"]}
     src = ["#include <stdio.h>", "#include <stddef.h>", '#include "gx.h"', "int main(void) {"]

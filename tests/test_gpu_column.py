@@ -19,7 +19,7 @@ def scenes():
     build.build()
     sc = [I.room_scene(1000, 2000), I.apartment_scene(1003, 20000)]
     ss = gx.SceneSet(sc)
-    orcs = [O.Oracle(ROBOT, s, I.icosahedron(), I.object_colors(64)) for s in sc]
+    orcs = [O.Oracle(ROBOT, s, I.icosahedron(), I.object_colors(256)) for s in sc]
     yield gx, sc, ss, orcs
     ss.close()
 

@@ -20,7 +20,7 @@ def room():
     build.build()
     scene = I.room_scene(1000, 2000)
     ss = gx.SceneSet([scene])
-    orc = O.Oracle(ROBOT, scene, I.icosahedron(), I.object_colors(64))
+    orc = O.Oracle(ROBOT, scene, I.icosahedron(), I.object_colors(256))
     yield gx, scene, ss, orc
     ss.close()
 

@@ -60,7 +60,7 @@ def two_rooms():
         P[-1] = 0.3 + 0.2 * k          # output bias: a mix of trusted and checked spheres
         ss.nsdf_set_weights(k, B, P)
         Ps.append(P)
-    orcs = [O.Oracle(ROBOT, sc, I.icosahedron(), I.object_colors(64)) for sc in scenes]
+    orcs = [O.Oracle(ROBOT, sc, I.icosahedron(), I.object_colors(256)) for sc in scenes]
     yield gx, scenes, ss, orcs, B, Ps
     ss.close()
 

@@ -52,7 +52,7 @@ def setup():
     rng = np.random.default_rng(3)
     P0 = P0 + rng.normal(0, 0.02, P0.shape).astype(np.float32)
     ss.nsdf_set_weights(0, B, P0)
-    orc = O.Oracle(I.fetch_like_robot(), scene, I.icosahedron(), I.object_colors(64))
+    orc = O.Oracle(I.fetch_like_robot(), scene, I.icosahedron(), I.object_colors(256))
     yield gx, scene, ss, orc, B, P0
     ss.close()
 

@@ -26,7 +26,7 @@ def room():
     gx = _gx()
     scene = I.room_scene(1000, 2000)
     ss = gx.SceneSet([scene])
-    orc = O.Oracle(ROBOT, scene, I.icosahedron(), I.object_colors(64))
+    orc = O.Oracle(ROBOT, scene, I.icosahedron(), I.object_colors(256))
     yield gx, scene, ss, orc
     ss.close()
 
@@ -256,7 +256,7 @@ def test_apartments_full_size_sampled(apartments):
     sim.reset()
     assert sim.device_error() == 0
     env_scene = I.env_scene_map(n, w.n_scenes)
-    orcs = {s: O.Oracle(ROBOT, scenes[s], I.icosahedron(), I.object_colors(64))
+    orcs = {s: O.Oracle(ROBOT, scenes[s], I.icosahedron(), I.object_colors(256))
             for s in range(w.n_scenes)}
     rng = np.random.default_rng(0)
     acts = I.make_actions(3, n, w.action_dist, seed=w.action_seed)
@@ -303,7 +303,7 @@ def test_uneven_fp16_sampled():
     after = sim.state_arrays()
     tally = Tally()
     for s in (big, small):
-        orc = O.Oracle(ROBOT, scenes[s], I.icosahedron(), I.object_colors(64))
+        orc = O.Oracle(ROBOT, scenes[s], I.icosahedron(), I.object_colors(256))
         envs = np.nonzero(env_scene == s)[0][:32]
         check_step(orc, before, after, out, acts[0], envs, M, tally)
         for e in envs[:3]:
@@ -318,7 +318,7 @@ def test_robot_body_rendering_lockstep(room):
     rendering the same spheres from the state after the step."""
     gx, scene, ss, orc = room
     n, M, W = 16, 10, 64
-    orc_b = O.Oracle(ROBOT, scene, I.icosahedron(), I.object_colors(64),
+    orc_b = O.Oracle(ROBOT, scene, I.icosahedron(), I.object_colors(256),
                      robot_rgb=I.robot_colors(ROBOT))
     sim = gx.Sim(ss, ROBOT, n, img=(W, W), n_objects=M, obj_radius=(0.03, 0.06), seed=1,
                  render_robot=True)
@@ -336,7 +336,7 @@ def test_robot_body_rendering_lockstep(room):
         for e in range(n):
             check_image(orc_b, after, out, e, W, W, M, tally)
             st = oracle_state(after, e, M)
-            robot_px += int((orc_b.render(st, W, W)[3] >= n_tris + 64 * nt).sum())
+            robot_px += int((orc_b.render(st, W, W)[3] >= n_tris + O.MAX_OBJ * nt).sum())
     print(tally, f"robot pixels {robot_px}")
     assert robot_px > 1000
     assert tally.ambiguous < 0.03 * (tally.pixels + tally.ambiguous)

@@ -41,7 +41,7 @@ FLOOR = [-20, -1, -20, 20, 0, 20]   # a floor slab whose top is y = 0
 
 
 def oracle_for(scene, robot=ROBOT):
-    return O.Oracle(robot, scene, I.icosahedron(), I.object_colors(64))
+    return O.Oracle(robot, scene, I.icosahedron(), I.object_colors(256))
 
 
 # ---------------------------------------------------------------- Philox
@@ -553,7 +553,7 @@ def test_near_plane_clips_and_objects_render():
     st = O.Oracle.make_state((0, 0, 0), ROBOT.q_rest, objs=objs)
     depth, rgb, amb, win, _ = orc.render(st, 32, 32)
     centre = rgb[15:17, 15:17]
-    assert np.all(centre == I.object_colors(64)[0])
+    assert np.all(centre == I.object_colors(256)[0])
     assert np.all(depth[depth > 0] >= ROBOT.cam_near)
     # the icosahedron is inscribed in the sphere: its surface lies between the
     # inradius (0.7947 of the circumradius) and the circumradius from the centre
@@ -664,15 +664,15 @@ def test_robot_body_renders_as_instanced_spheres():
     elsewhere are unchanged, and the arm in front of the head camera shows."""
     sc = scene_from_boxes([FLOOR], (-3, -0.3, -3), (3, 2.5, 3), h=0.05)
     rc = I.robot_colors(ROBOT)
-    plain = O.Oracle(ROBOT, sc, I.icosahedron(), I.object_colors(64))
-    body = O.Oracle(ROBOT, sc, I.icosahedron(), I.object_colors(64), robot_rgb=rc)
+    plain = O.Oracle(ROBOT, sc, I.icosahedron(), I.object_colors(256))
+    body = O.Oracle(ROBOT, sc, I.icosahedron(), I.object_colors(256), robot_rgb=rc)
     st = O.Oracle.make_state((0, 0, 0), ROBOT.q_rest)
     d0, c0, a0, w0, _ = plain.render(st, 64, 64)
     d1, c1, a1, w1, _ = body.render(st, 64, 64)
     n_tris, nt = len(sc.tris), len(I.icosahedron()[1])
-    rob = w1 >= n_tris + 64 * nt
+    rob = w1 >= n_tris + O.MAX_OBJ * nt
     assert rob.sum() > 20                                  # the arm is in view
-    sphere = (w1[rob] - n_tris) // nt - 64
+    sphere = (w1[rob] - n_tris) // nt - O.MAX_OBJ
     assert np.array_equal(c1[rob], rc[sphere])
     assert np.all(d1[rob] <= np.where(d0[rob] > 0, d0[rob], np.inf) + 1e-12)
     same = ~rob & ~a0 & ~a1

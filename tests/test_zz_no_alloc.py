@@ -42,7 +42,7 @@ def test_render_noalloc_matches_step_on_two_calls():
     n, M, W = 16, 10, 64
     sim = gx.Sim(ss, ROBOT, n, img=(W, W), n_objects=M, obj_radius=(0.03, 0.06), seed=21)
     sim.reset()
-    orc = O.Oracle(ROBOT, scene, I.icosahedron(), I.object_colors(64))
+    orc = O.Oracle(ROBOT, scene, I.icosahedron(), I.object_colors(256))
     env_scene = torch.zeros(n, dtype=torch.int32, device="cuda")
     depth = torch.empty((n, W, W), dtype=torch.float32, device="cuda")
     rgb = torch.empty((n, W, W, 3), dtype=torch.uint8, device="cuda")
