@@ -53,6 +53,15 @@ class Tally:
         self.max_task_err = 0.0        # reward, task observations and task state
         self.fp16_max_err = 0.0        # FP16 depth: largest |gpu - oracle| (m)
         self.fp16_max_frac = 0.0       # ... as a fraction of its bound
+        self.per_result = {}           # result name -> largest |gpu - oracle|
+
+    def note(self, name, err):
+        err = float(np.max(err)) if np.size(err) else 0.0
+        self.per_result[name] = max(self.per_result.get(name, 0.0), err)
+
+    def report(self):
+        """One line per result: the largest error seen against the oracle."""
+        return "\n".join(f"  {k:<14s} {v:.2e}" for k, v in sorted(self.per_result.items()))
 
     def __repr__(self):
         r = (f"envs={self.envs} near_band={self.near_band} contacts={self.contacts} "
@@ -91,16 +100,21 @@ def check_step(orc, before, after, out, acts, envs, M, tally, step_fn=None):
         assert held[e] == st.held == after["held"][e], (e, held[e], st.held)
         tally.contacts += int(o.contact_mask != 0)
         tally.events[int(o.event)] = tally.events.get(int(o.event), 0) + 1
-        errs = [abs(after["base_x"][e] - st.base[0]), abs(after["base_z"][e] - st.base[1]),
-                ang_diff(after["yaw"][e], st.base[2])]
-        errs += list(np.abs(after["q"][:, e] - np.array(list(st.q))))
-        errs += list(np.abs(pose[e, 11:14] - np.array(list(o.ee))))
+        parts = {"base_xz_m": [abs(after["base_x"][e] - st.base[0]),
+                               abs(after["base_z"][e] - st.base[1])],
+                 "yaw_rad": [ang_diff(after["yaw"][e], st.base[2])],
+                 "joints_rad": np.abs(after["q"][:, e] - np.array(list(st.q))),
+                 "tool_tip_m": np.abs(pose[e, 11:14] - np.array(list(o.ee)))}
         so = O.Oracle.state_objs(st)
-        errs += list(np.abs(after["obj"][e, :M, :4] - so).ravel())
-        errs += list(np.abs(objo[e, :M] - so).ravel())
+        parts["objects_m"] = np.abs(after["obj"][e, :M, :4] - so).ravel()
+        parts["obj_pos_out_m"] = np.abs(objo[e, :M] - so).ravel()
         if st.held >= 0:
-            errs += list(np.abs(after["c_off"][:, e] - np.array(list(st.c_off))))
-            errs += list(np.abs(after["p_pre"][:, e] - np.array(list(st.p_pre))))
+            parts["attach_off_m"] = np.abs(after["c_off"][:, e] - np.array(list(st.c_off)))
+            parts["pre_grasp_m"] = np.abs(after["p_pre"][:, e] - np.array(list(st.p_pre)))
+        errs = []
+        for k, v in parts.items():
+            tally.note(k, v)
+            errs += list(np.ravel(v))
         m = float(max(errs))
         tally.max_pose_err = max(tally.max_pose_err, m)
         assert m <= POSE_TOL, (e, m)
@@ -109,10 +123,14 @@ def check_step(orc, before, after, out, acts, envs, M, tally, step_fn=None):
         if reward is not None:
             # the task epilogue: reward, success and egomotion observations
             assert succ[e] == o.success, (e, succ[e], o.success)
-            terr = [abs(float(reward[e]) - o.reward)] + list(np.abs(tobs[e] - np.array(list(o.task_obs))))
-            terr += list(np.abs(after["task"][e, :15] - np.array(
-                [*st.goal, *st.obj_start, *st.prev_a, st.prev_d, st.prev_e])))
-            m2 = float(max(terr))
+            r_err = abs(float(reward[e]) - o.reward)
+            obs_err = np.abs(tobs[e] - np.array(list(o.task_obs)))
+            ts_err = np.abs(after["task"][e, :15] - np.array(
+                [*st.goal, *st.obj_start, *st.prev_a, st.prev_d, st.prev_e]))
+            tally.note("reward", r_err)
+            tally.note("task_obs", obs_err)
+            tally.note("task_state", ts_err)
+            m2 = float(max([r_err, *obs_err, *ts_err]))
             tally.max_task_err = max(tally.max_task_err, m2)
             assert m2 <= POSE_TOL, (e, m2)
 
@@ -125,17 +143,21 @@ def check_image(orc, after, out, e, W, H, M, tally, fp16=False):
     ok = ~amb
     tally.pixels += int(ok.sum())
     tally.ambiguous += int(amb.sum())
-    assert np.array_equal(gd[ok] > 0, depth[ok] > 0), (e, int(((gd > 0) != (depth > 0))[ok].sum()))
+    cov_bad = int(((gd > 0) != (depth > 0))[ok].sum())
+    tally.note("coverage_mismatch_px", cov_bad)
+    assert cov_bad == 0, (e, cov_bad)
     if out.get("rgb") is not None:
         g = out["rgb"][e].cpu().numpy().astype(np.uint32)
         grgb = (g[..., 0] << 16) | (g[..., 1] << 8) | g[..., 2]
         bad = ok & (grgb != rgb)
+        tally.note("rgb_mismatch_px", int(bad.sum()))
         assert not bad.any(), (e, int(bad.sum()))
     cov = ok & (depth > 0)
     if fp16:
         ulp = np.spacing(depth[cov].astype(np.float16)).astype(np.float64)
         lim = 0.5 * ulp + DEPTH_REL * depth[cov]
         err = np.abs(gd[cov] - depth[cov])
+        tally.note("depth_fp16_m", err)
         if err.size:
             tally.fp16_max_err = max(tally.fp16_max_err, float(err.max()))
             tally.fp16_max_frac = max(tally.fp16_max_frac, float((err / lim).max()))
@@ -143,6 +165,8 @@ def check_image(orc, after, out, e, W, H, M, tally, fp16=False):
     else:
         err = np.abs(gd[cov] - depth[cov])
         rel = err / depth[cov]
+        tally.note("depth_fp32_m", err)
+        tally.note("depth_fp32_rel", rel)
         if rel.size:
             tally.max_depth_rel = max(tally.max_depth_rel, float(rel.max()))
         lim = DEPTH_REL * depth[cov] + DEPTH_ABS / np.maximum(cosv[cov], 0.05)

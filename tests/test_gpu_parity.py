@@ -91,6 +91,7 @@ def test_room16_trajectory_lockstep(room):
     tally = Tally()
     _run_lockstep(sim, orc, acts, M, W, W, lambda t: range(n), tally)
     print(tally)
+    print(tally.report())
     assert tally.envs == 320 and tally.near_band <= 8
     assert tally.ambiguous < 0.03 * (tally.pixels + tally.ambiguous)
     assert sim.device_error() == 0
@@ -129,6 +130,7 @@ def test_grasp_carry_release(room):
     tally = Tally()
     _run_lockstep(sim, orc, acts, M, W, W, lambda t: [0, 5] if t in (0, 5) else [], tally)
     print(tally)
+    print(tally.report())
     assert tally.events.get(1, 0) >= 12
     assert tally.events.get(3, 0) + tally.events.get(4, 0) >= 10
     sim.close()
@@ -275,6 +277,7 @@ def test_apartments_full_size_sampled(apartments):
             for e in envs[:8]:
                 check_image(orcs[int(env_scene[e])], after, out, e, W, W, M, tally)
     print(tally)
+    print(tally.report())
     assert tally.near_band <= 0.05 * tally.envs
     assert tally.ambiguous < 0.05 * (tally.pixels + tally.ambiguous)
     sim.close()
@@ -309,6 +312,7 @@ def test_uneven_fp16_sampled():
         for e in envs[:3]:
             check_image(orc, after, out, int(e), W, W, M, tally, fp16=True)
     print(tally, tris[big], tris[small])
+    print(tally.report())
     sim.close()
     ss.close()
 
@@ -338,6 +342,7 @@ def test_robot_body_rendering_lockstep(room):
             st = oracle_state(after, e, M)
             robot_px += int((orc_b.render(st, W, W)[3] >= n_tris + O.MAX_OBJ * nt).sum())
     print(tally, f"robot pixels {robot_px}")
+    print(tally.report())
     assert robot_px > 1000
     assert tally.ambiguous < 0.03 * (tally.pixels + tally.ambiguous)
     sim.close()
