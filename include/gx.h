@@ -312,6 +312,15 @@ gx_status gx_autotune(gx_ctx* ctx, const float* actions, const gx_outputs* out, 
  * context does not count. */
 gx_status gx_nsdf_counters(gx_ctx* ctx, int64_t out[4]);
 
+/* The network's predictions d^ that the last step's static test used
+ * (sdf_mode 1), copied into the host buffer `host` of n_values = n_envs * 32
+ * floats: [env][slot], slot s < 30 robot sphere s at the candidate pose,
+ * slot 30 the held object; a slot is meaningful only where that sphere was
+ * tested (slot 31 and spheres without a held object are not).  NaN before
+ * the first step.  Waits for the device.  GX_ESTATE when sdf_mode is not 1,
+ * GX_EINVAL on a size mismatch. */
+gx_status gx_nsdf_step_predictions(gx_ctx* ctx, float* host, size_t n_values);
+
 /* ----------------------------------------------------------------------------
  * Neural SDF (not in the paper; the learned stand-in for the distance grid).
  * Per scene, a Fourier-feature MLP

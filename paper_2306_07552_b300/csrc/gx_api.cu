@@ -576,6 +576,7 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
     x->n_nsdf_tiles = (int)tiles.size();
     if ((e = cudaMalloc(&x->d_nsdf_pts, n * 32 * sizeof(float4))) != cudaSuccess ||
         (e = cudaMalloc(&x->d_nsdf_d, n * 32 * sizeof(float))) != cudaSuccess ||
+        (e = cudaMemset(x->d_nsdf_d, 0xff, n * 32 * sizeof(float))) != cudaSuccess ||  // NaN
         (e = cudaMalloc(&x->d_nsdf_tiles, tiles.size() * sizeof(int4))) != cudaSuccess ||
         (e = cudaMalloc(&x->d_nsdf_perm, n * sizeof(int))) != cudaSuccess ||
         (e = cudaMalloc(&x->d_nsdf_blobs, set->n * sizeof(void*))) != cudaSuccess ||
@@ -917,6 +918,16 @@ extern "C" gx_status gx_nsdf_counters(gx_ctx* x, int64_t out[4]) {
   CK(x, cudaMemcpy(h, x->d_nsdf_counters, sizeof(h), cudaMemcpyDeviceToHost));
   CK(x, cudaMemset(x->d_nsdf_counters, 0, sizeof(h)));
   for (int k = 0; k < kNsdfCounters; ++k) out[k] = (int64_t)h[k];
+  return GX_OK;
+}
+
+extern "C" gx_status gx_nsdf_step_predictions(gx_ctx* x, float* host, size_t n_values) {
+  if (!x || !host) return fail(x, GX_EINVAL, "gx_nsdf_step_predictions: bad argument");
+  if (!x->d_nsdf_d) return fail(x, GX_ESTATE, "gx_nsdf_step_predictions: sdf_mode is not 1");
+  if (n_values != (size_t)x->n * 32)
+    return fail(x, GX_EINVAL, "gx_nsdf_step_predictions: n_values must be n_envs * 32");
+  CK(x, cudaDeviceSynchronize());
+  CK(x, cudaMemcpy(host, x->d_nsdf_d, n_values * sizeof(float), cudaMemcpyDeviceToHost));
   return GX_OK;
 }
 

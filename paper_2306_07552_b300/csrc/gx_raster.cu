@@ -145,19 +145,28 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t phas
 __device__ __forceinline__ int floor_div256(int a) { return a >> 8; }
 __device__ __forceinline__ int ceil_div256(int a) { return -((-a) >> 8); }
 
+// Depth test of one fragment: invz = 1/z at the pixel centre, key (~bits(invz) << 32) | id
+// reduced with min into the framebuffer word fbp.
 template <bool kCount>
-__device__ __forceinline__ void frag(const View& vw, int i, int j, float A, float B, float C,
-                                     const Cam& cm, uint32_t id, Cnt& cn) {
+__device__ __forceinline__ void frag_key(const View& vw, unsigned long long* fbp, float invz,
+                                         uint32_t id, Cnt& cn) {
   if (kCount) cn.v[kCntFragments]++;
-  float invz = fmaf(A, (float)i + 0.5f - cm.cx, fmaf(B, (float)j + 0.5f - cm.cy, C));
   invz = fmaxf(invz, 1e-30f);
   const unsigned long long key =
       ((unsigned long long)(~__float_as_uint(invz)) << 32) | (unsigned long long)id;
   // fire-and-forget reduction in L2, the slot marked to stay resident there
-  asm volatile("red.relaxed.gpu.global.min.L2::cache_hint.u64 [%0], %1, %2;" ::"l"(
-                   vw.fb + j * vw.W + i),
+  asm volatile("red.relaxed.gpu.global.min.L2::cache_hint.u64 [%0], %1, %2;" ::"l"(fbp),
                "l"(key), "l"(vw.pol)
                : "memory");
+}
+
+// Pixel (i, j): the plane A u + B v + C at the pixel centre's offset from the
+// principal point.
+template <bool kCount>
+__device__ __forceinline__ void frag(const View& vw, int i, int j, float A, float B, float C,
+                                     const Cam& cm, uint32_t id, Cnt& cn) {
+  frag_key<kCount>(vw, vw.fb + j * vw.W + i,
+                   fmaf(A, (float)i + 0.5f - cm.cx, fmaf(B, (float)j + 0.5f - cm.cy, C)), id, cn);
 }
 
 // Bounding sphere (world centre c, radius r) vs the view frustum.
@@ -183,10 +192,11 @@ __device__ __forceinline__ void depth_plane(const Cam& cm, float nx, float ny, f
   const float ncx = cm.rx * nx + cm.ry * ny + cm.rz * nz;
   const float ncy = cm.ux * nx + cm.uy * ny + cm.uz * nz;
   const float ncz = cm.fx * nx + cm.fy * ny + cm.fz * nz;
-  const float ih = 1.0f / h;
-  A = ncx * ih / cm.f;
-  B = -ncy * ih / cm.f;
-  C = ncz * ih;
+  // one reciprocal: 1/z = (ncx u - ncy v) / (h f) + ncz / h at pixel offset (u, v)
+  const float s = __frcp_rn(h * cm.f);
+  A = ncx * s;
+  B = -ncy * s;
+  C = (ncz * cm.f) * s;
 }
 
 __device__ __forceinline__ int2 project_fix(const Cam& cm, float xc, float yc, float zc) {
@@ -450,10 +460,15 @@ __device__ void raster_cluster(const View& vw, const Cam& cm, WarpSmem& ws, int 
         const int e1 = q.e[1] + x * q.sx[1] + y * q.sy[1];
         const int e2 = q.e[2] + x * q.sx[2] + y * q.sy[2];
         const int i = (q.ixy & 0xffff) + x, j = (q.ixy >> 16) + y;
+        // the run's plane terms once: u + k is exact, so each fragment gets the
+        // same value as frag() at (i + k, j)
+        const float u0 = (float)i + 0.5f - cm.cx;
+        const float row = fmaf(q.B, (float)j + 0.5f - cm.cy, q.C);
+        unsigned long long* fbp = vw.fb + j * vw.W + i;
 #pragma unroll
         for (int u = 0; u < kSpan; ++u)
           if (x + u < bw && ((e0 + u * q.sx[0]) | (e1 + u * q.sx[1]) | (e2 + u * q.sx[2])) >= 0)
-            frag<kCount>(vw, i + u, j, q.A, q.B, q.C, cm, q.id, cn);
+            frag_key<kCount>(vw, fbp + u, fmaf(q.A, u0 + (float)u, row), q.id, cn);
       }
     }
     __syncwarp();
@@ -651,7 +666,7 @@ __global__ void __launch_bounds__(kThreads, kRasterMinBlocks) raster_kernel(cons
         col[k] = 0u;
         if (keys[k] != ~0ull) {
           const float invz = __uint_as_float(~(uint32_t)(keys[k] >> 32));
-          z[k] = 1.0f / invz;
+          z[k] = __frcp_rn(invz);
           const uint32_t id = (uint32_t)keys[k];
           col[k] = id < (uint32_t)S.n_tris ? __ldg(S.tri_rgb + id)
                                            : __ldg(P.obj_rgb + (id - (uint32_t)S.n_tris) / P.omesh_nt);

@@ -28,9 +28,10 @@ SYMBOLS = ["gx_scene_set_create", "gx_scene_set_destroy", "gx_create", "gx_destr
            "gx_step", "gx_step_host", "gx_sync", "gx_device_error", "gx_state_bytes",
            "gx_save_state", "gx_load_state", "gx_state_layout", "gx_phase_times",
            "gx_raster_counters", "gx_render_noalloc", "gx_nsdf_set_weights",
-           "gx_nsdf_get_weights", "gx_nsdf_query", "gx_nsdf_get_master", "gx_nsdf_samples", "gx_nsdf_grad",
-           "gx_nsdf_train", "gx_nsdf_counters", "gx_autotune", "gx_column_info", "gx_column_spans", "gx_device_outputs",
-           "gx_last_error"]
+           "gx_nsdf_get_weights", "gx_nsdf_query", "gx_nsdf_get_master", "gx_nsdf_samples",
+           "gx_nsdf_grad",
+           "gx_nsdf_train", "gx_nsdf_counters", "gx_nsdf_step_predictions", "gx_autotune",
+           "gx_column_info", "gx_column_spans", "gx_device_outputs", "gx_last_error"]
 NSDF_PARAMS = 57985
 NSDF_FREQ = 32
 RASTER_COUNTERS = ["clusters_tested", "clusters_drawn", "tris_seen", "tris_front", "tris_expand",
@@ -143,6 +144,7 @@ def lib():
         L.gx_nsdf_grad.argtypes = [vp, C.c_int32, vp, vp, C.c_int32, C.c_float, C.c_float, vp, vp,
                                    vp]
         L.gx_nsdf_counters.argtypes = [vp, C.POINTER(C.c_int64)]
+        L.gx_nsdf_step_predictions.argtypes = [vp, C.POINTER(C.c_float), C.c_size_t]
         L.gx_device_outputs.argtypes = [vp, P(GxOutputs)]
         L.gx_column_info.argtypes = [vp, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_uint64)]
         L.gx_column_spans.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, vp, C.c_int32]
@@ -448,6 +450,14 @@ class Sim:
         v = (C.c_int64 * 4)()
         _check(lib().gx_nsdf_counters(self.handle, v), self.handle)
         return dict(zip(["tests", "grid_fallbacks", "disagree", "env_disagree"], list(v)))
+
+    def nsdf_step_predictions(self):
+        """The network's predictions the last step's static test used, [n][32]
+        (sdf_mode 1; slot s < 30 robot sphere s, 30 the held object)."""
+        out = np.empty((self.n, 32), np.float32)
+        _check(lib().gx_nsdf_step_predictions(
+            self.handle, out.ctypes.data_as(C.POINTER(C.c_float)), out.size), self.handle)
+        return out
 
     def sync(self):
         _check(lib().gx_sync(self.handle), self.handle)

@@ -1,0 +1,144 @@
+"""The full-stack workload at full size against the FP64 oracle: 16384 envs
+over 64 apartments with log-uniform 5k-150k triangles, the neural SDF in the
+step (2 cm margin), FP16 depth + RGB8, Bernoulli(0.005) per-env resets and the
+graph-replayed step, in the launch configuration the bench times.
+
+Sampled checks, every step: the masked reset of the sampled envs that reset
+(against the oracle's reset from the state before it), physics in lockstep on
+envs of the largest, the median and the smallest scene (the oracle's rule
+takes the predictions the GPU's step used, which are themselves checked against
+the oracle's FP64 MLP in BF16-operand mode), and images of a few of them."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2306_07552_b300 import inputs as I
+from tests.parity import Tally, check_image, check_step, oracle_state
+from tests.test_gpu_nsdf_step import NEAR_BAND, grid_centre, network_errors, oracle_mlp
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+ROBOT = I.fetch_like_robot()
+
+
+def check_reset(orc, s0, s1, e, M, seed, rho):
+    """Env e reset between state s0 and s1: the oracle's reset from s0."""
+    st = oracle_state(s0, e, M)
+    r = orc.reset(st, seed, e, M, rho[0], rho[1])
+    if r.near_band:
+        return False
+    assert s1["episode"][e] == st.episode
+    assert s1["held"][e] == -1 and s1["step"][e] == 0
+    assert np.allclose(s1["obj"][e, :M], O.Oracle.state_objs(st), atol=1e-5)
+    assert abs(s1["base_x"][e] - st.base[0]) < 1e-5 and abs(s1["base_z"][e] - st.base[1]) < 1e-5
+    d = (s1["yaw"][e] - st.base[2]) % (2 * math.pi)
+    assert min(d, 2 * math.pi - d) < 1e-5
+    assert np.array_equal(s1["q"][:, e], np.asarray(ROBOT.q_rest, np.float32))
+    want = [*st.goal, *st.obj_start, *st.prev_a, st.prev_d, st.prev_e]
+    assert np.allclose(s1["task"][e, :15], want, atol=1e-5), (e, s1["task"][e], want)
+    return True
+
+
+def test_full_stack_16384_sampled():
+    from paper_2306_07552_b300 import build, gx
+    build.build()
+    w = I.WORKLOADS["uneven16384_nsdf"]
+    scenes = I.make_scenes(w)
+    ss = gx.SceneSet(scenes)
+    n, M, W = w.n_envs, w.n_objects, w.img
+    B = I.fourier_matrix(7)
+    Ps = []
+    for s in range(w.n_scenes):
+        P = I.nsdf_init(100 + s)
+        P[-1] = 0.3            # output bias: a mix of trusted and grid-checked spheres
+        ss.nsdf_set_weights(s, B, P)
+        Ps.append(P)
+    sim = gx.Sim(ss, ROBOT, n, img=(W, W), depth_fp16=True, render_rgb=True, n_objects=M,
+                 obj_radius=w.obj_radius, seed=w.reset_seed, use_graph=True, sdf_mode=1,
+                 sdf_margin=w.sdf_margin)
+    sim.reset()
+    assert sim.device_error() == 0
+
+    env_scene = I.env_scene_map(n, w.n_scenes)
+    tris = np.array([sc.n_tris for sc in scenes])
+    order = np.argsort(tris)
+    checked = [int(order[-1]), int(order[len(order) // 2]), int(order[0])]
+    orcs = {s: O.Oracle(ROBOT, scenes[s], I.icosahedron(), I.object_colors(256)) for s in checked}
+    mlps = {s: oracle_mlp(B, Ps[s]) for s in checked}
+    cents = {s: grid_centre(scenes[s]) for s in checked}
+    sample = {s: np.nonzero(env_scene == s)[0][:48] for s in checked}
+
+    T = 3
+    rng = np.random.default_rng(w.reset_seed)
+    masks = (rng.random((T, n)) < w.reset_prob).astype(np.uint8)
+    for s in checked:
+        masks[1, sample[s][:16]] = 1           # sampled envs reset mid-run
+    acts = I.make_actions(T, n, w.action_dist, seed=w.action_seed)
+    tally = Tally()
+    resets = reset_nb = 0
+    trusted = asked = 0
+    stream = torch.cuda.Stream()
+    abuf = torch.empty((n, 11), dtype=torch.float32, device="cuda")   # fixed graph inputs
+    mbuf = torch.empty((n,), dtype=torch.uint8, device="cuda")
+
+    errs, refs = [], []
+
+    def step_fn_for(s, pred):
+        def f(st, action, env):
+            nonlocal trusted, asked
+            c, r, act = orcs[s].candidate_spheres(st, action)
+            d = np.full(31, -1e9)
+            idx = np.flatnonzero(act)
+            d[idx] = pred[env, idx]
+            assert np.all(np.isfinite(d[idx])), env
+            ref = mlps[s].forward(c[idx] - cents[s])
+            errs.append(np.abs(d[idx] - ref))
+            refs.append(ref)
+            ok = d[idx] - r[idx] >= w.sdf_margin
+            trusted += int(ok.sum())
+            asked += int((~ok).sum())
+            return orcs[s].step_nsdf(st, action, d, w.sdf_margin, NEAR_BAND)
+        return f
+
+    for t in range(T):
+        s0 = {k: v.copy() for k, v in sim.state_arrays().items()}
+        with torch.cuda.stream(stream):
+            mbuf.copy_(torch.from_numpy(masks[t]))
+            sim.reset(mbuf, stream=stream)
+        torch.cuda.synchronize()
+        s1 = {k: v.copy() for k, v in sim.state_arrays().items()}
+        for s in checked:
+            for e in sample[s]:
+                if masks[t, e]:
+                    resets += 1
+                    reset_nb += 0 if check_reset(orcs[s], s0, s1, int(e), M, w.reset_seed,
+                                                 w.obj_radius) else 1
+        with torch.cuda.stream(stream):
+            abuf.copy_(torch.from_numpy(acts[t]))
+            out = sim.step(abuf, stream=stream)
+        torch.cuda.synchronize()
+        s2 = sim.state_arrays()
+        pred = sim.nsdf_step_predictions().astype(np.float64)
+        for s in checked:
+            check_step(orcs[s], s1, s2, out, acts[t], sample[s], M, tally,
+                       step_fn=step_fn_for(s, pred))
+            if t == T - 1:
+                for e in sample[s][:3]:
+                    check_image(orcs[s], s2, out, int(e), W, W, M, tally, fp16=True)
+    print(tally, f"resets checked {resets - reset_nb} (near band {reset_nb}), "
+          f"static tests trusting the network {trusted}, asking the grid {asked}",
+          "scenes", [int(tris[s]) for s in checked])
+    print(tally.report())
+    network_errors(errs, refs)
+    # a reset takes hundreds of decisions (64-try rejection loops for 40 objects
+    # and the base); a quarter or so of them have one inside the near band
+    assert resets >= 48 and resets - reset_nb >= resets // 2
+    assert tally.envs - tally.near_band >= 0.9 * tally.envs
+    assert trusted > 0 and asked > 0               # both branches of the rule exercised
+    assert tally.ambiguous < 0.05 * (tally.pixels + tally.ambiguous)
+    assert sim.device_error() == 0
+    sim.close()
+    ss.close()

@@ -73,6 +73,25 @@ def test_query_matches_oracle(nsdf_scene):
     assert err.max() < 2e-2 * (1 + np.abs(ref).mean())
 
 
+def test_query_is_deterministic(nsdf_scene):
+    """Same points, same bits: several launches, and the points in another
+    order (tiles are independent, so a row's value cannot depend on them)."""
+    gx, scene, ss = nsdf_scene
+    n = 5 * 128 + 3
+    pts = torch.from_numpy(_points(scene, n, 12)).cuda()
+    outs = []
+    for _ in range(3):
+        o = torch.empty(n, dtype=torch.float32, device="cuda")
+        ss.nsdf_query(0, pts, o)
+        outs.append(o)
+    perm = torch.randperm(n, generator=torch.Generator().manual_seed(0)).cuda()
+    o = torch.empty(n, dtype=torch.float32, device="cuda")
+    ss.nsdf_query(0, pts[perm].contiguous(), o)
+    torch.cuda.synchronize()
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+    assert torch.equal(outs[0][perm], o)
+
+
 def test_weights_round_trip_bf16(nsdf_scene):
     gx, scene, ss = nsdf_scene
     B, P, c = ss.nsdf_get_weights(0)

@@ -2,12 +2,13 @@
 
 The oracle applies the same rule (orc_step_nsdf): outside the lattice box is
 contact, a predicted clearance d - r of at least the margin is free, else the
-grid decides.  It computes the prediction itself with its FP64 MLP in the
-BF16-operand mode, from weights this test draws and rounds to BF16 with
-PyTorch.  The GPU's prediction differs from the oracle's by FP32 summation
-(~1e-7) and, for ~1% of queries, by a BF16 rounding flip of one hidden value
-(up to ~3e-3 m at these weights); decisions whose predicted clearance lies
-within 3e-3 m of the margin are therefore near band (counted, not compared).
+grid decides.  The check is split in two.  The rule: the oracle takes the
+predictions the GPU's step used (gx_nsdf_step_predictions) and must reach the
+same decisions, near band 1e-4 m as everywhere.  The network: those
+predictions against the oracle's FP64 MLP in the BF16-operand mode at the
+oracle's own sphere centres (weights drawn here, rounded to BF16 with
+PyTorch), within the query tolerance (FP32 sums ~1e-7; a BF16 rounding flip
+of one hidden value moves a prediction by up to ~1e-2 m at random weights).
 """
 import numpy as np
 import pytest
@@ -21,7 +22,18 @@ pytestmark = pytest.mark.gpu
 
 ROBOT = I.fetch_like_robot()
 MARGIN = 0.02
-RULE_BAND = 3e-3
+NEAR_BAND = 1e-4
+
+
+def network_errors(errs, refs):
+    """Prediction error of the step's network against the oracle MLP: the
+    query tolerance (median and max)."""
+    err, ref = np.concatenate(errs), np.concatenate(refs)
+    scale = 1 + np.abs(ref).mean()
+    print(f"step predictions vs oracle MLP: median {np.median(err):.2e}, "
+          f"p99 {np.quantile(err, .99):.2e}, max {err.max():.2e} over {err.size}")
+    assert np.median(err) < 1e-5 * scale
+    assert err.max() < 2e-2 * scale
 
 
 def _bf16(a):
@@ -88,6 +100,33 @@ def test_huge_margin_reproduces_the_grid_step(two_rooms):
     b.close()
 
 
+def test_neural_step_is_deterministic(two_rooms):
+    """Two contexts in neural mode, one replaying a CUDA graph: identical
+    results step after step."""
+    gx, scenes, ss, orcs, B, Ps = two_rooms
+    n, M = 96, 12
+    es = np.arange(n) % 2
+    kw = dict(img=(64, 64), n_objects=M, seed=3, env_scene=es, sdf_mode=1, sdf_margin=MARGIN)
+    a = gx.Sim(ss, ROBOT, n, **kw)
+    b = gx.Sim(ss, ROBOT, n, use_graph=True, **kw)
+    a.reset()
+    b.reset()
+    acts = I.make_actions(20, n, "gaussian", seed=4)
+    stream = torch.cuda.Stream()
+    x = torch.empty((n, 11), dtype=torch.float32, device="cuda")
+    for t in range(20):
+        with torch.cuda.stream(stream):
+            x.copy_(torch.from_numpy(acts[t]))
+            oa, ob = a.step(x, stream=stream), b.step(x, stream=stream)
+        torch.cuda.synchronize()
+        for k in ["depth", "rgb", "pose", "obj_pos", "held", "contact_mask", "contact_flags",
+                  "event", "reward"]:
+            assert torch.equal(oa[k], ob[k]), (t, k)
+        assert np.array_equal(a.nsdf_step_predictions(), b.nsdf_step_predictions(), equal_nan=True)
+    a.close()
+    b.close()
+
+
 def test_neural_rule_matches_oracle(two_rooms):
     gx, scenes, ss, orcs, B, Ps = two_rooms
     n, M, T = 64, 12, 30
@@ -100,16 +139,21 @@ def test_neural_rule_matches_oracle(two_rooms):
     acts = I.make_actions(T, n, "gaussian", seed=6)
     tallies = [Tally(), Tally()]
     trusted = 0
+    errs, refs = [], []
 
-    def step_fn_for(k):
+    def step_fn_for(k, pred):
         def f(st, action, env):
             nonlocal trusted
             c, r, act = orcs[k].candidate_spheres(st, action)
             d = np.full(31, -1e9)
             idx = np.flatnonzero(act)
-            d[idx] = mlps[k].forward(c[idx] - cents[k])
+            d[idx] = pred[env, idx]
+            assert np.all(np.isfinite(d[idx])), env
+            ref = mlps[k].forward(c[idx] - cents[k])
+            errs.append(np.abs(d[idx] - ref))
+            refs.append(ref)
             trusted += int(np.sum(d[idx] - r[idx] >= MARGIN))
-            return orcs[k].step_nsdf(st, action, d, MARGIN, RULE_BAND)
+            return orcs[k].step_nsdf(st, action, d, MARGIN, NEAR_BAND)
         return f
 
     for t in range(T):
@@ -117,13 +161,15 @@ def test_neural_rule_matches_oracle(two_rooms):
         out = sim.step(torch.from_numpy(acts[t]).cuda())
         torch.cuda.synchronize()
         after = sim.state_arrays()
+        pred = sim.nsdf_step_predictions().astype(np.float64)
         for k in range(2):
             check_step(orcs[k], before, after, out, acts[t], np.flatnonzero(es == k), M,
-                       tallies[k], step_fn=step_fn_for(k))
+                       tallies[k], step_fn=step_fn_for(k, pred))
     cnt = sim.nsdf_counters()
     print(tallies, f"trusted predictions {trusted}", cnt)
+    network_errors(errs, refs)
     checked = sum(tl.envs - tl.near_band for tl in tallies)
-    assert checked >= 0.8 * n * T
+    assert checked >= 0.9 * n * T
     assert trusted > 0 and cnt["grid_fallbacks"] > 0     # both branches exercised
     assert cnt["tests"] >= n * T * 30
     sim.close()
