@@ -163,7 +163,7 @@ struct RasterParams {
   const float4* omesh_v;   // [nv] unit instance mesh
   const uint32_t* omesh_t; // [nt] packed
   int omesh_nv, omesh_nt;
-  const uint32_t* obj_rgb; // [64 objects + 32 robot spheres]
+  const uint32_t* obj_rgb; // [GX_MAX_OBJECTS objects + 32 robot spheres]
   const float4* robot_sph; // optional [n][32] robot sphere centre, radius (0: unused)
   float near_;
   void* depth;

@@ -6,17 +6,17 @@
 // once) pulls environments from a work counter.  Each CTA owns one
 // framebuffer slot in global memory (L2-resident: slots x W x H x 8 bytes)
 // of 64-bit keys
-//     key = (~bits(1/z) << 32) | triangle id,
+//     key = (~bits(1/z) << 32) | colour (0xRRGGBB of the triangle),
 // updated with fire-and-forget atomicMin reductions, so the nearest fragment
-// wins and exact depth ties go to the lower triangle id, independently of
-// visiting order.  The resolve of an environment reads its slot, writes the
+// wins and exact depth ties go to the lower colour value, independently of
+// visiting order; the resolve needs no lookup for the colour.  The resolve of an environment reads its slot, writes the
 // observation rows and resets the slot for the CTA's next environment.
 //
 // Per environment, inside a CTA:
 //   1. each warp grabs 32 triangle clusters (meshlets) at a time, culls them
 //      lane-parallel against the view frustum and the cluster normal cone
 //      (whole clusters facing away), and keeps the survivors;
-//   2. lane 0 stages each surviving cluster's vertices and triangles into the
+//   2. lane 0 stages each surviving cluster's vertices, triangles and colours into the
 //      warp's shared buffers with bulk asynchronous copies (cp.async.bulk +
 //      mbarrier), double-buffered so the next cluster streams in while the
 //      current one is rasterised; warps never wait for each other until the
@@ -32,7 +32,7 @@
 //      start.  Huge or near-plane-clipped triangles are scanned by the warp
 //      with int64 edge functions, 8x4 blocks first rejected against edges;
 //   5. free objects are instanced icosahedra built in the same buffers;
-//   6. resolve: depth = 1 / (1/z), colour by triangle id, 16-byte row-major
+//   6. resolve: depth = 1 / (1/z), colour from the key, 16-byte row-major
 //      stores into the batched observation buffers.
 //
 // Every wait is bounded: a wait that gives up sets an error bit and the warp
@@ -62,7 +62,7 @@ struct __align__(16) ExpTri {
   int sx[3];      // edge increments per pixel step in x
   int bw;         // bounding-box width in pixels
   int sy[3];      // edge increments per pixel step in y
-  uint32_t id;
+  uint32_t rgb;   // colour, the key's low word
   float A, B, C;  // 1/z plane
   int off;        // first expansion slot of this round
   float inv_bp;   // 1 / pairs per row
@@ -73,6 +73,7 @@ struct __align__(16) WarpSmem {
   float4 vbuf[2][kMeshletMaxVerts];     // staged world-space vertices
   ExpTri q[32];                         // expansion queue of one round
   uint32_t tbuf[2][kMeshletMaxTris];    // staged packed triangles
+  uint32_t cbuf[2][kMeshletMaxTris];    // their colours, 0xRRGGBB
   int2 vfix[kMeshletMaxVerts];          // snapped screen coordinates (1/256 px)
   float vz[kMeshletMaxVerts];           // camera-space depth
   uint8_t voc[kMeshletMaxVerts];        // frustum outcode
@@ -145,15 +146,15 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t phas
 __device__ __forceinline__ int floor_div256(int a) { return a >> 8; }
 __device__ __forceinline__ int ceil_div256(int a) { return -((-a) >> 8); }
 
-// Depth test of one fragment: invz = 1/z at the pixel centre, key (~bits(invz) << 32) | id
+// Depth test of one fragment: invz = 1/z at the pixel centre, key (~bits(invz) << 32) | rgb
 // reduced with min into the framebuffer word fbp.
 template <bool kCount>
 __device__ __forceinline__ void frag_key(const View& vw, unsigned long long* fbp, float invz,
-                                         uint32_t id, Cnt& cn) {
+                                         uint32_t rgb, Cnt& cn) {
   if (kCount) cn.v[kCntFragments]++;
   invz = fmaxf(invz, 1e-30f);
   const unsigned long long key =
-      ((unsigned long long)(~__float_as_uint(invz)) << 32) | (unsigned long long)id;
+      ((unsigned long long)(~__float_as_uint(invz)) << 32) | (unsigned long long)rgb;
   // fire-and-forget reduction in L2, the slot marked to stay resident there
   asm volatile("red.relaxed.gpu.global.min.L2::cache_hint.u64 [%0], %1, %2;" ::"l"(fbp),
                "l"(key), "l"(vw.pol)
@@ -164,9 +165,9 @@ __device__ __forceinline__ void frag_key(const View& vw, unsigned long long* fbp
 // principal point.
 template <bool kCount>
 __device__ __forceinline__ void frag(const View& vw, int i, int j, float A, float B, float C,
-                                     const Cam& cm, uint32_t id, Cnt& cn) {
+                                     const Cam& cm, uint32_t rgb, Cnt& cn) {
   frag_key<kCount>(vw, vw.fb + j * vw.W + i,
-                   fmaf(A, (float)i + 0.5f - cm.cx, fmaf(B, (float)j + 0.5f - cm.cy, C)), id, cn);
+                   fmaf(A, (float)i + 0.5f - cm.cx, fmaf(B, (float)j + 0.5f - cm.cy, C)), rgb, cn);
 }
 
 // Bounding sphere (world centre c, radius r) vs the view frustum.
@@ -215,7 +216,7 @@ __device__ __forceinline__ bool top_left(int dx, int dy) { return dy < 0 || (dy 
 // scanned, one pixel per lane.
 template <bool kCount>
 __device__ void raster_warp_tri(const View& vw, const Cam& cm, int2 V0, int2 V1, int2 V2, float A,
-                                float B, float C, uint32_t id, int lane, Cnt& cn) {
+                                float B, float C, uint32_t rgb, int lane, Cnt& cn) {
   const long long area =
       (long long)(V1.x - V0.x) * (V2.y - V0.y) - (long long)(V2.x - V0.x) * (V1.y - V0.y);
   if (area == 0) return;
@@ -269,7 +270,7 @@ __device__ void raster_warp_tri(const View& vw, const Cam& cm, int2 V0, int2 V1,
 #pragma unroll
       for (int k = 0; k < 3; ++k)
         in &= (long long)dx[k] * (py - V[k].y) - (long long)dy[k] * (px - V[k].x) + b[k] >= 0;
-      if (in) frag<kCount>(vw, i, j, A, B, C, cm, id, cn);
+      if (in) frag<kCount>(vw, i, j, A, B, C, cm, rgb, cn);
     }
   }
 }
@@ -279,7 +280,7 @@ __device__ void raster_warp_tri(const View& vw, const Cam& cm, int2 V0, int2 V1,
 // warp scans the (one or two) resulting triangles.
 template <bool kCount>
 __device__ void raster_big(const View& vw, const Cam& cm, const WarpSmem& ws, int buf,
-                           uint32_t packed, uint32_t id, int lane, Cnt& cn) {
+                           uint32_t packed, uint32_t rgb, int lane, Cnt& cn) {
   if (kCount && lane == 0) cn.v[kCntTrisBig]++;
   const int idx[3] = {(int)(packed & 0xff), (int)((packed >> 8) & 0xff), (int)((packed >> 16) & 0xff)};
   const float4 P0 = ws.vbuf[buf][idx[0]], P1 = ws.vbuf[buf][idx[1]], P2 = ws.vbuf[buf][idx[2]];
@@ -314,15 +315,15 @@ __device__ void raster_big(const View& vw, const Cam& cm, const WarpSmem& ws, in
       poly[m++] = project_fix(cm, fmaf(t, b.x - a.x, a.x), fmaf(t, b.y - a.y, a.y), cm.near_);
     }
   }
-  if (m >= 3) raster_warp_tri<kCount>(vw, cm, poly[0], poly[1], poly[2], A, B, C, id, lane, cn);
-  if (m == 4) raster_warp_tri<kCount>(vw, cm, poly[0], poly[2], poly[3], A, B, C, id, lane, cn);
+  if (m >= 3) raster_warp_tri<kCount>(vw, cm, poly[0], poly[1], poly[2], A, B, C, rgb, lane, cn);
+  if (m == 4) raster_warp_tri<kCount>(vw, cm, poly[0], poly[2], poly[3], A, B, C, rgb, lane, cn);
 }
 
-// Rasterises the cluster staged in buffer `buf` (nv vertices, nt triangles,
-// triangle ids id0 + t).
+// Rasterises the cluster staged in buffer `buf` (nv vertices, nt triangles
+// with their colours).
 template <bool kCount>
 __device__ void raster_cluster(const View& vw, const Cam& cm, WarpSmem& ws, int buf, int nv, int nt,
-                               uint32_t id0, int big_px, int lane, Cnt& cn) {
+                               int big_px, int lane, Cnt& cn) {
   if (kCount && lane == 0) cn.v[kCntClustersDrawn]++;
   for (int k = lane; k < nv; k += 32) {
     const float4 P = ws.vbuf[buf][k];
@@ -402,7 +403,7 @@ __device__ void raster_cluster(const View& vw, const Cam& cm, WarpSmem& ws, int 
                   r.A = A;
                   r.B = B;
                   r.C = C;
-                  r.id = id0 + t;
+                  r.rgb = ws.cbuf[buf][t];
                   npx = ((bw + kSpan - 1) / kSpan) * bh;  // expansion slots: pixel runs
                   if (kCount) {
                     cn.v[kCntTrisSmall]++;
@@ -468,7 +469,7 @@ __device__ void raster_cluster(const View& vw, const Cam& cm, WarpSmem& ws, int 
 #pragma unroll
         for (int u = 0; u < kSpan; ++u)
           if (x + u < bw && ((e0 + u * q.sx[0]) | (e1 + u * q.sx[1]) | (e2 + u * q.sx[2])) >= 0)
-            frag_key<kCount>(vw, fbp + u, fmaf(q.A, u0 + (float)u, row), q.id, cn);
+            frag_key<kCount>(vw, fbp + u, fmaf(q.A, u0 + (float)u, row), q.rgb, cn);
       }
     }
     __syncwarp();
@@ -477,7 +478,7 @@ __device__ void raster_cluster(const View& vw, const Cam& cm, WarpSmem& ws, int 
       const int L = __ffs(bm) - 1;
       bm &= bm - 1;
       const uint32_t pk = __shfl_sync(kFull, packed, L);
-      raster_big<kCount>(vw, cm, ws, buf, pk, id0 + tb + L, lane, cn);
+      raster_big<kCount>(vw, cm, ws, buf, pk, ws.cbuf[buf][tb + L], lane, cn);
     }
   }
   __syncwarp();
@@ -487,9 +488,10 @@ __device__ __forceinline__ void issue_cluster(WarpSmem& ws, int buf, const DScen
   const uint32_t voff = e.x & 0xffffffu, nv = e.x >> 24;
   const uint32_t toff = e.y & 0xffffffu, nt = e.y >> 24;
   const uint32_t tbytes = ((nt + 3u) & ~3u) * 4u;
-  mbar_expect_tx(&ws.bar[buf], nv * 16u + tbytes);
+  mbar_expect_tx(&ws.bar[buf], nv * 16u + 2u * tbytes);
   bulk_g2s(ws.vbuf[buf], S.mverts + voff, nv * 16u, &ws.bar[buf]);
   bulk_g2s(ws.tbuf[buf], S.mtris + toff, tbytes, &ws.bar[buf]);
+  bulk_g2s(ws.cbuf[buf], S.tri_rgb + toff, tbytes, &ws.bar[buf]);
 }
 
 __device__ __forceinline__ int pop_item(int* ctr, int lane) {
@@ -606,8 +608,8 @@ __global__ void __launch_bounds__(kThreads, kRasterMinBlocks) raster_kernel(cons
           break;
         }
         const uint2 e = list[cur];
-        raster_cluster<kCount>(vw, cm, ws, buf, (int)(e.x >> 24), (int)(e.y >> 24),
-                               e.y & 0xffffffu, P.big_px, lane, cn);
+        raster_cluster<kCount>(vw, cm, ws, buf, (int)(e.x >> 24), (int)(e.y >> 24), P.big_px,
+                               lane, cn);
         cur = nxt;
         buf ^= 1;
       }
@@ -629,11 +631,13 @@ __global__ void __launch_bounds__(kThreads, kRasterMinBlocks) raster_kernel(cons
             ws.vbuf[0][k] = make_float4(fmaf(o.w, u.x, o.x), fmaf(o.w, u.y, o.y),
                                         fmaf(o.w, u.z, o.z), 0.f);
           }
-          for (int k = lane; k < P.omesh_nt; k += 32) ws.tbuf[0][k] = P.omesh_t[k];
+          const uint32_t rgb = __ldg(P.obj_rgb + slot);
+          for (int k = lane; k < P.omesh_nt; k += 32) {
+            ws.tbuf[0][k] = P.omesh_t[k];
+            ws.cbuf[0][k] = rgb;
+          }
           __syncwarp();
-          raster_cluster<kCount>(vw, cm, ws, 0, P.omesh_nv, P.omesh_nt,
-                                 (uint32_t)S.n_tris + (uint32_t)(slot * P.omesh_nt), P.big_px, lane,
-                                 cn);
+          raster_cluster<kCount>(vw, cm, ws, 0, P.omesh_nv, P.omesh_nt, P.big_px, lane, cn);
         }
         // object vertices were written to vbuf[0] by ordinary stores: order
         // them before later bulk copies into the same buffer
@@ -667,9 +671,7 @@ __global__ void __launch_bounds__(kThreads, kRasterMinBlocks) raster_kernel(cons
         if (keys[k] != ~0ull) {
           const float invz = __uint_as_float(~(uint32_t)(keys[k] >> 32));
           z[k] = __frcp_rn(invz);
-          const uint32_t id = (uint32_t)keys[k];
-          col[k] = id < (uint32_t)S.n_tris ? __ldg(S.tri_rgb + id)
-                                           : __ldg(P.obj_rgb + (id - (uint32_t)S.n_tris) / P.omesh_nt);
+          col[k] = (uint32_t)keys[k] & 0xffffffu;  // the winner's colour rides in the key
         }
       }
       if (P.depth_fp16) {
