@@ -43,7 +43,7 @@ UNIT = "env-steps/s"
 # covered fragment (three edge tests, depth plane, key, depth test).
 C_TRI = 70
 C_FRAG = 10
-SMS, LANES = 148, 128
+LANES = 128          # FP32/INT32 lanes per SM
 
 
 def dist_env():
@@ -144,6 +144,15 @@ def measured_peaks():
         d = json.load(open(p))
         return float(d["hbm_gbs"]), float(d.get("sm_max_mhz", 2032.0)), "measured"
     return 6400.0, 2032.0, "fallback"
+
+
+def loaded_clock_mhz():
+    """Median SM clock of the B300s under a seconds-long dense load
+    (written beside the measured peaks), or None."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if not os.path.exists(p):
+        return None
+    return json.load(open(p)).get("clocks_under_load", {}).get("sm_mhz_median")
 
 
 def rank_seeds(w, rank):
@@ -620,20 +629,35 @@ def main():
     roof = None
     if phase_n[1]:
         launch_ms = phase_ms[1] / phase_n[1]
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
         sm_mhz = clocks.get("sm_max_mhz") or sm_max_mhz
-        peak = SMS * LANES * sm_mhz * 1e6 / 1e12
+        peak = sms * LANES * sm_mhz * 1e6 / 1e12
         work = raster_work(w.name)
-        achieved = None
+        achieved = no_cull = None
         if work:
             ops = n * (C_TRI * work["tris_per_view"] + C_FRAG * work["frags_per_view"])
             achieved = ops / (launch_ms / 1e3) / 1e12
+            # upper bound of the work: every scene triangle set up in every view
+            env_tris = np.array([scenes[s].n_tris for s in I.env_scene_map(n, w.n_scenes)])
+            ops_all = C_TRI * env_tris.sum() + n * C_FRAG * work["frags_per_view"]
+            no_cull = {"achieved": ops_all / (launch_ms / 1e3) / 1e12,
+                       "frac": ops_all / (launch_ms / 1e3) / 1e12 / peak,
+                       "note": "work if every scene triangle were set up in every view"}
+        loaded = loaded_clock_mhz()
+        at_loaded = None
+        if loaded and achieved:
+            p_l = sms * LANES * loaded * 1e6 / 1e12
+            at_loaded = {"sm_mhz": loaded, "peak": p_l, "frac": achieved / p_l,
+                         "note": "peak at the median SM clock of a seconds-long dense load "
+                                 "(MEASURED_PEAKS.json); this run's own clocks are in 'clocks'"}
         obs = n * w.img * w.img * ((2 if w.depth_fp16 else 4) + (3 if w.rgb else 0))
         roof = {"bound": "alu", "kernel": "raster_kernel", "achieved": achieved, "peak": peak,
                 "unit": "Tops/s (FP32/INT32 lane ops)",
                 "frac": (achieved / peak) if achieved else None,
                 "traffic": kernel_traffic(w.name), "launch_ms": launch_ms,
-                "peak_basis": f"{SMS} SMs x {LANES} lanes x {sm_mhz:.0f} MHz ({peak_src} max "
+                "peak_basis": f"{sms} SMs x {LANES} lanes x {sm_mhz:.0f} MHz ({peak_src} max "
                               f"clock)",
+                "at_loaded_clock": at_loaded, "no_culling_bound": no_cull,
                 "work_basis": f"{C_TRI} ops per front-facing triangle reaching the image + "
                               f"{C_FRAG} per covered fragment; counts per view from the oracle",
                 "hbm_view": {"bytes_per_launch": obs,
