@@ -110,6 +110,7 @@ struct FwdSmem {
   unsigned char y[kImgH];          // pong
   NsdfTail tail;
   float dot[2][kTile];             // output-row partial dots of the two column halves
+  uint32_t mask[4][2][kTrainThreads];  // relu'(h_l) bits of each thread's 2 x 32 columns
   unsigned long long bar_w, bar_mma;
   uint32_t tmem_slot;
 };
@@ -179,10 +180,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) nsdf_fwd_bwd_kernel(const Fw
   bool ok = mbar_wait(&sm.bar_w, 0);
   if (!ok) mbar_wait(&sm.bar_w, 0);
   ok = __syncthreads_and(ok);
-  const uint32_t f_s = smem_u32(sm.f), x_s = smem_u32(sm.x), y_s = smem_u32(sm.y);
-  const uint32_t w_s[4] = {smem_u32(sm.w), smem_u32(sm.w + kNsdfW1Bytes),
-                           smem_u32(sm.w + kNsdfW1Bytes + kNsdfWhBytes),
-                           smem_u32(sm.w + kNsdfW1Bytes + 2 * kNsdfWhBytes)};
+  const uint32_t x_s = smem_u32(sm.x);
   const uint32_t idesc_f = idesc_bf16(kTile, kNsdfWidth);
   float acc5[2] = {0.f, 0.f}, acc_b5 = 0.f, acc_loss = 0.f;
   uint32_t phase = 0;
@@ -245,14 +243,14 @@ __global__ void __launch_bounds__(kTrainThreads, 1) nsdf_fwd_bwd_kernel(const Fw
     __syncthreads();
 
     // ------------------------------------------------ forward, layers 1..3
-    uint32_t mask[4][2];
-    const uint32_t a_in[3] = {f_s, x_s, y_s};
-    unsigned char* const out_img[3] = {sm.x, sm.y, sm.x};
-    const unsigned char* const in_img[3] = {sm.f, sm.x, sm.y};
-#pragma unroll
+#pragma unroll 1
     for (int L = 0; L < 3; ++L) {
-      issue_and_wait(1, a_in[L], w_s[L], L == 0 ? 1 : 2, act + act_h(L), in_img[L],
-                     L == 0 ? kImgH0 : kImgH);
+      // h_L (features, x, y) in, h_{L+1} out to x, y, x
+      const unsigned char* in_img = L == 0 ? sm.f : (L == 1 ? sm.x : sm.y);
+      unsigned char* out_img = L == 1 ? sm.y : sm.x;
+      issue_and_wait(1, smem_u32(in_img),
+                     smem_u32(sm.w) + (L == 0 ? 0 : kNsdfW1Bytes + (L - 1) * kNsdfWhBytes),
+                     L == 0 ? 1 : 2, act + act_h(L), in_img, L == 0 ? kImgH0 : kImgH);
       if (!ok) break;
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
@@ -265,8 +263,8 @@ __global__ void __launch_bounds__(kTrainThreads, 1) nsdf_fwd_bwd_kernel(const Fw
           v[u] = bf16_round(fmaxf(v[u] + sm.tail.b[L][col + u], 0.f));
           bits |= (v[u] > 0.f ? 1u : 0u) << u;
         }
-        mask[L][c] = bits;
-        store_row32(out_img[L], row, col, v);
+        sm.mask[L][c][tid] = bits;
+        store_row32(out_img, row, col, v);
       }
       fence_proxy_async();
       tc_fence_before();
@@ -274,7 +272,8 @@ __global__ void __launch_bounds__(kTrainThreads, 1) nsdf_fwd_bwd_kernel(const Fw
     }
     if (!ok) break;
     // ------------------------------------- layer 4, output row, loss gradient
-    issue_and_wait(1, x_s, w_s[3], 2, act + act_h(3), sm.x, kImgH);
+    issue_and_wait(1, x_s, smem_u32(sm.w) + kNsdfW1Bytes + 2 * kNsdfWhBytes, 2, act + act_h(3),
+                   sm.x, kImgH);
     if (!ok) break;
     float dotp = 0.f;
 #pragma unroll
@@ -289,7 +288,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) nsdf_fwd_bwd_kernel(const Fw
         bits |= (h > 0.f ? 1u : 0u) << u;
         dotp = fmaf(h, sm.tail.w5[col + u], dotp);
       }
-      mask[3][c] = bits;
+      sm.mask[3][c][tid] = bits;
     }
     sm.dot[hf][row] = dotp;
     __syncthreads();
@@ -308,7 +307,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) nsdf_fwd_bwd_kernel(const Fw
 #pragma unroll
       for (int u = 0; u < 32; ++u) {
         const float h = bf16_round(fmaxf(v[u] + sm.tail.b[3][col + u], 0.f));
-        dl[u] = ((mask[3][c] >> u) & 1u) ? g * sm.tail.w5[col + u] : 0.f;
+        dl[u] = ((sm.mask[3][c][tid] >> u) & 1u) ? g * sm.tail.w5[col + u] : 0.f;
         v[u] = g * h;
       }
       acc5[c] += warp_reduce_scatter32(v, lane);
@@ -318,22 +317,24 @@ __global__ void __launch_bounds__(kTrainThreads, 1) nsdf_fwd_bwd_kernel(const Fw
     tc_fence_before();
     __syncthreads();
     // ------------------------------------------- backward through layers 4..2
-    const uint32_t a_b[3] = {y_s, x_s, y_s};       // delta_4, delta_3, delta_2
-    unsigned char* const o_b[3] = {sm.x, sm.y, sm.x};
-    const unsigned char* const i_b[3] = {sm.y, sm.x, sm.y};
-#pragma unroll
+#pragma unroll 1
     for (int s = 0; s < 3; ++s) {
       const int l = 3 - s;  // multiplies by W_{l+1}, masks with relu' of h_l
-      issue_and_wait(2, a_b[s], w_s[l], 0, act + act_d(l), i_b[s], kImgH);
+      // delta_4, delta_3, delta_2 in y, x, y; the next delta out to x, y, x
+      unsigned char* const i_b = (s & 1) ? sm.x : sm.y;
+      unsigned char* const o_b = (s & 1) ? sm.y : sm.x;
+      issue_and_wait(2, smem_u32(i_b), smem_u32(sm.w) + kNsdfW1Bytes + (l - 1) * kNsdfWhBytes, 0,
+                     act + act_d(l), i_b, kImgH);
       if (!ok) break;
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         const int col = hf * 64 + c * 32;
         float v[32];
         tmem_ld32(trow + col, v);
+        const uint32_t mk = sm.mask[l - 1][c][tid];
 #pragma unroll
-        for (int u = 0; u < 32; ++u) v[u] = ((mask[l - 1][c] >> u) & 1u) ? v[u] : 0.f;
-        store_row32(o_b[s], row, col, v);
+        for (int u = 0; u < 32; ++u) v[u] = ((mk >> u) & 1u) ? v[u] : 0.f;
+        store_row32(o_b, row, col, v);
       }
       fence_proxy_async();
       tc_fence_before();
@@ -368,6 +369,7 @@ struct WgradSmem {
   unsigned char ones[16 * kTile * 2]; // BF16 ones, 16 rows x 128 samples (K-major)
   unsigned long long full[3], empty[3], done;
   uint32_t tmem_slot;
+  uint32_t touched;  // layers this CTA accumulated (bit l)
 };
 constexpr int kStages = 3;
 // tensor-memory columns of dW_l (l = 0: 64 columns, else 128) and db_l (16 each)
@@ -398,14 +400,16 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = sm.tmem_slot;
-  const int t0 = (int)((long long)blockIdx.x * tiles / gridDim.x);
-  const int t1 = (int)((long long)(blockIdx.x + 1) * tiles / gridDim.x);
-  const int items = (t1 - t0) * 4;
+  // items (tile, layer) split evenly over the CTAs
+  const int g0 = (int)((long long)blockIdx.x * tiles * 4 / gridDim.x);
+  const int g1 = (int)((long long)(blockIdx.x + 1) * tiles * 4 / gridDim.x);
+  const int items = g1 - g0;
   bool ok = true;
   if (tid == 0) {
     bool pending[kStages] = {false, false, false};
+    uint32_t touched = 0u;
     auto load = [&](int k, int st) {
-      const int tile = t0 + k / 4, l = k % 4;
+      const int tile = (g0 + k) / 4, l = (g0 + k) % 4;
       const unsigned char* base = act + (size_t)tile * kActTile;
       const int hb = l == 0 ? kImgH0 : kImgH;
       mbar_expect_tx(&sm.full[st], kImgH + hb);
@@ -424,8 +428,9 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
       }
       pending[st] = false;
       tc_fence_after();
-      const int l = k % 4;
-      const bool first = k < 4;
+      const int l = (g0 + k) % 4;
+      const bool first = !((touched >> l) & 1u);
+      touched |= 1u << l;
       const uint32_t dimg = smem_u32(sm.stage[st]), himg = dimg + kImgH;
       const uint32_t id_w = idesc_bf16(kTile, in_dim(l), true, true);
       const uint32_t id_b = idesc_bf16(kTile, 16, true, false);
@@ -449,6 +454,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
       }
     }
     mma_commit(&sm.done);
+    sm.touched = touched;
     // copies still in flight after a failure: give each one bounded wait
     for (int s = 0; s < kStages; ++s)
       if (pending[s]) mbar_wait(&sm.full[s], 0), mbar_wait(&sm.full[s], 1);
@@ -456,29 +462,29 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
   const bool done = mbar_wait(&sm.done, 0);
   ok = __syncthreads_and(ok && done);
   tc_fence_after();
-  if (ok && items > 0) {
+  if (ok) {
     const int o = q * 32 + lane;  // output unit of this lane
     float* pc = part + (size_t)blockIdx.x * kPartStride;
+    const uint32_t touched = sm.touched;
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
       const int half = in_dim(l) / 2;
+      const bool has = (touched >> l) & 1u;  // else this CTA's partial is zero
       for (int c = 0; c < half; c += 32) {
         float v[32];
         tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + col_w(l) + hf * half + c, v);
+#pragma unroll
+        for (int u = 0; u < 32; ++u) v[u] = has ? v[u] : 0.f;
         float4* dst = reinterpret_cast<float4*>(pc + off_w(l) + (size_t)o * in_dim(l) + hf * half + c);
 #pragma unroll
         for (int u = 0; u < 8; ++u)
           dst[u] = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
       }
       const float b = tmem_ld1(tmem + ((uint32_t)(q * 32) << 16) + col_b(l));
-      if (hf == 0) pc[off_b(l) + o] = b;
+      if (hf == 0) pc[off_b(l) + o] = has ? b : 0.f;
     }
-  } else if (!ok && tid == 0 && err) {
+  } else if (tid == 0 && err) {
     atomicOr(err, kErrWaitTimeout);
-  }
-  if (ok && items == 0) {
-    float* pc = part + (size_t)blockIdx.x * kPartStride;
-    for (int i = tid; i < kOffW5; i += blockDim.x) pc[i] = 0.f;
   }
   tc_fence_before();
   __syncthreads();
