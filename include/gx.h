@@ -278,7 +278,9 @@ gx_status gx_phase_times(gx_ctx* ctx, double ms[4], int64_t launches[4]);
  * created with profile bit 1), then cleared: clusters tested, clusters drawn,
  * triangles seen, front-facing, rasterised by fragment expansion, pixels
  * they expand to, rasterised per warp, 8x4 blocks the warps scanned,
- * near-clipped, fragments written.  Fills out[0..n-1]; waits for the device.
+ * near-clipped, fragments written, mbarrier polls, expansion passes,
+ * 32-triangle set-up rounds, expansion slots (runs of up to four pixels).
+ * Fills out[0..n-1]; waits for the device.
  * GX_ESTATE when the context does not count. */
 gx_status gx_raster_counters(gx_ctx* ctx, int64_t* out, int32_t n);
 

@@ -188,6 +188,7 @@ enum RasterCounter {
   kCntWaitIters,     // mbarrier polls (per warp)
   kCntExpandTrips,   // fragment-expansion loop trips (per warp)
   kCntRounds,        // 32-triangle rounds (per warp)
+  kCntExpandSlots,   // fragment-expansion slots (runs of up to four pixels)
   kRasterCounters
 };
 

@@ -408,6 +408,7 @@ __device__ void raster_cluster(const View& vw, const Cam& cm, WarpSmem& ws, int 
                   if (kCount) {
                     cn.v[kCntTrisSmall]++;
                     cn.v[kCntSmallPixels] += bw * bh;
+                    cn.v[kCntExpandSlots] += npx;
                   }
                 } else {
                   big = true;

@@ -36,7 +36,7 @@ NSDF_PARAMS = 57985
 NSDF_FREQ = 32
 RASTER_COUNTERS = ["clusters_tested", "clusters_drawn", "tris_seen", "tris_front", "tris_expand",
                    "expand_pixels", "tris_warp", "warp_blocks", "tris_clipped", "fragments", "wait_polls",
-                   "expand_trips", "rounds"]
+                   "expand_trips", "rounds", "expand_slots"]
 
 f32p = C.POINTER(C.c_float)
 i32p = C.POINTER(C.c_int32)
