@@ -219,6 +219,22 @@ __global__ void __launch_bounds__(kQueryThreads, 1) nsdf_step_kernel(const NsdfS
   const int t1 = (int)((long long)(blockIdx.x + 1) * p.n_tiles / gridDim.x);
   const int g = threadIdx.x >> 7, gt = threadIdx.x & 127;
   const int slot = gt >> 5, lane = gt & 31;
+  // this thread's query of tile tt (its environment, -1 for none, and the
+  // sphere centre); the next round's is loaded while the current one runs
+  auto fetch = [&](int tt, int& env, float4& q) {
+    env = -1;
+    q = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (tt < t1) {
+      const int4 tile = p.tiles[tt];
+      if (slot < tile.z) {
+        env = p.perm[tile.y + slot];
+        q = p.pts[(size_t)env * 32 + lane];
+      }
+    }
+  };
+  int next_env;
+  float4 next_q;
+  fetch(t0 + g, next_env, next_q);
   for (int t = t0; ok && t < t1;) {
     const int4 first = p.tiles[t];
     if (first.x != loaded) {
@@ -229,16 +245,13 @@ __global__ void __launch_bounds__(kQueryThreads, 1) nsdf_step_kernel(const NsdfS
       loaded = first.x;
     }
     const int in_round = (t + 1 < t1 && p.tiles[t + 1].x == first.x) ? 2 : 1;
+    const int env = next_env;  // group g's query in this round's tile t + g
+    const float4 q = next_q;
+    fetch(t + in_round + g, next_env, next_q);
     if (g < in_round) {
-      const int4 tile = p.tiles[t + g];
-      int env = -1;
       Centred d = centre_point(sm.tail.centre[0], sm.tail.centre[1], sm.tail.centre[2],
                                sm.tail.centre);
-      if (slot < tile.z) {
-        env = p.perm[tile.y + slot];
-        const float4 q = p.pts[(size_t)env * 32 + lane];
-        d = centre_point(q.x, q.y, q.z, sm.tail.centre);
-      }
+      if (env >= 0) d = centre_point(q.x, q.y, q.z, sm.tail.centre);
       const float v = run_tile(sm, g, d, mma_phase, ok);
       if (ok && env >= 0) p.out[(size_t)env * 32 + lane] = v;
     }

@@ -214,18 +214,25 @@ __global__ void __launch_bounds__(kTrainThreads, 1) nsdf_fwd_bwd_kernel(const Fw
     tc_fence_after();
   };
 
+  // this thread's sample (point and label) of a tile; the next tile's is
+  // loaded while the current one runs
+  auto fetch = [&](int tile, float4& v) {
+    const int r = tile * kTile + row;
+    v = make_float4(sm.tail.centre[0], sm.tail.centre[1], sm.tail.centre[2], 0.f);
+    if (tile < tiles && r < p.n) {
+      const long long idx = (p.start + r) % p.n_set;
+      v = make_float4(p.pts[3 * idx], p.pts[3 * idx + 1], p.pts[3 * idx + 2], p.labels[idx]);
+    }
+  };
+  float4 next;
+  fetch(blockIdx.x, next);
   for (int tile = blockIdx.x; ok && tile < tiles; tile += gridDim.x) {
     unsigned char* act = p.act + (size_t)tile * kActTile;
-    const int r = tile * kTile + row;
-    const bool valid = r < p.n;
-    float label = 0.f;
-    Centred d = centre_point(sm.tail.centre[0], sm.tail.centre[1], sm.tail.centre[2],
-                             sm.tail.centre);
-    if (valid) {
-      const long long idx = (p.start + r) % p.n_set;
-      d = centre_point(p.pts[3 * idx], p.pts[3 * idx + 1], p.pts[3 * idx + 2], sm.tail.centre);
-      label = p.labels[idx];
-    }
+    const bool valid = tile * kTile + row < p.n;
+    const float4 cur = next;
+    fetch(tile + gridDim.x, next);
+    const float label = cur.w;
+    const Centred d = centre_point(cur.x, cur.y, cur.z, sm.tail.centre);
     if (tid == 0) bulk_wait_read<0>();  // the previous tile's stores left shared memory
     __syncthreads();
     // Fourier features: this thread's 16 frequencies of its row
