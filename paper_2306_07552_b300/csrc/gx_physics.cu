@@ -15,6 +15,8 @@
 // runs the (cheap) FK chain and keeps only its own link's frame.
 #include <math_constants.h>
 
+#include <algorithm>
+
 #include "gx_internal.h"
 #include "gx_device.cuh"
 
@@ -651,26 +653,22 @@ constexpr int kResetThreads = 256;
 constexpr int kTryWindow = 8;  // tries evaluated together before looking further
 static_assert(kResetThreads / 32 == kTryWindow, "one warp per try of a window");
 
-// (a12) masked reset, one CTA per environment: objects on support tops, then
-// the robot base in free space, by rejection sampling with at most 64
-// Philox draws each; the lowest accepted try wins, the same choice as trying
-// them in order.  Tries are evaluated in windows of 8 so that the scene-grid
-// gathers of a window are in flight together (random gathers into a
-// multi-gigabyte grid have long latency, and a reset is latency-bound):
+// (a12) masked reset, one CTA per environment at a time (the grid strides
+// over the environments; CTAs of unmasked ones move on at once): objects on
+// support tops, then the robot base in free space, by rejection sampling
+// with at most 64 Philox draws each; the lowest accepted try wins, the same
+// choice as trying them in order.  Tries are evaluated in windows of 8 so
+// that the scene-grid gathers of a window are in flight together (random
+// gathers into a multi-gigabyte grid have long latency, and a reset is
+// latency-bound):
 //   1. the static-scene test of tries 0..7 of every object, all at once;
-//   2. objects in order (one warp): the first try that passed step 1 and
-//      clears the objects already placed; when all 8 fail, the warp tests
-//      the following tries itself, 32 at a time;
+//   2. objects in order (one at a time): warp w tests try t0 + w of the
+//      window against the objects already placed, the first try that passed
+//      step 1 and clears them wins; when all 8 fail, the next window;
 //   3. every (robot try, sphere) pair of a window at once; the first window
 //      with a contact-free try decides.
-__global__ void __launch_bounds__(kResetThreads) reset_kernel(const ResetParams P) {
-  __shared__ float4 s_cand[GX_MAX_OBJECTS][kTryWindow];  // x, y, z, static test passed
-  __shared__ float4 so[GX_MAX_OBJECTS];
-  __shared__ float s_rho[GX_MAX_OBJECTS];
-  __shared__ unsigned s_bad;
-  __shared__ int s_robot_try;
-  const int env = blockIdx.x;
-  if (P.mask && !P.mask[env]) return;
+__device__ void reset_env(const ResetParams& P, int env, float4 (*s_cand)[kTryWindow], float4* so,
+                          float* s_rho, unsigned& s_bad, int& s_robot_try) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = P.n, M = P.M;
   const DScene& S = P.scenes[P.env_scene[env]];
@@ -840,6 +838,18 @@ __global__ void __launch_bounds__(kResetThreads) reset_kernel(const ResetParams 
   }
 }
 
+__global__ void __launch_bounds__(kResetThreads) reset_kernel(const ResetParams P) {
+  __shared__ float4 s_cand[GX_MAX_OBJECTS][kTryWindow];  // x, y, z, static test passed
+  __shared__ float4 so[GX_MAX_OBJECTS];
+  __shared__ float s_rho[GX_MAX_OBJECTS];
+  __shared__ unsigned s_bad;
+  __shared__ int s_robot_try;
+  for (int env = blockIdx.x; env < P.n; env += gridDim.x) {
+    if (P.mask && !P.mask[env]) continue;
+    reset_env(P, env, s_cand, so, s_rho, s_bad, s_robot_try);
+  }
+}
+
 // Rebuilds every environment's object broad-phase from the state (after a
 // state load): resting objects where they are, a held object where it
 // rested before the grasp.
@@ -876,10 +886,29 @@ void launch_physics(const PhysicsParams& p, cudaStream_t s) {
   physics_kernel<<<blocks, 32 * kEnvsPerBlock, 0, s>>>(p);
 }
 
-cudaError_t reset_configure() { return cudaSuccess; }
+namespace {
+int g_reset_grid = 0;  // CTAs resident at once on this device
+}
 
+cudaError_t reset_configure() {
+  if (g_reset_grid > 0) return cudaSuccess;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+      (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reset_kernel, kResetThreads, 0)) !=
+          cudaSuccess)
+    return e;
+  g_reset_grid = std::max(1, sms * per_sm);
+  return cudaSuccess;
+}
+
+// One wave of resident CTAs striding over the environments: a staggered reset
+// of a few environments no longer launches a CTA per environment.
 void launch_reset(const ResetParams& p, cudaStream_t s) {
-  reset_kernel<<<p.n, kResetThreads, 0, s>>>(p);
+  if (p.n <= 0) return;
+  const int grid = std::min(p.n, g_reset_grid > 0 ? g_reset_grid : p.n);
+  reset_kernel<<<grid, kResetThreads, 0, s>>>(p);
 }
 
 }  // namespace gx
