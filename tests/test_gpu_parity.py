@@ -153,6 +153,55 @@ def test_edge_sizes_and_no_objects(room):
         sim.close()
 
 
+def test_maximum_sizes(room):
+    """The largest image (256 wide), a non-square one, and the most objects
+    per environment (256): reset and steps in lockstep, images checked."""
+    gx, scene, ss, orc = room
+    n, M, W, H = 3, gx.MAX_OBJECTS, 256, 160
+    sim = gx.Sim(ss, ROBOT, n, img=(W, H), n_objects=M, obj_radius=(0.03, 0.035), seed=11)
+    before_reset = {k: v.copy() for k, v in sim.state_arrays().items()}
+    sim.reset()
+    # 256 objects crowd one room: placements that use up their 64 tries are
+    # reported (informational bit) and must still match the oracle's choice
+    assert sim.device_error() & ~gx.GX_DEV_PLACEMENT_FAILED == 0
+    s = sim.state_arrays()
+    for e in range(n):
+        st = oracle_state(before_reset, e, M)
+        r = orc.reset(st, 11, e, M, 0.03, 0.035)
+        if r.near_band:
+            continue
+        assert np.allclose(s["obj"][e, :M], O.Oracle.state_objs(st), atol=1e-5), e
+        assert abs(s["base_x"][e] - st.base[0]) < 1e-5 and abs(s["base_z"][e] - st.base[1]) < 1e-5
+    acts = I.make_actions(2, n, "gaussian", seed=12)
+    tally = Tally()
+    for t in range(2):
+        before = {k: v.copy() for k, v in sim.state_arrays().items()}
+        out = sim.step(torch.from_numpy(acts[t]).cuda())
+        torch.cuda.synchronize()
+        after = sim.state_arrays()
+        check_step(orc, before, after, out, acts[t], range(n), M, tally)
+        for e in range(n):
+            check_image(orc, after, out, e, W, H, M, tally)
+    print(tally)
+    assert tally.envs - tally.near_band >= 4
+    sim.close()
+
+
+def test_invalid_configurations_are_refused(room):
+    """Sizes outside the documented limits fail at creation with an error
+    status, before any kernel runs."""
+    gx, scene, ss, orc = room
+    for kw in [dict(img=(288, 128)), dict(img=(128, 40)), dict(img=(16, 16)),
+               dict(n_objects=gx.MAX_OBJECTS + 1), dict(n_objects=-1),
+               dict(obj_radius=(0.06, 0.03))]:
+        args = dict(img=(64, 64), n_objects=4)
+        args.update(kw)
+        with pytest.raises(gx.GxError):
+            gx.Sim(ss, ROBOT, 4, **args)
+    with pytest.raises(gx.GxError):
+        gx.Sim(ss, ROBOT, 0, img=(64, 64), n_objects=4)
+
+
 def test_graph_replay_and_determinism(room):
     gx, scene, ss, orc = room
     n, M, W = 16, 10, 64
