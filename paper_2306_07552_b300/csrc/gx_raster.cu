@@ -385,25 +385,25 @@ __device__ void raster_cluster(const View& vw, const Cam& cm, WarpSmem& ws, int 
                 if (fits32 && bw * bh <= big_px) {
                   // queued for pixel expansion; int32 edge values are exact
                   // because every visited pixel lies inside the bounding box
-                  ExpTri& r = ws.q[lane];
                   const int2 V[3] = {V0, V1, V2};
                   const int px = ix0 * 256 + 128, py = iy0 * 256 + 128;
+                  int e[3], sx[3], sy[3];
 #pragma unroll
                   for (int k = 0; k < 3; ++k) {
                     const int dxk = V[(k + 1) % 3].x - V[k].x, dyk = V[(k + 1) % 3].y - V[k].y;
-                    r.e[k] = dxk * (py - V[k].y) - dyk * (px - V[k].x) + (top_left(dxk, dyk) ? 0 : -1);
-                    r.sx[k] = -dyk * 256;
-                    r.sy[k] = dxk * 256;
+                    e[k] = dxk * (py - V[k].y) - dyk * (px - V[k].x) + (top_left(dxk, dyk) ? 0 : -1);
+                    sx[k] = -dyk * 256;
+                    sy[k] = dxk * 256;
                   }
                   float A, B, C;
                   depth_plane(cm, nx, ny, nz, h, A, B, C);
-                  r.ixy = ix0 | (iy0 << 16);
-                  r.bw = bw;
-                  r.inv_bp = __frcp_rn((float)((bw + kSpan - 1) / kSpan));
-                  r.A = A;
-                  r.B = B;
-                  r.C = C;
-                  r.rgb = ws.cbuf[buf][t];
+                  // the record in four 16-byte stores (the round's slot offset follows later)
+                  int4* r4 = reinterpret_cast<int4*>(&ws.q[lane]);
+                  r4[0] = make_int4(e[0], e[1], e[2], ix0 | (iy0 << 16));
+                  r4[1] = make_int4(sx[0], sx[1], sx[2], bw);
+                  r4[2] = make_int4(sy[0], sy[1], sy[2], (int)ws.cbuf[buf][t]);
+                  r4[3] = make_int4(__float_as_int(A), __float_as_int(B), __float_as_int(C), 0);
+                  ws.q[lane].inv_bp = __frcp_rn((float)((bw + kSpan - 1) / kSpan));
                   npx = ((bw + kSpan - 1) / kSpan) * bh;  // expansion slots: pixel runs
                   if (kCount) {
                     cn.v[kCntTrisSmall]++;
