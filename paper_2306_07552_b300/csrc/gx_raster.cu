@@ -453,24 +453,28 @@ __device__ void raster_cluster(const View& vw, const Cam& cm, WarpSmem& ws, int 
       started += __popc(smask);
       const int s = base + lane;
       if (s < total) {
-        const ExpTri& q = ws.q[ws.qlane[k]];
-        const int rr = s - q.off;
-        const int bw = q.bw;
-        const int y = __float2int_rz(((float)rr + 0.5f) * q.inv_bp);
+        // the record in five 16-byte loads: e | ixy, sx | bw, sy | rgb, A B C | off, inv_bp
+        const int4* q4 = reinterpret_cast<const int4*>(&ws.q[ws.qlane[k]]);
+        const int4 qe = q4[0], qx = q4[1], qy = q4[2], qp = q4[3];
+        const float inv_bp = __int_as_float(q4[4].x);
+        const int rr = s - qp.w;
+        const int bw = qx.w;
+        const int y = __float2int_rz(((float)rr + 0.5f) * inv_bp);
         const int x = kSpan * (rr - y * ((bw + kSpan - 1) / kSpan));
-        const int e0 = q.e[0] + x * q.sx[0] + y * q.sy[0];
-        const int e1 = q.e[1] + x * q.sx[1] + y * q.sy[1];
-        const int e2 = q.e[2] + x * q.sx[2] + y * q.sy[2];
-        const int i = (q.ixy & 0xffff) + x, j = (q.ixy >> 16) + y;
+        const int e0 = qe.x + x * qx.x + y * qy.x;
+        const int e1 = qe.y + x * qx.y + y * qy.y;
+        const int e2 = qe.z + x * qx.z + y * qy.z;
+        const int i = (qe.w & 0xffff) + x, j = (qe.w >> 16) + y;
         // the run's plane terms once: u + k is exact, so each fragment gets the
         // same value as frag() at (i + k, j)
         const float u0 = (float)i + 0.5f - cm.cx;
-        const float row = fmaf(q.B, (float)j + 0.5f - cm.cy, q.C);
+        const float row = fmaf(__int_as_float(qp.y), (float)j + 0.5f - cm.cy, __int_as_float(qp.z));
+        const float qa = __int_as_float(qp.x);
         unsigned long long* fbp = vw.fb + j * vw.W + i;
 #pragma unroll
         for (int u = 0; u < kSpan; ++u)
-          if (x + u < bw && ((e0 + u * q.sx[0]) | (e1 + u * q.sx[1]) | (e2 + u * q.sx[2])) >= 0)
-            frag_key<kCount>(vw, fbp + u, fmaf(q.A, u0 + (float)u, row), q.rgb, cn);
+          if (x + u < bw && ((e0 + u * qx.x) | (e1 + u * qx.y) | (e2 + u * qx.z)) >= 0)
+            frag_key<kCount>(vw, fbp + u, fmaf(qa, u0 + (float)u, row), (uint32_t)qy.w, cn);
       }
     }
     __syncwarp();
