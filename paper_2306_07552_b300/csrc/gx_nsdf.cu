@@ -130,8 +130,12 @@ __device__ float run_tile(QuerySmem& sm, int g, const Centred& d, uint32_t& mma_
     for (int c = 0; c < kNsdfWidth / 32; ++c) {
       float v[32];
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
+      {
+        float bias[32];
+        lds32(&sm.tail.b[layer][c * 32], bias);
 #pragma unroll
-      for (int u = 0; u < 32; ++u) v[u] = fmaxf(v[u] + sm.tail.b[layer][c * 32 + u], 0.f);
+        for (int u = 0; u < 32; ++u) v[u] = fmaxf(v[u] + bias[u], 0.f);
+      }
       if (layer < 3) {
         // store_chunk rounds to BF16 on the way into the next operand
 #pragma unroll
@@ -142,8 +146,12 @@ __device__ float run_tile(QuerySmem& sm, int g, const Centred& d, uint32_t& mma_
           store_chunk(act, warp * 32 + lane, c * 32 + q * 8, kTile, ch);
         }
       } else {
+        {
+          float w5[32];
+          lds32(&sm.tail.w5[c * 32], w5);
 #pragma unroll
-        for (int u = 0; u < 32; ++u) dot = fmaf(bf16_round(v[u]), sm.tail.w5[c * 32 + u], dot);
+          for (int u = 0; u < 32; ++u) dot = fmaf(bf16_round(v[u]), w5[u], dot);
+        }
       }
     }
     fence_proxy_async();

@@ -262,12 +262,13 @@ __global__ void __launch_bounds__(kTrainThreads, 1) nsdf_fwd_bwd_kernel(const Fw
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         const int col = hf * 64 + c * 32;
-        float v[32];
+        float v[32], bias[32];
         tmem_ld32(trow + col, v);
+        lds32(&sm.tail.b[L][col], bias);
         uint32_t bits = 0;
 #pragma unroll
         for (int u = 0; u < 32; ++u) {
-          v[u] = bf16_round(fmaxf(v[u] + sm.tail.b[L][col + u], 0.f));
+          v[u] = bf16_round(fmaxf(v[u] + bias[u], 0.f));
           bits |= (v[u] > 0.f ? 1u : 0u) << u;
         }
         sm.mask[L][c][tid] = bits;
@@ -286,14 +287,16 @@ __global__ void __launch_bounds__(kTrainThreads, 1) nsdf_fwd_bwd_kernel(const Fw
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       const int col = hf * 64 + c * 32;
-      float v[32];
+      float v[32], bias[32], w5[32];
       tmem_ld32(trow + col, v);
+      lds32(&sm.tail.b[3][col], bias);
+      lds32(&sm.tail.w5[col], w5);
       uint32_t bits = 0;
 #pragma unroll
       for (int u = 0; u < 32; ++u) {
-        const float h = bf16_round(fmaxf(v[u] + sm.tail.b[3][col + u], 0.f));
+        const float h = bf16_round(fmaxf(v[u] + bias[u], 0.f));
         bits |= (h > 0.f ? 1u : 0u) << u;
-        dotp = fmaf(h, sm.tail.w5[col + u], dotp);
+        dotp = fmaf(h, w5[u], dotp);
       }
       sm.mask[3][c][tid] = bits;
     }

@@ -146,6 +146,19 @@ __device__ __forceinline__ void store_chunk(unsigned char* tile, int row, int k8
   *reinterpret_cast<uint4*>(tile + sw128_offset(row, k8, rows)) = *reinterpret_cast<uint4*>(p);
 }
 
+// 32 consecutive floats of shared memory (16-byte aligned) in eight 16-byte loads.
+__device__ __forceinline__ void lds32(const float* p, float (&v)[32]) {
+  const float4* p4 = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const float4 t = p4[q];
+    v[4 * q] = t.x;
+    v[4 * q + 1] = t.y;
+    v[4 * q + 2] = t.z;
+    v[4 * q + 3] = t.w;
+  }
+}
+
 __device__ __forceinline__ float bf16_round(float x) {
   return __bfloat162float(__float2bfloat16_rn(x));
 }
