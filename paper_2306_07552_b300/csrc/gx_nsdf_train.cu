@@ -517,20 +517,34 @@ struct AdamParams {
   float* loss_out;     // optional
 };
 
-__global__ void nsdf_adam_kernel(const AdamParams p) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i == 0 && p.loss_out) {
+// A block of 8 warps takes 32 consecutive parameters: warp w sums the
+// partials c = w, w + 8, ... (coalesced rows), then warp 0 adds the eight sums
+// in order and applies Adam; the order is fixed, so the result is deterministic.
+constexpr int kAdamParamsPerBlock = 32;
+constexpr int kAdamWarps = 8;
+
+__global__ void __launch_bounds__(32 * kAdamWarps) nsdf_adam_kernel(const AdamParams p) {
+  __shared__ float sums[kAdamWarps][kAdamParamsPerBlock];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * kAdamParamsPerBlock + lane;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && p.loss_out) {
     float s = 0.f;
     for (int c = 0; c < p.n_part5; ++c) s += p.part5[(size_t)c * kPart5 + 129];
     *p.loss_out = s * p.inv_n;
   }
-  if (i >= kNsdfParams) return;
-  float g = 0.f;
+  float part = 0.f;
   if (i < kOffW5) {
-    for (int c = 0; c < p.n_part; ++c) g += p.part[(size_t)c * kPartStride + i];
-  } else {
-    for (int c = 0; c < p.n_part5; ++c) g += p.part5[(size_t)c * kPart5 + (i - kOffW5)];
+    for (int c = warp; c < p.n_part; c += kAdamWarps) part += p.part[(size_t)c * kPartStride + i];
+  } else if (i < kNsdfParams) {
+    for (int c = warp; c < p.n_part5; c += kAdamWarps)
+      part += p.part5[(size_t)c * kPart5 + (i - kOffW5)];
   }
+  sums[warp][lane] = part;
+  __syncthreads();
+  if (warp != 0 || i >= kNsdfParams) return;
+  float g = 0.f;
+#pragma unroll
+  for (int w = 0; w < kAdamWarps; ++w) g += sums[w][lane];
   if (p.grad_out) p.grad_out[i] = g;
   if (!p.master) return;
   const float m = p.beta1 * p.m[i] + (1.f - p.beta1) * g;
@@ -645,7 +659,8 @@ cudaError_t grad_and_update(unsigned char* blob, const float* pts, const float* 
   ap.n_part5 = w.g1 * 4;
   ap.inv_n = 1.f / (float)n;
   ap.blob = blob;
-  nsdf_adam_kernel<<<(kNsdfParams + 255) / 256, 256, 0, s>>>(ap);
+  nsdf_adam_kernel<<<(kNsdfParams + kAdamParamsPerBlock - 1) / kAdamParamsPerBlock,
+                     32 * kAdamWarps, 0, s>>>(ap);
   return cudaGetLastError();
 }
 
