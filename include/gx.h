@@ -131,7 +131,6 @@ typedef struct {
   uint64_t seed;           /* Philox key for resets                           */
   const int32_t* env_scene; /* host [n_envs] scene per env; NULL: env i uses
                                scene floor(i * n_scenes / n_envs)             */
-  int32_t raster_regions;  /* reserved, must be 0                             */
   int32_t small_tri_px;    /* triangles whose clipped bounding box exceeds this
                               many pixels are scanned block-wise by a warp
                               instead of by fragment expansion (0: only those

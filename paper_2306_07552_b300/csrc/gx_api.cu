@@ -441,7 +441,6 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
     for (int i = 0; i < c.n_envs; ++i)
       if (c.env_scene[i] < 0 || c.env_scene[i] >= set->n)
         return fail(nullptr, GX_EINVAL, "env_scene[%d] out of range", i);
-  if (c.raster_regions != 0) return fail(nullptr, GX_EINVAL, "raster_regions is reserved (0)");
   if (c.sdf_mode < 0 || c.sdf_mode > 2) return fail(nullptr, GX_EINVAL, "sdf_mode must be 0, 1 or 2");
   if (c.heuristics & ~3) return fail(nullptr, GX_EINVAL, "heuristics: only bits 0 and 1 are defined");
   if (c.sdf_mode == 1 && !(c.sdf_margin >= 0.f && c.sdf_margin < 1e30f))

@@ -71,7 +71,7 @@ class GxConfig(C.Structure):
     _fields_ = [("n_envs", C.c_int32), ("img_w", C.c_int32), ("img_h", C.c_int32),
                 ("depth_fp16", C.c_int32), ("render_rgb", C.c_int32), ("n_objects", C.c_int32),
                 ("obj_radius_min", C.c_float), ("obj_radius_max", C.c_float),
-                ("seed", C.c_uint64), ("env_scene", i32p), ("raster_regions", C.c_int32),
+                ("seed", C.c_uint64), ("env_scene", i32p),
                 ("small_tri_px", C.c_int32), ("use_graph", C.c_int32), ("profile", C.c_int32),
                 ("sdf_mode", C.c_int32), ("sdf_margin", C.c_float), ("broadphase", C.c_int32),
                 ("render_robot", C.c_int32), ("heuristics", C.c_int32)]
@@ -326,7 +326,7 @@ class Sim:
 
     def __init__(self, scene_set: SceneSet, robot: _inputs.Robot, n_envs: int, img=(128, 128),
                  depth_fp16=False, render_rgb=True, n_objects=40, obj_radius=(0.03, 0.06),
-                 seed=1, env_scene=None, raster_regions=0, small_tri_px=0, use_graph=False,
+                 seed=1, env_scene=None, small_tri_px=0, use_graph=False,
                  profile=0, sdf_mode=0, sdf_margin=0.02, heuristics=0, render_robot=False,
                  broadphase=False):
         import torch
@@ -345,7 +345,7 @@ class Sim:
         if env_scene is not None:
             es = np.ascontiguousarray(env_scene, np.int32)
             cfg.env_scene = es.ctypes.data_as(i32p)
-        cfg.raster_regions, cfg.small_tri_px, cfg.use_graph = raster_regions, small_tri_px, int(use_graph)
+        cfg.small_tri_px, cfg.use_graph = small_tri_px, int(use_graph)
         cfg.profile = int(profile)
         cfg.sdf_mode, cfg.sdf_margin = int(sdf_mode), float(sdf_margin)
         cfg.heuristics = int(heuristics)
