@@ -532,10 +532,13 @@ __global__ void __launch_bounds__(32 * kAdamWarps) nsdf_adam_kernel(const AdamPa
     for (int c = 0; c < p.n_part5; ++c) s += p.part5[(size_t)c * kPart5 + 129];
     *p.loss_out = s * p.inv_n;
   }
+  // unrolled so that several rows' loads are in flight before their sums
   float part = 0.f;
   if (i < kOffW5) {
+#pragma unroll 8
     for (int c = warp; c < p.n_part; c += kAdamWarps) part += p.part[(size_t)c * kPartStride + i];
   } else if (i < kNsdfParams) {
+#pragma unroll 8
     for (int c = warp; c < p.n_part5; c += kAdamWarps)
       part += p.part5[(size_t)c * kPart5 + (i - kOffW5)];
   }
