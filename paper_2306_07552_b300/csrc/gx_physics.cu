@@ -662,9 +662,9 @@ static_assert(kResetThreads / 32 == kTryWindow, "one warp per try of a window");
 // gathers into a multi-gigabyte grid have long latency, and a reset is
 // latency-bound):
 //   1. the static-scene test of tries 0..7 of every object, all at once;
-//   2. objects in order (one at a time): warp w tests try t0 + w of the
-//      window against the objects already placed, the first try that passed
-//      step 1 and clears them wins; when all 8 fail, the next window;
+//   2. objects in order by one warp, tries in order: the first try that passed
+//      its static test and clears the objects already placed wins (most
+//      objects take their first try, so the chain has no block barrier);
 //   3. every (robot try, sphere) pair of a window at once; the first window
 //      with a contact-free try decides.
 __device__ void reset_env(const ResetParams& P, int env, float4 (*s_cand)[kTryWindow], float4* so,
@@ -690,49 +690,41 @@ __device__ void reset_env(const ResetParams& P, int env, float4 (*s_cand)[kTryWi
   }
   if (tid == 0) s_robot_try = -1;
   __syncthreads();
-  // 2. objects in order; in each window of tries warp w takes try t0 + w and
-  // its lanes split the test against the objects already placed; the lowest
-  // accepted try wins (the same choice as trying them in order); after 64
-  // failed tries the last one stands
+  // 2. objects in order, by warp 0 alone: tries in order (the first 8 from
+  // step 1, later ones evaluated by the warp), the warp's lanes splitting each
+  // try's test against the objects already placed; the first accepted try
+  // wins; after 64 failed tries the last one stands.  Most objects take their
+  // first try, so no block-wide barrier sits in this chain.
   bool failed = false;
-  for (int j = 0; j < M; ++j) {
-    const float rho = s_rho[j];
-    int pick_t = -1;
-    for (int t0 = 0; t0 < 64 && pick_t < 0; t0 += kTryWindow) {
-      const int t = t0 + warp;
-      float4 c;
-      if (t0 == 0) {
-        c = s_cand[j][warp];
-      } else {
-        const uint4 wv = philox4x32_10(make_uint4((uint32_t)env, ep, (uint32_t)j, (uint32_t)t), key);
-        const float3 p = object_candidate(S, wv, rho, clear);
-        float d;
-        const bool sok = grid_query(S, p.x, p.y, p.z, d) && !(d < rho);
-        c = make_float4(p.x, p.y, p.z, sok ? 1.f : 0.f);
-      }
-      bool hit = false;
-      if (c.w > 0.5f)
-        for (int k = lane; k < j && !hit; k += 32) {
-          const float4 o = so[k];
-          const float dx = c.x - o.x, dy = c.y - o.y, dz = c.z - o.z, rr = rho + o.w;
-          hit = dx * dx + dy * dy + dz * dz < rr * rr;
+  if (warp == 0) {
+    for (int j = 0; j < M; ++j) {
+      const float rho = s_rho[j];
+      float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+      bool accepted = false;
+      for (int t = 0; t < 64 && !accepted; ++t) {
+        if (t < kTryWindow) {
+          c = s_cand[j][t];
+        } else {
+          const uint4 wv =
+              philox4x32_10(make_uint4((uint32_t)env, ep, (uint32_t)j, (uint32_t)t), key);
+          const float3 p = object_candidate(S, wv, rho, clear);
+          float d;
+          const bool sok = grid_query(S, p.x, p.y, p.z, d) && !(d < rho);
+          c = make_float4(p.x, p.y, p.z, sok ? 1.f : 0.f);
         }
-      const bool ok = c.w > 0.5f && !__any_sync(kFull, hit);
-      if (lane == 0) s_cand[j][warp] = c;  // this window's candidates, for the pick below
-      if (tid == 0) s_bad = 0u;
-      __syncthreads();
-      if (lane == 0 && ok) atomicOr(&s_bad, 1u << warp);
-      __syncthreads();
-      const unsigned okw = s_bad;
-      if (okw) pick_t = t0 + __ffs(okw) - 1;
-      if (pick_t >= 0 || t0 + kTryWindow >= 64) {
-        const int w = pick_t >= 0 ? pick_t - t0 : kTryWindow - 1;
-        const float4 cc = s_cand[j][w];
-        if (tid == 0) so[j] = make_float4(cc.x, cc.y, cc.z, rho);
+        bool hit = false;
+        if (c.w > 0.5f)
+          for (int k = lane; k < j && !hit; k += 32) {
+            const float4 o = so[k];
+            const float dx = c.x - o.x, dy = c.y - o.y, dz = c.z - o.z, rr = rho + o.w;
+            hit = dx * dx + dy * dy + dz * dz < rr * rr;
+          }
+        accepted = c.w > 0.5f && !__any_sync(kFull, hit);
       }
-      __syncthreads();
+      if (lane == 0) so[j] = make_float4(c.x, c.y, c.z, rho);
+      __syncwarp();
+      failed |= !accepted;
     }
-    failed |= pick_t < 0;
   }
   __syncthreads();
   if (P.bp) {  // the object broad-phase of this environment, rebuilt
