@@ -651,6 +651,7 @@ __device__ void sphere_world(const gx_robot& rb, int i, float x, float z, float 
 
 constexpr int kResetThreads = 256;
 constexpr int kTryWindow = 8;  // tries evaluated together before looking further
+constexpr int kSerialPlaceMax = 64;  // objects per env placed by the one-warp chain
 static_assert(kResetThreads / 32 == kTryWindow, "one warp per try of a window");
 
 // (a12) masked reset, one CTA per environment at a time (the grid strides
@@ -662,9 +663,10 @@ static_assert(kResetThreads / 32 == kTryWindow, "one warp per try of a window");
 // gathers into a multi-gigabyte grid have long latency, and a reset is
 // latency-bound):
 //   1. the static-scene test of tries 0..7 of every object, all at once;
-//   2. objects in order by one warp, tries in order: the first try that passed
-//      its static test and clears the objects already placed wins (most
-//      objects take their first try, so the chain has no block barrier);
+//   2. objects in order: up to 64 objects by one warp, tries in order (most
+//      take their first try, so the chain has no block barrier); more objects
+//      in windows of 8 tries, warp w testing try t0 + w; the first try that
+//      passed its static test and clears the objects already placed wins;
 //   3. every (robot try, sphere) pair of a window at once; the first window
 //      with a contact-free try decides.
 __device__ void reset_env(const ResetParams& P, int env, float4 (*s_cand)[kTryWindow], float4* so,
@@ -690,23 +692,59 @@ __device__ void reset_env(const ResetParams& P, int env, float4 (*s_cand)[kTryWi
   }
   if (tid == 0) s_robot_try = -1;
   __syncthreads();
-  // 2. objects in order, by warp 0 alone: tries in order (the first 8 from
-  // step 1, later ones evaluated by the warp), the warp's lanes splitting each
-  // try's test against the objects already placed; the first accepted try
-  // wins; after 64 failed tries the last one stands.  Most objects take their
-  // first try, so no block-wide barrier sits in this chain.
+  // 2. objects in order.  Up to kSerialPlaceMax objects (few collisions, most
+  // objects take their first try): one warp, tries in order, no block barrier
+  // in the chain.  More objects (crowded supports, many tries): windows of 8
+  // tries, one per warp, behind block barriers.  Both take the lowest accepted
+  // try; after 64 failed tries the last one stands.
   bool failed = false;
-  if (warp == 0) {
+  if (M <= kSerialPlaceMax) {
+    // warp 0: tries in order (the first 8 from step 1, later ones evaluated by
+    // the warp), its lanes splitting each try's test against the placed objects
+    if (warp == 0) {
+      for (int j = 0; j < M; ++j) {
+        const float rho = s_rho[j];
+        float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+        bool accepted = false;
+        for (int t = 0; t < 64 && !accepted; ++t) {
+          if (t < kTryWindow) {
+            c = s_cand[j][t];
+          } else {
+            const uint4 wv =
+                philox4x32_10(make_uint4((uint32_t)env, ep, (uint32_t)j, (uint32_t)t), key);
+            const float3 p = object_candidate(S, wv, rho, clear);
+            float d;
+            const bool sok = grid_query(S, p.x, p.y, p.z, d) && !(d < rho);
+            c = make_float4(p.x, p.y, p.z, sok ? 1.f : 0.f);
+          }
+          bool hit = false;
+          if (c.w > 0.5f)
+            for (int k = lane; k < j && !hit; k += 32) {
+              const float4 o = so[k];
+              const float dx = c.x - o.x, dy = c.y - o.y, dz = c.z - o.z, rr = rho + o.w;
+              hit = dx * dx + dy * dy + dz * dz < rr * rr;
+            }
+          accepted = c.w > 0.5f && !__any_sync(kFull, hit);
+        }
+        if (lane == 0) so[j] = make_float4(c.x, c.y, c.z, rho);
+        __syncwarp();
+        failed |= !accepted;
+      }
+    }
+    __syncthreads();
+  } else {
+    // in each window of tries warp w takes try t0 + w and its lanes split the
+    // test against the objects already placed
     for (int j = 0; j < M; ++j) {
       const float rho = s_rho[j];
-      float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
-      bool accepted = false;
-      for (int t = 0; t < 64 && !accepted; ++t) {
-        if (t < kTryWindow) {
-          c = s_cand[j][t];
+      int pick_t = -1;
+      for (int t0 = 0; t0 < 64 && pick_t < 0; t0 += kTryWindow) {
+        const int t = t0 + warp;
+        float4 c;
+        if (t0 == 0) {
+          c = s_cand[j][warp];
         } else {
-          const uint4 wv =
-              philox4x32_10(make_uint4((uint32_t)env, ep, (uint32_t)j, (uint32_t)t), key);
+          const uint4 wv = philox4x32_10(make_uint4((uint32_t)env, ep, (uint32_t)j, (uint32_t)t), key);
           const float3 p = object_candidate(S, wv, rho, clear);
           float d;
           const bool sok = grid_query(S, p.x, p.y, p.z, d) && !(d < rho);
@@ -719,14 +757,25 @@ __device__ void reset_env(const ResetParams& P, int env, float4 (*s_cand)[kTryWi
             const float dx = c.x - o.x, dy = c.y - o.y, dz = c.z - o.z, rr = rho + o.w;
             hit = dx * dx + dy * dy + dz * dz < rr * rr;
           }
-        accepted = c.w > 0.5f && !__any_sync(kFull, hit);
+        const bool ok = c.w > 0.5f && !__any_sync(kFull, hit);
+        if (lane == 0) s_cand[j][warp] = c;  // this window's candidates, for the pick below
+        if (tid == 0) s_bad = 0u;
+        __syncthreads();
+        if (lane == 0 && ok) atomicOr(&s_bad, 1u << warp);
+        __syncthreads();
+        const unsigned okw = s_bad;
+        if (okw) pick_t = t0 + __ffs(okw) - 1;
+        if (pick_t >= 0 || t0 + kTryWindow >= 64) {
+          const int w = pick_t >= 0 ? pick_t - t0 : kTryWindow - 1;
+          const float4 cc = s_cand[j][w];
+          if (tid == 0) so[j] = make_float4(cc.x, cc.y, cc.z, rho);
+        }
+        __syncthreads();
       }
-      if (lane == 0) so[j] = make_float4(c.x, c.y, c.z, rho);
-      __syncwarp();
-      failed |= !accepted;
+      failed |= pick_t < 0;
     }
+    __syncthreads();
   }
-  __syncthreads();
   if (P.bp) {  // the object broad-phase of this environment, rebuilt
     BpCell* grids = P.bp + (size_t)env * 4 * P.bp_cells;
     uint4* raw = reinterpret_cast<uint4*>(grids);
