@@ -177,7 +177,7 @@ def test_neural_rule_matches_oracle(two_rooms):
 
 def test_trained_network_agrees_with_the_grid(two_rooms):
     """Networks trained on each scene: the step's decisions against the
-    grid-only rule (the grid is the judge), and what the network gains over
+    grid-only rule (the grid is the reference), and what the network gains over
     the method without it: most static tests are decided by 116 KB of weights
     instead of gathers into the scene's distance grid."""
     gx, scenes, ss, orcs, B, Ps = two_rooms

@@ -1,6 +1,6 @@
 """Neural-SDF training on the tensor cores against the FP64 oracle: the sample
 stream, the loss gradient (forward, backward-data and weight-gradient
-kernels), the Adam update, and a short training run judged by the grid.
+kernels), the Adam update, and a short training run checked against the grid.
 
 Gradient tolerance.  Both sides round the same operands to BF16 (features,
 hidden activations, hidden-layer gradients); the kernels sum in FP32 where
