@@ -146,7 +146,7 @@ def test_training_fits_the_grid(setup):
     print(f"loss first {losses[0]:.4f} last {losses[-20:].mean():.4f}; 400 steps in {dt:.3f} s "
           f"(samples and workspace included)")
     assert losses[-20:].mean() < 0.5 * losses[0]
-    # held out: a different sample stream, judged by the FP64 grid
+    # held out: a different sample stream, compared with the FP64 grid
     pts, _ = ss.nsdf_samples(0, seed=99, first=0, n=4000)
     out = torch.empty(4000, dtype=torch.float32, device="cuda")
     ss.nsdf_query(0, pts, out)
