@@ -581,6 +581,21 @@ def main():
     # the timed region: actions in, the step's result (reward, success,
     # events) back; observations stay on the device for a GPU policy (the
     # paper's zero-copy hand-off).  Also timed: every output back to the host.
+    # A user's context: the step replayed as a CUDA graph, no per-kernel
+    # timing events, the rasteriser setting the autotuner picks for it.
+    sim.close()
+    sim = gx.Sim(ss, I.fetch_like_robot(), n, profile=0, use_graph=True, sdf_mode=sdf_mode,
+                 sdf_margin=w.sdf_margin, **sim_kw)
+    with torch.cuda.stream(stream):
+        sim.reset(stream=stream)
+        for t in range(args.warmup):
+            abuf.copy_(acts[t])
+            mbuf.copy_(mask_at(t))
+            sim.reset(mbuf, stream=stream)
+            sim.step(abuf, stream=stream)
+        if not args.no_autotune:
+            sim.autotune(abuf, steps=3, stream=stream)
+    torch.cuda.synchronize()
     full = sim.host_outputs(pinned=True)
     result = {k: (v if k in ("reward", "success", "event") else None) for k, v in full.items()}
     acts_h = torch.empty((n, 11), dtype=torch.float32, pin_memory=True)
