@@ -291,7 +291,7 @@ extern "C" gx_status gx_scene_set_create(const gx_scene_desc* scenes, int32_t n_
     DScene& ds = s->host[i];
     HostMeshlets hm;
     build_meshlets(d, hm);
-    s->meshlets_per_scene.push_back((int)(hm.hdr.size() / 3));
+    s->meshlets_per_scene.push_back((int)(hm.hdr.size() / kMeshletHdr));
     if (hm.verts.size() >= (1u << 24) || hm.tris.size() >= (1u << 24)) {
       free_set(s);
       return fail(nullptr, GX_EINVAL, "scene %d: more than 2^24 cluster vertices or triangles", i);
@@ -304,7 +304,7 @@ extern "C" gx_status gx_scene_set_create(const gx_scene_desc* scenes, int32_t n_
       return bail(e, "upload triangles");
     if ((e = upload(s, (uint32_t**)&ds.tri_rgb, hm.rgb.data(), hm.rgb.size())) != cudaSuccess)
       return bail(e, "upload colours");
-    ds.n_meshlets = (int)(hm.hdr.size() / 3);
+    ds.n_meshlets = (int)(hm.hdr.size() / kMeshletHdr);
     ds.n_tris = (int)hm.tris.size();
     if ((e = upload(s, (float**)&ds.supports, d.supports, (size_t)5 * d.n_supports)) != cudaSuccess)
       return bail(e, "upload supports");

@@ -21,11 +21,15 @@ namespace gx {
 constexpr int kMeshletMaxVerts = 64;
 constexpr int kMeshletMaxTris = 64;
 
-// Three float4 per meshlet:
+// Five float4 per meshlet (kMeshletHdr):
 //   [0] bounding sphere centre xyz, radius
 //   [1] normal-cone axis xyz, sin(half angle)   (cos < -0.5 disables the test)
 //   [2] cos(half angle), vertex offset (float4 units, as bits),
 //       triangle offset (as bits), n_verts | n_tris << 8 (as bits)
+//   [3] bounding box min xyz, min over the vertices of axis . p
+//   [4] bounding box max xyz, 1 when every face normal equals the axis
+//       (then the cluster is back-facing as a whole iff axis . eye <= [3].w)
+constexpr int kMeshletHdr = 5;
 struct DScene {
   const float4* mhdr;
   const float4* mverts;     // world positions, w unused

@@ -105,6 +105,12 @@ void build_meshlets(const gx_scene_desc& s, HostMeshlets& out) {
       }
     }
     if (cosang < -0.5) ax = {0, 0, 1};
+    // one face normal for the whole cluster (axis-aligned faces of boxes): the
+    // exact plane test applies; dmin is the smallest axis . p over its vertices
+    bool single_normal = al > 1e-12;
+    for (int t : cur_tris) single_normal = single_normal && dot(ax, nrm[t]) >= 1.0 - 1e-12;
+    double dmin = 1e300;
+    for (int gv : cur_verts) dmin = std::min(dmin, dot(ax, vert(gv)));
     for (int t : cur_tris) {
       uint32_t packed = 0;
       for (int k = 0; k < 3; ++k) packed |= (uint32_t)local[s.tris[3 * t + k]] << (8 * k);
@@ -127,6 +133,11 @@ void build_meshlets(const gx_scene_desc& s, HostMeshlets& out) {
     out.hdr.push_back(h0);
     out.hdr.push_back(h1);
     out.hdr.push_back(h2);
+    // the box of the (float) vertices: exact; dmin rounded down
+    out.hdr.push_back(make_float4((float)bl.x, (float)bl.y, (float)bl.z,
+                                  std::nextafter((float)dmin, -INFINITY)));
+    out.hdr.push_back(make_float4((float)bh.x, (float)bh.y, (float)bh.z,
+                                  single_normal ? 1.f : 0.f));
     cur_tris.clear();
     cur_verts.clear();
     local.clear();

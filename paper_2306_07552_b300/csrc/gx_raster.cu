@@ -185,6 +185,40 @@ __device__ __forceinline__ bool sphere_visible(const Cam& cm, const View& vw, fl
   return true;
 }
 
+// Bounding box (corners lo.xyz, hi.xyz) vs the view frustum: false when all
+// its corners lie outside one side plane or in front of the near plane (then
+// so do all the cluster's vertices, whose outcodes would reject every
+// triangle).  A plane n . (P - eye) >= 0 holds somewhere in the box iff it
+// holds at the corner n points to; a small relative margin keeps the test
+// conservative against rounding.
+__device__ __forceinline__ float plane_max(float nx, float ny, float nz, const Cam& cm, float4 lo,
+                                           float4 hi) {
+  const float px = nx >= 0.f ? hi.x : lo.x, py = ny >= 0.f ? hi.y : lo.y,
+              pz = nz >= 0.f ? hi.z : lo.z;
+  return nx * (px - cm.ex) + ny * (py - cm.ey) + nz * (pz - cm.ez);
+}
+
+__device__ __forceinline__ bool box_visible(const Cam& cm, const View& vw, float4 lo, float4 hi) {
+  const float ext = fabsf(hi.x - cm.ex) + fabsf(hi.y - cm.ey) + fabsf(hi.z - cm.ez) +
+                    fabsf(lo.x - cm.ex) + fabsf(lo.y - cm.ey) + fabsf(lo.z - cm.ez);
+  const float eps = 1e-5f * ext + 1e-5f;
+  // camera axes: right r, up u, forward f (rows of the view rotation)
+  if (plane_max(cm.fx, cm.fy, cm.fz, cm, lo, hi) < cm.near_ - eps) return false;
+  if (plane_max(cm.rx - vw.tl * cm.fx, cm.ry - vw.tl * cm.fy, cm.rz - vw.tl * cm.fz, cm, lo, hi) <
+      -eps * (1.f + fabsf(vw.tl)))
+    return false;
+  if (plane_max(vw.tr * cm.fx - cm.rx, vw.tr * cm.fy - cm.ry, vw.tr * cm.fz - cm.rz, cm, lo, hi) <
+      -eps * (1.f + fabsf(vw.tr)))
+    return false;
+  if (plane_max(vw.tt * cm.fx - cm.ux, vw.tt * cm.fy - cm.uy, vw.tt * cm.fz - cm.uz, cm, lo, hi) <
+      -eps * (1.f + fabsf(vw.tt)))
+    return false;
+  if (plane_max(cm.ux - vw.tb * cm.fx, cm.uy - vw.tb * cm.fy, cm.uz - vw.tb * cm.fz, cm, lo, hi) <
+      -eps * (1.f + fabsf(vw.tb)))
+    return false;
+  return true;
+}
+
 // Depth plane of a triangle: 1/z at pixel centre (u, v) equals
 // A (u - cx) + B (v - cy) + C, from the world-space plane through P0 with
 // normal n (h = n . (P0 - eye) < 0 for a front face).
@@ -573,10 +607,12 @@ __global__ void __launch_bounds__(kThreads, kRasterMinBlocks) raster_kernel(cons
       const int end = min(base + kListCap, S.n_meshlets);
       for (int m = base + tid; m < end; m += kThreads) {
         if (kCount) cn.v[kCntClustersTested]++;
-        const float4 h0 = __ldg(S.mhdr + 3 * m);
+        const float4* hd = S.mhdr + (size_t)kMeshletHdr * m;
+        const float4 h0 = __ldg(hd);
         bool vis = sphere_visible(cm, vw, h0.x, h0.y, h0.z, h0.w);
         if (vis) {
-          const float4 h1 = __ldg(S.mhdr + 3 * m + 1), h2 = __ldg(S.mhdr + 3 * m + 2);
+          const float4 h1 = __ldg(hd + 1), h2 = __ldg(hd + 2), h3 = __ldg(hd + 3),
+                       h4 = __ldg(hd + 4);
           if (h2.x > -0.5f) {  // normal cone: every face looks away from the eye
             const float vx = h0.x - cm.ex, vy = h0.y - cm.ey, vz = h0.z - cm.ez;
             const float av = h1.x * vx + h1.y * vy + h1.z * vz;
@@ -585,6 +621,13 @@ __global__ void __launch_bounds__(kThreads, kRasterMinBlocks) raster_kernel(cons
             const float cr = sqrtf(cx_ * cx_ + cy_ * cy_ + cz_ * cz_);
             if (av * h2.x - cr * h1.w > h0.w * 1.001f + 1e-4f) vis = false;
           }
+          // one face normal: back-facing as a whole when the eye is on the back
+          // side of (or on) every face's plane
+          if (vis && h4.w > 0.5f &&
+              h1.x * cm.ex + h1.y * cm.ey + h1.z * cm.ez <
+                  h3.w - 1e-4f - 1e-5f * (fabsf(cm.ex) + fabsf(cm.ey) + fabsf(cm.ez)))
+            vis = false;
+          if (vis) vis = box_visible(cm, vw, h3, h4);
           if (vis) {
             const uint32_t cnt = __float_as_uint(h2.w);
             list[atomicAdd(&ctr[1], 1)] =
