@@ -1,8 +1,10 @@
 // Host-side clustering of a scene's triangles into meshlets: at most 64
-// triangles and 64 distinct vertices per cluster, each with a bounding sphere
-// and a cone bounding its face normals.  A camera rejects a whole cluster when
-// the sphere is outside its view or every face in the cone faces away, so the
-// rasteriser only stages and sets up triangles that can be visible.
+// triangles and 64 distinct vertices per cluster, each with a bounding sphere,
+// a bounding box, a cone bounding its face normals and, when all its faces
+// share one normal, the smallest plane offset along it.  A camera rejects a
+// whole cluster when the sphere or the box is outside its view or every face
+// faces away, so the rasteriser only stages and sets up triangles that can be
+// visible.
 //
 // Clusters are formed greedily over triangles sorted by (dominant normal
 // direction, Morton code of the centroid), which keeps each cluster compact

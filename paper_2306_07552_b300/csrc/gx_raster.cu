@@ -13,11 +13,12 @@
 // observation rows and resets the slot for the CTA's next environment.
 //
 // Per environment, inside a CTA:
-//   1. each warp grabs 32 triangle clusters (meshlets) at a time, culls them
-//      lane-parallel against the view frustum and the cluster normal cone
-//      (whole clusters facing away), and keeps the survivors;
-//   2. lane 0 stages each surviving cluster's vertices, triangles and colours into the
-//      warp's shared buffers with bulk asynchronous copies (cp.async.bulk +
+//   1. the CTA culls the scene's triangle clusters (meshlets), one thread per
+//      cluster: bounding sphere and bounding box against the view frustum,
+//      the normal cone, and for a cluster whose faces share one normal the
+//      exact plane test (the eye behind every face), and lists the survivors;
+//   2. lane 0 of each warp stages a listed cluster's vertices, triangles and
+//      colours into the warp's shared buffers with bulk asynchronous copies (cp.async.bulk +
 //      mbarrier), double-buffered so the next cluster streams in while the
 //      current one is rasterised; warps never wait for each other until the
 //      resolve;
