@@ -32,6 +32,7 @@ struct gx_ctx {
   int* d_order = nullptr;              // environments, costliest scene first
   int sms = 0;
   unsigned long long* d_fb = nullptr;  // rasteriser framebuffer slots
+  uint32_t* d_fb_epoch = nullptr;      // epoch of each slot's keys
   int* d_raster_work = nullptr;
   float near_ = 0.05f;
   Robot* d_robot = nullptr;
@@ -222,6 +223,7 @@ void enqueue_step(gx_ctx* c, const float* actions, const gx_outputs& out, cudaSt
   rp.H = c->cfg.img_h;
   rp.big_px = c->big_px;
   rp.fb_slots = c->d_fb;
+  rp.fb_epoch = c->d_fb_epoch;
   rp.n_slots = c->raster_ctas;
   rp.order = c->order_mode ? c->d_order : nullptr;
   rp.work = c->d_raster_work;
@@ -473,6 +475,9 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
     const size_t fb_bytes = (size_t)x->n_slots * c.img_w * c.img_h * 8;
     if ((e = cudaMalloc(&x->d_fb, fb_bytes)) != cudaSuccess) return bail(e, "fb slots");
     if ((e = cudaMemset(x->d_fb, 0xff, fb_bytes)) != cudaSuccess) return bail(e, "fb slots");
+    if ((e = cudaMalloc(&x->d_fb_epoch, x->n_slots * sizeof(uint32_t))) != cudaSuccess ||
+        (e = cudaMemset(x->d_fb_epoch, 0, x->n_slots * sizeof(uint32_t))) != cudaSuccess)
+      return bail(e, "fb epochs");
     if ((e = cudaMalloc(&x->d_raster_work, sizeof(int))) != cudaSuccess) return bail(e, "work");
     if ((e = cudaMemset(x->d_raster_work, 0, sizeof(int))) != cudaSuccess) return bail(e, "work");
   }
@@ -611,6 +616,7 @@ extern "C" void gx_destroy(gx_ctx* x) {
   cudaFree(x->d_state);
   cudaFree(x->d_cam);
   cudaFree(x->d_fb);
+  cudaFree(x->d_fb_epoch);
   cudaFree(x->d_raster_work);
   cudaFree(x->d_err);
   if (x->h_err) cudaFreeHost(x->h_err);

@@ -156,7 +156,8 @@ constexpr int kRasterMinBlocks = 3;
 struct RasterParams {
   int n, M, W, H;
   int big_px;                    // larger bounding boxes go to the warp scan
-  unsigned long long* fb_slots;  // [n_slots][H][W] keys, all ~0 between launches
+  unsigned long long* fb_slots;  // [n_slots][H][W] keys
+  uint32_t* fb_epoch;            // [n_slots] epoch of each slot's keys (NULL: slots cleared)
   int n_slots;                   // = grid size
   int* work;                     // environment counter, zeroed before each launch
   const int* order;              // optional: k-th environment to render (costliest first)

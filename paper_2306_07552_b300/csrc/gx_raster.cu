@@ -6,11 +6,14 @@
 // once) pulls environments from a work counter.  Each CTA owns one
 // framebuffer slot in global memory (L2-resident: slots x W x H x 8 bytes)
 // of 64-bit keys
-//     key = (~bits(1/z) << 32) | colour (0xRRGGBB of the triangle),
+//     key = (255 - epoch) << 56 | ~bits(1/z) << 24 | colour (0xRRGGBB),
 // updated with fire-and-forget atomicMin reductions, so the nearest fragment
 // wins and exact depth ties go to the lower colour value, independently of
-// visiting order; the resolve needs no lookup for the colour.  The resolve of an environment reads its slot, writes the
-// observation rows and resets the slot for the CTA's next environment.
+// visiting order; the resolve needs no lookup for the colour.  Each
+// environment a CTA draws takes the slot's next epoch, whose keys outrank
+// every older key, so the slot is never cleared between environments (only
+// when the 8-bit epoch wraps, every 255 environments).  The resolve of an
+// environment reads its slot and writes the observation rows.
 //
 // Per environment, inside a CTA:
 //   1. the CTA culls the scene's triangle clusters (meshlets), one thread per
@@ -96,6 +99,7 @@ struct View {
   int W, H;
   unsigned long long* fb;  // this CTA's slot, [H][W]
   uint64_t pol;            // L2 policy keeping the slot resident
+  unsigned long long tag;  // this environment's epoch field, (255 - epoch) << 56
   // side planes of the frustum as slopes x/z, y/z, with 1/|n|
   float tl, tr, tt, tb, kl, kr, kt, kb;
 };
@@ -155,7 +159,7 @@ __device__ __forceinline__ void frag_key(const View& vw, unsigned long long* fbp
   if (kCount) cn.v[kCntFragments]++;
   invz = fmaxf(invz, 1e-30f);
   const unsigned long long key =
-      ((unsigned long long)(~__float_as_uint(invz)) << 32) | (unsigned long long)rgb;
+      vw.tag | ((unsigned long long)(~__float_as_uint(invz)) << 24) | (unsigned long long)rgb;
   // fire-and-forget reduction in L2, the slot marked to stay resident there
   asm volatile("red.relaxed.gpu.global.min.L2::cache_hint.u64 [%0], %1, %2;" ::"l"(fbp),
                "l"(key), "l"(vw.pol)
@@ -557,6 +561,7 @@ __global__ void __launch_bounds__(kThreads, kRasterMinBlocks) raster_kernel(cons
   vw.W = W;
   vw.H = H;
   vw.fb = P.fb_slots + (size_t)blockIdx.x * npix;
+  uint32_t epoch = P.fb_epoch ? P.fb_epoch[blockIdx.x] : 0u;  // slot epochs persist across launches
   // the slot stays in L2 while observations stream through it
   asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(vw.pol));
   if (lane == 0) {
@@ -575,6 +580,19 @@ __global__ void __launch_bounds__(kThreads, kRasterMinBlocks) raster_kernel(cons
     __syncthreads();
     const int env = ctr[0];
     if (env >= P.n) break;
+    // a new epoch for this slot: its keys outrank every older key, so the slot
+    // needs no clearing between environments; every 255 environments it wraps
+    // and is cleared once
+    if (++epoch == 256u) {
+      for (int p = tid * 2; p < npix; p += kThreads * 2)
+        asm volatile("st.global.cg.L2::cache_hint.v2.u64 [%0], {%1, %1}, %2;" ::"l"(vw.fb + p),
+                     "l"(~0ull), "l"(vw.pol)
+                     : "memory");
+      __threadfence();
+      __syncthreads();
+      epoch = 1u;
+    }
+    vw.tag = (unsigned long long)(255u - epoch) << 56;
     const DScene& S = P.scenes[P.env_scene[env]];
     Cam cm;
     {
@@ -699,7 +717,8 @@ __global__ void __launch_bounds__(kThreads, kRasterMinBlocks) raster_kernel(cons
     __syncthreads();
 
     // resolve four pixels per thread: 16-byte streaming stores, row-major; the
-    // slot is read from L2 and reset for this CTA's next environment
+    // slot is read from L2 and left as it is (the next environment's keys carry
+    // a newer epoch); keys of older epochs are background
     const size_t out0 = (size_t)env * npix;
     for (int p = tid * 4; p < npix; p += kThreads * 4) {
       unsigned long long keys[4];
@@ -707,18 +726,15 @@ __global__ void __launch_bounds__(kThreads, kRasterMinBlocks) raster_kernel(cons
                    : "=l"(keys[0]), "=l"(keys[1]) : "l"(vw.fb + p), "l"(vw.pol));
       asm volatile("ld.global.cg.L2::cache_hint.v2.u64 {%0, %1}, [%2], %3;"
                    : "=l"(keys[2]), "=l"(keys[3]) : "l"(vw.fb + p + 2), "l"(vw.pol));
-      asm volatile("st.global.cg.L2::cache_hint.v2.u64 [%0], {%1, %1}, %2;"
-                   :: "l"(vw.fb + p), "l"(~0ull), "l"(vw.pol) : "memory");
-      asm volatile("st.global.cg.L2::cache_hint.v2.u64 [%0], {%1, %1}, %2;"
-                   :: "l"(vw.fb + p + 2), "l"(~0ull), "l"(vw.pol) : "memory");
+
       float z[4];
       uint32_t col[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         z[k] = 0.f;
         col[k] = 0u;
-        if (keys[k] != ~0ull) {
-          const float invz = __uint_as_float(~(uint32_t)(keys[k] >> 32));
+        if ((keys[k] & (0xffull << 56)) == vw.tag) {  // written in this epoch
+          const float invz = __uint_as_float(~(uint32_t)(keys[k] >> 24));
           z[k] = __frcp_rn(invz);
           col[k] = (uint32_t)keys[k] & 0xffffffu;  // the winner's colour rides in the key
         }
@@ -750,6 +766,7 @@ __global__ void __launch_bounds__(kThreads, kRasterMinBlocks) raster_kernel(cons
     }
     __syncthreads();
   }
+  if (P.fb_epoch && tid == 0) P.fb_epoch[blockIdx.x] = epoch;
   if (kCount) {
     for (int k = 0; k < kRasterCounters; ++k) {
       unsigned long long v = cn.v[k];
