@@ -20,6 +20,11 @@ namespace gx {
 
 namespace {
 
+// Largest bounding-box diagonal of a cluster (m).  Measured on the apartment
+// workload (raster ms per step): no limit 1.33, 8 m 1.31, 5 m 1.29, 4 m 1.27,
+// 3 m 1.27, 2 m 1.33, 1 m 2.10 (many small clusters to stage).
+constexpr double kMaxClusterExtent = 4.0;
+
 uint32_t part1by2(uint32_t x) {
   x &= 0x3ff;
   x = (x | (x << 16)) & 0x030000ff;
@@ -144,14 +149,35 @@ void build_meshlets(const gx_scene_desc& s, HostMeshlets& out) {
     cur_verts.clear();
     local.clear();
   };
+  V3 clo{1e30, 1e30, 1e30}, chi{-1e30, -1e30, -1e30};  // box of the open cluster
   for (int t : order) {
     int need = 0;
     for (int k = 0; k < 3; ++k) need += local.count(s.tris[3 * t + k]) ? 0 : 1;
     // keep vertex, triangle and direction-bucket limits per cluster
     bool dir_change = !cur_tris.empty() && (key[cur_tris[0]] >> 32) != (key[t] >> 32);
+    // and a bounded extent: a cluster stretched across a whole apartment (a
+    // floor or wall strip) is seldom culled by its bounding volumes
+    bool too_wide = false;
+    if (!cur_tris.empty()) {
+      V3 lo2 = clo, hi2 = chi;
+      for (int k = 0; k < 3; ++k) {
+        V3 p = vert(s.tris[3 * t + k]);
+        lo2 = {std::min(lo2.x, p.x), std::min(lo2.y, p.y), std::min(lo2.z, p.z)};
+        hi2 = {std::max(hi2.x, p.x), std::max(hi2.y, p.y), std::max(hi2.z, p.z)};
+      }
+      too_wide = norm(sub(hi2, lo2)) > kMaxClusterExtent;
+    }
     if ((int)cur_tris.size() == kMeshletMaxTris ||
-        (int)cur_verts.size() + need > kMeshletMaxVerts || dir_change)
+        (int)cur_verts.size() + need > kMeshletMaxVerts || dir_change || too_wide) {
       flush();
+      clo = {1e30, 1e30, 1e30};
+      chi = {-1e30, -1e30, -1e30};
+    }
+    for (int k = 0; k < 3; ++k) {
+      V3 p = vert(s.tris[3 * t + k]);
+      clo = {std::min(clo.x, p.x), std::min(clo.y, p.y), std::min(clo.z, p.z)};
+      chi = {std::max(chi.x, p.x), std::max(chi.y, p.y), std::max(chi.z, p.z)};
+    }
     for (int k = 0; k < 3; ++k) {
       int gv = s.tris[3 * t + k];
       if (!local.count(gv)) {
