@@ -224,6 +224,18 @@ __device__ __forceinline__ bool box_visible(const Cam& cm, const View& vw, float
   return true;
 }
 
+// Reciprocal by the hardware approximation (PTX rcp.approx.f32, within 1 ulp).
+// Every use tolerates it: depth-plane coefficients and the resolved depth stay
+// within a few ulp (the depth tolerance is 1e-5 relative); a projected vertex
+// moves by far less than its 1/256-pixel snapping step; and the row of an
+// expansion slot, floor((r + 0.5) / runs), keeps at least 1/128 between its
+// argument and an integer for the at most 64 four-pixel runs of a row.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // Depth plane of a triangle: 1/z at pixel centre (u, v) equals
 // A (u - cx) + B (v - cy) + C, from the world-space plane through P0 with
 // normal n (h = n . (P0 - eye) < 0 for a front face).
@@ -233,14 +245,14 @@ __device__ __forceinline__ void depth_plane(const Cam& cm, float nx, float ny, f
   const float ncy = cm.ux * nx + cm.uy * ny + cm.uz * nz;
   const float ncz = cm.fx * nx + cm.fy * ny + cm.fz * nz;
   // one reciprocal: 1/z = (ncx u - ncy v) / (h f) + ncz / h at pixel offset (u, v)
-  const float s = __frcp_rn(h * cm.f);
+  const float s = rcp_approx(h * cm.f);
   A = ncx * s;
   B = -ncy * s;
   C = (ncz * cm.f) * s;
 }
 
 __device__ __forceinline__ int2 project_fix(const Cam& cm, float xc, float yc, float zc) {
-  const float iz = __frcp_rn(zc);
+  const float iz = rcp_approx(zc);
   const float px = fminf(fmaxf(xc * iz, -1000.f), 1000.f);
   const float py = fminf(fmaxf(yc * iz, -1000.f), 1000.f);
   return make_int2(__float2int_rn(fmaf(cm.f, px, cm.cx) * 256.f),
@@ -442,7 +454,7 @@ __device__ void raster_cluster(const View& vw, const Cam& cm, WarpSmem& ws, int 
                   r4[1] = make_int4(sx[0], sx[1], sx[2], bw);
                   r4[2] = make_int4(sy[0], sy[1], sy[2], (int)ws.cbuf[buf][t]);
                   r4[3] = make_int4(__float_as_int(A), __float_as_int(B), __float_as_int(C), 0);
-                  ws.q[lane].inv_bp = __frcp_rn((float)((bw + kSpan - 1) / kSpan));
+                  ws.q[lane].inv_bp = rcp_approx((float)((bw + kSpan - 1) / kSpan));
                   npx = ((bw + kSpan - 1) / kSpan) * bh;  // expansion slots: pixel runs
                   if (kCount) {
                     cn.v[kCntTrisSmall]++;
@@ -735,7 +747,7 @@ __global__ void __launch_bounds__(kThreads, kRasterMinBlocks) raster_kernel(cons
         col[k] = 0u;
         if ((keys[k] & (0xffull << 56)) == vw.tag) {  // written in this epoch
           const float invz = __uint_as_float(~(uint32_t)(keys[k] >> 24));
-          z[k] = __frcp_rn(invz);
+          z[k] = rcp_approx(invz);
           col[k] = (uint32_t)keys[k] & 0xffffffu;  // the winner's colour rides in the key
         }
       }
