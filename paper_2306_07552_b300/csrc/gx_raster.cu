@@ -763,13 +763,11 @@ __global__ void __launch_bounds__(kThreads, kRasterMinBlocks) raster_kernel(cons
       }
       if (P.rgb) {
         // 4 pixels = 12 bytes R G B R G B ... packed into three words
+        // (one byte permutation per word: colours are 0x00RRGGBB)
         const uint32_t r0 = col[0], r1 = col[1], r2 = col[2], r3 = col[3];
-        const uint32_t w0 = ((r0 >> 16) & 0xff) | (((r0 >> 8) & 0xff) << 8) | ((r0 & 0xff) << 16) |
-                            (((r1 >> 16) & 0xff) << 24);
-        const uint32_t w1 = ((r1 >> 8) & 0xff) | ((r1 & 0xff) << 8) | (((r2 >> 16) & 0xff) << 16) |
-                            (((r2 >> 8) & 0xff) << 24);
-        const uint32_t w2 = (r2 & 0xff) | (((r3 >> 16) & 0xff) << 8) | (((r3 >> 8) & 0xff) << 16) |
-                            ((r3 & 0xff) << 24);
+        const uint32_t w0 = __byte_perm(r0, r1, 0x6012);  // R0 G0 B0 R1
+        const uint32_t w1 = __byte_perm(r1, r2, 0x5601);  // G1 B1 R2 G2
+        const uint32_t w2 = __byte_perm(r2, r3, 0x4560);  // B2 R3 G3 B3
         unsigned int* o = reinterpret_cast<unsigned int*>(P.rgb + (out0 + p) * 3);
         __stcs(o, w0);
         __stcs(o + 1, w1);
