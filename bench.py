@@ -125,9 +125,10 @@ def raster_work(workload):
     return golden(f"raster_work_{SAME_VIEWS.get(base, base)}.json")
 
 
-def kernel_traffic(workload):
-    """DRAM bytes per rasteriser launch scaled to the full workload from an
-    ncu capture of a smaller case; None once the rasteriser source changed."""
+def kernel_capture(workload):
+    """Per-launch figures of the rasteriser (DRAM bytes, warp instructions)
+    scaled to the full workload from an ncu capture of a smaller case; None
+    once the rasteriser source changed since the capture."""
     p = os.path.join(ROOT, "profiles", f"raster_{SAME_VIEWS.get(workload, workload)}_traffic.json")
     if not os.path.exists(p):
         return None
@@ -135,7 +136,12 @@ def kernel_traffic(workload):
     src = open(os.path.join(ROOT, "paper_2306_07552_b300", "csrc", "gx_raster.cu"), "rb").read()
     if d.get("source_sha1") != hashlib.sha1(src).hexdigest():
         return None
-    return d.get("bytes_per_launch_full")
+    return d
+
+
+def kernel_traffic(workload):
+    d = kernel_capture(workload)
+    return d.get("bytes_per_launch_full") if d else None
 
 
 def measured_peaks():
@@ -665,6 +671,17 @@ def main():
             at_loaded = {"sm_mhz": loaded, "peak": p_l, "frac": achieved / p_l,
                          "note": "peak at the median SM clock of a seconds-long dense load "
                                  "(MEASURED_PEAKS.json); this run's own clocks are in 'clocks'"}
+        # the rasteriser is instruction-bound: warp instructions issued per
+        # second against 4 schedulers x 1 instruction per cycle per SM
+        cap = kernel_capture(w.name)
+        issue = None
+        if cap and cap.get("warp_inst_per_launch_full"):
+            rate = cap["warp_inst_per_launch_full"] / (launch_ms / 1e3) / 1e9
+            pk = sms * 4 * sm_mhz * 1e6 / 1e9
+            issue = {"warp_inst_per_launch": cap["warp_inst_per_launch_full"],
+                     "achieved_ginst_s": rate, "peak_ginst_s": pk, "frac": rate / pk,
+                     "note": "instructions from the ncu capture, scaled per environment; "
+                             "the issue slots the kernel's own instruction stream fills"}
         obs = n * w.img * w.img * ((2 if w.depth_fp16 else 4) + (3 if w.rgb else 0))
         roof = {"bound": "alu", "kernel": "raster_kernel", "achieved": achieved, "peak": peak,
                 "unit": "Tops/s (FP32/INT32 lane ops)",
@@ -675,6 +692,7 @@ def main():
                 "at_loaded_clock": at_loaded, "no_culling_bound": no_cull,
                 "work_basis": f"{C_TRI} ops per front-facing triangle reaching the image + "
                               f"{C_FRAG} per covered fragment; counts per view from the oracle",
+                "issue_view": issue,
                 "hbm_view": {"bytes_per_launch": obs,
                              "achieved_gbs": obs / (launch_ms / 1e3) / 1e9,
                              "peak_gbs": hbm_peak, "peak_source": peak_src,
