@@ -176,10 +176,11 @@ __device__ bool snap_down(const DScene& s, const float p[3], float target, float
   return false;
 }
 
-// Eight blocks per SM (64 registers, a few spilled): the kernel waits on
-// random grid gathers, and the extra resident warps hide more of that latency
-// than the spills cost (0.050 -> 0.044 ms for 4096 environments).
-__global__ void __launch_bounds__(32 * kEnvsPerBlock, 8) physics_kernel(const PhysicsParams P) {
+// Seven blocks per SM (72 registers, a few spilled): the kernel waits on
+// random grid gathers, and resident warps hide that latency; six blocks (80
+// registers), seven and eight (64) measured 0.051, 0.043 and 0.044 ms for
+// 4096 environments.
+__global__ void __launch_bounds__(32 * kEnvsPerBlock, 7) physics_kernel(const PhysicsParams P) {
   __shared__ float4 s_obj[kEnvsPerBlock][GX_MAX_OBJECTS];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int env = blockIdx.x * kEnvsPerBlock + w;
