@@ -702,7 +702,8 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic (procedural apartments standing in for ReplicaCAD; see DESIGN.md)",
+        "data": "synthetic (procedural apartments standing in for ReplicaCAD scenes, spheres for "
+                "YCB objects, random actions for policy actions)",
         "config": {**config_of(w), "heuristics": {"sliding": bool(args.heuristics & 1),
                                                   "object_placing": bool(args.heuristics & 2)},
                    "robot_body_rendered": bool(args.render_robot),

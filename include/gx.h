@@ -428,16 +428,33 @@ int32_t gx_column_spans(const gx_scene_set* set, int32_t scene, int32_t radius_i
  * forward, then the eye position; obj [n][n_objects][4] object centre and
  * radius.  Outputs: depth [n][img_h][img_w] float32 (or half when depth_fp16),
  * rgb [n][img_h][img_w][3] (optional).  Image sides must be multiples of 32
- * and at most 256 (larger sizes return GX_EINVAL); n_objects <= 256.
+ * and at most 256 (larger sizes return GX_EINVAL); n_objects <= 256.  The
+ * scene set must live on the current device (else GX_EINVAL).  The images
+ * are those of a gx_step with render_robot 0: scene triangles and the
+ * objects given, not the robot body.
  * The first call on a device (the current one) sets the scratch up
  * synchronously; make that first call before any stream capture.  Every call
  * shares the same scratch and clears what it needs at the start, so calls
  * that overlap on the GPU (other streams, other host threads) race: order
- * them on one stream.  Asynchronous on `stream` after the first call. */
+ * them on one stream.  Asynchronous on `stream` after the first call.
+ * Problems only the device sees are recorded in an error word inside the
+ * scratch and accumulate over calls until gx_render_noalloc_error reads
+ * them: an env_scene value outside [0, n_scenes) draws that environment
+ * empty (depth 0, RGB 0) and sets GX_NOALLOC_BAD_SCENE; a bounded wait that
+ * gave up leaves some images incomplete and sets GX_NOALLOC_WAIT_TIMEOUT. */
 gx_status gx_render_noalloc(const gx_scene_set* set, int32_t n, const int32_t* env_scene,
                             const float* cam, const float* obj, int32_t n_objects, int32_t img_w,
                             int32_t img_h, float cam_near, void* depth, int32_t depth_fp16,
                             uint8_t* rgb, void* stream);
+
+/* Device error bits of gx_render_noalloc calls on the current device since
+ * the previous query: waits for the whole device (every stream), copies the
+ * word into *bits (may be NULL), clears it, and returns GX_EDEVICE with a
+ * message when any bit is set, GX_OK otherwise (also before any call).
+ * Allocates nothing. */
+#define GX_NOALLOC_WAIT_TIMEOUT 0x100u
+#define GX_NOALLOC_BAD_SCENE 0x200u
+gx_status gx_render_noalloc_error(uint32_t* bits);
 
 const char* gx_last_error(const gx_ctx* ctx);
 

@@ -149,7 +149,8 @@ def _p(a, t):
 class Oracle:
     """FP64 oracle bound to one robot, one scene and the instanced object mesh."""
 
-    # rasteriser ambiguity band and depth tolerance (see DESIGN.md, "Readings")
+    # rasteriser ambiguity band (1/64 px), relative depth tolerance and the
+    # smallest |cos| of a hit that is not flagged as grazing
     EPS_PX = 1.0 / 64.0
     TOL_REL = 1e-5
     COS_MIN = 0.05

@@ -133,10 +133,11 @@ gx_status poll_device_error(gx_ctx* c, bool wait) {
     // a crowded reset keeping an object's last try is reported by
     // gx_device_error but does not fail the call
     if ((v & ~GX_DEV_PLACEMENT_FAILED) == 0) return GX_OK;
-    return fail(c, GX_EDEVICE, "device error word 0x%x:%s%s%s", v,
+    return fail(c, GX_EDEVICE, "device error word 0x%x:%s%s%s%s", v,
                 (v & GX_DEV_NONFINITE_ACTION) ? " non-finite action (used 0)" : "",
                 (v & GX_DEV_PLACEMENT_FAILED) ? " reset placement used all tries" : "",
-                (v & kErrWaitTimeout) ? " bounded wait gave up" : "");
+                (v & kErrWaitTimeout) ? " bounded wait gave up" : "",
+                (v & kErrBadScene) ? " scene index out of range" : "");
   }
   return GX_OK;
 }
@@ -228,6 +229,7 @@ void enqueue_step(gx_ctx* c, const float* actions, const gx_outputs& out, cudaSt
   rp.order = c->order_mode ? c->d_order : nullptr;
   rp.work = c->d_raster_work;
   rp.scenes = c->set->d_scenes;
+  rp.n_scenes = c->set->n;
   rp.env_scene = c->d_env_scene;
   rp.cam = c->d_cam;
   rp.obj = c->st.obj;
@@ -288,6 +290,7 @@ extern "C" gx_status gx_scene_set_create(const gx_scene_desc* scenes, int32_t n_
                 cudaGetErrorString(e));
   };
   cudaError_t e;
+  if ((e = cudaGetDevice(&s->device)) != cudaSuccess) return bail(e, "current device");
   for (int i = 0; i < n_scenes; ++i) {
     const gx_scene_desc& d = scenes[i];
     DScene& ds = s->host[i];
@@ -981,6 +984,7 @@ bool gx::scene_set_view(const gx_scene_set* set, SceneSetView* out) {
   out->omesh_nv = set->omesh_nv;
   out->omesh_nt = set->omesh_nt;
   out->obj_rgb = set->obj_rgb;
+  out->device = set->device;
   return true;
 }
 

@@ -162,6 +162,7 @@ struct RasterParams {
   int* work;                     // environment counter, zeroed before each launch
   const int* order;              // optional: k-th environment to render (costliest first)
   const DScene* scenes;
+  int n_scenes;                  // env_scene values outside [0, n_scenes) are refused
   const int* env_scene;
   const float* cam;        // [n][12]
   const float4* obj;       // [n][M]
@@ -244,6 +245,7 @@ struct gx_scene_set {
   std::vector<int> meshlets_per_scene;
   std::vector<gx::NsdfScene> nsdf;
   std::vector<size_t> column_bytes;  // column grid size per scene
+  int device = -1;                   // CUDA device current at creation (holds every buffer)
 };
 
 namespace gx {
@@ -272,6 +274,7 @@ struct SceneSetView {
   const uint32_t* omesh_t;
   int omesh_nv, omesh_nt;
   const uint32_t* obj_rgb;
+  int device;                         // CUDA device holding the set's buffers
 };
 bool scene_set_view(const gx_scene_set* set, SceneSetView* out);
 gx_status set_last_error(gx_status s, const char* msg);
@@ -291,5 +294,6 @@ void launch_grid_build(float* grid, const float* boxes, int n_boxes, float ox, f
 
 // device error bits beyond the public ones
 constexpr unsigned kErrWaitTimeout = 0x100u;  // a bounded mbarrier wait gave up
+constexpr unsigned kErrBadScene = 0x200u;     // a scene index outside the set (env drawn empty)
 
 }  // namespace gx

@@ -44,6 +44,7 @@
 #include <math_constants.h>
 #include <cuda_fp16.h>
 
+#include <cstdio>
 #include <mutex>
 
 #include "gx_internal.h"
@@ -605,7 +606,13 @@ __global__ void __launch_bounds__(kThreads, kRasterMinBlocks) raster_kernel(cons
       epoch = 1u;
     }
     vw.tag = (unsigned long long)(255u - epoch) << 56;
-    const DScene& S = P.scenes[P.env_scene[env]];
+    // a scene index outside the set is refused before any scene data is
+    // read: the environment is drawn empty (no clusters, no objects), so its
+    // images resolve to background, and an error bit is set
+    const int scene = P.env_scene[env];
+    const bool scene_ok = (unsigned)scene < (unsigned)P.n_scenes;
+    if (!scene_ok && tid == 0) atomicOr(P.err, kErrBadScene);
+    const DScene& S = P.scenes[scene_ok ? scene : 0];
     Cam cm;
     {
       const float* c = P.cam + (size_t)env * 12;
@@ -627,7 +634,7 @@ __global__ void __launch_bounds__(kThreads, kRasterMinBlocks) raster_kernel(cons
     vw.kt = rsqrtf(1.f + vw.tt * vw.tt);
     vw.kb = rsqrtf(1.f + vw.tb * vw.tb);
 
-    for (int base = 0; base < S.n_meshlets || base == 0; base += kListCap) {
+    for (int base = 0; scene_ok && (base < S.n_meshlets || base == 0); base += kListCap) {
       if (tid == 0) {
         ctr[1] = 0;
         ctr[2] = 0;
@@ -833,6 +840,8 @@ namespace gx {
 namespace {
 
 constexpr size_t kNoAllocFbBytes = 16u << 20;  // framebuffer slots (16 MiB)
+static_assert(kErrWaitTimeout == GX_NOALLOC_WAIT_TIMEOUT && kErrBadScene == GX_NOALLOC_BAD_SCENE,
+              "public error bits of gx_render_noalloc");
 constexpr int kNoAllocMaxSide = 256;           // largest image side it accepts
 
 // [0, kNoAllocFbBytes): framebuffer slots; then the work counter and a spare
@@ -874,6 +883,10 @@ extern "C" gx_status gx_render_noalloc(const gx_scene_set* set, int32_t n,
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
     return set_last_error(GX_ECUDA, "gx_render_noalloc: no usable current device");
+  if (dev != sv.device)
+    return set_last_error(GX_EINVAL,
+                          "gx_render_noalloc: the scene set lives on another device than the "
+                          "current one");
   NoAllocDevice& d = g_noalloc[dev];
   {
     // one-time set-up on this device (the current one): find the array's
@@ -903,8 +916,9 @@ extern "C" gx_status gx_render_noalloc(const gx_scene_set* set, int32_t n,
   cudaStream_t s = (cudaStream_t)stream;
   int* work = reinterpret_cast<int*>(d.base + kNoAllocFbBytes);
   unsigned* err = reinterpret_cast<unsigned*>(d.base + kNoAllocFbBytes + 4);
-  // shared by every call: start from a zero work counter and empty keys
-  if ((e = cudaMemsetAsync(work, 0, 8, s)) != cudaSuccess ||
+  // shared by every call: start from a zero work counter and empty keys; the
+  // error word keeps accumulating until gx_render_noalloc_error reads it
+  if ((e = cudaMemsetAsync(work, 0, 4, s)) != cudaSuccess ||
       (e = cudaMemsetAsync(d.base, 0xff, (size_t)slots * slot_bytes, s)) != cudaSuccess)
     return set_last_error(GX_ECUDA, "gx_render_noalloc: clearing the scratch failed");
   RasterParams rp{};
@@ -917,6 +931,7 @@ extern "C" gx_status gx_render_noalloc(const gx_scene_set* set, int32_t n,
   rp.n_slots = slots;
   rp.work = work;
   rp.scenes = sv.scenes;
+  rp.n_scenes = sv.n;
   rp.env_scene = env_scene;
   rp.cam = cam;
   rp.obj = reinterpret_cast<const float4*>(obj);
@@ -935,4 +950,33 @@ extern "C" gx_status gx_render_noalloc(const gx_scene_set* set, int32_t n,
   if ((e = cudaGetLastError()) != cudaSuccess)
     return set_last_error(GX_ECUDA, "gx_render_noalloc: launch failed");
   return GX_OK;
+}
+
+extern "C" gx_status gx_render_noalloc_error(uint32_t* bits) {
+  using namespace gx;
+  if (bits) *bits = 0;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+    return set_last_error(GX_ECUDA, "gx_render_noalloc_error: no usable current device");
+  unsigned char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (g_noalloc[dev].ready) base = g_noalloc[dev].base;
+  }
+  if (!base) return GX_OK;  // no call has run on this device: nothing to report
+  unsigned* err = reinterpret_cast<unsigned*>(base + kNoAllocFbBytes + 4);
+  unsigned v = 0;
+  // every earlier call must have finished, on whatever stream it was issued
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess ||
+      (e = cudaMemcpy(&v, err, sizeof(v), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+      (e = cudaMemset(err, 0, sizeof(v))) != cudaSuccess)
+    return set_last_error(GX_ECUDA, "gx_render_noalloc_error: reading the error word failed");
+  if (bits) *bits = v;
+  if (v == 0) return GX_OK;
+  char msg[200];
+  snprintf(msg, sizeof(msg), "gx_render_noalloc: device error 0x%x:%s%s", v,
+           (v & kErrBadScene) ? " scene index out of range (environment drawn empty)" : "",
+           (v & kErrWaitTimeout) ? " bounded wait gave up (images incomplete)" : "");
+  return set_last_error(GX_EDEVICE, msg);
 }

@@ -21,13 +21,16 @@ SO_PATH = os.path.join(_HERE, "libgx.so")
 GX_OK, GX_EINVAL, GX_ENOMEM, GX_ECUDA, GX_EDEVICE, GX_ESTATE = range(6)
 GX_DEV_NONFINITE_ACTION = 0x1
 GX_DEV_PLACEMENT_FAILED = 0x2
+GX_NOALLOC_WAIT_TIMEOUT = 0x100
+GX_NOALLOC_BAD_SCENE = 0x200
 MAX_OBJECTS = 256
 MAX_SPHERES = 31
 
 SYMBOLS = ["gx_scene_set_create", "gx_scene_set_destroy", "gx_create", "gx_destroy", "gx_reset",
            "gx_step", "gx_step_host", "gx_sync", "gx_device_error", "gx_state_bytes",
            "gx_save_state", "gx_load_state", "gx_state_layout", "gx_phase_times",
-           "gx_raster_counters", "gx_render_noalloc", "gx_nsdf_set_weights",
+           "gx_raster_counters", "gx_render_noalloc", "gx_render_noalloc_error",
+           "gx_nsdf_set_weights",
            "gx_nsdf_get_weights", "gx_nsdf_query", "gx_nsdf_get_master", "gx_nsdf_samples",
            "gx_nsdf_grad",
            "gx_nsdf_train", "gx_nsdf_counters", "gx_nsdf_step_predictions", "gx_autotune",
@@ -135,6 +138,7 @@ def lib():
         L.gx_raster_counters.argtypes = [vp, C.POINTER(C.c_int64), C.c_int32]
         L.gx_render_noalloc.argtypes = [vp, C.c_int32, vp, vp, vp, C.c_int32, C.c_int32,
                                         C.c_int32, C.c_float, vp, C.c_int32, vp, vp]
+        L.gx_render_noalloc_error.argtypes = [C.POINTER(C.c_uint32)]
         L.gx_nsdf_set_weights.argtypes = [vp, C.c_int32, vp, vp]
         L.gx_nsdf_get_weights.argtypes = [vp, C.c_int32, vp, vp, vp]
         L.gx_nsdf_query.argtypes = [vp, C.c_int32, vp, C.c_int32, vp, vp]
