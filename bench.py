@@ -3,17 +3,23 @@
 
 Metric: sim steps/sec = environments x steps / device time of the timed loop
 (render + kinematics + collision, resets included at the workload's rate).
-Default workload: 4096 envs over 16 procedural apartments (20k-60k
-triangles, 2 cm distance grid), 40 objects per env, 128x128 FP32 depth +
-RGB8, Gaussian actions, 200-step episodes (staggered: every step resets the
-envs whose episode ends).
+Default workload (uneven16384_nsdf, the full stack): 16384 envs over 64
+procedural apartments with log-uniform 5k-150k triangles (2 cm distance
+grid), 40 objects per env, 128x128 FP16 depth + RGB8, Gaussian actions,
+Bernoulli(0.005) resets per env-step, and the per-scene neural SDF in the
+static test (every scene's network trained before the timed loop by the
+library's own kernels), timed beside the plain distance-grid form of the same
+batch, with the share of contact decisions that differ between the two.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gx|reference]
+                  [--workload NAME]
 
-Under torchrun every rank runs its own full batch on its own GPU (weak
-scaling, no collective on the data path); rank 0 prints one JSON line.
---impl reference times the FP64 CPU oracle on the host on a bounded sample
-of the same workload.
+Under torchrun the global batch is N x the workload's environments (weak
+scaling); rank g steps environments [g*E, (g+1)*E) of it, loads only the
+scenes they use and draws its resets from the global environment indices;
+no collective on the data path, per-step counters summed on the host; rank 0
+prints one JSON line.  --impl reference times the FP64 CPU oracle on the host
+on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -34,6 +40,7 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 from paper_2306_07552_b300 import inputs as I  # noqa: E402
+from paper_2306_07552_b300 import shard  # noqa: E402
 
 METRIC = "sim steps/sec (render+kinematics+collision) on 1 B300; fraction of roofline"
 UNIT = "env-steps/s"
@@ -161,12 +168,6 @@ def loaded_clock_mhz():
     return json.load(open(p)).get("clocks_under_load", {}).get("sm_mhz_median")
 
 
-def rank_seeds(w, rank):
-    """Reset and action seeds of one rank: every rank runs its own batch of
-    independent environments (weak scaling), so their streams must differ."""
-    return w.reset_seed + 7919 * rank, w.action_seed + rank
-
-
 def job_value(dist, n_envs, steps, ms_local):
     """Whole-job env-steps/s: all ranks' environments over the slowest rank's
     time (max over ranks)."""
@@ -181,20 +182,22 @@ def job_value(dist, n_envs, steps, ms_local):
     return world * n_envs * steps / (ms / 1e3), ms
 
 
-def reset_masks(n, period):
+def reset_masks(n, period, first=0):
+    """Staggered episodes of the global environments first .. first+n-1."""
     masks = np.zeros((period, n), np.uint8)
     for t in range(period):
-        masks[t, (np.arange(n) + t) % period == 0] = 1
+        masks[t, (np.arange(first, first + n) + t) % period == 0] = 1
     return masks
 
 
-def work_counters(ss, w, acts, mask_at, steps):
+def work_counters(ss, w, acts, mask_at, steps, plan):
     """Rasteriser work counters per view from a separate, untimed context
     running the counting variant of the kernel."""
     from paper_2306_07552_b300 import gx
     sim = gx.Sim(ss, I.fetch_like_robot(), w.n_envs, img=(w.img, w.img),
                  depth_fp16=w.depth_fp16, render_rgb=w.rgb, n_objects=w.n_objects,
-                 obj_radius=w.obj_radius, seed=w.reset_seed, profile=3)
+                 obj_radius=w.obj_radius, seed=w.reset_seed, profile=3,
+                 env_scene=plan.env_scene, env_offset=plan.first)
     sim.reset()
     for t in range(steps):
         sim.reset(mask_at(t))
@@ -291,7 +294,9 @@ def cpu_baseline(w, scenes, seconds):
     dt = time.perf_counter() - t0
     return {"value": done / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{done} env-steps (physics + {w.img}x{w.img} render) over "
-                      f"{len(sample_envs)} envs of {w.name}, {dt:.1f} s, one thread, FP64",
+                      f"{len(sample_envs)} envs of {w.name}, {dt:.1f} s, one thread, FP64"
+                      + ("; static test on the distance grid (the rule the neural form must "
+                         "agree with)" if w.sdf == "neural" else ""),
             "cpu_model": cpu_model(), "nproc": os.cpu_count()}
 
 
@@ -306,24 +311,26 @@ NSDF_BLOB_BYTES = 114688 + 2976
 
 def train_scenes(ss, w, scenes_used):
     """Trains every used scene's network (untimed for the step metric);
-    returns the training measurement.  The per-step time is the difference
-    of a full and a short run on the first scene, so sample generation and
-    workspace allocation cancel out."""
+    scenes_used: (index in the scene set, global scene index) pairs, the
+    global index seeding the scene's sample stream.  Returns the training
+    measurement.  The per-step time is the difference of a full and a short
+    run on the first scene, so sample generation and workspace allocation
+    cancel out."""
     B = I.fourier_matrix(w.nsdf_seed)
     P0 = I.nsdf_init(w.nsdf_seed)
-    first = scenes_used[0]
+    first, first_g = scenes_used[0]
     ss.nsdf_set_weights(first, B, P0)
     short = max(w.nsdf_steps // 4, 1)
     t0 = time.perf_counter()
     ss.nsdf_train(first, n_samples=w.nsdf_samples, batch=NSDF_BATCH, steps=short,
-                  seed=w.nsdf_seed + first)
+                  seed=w.nsdf_seed + first_g)
     t_short = time.perf_counter() - t0
     losses, total = [], 0.0
-    for s in scenes_used:
+    for s, g in scenes_used:
         ss.nsdf_set_weights(s, B, P0)
         t0 = time.perf_counter()
         lo = ss.nsdf_train(s, n_samples=w.nsdf_samples, batch=NSDF_BATCH, steps=w.nsdf_steps,
-                           seed=w.nsdf_seed + s)
+                           seed=w.nsdf_seed + g)
         dt = time.perf_counter() - t0
         total += dt
         if s == first:
@@ -358,10 +365,11 @@ def run_reference(args, w, rank, world):
     if rank != 0:
         return
     import oracle as O
-    scenes = I.make_scenes(w)
     robot = I.fetch_like_robot()
     env_scene = I.env_scene_map(w.n_envs, w.n_scenes)
     sample = [int(e) for e in np.linspace(0, w.n_envs - 1, args.ref_envs)]
+    used = sorted(set(int(env_scene[e]) for e in sample))
+    scenes = dict(zip(used, I.make_scenes(w, only=used)))
     orcs, sts = {}, []
     for e in sample:
         s = int(env_scene[e])
@@ -393,7 +401,10 @@ def run_reference(args, w, rank, world):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of(w),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{len(sample)} envs of {w.name} per step, each step "
-                                       f"physics + {w.img}x{w.img} render, FP64, one thread"},
+                                       f"physics + {w.img}x{w.img} render, FP64, one thread"
+                                       + ("; static test on the distance grid (the rule the "
+                                          "neural form must agree with)"
+                                          if w.sdf == "neural" else "")},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -405,7 +416,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gx", choices=["gx", "reference"])
-    ap.add_argument("--workload", default="apartments4096", choices=list(I.WORKLOADS))
+    ap.add_argument("--workload", default="uneven16384_nsdf", choices=list(I.WORKLOADS))
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -446,33 +457,39 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     n = w.n_envs
-    scenes = I.make_scenes(w)
+    # this rank's shard of the global batch (world x n environments): its
+    # environment range, the scenes those environments use, their map
+    plan = shard.plan(world * n, w.n_scenes, world, rank)
+    scenes = I.make_scenes(w, only=plan.scenes)
     ss = gx.SceneSet(scenes)
     neural = w.sdf == "neural"
     nsdf = None
     if neural:
-        nsdf = train_scenes(ss, w, sorted(set(int(x) for x in I.env_scene_map(n, w.n_scenes))))
+        nsdf = train_scenes(ss, w, list(enumerate(plan.scenes)))
     sim_kw = dict(img=(w.img, w.img), depth_fp16=w.depth_fp16, render_rgb=w.rgb,
-                  n_objects=w.n_objects, obj_radius=w.obj_radius, seed=rank_seeds(w, rank)[0],
+                  n_objects=w.n_objects, obj_radius=w.obj_radius, seed=w.reset_seed,
                   small_tri_px=args.small_px, heuristics=args.heuristics,
-                  render_robot=args.render_robot, broadphase=args.broadphase)
+                  render_robot=args.render_robot, broadphase=args.broadphase,
+                  env_scene=plan.env_scene, env_offset=plan.first)
     column = w.sdf == "column"
     sdf_mode = 1 if neural else (2 if column else 0)
     sim = gx.Sim(ss, I.fetch_like_robot(), n, profile=0 if args.graph else 1,
                  use_graph=args.graph, sdf_mode=sdf_mode, sdf_margin=w.sdf_margin,
                  **sim_kw)
     total = args.warmup + args.steps
-    acts = torch.from_numpy(I.make_actions(total, n, w.action_dist,
-                                           seed=rank_seeds(w, rank)[1])).cuda()
+    # actions and reset draws of the global batch, this shard's columns
+    sl = slice(plan.first, plan.first + n)
+    acts = torch.from_numpy(np.ascontiguousarray(
+        I.make_actions(total, world * n, w.action_dist, seed=w.action_seed)[:, sl])).cuda()
     if w.reset_every:
-        masks_np = reset_masks(n, w.reset_every)
+        masks_np = reset_masks(n, w.reset_every, plan.first)
         masks = torch.from_numpy(masks_np).cuda()
         mask_at = lambda t: masks[t % w.reset_every]  # noqa: E731
         host_mask = lambda t: masks_np[t % w.reset_every]  # noqa: E731
     else:
-        rng = np.random.default_rng(w.reset_seed + rank)
-        mk_np = (rng.random((total + 2 * max(1, args.e2e_steps), n)) < w.reset_prob).astype(
-            np.uint8)
+        rng = np.random.default_rng(w.reset_seed)
+        mk_np = np.ascontiguousarray((rng.random((total + 2 * max(1, args.e2e_steps), world * n))
+                                      < w.reset_prob).astype(np.uint8)[:, sl])
         mk = torch.from_numpy(mk_np).cuda()
         mask_at = lambda t: mk[t]  # noqa: E731
         host_mask = lambda t: mk_np[t]  # noqa: E731
@@ -522,6 +539,17 @@ def main():
     phase_ms, phase_n = sim.phase_times() if not args.graph else ([0] * 4, [0] * 4)
     dev_err = sim.device_error()
     value, ms = job_value(dist, n, args.steps, ms)
+    # the last step's per-env results, summed over every rank's shard on the
+    # host (a gloo group beside the NCCL one): no collective touches the step
+    o = sim.out
+    last = {"env_steps": float(n), "contacts": float((o["contact_mask"] != 0).sum().item()),
+            "grasps": float((o["event"] == 1).sum().item()),
+            "releases": float(((o["event"] >= 3) & (o["event"] <= 5)).sum().item()),
+            "reward_sum": float(o["reward"].double().sum().item())}
+    shards = {"global_envs": world * n, "envs_per_rank": n, "rank0_envs": [plan.first, n],
+              "rank0_scenes": list(plan.scenes),
+              "last_step_summed": shard.sum_counters(
+                  (dist, dist.new_group(backend="gloo")) if dist else None, last)}
     static_form = None
     if neural or column:
         # the grid form of the same workload, timed the same way
@@ -634,7 +662,7 @@ def main():
                            "note": "every output (images included) copied back each step"}}
     counters = None
     if rank == 0 and not args.no_counters:
-        counters = work_counters(ss, w, acts, mask_at, min(args.warmup, 5))
+        counters = work_counters(ss, w, acts, mask_at, min(args.warmup, 5), plan)
     sim.close()
     if rank != 0:
         ss.close()
@@ -659,7 +687,7 @@ def main():
             ops = n * (C_TRI * work["tris_per_view"] + C_FRAG * work["frags_per_view"])
             achieved = ops / (launch_ms / 1e3) / 1e12
             # upper bound of the work: every scene triangle set up in every view
-            env_tris = np.array([scenes[s].n_tris for s in I.env_scene_map(n, w.n_scenes)])
+            env_tris = np.array([scenes[s].n_tris for s in plan.env_scene])
             ops_all = C_TRI * env_tris.sum() + n * C_FRAG * work["frags_per_view"]
             no_cull = {"achieved": ops_all / (launch_ms / 1e3) / 1e12,
                        "frac": ops_all / (launch_ms / 1e3) / 1e12 / peak,
@@ -714,6 +742,7 @@ def main():
         "nsdf": nsdf,
         "column_grid": static_form,
         "autotune": tune,
+        "shards": shards,
         "raster_counters_per_view": counters,
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches, "clocks": clocks, "device_error": dev_err,

@@ -175,6 +175,16 @@ typedef struct {
                               objects (random turn in [-pi/4, pi/4), Philox on
                               env, step, k, 0x4A495454 with the reset seed) and
                               re-cast down (event 5 when that lands)          */
+  int32_t raster_order;    /* rasteriser work order: 0 chosen at creation
+                              (costliest scene first when the scenes' cluster
+                              counts differ by more than 1.5x, else index
+                              order), 1 index order, 2 costliest scene first;
+                              gx_autotune may change it                       */
+  int32_t env_offset;      /* global index of this context's environment 0:
+                              the Philox counters of resets and placing jitters
+                              use env_offset + local index, so a batch split
+                              over several contexts (one per GPU) draws exactly
+                              what one context over the whole batch draws    */
 } gx_config;
 
 /* Outputs of one step, device memory owned by the caller (e.g. torch

@@ -194,6 +194,7 @@ void enqueue_step(gx_ctx* c, const float* actions, const gx_outputs& out, cudaSt
   pp.slide = c->cfg.heuristics & 1;
   pp.place_jitter = (c->cfg.heuristics >> 1) & 1;
   pp.seed = c->cfg.seed;
+  pp.env_offset = c->cfg.env_offset;
   pp.column = c->cfg.sdf_mode == 2;
   if (c->cfg.sdf_mode == 1) {
     pp.nsdf_pts = c->d_nsdf_pts;
@@ -450,6 +451,10 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
   if (c.heuristics & ~3) return fail(nullptr, GX_EINVAL, "heuristics: only bits 0 and 1 are defined");
   if (c.sdf_mode == 1 && !(c.sdf_margin >= 0.f && c.sdf_margin < 1e30f))
     return fail(nullptr, GX_EINVAL, "sdf_margin must be finite and >= 0");
+  if (c.raster_order < 0 || c.raster_order > 2)
+    return fail(nullptr, GX_EINVAL, "raster_order must be 0, 1 or 2");
+  if (c.env_offset < 0 || (int64_t)c.env_offset + c.n_envs > INT32_MAX)
+    return fail(nullptr, GX_EINVAL, "env_offset must be >= 0 with env_offset + n_envs < 2^31");
   gx_ctx* x = new gx_ctx();
   x->set = set;
   x->cfg = c;
@@ -555,7 +560,7 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
       lo = std::min(lo, ms[es[i]]);
       hi = std::max(hi, ms[es[i]]);
     }
-    x->order_mode = hi > 1.5 * lo ? 1 : 0;
+    x->order_mode = c.raster_order ? c.raster_order - 1 : (hi > 1.5 * lo ? 1 : 0);
     if ((e = cudaMalloc(&x->d_order, n * sizeof(int))) != cudaSuccess ||
         (e = cudaMemcpy(x->d_order, ord.data(), n * sizeof(int), cudaMemcpyHostToDevice)) !=
             cudaSuccess)
@@ -654,6 +659,7 @@ extern "C" gx_status gx_reset(gx_ctx* x, const uint8_t* env_mask, void* stream) 
   rp.st = x->st;
   rp.cam = x->d_cam;
   rp.seed = x->cfg.seed;
+  rp.env_offset = x->cfg.env_offset;
   rp.rho_min = x->cfg.obj_radius_min;
   rp.rho_max = x->cfg.obj_radius_max;
   rp.err = x->d_err;

@@ -123,6 +123,7 @@ struct PhysicsParams {
   const float* nsdf_d;                  // [n][32]
   float nsdf_margin;
   unsigned long long* nsdf_counters;    // optional [kNsdfCounters]
+  int env_offset;                       // global index of environment 0 (Philox counters)
 };
 
 // Neural-SDF decision counters (profiling only).
@@ -147,6 +148,7 @@ struct ResetParams {
   uint64_t seed;
   float rho_min, rho_max;
   unsigned* err;
+  int env_offset;      // global index of environment 0 (Philox counters)
 };
 
 // Rasteriser launch shape: threads per CTA and CTAs wanted per SM.

@@ -466,7 +466,7 @@ __global__ void __launch_bounds__(32 * kEnvsPerBlock, 7) physics_kernel(const Ph
           }
         }
         const uint4 w = philox4x32_10(
-            make_uint4((uint32_t)env, (uint32_t)(stepc - 1), (uint32_t)k, 0x4A495454u), key);
+            make_uint4((uint32_t)(env + P.env_offset), (uint32_t)(stepc - 1), (uint32_t)k, 0x4A495454u), key);
         const float u = unit24(w.x);
         const float dl = sqrtf(Dx * Dx + Dz * Dz);
         const float phi = dl > 1e-6f ? atan2f(Dz, Dx) + (u - 0.5f) * (0.5f * CUDART_PI_F)
@@ -682,10 +682,10 @@ __device__ void reset_env(const ResetParams& P, int env, float4 (*s_cand)[kTryWi
   // 1. radii (from each object's try 0) and the first window's static tests
   for (int jt = tid; jt < M * kTryWindow; jt += kResetThreads) {
     const int j = jt / kTryWindow, t = jt % kTryWindow;
-    const uint4 w0 = philox4x32_10(make_uint4((uint32_t)env, ep, (uint32_t)j, 0u), key);
+    const uint4 w0 = philox4x32_10(make_uint4((uint32_t)(env + P.env_offset), ep, (uint32_t)j, 0u), key);
     const float rho = P.rho_min + unit24(w0.w) * (P.rho_max - P.rho_min);
     if (t == 0) s_rho[j] = rho;
-    const uint4 wv = t == 0 ? w0 : philox4x32_10(make_uint4((uint32_t)env, ep, (uint32_t)j, (uint32_t)t), key);
+    const uint4 wv = t == 0 ? w0 : philox4x32_10(make_uint4((uint32_t)(env + P.env_offset), ep, (uint32_t)j, (uint32_t)t), key);
     const float3 p = object_candidate(S, wv, rho, clear);
     float d;
     const bool ok = grid_query(S, p.x, p.y, p.z, d) && !(d < rho);
@@ -712,7 +712,7 @@ __device__ void reset_env(const ResetParams& P, int env, float4 (*s_cand)[kTryWi
             c = s_cand[j][t];
           } else {
             const uint4 wv =
-                philox4x32_10(make_uint4((uint32_t)env, ep, (uint32_t)j, (uint32_t)t), key);
+                philox4x32_10(make_uint4((uint32_t)(env + P.env_offset), ep, (uint32_t)j, (uint32_t)t), key);
             const float3 p = object_candidate(S, wv, rho, clear);
             float d;
             const bool sok = grid_query(S, p.x, p.y, p.z, d) && !(d < rho);
@@ -745,7 +745,7 @@ __device__ void reset_env(const ResetParams& P, int env, float4 (*s_cand)[kTryWi
         if (t0 == 0) {
           c = s_cand[j][warp];
         } else {
-          const uint4 wv = philox4x32_10(make_uint4((uint32_t)env, ep, (uint32_t)j, (uint32_t)t), key);
+          const uint4 wv = philox4x32_10(make_uint4((uint32_t)(env + P.env_offset), ep, (uint32_t)j, (uint32_t)t), key);
           const float3 p = object_candidate(S, wv, rho, clear);
           float d;
           const bool sok = grid_query(S, p.x, p.y, p.z, d) && !(d < rho);
@@ -794,7 +794,7 @@ __device__ void reset_env(const ResetParams& P, int env, float4 (*s_cand)[kTryWi
     __syncthreads();
     for (int p = tid; p < kTryWindow * ns; p += kResetThreads) {
       const int tw = p / ns, i = p - tw * ns;
-      const uint4 wv = philox4x32_10(make_uint4((uint32_t)env, ep, kRobotStream, (uint32_t)(t0 + tw)), key);
+      const uint4 wv = philox4x32_10(make_uint4((uint32_t)(env + P.env_offset), ep, kRobotStream, (uint32_t)(t0 + tw)), key);
       float x, z, yaw;
       robot_try(S, wv, x, z, yaw);
       float cc[3];
@@ -821,7 +821,7 @@ __device__ void reset_env(const ResetParams& P, int env, float4 (*s_cand)[kTryWi
   int t = s_robot_try;
   failed |= t < 0;
   if (t < 0) t = 63;
-  const uint4 wv = philox4x32_10(make_uint4((uint32_t)env, ep, kRobotStream, (uint32_t)t), key);
+  const uint4 wv = philox4x32_10(make_uint4((uint32_t)(env + P.env_offset), ep, kRobotStream, (uint32_t)t), key);
   float bx, bz, byaw;
   robot_try(S, wv, bx, bz, byaw);
   if (failed && lane == 0) atomicOr(P.err, GX_DEV_PLACEMENT_FAILED);
@@ -845,7 +845,7 @@ __device__ void reset_env(const ResetParams& P, int env, float4 (*s_cand)[kTryWi
 #pragma unroll
     for (int k = 0; k < 16; ++k) task[k] = 0.f;
     if (M > 0 && S.n_supports > 0) {
-      const uint4 wg = philox4x32_10(make_uint4((uint32_t)env, ep, kGoalStream, 0u), key);
+      const uint4 wg = philox4x32_10(make_uint4((uint32_t)(env + P.env_offset), ep, kGoalStream, 0u), key);
       const float4 o = so[0];
       const float3 g = object_candidate(S, wg, o.w, rb.rest_clearance);
       task[0] = g.x;

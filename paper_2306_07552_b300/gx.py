@@ -77,7 +77,8 @@ class GxConfig(C.Structure):
                 ("seed", C.c_uint64), ("env_scene", i32p),
                 ("small_tri_px", C.c_int32), ("use_graph", C.c_int32), ("profile", C.c_int32),
                 ("sdf_mode", C.c_int32), ("sdf_margin", C.c_float), ("broadphase", C.c_int32),
-                ("render_robot", C.c_int32), ("heuristics", C.c_int32)]
+                ("render_robot", C.c_int32), ("heuristics", C.c_int32),
+                ("raster_order", C.c_int32), ("env_offset", C.c_int32)]
 
 
 OUTPUT_KEYS = ["depth", "rgb", "pose", "obj_pos", "held", "contact_mask", "contact_flags", "event",
@@ -332,7 +333,7 @@ class Sim:
                  depth_fp16=False, render_rgb=True, n_objects=40, obj_radius=(0.03, 0.06),
                  seed=1, env_scene=None, small_tri_px=0, use_graph=False,
                  profile=0, sdf_mode=0, sdf_margin=0.02, heuristics=0, render_robot=False,
-                 broadphase=False):
+                 broadphase=False, raster_order=0, env_offset=0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("gx needs a CUDA device; there is no CPU fallback")
@@ -355,6 +356,8 @@ class Sim:
         cfg.heuristics = int(heuristics)
         cfg.render_robot = int(render_robot)
         cfg.broadphase = int(broadphase)
+        cfg.raster_order = int(raster_order)
+        cfg.env_offset = int(env_offset)
         self.robot_c = robot_struct(robot)
         self.handle = C.c_void_p()
         _check(lib().gx_create(scene_set.handle, C.byref(self.robot_c), C.byref(cfg),

@@ -571,10 +571,12 @@ def scene_tri_targets(w: Workload) -> list[int]:
     return [int(x) for x in np.exp(rng.uniform(math.log(lo), math.log(hi), w.n_scenes))]
 
 
-def make_scenes(w: Workload) -> list[Scene]:
+def make_scenes(w: Workload, only=None) -> list[Scene]:
+    """The workload's scenes in index order, or only the global indices in
+    `only` (in that order): each scene depends on its own seed alone."""
     targets = scene_tri_targets(w)
     out = []
-    for s in range(w.n_scenes):
+    for s in (range(w.n_scenes) if only is None else only):
         if w.scene_kind == "room":
             out.append(room_scene(w.scene_seed + s, targets[s], grid_h=w.grid_h))
         else:
