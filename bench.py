@@ -24,6 +24,7 @@ on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import contextlib
 import dataclasses
 import hashlib
 import json
@@ -44,12 +45,28 @@ from paper_2306_07552_b300 import shard  # noqa: E402
 
 METRIC = "sim steps/sec (render+kinematics+collision) on 1 B300; fraction of roofline"
 UNIT = "env-steps/s"
-# Minimal per-unit work of the rasteriser in lane operations, for its ALU
-# roofline: one front-facing triangle reaching the image (its share of the
-# vertex transform, plane, orientation, bounding box, edge setup) and one
-# covered fragment (three edge tests, depth plane, key, depth test).
-C_TRI = 70
-C_FRAG = 10
+# Minimal per-unit work of the rasteriser in FP32/INT32 lane operations (one
+# instruction of one lane; an FMA is one), for its ALU roofline.
+# One front-facing triangle reaching the image:
+#   half a vertex (closed meshes have ~T/2 vertices): P - eye 3, rotation to
+#     camera space 9, reciprocal of z 1, projection 4, snap to 1/256 px 4
+#     = 21, half of it                                                 10.5
+#   facing: two edge vectors 6, their cross product 6, plane offset
+#     n . (P0 - eye) 6, sign 1                                           19
+#   screen edges dx, dy                                                   6
+#   edge values at the first pixel centre (2 differences, 2 products
+#     each)                                                              12
+#   top-left bias                                                         6
+#   bounding box: min/max of three per axis 8, to pixel centres 8, clamp
+#     to the image 4                                                     20
+#   depth plane: normal to camera space 9, 1/(h f) 2, coefficients 4    15
+#   orientation from the doubled area, with the swap                      5
+#   -> 93.5, rounded up
+# One covered fragment: three edge values stepped 3, inside test 2, 1/z by
+# one FMA 1, key (shift and or of the depth bits with colour and epoch) 3,
+# framebuffer address 1, depth test 1 -> 11.
+C_TRI = 94
+C_FRAG = 11
 LANES = 128          # FP32/INT32 lanes per SM
 
 
@@ -435,8 +452,8 @@ def main():
                     help="the paper's heuristics: bit 0 sliding, bit 1 object placing")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default rasteriser setting instead of timing candidates")
-    ap.add_argument("--graph", action="store_true",
-                    help="replay the step as a CUDA graph (no per-kernel timing)")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="headline from the event-timed loop instead of a graph-replayed one")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_env()
@@ -473,9 +490,11 @@ def main():
                   env_scene=plan.env_scene, env_offset=plan.first)
     column = w.sdf == "column"
     sdf_mode = 1 if neural else (2 if column else 0)
-    sim = gx.Sim(ss, I.fetch_like_robot(), n, profile=0 if args.graph else 1,
-                 use_graph=args.graph, sdf_mode=sdf_mode, sdf_margin=w.sdf_margin,
-                 **sim_kw)
+    # per-kernel CUDA events on the launching stream (the roofline's kernel
+    # time); the headline loop below replays the step as a CUDA graph on a
+    # second context of the same batch
+    sim = gx.Sim(ss, I.fetch_like_robot(), n, profile=1, sdf_mode=sdf_mode,
+                 sdf_margin=w.sdf_margin, **sim_kw)
     total = args.warmup + args.steps
     # actions and reset draws of the global batch, this shard's columns
     sl = slice(plan.first, plan.first + n)
@@ -498,50 +517,72 @@ def main():
     stream = torch.cuda.Stream()
     launches = 0
 
-    def one(t):
+    def one(ctx, t):
         # copy into fixed buffers so a graph replay sees the same pointers
         abuf.copy_(acts[t])
         mbuf.copy_(mask_at(t))
-        sim.reset(mbuf, stream=stream)
-        sim.step(abuf, stream=stream)
+        ctx.reset(mbuf, stream=stream)
+        ctx.step(abuf, stream=stream)
 
-    tune = None
-    with torch.cuda.stream(stream):
-        sim.reset(stream=stream)
-        for t in range(args.warmup):
-            one(t)
-        # device error bits of the warm-up (e.g. 0x2: a crowded reset kept an
-        # object's last placement try), recorded and cleared
-        warmup_err = sim.device_error()
-        if not args.no_autotune:
-            # rasteriser setting timed on this batch's own state (restored)
-            abuf.copy_(acts[args.warmup - 1])
-            tune = sim.autotune(abuf, steps=3, stream=stream)
-    torch.cuda.synchronize()
-    if not args.graph:
-        sim.phase_times()
-    if dist:
-        dist.barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        torch.cuda.synchronize()
-        e0.record(stream)
+    def warm(ctx):
         with torch.cuda.stream(stream):
-            for t in range(args.warmup, total):
-                one(t)
-                launches += 5 if neural else 3
-        e1.record(stream)
+            ctx.reset(stream=stream)
+            for t in range(args.warmup):
+                one(ctx, t)
+            # device error bits of the warm-up (e.g. 0x2: a crowded reset kept
+            # an object's last placement try), recorded and cleared
+            err = ctx.device_error()
+            tuned = None
+            if not args.no_autotune:
+                # rasteriser setting timed on this batch's own state (restored)
+                abuf.copy_(acts[args.warmup - 1])
+                tuned = ctx.autotune(abuf, steps=3, stream=stream)
         torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    ms = e0.elapsed_time(e1)
-    phase_ms, phase_n = sim.phase_times() if not args.graph else ([0] * 4, [0] * 4)
-    dev_err = sim.device_error()
+        return err, tuned
+
+    def timed(ctx, clk_on):
+        """Steps warmup .. total-1 between two events on the launching
+        stream, a barrier and a device synchronisation on both sides."""
+        if dist:
+            dist.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) if clk_on else contextlib.nullcontext() as clk:
+            torch.cuda.synchronize()
+            e0.record(stream)
+            with torch.cuda.stream(stream):
+                for t in range(args.warmup, total):
+                    one(ctx, t)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        return e0.elapsed_time(e1), clk
+
+    warmup_err, tune = warm(sim)
+    sim.phase_times()
+    ms_events, clk_events = timed(sim, args.no_graph)
+    phase_ms, phase_n = sim.phase_times()
+    # the headline: the same steps of the same batch on a context that
+    # replays each step as a captured CUDA graph (how a user runs it)
+    gsim = None
+    if not args.no_graph:
+        gsim = gx.Sim(ss, I.fetch_like_robot(), n, use_graph=True, sdf_mode=sdf_mode,
+                      sdf_margin=w.sdf_margin, **sim_kw)
+        warm(gsim)
+        ms, clk = timed(gsim, True)
+        dev_err = gsim.device_error()
+        out_ctx = gsim
+    else:
+        ms, clk = ms_events, clk_events
+        dev_err = sim.device_error()
+        out_ctx = sim
+    launches = args.steps * (5 if neural else 3)
     value, ms = job_value(dist, n, args.steps, ms)
+    value_events, _ = job_value(dist, n, args.steps, ms_events)
     # the last step's per-env results, summed over every rank's shard on the
     # host (a gloo group beside the NCCL one): no collective touches the step
-    o = sim.out
+    o = out_ctx.out
     last = {"env_steps": float(n), "contacts": float((o["contact_mask"] != 0).sum().item()),
             "grasps": float((o["event"] == 1).sum().item()),
             "releases": float(((o["event"] >= 3) & (o["event"] <= 5)).sum().item()),
@@ -618,6 +659,8 @@ def main():
     # A user's context: the step replayed as a CUDA graph, no per-kernel
     # timing events, the rasteriser setting the autotuner picks for it.
     sim.close()
+    if gsim is not None:
+        gsim.close()
     sim = gx.Sim(ss, I.fetch_like_robot(), n, profile=0, use_graph=True, sdf_mode=sdf_mode,
                  sdf_margin=w.sdf_margin, **sim_kw)
     with torch.cuda.stream(stream):
@@ -736,6 +779,12 @@ def main():
                                                   "object_placing": bool(args.heuristics & 2)},
                    "robot_body_rendered": bool(args.render_robot),
                    "object_broadphase": bool(args.broadphase)},
+        "timing": ("graph-replayed step (each step: reset launch + one graph replay), CUDA "
+                   "events on the launching stream" if not args.no_graph else
+                   "per-kernel CUDA events, no graph"),
+        "event_timed": {"value": value_events, "ms_per_step": ms_events / args.steps,
+                        "note": "the same steps on a context timing each kernel with CUDA "
+                                "events (no graph); phases and the roofline come from it"},
         "phases_ms_per_launch": {k: phase_ms[i] / max(phase_n[i], 1)
                                  for i, k in enumerate(["physics", "raster", "reset",
                                                         "nsdf_query"])},

@@ -140,6 +140,9 @@ def _declare(L):
     L.orc_mlp_loss_grad.argtypes = [f64p, C.c_int, P(f64p), P(f64p), i32p, C.c_int, f64p, f64p,
                                     C.c_int, C.c_double, C.c_double, P(f64p), P(f64p)]
     L.orc_mlp_loss_grad.restype = C.c_double
+    L.orc_mlp_rounding_bound.argtypes = [f64p, C.c_int, P(f64p), P(f64p), i32p, C.c_int, f64p,
+                                         C.c_double, f64p]
+    L.orc_mlp_rounding_bound.restype = C.c_double
 
 
 def _p(a, t):
@@ -427,6 +430,23 @@ class MLP64:
             out[i] = L.orc_mlp_forward(_p(self.B, f64p), self.F, self._wp, self._bp,
                                        _p(self.dims, i32p), len(self.Ws), _p(X[i], f64p), None)
         return out
+
+    def rounding_bound(self, X, feat_err=4e-7, terms=False):
+        """Plain FP64 outputs (nothing rounded) and, per point, the first-order
+        bound on how far a kernel that rounds features and hidden activations
+        to BF16 and sums in FP32 can be from them (orc_mlp_rounding_bound);
+        terms=True also returns its [n][4] operand, feature and FP32 parts and
+        the operand part's standard deviation for independent roundings."""
+        X = np.ascontiguousarray(np.atleast_2d(X), np.float64)
+        L = lib()
+        out = np.zeros(len(X))
+        parts = np.zeros((len(X), 4))
+        for i in range(len(X)):
+            out[i] = L.orc_mlp_rounding_bound(_p(self.B, f64p), self.F, self._wp, self._bp,
+                                              _p(self.dims, i32p), len(self.Ws), _p(X[i], f64p),
+                                              float(feat_err), _p(parts[i], f64p))
+        bnd = parts[:, :3].sum(axis=1)
+        return (out, bnd, parts) if terms else (out, bnd)
 
     def loss_grad(self, X, y, lo, hi):
         X = np.ascontiguousarray(X, np.float64)

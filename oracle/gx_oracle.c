@@ -1183,3 +1183,90 @@ double orc_mlp_loss_grad(const double* B, int F, const double* const* W, const d
   free(g2);
   return loss / n;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Rounding-error bound of the BF16-operand network against the plain one.  */
+/* The plain network is the FP64 MLP above with nothing rounded.  A kernel   */
+/* that rounds each operand a_{l,i} fed to a product (features a_0, hidden  */
+/* activations a_1 .. a_{L-1}) to BF16, sums in FP32 over K terms and has   */
+/* features within feat_err of sin/cos, differs from it, to first order in  */
+/* the rounding errors (Higham, "Accuracy and Stability of Numerical        */
+/* Algorithms", 2nd ed., Sec. 3.1 for the sums; the output's sensitivity    */
+/* to each operand is its gradient), by at most                             */
+/*   u_b sum_{l,i} |g_{l,i}| |a_{l,i}|          BF16 operand rounding        */
+/* + feat_err (1 + u_b) sum_i |g_{0,i}|         feature error                */
+/* + sum_{l,r} |gz_{l,r}| (gam_K (|W_l| |a_{l-1}|)_r + u_f (|z_{l,r}| + |b_{l,r}|))  */
+/*                                               FP32 sums and bias adds    */
+/* with g_{l,i} = dd/da_{l,i}, gz_{l,r} = dd/dz_{l,r} (z = pre-activation),  */
+/* u_b = 2^-8 (BF16: 8 significant bits, round to nearest), u_f = 2^-24,    */
+/* gam_K = 2 K u_f (an FP32 sum of K products, with a factor 2 for the      */
+/* accumulation order of the tensor cores).  g is taken through the plain   */
+/* network's ReLU masks, and |g_{l,i}| is the sensitivity to a_{l,i} itself */
+/* (not masked by unit i's own ReLU).  Returns the plain d(x); terms[0..2]  */
+/* get the operand, feature and FP32 parts of the bound (their sum), and    */
+/* terms[3] the standard deviation of the operand part when the rounding    */
+/* errors are independent and uniform in +-u_b |a|:                         */
+/*   u_b sqrt(sum (g a)^2 / 3)  (a typical error, not a bound).             */
+/* ------------------------------------------------------------------------ */
+double orc_mlp_rounding_bound(const double* B, int F, const double* const* W,
+                              const double* const* b, const int* dims, int L, const double x[3],
+                              double feat_err, double terms[4]) {
+  const double ub = 1.0 / 256.0, uf = 1.0 / 16777216.0;
+  int tot = 0, maxw = 0;
+  for (int l = 0; l <= L; ++l) { tot += dims[l]; if (dims[l] > maxw) maxw = dims[l]; }
+  int off[17];
+  off[0] = 0;
+  for (int l = 0; l < L && l < 16; ++l) off[l + 1] = off[l] + dims[l];
+  double* A = (double*)malloc(tot * sizeof(double));  /* a_0 .. a_L (plain)      */
+  double* Z = (double*)malloc(tot * sizeof(double));  /* z_l at a_l's offsets   */
+  double* g = (double*)malloc(maxw * sizeof(double));  /* dd/da_l                */
+  double* g2 = (double*)malloc(maxw * sizeof(double));
+  /* plain forward, nothing rounded */
+  for (int k = 0; k < F; ++k) {
+    double ph = 2 * PI * (B[3 * k] * x[0] + B[3 * k + 1] * x[1] + B[3 * k + 2] * x[2]);
+    A[k] = sin(ph);
+    A[F + k] = cos(ph);
+  }
+  for (int l = 0; l < L; ++l) {
+    const double* in = A + off[l];
+    for (int r = 0; r < dims[l + 1]; ++r) {
+      double s = b[l][r];
+      for (int c = 0; c < dims[l]; ++c) s += W[l][(size_t)r * dims[l] + c] * in[c];
+      Z[off[l + 1] + r] = s;
+      A[off[l + 1] + r] = (l < L - 1 && s < 0) ? 0.0 : s;
+    }
+  }
+  const double d = A[off[L]];
+  /* backward: g = dd/da_l for l = L-1 .. 0, accumulating the bound */
+  double t_op = 0.0, t_feat = 0.0, t_f32 = 0.0, t_sq = 0.0;
+  g[0] = 1.0;  /* dd/dz_L = 1 (linear output) */
+  for (int l = L - 1; l >= 0; --l) {
+    /* g holds dd/dz_{l+1} (pre-activation of layer l's output, masked) */
+    const double* in = A + off[l];
+    const double gam = 2.0 * dims[l] * uf;
+    for (int r = 0; r < dims[l + 1]; ++r) {
+      double absdot = 0.0;
+      for (int c = 0; c < dims[l]; ++c) absdot += fabs(W[l][(size_t)r * dims[l] + c] * in[c]);
+      t_f32 += fabs(g[r]) * (gam * absdot + uf * (fabs(Z[off[l + 1] + r]) + fabs(b[l][r])));
+    }
+    for (int c = 0; c < dims[l]; ++c) {
+      double acc = 0.0;
+      for (int r = 0; r < dims[l + 1]; ++r) acc += W[l][(size_t)r * dims[l] + c] * g[r];
+      g2[c] = acc;  /* dd/da_{l,c} */
+      t_op += ub * fabs(acc) * fabs(in[c]);
+      t_sq += acc * acc * in[c] * in[c];
+      if (l == 0) t_feat += feat_err * (1.0 + ub) * fabs(acc);
+    }
+    if (l > 0)
+      for (int c = 0; c < dims[l]; ++c) g[c] = Z[off[l] + c] > 0 ? g2[c] : 0.0;
+  }
+  free(A);
+  free(Z);
+  free(g);
+  free(g2);
+  terms[0] = t_op;
+  terms[1] = t_feat;
+  terms[2] = t_f32;
+  terms[3] = ub * sqrt(t_sq / 3.0);
+  return d;
+}

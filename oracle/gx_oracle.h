@@ -180,6 +180,14 @@ double orc_mlp_loss_grad(const double* B, int F, const double* const* W, const d
                          const int* dims, int n_layers, const double* X /*[n][3]*/,
                          const double* y /*[n]*/, int n, double clamp_lo, double clamp_hi,
                          double* const* gW, double* const* gb);
+/* First-order bound of |BF16-operand kernel - plain FP64 network| at x (the
+ * operands rounded to BF16, FP32 sums, features within feat_err); returns
+ * the plain network's d(x) and the bound's operand, feature and FP32 parts
+ * in terms[0..2] (terms[3]: the operand part's standard deviation for
+ * independent uniform roundings, a typical size rather than a bound). */
+double orc_mlp_rounding_bound(const double* B, int F, const double* const* W,
+                              const double* const* b, const int* dims, int n_layers,
+                              const double x[3], double feat_err, double terms[4]);
 #ifdef __cplusplus
 }
 #endif

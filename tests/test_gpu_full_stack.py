@@ -28,7 +28,12 @@ def check_reset(orc, s0, s1, e, M, seed, rho):
     """Env e reset between state s0 and s1: the oracle's reset from s0."""
     st = oracle_state(s0, e, M)
     r = orc.reset(st, seed, e, M, rho[0], rho[1])
-    if r.near_band:
+    placed = (np.allclose(s1["obj"][e, :M], O.Oracle.state_objs(st), atol=1e-5)
+              and abs(s1["base_x"][e] - st.base[0]) < 1e-5
+              and abs(s1["base_z"][e] - st.base[1]) < 1e-5)
+    if r.near_band and not placed:
+        # a near-band test inside the rejection loop accepted a different
+        # try on the two sides: only then is the comparison excused
         return False
     assert s1["episode"][e] == st.episode
     assert s1["held"][e] == -1 and s1["step"][e] == 0
@@ -136,7 +141,7 @@ def test_full_stack_16384_sampled():
     # a reset takes hundreds of decisions (64-try rejection loops for 40 objects
     # and the base); a quarter or so of them have one inside the near band
     assert resets >= 48 and resets - reset_nb >= resets // 2
-    assert tally.envs - tally.near_band >= 0.9 * tally.envs
+    assert tally.envs - tally.near_band_flips >= 0.9 * tally.envs
     assert trusted > 0 and asked > 0               # both branches of the rule exercised
     assert tally.ambiguous < 0.05 * (tally.pixels + tally.ambiguous)
     assert sim.device_error() == 0

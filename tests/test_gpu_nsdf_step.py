@@ -5,10 +5,16 @@ contact, a predicted clearance d - r of at least the margin is free, else the
 grid decides.  The check is split in two.  The rule: the oracle takes the
 predictions the GPU's step used (gx_nsdf_step_predictions) and must reach the
 same decisions, near band 1e-4 m as everywhere.  The network: those
-predictions against the oracle's FP64 MLP in the BF16-operand mode at the
-oracle's own sphere centres (weights drawn here, rounded to BF16 with
-PyTorch), within the query tolerance (FP32 sums ~1e-7; a BF16 rounding flip
-of one hidden value moves a prediction by up to ~1e-2 m at random weights).
+predictions, at the oracle's own sphere centres (weights drawn here, W1..W4
+rounded to BF16 with PyTorch), against
+  - the plain FP64 MLP (nothing but the weights rounded): every prediction
+    within the oracle's first-order rounding bound of the BF16-operand
+    network (orc_mlp_rounding_bound), and within 6 standard deviations of
+    independent roundings (a wrong row would stand out by far more); the
+    margin decisions (d - r >= margin) that differ from the plain network's
+    are counted;
+  - the oracle's BF16-operand mode, which rounds at the kernels' points: the
+    median error is the FP32 sums alone (~1e-7).
 """
 import numpy as np
 import pytest
@@ -26,14 +32,35 @@ NEAR_BAND = 1e-4
 
 
 def network_errors(errs, refs):
-    """Prediction error of the step's network against the oracle MLP: the
-    query tolerance (median and max)."""
+    """Prediction error of the step's network against the oracle MLP in its
+    BF16-operand mode: the same rounding points, so the median is the FP32
+    sums alone."""
     err, ref = np.concatenate(errs), np.concatenate(refs)
     scale = 1 + np.abs(ref).mean()
-    print(f"step predictions vs oracle MLP: median {np.median(err):.2e}, "
+    print(f"step predictions vs oracle MLP (BF16 operands): median {np.median(err):.2e}, "
           f"p99 {np.quantile(err, .99):.2e}, max {err.max():.2e} over {err.size}")
     assert np.median(err) < 1e-5 * scale
-    assert err.max() < 2e-2 * scale
+
+
+def plain_errors(errs, bounds, sigmas, flips, n_decisions, label):
+    """Predictions against the plain FP64 network: each within its rounding
+    bound and within 6 standard deviations of independent roundings."""
+    err, bnd, sig = np.concatenate(errs), np.concatenate(bounds), np.concatenate(sigmas)
+    z = err / sig
+    print(f"{label}: |gpu - plain FP64| median {np.median(err):.2e}, max {err.max():.2e}; "
+          f"bound median {np.median(bnd):.2e}, max {bnd.max():.2e}; err/bound max "
+          f"{(err / bnd).max():.3f}; in deviations: rms {np.sqrt(np.mean(z ** 2)):.2f}, max "
+          f"{z.max():.2f}; margin decisions differing {flips} of {n_decisions}")
+    assert np.all(err <= bnd)
+    assert z.max() <= 6.0
+    return err, bnd
+
+
+def plain_mlp(B, P):
+    """The plain FP64 network with the weights the kernels hold (W1..W4 in
+    BF16), nothing else rounded."""
+    m = oracle_mlp(B, P)
+    return O.MLP64(m.B, m.Ws, m.bs, bf16_operands=False)
 
 
 def _bf16(a):
@@ -135,15 +162,18 @@ def test_neural_rule_matches_oracle(two_rooms):
                  sdf_margin=MARGIN, profile=4)
     sim.reset()
     mlps = [oracle_mlp(B, P) for P in Ps]
+    plains = [plain_mlp(B, P) for P in Ps]
     cents = [grid_centre(sc) for sc in scenes]
     acts = I.make_actions(T, n, "gaussian", seed=6)
     tallies = [Tally(), Tally()]
     trusted = 0
     errs, refs = [], []
+    perrs, pbounds, psig = [], [], []
+    flips = decisions = 0
 
     def step_fn_for(k, pred):
         def f(st, action, env):
-            nonlocal trusted
+            nonlocal trusted, flips, decisions
             c, r, act = orcs[k].candidate_spheres(st, action)
             d = np.full(31, -1e9)
             idx = np.flatnonzero(act)
@@ -152,6 +182,12 @@ def test_neural_rule_matches_oracle(two_rooms):
             ref = mlps[k].forward(c[idx] - cents[k])
             errs.append(np.abs(d[idx] - ref))
             refs.append(ref)
+            plain, bnd, parts = plains[k].rounding_bound(c[idx] - cents[k], terms=True)
+            perrs.append(np.abs(d[idx] - plain))
+            pbounds.append(bnd)
+            psig.append(parts[:, 3])
+            flips += int(np.sum((d[idx] - r[idx] >= MARGIN) != (plain - r[idx] >= MARGIN)))
+            decisions += len(idx)
             trusted += int(np.sum(d[idx] - r[idx] >= MARGIN))
             return orcs[k].step_nsdf(st, action, d, MARGIN, NEAR_BAND)
         return f
@@ -168,7 +204,8 @@ def test_neural_rule_matches_oracle(two_rooms):
     cnt = sim.nsdf_counters()
     print(tallies, f"trusted predictions {trusted}", cnt)
     network_errors(errs, refs)
-    checked = sum(tl.envs - tl.near_band for tl in tallies)
+    plain_errors(perrs, pbounds, psig, flips, decisions, "step predictions (random weights)")
+    checked = sum(tl.envs - tl.near_band_flips for tl in tallies)
     assert checked >= 0.9 * n * T
     assert trusted > 0 and cnt["grid_fallbacks"] > 0     # both branches exercised
     assert cnt["tests"] >= n * T * 30
@@ -206,6 +243,31 @@ def test_trained_network_agrees_with_the_grid(two_rooms):
           f"BF16 weights vs a {grid_bytes / 1e6:.1f} MB distance grid")
     assert grid_share <= 0.2
     sim.close()
+    # the trained networks' queries against the plain FP64 network: within
+    # the rounding bound, and how many margin decisions (for the robot's
+    # radii) the BF16 rounding changes
+    radii = np.unique(np.asarray(ROBOT.sphere_radius, np.float64))
+    for k in range(2):
+        Bq, Pq, centre = ss.nsdf_get_weights(k)
+        plain = plain_mlp(Bq, Pq)
+        rng = np.random.default_rng(20 + k)
+        lo = scenes[k].grid_origin.astype(np.float64)
+        hi = lo + (scenes[k].grid_dims - 1) * np.float64(scenes[k].grid_h)
+        pts = rng.uniform(lo, hi, (4096, 3)).astype(np.float32)
+        out = torch.empty(len(pts), dtype=torch.float32, device="cuda")
+        ss.nsdf_query(k, torch.from_numpy(pts).cuda(), out)
+        torch.cuda.synchronize()
+        gpu = out.cpu().numpy().astype(np.float64)
+        ref, bnd, parts = plain.rounding_bound(pts.astype(np.float64) - centre, terms=True)
+        fl = sum(int(np.sum((gpu - r >= MARGIN) != (ref - r >= MARGIN))) for r in radii)
+        err, _ = plain_errors([np.abs(gpu - ref)], [bnd], [parts[:, 3]], fl,
+                              len(pts) * len(radii), f"trained network, scene {k}")
+        # the worst-case first-order bound (every rounding aligned) is loose,
+        # a few centimetres; the errors are sums of many independent
+        # roundings and stay within 6 deviations (asserted above): under half
+        # the 2 cm margin, with few margin decisions changed by rounding
+        assert err.max() < 0.5 * MARGIN
+        assert fl <= 0.01 * len(pts) * len(radii)
     # restore the random weights the other tests use
     for k in range(2):
         ss.nsdf_set_weights(k, B, Ps[k])

@@ -57,9 +57,13 @@ def test_reset_matches_oracle(room):
         st = O.Oracle.make_state((0, 0, 0), np.zeros(7))
         r = orc.reset(st, 1, e, M, 0.03, 0.06)
         assert r.failed == 0
+        placed = (np.allclose(s["obj"][e, :M], O.Oracle.state_objs(st), atol=1e-5)
+                  and abs(s["base_x"][e] - st.base[0]) < 1e-5
+                  and abs(s["base_z"][e] - st.base[1]) < 1e-5)
         if r.near_band:
             nb += 1
-            continue
+            if not placed:   # a near-band test chose another try: excused
+                continue
         assert s["episode"][e] == st.episode == 1
         assert s["held"][e] == -1 and s["step"][e] == 0
         assert np.allclose(s["obj"][e, :M], O.Oracle.state_objs(st), atol=1e-5)
@@ -168,7 +172,10 @@ def test_maximum_sizes(room):
     for e in range(n):
         st = oracle_state(before_reset, e, M)
         r = orc.reset(st, 11, e, M, 0.03, 0.035)
-        if r.near_band:
+        placed = (np.allclose(s["obj"][e, :M], O.Oracle.state_objs(st), atol=1e-5)
+                  and abs(s["base_x"][e] - st.base[0]) < 1e-5
+                  and abs(s["base_z"][e] - st.base[1]) < 1e-5)
+        if r.near_band and not placed:   # a near-band test chose another try: excused
             continue
         assert np.allclose(s["obj"][e, :M], O.Oracle.state_objs(st), atol=1e-5), e
         assert abs(s["base_x"][e] - st.base[0]) < 1e-5 and abs(s["base_z"][e] - st.base[1]) < 1e-5
@@ -183,7 +190,7 @@ def test_maximum_sizes(room):
         for e in range(n):
             check_image(orc, after, out, e, W, H, M, tally)
     print(tally)
-    assert tally.envs - tally.near_band >= 4
+    assert tally.envs - tally.near_band_flips >= 4
     sim.close()
 
 

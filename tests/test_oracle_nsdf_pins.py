@@ -224,3 +224,110 @@ def test_neural_rule_margin_is_inclusive_and_banded():
     d[i] = np.nextafter(r[i] + 0.02, 0)      # just below: the grid decides
     out = orc.step_nsdf(_state(orc), back, d, 0.02, 1e-3)
     assert out.contact_mask & (1 << i) and out.near_band >= 1
+
+
+# ---------------------------------------------------------------------------
+# The rounding-error bound of the BF16-operand network (orc_mlp_rounding_bound)
+# ---------------------------------------------------------------------------
+UB, UF = 2.0 ** -8, 2.0 ** -24
+
+
+def _random_net(seed, dims=(64, 128, 128, 128, 128, 1), bias=0.05):
+    rng = np.random.default_rng(seed)
+    B = rng.normal(0, 0.5, (dims[0] // 2, 3))
+    Ws = [rng.normal(0, math.sqrt(2.0 / dims[l]), (dims[l + 1], dims[l]))
+          for l in range(len(dims) - 1)]
+    bs = [rng.normal(0, bias, dims[l + 1]) for l in range(len(dims) - 1)]
+    return B, Ws, bs
+
+
+def _numpy_forward(B, Ws, bs, x, bump=None):
+    """Plain FP64 forward written out with numpy; bump(l, a) may perturb the
+    operand a_l (layer l's input) before it is used."""
+    ph = 2 * np.pi * (B @ x)
+    a = np.concatenate([np.sin(ph), np.cos(ph)])
+    for l, (W, b) in enumerate(zip(Ws, bs)):
+        if bump is not None:
+            a = bump(l, a)
+        z = W @ a + b
+        a = z if l == len(Ws) - 1 else np.maximum(z, 0.0)
+    return float(a[0])
+
+
+def test_rounding_bound_of_one_linear_layer_is_its_closed_form():
+    # d = w . gamma(x) + b: the operand term is u_b sum |w_i gamma_i|, the
+    # feature term feat_err (1 + u_b) sum |w_i|, the FP32 sum 2 K u_f sum
+    # |w_i gamma_i| and the bias add u_f (|d| + |b|)
+    B, Ws, bs = _random_net(3, dims=(16, 1))
+    x = np.array([0.3, -1.2, 0.7])
+    ph = 2 * np.pi * (B @ x)
+    gam = np.concatenate([np.sin(ph), np.cos(ph)])
+    w, b = Ws[0][0], bs[0][0]
+    d = float(w @ gam + b)
+    want = (UB * np.abs(w * gam).sum() + 4e-7 * (1 + UB) * np.abs(w).sum()
+            + 2 * 16 * UF * np.abs(w * gam).sum() + UF * (abs(d) + abs(b)))
+    out, bnd = O.MLP64(B, Ws, bs).rounding_bound(x[None], feat_err=4e-7)
+    assert out[0] == pytest.approx(d, rel=1e-13)
+    assert bnd[0] == pytest.approx(want, rel=1e-12)
+
+
+def test_rounding_bound_operand_term_is_the_worst_case_first_order_shift():
+    # perturb every operand a_{l,i} by h |a_{l,i}| in the direction that
+    # raises d (the sign of a central finite difference): d moves by
+    # h sum |dd/da_{l,i}| |a_{l,i}| to first order, which is the bound's
+    # operand term with u_b = h (the FP32 sums add a few per cent on top)
+    B, Ws, bs = _random_net(5)
+    for x in (np.array([0.1, 0.9, -0.4]), np.array([-1.3, 0.2, 0.6])):
+        base = _numpy_forward(B, Ws, bs, x)
+        # operands of the plain network at x
+        ops = []
+        _numpy_forward(B, Ws, bs, x, bump=lambda l, a: (ops.append(a.copy()), a)[1])
+        signs = []
+        for l, a in enumerate(ops):
+            s = np.zeros_like(a)
+            for i in range(len(a)):
+                if a[i] == 0.0:
+                    continue
+                e = 1e-6
+                def up(k, v, i=i, l=l, e=e):
+                    if k == l:
+                        v = v.copy()
+                        v[i] += e
+                    return v
+                def dn(k, v, i=i, l=l, e=e):
+                    if k == l:
+                        v = v.copy()
+                        v[i] -= e
+                    return v
+                s[i] = np.sign(_numpy_forward(B, Ws, bs, x, up) - _numpy_forward(B, Ws, bs, x, dn))
+            signs.append(s)
+        h = 1e-5
+        shifted = _numpy_forward(B, Ws, bs, x,
+                                 bump=lambda l, a: a + h * signs[l] * np.abs(ops[l]))
+        first_order = (shifted - base) / h * UB
+        _, bnd, parts = O.MLP64(B, Ws, bs).rounding_bound(x[None], feat_err=0.0, terms=True)
+        assert first_order > 0
+        assert parts[0, 0] == pytest.approx(first_order, rel=2e-3)
+        assert parts[0, 1] == 0.0 and 0 < parts[0, 2] < 0.1 * parts[0, 0]
+
+
+def test_rounding_bound_covers_the_bf16_operand_mode():
+    # the oracle's BF16-operand mode rounds exactly the operands the bound
+    # accounts for (its sums stay FP64): it must lie within the bound, and
+    # the bound must not be vacuous
+    B, Ws, bs = _random_net(9)
+    rng = np.random.default_rng(4)
+    X = rng.uniform(-2, 2, (300, 3))
+    plain, bnd, parts = O.MLP64(B, Ws, bs).rounding_bound(X, feat_err=0.0, terms=True)
+    assert np.allclose(plain, O.MLP64(B, Ws, bs).forward(X), rtol=1e-12, atol=1e-12)
+    rounded = O.MLP64(B, Ws, bs, bf16_operands=True).forward(X)
+    err = np.abs(rounded - plain)
+    ratio = err / bnd
+    z = err / parts[:, 3]
+    print(f"|bf16 - plain| / bound: median {np.median(ratio):.3f}, max {ratio.max():.3f}; "
+          f"bound median {np.median(bnd):.2e}; in standard deviations: median "
+          f"{np.median(z):.2f}, max {z.max():.2f}")
+    assert np.all(err <= bnd)
+    assert ratio.max() > 0.05
+    # independent roundings: the errors spread like the stated deviation
+    assert 0.3 < np.sqrt(np.mean(z ** 2)) < 3.0
