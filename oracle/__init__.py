@@ -72,7 +72,9 @@ class State_c(C.Structure):
                 ("c_off", C.c_double * 3), ("p_pre", C.c_double * 3), ("n_obj", C.c_int32),
                 ("obj", (C.c_double * 4) * MAX_OBJ), ("step_count", C.c_int32),
                 ("episode", C.c_int32), ("goal", C.c_double * 3), ("obj_start", C.c_double * 3),
-                ("prev_a", C.c_double * 7), ("prev_d", C.c_double), ("prev_e", C.c_double)]
+                ("prev_a", C.c_double * 7), ("prev_d", C.c_double), ("prev_e", C.c_double),
+                ("boxes", C.c_int32), ("box", (C.c_double * 4) * MAX_OBJ),
+                ("r_off", C.c_double * 9)]
 
 
 class StepOut_c(C.Structure):
@@ -143,6 +145,12 @@ def _declare(L):
     L.orc_mlp_rounding_bound.argtypes = [f64p, C.c_int, P(f64p), P(f64p), i32p, C.c_int, f64p,
                                          C.c_double, f64p]
     L.orc_mlp_rounding_bound.restype = C.c_double
+    L.orc_box_distance.argtypes = [P(State_c), C.c_int, f64p]
+    L.orc_box_distance.restype = C.c_double
+    L.orc_box_spheres.argtypes = [f64p, f64p]
+    L.orc_box_spheres.restype = C.c_double
+    L.orc_boxes_overlap.argtypes = [f64p, f64p, f64p, f64p, P(C.c_int)]
+    L.orc_boxes_overlap.restype = C.c_int
 
 
 def _p(a, t):
@@ -150,7 +158,8 @@ def _p(a, t):
 
 
 class Oracle:
-    """FP64 oracle bound to one robot, one scene and the instanced object mesh."""
+    """FP64 oracle bound to one robot, one scene and the instanced object mesh
+    (the icosahedron for sphere objects, the unit cube for box objects)."""
 
     # rasteriser ambiguity band (1/64 px), relative depth tolerance and the
     # smallest |cos| of a hit that is not flagged as grazing
@@ -216,9 +225,12 @@ class Oracle:
     # ---------------------------------------------------------------- state
     @staticmethod
     def make_state(base, q, held=-1, c_off=(0, 0, 0), p_pre=(0, 0, 0), objs=None,
-                   step_count=0, episode=0, task=None):
+                   step_count=0, episode=0, task=None, boxes=None, r_off=None):
         """task: [16] goal xyz, target start xyz, previous joint actions [7],
-        previous tip-target and target-goal distances (the GPU's layout)."""
+        previous tip-target and target-goal distances (the GPU's layout).
+        boxes: [n][4] half extents and yaw per object (the oriented-box object
+        model; None: spheres); r_off: [9] the held box's rotation in the
+        tool frame, row-major."""
         st = State_c()
         st.base[:] = [float(x) for x in base]
         st.q[:] = [float(x) for x in q]
@@ -237,7 +249,18 @@ class Oracle:
             st.obj_start[:] = t[3:6]
             st.prev_a[:] = t[6:13]
             st.prev_d, st.prev_e = t[13], t[14]
+        if boxes is not None:
+            st.boxes = 1
+            bx = np.asarray(boxes, np.float64)
+            for j in range(len(bx)):
+                st.box[j][:] = [float(x) for x in bx[j]]
+            if r_off is not None:
+                st.r_off[:] = [float(x) for x in np.ravel(r_off)]
         return st
+
+    @staticmethod
+    def state_boxes(st):
+        return np.array([[st.box[j][a] for a in range(4)] for j in range(st.n_obj)]).reshape(-1, 4)
 
     @staticmethod
     def state_objs(st):
@@ -388,6 +411,30 @@ class Oracle:
             cos_out[...] = cs.reshape(H, W)
         return (depth.reshape(H, W), rgb.reshape(H, W), amb.reshape(H, W).astype(bool),
                 win.reshape(H, W), stats)
+
+
+def box_distance(st, j, c):
+    """Exact signed distance from c to resting box j of state st."""
+    cc = np.ascontiguousarray(c, np.float64)
+    return lib().orc_box_distance(C.byref(st), int(j), _p(cc, f64p))
+
+
+def box_spheres(h):
+    """The eight carried spheres of a box with half extents h: centres in
+    its frame [8][3] and their radius."""
+    hh = np.ascontiguousarray(h, np.float64)
+    out = np.zeros((8, 3))
+    s = lib().orc_box_spheres(_p(hh, f64p), _p(out, f64p))
+    return out, s
+
+
+def boxes_overlap(pa, ba, pb, bb):
+    """Overlap of two upright boxes (centres p, (hx, hy, hz, yaw)) and the
+    near-band count of the decision."""
+    a = [np.ascontiguousarray(x, np.float64) for x in (pa, ba, pb, bb)]
+    nb = C.c_int(0)
+    r = lib().orc_boxes_overlap(*[_p(x, f64p) for x in a], C.byref(nb))
+    return bool(r), nb.value
 
 
 def philox4x32_10(ctr, key):

@@ -533,8 +533,295 @@ static int slide_search(const orc_robot* rb, const orc_scene* sc, const orc_stat
   return 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Oriented boxes (appendix "Additional Collision-Detection Details": the   */
+/* paper's resting objects are oriented boxes and a grasped object is a set */
+/* of spheres).  A resting box stands upright: centre p, half extents h,    */
+/* rotation R_y(yaw) (the robot base's convention: x axis (cos, 0, -sin),   */
+/* z axis (sin, 0, cos)).                                                   */
+/* ------------------------------------------------------------------------ */
+void orc_box_local(const double p[3], double yaw, const double c[3], double q[3]) {
+  /* q = R_y(yaw)^T (c - p) */
+  const double cy = cos(yaw), sy = sin(yaw);
+  const double dx = c[0] - p[0], dy = c[1] - p[1], dz = c[2] - p[2];
+  q[0] = cy * dx - sy * dz;
+  q[1] = dy;
+  q[2] = sy * dx + cy * dz;
+}
+
+/* Exact signed distance from q (box frame) to the box [-h, h]. */
+static double sd_box_local(const double q[3], const double h[3]) {
+  double o[3], out = 0.0, in = -INFINITY;
+  for (int a = 0; a < 3; ++a) {
+    o[a] = fabs(q[a]) - h[a];
+    if (o[a] > 0) out += o[a] * o[a];
+    if (o[a] > in) in = o[a];
+  }
+  return sqrt(out) + (in < 0 ? in : 0.0);
+}
+
+double orc_box_distance(const orc_state* st, int j, const double c[3]) {
+  double q[3];
+  orc_box_local(st->obj[j], st->box[j][3], c, q);
+  return sd_box_local(q, st->box[j]);
+}
+
+static int sphere_box_contact(const orc_state* st, int j, const double c[3], double r, int* nb) {
+  const double d = orc_box_distance(st, j, c);
+  if (fabs(d - r) < ORC_BAND) (*nb)++;
+  return d < r;
+}
+
+/* The eight carried spheres: radius s = min(h), centres at the corners of
+ * the box shrunk by s, (+-(hx-s), +-(hy-s), +-(hz-s)); corner k has the
+ * signs of bits 0 (x), 1 (y), 2 (z) of k (bit clear = minus). */
+double orc_box_spheres(const double h[3], double centres[8][3]) {
+  const double s = fmin(h[0], fmin(h[1], h[2]));
+  for (int k = 0; k < 8; ++k)
+    for (int a = 0; a < 3; ++a) centres[k][a] = ((k >> a) & 1 ? 1.0 : -1.0) * (h[a] - s);
+  return s;
+}
+
+/* Two upright boxes overlap iff their vertical intervals overlap and no
+ * ground-plane axis among the four box axes separates their footprints
+ * (separating-axis theorem for convex polygons); touching is not overlap. */
+int orc_boxes_overlap(const double pa[3], const double ba[4], const double pb[3],
+                      const double bb[4], int* nb) {
+  const double gy = fabs(pa[1] - pb[1]) - (ba[1] + bb[1]);
+  if (fabs(gy) < ORC_BAND) (*nb)++;
+  if (gy >= 0) return 0;
+  const double ax[4][2] = {{cos(ba[3]), -sin(ba[3])}, {sin(ba[3]), cos(ba[3])},
+                           {cos(bb[3]), -sin(bb[3])}, {sin(bb[3]), cos(bb[3])}};
+  const double d[2] = {pb[0] - pa[0], pb[2] - pa[2]};
+  double sep = -INFINITY;
+  for (int k = 0; k < 4; ++k) {
+    const double* u = ax[k];
+    const double ra = ba[0] * fabs(u[0] * ax[0][0] + u[1] * ax[0][1]) +
+                      ba[2] * fabs(u[0] * ax[1][0] + u[1] * ax[1][1]);
+    const double rb_ = bb[0] * fabs(u[0] * ax[2][0] + u[1] * ax[2][1]) +
+                       bb[2] * fabs(u[0] * ax[3][0] + u[1] * ax[3][1]);
+    const double sk = fabs(d[0] * u[0] + d[1] * u[1]) - (ra + rb_);
+    if (sk > sep) sep = sk;
+  }
+  if (fabs(sep) < ORC_BAND) (*nb)++;
+  return sep < 0;
+}
+
+/* World rotation of object j: R_y(yaw) resting, R_ee R_off while held. */
+static void box_rotation(const orc_state* st, int j, const double ee[12], double R[9]) {
+  if (j == st->held) {
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c)
+        R[3 * r + c] = ee[3 * r] * st->r_off[c] + ee[3 * r + 1] * st->r_off[3 + c] +
+                       ee[3 * r + 2] * st->r_off[6 + c];
+  } else {
+    const double cy = cos(st->box[j][3]), sy = sin(st->box[j][3]);
+    const double Ry[9] = {cy, 0, sy, 0, 1, 0, -sy, 0, cy};
+    memcpy(R, Ry, sizeof(Ry));
+  }
+}
+
+/* Upright yaw of a box with world rotation R: the heading of its x axis in
+ * the ground plane, or of its z axis when the x axis points (nearly) up. */
+static double upright_yaw(const double R[9], int* nb) {
+  const double hx = hypot(R[0], R[6]);
+  if (fabs(hx - 1e-3) < ORC_BAND) (*nb)++;
+  if (hx >= 1e-3) return atan2(-R[6], R[0]);
+  return atan2(R[2], R[8]);
+}
+
+/* Reward of the rearrangement task and the egomotion observations, after
+ * the step's motion and grasp/release (st updated, ee the tool frame at the
+ * accepted pose, event the step's grasp event). */
+static void task_epilogue(orc_state* st, const double a[11], const double ee[12], uint8_t event,
+                          orc_step_out* out, int* nbp) {
+  int nb = 0;
+  /* reward of the rearrangement task (App. "Additional Task Details"):
+   *   r = 10 I_success + 5 I_pick + (d_{t-1} - d_t) + (e_{t-1} - e_t) - 0.001 C_t
+   * with d the tip-target distance, e the target-goal distance, C_t the
+   * squared change of the 7 joint actions; success = stop called while the
+   * target rests within 15 cm of the goal; pick = the target just grasped.
+   * Egomotion observations (Sec. 4.1): the target's start and the goal
+   * relative to the base and to the tool tip, in the base frame. */
+  {
+    const double tip[3] = {ee[9], ee[10], ee[11]};
+    double C = 0.0;
+    for (int k = 0; k < 7; ++k) C += (a[2 + k] - st->prev_a[k]) * (a[2 + k] - st->prev_a[k]);
+    double r = -0.001 * C;
+    uint8_t success = 0;
+    if (st->n_obj > 0) {
+      const double d = dist3(tip, st->obj[0]), e = dist3(st->obj[0], st->goal);
+      const int pick = event == 1 && st->held == 0;
+      if (a[10] >= 0.5 && st->held != 0) {
+        if (fabs(e - 0.15) < ORC_BAND) nb++;
+        success = e < 0.15;
+      }
+      r += 10.0 * success + 5.0 * pick + (st->prev_d - d) + (st->prev_e - e);
+      st->prev_d = d;
+      st->prev_e = e;
+    }
+    for (int k = 0; k < 7; ++k) st->prev_a[k] = a[2 + k];
+    const double c = cos(st->base[2]), sn = sin(st->base[2]);
+    const double pb[3] = {st->base[0], 0.0, st->base[1]};
+    const double* from[4] = {pb, pb, tip, tip};
+    const double* to[4] = {st->obj_start, st->goal, st->obj_start, st->goal};
+    for (int v = 0; v < 4; ++v) {
+      const double w[3] = {to[v][0] - from[v][0], to[v][1] - from[v][1], to[v][2] - from[v][2]};
+      out->task_obs[3 * v] = c * w[0] - sn * w[2];
+      out->task_obs[3 * v + 1] = w[1];
+      out->task_obs[3 * v + 2] = sn * w[0] + c * w[2];
+    }
+    out->reward = r;
+    out->success = success;
+  }
+
+  *nbp += nb;
+}
+
+/* One step with the oriented-box object model (st->boxes): robot spheres
+ * against the static grid and the resting boxes (exact sphere-box distance
+ * in the box frame); a held box as its eight spheres against the static
+ * grid and the other boxes; grasp of the box nearest the tip sphere (by the
+ * exact distance); release: the box turns upright about its current
+ * heading, its four bottom spheres are cast down and it rests on the
+ * highest of their landing heights, unless a cast finds no surface or it
+ * would overlap another box (then it goes back to its pre-grasp pose). */
+static void step_boxes(const orc_robot* rb, const orc_scene* sc, orc_state* st, const double a[11],
+                       orc_step_out* out) {
+  int nb = 0;
+  double cb[3], cq[7];
+  candidate_pose(rb, st, a, cb, cq);
+  double links[8][12], ee[12], cam[12];
+  double cs[ORC_MAX_SPHERES][3];
+  orc_fk(rb, cb, cq, links, ee, NULL);
+  for (int i = 0; i < rb->n_spheres; ++i) {
+    double p[3] = {rb->sphere_pos[3 * i], rb->sphere_pos[3 * i + 1], rb->sphere_pos[3 * i + 2]};
+    fr_apply(links[rb->sphere_link[i]], p, cs[i]);
+  }
+  uint32_t mask = 0;
+  uint8_t flags = 0;
+  const int h = st->held;
+  for (int i = 0; i < rb->n_spheres; ++i) {
+    const double r = rb->sphere_radius[i];
+    if (static_contact(sc, cs[i], r, &nb)) { mask |= 1u << i; flags |= 1; }
+    for (int j = 0; j < st->n_obj; ++j)
+      if (j != h && sphere_box_contact(st, j, cs[i], r, &nb)) { mask |= 1u << i; flags |= 2; }
+  }
+  if (h >= 0) {
+    /* the carried spheres at the candidate tool frame: c = T_ee (c_off + R_off k) */
+    double loc[8][3];
+    const double s = orc_box_spheres(st->box[h], loc);
+    for (int k = 0; k < 8; ++k) {
+      double o[3];
+      for (int r = 0; r < 3; ++r)
+        o[r] = st->c_off[r] + st->r_off[3 * r] * loc[k][0] + st->r_off[3 * r + 1] * loc[k][1] +
+               st->r_off[3 * r + 2] * loc[k][2];
+      double c[3];
+      fr_apply(ee, o, c);
+      if (static_contact(sc, c, s, &nb)) { mask |= 1u << 30; flags |= 1 | 4; }
+      for (int j = 0; j < st->n_obj; ++j)
+        if (j != h && sphere_box_contact(st, j, c, s, &nb)) { mask |= 1u << 30; flags |= 2 | 4; }
+    }
+  }
+  const int reverted = mask != 0;
+  if (!reverted) {
+    memcpy(st->base, cb, sizeof(cb));
+    memcpy(st->q, cq, sizeof(cq));
+  }
+  orc_fk(rb, st->base, st->q, links, ee, cam);
+
+  uint8_t event = 0;
+  const int grasp = a[9] >= 0.5;
+  if (grasp && st->held < 0) {
+    const double tip[3] = {ee[9], ee[10], ee[11]};
+    const double rg = rb->grasp_radius;
+    int best = -1;
+    double bests = INFINITY;
+    for (int j = 0; j < st->n_obj; ++j) {
+      const double d = orc_box_distance(st, j, tip);
+      if (fabs(d - rg) < ORC_BAND) nb++;
+      if (d < rg) {
+        if (best >= 0 && fabs(d - bests) < ORC_BAND) nb++;
+        if (d < bests) { bests = d; best = j; }
+      }
+    }
+    if (best >= 0) {
+      /* c_off = R_ee^T (p - t_ee), R_off = R_ee^T R_y(yaw) */
+      const double* p = st->obj[best];
+      const double dp[3] = {p[0] - ee[9], p[1] - ee[10], p[2] - ee[11]};
+      double Ry[9];
+      box_rotation(st, best, ee, Ry);  /* not yet held: R_y(yaw) */
+      for (int r = 0; r < 3; ++r) {
+        st->c_off[r] = ee[r] * dp[0] + ee[3 + r] * dp[1] + ee[6 + r] * dp[2];
+        for (int c = 0; c < 3; ++c)
+          st->r_off[3 * r + c] = ee[r] * Ry[c] + ee[3 + r] * Ry[3 + c] + ee[6 + r] * Ry[6 + c];
+      }
+      memcpy(st->p_pre, p, 3 * sizeof(double));
+      st->held = best;
+      event = 1;
+    } else {
+      event = 2;
+    }
+  } else if (!grasp && st->held >= 0) {
+    const int j = st->held;
+    double p[3], R[9];
+    fr_apply(ee, st->c_off, p);
+    box_rotation(st, j, ee, R);
+    const double yaw = upright_yaw(R, &nb);
+    const double* hb = st->box[j];
+    double loc[8][3];
+    const double s = orc_box_spheres(hb, loc);
+    const double cy = cos(yaw), sy = sin(yaw);
+    int ok = 1;
+    double ytop = -INFINITY;
+    for (int k = 0; k < 8; ++k) {
+      if ((k >> 1) & 1) continue;  /* the four bottom spheres */
+      const double b[3] = {p[0] + cy * loc[k][0] + sy * loc[k][2], p[1] + loc[k][1],
+                           p[2] - sy * loc[k][0] + cy * loc[k][2]};
+      int okk = 0;
+      const double y = orc_snap(sc, b, s + (double)rb->rest_clearance, &okk, &nb);
+      ok &= okk;
+      if (y > ytop) ytop = y;
+    }
+    const double land[3] = {p[0], ytop + (hb[1] - s), p[2]};
+    const double bl[4] = {hb[0], hb[1], hb[2], yaw};
+    int overlap = 0;
+    if (ok)
+      for (int m = 0; m < st->n_obj; ++m)
+        if (m != j && orc_boxes_overlap(land, bl, st->obj[m], st->box[m], &nb)) overlap = 1;
+    if (ok && !overlap) {
+      memcpy(st->obj[j], land, sizeof(land));
+      st->box[j][3] = yaw;
+      event = 3;
+    } else {
+      memcpy(st->obj[j], st->p_pre, 3 * sizeof(double));
+      event = 4;
+    }
+    st->held = -1;
+    memset(st->c_off, 0, sizeof(st->c_off));
+    memset(st->r_off, 0, sizeof(st->r_off));
+  }
+  if (st->held >= 0) fr_apply(ee, st->c_off, st->obj[st->held]);
+  st->step_count += 1;
+  task_epilogue(st, a, ee, event, out, &nb);
+  out->contact_mask = mask;
+  out->flags = flags;
+  out->event = event;
+  out->reverted = (uint8_t)reverted;
+  out->near_band = nb;
+  out->ee[0] = ee[9]; out->ee[1] = ee[10]; out->ee[2] = ee[11];
+  memcpy(out->cam_R, cam, 9 * sizeof(double));
+  memcpy(out->cam_t, cam + 9, 3 * sizeof(double));
+}
+
 void orc_step_ex(const orc_robot* rb, const orc_scene* sc, orc_state* st, const float act[11],
                  const orc_step_opts* opt, orc_step_out* out) {
+  if (st->boxes) {  /* the oriented-box object model: the plain step only */
+    double ab[11];
+    clip_actions(act, ab);
+    step_boxes(rb, sc, st, ab, out);
+    return;
+  }
   const double* dhat = opt->dhat;
   const double margin = opt->margin, band = opt->band;
   double a[11];
@@ -702,44 +989,7 @@ void orc_step_ex(const orc_robot* rb, const orc_scene* sc, orc_state* st, const 
   if (st->held >= 0) fr_apply(ee, st->c_off, st->obj[st->held]);
   st->step_count += 1;
 
-  /* reward of the rearrangement task (App. "Additional Task Details"):
-   *   r = 10 I_success + 5 I_pick + (d_{t-1} - d_t) + (e_{t-1} - e_t) - 0.001 C_t
-   * with d the tip-target distance, e the target-goal distance, C_t the
-   * squared change of the 7 joint actions; success = stop called while the
-   * target rests within 15 cm of the goal; pick = the target just grasped.
-   * Egomotion observations (Sec. 4.1): the target's start and the goal
-   * relative to the base and to the tool tip, in the base frame. */
-  {
-    const double tip[3] = {ee[9], ee[10], ee[11]};
-    double C = 0.0;
-    for (int k = 0; k < 7; ++k) C += (a[2 + k] - st->prev_a[k]) * (a[2 + k] - st->prev_a[k]);
-    double r = -0.001 * C;
-    uint8_t success = 0;
-    if (st->n_obj > 0) {
-      const double d = dist3(tip, st->obj[0]), e = dist3(st->obj[0], st->goal);
-      const int pick = event == 1 && st->held == 0;
-      if (a[10] >= 0.5 && st->held != 0) {
-        if (fabs(e - 0.15) < ORC_BAND) nb++;
-        success = e < 0.15;
-      }
-      r += 10.0 * success + 5.0 * pick + (st->prev_d - d) + (st->prev_e - e);
-      st->prev_d = d;
-      st->prev_e = e;
-    }
-    for (int k = 0; k < 7; ++k) st->prev_a[k] = a[2 + k];
-    const double c = cos(st->base[2]), sn = sin(st->base[2]);
-    const double pb[3] = {st->base[0], 0.0, st->base[1]};
-    const double* from[4] = {pb, pb, tip, tip};
-    const double* to[4] = {st->obj_start, st->goal, st->obj_start, st->goal};
-    for (int v = 0; v < 4; ++v) {
-      const double w[3] = {to[v][0] - from[v][0], to[v][1] - from[v][1], to[v][2] - from[v][2]};
-      out->task_obs[3 * v] = c * w[0] - sn * w[2];
-      out->task_obs[3 * v + 1] = w[1];
-      out->task_obs[3 * v + 2] = sn * w[0] + c * w[2];
-    }
-    out->reward = r;
-    out->success = success;
-  }
+  task_epilogue(st, a, ee, event, out, &nb);
 
   out->contact_mask = mask;
   out->flags = flags;
@@ -764,7 +1014,45 @@ void orc_reset(const orc_robot* rb, const orc_scene* sc, orc_state* st, uint64_t
   st->episode += 1;
   st->n_obj = n_obj;
   double clear = rb->rest_clearance;
-  for (int j = 0; j < n_obj; ++j) {
+  for (int j = 0; j < n_obj && st->boxes; ++j) {
+    /* oriented boxes: half extents from one draw per object (counter word 3
+     * = 0x424F5845), each try a support, a position on its top shrunk by
+     * the footprint's circumradius, and a yaw; accepted when the box's
+     * eight spheres are clear of the static scene and it overlaps no box
+     * placed before it */
+    uint32_t cs0[4] = {(uint32_t)env, (uint32_t)st->episode, (uint32_t)j, 0x424F5845u}, ws[4];
+    orc_philox4x32_10(cs0, key, ws);
+    double* hb = st->box[j];
+    for (int a = 0; a < 3; ++a)
+      hb[a] = (double)rho_min + unit24(ws[a]) * ((double)rho_max - (double)rho_min);
+    const double rxz = sqrt(hb[0] * hb[0] + hb[2] * hb[2]);
+    double loc[8][3];
+    const double sr = orc_box_spheres(hb, loc);
+    int ok = 0;
+    for (uint32_t t = 0; t < 64 && !ok; ++t) {
+      uint32_t ctr[4] = {(uint32_t)env, (uint32_t)st->episode, (uint32_t)j, t}, w[4];
+      orc_philox4x32_10(ctr, key, w);
+      uint32_t si = (uint32_t)(((uint64_t)(w[0] >> 8) * (uint64_t)sc->n_supports) >> 24);
+      const float* sp = sc->supports + 5 * si;
+      double x0 = sp[0] + rxz, x1 = sp[2] - rxz, z0 = sp[1] + rxz, z1 = sp[3] - rxz;
+      double p[3] = {x0 + unit24(w[1]) * (x1 - x0), (double)sp[4] + hb[1] + clear,
+                     z0 + unit24(w[2]) * (z1 - z0)};
+      hb[3] = -PI + unit24(w[3]) * (2 * PI);
+      st->obj[j][0] = p[0]; st->obj[j][1] = p[1]; st->obj[j][2] = p[2];
+      st->obj[j][3] = sqrt(hb[0] * hb[0] + hb[1] * hb[1] + hb[2] * hb[2]);
+      const double cy = cos(hb[3]), sy = sin(hb[3]);
+      ok = 1;
+      for (int k = 0; k < 8 && ok; ++k) {
+        const double c[3] = {p[0] + cy * loc[k][0] + sy * loc[k][2], p[1] + loc[k][1],
+                             p[2] - sy * loc[k][0] + cy * loc[k][2]};
+        if (static_contact(sc, c, sr, &nb)) ok = 0;
+      }
+      for (int k = 0; k < j && ok; ++k)
+        if (orc_boxes_overlap(p, hb, st->obj[k], st->box[k], &nb)) ok = 0;
+    }
+    if (!ok) failed++;
+  }
+  for (int j = 0; j < n_obj && !st->boxes; ++j) {
     double rho = 0.0;
     int ok = 0;
     for (uint32_t t = 0; t < 64 && !ok; ++t) {
@@ -798,7 +1086,9 @@ void orc_reset(const orc_robot* rb, const orc_scene* sc, orc_state* st, uint64_t
     for (int i = 0; i < rb->n_spheres; ++i) {
       double r = rb->sphere_radius[i];
       int c = static_contact(sc, cs[i], r, &nb);
-      for (int j = 0; j < n_obj; ++j) c |= pair_contact(cs[i], r, st->obj[j], st->obj[j][3], &nb);
+      for (int j = 0; j < n_obj; ++j)
+        c |= st->boxes ? sphere_box_contact(st, j, cs[i], r, &nb)
+                       : pair_contact(cs[i], r, st->obj[j], st->obj[j][3], &nb);
       if (c) ok = 0;
     }
   }
@@ -806,6 +1096,7 @@ void orc_reset(const orc_robot* rb, const orc_scene* sc, orc_state* st, uint64_t
   st->held = -1;
   memset(st->c_off, 0, sizeof(st->c_off));
   memset(st->p_pre, 0, sizeof(st->p_pre));
+  memset(st->r_off, 0, sizeof(st->r_off));
   st->step_count = 0;
   /* task: object 0 is the target; its goal lies on a support top, drawn
    * like an object placement from stream ORC_MAX_OBJ + 1 (first draw, not tested for
@@ -818,12 +1109,15 @@ void orc_reset(const orc_robot* rb, const orc_scene* sc, orc_state* st, uint64_t
   if (n_obj > 0 && sc->n_supports > 0) {
     uint32_t ctr[4] = {(uint32_t)env, (uint32_t)st->episode, ORC_MAX_OBJ + 1, 0u}, w[4];
     orc_philox4x32_10(ctr, key, w);
-    const double rho = st->obj[0][3];
+    /* a box target: shrunk by its footprint's circumradius, raised by hy */
+    const double rho = st->boxes ? sqrt(st->box[0][0] * st->box[0][0] + st->box[0][2] * st->box[0][2])
+                                 : st->obj[0][3];
+    const double lift = st->boxes ? st->box[0][1] : st->obj[0][3];
     uint32_t si = (uint32_t)(((uint64_t)(w[0] >> 8) * (uint64_t)sc->n_supports) >> 24);
     const float* sp = sc->supports + 5 * si;
     double x0 = sp[0] + rho, x1 = sp[2] - rho, z0 = sp[1] + rho, z1 = sp[3] - rho;
     st->goal[0] = x0 + unit24(w[1]) * (x1 - x0);
-    st->goal[1] = (double)sp[4] + rho + clear;
+    st->goal[1] = (double)sp[4] + lift + clear;
     st->goal[2] = z0 + unit24(w[2]) * (z1 - z0);
     memcpy(st->obj_start, st->obj[0], 3 * sizeof(double));
     double links[8][12], ee[12];
@@ -993,11 +1287,25 @@ void orc_render_cos(const orc_robot* rb, const orc_scene* sc, const orc_objmesh*
       for (int a = 0; a < 3; ++a) P[k][a] = sc->verts[3 * sc->tris[3 * t + k] + a];
     render_tri(P, t, sc->tri_rgb[t], cam, near, W, H, eps_px, C, cnt, dropz, &local);
   }
+  double ee[12];
+  if (st->boxes) orc_fk(rb, st->base, st->q, links, ee, NULL);
   for (int j = 0; j < st->n_obj; ++j) {
+    /* a sphere: the mesh scaled by rho; a box: the unit cube mesh mapped by
+     * R diag(h), R its world rotation */
+    double M[9] = {st->obj[j][3], 0, 0, 0, st->obj[j][3], 0, 0, 0, st->obj[j][3]};
+    if (st->boxes) {
+      double R[9];
+      box_rotation(st, j, ee, R);
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) M[3 * r + c] = R[3 * r + c] * st->box[j][c];
+    }
     for (int t = 0; t < om->n_tris; ++t) {
-      for (int k = 0; k < 3; ++k)
+      for (int k = 0; k < 3; ++k) {
+        const float* u = om->verts + 3 * om->tris[3 * t + k];
         for (int a = 0; a < 3; ++a)
-          P[k][a] = st->obj[j][a] + st->obj[j][3] * (double)om->verts[3 * om->tris[3 * t + k] + a];
+          P[k][a] = st->obj[j][a] + M[3 * a] * (double)u[0] + M[3 * a + 1] * (double)u[1] +
+                    M[3 * a + 2] * (double)u[2];
+      }
       render_tri(P, sc->n_tris + j * om->n_tris + t, om->obj_rgb[j], cam, near, W, H, eps_px, C,
                  cnt, dropz, &local);
     }

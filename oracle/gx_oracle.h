@@ -71,6 +71,15 @@ typedef struct {
   double obj_start[3];      /* the target's position at the episode start   */
   double prev_a[7];         /* previous step's joint actions (clipped)      */
   double prev_d, prev_e;    /* previous tip-target, target-goal distances   */
+  /* object model (appendix "Additional Collision-Detection Details"): 0 =
+   * objects are spheres of radius obj[j][3]; 1 = resting objects are boxes
+   * standing upright (half extents box[j][0..2], yaw box[j][3]; obj[j][3]
+   * is then the bounding radius |h|) and a grasped box is carried as a set
+   * of eight spheres, turning with the tool (r_off: its rotation in the
+   * tool frame, row-major). */
+  int32_t boxes;
+  double box[ORC_MAX_OBJ][4];
+  double r_off[9];
 } orc_state;
 
 typedef struct {
@@ -150,6 +159,16 @@ void orc_candidate_spheres(const orc_robot* rb, const orc_state* st, const float
                            double c[31][3], double r[31], int32_t active[31]);
 void orc_reset(const orc_robot* rb, const orc_scene* sc, orc_state* st, uint64_t seed,
                int32_t env, int32_t n_obj, float rho_min, float rho_max, orc_reset_out* out);
+/* Oriented boxes (st->boxes = 1): the exact distance from c to box j
+ * (negative inside), the box-frame coordinates of c, the eight carried
+ * spheres of a box (centres in its frame, common radius min(h)), and the
+ * overlap of two upright boxes (separating axes in the ground plane plus
+ * the vertical intervals; strict). */
+double orc_box_distance(const orc_state* st, int j, const double c[3]);
+void orc_box_local(const double p[3], double yaw, const double c[3], double q[3]);
+double orc_box_spheres(const double h[3], double centres[8][3]);
+int orc_boxes_overlap(const double pa[3], const double ba[4], const double pb[3],
+                      const double bb[4], int* nb);
 double orc_snap(const orc_scene* s, const double p[3], double target, int* ok, int* near_band);
 void orc_render(const orc_robot* rb, const orc_scene* sc, const orc_objmesh* om,
                 const orc_state* st, int32_t W, int32_t H, double eps_px, double tol_rel,

@@ -146,6 +146,16 @@ def icosahedron() -> tuple[np.ndarray, np.ndarray]:
     return v.astype(np.float32), f
 
 
+def unit_cube() -> tuple[np.ndarray, np.ndarray]:
+    """The box objects' instance mesh: corners (+-1, +-1, +-1), corner k
+    having the signs of bits 0 (x), 1 (y), 2 (z) of k (clear = minus); two
+    triangles per face, counter-clockwise seen from outside."""
+    v = np.array([[1.0 if (k >> a) & 1 else -1.0 for a in range(3)] for k in range(8)])
+    f = np.array([[0, 4, 6], [0, 6, 2], [1, 3, 7], [1, 7, 5], [0, 1, 5], [0, 5, 4],
+                  [2, 6, 7], [2, 7, 3], [0, 2, 3], [0, 3, 1], [4, 5, 7], [4, 7, 6]], np.int32)
+    return v.astype(np.float32), f
+
+
 def robot_colors(robot: "Robot") -> np.ndarray:
     """Flat colour of each robot collision sphere when the robot body is
     rendered: grey shades by link (base darkest)."""
