@@ -153,7 +153,10 @@ def kernel_capture(workload):
     """Per-launch figures of the rasteriser (DRAM bytes, warp instructions)
     scaled to the full workload from an ncu capture of a smaller case; None
     once the rasteriser source changed since the capture."""
-    p = os.path.join(ROOT, "profiles", f"raster_{SAME_VIEWS.get(workload, workload)}_traffic.json")
+    p = os.path.join(ROOT, "profiles", f"raster_{workload}_traffic.json")
+    if not os.path.exists(p):
+        p = os.path.join(ROOT, "profiles",
+                         f"raster_{SAME_VIEWS.get(workload, workload)}_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
