@@ -185,6 +185,22 @@ typedef struct {
                               use env_offset + local index, so a batch split
                               over several contexts (one per GPU) draws exactly
                               what one context over the whole batch draws    */
+  int32_t object_boxes;    /* the paper's object model (appendix "Additional
+                              Collision-Detection Details"): 0 objects are
+                              spheres; 1 resting objects are upright oriented
+                              boxes (half extents drawn in [obj_radius_min,
+                              obj_radius_max) per axis, yaw uniform; robot
+                              spheres tested by the exact sphere-box distance
+                              in the box frame) and a grasped box is carried
+                              as eight spheres of radius min(h) at its inset
+                              corners, turning with the tool; release stands
+                              it upright about its heading and rests it on the
+                              highest landing of its four bottom spheres unless
+                              it would overlap another box (separating axes),
+                              else restores it.  Boxes render as cubes mapped
+                              by rotation x half extents.  Only with sdf_mode 0
+                              and without heuristics, broad-phase or robot-body
+                              rendering (GX_EINVAL otherwise)                 */
 } gx_config;
 
 /* Outputs of one step, device memory owned by the caller (e.g. torch
@@ -271,11 +287,15 @@ gx_status gx_load_state(gx_ctx* ctx, const void* host, size_t bytes);
 /* Byte offsets of the state arrays, in this order: base_x, base_z, yaw
  * [n] f32; q [7][n] f32; held [n] i32; c_off [3][n] f32 (held object in the
  * tool-tip frame); p_pre [3][n] f32 (its pre-grasp position); obj
- * [n][n_objects][4] f32 (x, y, z, radius); step [n] i32; episode [n] i32;
- * task [n][16] f32 (goal xyz, target start xyz, previous joint actions [7],
- * previous tip-target and target-goal distances, unused).
+ * [n][n_objects][4] f32 (x, y, z, radius; for box objects the bounding
+ * radius); step [n] i32; episode [n] i32; task [n][16] f32 (goal xyz,
+ * target start xyz, previous joint actions [7], previous tip-target and
+ * target-goal distances, unused); box [n][n_objects][4] f32 (box objects:
+ * half extents xyz and resting yaw; unused with spheres); r_off [9][n] f32
+ * (box objects: the held box's rotation in the tool frame, row-major).
  * Each array starts on a 256-byte boundary of the blob. */
-gx_status gx_state_layout(const gx_ctx* ctx, size_t offsets[11]);
+#define GX_STATE_ARRAYS 13
+gx_status gx_state_layout(const gx_ctx* ctx, size_t offsets[GX_STATE_ARRAYS]);
 
 /* Per-kernel device time recorded since the previous call when the context
  * was created with profile bit 0 set: ms[0] physics (both passes when

@@ -39,10 +39,11 @@ struct gx_ctx {
   int* d_env_scene = nullptr;
   void* d_state = nullptr;
   size_t state_bytes = 0;
-  size_t off[11] = {0};
+  size_t off[kStateArrays] = {0};
   StateView st{};
   float* d_cam = nullptr;
   float4* d_robot_sph = nullptr;       // robot spheres for rendering the robot body
+  float4* d_held_M = nullptr;          // box objects: the held box's world rotation x extents
   BpCell* d_bp = nullptr;              // object broad-phase cells
   int bp_cells = 0;
   unsigned* d_err = nullptr;
@@ -216,7 +217,12 @@ void enqueue_step(gx_ctx* c, const float* actions, const gx_outputs& out, cudaSt
     if (ev) cudaEventRecord(ev[2], s);
     pp.nsdf_pass = 2;
   }
-  launch_physics(pp, s);
+  if (c->cfg.object_boxes) {
+    pp.held_M = c->d_held_M;
+    launch_physics_boxes(pp, s);
+  } else {
+    launch_physics(pp, s);
+  }
   if (ev) cudaEventRecord(ev[3], s);
   RasterParams rp{};
   rp.n = c->n;
@@ -240,6 +246,11 @@ void enqueue_step(gx_ctx* c, const float* actions, const gx_outputs& out, cudaSt
   rp.omesh_nt = c->set->omesh_nt;
   rp.obj_rgb = c->set->obj_rgb;
   rp.robot_sph = c->d_robot_sph;
+  if (c->cfg.object_boxes) {
+    rp.obox = c->st.obox;
+    rp.held_M = c->d_held_M;
+    rp.held = c->st.held;
+  }
   rp.near_ = c->near_;
   rp.depth = out.depth;
   rp.depth_fp16 = c->cfg.depth_fp16;
@@ -455,6 +466,12 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
     return fail(nullptr, GX_EINVAL, "raster_order must be 0, 1 or 2");
   if (c.env_offset < 0 || (int64_t)c.env_offset + c.n_envs > INT32_MAX)
     return fail(nullptr, GX_EINVAL, "env_offset must be >= 0 with env_offset + n_envs < 2^31");
+  if (c.object_boxes < 0 || c.object_boxes > 1)
+    return fail(nullptr, GX_EINVAL, "object_boxes must be 0 or 1");
+  if (c.object_boxes && (c.heuristics || c.broadphase || c.render_robot || c.sdf_mode != 0))
+    return fail(nullptr, GX_EINVAL,
+                "object_boxes: the box model runs the plain step on the distance grid "
+                "(no heuristics, broad-phase, robot-body rendering or other static test)");
   gx_ctx* x = new gx_ctx();
   x->set = set;
   x->cfg = c;
@@ -503,10 +520,11 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
     return bail(e, "map");
   // state blob: arrays on 256-byte boundaries
   const size_t n = x->n, M = x->M;
-  const size_t sizes[11] = {n * 4, n * 4, n * 4, 7 * n * 4, n * 4, 3 * n * 4, 3 * n * 4,
-                            n * (M ? M : 1) * 16, n * 4, n * 4, n * 64};
+  const size_t sizes[kStateArrays] = {n * 4, n * 4, n * 4, 7 * n * 4, n * 4, 3 * n * 4,
+                                      3 * n * 4, n * (M ? M : 1) * 16, n * 4, n * 4, n * 64,
+                                      n * (M ? M : 1) * 16, 9 * n * 4};
   size_t off = 0;
-  for (int k = 0; k < 11; ++k) {
+  for (int k = 0; k < kStateArrays; ++k) {
     x->off[k] = off;
     off += (sizes[k] + 255) & ~(size_t)255;
   }
@@ -525,6 +543,12 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
   x->st.step = (int*)(b + x->off[8]);
   x->st.episode = (int*)(b + x->off[9]);
   x->st.task = (float*)(b + x->off[10]);
+  x->st.obox = (float4*)(b + x->off[11]);
+  x->st.roff = (float*)(b + x->off[12]);
+  if (c.object_boxes &&
+      ((e = cudaMalloc(&x->d_held_M, n * 3 * sizeof(float4))) != cudaSuccess ||
+       (e = cudaMemset(x->d_held_M, 0, n * 3 * sizeof(float4))) != cudaSuccess))
+    return bail(e, "held box rotation");
   if ((e = cudaMemset(x->st.held, 0xff, n * 4)) != cudaSuccess) return bail(e, "state");
   if ((e = cudaMalloc(&x->d_cam, n * 12 * sizeof(float))) != cudaSuccess) return bail(e, "cam");
   if ((e = cudaMemset(x->d_cam, 0, n * 12 * sizeof(float))) != cudaSuccess) return bail(e, "cam");
@@ -621,6 +645,7 @@ extern "C" void gx_destroy(gx_ctx* x) {
   if (x->gexec) cudaGraphExecDestroy(x->gexec);
   cudaFree(x->d_robot);
   cudaFree(x->d_env_scene);
+  cudaFree(x->d_held_M);
   cudaFree(x->d_state);
   cudaFree(x->d_cam);
   cudaFree(x->d_fb);
@@ -667,7 +692,10 @@ extern "C" gx_status gx_reset(gx_ctx* x, const uint8_t* env_mask, void* stream) 
   rp.bp_cells = x->bp_cells;
   cudaEvent_t* ev = (x->cfg.profile & 1) ? prof_slot(x, 1) : nullptr;
   if (ev) cudaEventRecord(ev[0], s);
-  launch_reset(rp, s);
+  if (x->cfg.object_boxes)
+    launch_reset_boxes(rp, s);
+  else
+    launch_reset(rp, s);
   if (ev) cudaEventRecord(ev[1], s);
   CK(x, cudaGetLastError());
   return post_error_copy(x, s);
@@ -793,9 +821,9 @@ extern "C" gx_status gx_load_state(gx_ctx* x, const void* host, size_t bytes) {
   return GX_OK;
 }
 
-extern "C" gx_status gx_state_layout(const gx_ctx* x, size_t offsets[11]) {
+extern "C" gx_status gx_state_layout(const gx_ctx* x, size_t offsets[GX_STATE_ARRAYS]) {
   if (!x || !offsets) return fail(nullptr, GX_EINVAL, "gx_state_layout: NULL argument");
-  for (int k = 0; k < 11; ++k) offsets[k] = x->off[k];
+  for (int k = 0; k < kStateArrays; ++k) offsets[k] = x->off[k];
   return GX_OK;
 }
 

@@ -82,6 +82,7 @@ static_assert(sizeof(BpCell) == 16, "broad-phase cell");
 // ---------------------------------------------------------------------------
 // State: one device allocation, structure of arrays per field.
 // ---------------------------------------------------------------------------
+constexpr int kStateArrays = GX_STATE_ARRAYS;
 struct StateView {
   float* bx;      // [n]
   float* bz;      // [n]
@@ -95,6 +96,8 @@ struct StateView {
   int* episode;   // [n]
   float* task;    // [n][16]: goal xyz, target start xyz, previous joint actions [7],
                   // previous tip-target and target-goal distances, unused
+  float4* obox;   // [n][M] box objects: half extents xyz, resting yaw (NULL: spheres)
+  float* roff;    // [9][n] box objects: the held box's rotation in the tool frame
 };
 
 struct PhysicsParams {
@@ -124,6 +127,8 @@ struct PhysicsParams {
   float nsdf_margin;
   unsigned long long* nsdf_counters;    // optional [kNsdfCounters]
   int env_offset;                       // global index of environment 0 (Philox counters)
+  float4* held_M;                       // box objects: [n][3] rows of the held box's world
+                                        // rotation times its half extents (rasteriser)
 };
 
 // Neural-SDF decision counters (profiling only).
@@ -173,6 +178,9 @@ struct RasterParams {
   int omesh_nv, omesh_nt;
   const uint32_t* obj_rgb; // [GX_MAX_OBJECTS objects + 32 robot spheres]
   const float4* robot_sph; // optional [n][32] robot sphere centre, radius (0: unused)
+  const float4* obox;      // box objects: [n][M] half extents, yaw (NULL: spheres)
+  const float4* held_M;    // box objects: [n][3] the held box's world rotation x extents
+  const int* held;         // box objects: [n] held object index
   float near_;
   void* depth;
   int depth_fp16;
@@ -204,6 +212,8 @@ void launch_physics(const PhysicsParams& p, cudaStream_t s);
 void launch_bp_rebuild(const DScene* scenes, const int* env_scene, const StateView& st, int n,
                        int M, BpCell* bp, int cells, cudaStream_t s);
 void launch_reset(const ResetParams& p, cudaStream_t s);
+void launch_physics_boxes(const PhysicsParams& p, cudaStream_t s);
+void launch_reset_boxes(const ResetParams& p, cudaStream_t s);
 cudaError_t reset_configure();
 void launch_raster(const RasterParams& p, cudaStream_t s);
 // ---------------------------------------------------------------------------

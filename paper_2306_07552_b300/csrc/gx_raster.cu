@@ -60,6 +60,14 @@ constexpr long kWaitLimit = 1L << 22;  // bounded waits
 constexpr int kListCap = 2048;          // clusters culled per pass
 constexpr int kSpan = 4;                // adjacent pixels of a row per expansion slot
 
+// The box objects' instance mesh: the unit cube's twelve triangles (corner k
+// has the signs of bits 0/1/2 of k on x/y/z), counter-clockwise seen from
+// outside, packed i0 | i1 << 8 | i2 << 16.
+__constant__ uint32_t kCubeTris[12] = {
+    0 | 4 << 8 | 6 << 16, 0 | 6 << 8 | 2 << 16, 1 | 3 << 8 | 7 << 16, 1 | 7 << 8 | 5 << 16,
+    0 | 1 << 8 | 5 << 16, 0 | 5 << 8 | 4 << 16, 2 | 6 << 8 | 7 << 16, 2 | 7 << 8 | 3 << 16,
+    0 | 2 << 8 | 3 << 16, 0 | 3 << 8 | 1 << 16, 4 | 5 << 8 | 7 << 16, 4 | 7 << 8 | 6 << 16};
+
 // Setup of one triangle queued for pixel expansion.
 struct __align__(16) ExpTri {
   int e[3];       // edge values at the bounding box's first pixel centre (bias included)
@@ -712,18 +720,53 @@ __global__ void __launch_bounds__(kThreads, kRasterMinBlocks) raster_kernel(cons
           if (!(o.w > 0.f)) continue;
           const int slot = j < P.M ? j : GX_MAX_OBJECTS + (j - P.M);
           if (!sphere_visible(cm, vw, o.x, o.y, o.z, o.w * 1.0001f + 1e-6f)) continue;
-          for (int k = lane; k < P.omesh_nv; k += 32) {
-            const float4 u = P.omesh_v[k];
-            ws.vbuf[0][k] = make_float4(fmaf(o.w, u.x, o.x), fmaf(o.w, u.y, o.y),
-                                        fmaf(o.w, u.z, o.z), 0.f);
-          }
           const uint32_t rgb = __ldg(P.obj_rgb + slot);
-          for (int k = lane; k < P.omesh_nt; k += 32) {
-            ws.tbuf[0][k] = P.omesh_t[k];
-            ws.cbuf[0][k] = rgb;
+          int nv = P.omesh_nv, nt = P.omesh_nt;
+          if (P.obox) {
+            // an oriented box (its bounding sphere was culled above): the unit
+            // cube, corner k = signs of bits 0/1/2 of k, mapped by its world
+            // rotation times diag(half extents) -- R_y(yaw) resting, the
+            // tool-carried rotation while held
+            float4 r0, r1, r2;
+            if (j == P.held[env]) {
+              r0 = P.held_M[(size_t)env * 3];
+              r1 = P.held_M[(size_t)env * 3 + 1];
+              r2 = P.held_M[(size_t)env * 3 + 2];
+            } else {
+              const float4 b = P.obox[(size_t)env * P.M + j];
+              float sy, cy;
+              sincosf(b.w, &sy, &cy);
+              r0 = make_float4(cy * b.x, 0.f, sy * b.z, 0.f);
+              r1 = make_float4(0.f, b.y, 0.f, 0.f);
+              r2 = make_float4(-sy * b.x, 0.f, cy * b.z, 0.f);
+            }
+            if (lane < 8) {
+              const float ux = (lane & 1) ? 1.f : -1.f, uy = (lane & 2) ? 1.f : -1.f,
+                          uz = (lane & 4) ? 1.f : -1.f;
+              ws.vbuf[0][lane] = make_float4(fmaf(r0.x, ux, fmaf(r0.y, uy, fmaf(r0.z, uz, o.x))),
+                                             fmaf(r1.x, ux, fmaf(r1.y, uy, fmaf(r1.z, uz, o.y))),
+                                             fmaf(r2.x, ux, fmaf(r2.y, uy, fmaf(r2.z, uz, o.z))),
+                                             0.f);
+            }
+            if (lane < 12) {
+              ws.tbuf[0][lane] = kCubeTris[lane];
+              ws.cbuf[0][lane] = rgb;
+            }
+            nv = 8;
+            nt = 12;
+          } else {
+            for (int k = lane; k < P.omesh_nv; k += 32) {
+              const float4 u = P.omesh_v[k];
+              ws.vbuf[0][k] = make_float4(fmaf(o.w, u.x, o.x), fmaf(o.w, u.y, o.y),
+                                          fmaf(o.w, u.z, o.z), 0.f);
+            }
+            for (int k = lane; k < P.omesh_nt; k += 32) {
+              ws.tbuf[0][k] = P.omesh_t[k];
+              ws.cbuf[0][k] = rgb;
+            }
           }
           __syncwarp();
-          raster_cluster<kCount>(vw, cm, ws, 0, P.omesh_nv, P.omesh_nt, P.big_px, lane, cn);
+          raster_cluster<kCount>(vw, cm, ws, 0, nv, nt, P.big_px, lane, cn);
         }
         // object vertices were written to vbuf[0] by ordinary stores: order
         // them before later bulk copies into the same buffer

@@ -24,6 +24,7 @@ GX_DEV_PLACEMENT_FAILED = 0x2
 GX_NOALLOC_WAIT_TIMEOUT = 0x100
 GX_NOALLOC_BAD_SCENE = 0x200
 MAX_OBJECTS = 256
+STATE_ARRAYS = 13
 MAX_SPHERES = 31
 
 SYMBOLS = ["gx_scene_set_create", "gx_scene_set_destroy", "gx_create", "gx_destroy", "gx_reset",
@@ -78,7 +79,8 @@ class GxConfig(C.Structure):
                 ("small_tri_px", C.c_int32), ("use_graph", C.c_int32), ("profile", C.c_int32),
                 ("sdf_mode", C.c_int32), ("sdf_margin", C.c_float), ("broadphase", C.c_int32),
                 ("render_robot", C.c_int32), ("heuristics", C.c_int32),
-                ("raster_order", C.c_int32), ("env_offset", C.c_int32)]
+                ("raster_order", C.c_int32), ("env_offset", C.c_int32),
+                ("object_boxes", C.c_int32)]
 
 
 OUTPUT_KEYS = ["depth", "rgb", "pose", "obj_pos", "held", "contact_mask", "contact_flags", "event",
@@ -333,7 +335,7 @@ class Sim:
                  depth_fp16=False, render_rgb=True, n_objects=40, obj_radius=(0.03, 0.06),
                  seed=1, env_scene=None, small_tri_px=0, use_graph=False,
                  profile=0, sdf_mode=0, sdf_margin=0.02, heuristics=0, render_robot=False,
-                 broadphase=False, raster_order=0, env_offset=0):
+                 broadphase=False, raster_order=0, env_offset=0, object_boxes=False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("gx needs a CUDA device; there is no CPU fallback")
@@ -358,6 +360,8 @@ class Sim:
         cfg.broadphase = int(broadphase)
         cfg.raster_order = int(raster_order)
         cfg.env_offset = int(env_offset)
+        cfg.object_boxes = int(object_boxes)
+        self.object_boxes = bool(object_boxes)
         self.robot_c = robot_struct(robot)
         self.handle = C.c_void_p()
         _check(lib().gx_create(scene_set.handle, C.byref(self.robot_c), C.byref(cfg),
@@ -486,7 +490,7 @@ class Sim:
         _check(lib().gx_load_state(self.handle, buf.ctypes.data, buf.nbytes), self.handle)
 
     def layout(self):
-        offs = (C.c_size_t * 11)()
+        offs = (C.c_size_t * STATE_ARRAYS)()
         _check(lib().gx_state_layout(self.handle, offs), self.handle)
         return list(offs)
 
@@ -505,7 +509,8 @@ class Sim:
                     held=arr(4, np.int32, (n,)), c_off=arr(5, np.float32, (3, n)),
                     p_pre=arr(6, np.float32, (3, n)), obj=arr(7, np.float32, (n, M, 4)),
                     step=arr(8, np.int32, (n,)), episode=arr(9, np.int32, (n,)),
-                    task=arr(10, np.float32, (n, 16)))
+                    task=arr(10, np.float32, (n, 16)), box=arr(11, np.float32, (n, M, 4)),
+                    r_off=arr(12, np.float32, (9, n)))
 
     def close(self):
         if self.handle:

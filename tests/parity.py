@@ -32,12 +32,16 @@ DEPTH_ABS = 5e-6
 ROBOT_SLOT0 = 256
 
 
-def oracle_state(arrs, e, M):
+def oracle_state(arrs, e, M, boxes=False):
+    """The GPU state of environment e widened to FP64 (boxes: the oriented-box
+    object model's extents, yaws and carried rotation too)."""
     return O.Oracle.make_state((float(arrs["base_x"][e]), float(arrs["base_z"][e]),
                                 float(arrs["yaw"][e])), arrs["q"][:, e], int(arrs["held"][e]),
                                arrs["c_off"][:, e], arrs["p_pre"][:, e], arrs["obj"][e, :M],
                                int(arrs["step"][e]), int(arrs["episode"][e]),
-                               task=arrs["task"][e] if "task" in arrs else None)
+                               task=arrs["task"][e] if "task" in arrs else None,
+                               boxes=arrs["box"][e, :M] if boxes else None,
+                               r_off=arrs["r_off"][:, e] if boxes else None)
 
 
 def ang_diff(a, b):
@@ -82,10 +86,10 @@ class Tally:
         return r
 
 
-def check_step(orc, before, after, out, acts, envs, M, tally, step_fn=None):
+def check_step(orc, before, after, out, acts, envs, M, tally, step_fn=None, boxes=False):
     """Physics parity of one step for the listed environments.  step_fn(st,
     action, env) replaces the oracle's plain step (e.g. with its neural-SDF
-    rule or the paper's heuristics)."""
+    rule or the paper's heuristics); boxes: the oriented-box object model."""
     mask = out["contact_mask"].cpu().numpy().view(np.uint32)
     flags = out["contact_flags"].cpu().numpy()
     event = out["event"].cpu().numpy()
@@ -96,7 +100,7 @@ def check_step(orc, before, after, out, acts, envs, M, tally, step_fn=None):
     tobs = out["task_obs"].cpu().numpy() if out.get("task_obs") is not None else None
     succ = out["success"].cpu().numpy() if out.get("success") is not None else None
     for e in envs:
-        st = oracle_state(before, e, M)
+        st = oracle_state(before, e, M, boxes)
         o = step_fn(st, acts[e], e) if step_fn else orc.step(st, acts[e])
         tally.envs += 1
         same = (mask[e] == o.contact_mask and flags[e] == o.flags and event[e] == o.event
@@ -128,6 +132,13 @@ def check_step(orc, before, after, out, acts, envs, M, tally, step_fn=None):
         if st.held >= 0:
             parts["attach_off_m"] = np.abs(after["c_off"][:, e] - np.array(list(st.c_off)))
             parts["pre_grasp_m"] = np.abs(after["p_pre"][:, e] - np.array(list(st.p_pre)))
+            if boxes:
+                parts["carried_rot"] = np.abs(after["r_off"][:, e] - np.array(list(st.r_off)))
+        if boxes:
+            sb = O.Oracle.state_boxes(st)
+            gb = after["box"][e, :M]
+            parts["box_extents_m"] = np.abs(gb[:, :3] - sb[:, :3]).ravel()
+            parts["box_yaw_rad"] = [ang_diff(float(gb[j, 3]), float(sb[j, 3])) for j in range(M)]
         errs = []
         for k, v in parts.items():
             tally.note(k, v)
@@ -152,20 +163,20 @@ def check_step(orc, before, after, out, acts, envs, M, tally, step_fn=None):
             assert m2 <= POSE_TOL, (e, m2)
 
 
-def oracle_image(orc, after, e, W, H, M):
+def oracle_image(orc, after, e, W, H, M, boxes=False):
     """The oracle's image of environment e's state: depth, RGB, ambiguity
     mask, |cos| of the winning hit, robot-body mask, counters."""
-    st = oracle_state(after, e, M)
+    st = oracle_state(after, e, M, boxes)
     cosv = np.ones((H, W))
     depth, rgb, amb, win, stats = orc.render(st, W, H, cos_out=cosv)
     robot = win >= orc.scene.n_tris + ROBOT_SLOT0 * (orc.objmesh.n_tris if orc.objmesh else 0)
     return depth, rgb, amb, cosv, robot, stats
 
 
-def check_image(orc, after, out, e, W, H, M, tally, fp16=False, ref=None):
+def check_image(orc, after, out, e, W, H, M, tally, fp16=False, ref=None, boxes=False):
     """One image against the oracle's (ref: a precomputed oracle_image)."""
     depth, rgb, amb, cosv, robot, stats = ref if ref is not None else oracle_image(
-        orc, after, e, W, H, M)
+        orc, after, e, W, H, M, boxes)
     gd = out["depth"][e].float().cpu().numpy().astype(np.float64)
     ok = ~amb
     tally.pixels += int(ok.sum())
