@@ -227,6 +227,19 @@ def work_counters(ss, w, acts, mask_at, steps, plan):
     return {k: v / (steps * w.n_envs) for k, v in c.items()}
 
 
+def object_mesh(w):
+    """The oracle's instance mesh for the workload's objects."""
+    return I.unit_cube() if w.objects == "boxes" else I.icosahedron()
+
+
+def oracle_blank_state(w):
+    """An empty oracle state in the workload's object model, ready for a reset."""
+    import oracle as O
+    st = O.Oracle.make_state((0, 0, 0), np.zeros(7))
+    st.boxes = 1 if w.objects == "boxes" else 0
+    return st
+
+
 def cpu_model():
     try:
         for line in open("/proc/cpuinfo"):
@@ -254,8 +267,8 @@ def _oracle_worker(args):
             sc = (I.room_scene(w.scene_seed + s, targets[s], grid_h=w.grid_h)
                   if w.scene_kind == "room" else
                   I.apartment_scene(w.scene_seed + s, targets[s], grid_h=w.grid_h))
-            scenes[s] = O.Oracle(robot, sc, I.icosahedron(), I.object_colors(256))
-        st = O.Oracle.make_state((0, 0, 0), np.zeros(7))
+            scenes[s] = O.Oracle(robot, sc, object_mesh(w), I.object_colors(256))
+        st = oracle_blank_state(w)
         scenes[s].reset(st, w.reset_seed, e, w.n_objects, *w.obj_radius)
         states.append((scenes[s], st))
     acts = I.make_actions(200, len(sample_envs), w.action_dist, seed=w.action_seed + 1)
@@ -298,8 +311,8 @@ def cpu_baseline(w, scenes, seconds):
     for e in sample_envs:
         s = int(env_scene[e])
         if s not in orcs:
-            orcs[s] = O.Oracle(robot, scenes[s], I.icosahedron(), I.object_colors(256))
-        st = O.Oracle.make_state((0, 0, 0), np.zeros(7))
+            orcs[s] = O.Oracle(robot, scenes[s], object_mesh(w), I.object_colors(256))
+        st = oracle_blank_state(w)
         orcs[s].reset(st, w.reset_seed, e, w.n_objects, *w.obj_radius)
         states.append((orcs[s], st))
     acts = I.make_actions(200, len(sample_envs), w.action_dist, seed=w.action_seed + 1)
@@ -374,6 +387,7 @@ def config_of(w):
             "resets": (f"{w.reset_every}-step episodes, staggered" if w.reset_every
                        else f"Bernoulli p={w.reset_prob} per env-step"),
             "l2": "no flush: each step writes more observation bytes than L2 holds",
+            "objects": w.objects,
             "static_test": {"neural": f"neural SDF, grid below {w.sdf_margin} m predicted "
                                       f"clearance",
                             "column": "column grid (radii 1.5/5/12 cm, 3 cm columns)"}.get(
@@ -394,8 +408,8 @@ def run_reference(args, w, rank, world):
     for e in sample:
         s = int(env_scene[e])
         if s not in orcs:
-            orcs[s] = O.Oracle(robot, scenes[s], I.icosahedron(), I.object_colors(256))
-        st = O.Oracle.make_state((0, 0, 0), np.zeros(7))
+            orcs[s] = O.Oracle(robot, scenes[s], object_mesh(w), I.object_colors(256))
+        st = oracle_blank_state(w)
         orcs[s].reset(st, w.reset_seed, e, w.n_objects, *w.obj_radius)
         sts.append((orcs[s], st))
     acts = I.make_actions(args.warmup + args.steps, len(sample), w.action_dist,
@@ -490,7 +504,8 @@ def main():
                   n_objects=w.n_objects, obj_radius=w.obj_radius, seed=w.reset_seed,
                   small_tri_px=args.small_px, heuristics=args.heuristics,
                   render_robot=args.render_robot, broadphase=args.broadphase,
-                  env_scene=plan.env_scene, env_offset=plan.first)
+                  env_scene=plan.env_scene, env_offset=plan.first,
+                  object_boxes=w.objects == "boxes")
     column = w.sdf == "column"
     sdf_mode = 1 if neural else (2 if column else 0)
     # per-kernel CUDA events on the launching stream (the roofline's kernel

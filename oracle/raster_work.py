@@ -30,8 +30,10 @@ def measure(name, n_envs=32, n_steps=8):
     for i, e in enumerate(envs):
         s = int(env_scene[e])
         if s not in orcs:
-            orcs[s] = O.Oracle(robot, scenes[s], I.icosahedron(), I.object_colors(64))
+            mesh = I.unit_cube() if w.objects == "boxes" else I.icosahedron()
+            orcs[s] = O.Oracle(robot, scenes[s], mesh, I.object_colors(64))
         st = O.Oracle.make_state((0, 0, 0), np.zeros(7))
+        st.boxes = 1 if w.objects == "boxes" else 0
         orcs[s].reset(st, w.reset_seed, e, w.n_objects, *w.obj_radius)
         for t in range(n_steps):
             orcs[s].step(st, acts[t, i])

@@ -545,6 +545,8 @@ class Workload:
     nsdf_samples: int = 10_000_000
     nsdf_steps: int = 2000   # Adam steps per scene, batch 65,536
     nsdf_seed: int = 7
+    objects: str = "spheres"  # "spheres" | "boxes" (upright oriented boxes, carried as
+                              # eight spheres; half extents in obj_radius per axis)
 
 
 WORKLOADS = {
@@ -562,6 +564,10 @@ WORKLOADS = {
     "apartments4096_obj200": Workload("apartments4096_obj200", 4096, 16, "apartment",
                                       (20000, 60000), "uniform", 0.02, 200, (0.03, 0.06), 128,
                                       False, True, 500, "gauss0.5", 200, 0.0, 1000),
+    "apartments4096_boxes": Workload("apartments4096_boxes", 4096, 16, "apartment",
+                                     (20000, 60000), "uniform", 0.02, 40, (0.03, 0.06), 128,
+                                     False, True, 500, "gauss0.5", 200, 0.0, 1000,
+                                     objects="boxes"),
     "apartments4096_column": Workload("apartments4096_column", 4096, 16, "apartment",
                                       (20000, 60000), "uniform", 0.02, 40, (0.03, 0.06), 128,
                                       False, True, 500, "gauss0.5", 200, 0.0, 1000, sdf="column"),

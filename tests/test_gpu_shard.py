@@ -57,7 +57,7 @@ def test_two_shards_equal_the_whole_batch():
         sp = s.state_arrays()
         for k, v in sp.items():
             ref = sf[k]
-            sl = (ref[:, p.first:p.first + p.count] if k in ("q", "c_off", "p_pre")
+            sl = (ref[:, p.first:p.first + p.count] if k in ("q", "c_off", "p_pre", "r_off")
                   else ref[p.first:p.first + p.count])
             assert np.array_equal(v, sl), k
     # the reset draws really depend on the global index: the second shard
