@@ -387,7 +387,7 @@ def config_of(w):
             "resets": (f"{w.reset_every}-step episodes, staggered" if w.reset_every
                        else f"Bernoulli p={w.reset_prob} per env-step"),
             "l2": "no flush: each step writes more observation bytes than L2 holds",
-            "objects": w.objects,
+            "object_model": w.objects,
             "static_test": {"neural": f"neural SDF, grid below {w.sdf_margin} m predicted "
                                       f"clearance",
                             "column": "column grid (radii 1.5/5/12 cm, 3 cm columns)"}.get(
@@ -469,6 +469,9 @@ def main():
                     help="the paper's heuristics: bit 0 sliding, bit 1 object placing")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default rasteriser setting instead of timing candidates")
+    ap.add_argument("--fused", action="store_true",
+                    help="one cooperative persistent launch per step (resets, physics, "
+                         "rendering)")
     ap.add_argument("--no-graph", action="store_true",
                     help="headline from the event-timed loop instead of a graph-replayed one")
     args = ap.parse_args()
@@ -505,7 +508,7 @@ def main():
                   small_tri_px=args.small_px, heuristics=args.heuristics,
                   render_robot=args.render_robot, broadphase=args.broadphase,
                   env_scene=plan.env_scene, env_offset=plan.first,
-                  object_boxes=w.objects == "boxes")
+                  object_boxes=w.objects == "boxes", fused_step=args.fused)
     column = w.sdf == "column"
     sdf_mode = 1 if neural else (2 if column else 0)
     # per-kernel CUDA events on the launching stream (the roofline's kernel
@@ -536,11 +539,12 @@ def main():
     launches = 0
 
     def one(ctx, t):
-        # copy into fixed buffers so a graph replay sees the same pointers
+        # copy into fixed buffers so a graph replay sees the same pointers;
+        # the step's resets and the step in one call (one graph, or with
+        # --fused one kernel launch)
         abuf.copy_(acts[t])
         mbuf.copy_(mask_at(t))
-        ctx.reset(mbuf, stream=stream)
-        ctx.step(abuf, stream=stream)
+        ctx.step_reset(mbuf, abuf, stream=stream)
 
     def warm(ctx):
         with torch.cuda.stream(stream):
@@ -595,7 +599,7 @@ def main():
         ms, clk = ms_events, clk_events
         dev_err = sim.device_error()
         out_ctx = sim
-    launches = args.steps * (5 if neural else 3)
+    launches = args.steps * (1 if args.fused else (5 if neural else 3))
     value, ms = job_value(dist, n, args.steps, ms)
     value_events, _ = job_value(dist, n, args.steps, ms_events)
     # the last step's per-env results, summed over every rank's shard on the
@@ -793,7 +797,10 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (procedural apartments standing in for ReplicaCAD scenes, spheres for "
                 "YCB objects, random actions for policy actions)",
-        "config": {**config_of(w), "heuristics": {"sliding": bool(args.heuristics & 1),
+        "config": {**config_of(w),
+                   "step_launch": ("fused: one cooperative launch per step" if args.fused else
+                                   "separate kernels: reset, physics, raster"),
+                   "heuristics": {"sliding": bool(args.heuristics & 1),
                                                   "object_placing": bool(args.heuristics & 2)},
                    "robot_body_rendered": bool(args.render_robot),
                    "object_broadphase": bool(args.broadphase)},

@@ -201,6 +201,15 @@ typedef struct {
                               by rotation x half extents.  Only with sdf_mode 0
                               and without heuristics, broad-phase or robot-body
                               rendering (GX_EINVAL otherwise)                 */
+  int32_t fused_step;      /* 1: each step (gx_step, gx_step_reset) is one
+                              cooperative persistent launch of the
+                              rasteriser's grid: masked resets, then physics
+                              (a warp per environment), then rendering,
+                              separated by grid-wide barriers with bounded
+                              waits (a wait that gives up sets the device error
+                              word).  Not with sdf_mode 1 or object_boxes
+                              (GX_EINVAL); gx_phase_times then reports the
+                              whole launch as ms[1].                          */
 } gx_config;
 
 /* Outputs of one step, device memory owned by the caller (e.g. torch
@@ -261,6 +270,15 @@ gx_status gx_reset(gx_ctx* ctx, const uint8_t* env_mask, void* stream);
  * offsets, grasp (>= 0.5 grasps, else releases), stop (ignored); each value
  * is clipped to [-1, 1] (App. A).  Asynchronous on `stream`. */
 gx_status gx_step(gx_ctx* ctx, const float* actions, const gx_outputs* out, void* stream);
+
+/* gx_reset(env_mask) followed by gx_step(actions) in one call: the
+ * environments whose byte in env_mask (device, [n_envs]; NULL: none) is
+ * non-zero start a new episode, then every environment advances one step.
+ * With fused_step this is a single kernel launch; otherwise the launches of
+ * the two calls.  With use_graph the whole call is replayed as one captured
+ * graph (keyed on the mask, action and output pointers). */
+gx_status gx_step_reset(gx_ctx* ctx, const uint8_t* env_mask, const float* actions,
+                        const gx_outputs* out, void* stream);
 
 /* Same step with HOST actions: copies the actions (pinned host memory is
  * fastest) to the device, steps into the context's own device output

@@ -44,6 +44,13 @@ struct gx_ctx {
   float* d_cam = nullptr;
   float4* d_robot_sph = nullptr;       // robot spheres for rendering the robot body
   float4* d_held_M = nullptr;          // box objects: the held box's world rotation x extents
+  // fused step (one cooperative launch per step)
+  int fused_ctas = 0;
+  float4* d_fused_scratch = nullptr;   // reset try tables, per CTA
+  float4* d_fused_obj = nullptr;       // physics object copies above 128 objects, per CTA
+  unsigned* d_barrier = nullptr;       // grid barrier: arrivals, generation
+  cudaError_t launch_err = cudaSuccess;
+  const uint8_t* g_mask = nullptr;     // reset mask captured in the graph (gx_step_reset)
   BpCell* d_bp = nullptr;              // object broad-phase cells
   int bp_cells = 0;
   unsigned* d_err = nullptr;
@@ -159,7 +166,7 @@ bool same_outputs(const gx_outputs& a, const gx_outputs& b) {
 // rasteriser), 2 for a reset.  nullptr once the pool is full;
 // gx_phase_times drains it.
 cudaEvent_t* prof_slot(gx_ctx* c, int kind) {
-  const size_t kMax = 5 * 8192, k = kind == 1 ? 2 : 5;
+  const size_t kMax = 5 * 8192, k = (kind == 1 || kind == 3) ? 2 : 5;
   if (c->prof_used + k > kMax) return nullptr;
   while (c->prof_ev.size() < c->prof_used + k) {
     cudaEvent_t e;
@@ -173,10 +180,7 @@ cudaEvent_t* prof_slot(gx_ctx* c, int kind) {
   return r;
 }
 
-void enqueue_step(gx_ctx* c, const float* actions, const gx_outputs& out, cudaStream_t s) {
-  const bool neural = c->cfg.sdf_mode == 1;
-  cudaEvent_t* ev = (c->cfg.profile & 1) ? prof_slot(c, neural ? 2 : 0) : nullptr;
-  if (ev) cudaEventRecord(ev[0], s);
+PhysicsParams physics_params(gx_ctx* c, const float* actions, const gx_outputs& out) {
   PhysicsParams pp{};
   pp.n = c->n;
   pp.M = c->M;
@@ -197,33 +201,10 @@ void enqueue_step(gx_ctx* c, const float* actions, const gx_outputs& out, cudaSt
   pp.seed = c->cfg.seed;
   pp.env_offset = c->cfg.env_offset;
   pp.column = c->cfg.sdf_mode == 2;
-  if (c->cfg.sdf_mode == 1) {
-    pp.nsdf_pts = c->d_nsdf_pts;
-    pp.nsdf_d = c->d_nsdf_d;
-    pp.nsdf_margin = c->cfg.sdf_margin;
-    pp.nsdf_counters = (c->cfg.profile & 4) ? c->d_nsdf_counters : nullptr;
-    pp.nsdf_pass = 1;
-    launch_physics(pp, s);
-    if (ev) cudaEventRecord(ev[1], s);
-    NsdfStepParams np{};
-    np.blobs = c->d_nsdf_blobs;
-    np.tiles = c->d_nsdf_tiles;
-    np.n_tiles = c->n_nsdf_tiles;
-    np.perm = c->d_nsdf_perm;
-    np.pts = c->d_nsdf_pts;
-    np.out = c->d_nsdf_d;
-    np.err = c->d_err;
-    nsdf_launch_step(np, s);
-    if (ev) cudaEventRecord(ev[2], s);
-    pp.nsdf_pass = 2;
-  }
-  if (c->cfg.object_boxes) {
-    pp.held_M = c->d_held_M;
-    launch_physics_boxes(pp, s);
-  } else {
-    launch_physics(pp, s);
-  }
-  if (ev) cudaEventRecord(ev[3], s);
+  return pp;
+}
+
+RasterParams raster_params(gx_ctx* c, const gx_outputs& out) {
   RasterParams rp{};
   rp.n = c->n;
   rp.M = c->M;
@@ -257,8 +238,84 @@ void enqueue_step(gx_ctx* c, const float* actions, const gx_outputs& out, cudaSt
   rp.rgb = c->cfg.render_rgb ? out.rgb : nullptr;
   rp.err = c->d_err;
   rp.counters = (c->cfg.profile & 2) ? c->d_counters : nullptr;
-  launch_raster(rp, s);
+  return rp;
+}
+
+ResetParams reset_params(gx_ctx* x, const uint8_t* env_mask) {
+  ResetParams rp{};
+  rp.n = x->n;
+  rp.M = x->M;
+  rp.scenes = x->set->d_scenes;
+  rp.env_scene = x->d_env_scene;
+  rp.robot = x->d_robot;
+  rp.mask = env_mask;
+  rp.st = x->st;
+  rp.cam = x->d_cam;
+  rp.seed = x->cfg.seed;
+  rp.env_offset = x->cfg.env_offset;
+  rp.rho_min = x->cfg.obj_radius_min;
+  rp.rho_max = x->cfg.obj_radius_max;
+  rp.err = x->d_err;
+  rp.bp = x->d_bp;
+  rp.bp_cells = x->bp_cells;
+  return rp;
+}
+
+void enqueue_step(gx_ctx* c, const float* actions, const gx_outputs& out, cudaStream_t s) {
+  const bool neural = c->cfg.sdf_mode == 1;
+  cudaEvent_t* ev = (c->cfg.profile & 1) ? prof_slot(c, neural ? 2 : 0) : nullptr;
+  if (ev) cudaEventRecord(ev[0], s);
+  PhysicsParams pp = physics_params(c, actions, out);
+  if (c->cfg.sdf_mode == 1) {
+    pp.nsdf_pts = c->d_nsdf_pts;
+    pp.nsdf_d = c->d_nsdf_d;
+    pp.nsdf_margin = c->cfg.sdf_margin;
+    pp.nsdf_counters = (c->cfg.profile & 4) ? c->d_nsdf_counters : nullptr;
+    pp.nsdf_pass = 1;
+    launch_physics(pp, s);
+    if (ev) cudaEventRecord(ev[1], s);
+    NsdfStepParams np{};
+    np.blobs = c->d_nsdf_blobs;
+    np.tiles = c->d_nsdf_tiles;
+    np.n_tiles = c->n_nsdf_tiles;
+    np.perm = c->d_nsdf_perm;
+    np.pts = c->d_nsdf_pts;
+    np.out = c->d_nsdf_d;
+    np.err = c->d_err;
+    nsdf_launch_step(np, s);
+    if (ev) cudaEventRecord(ev[2], s);
+    pp.nsdf_pass = 2;
+  }
+  if (c->cfg.object_boxes) {
+    pp.held_M = c->d_held_M;
+    launch_physics_boxes(pp, s);
+  } else {
+    launch_physics(pp, s);
+  }
+  if (ev) cudaEventRecord(ev[3], s);
+  launch_raster(raster_params(c, out), s);
   if (ev) cudaEventRecord(ev[4], s);
+}
+
+// The fused step: masked resets (mask may be NULL), physics and rendering in
+// one cooperative launch; the barrier's arrival count is cleared first.
+void enqueue_fused(gx_ctx* c, const uint8_t* mask, const float* actions, const gx_outputs& out,
+                   cudaStream_t s) {
+  cudaEvent_t* ev = (c->cfg.profile & 1) ? prof_slot(c, 3) : nullptr;
+  FusedParams f{};
+  f.pp = physics_params(c, actions, out);
+  f.pp.raster_work = nullptr;
+  f.rs = reset_params(c, mask);
+  f.rp = raster_params(c, out);
+  f.reset_mask = mask;
+  f.reset_scratch = c->d_fused_scratch;
+  f.obj_scratch = c->d_fused_obj;
+  f.barrier = c->d_barrier;
+  cudaMemsetAsync(c->d_barrier, 0, sizeof(unsigned), s);
+  if (ev) cudaEventRecord(ev[0], s);
+  cudaError_t e = launch_fused_step(f, std::min(c->fused_ctas, c->raster_ctas), s);
+  if (e != cudaSuccess) c->launch_err = e;
+  if (ev) cudaEventRecord(ev[1], s);
 }
 
 }  // namespace
@@ -466,6 +523,12 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
     return fail(nullptr, GX_EINVAL, "raster_order must be 0, 1 or 2");
   if (c.env_offset < 0 || (int64_t)c.env_offset + c.n_envs > INT32_MAX)
     return fail(nullptr, GX_EINVAL, "env_offset must be >= 0 with env_offset + n_envs < 2^31");
+  if (c.fused_step < 0 || c.fused_step > 1)
+    return fail(nullptr, GX_EINVAL, "fused_step must be 0 or 1");
+  if (c.fused_step && (c.sdf_mode == 1 || c.object_boxes))
+    return fail(nullptr, GX_EINVAL,
+                "fused_step: not with the neural SDF (its tensor-core query runs between the "
+                "physics passes) or the box objects");
   if (c.object_boxes < 0 || c.object_boxes > 1)
     return fail(nullptr, GX_EINVAL, "object_boxes must be 0 or 1");
   if (c.object_boxes && (c.heuristics || c.broadphase || c.render_robot || c.sdf_mode != 0))
@@ -549,6 +612,17 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
       ((e = cudaMalloc(&x->d_held_M, n * 3 * sizeof(float4))) != cudaSuccess ||
        (e = cudaMemset(x->d_held_M, 0, n * 3 * sizeof(float4))) != cudaSuccess))
     return bail(e, "held box rotation");
+  if (c.fused_step) {
+    if ((e = fused_max_ctas(&x->fused_ctas)) != cudaSuccess) return bail(e, "fused config");
+    const size_t ctas = (size_t)std::max(x->fused_ctas, x->n_slots);
+    if ((e = cudaMalloc(&x->d_fused_scratch, ctas * kFusedResetScratch * sizeof(float4))) !=
+            cudaSuccess ||
+        (e = cudaMalloc(&x->d_fused_obj, ctas * 8 * GX_MAX_OBJECTS * sizeof(float4))) !=
+            cudaSuccess ||
+        (e = cudaMalloc(&x->d_barrier, 2 * sizeof(unsigned))) != cudaSuccess ||
+        (e = cudaMemset(x->d_barrier, 0, 2 * sizeof(unsigned))) != cudaSuccess)
+      return bail(e, "fused step scratch");
+  }
   if ((e = cudaMemset(x->st.held, 0xff, n * 4)) != cudaSuccess) return bail(e, "state");
   if ((e = cudaMalloc(&x->d_cam, n * 12 * sizeof(float))) != cudaSuccess) return bail(e, "cam");
   if ((e = cudaMemset(x->d_cam, 0, n * 12 * sizeof(float))) != cudaSuccess) return bail(e, "cam");
@@ -646,6 +720,9 @@ extern "C" void gx_destroy(gx_ctx* x) {
   cudaFree(x->d_robot);
   cudaFree(x->d_env_scene);
   cudaFree(x->d_held_M);
+  cudaFree(x->d_fused_scratch);
+  cudaFree(x->d_fused_obj);
+  cudaFree(x->d_barrier);
   cudaFree(x->d_state);
   cudaFree(x->d_cam);
   cudaFree(x->d_fb);
@@ -674,22 +751,7 @@ extern "C" gx_status gx_reset(gx_ctx* x, const uint8_t* env_mask, void* stream) 
   gx_status st = poll_device_error(x, false);
   if (st != GX_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  ResetParams rp{};
-  rp.n = x->n;
-  rp.M = x->M;
-  rp.scenes = x->set->d_scenes;
-  rp.env_scene = x->d_env_scene;
-  rp.robot = x->d_robot;
-  rp.mask = env_mask;
-  rp.st = x->st;
-  rp.cam = x->d_cam;
-  rp.seed = x->cfg.seed;
-  rp.env_offset = x->cfg.env_offset;
-  rp.rho_min = x->cfg.obj_radius_min;
-  rp.rho_max = x->cfg.obj_radius_max;
-  rp.err = x->d_err;
-  rp.bp = x->d_bp;
-  rp.bp_cells = x->bp_cells;
+  ResetParams rp = reset_params(x, env_mask);
   cudaEvent_t* ev = (x->cfg.profile & 1) ? prof_slot(x, 1) : nullptr;
   if (ev) cudaEventRecord(ev[0], s);
   if (x->cfg.object_boxes)
@@ -701,36 +763,71 @@ extern "C" gx_status gx_reset(gx_ctx* x, const uint8_t* env_mask, void* stream) 
   return post_error_copy(x, s);
 }
 
-extern "C" gx_status gx_step(gx_ctx* x, const float* actions, const gx_outputs* out,
-                             void* stream) {
-  if (!x) return fail(nullptr, GX_EINVAL, "gx_step: ctx is NULL");
-  if (!actions || !out || !out->depth) return fail(x, GX_EINVAL, "gx_step: actions and depth required");
-  if (x->cfg.render_rgb && !out->rgb) return fail(x, GX_EINVAL, "gx_step: render_rgb needs rgb");
+// Enqueues one step, with the masked resets first when mask is set: the
+// regular launches, or the fused cooperative launch; replayed as a captured
+// CUDA graph when the context asks for it.
+gx_status run_step(gx_ctx* x, const uint8_t* mask, const float* actions, const gx_outputs* out,
+                   void* stream, const char* who) {
+  if (!x) return fail(nullptr, GX_EINVAL, "%s: ctx is NULL", who);
+  if (!actions || !out || !out->depth)
+    return fail(x, GX_EINVAL, "%s: actions and depth required", who);
+  if (x->cfg.render_rgb && !out->rgb) return fail(x, GX_EINVAL, "%s: render_rgb needs rgb", who);
   gx_status st = poll_device_error(x, false);
   if (st != GX_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
+  auto enqueue = [&]() {
+    if (x->cfg.fused_step) {
+      enqueue_fused(x, mask, actions, *out, s);
+    } else {
+      if (mask) {
+        ResetParams rp = reset_params(x, mask);
+        cudaEvent_t* ev = (x->cfg.profile & 1) ? prof_slot(x, 1) : nullptr;
+        if (ev) cudaEventRecord(ev[0], s);
+        if (x->cfg.object_boxes)
+          launch_reset_boxes(rp, s);
+        else
+          launch_reset(rp, s);
+        if (ev) cudaEventRecord(ev[1], s);
+      }
+      enqueue_step(x, actions, *out, s);
+    }
+  };
+  x->launch_err = cudaSuccess;
   if (x->cfg.use_graph && !x->cfg.profile && s != nullptr) {
-    if (!x->gexec || x->g_actions != actions || !same_outputs(x->g_out, *out)) {
+    if (!x->gexec || x->g_actions != actions || x->g_mask != mask || !same_outputs(x->g_out, *out)) {
       if (x->gexec) {
         cudaGraphExecDestroy(x->gexec);
         x->gexec = nullptr;
       }
       cudaGraph_t g;
       CK(x, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-      enqueue_step(x, actions, *out, s);
+      enqueue();
       CK(x, cudaStreamEndCapture(s, &g));
       cudaError_t e = cudaGraphInstantiate(&x->gexec, g, 0);
       cudaGraphDestroy(g);
       CK(x, e);
+      CK(x, x->launch_err);
       x->g_actions = actions;
+      x->g_mask = mask;
       x->g_out = *out;
     }
     CK(x, cudaGraphLaunch(x->gexec, s));
   } else {
-    enqueue_step(x, actions, *out, s);
+    enqueue();
+    CK(x, x->launch_err);
     CK(x, cudaGetLastError());
   }
   return post_error_copy(x, s);
+}
+
+extern "C" gx_status gx_step(gx_ctx* x, const float* actions, const gx_outputs* out,
+                             void* stream) {
+  return run_step(x, nullptr, actions, out, stream, "gx_step");
+}
+
+extern "C" gx_status gx_step_reset(gx_ctx* x, const uint8_t* env_mask, const float* actions,
+                                   const gx_outputs* out, void* stream) {
+  return run_step(x, env_mask, actions, out, stream, "gx_step_reset");
 }
 
 extern "C" gx_status gx_step_host(gx_ctx* x, const float* actions_host, const gx_outputs* host_out,
@@ -840,6 +937,12 @@ extern "C" gx_status gx_phase_times(gx_ctx* x, double ms[4], int64_t launches[4]
       x->prof_n[2]++;
       continue;
     }
+    if (x->prof_kind[g] == 3) {   // the fused step: the whole launch
+      CK(x, el(e[0], e[1], &a));
+      x->prof_ms[1] += a;
+      x->prof_n[1]++;
+      continue;
+    }
     if (x->prof_kind[g] == 2) {     // physics = both passes, queries separately
       CK(x, el(e[0], e[1], &a));
       CK(x, el(e[1], e[2], &q));
@@ -914,9 +1017,13 @@ extern "C" gx_status gx_autotune(gx_ctx* x, const float* actions, const gx_outpu
         x->big_px = px[ci] > 0 ? px[ci] : (1 << 30);
         x->order_mode = order;
         x->raster_ctas = std::min(ctas, x->n_slots);
-        enqueue_step(x, actions, *out, s);  // warm-up
+        if (x->cfg.fused_step) enqueue_fused(x, nullptr, actions, *out, s);  // warm-up
+        else enqueue_step(x, actions, *out, s);
         cudaEventRecord(e0, s);
-        for (int t = 0; t < steps; ++t) enqueue_step(x, actions, *out, s);
+        for (int t = 0; t < steps; ++t) {
+          if (x->cfg.fused_step) enqueue_fused(x, nullptr, actions, *out, s);
+          else enqueue_step(x, actions, *out, s);
+        }
         cudaEventRecord(e1, s);
         err = cudaMemcpyAsync(x->d_state, saved, x->state_bytes, cudaMemcpyDeviceToDevice, s);
         if (err == cudaSuccess && x->d_bp) {

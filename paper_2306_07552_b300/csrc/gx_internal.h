@@ -213,6 +213,22 @@ void launch_bp_rebuild(const DScene* scenes, const int* env_scene, const StateVi
                        int M, BpCell* bp, int cells, cudaStream_t s);
 void launch_reset(const ResetParams& p, cudaStream_t s);
 void launch_physics_boxes(const PhysicsParams& p, cudaStream_t s);
+
+// One persistent cooperative launch per step: masked resets, physics and
+// rendering separated by grid-wide barriers (gx_fused.cu).
+constexpr int kFusedResetScratch = 2376;  // float4 per CTA: the reset's try table and objects
+struct FusedParams {
+  PhysicsParams pp;
+  ResetParams rs;
+  RasterParams rp;
+  const uint8_t* reset_mask;  // NULL: no reset phase
+  float4* reset_scratch;      // [ctas][kFusedResetScratch]
+  float4* obj_scratch;        // [ctas][8 warps][GX_MAX_OBJECTS] objects of physics (> 128 objects)
+  unsigned* barrier;          // [2] arrivals (zeroed before each launch), generation
+};
+cudaError_t fused_configure();
+cudaError_t fused_max_ctas(int* ctas);
+cudaError_t launch_fused_step(const FusedParams& f, int ctas, cudaStream_t s);
 void launch_reset_boxes(const ResetParams& p, cudaStream_t s);
 cudaError_t reset_configure();
 void launch_raster(const RasterParams& p, cudaStream_t s);

@@ -28,7 +28,7 @@ STATE_ARRAYS = 13
 MAX_SPHERES = 31
 
 SYMBOLS = ["gx_scene_set_create", "gx_scene_set_destroy", "gx_create", "gx_destroy", "gx_reset",
-           "gx_step", "gx_step_host", "gx_sync", "gx_device_error", "gx_state_bytes",
+           "gx_step", "gx_step_reset", "gx_step_host", "gx_sync", "gx_device_error", "gx_state_bytes",
            "gx_save_state", "gx_load_state", "gx_state_layout", "gx_phase_times",
            "gx_raster_counters", "gx_render_noalloc", "gx_render_noalloc_error",
            "gx_nsdf_set_weights",
@@ -80,7 +80,7 @@ class GxConfig(C.Structure):
                 ("sdf_mode", C.c_int32), ("sdf_margin", C.c_float), ("broadphase", C.c_int32),
                 ("render_robot", C.c_int32), ("heuristics", C.c_int32),
                 ("raster_order", C.c_int32), ("env_offset", C.c_int32),
-                ("object_boxes", C.c_int32)]
+                ("object_boxes", C.c_int32), ("fused_step", C.c_int32)]
 
 
 OUTPUT_KEYS = ["depth", "rgb", "pose", "obj_pos", "held", "contact_mask", "contact_flags", "event",
@@ -128,6 +128,7 @@ def lib():
         L.gx_destroy.restype = None
         L.gx_reset.argtypes = [vp, vp, vp]
         L.gx_step.argtypes = [vp, vp, P(GxOutputs), vp]
+        L.gx_step_reset.argtypes = [vp, vp, vp, P(GxOutputs), vp]
         L.gx_step_host.argtypes = [vp, vp, P(GxOutputs), vp]
         L.gx_sync.argtypes = [vp]
         L.gx_device_error.argtypes = [vp]
@@ -335,7 +336,8 @@ class Sim:
                  depth_fp16=False, render_rgb=True, n_objects=40, obj_radius=(0.03, 0.06),
                  seed=1, env_scene=None, small_tri_px=0, use_graph=False,
                  profile=0, sdf_mode=0, sdf_margin=0.02, heuristics=0, render_robot=False,
-                 broadphase=False, raster_order=0, env_offset=0, object_boxes=False):
+                 broadphase=False, raster_order=0, env_offset=0, object_boxes=False,
+                 fused_step=False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("gx needs a CUDA device; there is no CPU fallback")
@@ -361,6 +363,7 @@ class Sim:
         cfg.raster_order = int(raster_order)
         cfg.env_offset = int(env_offset)
         cfg.object_boxes = int(object_boxes)
+        cfg.fused_step = int(fused_step)
         self.object_boxes = bool(object_boxes)
         self.robot_c = robot_struct(robot)
         self.handle = C.c_void_p()
@@ -407,6 +410,16 @@ class Sim:
         assert tuple(actions.shape) == (self.n, 11)
         _check(lib().gx_step(self.handle, C.c_void_p(actions.data_ptr()), C.byref(self._outs),
                              self._stream(stream)), self.handle)
+        return self.out
+
+    def step_reset(self, mask, actions, stream=None):
+        """Resets the environments whose mask byte is set (CUDA uint8 [n], or
+        None), then steps every environment: one launch with fused_step."""
+        assert actions.is_cuda and actions.dtype == self.torch.float32 and actions.is_contiguous()
+        assert tuple(actions.shape) == (self.n, 11)
+        mp = None if mask is None else C.c_void_p(mask.data_ptr())
+        _check(lib().gx_step_reset(self.handle, mp, C.c_void_p(actions.data_ptr()),
+                                   C.byref(self._outs), self._stream(stream)), self.handle)
         return self.out
 
     def host_outputs(self, pinned=True):
