@@ -201,6 +201,8 @@ typedef struct {
                               by rotation x half extents.  Only with sdf_mode 0
                               and without heuristics, broad-phase or robot-body
                               rendering (GX_EINVAL otherwise)                 */
+  int32_t raster_warps;    /* warps per rasteriser CTA: 0 or 8 (three CTAs per
+                              SM), 12 (two per SM); gx_autotune may change it */
   int32_t fused_step;      /* 1: each step (gx_step, gx_step_reset) is one
                               cooperative persistent launch of the
                               rasteriser's grid: masked resets, then physics
@@ -338,12 +340,15 @@ typedef struct {
                                      triangle clusters are rendered first       */
   int32_t raster_ctas;            /* persistent CTAs launched                    */
   float ms_per_step;              /* measured step time with these settings      */
+  int32_t raster_warps;           /* warps per rasteriser CTA (8 or 12)          */
 } gx_tune_result;
 
 /* Times the step on this context's own state under each candidate rasteriser
  * setting -- expansion limit small_tri_px in {0, 256, 96, 48}, work order
- * {index, costliest scene first}, resident CTAs per SM {occupancy,
- * occupancy - 1} -- for `steps` steps each (plus one warm-up), restoring the
+ * {index, costliest scene first}, CTA shape {8 warps at the occupancy (three
+ * CTAs per SM), 8 warps one CTA per SM fewer, 12 warps at its occupancy (two
+ * per SM); the fused step keeps 8 warps} -- for `steps` steps each (plus one
+ * warm-up), restoring the
  * state after every candidate, and keeps the fastest (written to *best when
  * not NULL).  The outputs are overwritten; the state is left as before the
  * call.  actions: device [n][11], reused for every step.  Allocates one copy

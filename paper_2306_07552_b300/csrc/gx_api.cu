@@ -28,6 +28,7 @@ struct gx_ctx {
   gx_config cfg{};
   int n = 0, M = 0, big_px = 0, n_slots = 0;
   int raster_ctas = 0;                 // CTAs launched (<= n_slots), set by the autotuner
+  int raster_warps = 8;                // warps per rasteriser CTA (8 or 12)
   int order_mode = 0;                  // 0: index order, 1: costliest scene first
   int* d_order = nullptr;              // environments, costliest scene first
   int sms = 0;
@@ -210,6 +211,7 @@ RasterParams raster_params(gx_ctx* c, const gx_outputs& out) {
   rp.M = c->M;
   rp.W = c->cfg.img_w;
   rp.H = c->cfg.img_h;
+  rp.warps = c->cfg.fused_step ? 8 : c->raster_warps;
   rp.big_px = c->big_px;
   rp.fb_slots = c->d_fb;
   rp.fb_epoch = c->d_fb_epoch;
@@ -523,6 +525,8 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
     return fail(nullptr, GX_EINVAL, "raster_order must be 0, 1 or 2");
   if (c.env_offset < 0 || (int64_t)c.env_offset + c.n_envs > INT32_MAX)
     return fail(nullptr, GX_EINVAL, "env_offset must be >= 0 with env_offset + n_envs < 2^31");
+  if (c.raster_warps != 0 && c.raster_warps != 8 && c.raster_warps != 12)
+    return fail(nullptr, GX_EINVAL, "raster_warps must be 0, 8 or 12");
   if (c.fused_step < 0 || c.fused_step > 1)
     return fail(nullptr, GX_EINVAL, "fused_step must be 0 or 1");
   if (c.fused_step && (c.sdf_mode == 1 || c.object_boxes))
@@ -553,6 +557,15 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
   if ((e = reset_configure()) != cudaSuccess) return bail(e, "reset config");
   if (x->n_slots > x->n) x->n_slots = x->n;
   x->raster_ctas = x->n_slots;
+  if (c.raster_warps == 12 && !c.fused_step) {
+    int per_sm12 = 0;
+    if ((e = raster_ctas_per_sm(12, &per_sm12)) != cudaSuccess) return bail(e, "raster config");
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    x->raster_warps = 12;
+    x->raster_ctas = std::min(x->n_slots, std::max(1, per_sm12) * sms);
+  }
   {
     int dev = 0;
     cudaGetDevice(&dev);
@@ -999,7 +1012,8 @@ extern "C" gx_status gx_autotune(gx_ctx* x, const float* actions, const gx_outpu
     release();
     return fail(x, GX_ECUDA, "gx_autotune: state copy failed");
   }
-  const int per_sm = std::max(1, x->n_slots / std::max(1, x->sms));
+  int per_sm12 = 0;
+  CK(x, raster_ctas_per_sm(12, &per_sm12));
   const int px[4] = {0, 256, 96, 48};
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
@@ -1009,13 +1023,19 @@ extern "C" gx_status gx_autotune(gx_ctx* x, const float* actions, const gx_outpu
   gx_tune_result b{};
   b.ms_per_step = 1e30f;
   cudaError_t err = cudaSuccess;
+  // CTA shapes: 8 warps at the occupancy and one CTA per SM fewer, 12 warps
+  // at its occupancy (the fused step keeps 8 warps)
+  const int shapes = x->cfg.fused_step ? 2 : 3;
   for (int ci = 0; ci < 4 && err == cudaSuccess; ++ci)
     for (int order = 0; order < 2 && err == cudaSuccess; ++order)
-      for (int k = 0; k < 2 && err == cudaSuccess; ++k) {
-        const int ctas = std::min(x->n, std::max(1, per_sm - k) * x->sms);
+      for (int k = 0; k < shapes && err == cudaSuccess; ++k) {
+        const int warps = k == 2 ? 12 : 8;
+        const int per_sm = std::max(1, warps == 12 ? per_sm12 : x->n_slots / std::max(1, x->sms));
         if (k == 1 && per_sm == 1) continue;
+        const int ctas = std::min(x->n, std::max(1, per_sm - (k == 1 ? 1 : 0)) * x->sms);
         x->big_px = px[ci] > 0 ? px[ci] : (1 << 30);
         x->order_mode = order;
+        x->raster_warps = warps;
         x->raster_ctas = std::min(ctas, x->n_slots);
         if (x->cfg.fused_step) enqueue_fused(x, nullptr, actions, *out, s);  // warm-up
         else enqueue_step(x, actions, *out, s);
@@ -1039,6 +1059,7 @@ extern "C" gx_status gx_autotune(gx_ctx* x, const float* actions, const gx_outpu
           b.small_tri_px = px[ci];
           b.order_costliest_first = order;
           b.raster_ctas = x->raster_ctas;
+          b.raster_warps = warps;
         }
       }
   x->cfg.profile = saved_profile;
@@ -1050,6 +1071,7 @@ extern "C" gx_status gx_autotune(gx_ctx* x, const float* actions, const gx_outpu
   x->big_px = b.small_tri_px > 0 ? b.small_tri_px : (1 << 30);
   x->order_mode = b.order_costliest_first;
   x->raster_ctas = b.raster_ctas;
+  x->raster_warps = b.raster_warps;
   x->cfg.small_tri_px = b.small_tri_px;
   if (x->gexec) {  // a captured step holds the old settings
     cudaGraphExecDestroy(x->gexec);

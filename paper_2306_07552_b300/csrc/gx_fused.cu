@@ -68,6 +68,18 @@ __device__ void grid_barrier(unsigned* bar, unsigned* err) {
   __syncthreads();
 }
 
+// The reset and physics phases as separate (not inlined) functions, so their
+// register needs do not shape the rendering loop's allocation.
+__device__ __noinline__ void fused_reset(const ResetParams& P, int env,
+                                         float4 (*s_cand)[phys::kTryWindow], float4* so,
+                                         float* s_rho, unsigned* s_bad, int* s_robot_try) {
+  phys::reset_env(P, env, s_cand, so, s_rho, *s_bad, *s_robot_try);
+}
+
+__device__ __noinline__ void fused_physics(const PhysicsParams& P, int env, int lane, float4* so) {
+  phys::physics_env(P, env, lane, so);
+}
+
 template <bool kCount>
 __global__ void __launch_bounds__(kThreads, kRasterMinBlocks) fused_step_kernel(const FusedParams F) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -87,7 +99,7 @@ __global__ void __launch_bounds__(kThreads, kRasterMinBlocks) fused_step_kernel(
     int* s_robot_try = reinterpret_cast<int*>(s_bad + 1);
     for (int env = blockIdx.x; env < n; env += gridDim.x) {
       if (!F.reset_mask[env]) continue;
-      phys::reset_env(F.rs, env, s_cand, so, s_rho, *s_bad, *s_robot_try);
+      fused_reset(F.rs, env, s_cand, so, s_rho, s_bad, s_robot_try);
       __syncthreads();
     }
     grid_barrier(F.barrier, F.rp.err);
@@ -101,7 +113,7 @@ __global__ void __launch_bounds__(kThreads, kRasterMinBlocks) fused_step_kernel(
                      ? reinterpret_cast<float4*>(C.list) + (size_t)C.warp * M
                      : F.obj_scratch + ((size_t)blockIdx.x * kWarps + C.warp) * GX_MAX_OBJECTS;
     for (int env = blockIdx.x * kWarps + C.warp; env < n; env += gridDim.x * kWarps) {
-      phys::physics_env(F.pp, env, C.lane, so);
+      fused_physics(F.pp, env, C.lane, so);
       __syncwarp();
     }
   }
@@ -116,7 +128,7 @@ __global__ void __launch_bounds__(kThreads, kRasterMinBlocks) fused_step_kernel(
     __syncthreads();
     const int env = C.ctr[0];
     if (env >= n) break;
-    render_env<kCount>(F.rp, env, C, phase, cn);
+    render_env<kCount, kWarps>(F.rp, env, C, phase, cn);
   }
   raster_cta_end<kCount>(F.rp, C, cn);
 }
@@ -124,7 +136,7 @@ __global__ void __launch_bounds__(kThreads, kRasterMinBlocks) fused_step_kernel(
 }  // namespace
 
 cudaError_t fused_configure() {
-  const int bytes = (int)raster_smem_bytes();
+  const int bytes = (int)raster_smem_bytes(8);
   cudaError_t e = cudaFuncSetAttribute(fused_step_kernel<false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e != cudaSuccess) return e;
@@ -137,7 +149,7 @@ cudaError_t fused_max_ctas(int* ctas) {
   cudaError_t e = fused_configure();
   if (e != cudaSuccess) return e;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_step_kernel<false>, kThreads,
-                                                         raster_smem_bytes())) != cudaSuccess)
+                                                         raster_smem_bytes(8))) != cudaSuccess)
     return e;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
@@ -149,7 +161,7 @@ cudaError_t launch_fused_step(const FusedParams& f, int ctas, cudaStream_t s) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(ctas);
   cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = raster_smem_bytes();
+  cfg.dynamicSmemBytes = raster_smem_bytes(8);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;

@@ -162,6 +162,7 @@ constexpr int kRasterMinBlocks = 3;
 
 struct RasterParams {
   int n, M, W, H;
+  int warps;                     // warps per CTA: 8 (0 = 8) or 12
   int big_px;                    // larger bounding boxes go to the warp scan
   unsigned long long* fb_slots;  // [n_slots][H][W] keys
   uint32_t* fb_epoch;            // [n_slots] epoch of each slot's keys (NULL: slots cleared)
@@ -315,8 +316,9 @@ void launch_column_build(const float* boxes, int n_boxes, double ox, double oz, 
                          double yhi, int ncx, int ncz, const uint32_t* offsets, uint32_t* counts,
                          float2* spans, unsigned* overflow, cudaStream_t s);
 
-size_t raster_smem_bytes();
+size_t raster_smem_bytes(int warps = 8);
 cudaError_t raster_configure(int* slots);
+cudaError_t raster_ctas_per_sm(int warps, int* per_sm);
 void launch_grid_build(float* grid, const float* boxes, int n_boxes, float ox, float oy, float oz,
                        float h, int nx, int ny, int nz, cudaStream_t s);
 

@@ -56,8 +56,11 @@ namespace {
 
 using namespace rast;
 
-template <bool kCount>
-__global__ void __launch_bounds__(kThreads, kRasterMinBlocks) raster_kernel(const RasterParams P) {
+// kW warps per CTA: 8 (three CTAs per SM) or 12 (two), a rasteriser
+// setting the autotuner chooses.
+template <bool kCount, int kW>
+__global__ void __launch_bounds__(kW * 32, kW == 8 ? kRasterMinBlocks : 2)
+    raster_kernel(const RasterParams P) {
   extern __shared__ __align__(128) unsigned char smem[];
   RasterCta<kCount> C;
   uint32_t phase[2];
@@ -71,24 +74,31 @@ __global__ void __launch_bounds__(kThreads, kRasterMinBlocks) raster_kernel(cons
     __syncthreads();
     const int env = C.ctr[0];
     if (env >= P.n) break;
-    render_env<kCount>(P, env, C, phase, cn);
+    render_env<kCount, kW>(P, env, C, phase, cn);
   }
   raster_cta_end<kCount>(P, C, cn);
 }
 
 }  // namespace
 
-size_t raster_smem_bytes() { return 128 + kListCap * sizeof(uint2) + kWarps * sizeof(WarpSmem); }
+size_t raster_smem_bytes(int warps) {
+  return 128 + kListCap * sizeof(uint2) + (size_t)(warps > 0 ? warps : kWarps) * sizeof(WarpSmem);
+}
 
 cudaError_t raster_configure(int* slots) {
-  const int bytes = (int)raster_smem_bytes();
-  cudaError_t e = cudaFuncSetAttribute(raster_kernel<false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(raster_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
+  const int b8 = (int)raster_smem_bytes(8), b12 = (int)raster_smem_bytes(12);
+  if ((e = cudaFuncSetAttribute(raster_kernel<false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                b8)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(raster_kernel<true, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                b8)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(raster_kernel<false, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                b12)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(raster_kernel<true, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                b12)) != cudaSuccess)
+    return e;
   int per_sm = 0, dev = 0, sms = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raster_kernel<false>, kThreads, bytes);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raster_kernel<false, 8>, 256, b8);
   if (e != cudaSuccess) return e;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
@@ -96,13 +106,29 @@ cudaError_t raster_configure(int* slots) {
   return cudaSuccess;
 }
 
+cudaError_t raster_ctas_per_sm(int warps, int* per_sm) {
+  return warps == 12
+             ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, raster_kernel<false, 12>, 384,
+                                                             raster_smem_bytes(12))
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, raster_kernel<false, 8>, 256,
+                                                             raster_smem_bytes(8));
+}
+
 void launch_raster(const RasterParams& p, cudaStream_t s) {
-  const size_t smem = raster_smem_bytes();
   const int grid = p.n < p.n_slots ? p.n : p.n_slots;  // n_slots: CTAs to launch
-  if (p.counters)
-    raster_kernel<true><<<grid, kThreads, smem, s>>>(p);
-  else
-    raster_kernel<false><<<grid, kThreads, smem, s>>>(p);
+  if (p.warps == 12) {
+    const size_t smem = raster_smem_bytes(12);
+    if (p.counters)
+      raster_kernel<true, 12><<<grid, 384, smem, s>>>(p);
+    else
+      raster_kernel<false, 12><<<grid, 384, smem, s>>>(p);
+  } else {
+    const size_t smem = raster_smem_bytes(8);
+    if (p.counters)
+      raster_kernel<true, 8><<<grid, 256, smem, s>>>(p);
+    else
+      raster_kernel<false, 8><<<grid, 256, smem, s>>>(p);
+  }
 }
 
 }  // namespace gx

@@ -570,8 +570,9 @@ __device__ __forceinline__ void raster_cta_begin(const RasterParams& P, unsigned
   C.dead = false;
 }
 
-// Renders environment env into its observation rows (the whole CTA).
-template <bool kCount>
+// Renders environment env into its observation rows (the whole CTA of kW
+// warps).
+template <bool kCount, int kW>
 __device__ __forceinline__ void render_env(const RasterParams& P, const int env,
                                            RasterCta<kCount>& C, uint32_t phase[2], Cnt& cn) {
   int* ctr = C.ctr;
@@ -588,7 +589,7 @@ __device__ __forceinline__ void render_env(const RasterParams& P, const int env,
   // needs no clearing between environments; every 255 environments it wraps
   // and is cleared once
   if (++epoch == 256u) {
-    for (int p = tid * 2; p < npix; p += kThreads * 2)
+    for (int p = tid * 2; p < npix; p += kW * 32 * 2)
       asm volatile("st.global.cg.L2::cache_hint.v2.u64 [%0], {%1, %1}, %2;" ::"l"(vw.fb + p),
                    "l"(~0ull), "l"(vw.pol)
                    : "memory");
@@ -634,7 +635,7 @@ __device__ __forceinline__ void render_env(const RasterParams& P, const int env,
     __syncthreads();
     // 1. the whole CTA culls the clusters of this pass into the list
     const int end = min(base + kListCap, S.n_meshlets);
-    for (int m = base + tid; m < end; m += kThreads) {
+    for (int m = base + tid; m < end; m += kW * 32) {
       if (kCount) cn.v[kCntClustersTested]++;
       const float4* hd = S.mhdr + (size_t)kMeshletHdr * m;
       const float4 h0 = __ldg(hd);
@@ -765,7 +766,7 @@ __device__ __forceinline__ void render_env(const RasterParams& P, const int env,
   // slot is read from L2 and left as it is (the next environment's keys carry
   // a newer epoch); keys of older epochs are background
   const size_t out0 = (size_t)env * npix;
-  for (int p = tid * 4; p < npix; p += kThreads * 4) {
+  for (int p = tid * 4; p < npix; p += kW * 32 * 4) {
     unsigned long long keys[4];
     asm volatile("ld.global.cg.L2::cache_hint.v2.u64 {%0, %1}, [%2], %3;"
                  : "=l"(keys[0]), "=l"(keys[1]) : "l"(vw.fb + p), "l"(vw.pol));

@@ -80,7 +80,8 @@ class GxConfig(C.Structure):
                 ("sdf_mode", C.c_int32), ("sdf_margin", C.c_float), ("broadphase", C.c_int32),
                 ("render_robot", C.c_int32), ("heuristics", C.c_int32),
                 ("raster_order", C.c_int32), ("env_offset", C.c_int32),
-                ("object_boxes", C.c_int32), ("fused_step", C.c_int32)]
+                ("object_boxes", C.c_int32), ("raster_warps", C.c_int32),
+                ("fused_step", C.c_int32)]
 
 
 OUTPUT_KEYS = ["depth", "rgb", "pose", "obj_pos", "held", "contact_mask", "contact_flags", "event",
@@ -100,7 +101,8 @@ class GxTrainParams(C.Structure):
 
 class GxTuneResult(C.Structure):
     _fields_ = [("small_tri_px", C.c_int32), ("order_costliest_first", C.c_int32),
-                ("raster_ctas", C.c_int32), ("ms_per_step", C.c_float)]
+                ("raster_ctas", C.c_int32), ("ms_per_step", C.c_float),
+                ("raster_warps", C.c_int32)]
 
 
 class GxError(RuntimeError):
@@ -337,7 +339,7 @@ class Sim:
                  seed=1, env_scene=None, small_tri_px=0, use_graph=False,
                  profile=0, sdf_mode=0, sdf_margin=0.02, heuristics=0, render_robot=False,
                  broadphase=False, raster_order=0, env_offset=0, object_boxes=False,
-                 fused_step=False):
+                 fused_step=False, raster_warps=0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("gx needs a CUDA device; there is no CPU fallback")
@@ -364,6 +366,7 @@ class Sim:
         cfg.env_offset = int(env_offset)
         cfg.object_boxes = int(object_boxes)
         cfg.fused_step = int(fused_step)
+        cfg.raster_warps = int(raster_warps)
         self.object_boxes = bool(object_boxes)
         self.robot_c = robot_struct(robot)
         self.handle = C.c_void_p()
@@ -467,7 +470,8 @@ class Sim:
                                  C.byref(self._outs), int(steps), C.byref(r),
                                  self._stream(stream)), self.handle)
         return {"small_tri_px": r.small_tri_px, "order_costliest_first": r.order_costliest_first,
-                "raster_ctas": r.raster_ctas, "ms_per_step": r.ms_per_step}
+                "raster_ctas": r.raster_ctas, "raster_warps": r.raster_warps,
+                "ms_per_step": r.ms_per_step}
 
     def nsdf_counters(self):
         """Neural-SDF decision counters since the last call (profile bit 2 only)."""

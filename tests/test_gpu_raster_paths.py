@@ -3,7 +3,8 @@
 The autotuner chooses among expansion limits small_tri_px in {0, 256, 96, 48}
 (triangles whose clipped bounding box exceeds the limit are scanned by a whole
 warp over 8x4 blocks with int64 edge functions instead of being expanded
-pixel by pixel) and two work orders (index order, costliest scene first).
+pixel by pixel), two work orders (index order, costliest scene first) and
+two CTA shapes (8 warps, three CTAs per SM; 12 warps, two per SM).
 Each candidate is checked against the FP64 oracle's images of the same
 state, pixel by pixel, on views forced close to walls so that the block-scan
 path draws many large triangles per view (coarsely tessellated walls a
@@ -82,22 +83,24 @@ def test_every_autotune_candidate_renders_the_oracle_images():
     assert per_view >= 60
 
     refs, after0, tally = None, None, Tally()
-    for px in (0, 256, 96, 48):
-        for order in (1, 2):
-            sim = gx.Sim(ss, ROBOT, n, small_tri_px=px, raster_order=order, **kw)
-            sim.load_state(blob)
-            out = sim.step(still)
-            torch.cuda.synchronize()
-            after = sim.state_arrays()
-            if refs is None:
-                after0 = {k: v.copy() for k, v in after.items()}
-                refs = [oracle_image(orcs[env_scene[e]], after0, e, W, W, M) for e in range(n)]
-            for k in after0:
-                assert np.array_equal(after[k], after0[k]), (px, order, k)
-            for e in range(n):
-                check_image(orcs[env_scene[e]], after0, out, e, W, W, M, tally, ref=refs[e])
-            sim.close()
+    cands = [(px, order, 8) for px in (0, 256, 96, 48) for order in (1, 2)]
+    cands += [(px, 2, 12) for px in (0, 48)]     # the 12-warp CTA shape
+    for px, order, warps in cands:
+        sim = gx.Sim(ss, ROBOT, n, small_tri_px=px, raster_order=order, raster_warps=warps,
+                     **kw)
+        sim.load_state(blob)
+        out = sim.step(still)
+        torch.cuda.synchronize()
+        after = sim.state_arrays()
+        if refs is None:
+            after0 = {k: v.copy() for k, v in after.items()}
+            refs = [oracle_image(orcs[env_scene[e]], after0, e, W, W, M) for e in range(n)]
+        for k in after0:
+            assert np.array_equal(after[k], after0[k]), (px, order, warps, k)
+        for e in range(n):
+            check_image(orcs[env_scene[e]], after0, out, e, W, W, M, tally, ref=refs[e])
+        sim.close()
     print(tally)
     print(tally.report())
-    assert tally.pixels > 0.9 * 8 * n * W * W
+    assert tally.pixels > 0.9 * len(cands) * n * W * W
     ss.close()
