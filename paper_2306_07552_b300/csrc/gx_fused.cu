@@ -68,18 +68,6 @@ __device__ void grid_barrier(unsigned* bar, unsigned* err) {
   __syncthreads();
 }
 
-// The reset and physics phases as separate (not inlined) functions, so their
-// register needs do not shape the rendering loop's allocation.
-__device__ __noinline__ void fused_reset(const ResetParams& P, int env,
-                                         float4 (*s_cand)[phys::kTryWindow], float4* so,
-                                         float* s_rho, unsigned* s_bad, int* s_robot_try) {
-  phys::reset_env(P, env, s_cand, so, s_rho, *s_bad, *s_robot_try);
-}
-
-__device__ __noinline__ void fused_physics(const PhysicsParams& P, int env, int lane, float4* so) {
-  phys::physics_env(P, env, lane, so);
-}
-
 template <bool kCount>
 __global__ void __launch_bounds__(kThreads, kRasterMinBlocks) fused_step_kernel(const FusedParams F) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -99,7 +87,7 @@ __global__ void __launch_bounds__(kThreads, kRasterMinBlocks) fused_step_kernel(
     int* s_robot_try = reinterpret_cast<int*>(s_bad + 1);
     for (int env = blockIdx.x; env < n; env += gridDim.x) {
       if (!F.reset_mask[env]) continue;
-      fused_reset(F.rs, env, s_cand, so, s_rho, s_bad, s_robot_try);
+      phys::reset_env(F.rs, env, s_cand, so, s_rho, *s_bad, *s_robot_try);
       __syncthreads();
     }
     grid_barrier(F.barrier, F.rp.err);
@@ -113,7 +101,7 @@ __global__ void __launch_bounds__(kThreads, kRasterMinBlocks) fused_step_kernel(
                      ? reinterpret_cast<float4*>(C.list) + (size_t)C.warp * M
                      : F.obj_scratch + ((size_t)blockIdx.x * kWarps + C.warp) * GX_MAX_OBJECTS;
     for (int env = blockIdx.x * kWarps + C.warp; env < n; env += gridDim.x * kWarps) {
-      fused_physics(F.pp, env, C.lane, so);
+      phys::physics_env(F.pp, env, C.lane, so);
       __syncwarp();
     }
   }
