@@ -347,7 +347,7 @@ typedef struct {
  * setting -- expansion limit small_tri_px in {0, 256, 96, 48}, work order
  * {index, costliest scene first}, CTA shape {8 warps at the occupancy (three
  * CTAs per SM), 8 warps one CTA per SM fewer, 12 warps at its occupancy (two
- * per SM); the fused step keeps 8 warps} -- for `steps` steps each (plus one
+ * per SM); the fused step and box objects keep 8 warps} -- for `steps` steps each (plus one
  * warm-up), restoring the
  * state after every candidate, and keeps the fastest (written to *best when
  * not NULL).  The outputs are overwritten; the state is left as before the

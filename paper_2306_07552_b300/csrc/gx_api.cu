@@ -211,7 +211,7 @@ RasterParams raster_params(gx_ctx* c, const gx_outputs& out) {
   rp.M = c->M;
   rp.W = c->cfg.img_w;
   rp.H = c->cfg.img_h;
-  rp.warps = c->cfg.fused_step ? 8 : c->raster_warps;
+  rp.warps = (c->cfg.fused_step || c->cfg.object_boxes) ? 8 : c->raster_warps;
   rp.big_px = c->big_px;
   rp.fb_slots = c->d_fb;
   rp.fb_epoch = c->d_fb_epoch;
@@ -1025,7 +1025,7 @@ extern "C" gx_status gx_autotune(gx_ctx* x, const float* actions, const gx_outpu
   cudaError_t err = cudaSuccess;
   // CTA shapes: 8 warps at the occupancy and one CTA per SM fewer, 12 warps
   // at its occupancy (the fused step keeps 8 warps)
-  const int shapes = x->cfg.fused_step ? 2 : 3;
+  const int shapes = (x->cfg.fused_step || x->cfg.object_boxes) ? 2 : 3;
   for (int ci = 0; ci < 4 && err == cudaSuccess; ++ci)
     for (int order = 0; order < 2 && err == cudaSuccess; ++order)
       for (int k = 0; k < shapes && err == cudaSuccess; ++k) {

@@ -58,7 +58,7 @@ using namespace rast;
 
 // kW warps per CTA: 8 (three CTAs per SM) or 12 (two), a rasteriser
 // setting the autotuner chooses.
-template <bool kCount, int kW>
+template <bool kCount, int kW, bool kBoxes = false>
 __global__ void __launch_bounds__(kW * 32, kW == 8 ? kRasterMinBlocks : 2)
     raster_kernel(const RasterParams P) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(kW * 32, kW == 8 ? kRasterMinBlocks : 2)
     __syncthreads();
     const int env = C.ctr[0];
     if (env >= P.n) break;
-    render_env<kCount, kW>(P, env, C, phase, cn);
+    render_env<kCount, kW, kBoxes>(P, env, C, phase, cn);
   }
   raster_cta_end<kCount>(P, C, cn);
 }
@@ -95,7 +95,11 @@ cudaError_t raster_configure(int* slots) {
       (e = cudaFuncSetAttribute(raster_kernel<false, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 b12)) != cudaSuccess ||
       (e = cudaFuncSetAttribute(raster_kernel<true, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                b12)) != cudaSuccess)
+                                b12)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(raster_kernel<false, 8, true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, b8)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(raster_kernel<true, 8, true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, b8)) != cudaSuccess)
     return e;
   int per_sm = 0, dev = 0, sms = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raster_kernel<false, 8>, 256, b8);
@@ -116,7 +120,13 @@ cudaError_t raster_ctas_per_sm(int warps, int* per_sm) {
 
 void launch_raster(const RasterParams& p, cudaStream_t s) {
   const int grid = p.n < p.n_slots ? p.n : p.n_slots;  // n_slots: CTAs to launch
-  if (p.warps == 12) {
+  if (p.obox) {  // box objects: 8 warps
+    const size_t smem = raster_smem_bytes(8);
+    if (p.counters)
+      raster_kernel<true, 8, true><<<grid, 256, smem, s>>>(p);
+    else
+      raster_kernel<false, 8, true><<<grid, 256, smem, s>>>(p);
+  } else if (p.warps == 12) {
     const size_t smem = raster_smem_bytes(12);
     if (p.counters)
       raster_kernel<true, 12><<<grid, 384, smem, s>>>(p);

@@ -571,8 +571,9 @@ __device__ __forceinline__ void raster_cta_begin(const RasterParams& P, unsigned
 }
 
 // Renders environment env into its observation rows (the whole CTA of kW
-// warps).
-template <bool kCount, int kW>
+// warps).  kBoxes: the objects are oriented boxes (P.obox), drawn as cubes;
+// a separate instantiation, so the sphere objects' code stays as it is.
+template <bool kCount, int kW, bool kBoxes = false>
 __device__ __forceinline__ void render_env(const RasterParams& P, const int env,
                                            RasterCta<kCount>& C, uint32_t phase[2], Cnt& cn) {
   int* ctr = C.ctr;
@@ -706,7 +707,7 @@ __device__ __forceinline__ void render_env(const RasterParams& P, const int env,
         if (!sphere_visible(cm, vw, o.x, o.y, o.z, o.w * 1.0001f + 1e-6f)) continue;
         const uint32_t rgb = __ldg(P.obj_rgb + slot);
         int nv = P.omesh_nv, nt = P.omesh_nt;
-        if (P.obox) {
+        if (kBoxes) {
           // an oriented box (its bounding sphere was culled above): the unit
           // cube, corner k = signs of bits 0/1/2 of k, mapped by its world
           // rotation times diag(half extents) -- R_y(yaw) resting, the
