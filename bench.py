@@ -160,10 +160,18 @@ def kernel_capture(workload):
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    src = open(os.path.join(ROOT, "paper_2306_07552_b300", "csrc", "gx_raster.cu"), "rb").read()
-    if d.get("source_sha1") != hashlib.sha1(src).hexdigest():
+    if d.get("source_sha1") != raster_source_sha1():
         return None
     return d
+
+
+def raster_source_sha1():
+    """sha1 of the rasteriser's source (its kernel file, then its device code)."""
+    csrc = os.path.join(ROOT, "paper_2306_07552_b300", "csrc")
+    h = hashlib.sha1()
+    for f in ("gx_raster.cu", "gx_raster_dev.cuh"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()
 
 
 def kernel_traffic(workload):
