@@ -477,6 +477,8 @@ def main():
                     help="the paper's heuristics: bit 0 sliding, bit 1 object placing")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default rasteriser setting instead of timing candidates")
+    ap.add_argument("--occlusion", action="store_true",
+                    help="cull clusters by occlusion (two phases per environment)")
     ap.add_argument("--fused", action="store_true",
                     help="one cooperative persistent launch per step (resets, physics, "
                          "rendering)")
@@ -516,7 +518,8 @@ def main():
                   small_tri_px=args.small_px, heuristics=args.heuristics,
                   render_robot=args.render_robot, broadphase=args.broadphase,
                   env_scene=plan.env_scene, env_offset=plan.first,
-                  object_boxes=w.objects == "boxes", fused_step=args.fused)
+                  object_boxes=w.objects == "boxes", fused_step=args.fused,
+                  occlusion_cull=args.occlusion)
     column = w.sdf == "column"
     sdf_mode = 1 if neural else (2 if column else 0)
     # per-kernel CUDA events on the launching stream (the roofline's kernel

@@ -203,6 +203,18 @@ typedef struct {
                               rendering (GX_EINVAL otherwise)                 */
   int32_t raster_warps;    /* warps per rasteriser CTA: 0 or 8 (three CTAs per
                               SM), 12 (two per SM); gx_autotune may change it */
+  int32_t occlusion_cull;  /* 1: the rasteriser culls clusters by occlusion in
+                              two phases per environment: first the clusters
+                              it showed in its previous image (one bit per
+                              cluster, kept by the context), then the others
+                              and the objects only where the depth bound of
+                              some 8x8 tile they touch (the farthest of that
+                              tile's pixels so far) could still let them win;
+                              the bits are rewritten from the final image.
+                              Images are identical to the unculled ones; with
+                              it, gx_autotune also times the setting without
+                              it.  8 warps per CTA; not with fused_step or
+                              object_boxes (GX_EINVAL)                        */
   int32_t fused_step;      /* 1: each step (gx_step, gx_step_reset) is one
                               cooperative persistent launch of the
                               rasteriser's grid: masked resets, then physics
@@ -328,7 +340,8 @@ gx_status gx_phase_times(gx_ctx* ctx, double ms[4], int64_t launches[4]);
  * triangles seen, front-facing, rasterised by fragment expansion, pixels
  * they expand to, rasterised per warp, 8x4 blocks the warps scanned,
  * near-clipped, fragments written, mbarrier polls, expansion passes,
- * 32-triangle set-up rounds, expansion slots (runs of up to four pixels).
+ * 32-triangle set-up rounds, expansion slots (runs of up to four pixels),
+ * clusters skipped by the occlusion test.
  * Fills out[0..n-1]; waits for the device.
  * GX_ESTATE when the context does not count. */
 gx_status gx_raster_counters(gx_ctx* ctx, int64_t* out, int32_t n);
@@ -341,6 +354,7 @@ typedef struct {
   int32_t raster_ctas;            /* persistent CTAs launched                    */
   float ms_per_step;              /* measured step time with these settings      */
   int32_t raster_warps;           /* warps per rasteriser CTA (8 or 12)          */
+  int32_t occlusion_cull;         /* 1: clusters culled by occlusion             */
 } gx_tune_result;
 
 /* Times the step on this context's own state under each candidate rasteriser

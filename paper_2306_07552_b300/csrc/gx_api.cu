@@ -45,6 +45,9 @@ struct gx_ctx {
   float* d_cam = nullptr;
   float4* d_robot_sph = nullptr;       // robot spheres for rendering the robot body
   float4* d_held_M = nullptr;          // box objects: the held box's world rotation x extents
+  uint32_t* d_vis = nullptr;           // occlusion culling: clusters shown in the last image
+  int vis_words = 0;
+  bool occlusion = false;              // occlusion culling in use (the autotuner may change it)
   // fused step (one cooperative launch per step)
   int fused_ctas = 0;
   float4* d_fused_scratch = nullptr;   // reset try tables, per CTA
@@ -229,6 +232,10 @@ RasterParams raster_params(gx_ctx* c, const gx_outputs& out) {
   rp.omesh_nt = c->set->omesh_nt;
   rp.obj_rgb = c->set->obj_rgb;
   rp.robot_sph = c->d_robot_sph;
+  if (c->occlusion && !c->cfg.fused_step && !c->cfg.object_boxes) {
+    rp.vis = c->d_vis;
+    rp.vis_words = c->vis_words;
+  }
   if (c->cfg.object_boxes) {
     rp.obox = c->st.obox;
     rp.held_M = c->d_held_M;
@@ -525,6 +532,10 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
     return fail(nullptr, GX_EINVAL, "raster_order must be 0, 1 or 2");
   if (c.env_offset < 0 || (int64_t)c.env_offset + c.n_envs > INT32_MAX)
     return fail(nullptr, GX_EINVAL, "env_offset must be >= 0 with env_offset + n_envs < 2^31");
+  if (c.occlusion_cull < 0 || c.occlusion_cull > 1)
+    return fail(nullptr, GX_EINVAL, "occlusion_cull must be 0 or 1");
+  if (c.occlusion_cull && (c.fused_step || c.object_boxes))
+    return fail(nullptr, GX_EINVAL, "occlusion_cull: not with fused_step or object_boxes");
   if (c.raster_warps != 0 && c.raster_warps != 8 && c.raster_warps != 12)
     return fail(nullptr, GX_EINVAL, "raster_warps must be 0, 8 or 12");
   if (c.fused_step < 0 || c.fused_step > 1)
@@ -625,6 +636,18 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
       ((e = cudaMalloc(&x->d_held_M, n * 3 * sizeof(float4))) != cudaSuccess ||
        (e = cudaMemset(x->d_held_M, 0, n * 3 * sizeof(float4))) != cudaSuccess))
     return bail(e, "held box rotation");
+  if (c.occlusion_cull) {
+    int mmax = 1;
+    for (int sc = 0; sc < set->n; ++sc) mmax = std::max(mmax, set->meshlets_per_scene[sc]);
+    x->vis_words = (mmax + 31) / 32;
+    const size_t bytes = n * (size_t)x->vis_words * sizeof(uint32_t);
+    if ((e = cudaMalloc(&x->d_vis, bytes)) != cudaSuccess ||
+        (e = cudaMemset(x->d_vis, 0, bytes)) != cudaSuccess)
+      return bail(e, "visibility bits");
+    x->occlusion = true;
+    x->raster_warps = 8;
+    x->raster_ctas = x->n_slots;
+  }
   if (c.fused_step) {
     if ((e = fused_max_ctas(&x->fused_ctas)) != cudaSuccess) return bail(e, "fused config");
     const size_t ctas = (size_t)std::max(x->fused_ctas, x->n_slots);
@@ -733,6 +756,7 @@ extern "C" void gx_destroy(gx_ctx* x) {
   cudaFree(x->d_robot);
   cudaFree(x->d_env_scene);
   cudaFree(x->d_held_M);
+  cudaFree(x->d_vis);
   cudaFree(x->d_fused_scratch);
   cudaFree(x->d_fused_obj);
   cudaFree(x->d_barrier);
@@ -1025,10 +1049,15 @@ extern "C" gx_status gx_autotune(gx_ctx* x, const float* actions, const gx_outpu
   cudaError_t err = cudaSuccess;
   // CTA shapes: 8 warps at the occupancy and one CTA per SM fewer, 12 warps
   // at its occupancy (the fused step keeps 8 warps)
+  // (occlusion culling, when the context has its visibility bits, as a CTA
+  // shape of its own: 8 warps at the occupancy)
   const int shapes = (x->cfg.fused_step || x->cfg.object_boxes) ? 2 : 3;
+  const int occ_shape = x->d_vis ? shapes : -1;
   for (int ci = 0; ci < 4 && err == cudaSuccess; ++ci)
     for (int order = 0; order < 2 && err == cudaSuccess; ++order)
-      for (int k = 0; k < shapes && err == cudaSuccess; ++k) {
+      for (int k = 0; k < shapes + (x->d_vis ? 1 : 0) && err == cudaSuccess; ++k) {
+        const bool occ = k == occ_shape;
+        x->occlusion = occ;
         const int warps = k == 2 ? 12 : 8;
         const int per_sm = std::max(1, warps == 12 ? per_sm12 : x->n_slots / std::max(1, x->sms));
         if (k == 1 && per_sm == 1) continue;
@@ -1060,6 +1089,7 @@ extern "C" gx_status gx_autotune(gx_ctx* x, const float* actions, const gx_outpu
           b.order_costliest_first = order;
           b.raster_ctas = x->raster_ctas;
           b.raster_warps = warps;
+          b.occlusion_cull = occ ? 1 : 0;
         }
       }
   x->cfg.profile = saved_profile;
@@ -1072,6 +1102,7 @@ extern "C" gx_status gx_autotune(gx_ctx* x, const float* actions, const gx_outpu
   x->order_mode = b.order_costliest_first;
   x->raster_ctas = b.raster_ctas;
   x->raster_warps = b.raster_warps;
+  x->occlusion = b.occlusion_cull != 0;
   x->cfg.small_tri_px = b.small_tri_px;
   if (x->gexec) {  // a captured step holds the old settings
     cudaGraphExecDestroy(x->gexec);

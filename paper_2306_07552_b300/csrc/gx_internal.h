@@ -182,6 +182,8 @@ struct RasterParams {
   const float4* obox;      // box objects: [n][M] half extents, yaw (NULL: spheres)
   const float4* held_M;    // box objects: [n][3] the held box's world rotation x extents
   const int* held;         // box objects: [n] held object index
+  uint32_t* vis;           // occlusion culling: [n][vis_words] clusters shown in the last image
+  int vis_words;
   float near_;
   void* depth;
   int depth_fp16;
@@ -206,6 +208,7 @@ enum RasterCounter {
   kCntExpandTrips,   // fragment-expansion loop trips (per warp)
   kCntRounds,        // 32-triangle rounds (per warp)
   kCntExpandSlots,   // fragment-expansion slots (runs of up to four pixels)
+  kCntClustersOccluded,  // clusters skipped by the occlusion test
   kRasterCounters
 };
 
@@ -316,7 +319,7 @@ void launch_column_build(const float* boxes, int n_boxes, double ox, double oz, 
                          double yhi, int ncx, int ncz, const uint32_t* offsets, uint32_t* counts,
                          float2* spans, unsigned* overflow, cudaStream_t s);
 
-size_t raster_smem_bytes(int warps = 8);
+size_t raster_smem_bytes(int warps = 8, int hiz_tiles = 0);
 cudaError_t raster_configure(int* slots);
 cudaError_t raster_ctas_per_sm(int warps, int* per_sm);
 void launch_grid_build(float* grid, const float* boxes, int n_boxes, float ox, float oy, float oz,

@@ -58,7 +58,7 @@ using namespace rast;
 
 // kW warps per CTA: 8 (three CTAs per SM) or 12 (two), a rasteriser
 // setting the autotuner chooses.
-template <bool kCount, int kW, bool kBoxes = false>
+template <bool kCount, int kW, bool kBoxes = false, bool kOcc = false>
 __global__ void __launch_bounds__(kW * 32, kW == 8 ? kRasterMinBlocks : 2)
     raster_kernel(const RasterParams P) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -74,16 +74,22 @@ __global__ void __launch_bounds__(kW * 32, kW == 8 ? kRasterMinBlocks : 2)
     __syncthreads();
     const int env = C.ctr[0];
     if (env >= P.n) break;
-    render_env<kCount, kW, kBoxes>(P, env, C, phase, cn);
+    render_env<kCount, kW, kBoxes, kOcc>(P, env, C, phase, cn);
   }
   raster_cta_end<kCount>(P, C, cn);
 }
 
 }  // namespace
 
-size_t raster_smem_bytes(int warps) {
-  return 128 + kListCap * sizeof(uint2) + (size_t)(warps > 0 ? warps : kWarps) * sizeof(WarpSmem);
+size_t raster_smem_bytes(int warps, int hiz_tiles) {
+  return 128 + kListCap * sizeof(uint2) + (size_t)(warps > 0 ? warps : kWarps) * sizeof(WarpSmem) +
+         (size_t)hiz_tiles * sizeof(uint32_t);
 }
+
+namespace {
+// occlusion culling: the tile bounds of the largest image (256 x 256)
+constexpr int kMaxHizTiles = (256 / kHizTile) * (256 / kHizTile);
+}  // namespace
 
 cudaError_t raster_configure(int* slots) {
   cudaError_t e;
@@ -99,7 +105,13 @@ cudaError_t raster_configure(int* slots) {
       (e = cudaFuncSetAttribute(raster_kernel<false, 8, true>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, b8)) != cudaSuccess ||
       (e = cudaFuncSetAttribute(raster_kernel<true, 8, true>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, b8)) != cudaSuccess)
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, b8)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(raster_kernel<false, 8, false, true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)raster_smem_bytes(8, kMaxHizTiles))) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(raster_kernel<true, 8, false, true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)raster_smem_bytes(8, kMaxHizTiles))) != cudaSuccess)
     return e;
   int per_sm = 0, dev = 0, sms = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raster_kernel<false, 8>, 256, b8);
@@ -120,7 +132,13 @@ cudaError_t raster_ctas_per_sm(int warps, int* per_sm) {
 
 void launch_raster(const RasterParams& p, cudaStream_t s) {
   const int grid = p.n < p.n_slots ? p.n : p.n_slots;  // n_slots: CTAs to launch
-  if (p.obox) {  // box objects: 8 warps
+  if (p.vis && !p.obox) {  // occlusion culling: 8 warps, the tile bounds in shared memory
+    const size_t smem = raster_smem_bytes(8, (p.W / kHizTile) * (p.H / kHizTile));
+    if (p.counters)
+      raster_kernel<true, 8, false, true><<<grid, 256, smem, s>>>(p);
+    else
+      raster_kernel<false, 8, false, true><<<grid, 256, smem, s>>>(p);
+  } else if (p.obox) {  // box objects: 8 warps
     const size_t smem = raster_smem_bytes(8);
     if (p.counters)
       raster_kernel<true, 8, true><<<grid, 256, smem, s>>>(p);

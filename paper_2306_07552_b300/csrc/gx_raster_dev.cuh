@@ -519,6 +519,114 @@ __device__ __forceinline__ void issue_cluster(WarpSmem& ws, int buf, const DScen
   bulk_g2s(ws.cbuf[buf], S.tri_rgb + toff, tbytes, &ws.bar[buf]);
 }
 
+// ---------------------------------------------------------------------------
+// Occlusion culling of clusters (two phases per environment).  The depth
+// bound of a screen tile of 8x8 pixels is the smallest 1/z over its pixels
+// (0 where a pixel is not yet covered), kept as the bits of the positive
+// float so that integer order is float order.  Every pixel of the final
+// image is at least as near as the bound of its tile, so a cluster whose
+// nearest possible point is strictly farther than the bound of every tile
+// its screen rectangle touches cannot win any pixel: skipping it leaves the
+// image unchanged, bit for bit.
+// ---------------------------------------------------------------------------
+constexpr int kHizTile = 8;
+constexpr float kHizMargin = 1e-4f;  // relative; covers FP32 rounding of both sides
+
+// 1/z bits of a framebuffer key of the current epoch, 0 for background.
+__device__ __forceinline__ uint32_t key_invz_bits(unsigned long long key, unsigned long long tag) {
+  return (key & (0xffull << 56)) == tag ? ~(uint32_t)(key >> 24) : 0u;
+}
+
+// True when the axis-aligned box [lo, hi] (world) lies strictly behind the
+// depth bound of every tile its projection touches.  Conservative: a box
+// that reaches the near plane, or whose rectangle leaves the image, is kept.
+__device__ __forceinline__ bool hiz_occluded(const Cam& cm, const View& vw, float lx, float ly,
+                                             float lz, float hx, float hy, float hz,
+                                             const uint32_t* hiz) {
+  float zmin = CUDART_INF_F, umin = CUDART_INF_F, umax = -CUDART_INF_F, vmin = CUDART_INF_F,
+        vmax = -CUDART_INF_F;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const float dx = ((k & 1) ? hx : lx) - cm.ex, dy = ((k & 2) ? hy : ly) - cm.ey,
+                dz = ((k & 4) ? hz : lz) - cm.ez;
+    const float zc = cm.fx * dx + cm.fy * dy + cm.fz * dz;
+    const float xc = cm.rx * dx + cm.ry * dy + cm.rz * dz;
+    const float yc = cm.ux * dx + cm.uy * dy + cm.uz * dz;
+    if (!(zc >= cm.near_)) return false;
+    const float iz = 1.f / zc;
+    const float u = fmaf(cm.f, xc * iz, cm.cx), v = fmaf(-cm.f, yc * iz, cm.cy);
+    zmin = fminf(zmin, zc);
+    umin = fminf(umin, u);
+    umax = fmaxf(umax, u);
+    vmin = fminf(vmin, v);
+    vmax = fmaxf(vmax, v);
+  }
+  // one pixel of slack on every side, then the tiles that rectangle touches
+  if (umax < -1.f || vmax < -1.f || umin > (float)vw.W + 1.f || vmin > (float)vw.H + 1.f)
+    return false;
+  const int tw = vw.W / kHizTile, th = vw.H / kHizTile;
+  const int tx0 = max(0, (int)floorf(umin - 1.f) / kHizTile);
+  const int tx1 = min(tw - 1, max(0, (int)floorf(umax + 1.f)) / kHizTile);
+  const int ty0 = max(0, (int)floorf(vmin - 1.f) / kHizTile);
+  const int ty1 = min(th - 1, max(0, (int)floorf(vmax + 1.f)) / kHizTile);
+  // the nearest 1/z any point of the box can have, rounded outward
+  const uint32_t need = __float_as_uint((1.f / zmin) * (1.f + kHizMargin));
+  for (int ty = ty0; ty <= ty1; ++ty)
+    for (int tx = tx0; tx <= tx1; ++tx)
+      if (hiz[ty * tw + tx] <= need) return false;
+  return true;
+}
+
+// The depth bound of every tile from the framebuffer slot (current epoch).
+template <int kW>
+__device__ __forceinline__ void hiz_build(const View& vw, uint32_t* hiz, int tid) {
+  const int tw = vw.W / kHizTile, tiles = tw * (vw.H / kHizTile);
+  for (int t = tid; t < tiles; t += kW * 32) {
+    const int tx = t % tw, ty = t / tw;
+    uint32_t m = 0xffffffffu;
+#pragma unroll 2
+    for (int r = 0; r < kHizTile; ++r) {
+      const unsigned long long* row = vw.fb + (size_t)(ty * kHizTile + r) * vw.W + tx * kHizTile;
+#pragma unroll
+      for (int c = 0; c < kHizTile; c += 2) {
+        unsigned long long k0, k1;
+        asm volatile("ld.global.cg.L2::cache_hint.v2.u64 {%0, %1}, [%2], %3;"
+                     : "=l"(k0), "=l"(k1) : "l"(row + c), "l"(vw.pol));
+        m = min(m, min(key_invz_bits(k0, vw.tag), key_invz_bits(k1, vw.tag)));
+      }
+    }
+    hiz[t] = m;
+  }
+}
+
+// The frustum, normal-cone and plane tests of cluster m (as the cull pass
+// makes them); its bounding box corners in lo, hi when it passes.
+__device__ __forceinline__ bool cluster_in_view(const DScene& S, int m, const Cam& cm,
+                                                const View& vw, float4& lo, float4& hi,
+                                                uint2& entry) {
+  const float4* hd = S.mhdr + (size_t)kMeshletHdr * m;
+  const float4 h0 = __ldg(hd);
+  if (!sphere_visible(cm, vw, h0.x, h0.y, h0.z, h0.w)) return false;
+  const float4 h1 = __ldg(hd + 1), h2 = __ldg(hd + 2);
+  lo = __ldg(hd + 3);
+  hi = __ldg(hd + 4);
+  if (h2.x > -0.5f) {
+    const float vx = h0.x - cm.ex, vy = h0.y - cm.ey, vz = h0.z - cm.ez;
+    const float av = h1.x * vx + h1.y * vy + h1.z * vz;
+    const float cx_ = h1.y * vz - h1.z * vy, cy_ = h1.z * vx - h1.x * vz, cz_ = h1.x * vy - h1.y * vx;
+    const float cr = sqrtf(cx_ * cx_ + cy_ * cy_ + cz_ * cz_);
+    if (av * h2.x - cr * h1.w > h0.w * 1.001f + 1e-4f) return false;
+  }
+  if (hi.w > 0.5f && h1.x * cm.ex + h1.y * cm.ey + h1.z * cm.ez <
+                         lo.w - 1e-4f - 1e-5f * (fabsf(cm.ex) + fabsf(cm.ey) + fabsf(cm.ez)))
+    return false;
+  if (!box_visible(cm, vw, lo, hi)) return false;
+  const uint32_t cnt = __float_as_uint(h2.w);
+  entry = make_uint2(__float_as_uint(h2.y) | ((cnt & 0xffu) << 24),
+                     __float_as_uint(h2.z) | (((cnt >> 8) & 0xffu) << 24));
+  return true;
+}
+
 __device__ __forceinline__ int pop_item(int* ctr, int lane) {
   int i = 0;
   if (lane == 0) i = atomicAdd(ctr, 1);
@@ -573,7 +681,13 @@ __device__ __forceinline__ void raster_cta_begin(const RasterParams& P, unsigned
 // Renders environment env into its observation rows (the whole CTA of kW
 // warps).  kBoxes: the objects are oriented boxes (P.obox), drawn as cubes;
 // a separate instantiation, so the sphere objects' code stays as it is.
-template <bool kCount, int kW, bool kBoxes = false>
+// kOcc: clusters are culled by occlusion in two phases -- first the clusters
+// this environment showed in its previous image (visibility bits P.vis),
+// then the depth bound of every 8x8 tile is taken from the framebuffer and
+// the other clusters (and the objects) are drawn only when some tile they
+// touch could still show them; after the resolve the bits are rewritten from
+// the final image's tile bounds.  The image is the same bit for bit.
+template <bool kCount, int kW, bool kBoxes = false, bool kOcc = false>
 __device__ __forceinline__ void render_env(const RasterParams& P, const int env,
                                            RasterCta<kCount>& C, uint32_t phase[2], Cnt& cn) {
   int* ctr = C.ctr;
@@ -627,6 +741,14 @@ __device__ __forceinline__ void render_env(const RasterParams& P, const int env,
   vw.kt = rsqrtf(1.f + vw.tt * vw.tt);
   vw.kb = rsqrtf(1.f + vw.tb * vw.tb);
 
+  // occlusion culling: tile depth bounds after the bytes of the warps' buffers;
+  // the environment's visibility bits (one per cluster)
+  uint32_t* hiz = reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(ctr) + 128 +
+                                              kListCap * sizeof(uint2) + kW * sizeof(WarpSmem));
+  uint32_t* visw = kOcc ? P.vis + (size_t)env * P.vis_words : nullptr;
+  constexpr int kPhases = kOcc ? 2 : 1;
+#pragma unroll 1
+  for (int ph = 0; ph < kPhases; ++ph) {
   for (int base = 0; scene_ok && (base < S.n_meshlets || base == 0); base += kListCap) {
     if (tid == 0) {
       ctr[1] = 0;
@@ -636,6 +758,22 @@ __device__ __forceinline__ void render_env(const RasterParams& P, const int env,
     __syncthreads();
     // 1. the whole CTA culls the clusters of this pass into the list
     const int end = min(base + kListCap, S.n_meshlets);
+    if (kOcc) {
+      for (int m = base + tid; m < end; m += kW * 32) {
+        if (kCount && ph == 0) cn.v[kCntClustersTested]++;
+        const bool prev = (visw[m >> 5] >> (m & 31)) & 1u;
+        if (ph == 0 && !prev) continue;
+        if (ph == 1 && prev) continue;  // drawn in the first phase
+        float4 lo, hi;
+        uint2 entry;
+        if (!cluster_in_view(S, m, cm, vw, lo, hi, entry)) continue;
+        if (ph == 1 && hiz_occluded(cm, vw, lo.x, lo.y, lo.z, hi.x, hi.y, hi.z, hiz)) {
+          if (kCount) cn.v[kCntClustersOccluded]++;
+          continue;
+        }
+        list[atomicAdd(&ctr[1], 1)] = entry;
+      }
+    } else
     for (int m = base + tid; m < end; m += kW * 32) {
       if (kCount) cn.v[kCntClustersTested]++;
       const float4* hd = S.mhdr + (size_t)kMeshletHdr * m;
@@ -693,7 +831,7 @@ __device__ __forceinline__ void render_env(const RasterParams& P, const int env,
       buf ^= 1;
     }
     // 3. free objects (last pass): icosahedra scaled to each object's radius
-    if (base + kListCap >= S.n_meshlets) {
+    if (ph == kPhases - 1 && base + kListCap >= S.n_meshlets) {
       // objects, then (when rendered) the robot's 32 sphere slots, which
       // take instance slots 64.. so their colours follow the objects'
       const int n_inst = P.M + (P.robot_sph ? 32 : 0);
@@ -705,6 +843,11 @@ __device__ __forceinline__ void render_env(const RasterParams& P, const int env,
         if (!(o.w > 0.f)) continue;
         const int slot = j < P.M ? j : GX_MAX_OBJECTS + (j - P.M);
         if (!sphere_visible(cm, vw, o.x, o.y, o.z, o.w * 1.0001f + 1e-6f)) continue;
+        if (kOcc) {
+          const float r = o.w * 1.0001f + 1e-6f;
+          if (hiz_occluded(cm, vw, o.x - r, o.y - r, o.z - r, o.x + r, o.y + r, o.z + r, hiz))
+            continue;
+        }
         const uint32_t rgb = __ldg(P.obj_rgb + slot);
         int nv = P.omesh_nv, nt = P.omesh_nt;
         if (kBoxes) {
@@ -759,6 +902,18 @@ __device__ __forceinline__ void render_env(const RasterParams& P, const int env,
     }
     __syncthreads();  // the list is reused by the next pass
   }
+  if (kOcc && ph == 0) {
+    // the first phase's fragments must land before their tile bounds are read
+    __threadfence();
+    __syncthreads();
+    hiz_build<kW>(vw, hiz, tid);
+    __syncthreads();
+  }
+  }
+  if (kOcc) {  // the final image's tile bounds are gathered during the resolve
+    const int tiles = (W / kHizTile) * (H / kHizTile);
+    for (int t = tid; t < tiles; t += kW * 32) hiz[t] = 0xffffffffu;
+  }
   // the reductions must land before the resolve reads the slot
   __threadfence();
   __syncthreads();
@@ -786,6 +941,12 @@ __device__ __forceinline__ void render_env(const RasterParams& P, const int env,
         col[k] = (uint32_t)keys[k] & 0xffffffu;  // the winner's colour rides in the key
       }
     }
+    if (kOcc) {
+      const uint32_t b = min(min(key_invz_bits(keys[0], vw.tag), key_invz_bits(keys[1], vw.tag)),
+                             min(key_invz_bits(keys[2], vw.tag), key_invz_bits(keys[3], vw.tag)));
+      const int row = p / W, col0 = p - row * W;
+      atomicMin(&hiz[(row / kHizTile) * (W / kHizTile) + col0 / kHizTile], b);
+    }
     if (P.depth_fp16) {
       __half2 a = __floats2half2_rn(z[0], z[1]), b = __floats2half2_rn(z[2], z[3]);
       uint2 v;
@@ -810,6 +971,24 @@ __device__ __forceinline__ void render_env(const RasterParams& P, const int env,
     }
   }
   __syncthreads();
+  if (kOcc && scene_ok) {
+    // next image's first phase: the clusters in view that the final image's
+    // tile bounds do not rule out, one bit per cluster, a ballot per word
+    const int warp = C.warp;
+    for (int m0 = warp * 32; m0 < S.n_meshlets; m0 += kW * 32) {
+      const int m = m0 + lane;
+      bool v = false;
+      if (m < S.n_meshlets) {
+        float4 lo, hi;
+        uint2 entry;
+        v = cluster_in_view(S, m, cm, vw, lo, hi, entry) &&
+            !hiz_occluded(cm, vw, lo.x, lo.y, lo.z, hi.x, hi.y, hi.z, hiz);
+      }
+      const unsigned b = __ballot_sync(kFull, v);
+      if (lane == 0) visw[m0 >> 5] = b;
+    }
+    __syncthreads();
+  }
 }
 
 // Writes back the slot's epoch and the work counters.

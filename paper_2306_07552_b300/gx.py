@@ -40,7 +40,7 @@ NSDF_PARAMS = 57985
 NSDF_FREQ = 32
 RASTER_COUNTERS = ["clusters_tested", "clusters_drawn", "tris_seen", "tris_front", "tris_expand",
                    "expand_pixels", "tris_warp", "warp_blocks", "tris_clipped", "fragments", "wait_polls",
-                   "expand_trips", "rounds", "expand_slots"]
+                   "expand_trips", "rounds", "expand_slots", "clusters_occluded"]
 
 f32p = C.POINTER(C.c_float)
 i32p = C.POINTER(C.c_int32)
@@ -81,7 +81,7 @@ class GxConfig(C.Structure):
                 ("render_robot", C.c_int32), ("heuristics", C.c_int32),
                 ("raster_order", C.c_int32), ("env_offset", C.c_int32),
                 ("object_boxes", C.c_int32), ("raster_warps", C.c_int32),
-                ("fused_step", C.c_int32)]
+                ("occlusion_cull", C.c_int32), ("fused_step", C.c_int32)]
 
 
 OUTPUT_KEYS = ["depth", "rgb", "pose", "obj_pos", "held", "contact_mask", "contact_flags", "event",
@@ -102,7 +102,7 @@ class GxTrainParams(C.Structure):
 class GxTuneResult(C.Structure):
     _fields_ = [("small_tri_px", C.c_int32), ("order_costliest_first", C.c_int32),
                 ("raster_ctas", C.c_int32), ("ms_per_step", C.c_float),
-                ("raster_warps", C.c_int32)]
+                ("raster_warps", C.c_int32), ("occlusion_cull", C.c_int32)]
 
 
 class GxError(RuntimeError):
@@ -339,7 +339,7 @@ class Sim:
                  seed=1, env_scene=None, small_tri_px=0, use_graph=False,
                  profile=0, sdf_mode=0, sdf_margin=0.02, heuristics=0, render_robot=False,
                  broadphase=False, raster_order=0, env_offset=0, object_boxes=False,
-                 fused_step=False, raster_warps=0):
+                 fused_step=False, raster_warps=0, occlusion_cull=False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("gx needs a CUDA device; there is no CPU fallback")
@@ -367,6 +367,7 @@ class Sim:
         cfg.object_boxes = int(object_boxes)
         cfg.fused_step = int(fused_step)
         cfg.raster_warps = int(raster_warps)
+        cfg.occlusion_cull = int(occlusion_cull)
         self.object_boxes = bool(object_boxes)
         self.robot_c = robot_struct(robot)
         self.handle = C.c_void_p()
@@ -471,6 +472,7 @@ class Sim:
                                  self._stream(stream)), self.handle)
         return {"small_tri_px": r.small_tri_px, "order_costliest_first": r.order_costliest_first,
                 "raster_ctas": r.raster_ctas, "raster_warps": r.raster_warps,
+                "occlusion_cull": r.occlusion_cull,
                 "ms_per_step": r.ms_per_step}
 
     def nsdf_counters(self):
