@@ -30,13 +30,13 @@ def apartments():
     ss.close()
 
 
-def _run_pair(gx, ss, n, steps, seed, a_kw, b_kw, **kw):
+def _run_pair(gx, ss, n, steps, act_seed, a_kw, b_kw, **kw):
     a = gx.Sim(ss, ROBOT, n, **kw, **a_kw)
     b = gx.Sim(ss, ROBOT, n, **kw, **b_kw)
     a.reset()
     b.reset()
-    acts = I.make_actions(steps, n, "gauss0.5", seed=seed)
-    rng = np.random.default_rng(seed)
+    acts = I.make_actions(steps, n, "gauss0.5", seed=act_seed)
+    rng = np.random.default_rng(act_seed)
     x = torch.empty((n, 11), dtype=torch.float32, device="cuda")
     m = torch.empty((n,), dtype=torch.uint8, device="cuda")
     stream = torch.cuda.Stream()
