@@ -80,10 +80,12 @@ __device__ __forceinline__ float box_sphere(float4 b, int k, float l[3]) {
   return s;
 }
 
-__device__ __forceinline__ float4 lane_select(const float v[], int n, int lane) {
+// v[lane] from a register array, by selects (no dynamic register indexing).
+__device__ __forceinline__ float lane_select(const float v[], int n, int lane) {
   float x = v[0];
+#pragma unroll
   for (int k = 1; k < n; ++k) x = lane == k ? v[k] : x;
-  return make_float4(x, 0.f, 0.f, 0.f);
+  return x;
 }
 
 __global__ void __launch_bounds__(32 * kBoxEnvsPerBlock) physics_box_kernel(const PhysicsParams P) {
@@ -316,7 +318,7 @@ __global__ void __launch_bounds__(32 * kBoxEnvsPerBlock) physics_box_kernel(cons
     P.st.coff[(size_t)lane * n + env] = coff[lane];
     P.st.ppre[(size_t)lane * n + env] = ppre[lane];
   }
-  if (lane < 9) P.st.roff[(size_t)lane * n + env] = lane_select(roff, 9, lane).x;
+  if (lane < 9) P.st.roff[(size_t)lane * n + env] = lane_select(roff, 9, lane);
   for (int j = lane; j < M; j += 32) {
     P.st.obj[(size_t)env * M + j] = so[j];
     P.st.obox[(size_t)env * M + j] = sb[j];
@@ -325,11 +327,11 @@ __global__ void __launch_bounds__(32 * kBoxEnvsPerBlock) physics_box_kernel(cons
   // (a9) camera for the rasteriser
   float cam[12];
   camera(rb, ax, az, ayaw, cam);
-  if (lane < 12) P.cam[(size_t)env * 12 + lane] = lane_select(cam, 12, lane).x;
+  if (lane < 12) P.cam[(size_t)env * 12 + lane] = lane_select(cam, 12, lane);
   // (a11) observations other than images
   if (P.out.pose && lane < 16) {
     float v = 0.f;
-    if (lane < 7) v = lane_select(aq, 7, lane).x;
+    if (lane < 7) v = lane_select(aq, 7, lane);
     else if (lane == 7) v = nheld >= 0 ? 1.f : 0.f;
     else if (lane == 8) v = ax;
     else if (lane == 9) v = az;
@@ -516,11 +518,11 @@ __global__ void __launch_bounds__(32 * kBoxEnvsPerBlock) reset_box_kernel(const 
         task[13] = sqrtf(dx * dx + dy * dy + dz * dz);
         task[14] = sqrtf(gx * gx + gy * gy + gz * gz);
       }
-      if (lane < 16) P.st.task[(size_t)env * 16 + lane] = lane_select(task, 16, lane).x;
+      if (lane < 16) P.st.task[(size_t)env * 16 + lane] = lane_select(task, 16, lane);
     }
     float cam[12];
     camera(rb, bx, bz, byaw, cam);
-    if (lane < 12) P.cam[(size_t)env * 12 + lane] = lane_select(cam, 12, lane).x;
+    if (lane < 12) P.cam[(size_t)env * 12 + lane] = lane_select(cam, 12, lane);
     __syncwarp();
   }
 }
