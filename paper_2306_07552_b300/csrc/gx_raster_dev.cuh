@@ -19,6 +19,7 @@ constexpr int kWarps = kThreads / 32;
 constexpr long kWaitLimit = 1L << 22;  // bounded waits
 constexpr int kListCap = 2048;          // clusters culled per pass
 constexpr int kSpan = 4;                // adjacent pixels of a row per expansion slot
+constexpr float kClassPx = 64.f;        // screen radius (pixels) of the costliest cluster class
 
 // The box objects' instance mesh: the unit cube's twelve triangles (corner k
 // has the signs of bits 0/1/2 of k on x/y/z), counter-clockwise seen from
@@ -599,14 +600,28 @@ __device__ __forceinline__ void hiz_build(const View& vw, uint32_t* hiz, int tid
   }
 }
 
+// Cost class of a visible cluster by the screen radius of its bounding
+// sphere (h0: centre, radius): 0 above kClassPx pixels or reaching behind
+// the eye, 1 above half that, 2 above a quarter, else 3.  The culled list is
+// handed out class by class, costliest first, so that an environment's last
+// items are cheap and the warps' wait for one another before the resolve is
+// short.
+__device__ __forceinline__ uint32_t cluster_class(const Cam& cm, float4 h0) {
+  const float zc = cm.fx * (h0.x - cm.ex) + cm.fy * (h0.y - cm.ey) + cm.fz * (h0.z - cm.ez);
+  const float rf = h0.w * cm.f;
+  return rf > kClassPx * zc ? 0u : rf > 0.5f * kClassPx * zc ? 1u : rf > 0.25f * kClassPx * zc ? 2u : 3u;
+}
+
 // The frustum, normal-cone and plane tests of cluster m (as the cull pass
-// makes them); its bounding box corners in lo, hi when it passes.
+// makes them); its bounding box corners in lo, hi and its cost class when it
+// passes.
 __device__ __forceinline__ bool cluster_in_view(const DScene& S, int m, const Cam& cm,
                                                 const View& vw, float4& lo, float4& hi,
-                                                uint2& entry) {
+                                                uint2& entry, uint32_t& cls) {
   const float4* hd = S.mhdr + (size_t)kMeshletHdr * m;
   const float4 h0 = __ldg(hd);
   if (!sphere_visible(cm, vw, h0.x, h0.y, h0.z, h0.w)) return false;
+  cls = cluster_class(cm, h0);
   const float4 h1 = __ldg(hd + 1), h2 = __ldg(hd + 2);
   lo = __ldg(hd + 3);
   hi = __ldg(hd + 4);
@@ -640,7 +655,8 @@ __device__ __forceinline__ int pop_item(int* ctr, int lane) {
 // of their own beside it, so that the rest stays in registers.)
 template <bool kCount>
 struct RasterCta {
-  int* ctr;         // [0] environment, [1] clusters listed, [2] handed out, [3] objects handed out
+  int* ctr;         // [0] environment, [2] clusters handed out, [3] objects handed out,
+                    // [4..7] clusters listed per cost class, [8..11] their list fill
   uint2* list;
   WarpSmem* ws;
   int tid, lane, warp;
@@ -750,31 +766,33 @@ __device__ __forceinline__ void render_env(const RasterParams& P, const int env,
 #pragma unroll 1
   for (int ph = 0; ph < kPhases; ++ph) {
   for (int base = 0; scene_ok && (base < S.n_meshlets || base == 0); base += kListCap) {
-    if (tid == 0) {
-      ctr[1] = 0;
-      ctr[2] = 0;
-      ctr[3] = 0;
-    }
+    if (tid >= 1 && tid < 12) ctr[tid] = 0;
     __syncthreads();
-    // 1. the whole CTA culls the clusters of this pass into the list
+    // 1. the whole CTA culls the clusters of this pass; a visible one gets a
+    //    3-bit code per loop trip (1 + its cost class) and is counted in its class
     const int end = min(base + kListCap, S.n_meshlets);
+    static_assert((kListCap + kW * 32 - 1) / (kW * 32) <= 10, "codes of one pass in 30 bits");
+    uint32_t codes = 0;
+    int trip = 0;
     if (kOcc) {
-      for (int m = base + tid; m < end; m += kW * 32) {
+      for (int m = base + tid; m < end; m += kW * 32, ++trip) {
         if (kCount && ph == 0) cn.v[kCntClustersTested]++;
         const bool prev = (visw[m >> 5] >> (m & 31)) & 1u;
         if (ph == 0 && !prev) continue;
         if (ph == 1 && prev) continue;  // drawn in the first phase
         float4 lo, hi;
         uint2 entry;
-        if (!cluster_in_view(S, m, cm, vw, lo, hi, entry)) continue;
+        uint32_t cls;
+        if (!cluster_in_view(S, m, cm, vw, lo, hi, entry, cls)) continue;
         if (ph == 1 && hiz_occluded(cm, vw, lo.x, lo.y, lo.z, hi.x, hi.y, hi.z, hiz)) {
           if (kCount) cn.v[kCntClustersOccluded]++;
           continue;
         }
-        list[atomicAdd(&ctr[1], 1)] = entry;
+        codes |= (1u + cls) << (3 * trip);
+        atomicAdd(&ctr[4 + cls], 1);
       }
     } else
-    for (int m = base + tid; m < end; m += kW * 32) {
+    for (int m = base + tid; m < end; m += kW * 32, ++trip) {
       if (kCount) cn.v[kCntClustersTested]++;
       const float4* hd = S.mhdr + (size_t)kMeshletHdr * m;
       const float4 h0 = __ldg(hd);
@@ -798,16 +816,28 @@ __device__ __forceinline__ void render_env(const RasterParams& P, const int env,
           vis = false;
         if (vis) vis = box_visible(cm, vw, h3, h4);
         if (vis) {
-          const uint32_t cnt = __float_as_uint(h2.w);
-          list[atomicAdd(&ctr[1], 1)] =
-              make_uint2(__float_as_uint(h2.y) | ((cnt & 0xffu) << 24),
-                         __float_as_uint(h2.z) | (((cnt >> 8) & 0xffu) << 24));
+          const uint32_t cls = cluster_class(cm, h0);
+          codes |= (1u + cls) << (3 * trip);
+          atomicAdd(&ctr[4 + cls], 1);
         }
       }
     }
     __syncthreads();
-    const int count = ctr[1];
-    // 2. warps take one cluster at a time; the next streams in meanwhile
+    // 2. the list in class order (a counting sort): each thread places the
+    //    entries of its visible clusters, read again from their headers
+    for (int m = base + tid, t = 0; (codes >> (3 * t)) != 0u; m += kW * 32, ++t) {
+      const uint32_t code = (codes >> (3 * t)) & 7u;
+      if (code == 0u) continue;
+      const int at = (code > 1u ? ctr[4] : 0) + (code > 2u ? ctr[5] : 0) +
+                     (code > 3u ? ctr[6] : 0) + atomicAdd(&ctr[7 + code], 1);
+      const float4 h2 = __ldg(S.mhdr + (size_t)kMeshletHdr * m + 2);
+      const uint32_t cnt = __float_as_uint(h2.w);
+      list[at] = make_uint2(__float_as_uint(h2.y) | ((cnt & 0xffu) << 24),
+                            __float_as_uint(h2.z) | (((cnt >> 8) & 0xffu) << 24));
+    }
+    __syncthreads();
+    const int count = ctr[4] + ctr[5] + ctr[6] + ctr[7];
+    // 3. warps take one cluster at a time; the next streams in meanwhile
     int cur = dead ? count : pop_item(&ctr[2], lane);
     int buf = 0;
     if (cur < count && lane == 0) issue_cluster(ws, 0, S, list[cur]);
@@ -830,7 +860,7 @@ __device__ __forceinline__ void render_env(const RasterParams& P, const int env,
       cur = nxt;
       buf ^= 1;
     }
-    // 3. free objects (last pass): icosahedra scaled to each object's radius
+    // 4. free objects (last pass): icosahedra scaled to each object's radius
     if (ph == kPhases - 1 && base + kListCap >= S.n_meshlets) {
       // objects, then (when rendered) the robot's 32 sphere slots, which
       // take instance slots 64.. so their colours follow the objects'
@@ -981,7 +1011,8 @@ __device__ __forceinline__ void render_env(const RasterParams& P, const int env,
       if (m < S.n_meshlets) {
         float4 lo, hi;
         uint2 entry;
-        v = cluster_in_view(S, m, cm, vw, lo, hi, entry) &&
+        uint32_t cls;
+        v = cluster_in_view(S, m, cm, vw, lo, hi, entry, cls) &&
             !hiz_occluded(cm, vw, lo.x, lo.y, lo.z, hi.x, hi.y, hi.z, hiz);
       }
       const unsigned b = __ballot_sync(kFull, v);
