@@ -11,10 +11,11 @@
 //             Each tile's operands h0..h3 and delta_1..4 go to global memory
 //             as BF16 images in the swizzled layout the tensor cores read.
 //   wgrad     contracts over the batch: dW_l = delta_l^T . h_{l-1} and
-//             db_l = delta_l^T . 1 for the four hidden layers, all eight
-//             accumulators resident in tensor memory (512 columns) while a
-//             3-stage bulk-copy ring streams the tiles in; one partial sum per
-//             CTA.
+//             db_l = delta_l^T . 1 for the four hidden layers; the CTAs form
+//             one group per layer, each CTA accumulating its layer over a
+//             range of tiles (both accumulators resident in tensor memory)
+//             while a 3-stage bulk-copy ring streams the tiles in; one partial
+//             sum of its layer per CTA.
 //   adam      sums the partials in a fixed order, updates the FP32 master
 //             parameters and rewrites the BF16 weight images the other
 //             kernels read.
@@ -379,16 +380,32 @@ struct WgradSmem {
   unsigned char ones[16 * kTile * 2]; // BF16 ones, 16 rows x 128 samples (K-major)
   unsigned long long full[3], empty[3], done;
   uint32_t tmem_slot;
-  uint32_t touched;  // layers this CTA accumulated (bit l)
 };
 constexpr int kStages = 3;
-// tensor-memory columns of dW_l (l = 0: 64 columns, else 128) and db_l (16 each)
-__host__ __device__ constexpr int col_w(int l) { return l == 0 ? 384 : (l - 1) * 128; }
-__host__ __device__ constexpr int col_b(int l) { return 448 + 16 * l; }
+// tensor-memory columns of a CTA's dW_l (64 or 128 columns) and db_l (16)
+constexpr int kColW = 0, kColB = 128, kWgradCols = 256;
+
+// The weight-gradient CTAs in four groups, one per hidden layer: CTAs
+// [first[l], first[l + 1]) accumulate layer l, the tiles split evenly over
+// them.  Group sizes follow the bytes an item reads: 48 KB for the first
+// layer (64 features), 64 KB for the others.  Needs at least four CTAs.
+struct LayerGroups {
+  int first[5];
+};
+
+LayerGroups layer_groups(int ctas) {
+  LayerGroups g;
+  const int n0 = (ctas * 3 + 7) / 15 > 0 ? (ctas * 3 + 7) / 15 : 1;
+  const int rest = ctas - n0;
+  g.first[0] = 0;
+  g.first[1] = n0;
+  for (int l = 1; l < 4; ++l) g.first[l + 1] = g.first[l] + rest / 3 + (rest % 3 >= l ? 1 : 0);
+  return g;
+}
 
 __global__ void __launch_bounds__(kTrainThreads, 1)
     nsdf_wgrad_kernel(const unsigned char* __restrict__ act, int tiles, float* __restrict__ part,
-                      unsigned* err) {
+                      unsigned* err, const LayerGroups lg) {
   extern __shared__ unsigned char smem_raw[];
   WgradSmem& sm = *reinterpret_cast<WgradSmem*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -405,22 +422,22 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
   for (int i = tid; i < (int)sizeof(sm.ones) / 4; i += blockDim.x)
     reinterpret_cast<uint32_t*>(sm.ones)[i] = 0x3F803F80u;  // BF16 1.0 pairs
   fence_proxy_async();
-  if (warp == 0) tmem_alloc(&sm.tmem_slot, 512);
+  if (warp == 0) tmem_alloc(&sm.tmem_slot, kWgradCols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = sm.tmem_slot;
-  // items (tile, layer) split evenly over the CTAs
-  const int g0 = (int)((long long)blockIdx.x * tiles * 4 / gridDim.x);
-  const int g1 = (int)((long long)(blockIdx.x + 1) * tiles * 4 / gridDim.x);
-  const int items = g1 - g0;
+  // this CTA's layer and its range of tiles
+  int l = 0;
+  while (l < 3 && (int)blockIdx.x >= lg.first[l + 1]) ++l;
+  const int r = (int)blockIdx.x - lg.first[l], nl = lg.first[l + 1] - lg.first[l];
+  const int t0 = (int)((long long)r * tiles / nl);
+  const int items = (int)((long long)(r + 1) * tiles / nl) - t0;
   bool ok = true;
   if (tid == 0) {
     bool pending[kStages] = {false, false, false};
-    uint32_t touched = 0u;
     auto load = [&](int k, int st) {
-      const int tile = (g0 + k) / 4, l = (g0 + k) % 4;
-      const unsigned char* base = act + (size_t)tile * kActTile;
+      const unsigned char* base = act + (size_t)(t0 + k) * kActTile;
       const int hb = l == 0 ? kImgH0 : kImgH;
       mbar_expect_tx(&sm.full[st], kImgH + hb);
       bulk_g2s(sm.stage[st], base + act_d(l), kImgH, &sm.full[st]);
@@ -438,18 +455,15 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
       }
       pending[st] = false;
       tc_fence_after();
-      const int l = (g0 + k) % 4;
-      const bool first = !((touched >> l) & 1u);
-      touched |= 1u << l;
       const uint32_t dimg = smem_u32(sm.stage[st]), himg = dimg + kImgH;
       const uint32_t id_w = idesc_bf16(kTile, in_dim(l), true, true);
       const uint32_t id_b = idesc_bf16(kTile, 16, true, false);
 #pragma unroll
       for (int ks = 0; ks < 8; ++ks) {
-        const uint32_t acc = (first && ks == 0) ? 0u : 1u;
-        mma_bf16(tmem + col_w(l), desc_sw128(dimg + ks * 2048, kMnLbo),
+        const uint32_t acc = (k == 0 && ks == 0) ? 0u : 1u;
+        mma_bf16(tmem + kColW, desc_sw128(dimg + ks * 2048, kMnLbo),
                  desc_sw128(himg + ks * 2048, kMnLbo), id_w, acc);
-        mma_bf16(tmem + col_b(l), desc_sw128(dimg + ks * 2048, kMnLbo),
+        mma_bf16(tmem + kColB, desc_sw128(dimg + ks * 2048, kMnLbo),
                  desc_sw128(ones + (ks >> 2) * 16 * 128 + (ks & 3) * 32), id_b, acc);
       }
       mma_commit(&sm.empty[st]);
@@ -464,7 +478,6 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
       }
     }
     mma_commit(&sm.done);
-    sm.touched = touched;
     // copies still in flight after a failure: give each one bounded wait
     for (int s = 0; s < kStages; ++s)
       if (pending[s]) mbar_wait(&sm.full[s], 0), mbar_wait(&sm.full[s], 1);
@@ -473,38 +486,35 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
   ok = __syncthreads_and(ok && done);
   tc_fence_after();
   if (ok) {
+    // this CTA's partial of its layer, in the flat parameter layout of its row
     const int o = q * 32 + lane;  // output unit of this lane
     float* pc = part + (size_t)blockIdx.x * kPartStride;
-    const uint32_t touched = sm.touched;
+    const int half = in_dim(l) / 2;
+    const bool has = items > 0;  // else the partial is zero
+    for (int c = 0; c < half; c += 32) {
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + kColW + hf * half + c, v);
 #pragma unroll
-    for (int l = 0; l < 4; ++l) {
-      const int half = in_dim(l) / 2;
-      const bool has = (touched >> l) & 1u;  // else this CTA's partial is zero
-      for (int c = 0; c < half; c += 32) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + col_w(l) + hf * half + c, v);
+      for (int u = 0; u < 32; ++u) v[u] = has ? v[u] : 0.f;
+      float4* dst = reinterpret_cast<float4*>(pc + off_w(l) + (size_t)o * in_dim(l) + hf * half + c);
 #pragma unroll
-        for (int u = 0; u < 32; ++u) v[u] = has ? v[u] : 0.f;
-        float4* dst = reinterpret_cast<float4*>(pc + off_w(l) + (size_t)o * in_dim(l) + hf * half + c);
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-          dst[u] = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
-      }
-      const float b = tmem_ld1(tmem + ((uint32_t)(q * 32) << 16) + col_b(l));
-      if (hf == 0) pc[off_b(l) + o] = has ? b : 0.f;
+      for (int u = 0; u < 8; ++u)
+        dst[u] = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
     }
+    const float b = tmem_ld1(tmem + ((uint32_t)(q * 32) << 16) + kColB);
+    if (hf == 0) pc[off_b(l) + o] = has ? b : 0.f;
   } else if (tid == 0 && err) {
     atomicOr(err, kErrWaitTimeout);
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, 512);
+  if (warp == 0) tmem_dealloc(tmem, kWgradCols);
 }
 
 // --------------------------------------------------------------- Adam
 struct AdamParams {
-  const float* part;   // [n_part][kPartStride], hidden layers
-  int n_part;
+  const float* part;   // [ctas][kPartStride], hidden layers: row c holds c's layer only
+  LayerGroups groups;  // the rows of each layer
   const float* part5;  // [n_part5][kPart5], output row and loss
   int n_part5;
   float inv_n;
@@ -522,6 +532,9 @@ struct AdamParams {
 // in order and applies Adam; the order is fixed, so the result is deterministic.
 constexpr int kAdamParamsPerBlock = 32;
 constexpr int kAdamWarps = 8;
+static_assert(off_w(1) % kAdamParamsPerBlock == 0 && off_w(2) % kAdamParamsPerBlock == 0 &&
+                  off_w(3) % kAdamParamsPerBlock == 0 && kOffW5 % kAdamParamsPerBlock == 0,
+              "a block of parameters lies in one layer");
 
 __global__ void __launch_bounds__(32 * kAdamWarps) nsdf_adam_kernel(const AdamParams p) {
   __shared__ float sums[kAdamWarps][kAdamParamsPerBlock];
@@ -535,8 +548,12 @@ __global__ void __launch_bounds__(32 * kAdamWarps) nsdf_adam_kernel(const AdamPa
   // unrolled so that several rows' loads are in flight before their sums
   float part = 0.f;
   if (i < kOffW5) {
+    // the layer of this block's 32 parameters (layer offsets are multiples of 32)
+    int l = 3;
+    while (l > 0 && blockIdx.x * kAdamParamsPerBlock < off_w(l)) --l;
 #pragma unroll 8
-    for (int c = warp; c < p.n_part; c += kAdamWarps) part += p.part[(size_t)c * kPartStride + i];
+    for (int c = p.groups.first[l] + warp; c < p.groups.first[l + 1]; c += kAdamWarps)
+      part += p.part[(size_t)c * kPartStride + i];
   } else if (i < kNsdfParams) {
 #pragma unroll 8
     for (int c = warp; c < p.n_part5; c += kAdamWarps)
@@ -613,7 +630,7 @@ struct Work {
     const int tiles = (batch + kTile - 1) / kTile;
     const int sms = sm_count();
     g1 = tiles < sms ? tiles : sms;
-    g2 = g1;
+    g2 = 4 * tiles < sms ? 4 * tiles : sms;  // at least one CTA per layer
     void* a = nullptr;
     cudaError_t e;
     if ((e = cudaMalloc(&a, (size_t)tiles * kActTile)) != cudaSuccess) return e;
@@ -655,9 +672,11 @@ cudaError_t grad_and_update(unsigned char* blob, const float* pts, const float* 
   fp.err = w.err;
   const int tiles = (n + kTile - 1) / kTile;
   nsdf_fwd_bwd_kernel<<<w.g1, kTrainThreads, fwd_smem_bytes(), s>>>(fp);
-  nsdf_wgrad_kernel<<<w.g2, kTrainThreads, wgrad_smem_bytes(), s>>>(w.act, tiles, w.part, w.err);
+  const LayerGroups lg = layer_groups(w.g2);
+  nsdf_wgrad_kernel<<<w.g2, kTrainThreads, wgrad_smem_bytes(), s>>>(w.act, tiles, w.part, w.err,
+                                                                     lg);
   ap.part = w.part;
-  ap.n_part = w.g2;
+  ap.groups = lg;
   ap.part5 = w.part5;
   ap.n_part5 = w.g1 * 4;
   ap.inv_n = 1.f / (float)n;
