@@ -30,8 +30,10 @@ namespace gx {
 namespace {
 
 constexpr int kTile = 128;            // rows (queries) per MMA tile
-constexpr int kGroups = 2;            // warpgroups per CTA, each with a tile in flight
+constexpr int kGroups = 3;            // warpgroups per CTA, each with a tile in flight
 constexpr int kQueryThreads = 128 * kGroups;
+constexpr int kQueryTmemCols = kGroups <= 2 ? 256 : 512;  // a power of two >= 128 per group
+static_assert(kGroups >= 1 && kGroups <= 4, "tensor-memory columns");
 
 // Issues the K steps of one layer: D = A . W^T over K = 64 * kblocks.
 __device__ __forceinline__ void layer_mma(uint32_t tmem, uint32_t a_base, uint32_t w_base,
@@ -46,9 +48,9 @@ __device__ __forceinline__ void layer_mma(uint32_t tmem, uint32_t a_base, uint32
     }
 }
 
-// Two warpgroups share the weights; each owns an activation operand, 128
+// The warpgroups share the weights; each owns an activation operand, 128
 // tensor-memory columns and an mbarrier, and runs its own tiles, so one
-// group's products overlap the other's epilogue.
+// group's products overlap the others' epilogues.
 struct QuerySmem {
   unsigned char w[kNsdfImgBytes];           // W1 | W2 | W3 | W4 images
   unsigned char a[kGroups][kTile * 128 * 2];  // activation operand per group (K <= 128)
@@ -167,7 +169,7 @@ __device__ void query_setup(QuerySmem& sm) {
     for (int g = 0; g < kGroups; ++g) mbar_init(&sm.bar_mma[g], 1);
     fence_mbar_init();
   }
-  if (threadIdx.x < 32) tmem_alloc(&sm.tmem_slot, kGroups * kNsdfWidth);
+  if (threadIdx.x < 32) tmem_alloc(&sm.tmem_slot, kQueryTmemCols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -177,7 +179,7 @@ __device__ void query_teardown(QuerySmem& sm, bool ok, unsigned* err) {
   if (!ok && threadIdx.x == 0 && err) atomicOr(err, kErrWaitTimeout);
   tc_fence_before();
   __syncthreads();
-  if (threadIdx.x < 32) tmem_dealloc(sm.tmem_slot, kGroups * kNsdfWidth);
+  if (threadIdx.x < 32) tmem_dealloc(sm.tmem_slot, kQueryTmemCols);
 }
 
 __device__ __forceinline__ QuerySmem& query_smem(unsigned char* raw) {
@@ -214,8 +216,8 @@ __global__ void __launch_bounds__(kQueryThreads, 1)
 
 // The step's queries: each CTA takes a contiguous run of tiles (grouped by
 // scene, so it reloads weights only where the scene changes); a tile's 128
-// rows are 4 environments x 32 sphere slots.  In each round the two
-// warpgroups take up to two consecutive tiles of the loaded scene.
+// rows are 4 environments x 32 sphere slots.  In each round the warpgroups
+// take up to kGroups consecutive tiles of the loaded scene, one each.
 __global__ void __launch_bounds__(kQueryThreads, 1) nsdf_step_kernel(const NsdfStepParams p) {
   extern __shared__ unsigned char smem_raw[];
   QuerySmem& sm = query_smem(smem_raw);
@@ -252,7 +254,9 @@ __global__ void __launch_bounds__(kQueryThreads, 1) nsdf_step_kernel(const NsdfS
       if (!ok) break;
       loaded = first.x;
     }
-    const int in_round = (t + 1 < t1 && p.tiles[t + 1].x == first.x) ? 2 : 1;
+    int in_round = 1;  // consecutive tiles of the loaded scene, one per group
+    while (in_round < kGroups && t + in_round < t1 && p.tiles[t + in_round].x == first.x)
+      ++in_round;
     const int env = next_env;  // group g's query in this round's tile t + g
     const float4 q = next_q;
     fetch(t + in_round + g, next_env, next_q);

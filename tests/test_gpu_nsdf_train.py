@@ -78,7 +78,7 @@ def test_samples_match_oracle(setup):
         assert np.all(np.abs(D[acc & clean]) < 0.1)
 
 
-@pytest.mark.parametrize("n", [1000, 20000])
+@pytest.mark.parametrize("n", [300, 1000, 20000])
 def test_gradient_matches_oracle(setup, n):
     gx, scene, ss, orc, B, P0 = setup
     ss.nsdf_set_weights(0, B, P0)
