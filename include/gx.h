@@ -224,6 +224,20 @@ typedef struct {
                               word).  Not with sdf_mode 1 or object_boxes
                               (GX_EINVAL); gx_phase_times then reports the
                               whole launch as ms[1].                          */
+  int32_t static_store;    /* where the distance grid's node values come from
+                              for every static test of this context (the step,
+                              the neural SDF's fallback, release, reset, the
+                              sliding heuristic): 0 the dense FP32 grid built
+                              with the scene set; 1 the box store -- each node
+                              recomputed in FP32 from the scene's solid boxes
+                              as the minimum over a short per-cell list of
+                              candidate boxes (cells of 16 node intervals per
+                              axis, chosen so the list holds the nearest box of
+                              every node of the cell), within 1e-5 m of the
+                              FP64 node value for coordinates up to 20 m;
+                              about 0.1% of the dense grid's bytes, so a scene
+                              set created without dense grids
+                              (gx_scene_set_create_ex) can serve it           */
 } gx_config;
 
 /* Outputs of one step, device memory owned by the caller (e.g. torch
@@ -263,6 +277,38 @@ typedef struct {
 gx_status gx_scene_set_create(const gx_scene_desc* scenes, int32_t n_scenes,
                               const gx_object_mesh* mesh, gx_scene_set** out);
 gx_status gx_scene_set_destroy(gx_scene_set* set);
+
+/* Which static structures gx_scene_set_create_ex builds (gx_scene_set_create
+ * builds all).  The box store (gx_config.static_store 1) is always built; it
+ * is the distance grid's definition evaluated on demand, so a set without
+ * dense grids keeps every static test of the step, and a set without column
+ * grids only loses sdf_mode 2.  Training samples (gx_nsdf_samples,
+ * gx_nsdf_train) read the dense grid when the set has it, else the box
+ * store. */
+typedef struct {
+  int32_t dense_grid;      /* 1: the dense FP32 grid [nz][ny][nx] per scene   */
+  int32_t column_grid;     /* 1: the column grid per scene (sdf_mode 2)       */
+} gx_scene_options;
+/* Errors as gx_scene_set_create; GX_EINVAL for options other than 0 or 1. */
+gx_status gx_scene_set_create_ex(const gx_scene_desc* scenes, int32_t n_scenes,
+                                 const gx_object_mesh* mesh, const gx_scene_options* options,
+                                 gx_scene_set** out);
+
+/* Device bytes of one scene's structures: bytes[0] dense distance grid (0
+ * when not built), [1] box store (boxes and candidate lists), [2] column grid
+ * (0 when not built), [3] render clusters (headers, vertices, triangles,
+ * colours), [4] neural-SDF weights (0 before gx_nsdf_set_weights), [5]
+ * neural-SDF FP32 master copy kept for training (0 when none). */
+gx_status gx_scene_bytes(const gx_scene_set* set, int32_t scene, uint64_t bytes[6]);
+
+/* Static distance at n points (device pts [n][3]) into dist (device [n]):
+ * the trilinear interpolation of the scene's distance grid whose nodes come
+ * from `store` (0 dense grid, 1 box store; see gx_config.static_store); NaN
+ * where a point lies outside the lattice box (contact for the step).
+ * Asynchronous on `stream`.  GX_EINVAL for store 0 on a set without dense
+ * grids. */
+gx_status gx_static_distance(const gx_scene_set* set, int32_t scene, int32_t store,
+                             const float* pts, int32_t n, float* dist, void* stream);
 
 /* Allocates the structure-of-arrays state for cfg->n_envs environments on
  * the current device, borrowing `set`.  All environments start unplaced:

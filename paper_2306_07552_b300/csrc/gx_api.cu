@@ -25,6 +25,7 @@ struct DevBuf {
 
 struct gx_ctx {
   const gx_scene_set* set = nullptr;
+  const DScene* scenes = nullptr;      // the set's scenes with this context's static store
   gx_config cfg{};
   int n = 0, M = 0, big_px = 0, n_slots = 0;
   int raster_ctas = 0;                 // CTAs launched (<= n_slots), set by the autotuner
@@ -188,7 +189,7 @@ PhysicsParams physics_params(gx_ctx* c, const float* actions, const gx_outputs& 
   PhysicsParams pp{};
   pp.n = c->n;
   pp.M = c->M;
-  pp.scenes = c->set->d_scenes;
+  pp.scenes = c->scenes;
   pp.env_scene = c->d_env_scene;
   pp.robot = c->d_robot;
   pp.actions = actions;
@@ -205,6 +206,7 @@ PhysicsParams physics_params(gx_ctx* c, const float* actions, const gx_outputs& 
   pp.seed = c->cfg.seed;
   pp.env_offset = c->cfg.env_offset;
   pp.column = c->cfg.sdf_mode == 2;
+  pp.store = c->cfg.static_store;
   return pp;
 }
 
@@ -221,7 +223,7 @@ RasterParams raster_params(gx_ctx* c, const gx_outputs& out) {
   rp.n_slots = c->raster_ctas;
   rp.order = c->order_mode ? c->d_order : nullptr;
   rp.work = c->d_raster_work;
-  rp.scenes = c->set->d_scenes;
+  rp.scenes = c->scenes;
   rp.n_scenes = c->set->n;
   rp.env_scene = c->d_env_scene;
   rp.cam = c->d_cam;
@@ -254,7 +256,7 @@ ResetParams reset_params(gx_ctx* x, const uint8_t* env_mask) {
   ResetParams rp{};
   rp.n = x->n;
   rp.M = x->M;
-  rp.scenes = x->set->d_scenes;
+  rp.scenes = x->scenes;
   rp.env_scene = x->d_env_scene;
   rp.robot = x->d_robot;
   rp.mask = env_mask;
@@ -267,6 +269,7 @@ ResetParams reset_params(gx_ctx* x, const uint8_t* env_mask) {
   rp.err = x->d_err;
   rp.bp = x->d_bp;
   rp.bp_cells = x->bp_cells;
+  rp.store = x->cfg.static_store;
   return rp;
 }
 
@@ -334,8 +337,20 @@ void enqueue_fused(gx_ctx* c, const uint8_t* mask, const float* actions, const g
 // ===========================================================================
 extern "C" gx_status gx_scene_set_create(const gx_scene_desc* scenes, int32_t n_scenes,
                                          const gx_object_mesh* mesh, gx_scene_set** out) {
+  gx_scene_options opt{};
+  opt.dense_grid = 1;
+  opt.column_grid = 1;
+  return gx_scene_set_create_ex(scenes, n_scenes, mesh, &opt, out);
+}
+
+extern "C" gx_status gx_scene_set_create_ex(const gx_scene_desc* scenes, int32_t n_scenes,
+                                            const gx_object_mesh* mesh,
+                                            const gx_scene_options* opt, gx_scene_set** out) {
   if (!out) return fail(nullptr, GX_EINVAL, "gx_scene_set_create: out is NULL");
   *out = nullptr;
+  if (!opt || (opt->dense_grid != 0 && opt->dense_grid != 1) ||
+      (opt->column_grid != 0 && opt->column_grid != 1))
+    return fail(nullptr, GX_EINVAL, "scene options: dense_grid and column_grid must be 0 or 1");
   if (!scenes || n_scenes < 1) return fail(nullptr, GX_EINVAL, "need at least one scene");
   if (!mesh || mesh->n_verts < 1 || mesh->n_verts > 32 || mesh->n_tris < 1 ||
       mesh->n_tris > 32 || !mesh->verts || !mesh->tris)
@@ -362,6 +377,8 @@ extern "C" gx_status gx_scene_set_create(const gx_scene_desc* scenes, int32_t n_
   gx_scene_set* s = new gx_scene_set();
   s->n = n_scenes;
   s->host.resize(n_scenes);
+  s->dense = opt->dense_grid == 1;
+  s->columns = opt->column_grid == 1;
   auto bail = [&](cudaError_t e, const char* what) {
     free_set(s);
     return fail(nullptr, e == cudaErrorMemoryAllocation ? GX_ENOMEM : GX_ECUDA, "%s: %s", what,
@@ -401,22 +418,54 @@ extern "C" gx_status gx_scene_set_create(const gx_scene_desc* scenes, int32_t n_
     ds.ny = d.grid_dims[1];
     ds.nz = d.grid_dims[2];
     for (int k = 0; k < 4; ++k) ds.spawn[k] = d.spawn[k];
+    s->render_bytes.push_back((hm.hdr.size() + hm.verts.size()) * sizeof(float4) +
+                              (hm.tris.size() + hm.rgb.size()) * sizeof(uint32_t));
     const size_t nodes = (size_t)ds.nx * ds.ny * ds.nz;
-    float* grid = nullptr;
-    if ((e = cudaMalloc(&grid, nodes * sizeof(float))) != cudaSuccess) return bail(e, "grid");
-    s->allocs.push_back(grid);
     float* dboxes = nullptr;
     if ((e = upload(s, &dboxes, d.boxes, (size_t)6 * d.n_boxes)) != cudaSuccess)
       return bail(e, "upload boxes");
-    launch_grid_build(grid, dboxes, d.n_boxes, ds.ox, ds.oy, ds.oz, ds.h, ds.nx, ds.ny, ds.nz, 0);
-    if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "grid kernel");
-    ds.grid = grid;
+    ds.grid = nullptr;
+    if (s->dense) {
+      float* grid = nullptr;
+      if ((e = cudaMalloc(&grid, nodes * sizeof(float))) != cudaSuccess) return bail(e, "grid");
+      s->allocs.push_back(grid);
+      launch_grid_build(grid, dboxes, d.n_boxes, ds.ox, ds.oy, ds.oz, ds.h, ds.nx, ds.ny, ds.nz, 0);
+      if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "grid kernel");
+      ds.grid = grid;
+    }
+    s->dense_bytes.push_back(s->dense ? nodes * sizeof(float) : 0);
+    {
+      // box store: boxes and per-cell candidate lists (the kernels pick it
+      // per context; see gx_config.static_store)
+      StoreHost sh;
+      if (!build_box_store(d, sh)) {
+        free_set(s);
+        return fail(nullptr, GX_EINVAL, "scene %d: box store too large", i);
+      }
+      if ((e = upload(s, (float4**)&ds.sbox, sh.boxes.data(), sh.boxes.size())) != cudaSuccess ||
+          (e = upload(s, (uint32_t**)&ds.sb_off, sh.off.data(), sh.off.size())) != cudaSuccess)
+        return bail(e, "upload box store");
+      if (!sh.ids.empty() &&
+          (e = upload(s, (uint16_t**)&ds.sb_ids, sh.ids.data(), sh.ids.size())) != cudaSuccess)
+        return bail(e, "upload box store");
+      ds.sbx = sh.sbx;
+      ds.sby = sh.sby;
+      ds.sbz = sh.sbz;
+      ds.store = 0;
+      s->store_bytes.push_back(sh.boxes.size() * sizeof(float4) + sh.off.size() * 4 +
+                               sh.ids.size() * 2);
+    }
     // object broad-phase lattice: the grid box with a cell of margin
     ds.bp_x0 = ds.ox - kBpCell;
     ds.bp_z0 = ds.oz - kBpCell;
     ds.bp_nx = (int)std::ceil(((ds.nx - 1) * (double)ds.h + 2 * kBpCell) / kBpCell) + 1;
     ds.bp_nz = (int)std::ceil(((ds.nz - 1) * (double)ds.h + 2 * kBpCell) / kBpCell) + 1;
-    {
+    if (!s->columns) {
+      ds.ncx = ds.ncz = 0;
+      ds.col_off = nullptr;
+      ds.col_spans = nullptr;
+      s->column_bytes.push_back(0);
+    } else {
       // column grid over the same box: count, prefix sum on the host, fill
       const double h = (double)ds.h;
       ds.ncx = (int)std::floor((ds.nx - 1) * h / kColumnSpacing + 1e-6) + 1;
@@ -482,8 +531,17 @@ extern "C" gx_status gx_scene_set_create(const gx_scene_desc* scenes, int32_t n_
     return bail(e, "colours");
   s->omesh_nv = mesh->n_verts;
   s->omesh_nt = mesh->n_tris;
-  if ((e = upload(s, &s->d_scenes, s->host.data(), s->host.size())) != cudaSuccess)
+  std::vector<DScene> boxed = s->host;
+  for (DScene& ds : boxed) ds.store = 1;
+  if ((e = upload(s, &s->d_scenes_box, boxed.data(), boxed.size())) != cudaSuccess)
     return bail(e, "scene table");
+  if (s->dense) {
+    if ((e = upload(s, &s->d_scenes, s->host.data(), s->host.size())) != cudaSuccess)
+      return bail(e, "scene table");
+  } else {
+    s->host = boxed;
+    s->d_scenes = s->d_scenes_box;
+  }
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail(e, "scene build");
   *out = s;
   return GX_OK;
@@ -550,8 +608,21 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
     return fail(nullptr, GX_EINVAL,
                 "object_boxes: the box model runs the plain step on the distance grid "
                 "(no heuristics, broad-phase, robot-body rendering or other static test)");
+  if (c.static_store < 0 || c.static_store > 1)
+    return fail(nullptr, GX_EINVAL, "static_store must be 0 or 1");
+  if (c.static_store == 1 && (c.fused_step || c.object_boxes))
+    return fail(nullptr, GX_EINVAL,
+                "static_store 1: not with fused_step or object_boxes (their kernels read the "
+                "dense grid)");
+  if (c.static_store == 0 && !set->dense)
+    return fail(nullptr, GX_EINVAL,
+                "static_store 0 needs the dense grid, which this scene set was created without");
+  if (c.sdf_mode == 2 && !set->columns)
+    return fail(nullptr, GX_EINVAL,
+                "sdf_mode 2 needs the column grid, which this scene set was created without");
   gx_ctx* x = new gx_ctx();
   x->set = set;
+  x->scenes = c.static_store ? set->d_scenes_box : set->d_scenes;
   x->cfg = c;
   x->cfg.env_scene = nullptr;
   x->n = c.n_envs;
@@ -949,7 +1020,7 @@ extern "C" gx_status gx_load_state(gx_ctx* x, const void* host, size_t bytes) {
   CK(x, cudaDeviceSynchronize());
   CK(x, cudaMemcpy(x->d_state, host, bytes, cudaMemcpyHostToDevice));
   if (x->d_bp) {  // the object broad-phase follows the loaded objects
-    launch_bp_rebuild(x->set->d_scenes, x->d_env_scene, x->st, x->n, x->M, x->d_bp, x->bp_cells, 0);
+    launch_bp_rebuild(x->scenes, x->d_env_scene, x->st, x->n, x->M, x->d_bp, x->bp_cells, 0);
     CK(x, cudaDeviceSynchronize());
   }
   return GX_OK;
@@ -1076,7 +1147,7 @@ extern "C" gx_status gx_autotune(gx_ctx* x, const float* actions, const gx_outpu
         cudaEventRecord(e1, s);
         err = cudaMemcpyAsync(x->d_state, saved, x->state_bytes, cudaMemcpyDeviceToDevice, s);
         if (err == cudaSuccess && x->d_bp) {
-          launch_bp_rebuild(x->set->d_scenes, x->d_env_scene, x->st, x->n, x->M, x->d_bp,
+          launch_bp_rebuild(x->scenes, x->d_env_scene, x->st, x->n, x->M, x->d_bp,
                             x->bp_cells, s);
           err = cudaGetLastError();
         }
@@ -1160,6 +1231,34 @@ extern "C" int32_t gx_column_spans(const gx_scene_set* set, int32_t scene, int32
           cudaSuccess)
     return -1;
   return n;
+}
+
+extern "C" gx_status gx_scene_bytes(const gx_scene_set* set, int32_t scene, uint64_t bytes[6]) {
+  if (!set || scene < 0 || scene >= set->n || !bytes)
+    return fail(nullptr, GX_EINVAL, "gx_scene_bytes: bad argument");
+  bytes[0] = set->dense_bytes[scene];
+  bytes[1] = set->store_bytes[scene];
+  bytes[2] = set->column_bytes[scene];
+  bytes[3] = set->render_bytes[scene];
+  const bool has_nsdf = scene < (int)set->nsdf.size();
+  bytes[4] = has_nsdf && set->nsdf[scene].blob ? (uint64_t)kNsdfBlobBytes : 0;
+  bytes[5] = has_nsdf && set->nsdf[scene].master ? (uint64_t)kNsdfParams * 4 : 0;
+  return GX_OK;
+}
+
+extern "C" gx_status gx_static_distance(const gx_scene_set* set, int32_t scene, int32_t store,
+                                        const float* pts, int32_t n, float* dist, void* stream) {
+  if (!set || scene < 0 || scene >= set->n || n < 0 || (n > 0 && (!pts || !dist)) ||
+      (store != 0 && store != 1))
+    return fail(nullptr, GX_EINVAL, "gx_static_distance: bad argument");
+  if (store == 0 && !set->dense)
+    return fail(nullptr, GX_EINVAL, "gx_static_distance: the scene set has no dense grids");
+  if (n == 0) return GX_OK;
+  const cudaError_t e = launch_static_distance(store ? set->d_scenes_box : set->d_scenes, scene,
+                                               pts, n, dist, (cudaStream_t)stream);
+  if (e != cudaSuccess)
+    return fail(nullptr, GX_ECUDA, "gx_static_distance: %s", cudaGetErrorString(e));
+  return GX_OK;
 }
 
 extern "C" const char* gx_last_error(const gx_ctx* x) {

@@ -2,7 +2,18 @@
 // the counter-based random generator and the distance-grid query.
 #pragma once
 
+#include <math_constants.h>
+
 #include "gx_internal.h"
+
+// Where this translation unit's kernels read distance-grid nodes: 0 the dense
+// grid only, 1 the box store only (a second instantiation of the step
+// kernels), 2 chosen per scene at run time by DScene::store (set-up and query
+// kernels).  The step kernels are compiled once per store so the dense path
+// keeps its register allocation.
+#ifndef GX_STATIC_STORE
+#define GX_STATIC_STORE 0
+#endif
 
 namespace gx {
 namespace {
@@ -25,8 +36,130 @@ __device__ __forceinline__ float unit24(uint32_t w) {
   return (float)(w >> 8) * (1.0f / 16777216.0f);
 }
 
+#if GX_STATIC_STORE == 1
+#define GX_STORE_INLINE __forceinline__
+#else
+#define GX_STORE_INLINE __noinline__
+#endif
+
+// Box store (DScene::store == 1): a node's value is recomputed from the
+// scene's solid boxes instead of read from the dense grid.  The lattice is
+// cut into cells of 16 node intervals per axis; cell c lists the boxes that
+// can be nearest anywhere in its nodes [16c, 16c + 16] (a superset of the
+// argmin, chosen on the host by exact convex bounds), so the minimum over the
+// list equals the minimum over all boxes.  FP32: within ~1e-5 m of the FP64
+// node value for coordinates up to ~20 m.
+__device__ __forceinline__ const uint16_t* store_list(const DScene& s, int i, int j, int k,
+                                                      int& n) {
+  const int ci = min(i >> kStoreShift, s.sbx - 1), cj = min(j >> kStoreShift, s.sby - 1),
+            ck = min(k >> kStoreShift, s.sbz - 1);
+  const int c = (ck * s.sby + cj) * s.sbx + ci;
+  const uint32_t a = __ldg(s.sb_off + c), b = __ldg(s.sb_off + c + 1);
+  n = (int)(b - a);
+  return s.sb_ids + a;
+}
+
+// Signed distance of the union of boxes at node (i, j, k): for each box the
+// per-axis excess q = |p - centre| - half; outside (max q > 0) the distance
+// is |max(q, 0)|, inside it is max q.  min over boxes of both parts at once:
+// out2 = min of |max(q, 0)|^2 (0 when some box holds p) and in = min(0, min
+// of max q), so the value is sqrt(out2) + in.
+__device__ GX_STORE_INLINE float store_node(const DScene& s, int i, int j, int k) {
+  int n;
+  const uint16_t* ids = store_list(s, i, j, k, n);
+  const float x = fmaf((float)i, s.h, s.ox), y = fmaf((float)j, s.h, s.oy),
+              z = fmaf((float)k, s.h, s.oz);
+  float out2 = CUDART_INF_F, in = 0.f;
+  for (int t = 0; t < n; ++t) {
+    const int b = __ldg(ids + t);
+    const float4 c = __ldg(s.sbox + 2 * b), e = __ldg(s.sbox + 2 * b + 1);
+    const float qx = fabsf(x - c.x) - e.x, qy = fabsf(y - c.y) - e.y, qz = fabsf(z - c.z) - e.z;
+    const float px = fmaxf(qx, 0.f), py = fmaxf(qy, 0.f), pz = fmaxf(qz, 0.f);
+    out2 = fminf(out2, __fadd_rn(__fadd_rn(__fmul_rn(px, px), __fmul_rn(py, py)), __fmul_rn(pz, pz)));
+    in = fminf(in, fmaxf(qx, fmaxf(qy, qz)));
+  }
+  return sqrtf(out2) + in;
+}
+
+// The eight corners of lattice cell (i, j, k) from the box store, one list.
+__device__ GX_STORE_INLINE void store_cell(const DScene& s, int i, int j, int k, float cc[8]) {
+  int n;
+  const uint16_t* ids = store_list(s, i, j, k, n);
+  const float x0 = fmaf((float)i, s.h, s.ox), x1 = fmaf((float)(i + 1), s.h, s.ox);
+  const float y0 = fmaf((float)j, s.h, s.oy), y1 = fmaf((float)(j + 1), s.h, s.oy);
+  const float z0 = fmaf((float)k, s.h, s.oz), z1 = fmaf((float)(k + 1), s.h, s.oz);
+  float out2[8], in[8];
+#pragma unroll
+  for (int v = 0; v < 8; ++v) {
+    out2[v] = CUDART_INF_F;
+    in[v] = 0.f;
+  }
+  for (int t = 0; t < n; ++t) {
+    const int b = __ldg(ids + t);
+    const float4 c = __ldg(s.sbox + 2 * b), e = __ldg(s.sbox + 2 * b + 1);
+    const float qx[2] = {fabsf(x0 - c.x) - e.x, fabsf(x1 - c.x) - e.x};
+    const float qy[2] = {fabsf(y0 - c.y) - e.y, fabsf(y1 - c.y) - e.y};
+    const float qz[2] = {fabsf(z0 - c.z) - e.z, fabsf(z1 - c.z) - e.z};
+    float sx[2], sy[2], sz[2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      const float px = fmaxf(qx[a], 0.f), py = fmaxf(qy[a], 0.f), pz = fmaxf(qz[a], 0.f);
+      sx[a] = __fmul_rn(px, px);  // no contraction: store_node rounds the same way
+      sy[a] = __fmul_rn(py, py);
+      sz[a] = __fmul_rn(pz, pz);
+    }
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {  // corner v: x offset bit 0, y bit 1, z bit 2
+      const int a = v & 1, bb = (v >> 1) & 1, cz = v >> 2;
+      out2[v] = fminf(out2[v], __fadd_rn(__fadd_rn(sx[a], sy[bb]), sz[cz]));
+      in[v] = fminf(in[v], fmaxf(qx[a], fmaxf(qy[bb], qz[cz])));
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < 8; ++v) cc[v] = sqrtf(out2[v]) + in[v];
+}
+
 __device__ __forceinline__ float gnode(const DScene& s, int i, int j, int k) {
+#if GX_STATIC_STORE == 1
+  return store_node(s, i, j, k);
+#else
+#if GX_STATIC_STORE == 2
+  if (s.store) return store_node(s, i, j, k);
+#endif
   return __ldg(s.grid + ((size_t)k * s.ny + j) * s.nx + i);
+#endif
+}
+
+// Corner values of lattice cell (i, j, k), corner v at (i + (v & 1),
+// j + (v >> 1 & 1), k + (v >> 2)), from the dense grid or the box store.
+__device__ __forceinline__ void cell_corners(const DScene& s, int i, int j, int k, float cc[8]) {
+#if GX_STATIC_STORE == 1
+  store_cell(s, i, j, k, cc);
+  return;
+#endif
+#if GX_STATIC_STORE == 2
+  if (s.store) {
+    store_cell(s, i, j, k, cc);
+    return;
+  }
+#endif
+  const float* g = s.grid + ((size_t)k * s.ny + j) * s.nx + i;
+  const size_t sy = s.nx, sz = (size_t)s.nx * s.ny;
+  cc[0] = __ldg(g);
+  cc[1] = __ldg(g + 1);
+  cc[2] = __ldg(g + sy);
+  cc[3] = __ldg(g + sy + 1);
+  cc[4] = __ldg(g + sz);
+  cc[5] = __ldg(g + sz + 1);
+  cc[6] = __ldg(g + sz + sy);
+  cc[7] = __ldg(g + sz + sy + 1);
+}
+
+__device__ __forceinline__ float lerp8(const float cc[8], float tx, float ty, float tz) {
+  const float c00 = cc[0] + tx * (cc[1] - cc[0]), c10 = cc[2] + tx * (cc[3] - cc[2]);
+  const float c01 = cc[4] + tx * (cc[5] - cc[4]), c11 = cc[6] + tx * (cc[7] - cc[6]);
+  const float c0 = c00 + ty * (c10 - c00), c1 = c01 + ty * (c11 - c01);
+  return c0 + tz * (c1 - c0);
 }
 
 // Trilinear interpolation at lattice coordinates g (0 <= g <= n - 1 per axis).
@@ -35,16 +168,9 @@ __device__ __forceinline__ float grid_lerp(const DScene& s, float gx, float gy, 
   const int j = min((int)floorf(gy), s.ny - 2);
   const int k = min((int)floorf(gz), s.nz - 2);
   const float tx = gx - i, ty = gy - j, tz = gz - k;
-  const float* g = s.grid + ((size_t)k * s.ny + j) * s.nx + i;
-  const size_t sy = s.nx, sz = (size_t)s.nx * s.ny;
-  const float c000 = __ldg(g), c100 = __ldg(g + 1);
-  const float c010 = __ldg(g + sy), c110 = __ldg(g + sy + 1);
-  const float c001 = __ldg(g + sz), c101 = __ldg(g + sz + 1);
-  const float c011 = __ldg(g + sz + sy), c111 = __ldg(g + sz + sy + 1);
-  const float c00 = c000 + tx * (c100 - c000), c10 = c010 + tx * (c110 - c010);
-  const float c01 = c001 + tx * (c101 - c001), c11 = c011 + tx * (c111 - c011);
-  const float c0 = c00 + ty * (c10 - c00), c1 = c01 + ty * (c11 - c01);
-  return c0 + tz * (c1 - c0);
+  float cc[8];
+  cell_corners(s, i, j, k, cc);
+  return lerp8(cc, tx, ty, tz);
 }
 
 // Trilinear distance and its horizontal gradient (x and z, per metre) at c;
@@ -55,17 +181,15 @@ __device__ bool grid_query_grad(const DScene& s, float cx, float cy, float cz, f
   if (!(gx >= 0.f && gx <= (float)(s.nx - 1) && gy >= 0.f && gy <= (float)(s.ny - 1) &&
         gz >= 0.f && gz <= (float)(s.nz - 1)))
     return false;
-  d = grid_lerp(s, gx, gy, gz);
   const int i = min((int)floorf(gx), s.nx - 2);
   const int j = min((int)floorf(gy), s.ny - 2);
   const int k = min((int)floorf(gz), s.nz - 2);
   const float tx = gx - i, ty = gy - j, tz = gz - k;
-  const float* g = s.grid + ((size_t)k * s.ny + j) * s.nx + i;
-  const size_t sy = s.nx, sz = (size_t)s.nx * s.ny;
-  const float c000 = __ldg(g), c100 = __ldg(g + 1);
-  const float c010 = __ldg(g + sy), c110 = __ldg(g + sy + 1);
-  const float c001 = __ldg(g + sz), c101 = __ldg(g + sz + 1);
-  const float c011 = __ldg(g + sz + sy), c111 = __ldg(g + sz + sy + 1);
+  float cc[8];
+  cell_corners(s, i, j, k, cc);
+  d = lerp8(cc, tx, ty, tz);
+  const float c000 = cc[0], c100 = cc[1], c010 = cc[2], c110 = cc[3];
+  const float c001 = cc[4], c101 = cc[5], c011 = cc[6], c111 = cc[7];
   gxo = ((c100 - c000) * (1.f - ty) * (1.f - tz) + (c110 - c010) * ty * (1.f - tz) +
          (c101 - c001) * (1.f - ty) * tz + (c111 - c011) * ty * tz) * s.inv_h;
   gzo = ((c001 - c000) * (1.f - tx) * (1.f - ty) + (c101 - c100) * tx * (1.f - ty) +

@@ -3,7 +3,11 @@
 // Collision-Detection Details"); here the structure is a lattice of signed
 // distances to the union of the scene's solid boxes, one thread per node, in
 // FP64, rounded once to FP32 for storage.
-#include "gx_internal.h"
+// node values from the dense grid or the box store, per scene at run time
+#define GX_STATIC_STORE 2
+#include <algorithm>
+
+#include "gx_device.cuh"
 
 namespace gx {
 
@@ -114,6 +118,23 @@ void launch_column_build(const float* boxes, int n_boxes, double ox, double oz, 
   if (blocks > 148 * 16) blocks = 148 * 16;
   column_kernel<<<blocks, 128, (size_t)n_boxes * 6 * sizeof(double), s>>>(
       boxes, n_boxes, ox, oz, ylo, yhi, ncx, ncz, offsets, counts, spans, overflow);
+}
+
+__global__ void static_distance_kernel(const DScene* __restrict__ scenes, int scene,
+                                       const float* __restrict__ pts, int n,
+                                       float* __restrict__ dist) {
+  const DScene& s = scenes[scene];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    float d;
+    dist[t] = grid_query(s, pts[3 * t], pts[3 * t + 1], pts[3 * t + 2], d) ? d : CUDART_NAN_F;
+  }
+}
+
+cudaError_t launch_static_distance(const DScene* scenes, int scene, const float* pts, int n,
+                                   float* dist, cudaStream_t s) {
+  const int blocks = std::min((n + 255) / 256, 148 * 8);
+  static_distance_kernel<<<blocks, 256, 0, s>>>(scenes, scene, pts, n, dist);
+  return cudaGetLastError();
 }
 
 void launch_grid_build(float* grid, const float* boxes, int n_boxes, float ox, float oy, float oz,

@@ -51,7 +51,17 @@ struct DScene {
   const float* supports;    // [P][5]
   int n_supports;
   float spawn[4];
+  // static distance source: 0 the dense grid above; 1 the box store, node
+  // values recomputed from the solid boxes (centre xyz, -, half extents xyz,
+  // - as two float4 per box) over per-cell candidate lists (cells of
+  // 2^kStoreShift node intervals per axis, CSR offsets and box indices)
+  int store;
+  const float4* sbox;       // [n_boxes][2]
+  const uint32_t* sb_off;   // [sbx * sby * sbz + 1]
+  const uint16_t* sb_ids;
+  int sbx, sby, sbz;
 };
+constexpr int kStoreShift = 4;
 
 struct HostMeshlets {
   std::vector<float4> hdr, verts;
@@ -60,6 +70,16 @@ struct HostMeshlets {
 
 // Builds the meshlet arrays of one scene (host, deterministic).
 void build_meshlets(const gx_scene_desc& s, HostMeshlets& out);
+
+// Box store of one scene (host, deterministic; gx_store.cpp): the boxes as
+// centre / half-extent float4 pairs and the CSR candidate lists per cell.
+struct StoreHost {
+  std::vector<float4> boxes;
+  std::vector<uint32_t> off;
+  std::vector<uint16_t> ids;
+  int sbx = 0, sby = 0, sbz = 0;
+};
+bool build_box_store(const gx_scene_desc& s, StoreHost& out);
 
 // Device robot table: gx_robot as given.
 struct Robot {
@@ -129,6 +149,7 @@ struct PhysicsParams {
   int env_offset;                       // global index of environment 0 (Philox counters)
   float4* held_M;                       // box objects: [n][3] rows of the held box's world
                                         // rotation times its half extents (rasteriser)
+  int store;                            // 1: scenes use the box store (kernels compiled for it)
 };
 
 // Neural-SDF decision counters (profiling only).
@@ -154,6 +175,7 @@ struct ResetParams {
   float rho_min, rho_max;
   unsigned* err;
   int env_offset;      // global index of environment 0 (Philox counters)
+  int store;           // 1: scenes use the box store (kernels compiled for it)
 };
 
 // Rasteriser launch shape: threads per CTA and CTAs wanted per SM.
@@ -212,7 +234,10 @@ enum RasterCounter {
   kRasterCounters
 };
 
-void launch_physics(const PhysicsParams& p, cudaStream_t s);
+void launch_physics(const PhysicsParams& p, cudaStream_t s);        // dispatches on p.store
+void launch_physics_store(const PhysicsParams& p, cudaStream_t s);  // box-store kernels
+void launch_reset_store(const ResetParams& p, cudaStream_t s);
+cudaError_t reset_configure_store();
 void launch_bp_rebuild(const DScene* scenes, const int* env_scene, const StateView& st, int n,
                        int M, BpCell* bp, int cells, cudaStream_t s);
 void launch_reset(const ResetParams& p, cudaStream_t s);
@@ -268,7 +293,11 @@ struct NsdfScene {
 struct gx_scene_set {
   int n = 0;
   std::vector<gx::DScene> host;
-  gx::DScene* d_scenes = nullptr;
+  gx::DScene* d_scenes = nullptr;     // default view: dense grid when built, else box store
+  gx::DScene* d_scenes_box = nullptr; // the same scenes with the box store
+  bool dense = true;                  // dense grids built
+  bool columns = true;                // column grids built
+  std::vector<size_t> dense_bytes, store_bytes, render_bytes;
   std::vector<void*> allocs;
   float4* omesh_v = nullptr;
   uint32_t* omesh_t = nullptr;
@@ -324,6 +353,9 @@ cudaError_t raster_configure(int* slots);
 cudaError_t raster_ctas_per_sm(int warps, int* per_sm);
 void launch_grid_build(float* grid, const float* boxes, int n_boxes, float ox, float oy, float oz,
                        float h, int nx, int ny, int nz, cudaStream_t s);
+// Trilinear static distance of scene `scene` at n points (NaN outside the box).
+cudaError_t launch_static_distance(const DScene* scenes, int scene, const float* pts, int n,
+                                   float* dist, cudaStream_t s);
 
 // device error bits beyond the public ones
 constexpr unsigned kErrWaitTimeout = 0x100u;  // a bounded mbarrier wait gave up

@@ -22,6 +22,8 @@
 // The same images serve both directions: a weight image read K-major is W
 // (forward), read MN-major it is W^T (backward); an activation or gradient
 // image read MN-major is its transpose over the batch (weight gradient).
+// node values from the dense grid or the box store, per scene at run time
+#define GX_STATIC_STORE 2
 #include <math_constants.h>
 
 #include <cmath>

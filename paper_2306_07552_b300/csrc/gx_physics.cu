@@ -17,6 +17,18 @@
 
 #include <algorithm>
 
+// This file is compiled twice: as itself (dense grid) and, through
+// gx_physics_store.cu, with GX_STATIC_STORE 1 (box store), whose launchers
+// carry the suffix _store.
+#ifndef GX_STATIC_STORE
+#define GX_STATIC_STORE 0
+#endif
+#if GX_STATIC_STORE == 1
+#define GX_LAUNCHER(name) name##_store
+#else
+#define GX_LAUNCHER(name) name
+#endif
+
 #include "gx_internal.h"
 #include "gx_device.cuh"
 #include "gx_kin.cuh"
@@ -32,7 +44,11 @@ using namespace phys;
 // random grid gathers, and resident warps hide that latency; six blocks (80
 // registers), seven and eight (64) measured 0.051, 0.043 and 0.044 ms for
 // 4096 environments.
-__global__ void __launch_bounds__(32 * kEnvsPerBlock, 7) physics_kernel(const PhysicsParams P) {
+#ifndef GX_PHYS_BLOCKS
+#define GX_PHYS_BLOCKS (GX_STATIC_STORE == 1 ? 6 : 7)
+#endif
+__global__ void __launch_bounds__(32 * kEnvsPerBlock, GX_PHYS_BLOCKS)
+    physics_kernel(const PhysicsParams P) {
   __shared__ float4 s_obj[kEnvsPerBlock][GX_MAX_OBJECTS];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int env = blockIdx.x * kEnvsPerBlock + w;
@@ -80,12 +96,21 @@ __global__ void bp_rebuild_kernel(const DScene* scenes, const int* env_scene, St
 
 }  // namespace
 
+#if GX_STATIC_STORE == 0
 void launch_bp_rebuild(const DScene* scenes, const int* env_scene, const StateView& st, int n,
                        int M, BpCell* bp, int cells, cudaStream_t s) {
   if (n > 0) bp_rebuild_kernel<<<n, 256, 0, s>>>(scenes, env_scene, st, n, M, bp, cells);
 }
 
-void launch_physics(const PhysicsParams& p, cudaStream_t s) {
+#endif
+
+void GX_LAUNCHER(launch_physics)(const PhysicsParams& p, cudaStream_t s) {
+#if GX_STATIC_STORE == 0
+  if (p.store) {
+    launch_physics_store(p, s);
+    return;
+  }
+#endif
   const int blocks = (p.n + kEnvsPerBlock - 1) / kEnvsPerBlock;
   physics_kernel<<<blocks, 32 * kEnvsPerBlock, 0, s>>>(p);
 }
@@ -94,7 +119,11 @@ namespace {
 int g_reset_grid = 0;  // CTAs resident at once on this device
 }
 
-cudaError_t reset_configure() {
+cudaError_t GX_LAUNCHER(reset_configure)() {
+#if GX_STATIC_STORE == 0
+  cudaError_t es = reset_configure_store();
+  if (es != cudaSuccess) return es;
+#endif
   if (g_reset_grid > 0) return cudaSuccess;
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e;
@@ -109,7 +138,13 @@ cudaError_t reset_configure() {
 
 // One wave of resident CTAs striding over the environments: a staggered reset
 // of a few environments no longer launches a CTA per environment.
-void launch_reset(const ResetParams& p, cudaStream_t s) {
+void GX_LAUNCHER(launch_reset)(const ResetParams& p, cudaStream_t s) {
+#if GX_STATIC_STORE == 0
+  if (p.store) {
+    launch_reset_store(p, s);
+    return;
+  }
+#endif
   if (p.n <= 0) return;
   const int grid = std::min(p.n, g_reset_grid > 0 ? g_reset_grid : p.n);
   reset_kernel<<<grid, kResetThreads, 0, s>>>(p);

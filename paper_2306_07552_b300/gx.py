@@ -35,7 +35,8 @@ SYMBOLS = ["gx_scene_set_create", "gx_scene_set_destroy", "gx_create", "gx_destr
            "gx_nsdf_get_weights", "gx_nsdf_query", "gx_nsdf_get_master", "gx_nsdf_samples",
            "gx_nsdf_grad",
            "gx_nsdf_train", "gx_nsdf_counters", "gx_nsdf_step_predictions", "gx_autotune",
-           "gx_column_info", "gx_column_spans", "gx_device_outputs", "gx_last_error"]
+           "gx_column_info", "gx_column_spans", "gx_device_outputs", "gx_last_error",
+           "gx_scene_set_create_ex", "gx_scene_bytes", "gx_static_distance"]
 NSDF_PARAMS = 57985
 NSDF_FREQ = 32
 RASTER_COUNTERS = ["clusters_tested", "clusters_drawn", "tris_seen", "tris_front", "tris_expand",
@@ -81,7 +82,12 @@ class GxConfig(C.Structure):
                 ("render_robot", C.c_int32), ("heuristics", C.c_int32),
                 ("raster_order", C.c_int32), ("env_offset", C.c_int32),
                 ("object_boxes", C.c_int32), ("raster_warps", C.c_int32),
-                ("occlusion_cull", C.c_int32), ("fused_step", C.c_int32)]
+                ("occlusion_cull", C.c_int32), ("fused_step", C.c_int32),
+                ("static_store", C.c_int32)]
+
+
+class GxSceneOptions(C.Structure):
+    _fields_ = [("dense_grid", C.c_int32), ("column_grid", C.c_int32)]
 
 
 OUTPUT_KEYS = ["depth", "rgb", "pose", "obj_pos", "held", "contact_mask", "contact_flags", "event",
@@ -124,6 +130,10 @@ def lib():
         P = C.POINTER
         vp = C.c_void_p
         L.gx_scene_set_create.argtypes = [P(GxSceneDesc), C.c_int32, P(GxObjectMesh), P(vp)]
+        L.gx_scene_set_create_ex.argtypes = [P(GxSceneDesc), C.c_int32, P(GxObjectMesh),
+                                             P(GxSceneOptions), P(vp)]
+        L.gx_scene_bytes.argtypes = [vp, C.c_int32, C.POINTER(C.c_uint64)]
+        L.gx_static_distance.argtypes = [vp, C.c_int32, C.c_int32, vp, C.c_int32, vp, vp]
         L.gx_scene_set_destroy.argtypes = [vp]
         L.gx_create.argtypes = [vp, P(GxRobot), P(GxConfig), P(vp)]
         L.gx_destroy.argtypes = [vp]
@@ -197,7 +207,8 @@ def robot_struct(r: _inputs.Robot) -> GxRobot:
 class SceneSet:
     """Device copies of a list of scenes (grid, clusters, supports)."""
 
-    def __init__(self, scenes, obj_mesh=None, obj_rgb=None, robot_rgb=None):
+    def __init__(self, scenes, obj_mesh=None, obj_rgb=None, robot_rgb=None, dense_grid=True,
+                 column_grid=True):
         self._keep = []
         n = len(scenes)
         descs = (GxSceneDesc * n)()
@@ -231,9 +242,31 @@ class SceneSet:
         m.robot_rgb[:] = [int(x) for x in rr]
         self.n_obj_tris = len(mt)
         self.handle = C.c_void_p()
-        _check(lib().gx_scene_set_create(descs, n, C.byref(m), C.byref(self.handle)))
+        opt = GxSceneOptions()
+        opt.dense_grid, opt.column_grid = int(dense_grid), int(column_grid)
+        _check(lib().gx_scene_set_create_ex(descs, n, C.byref(m), C.byref(opt),
+                                            C.byref(self.handle)))
         self._keep = []   # the library copied everything
         self.n = n
+
+    def scene_bytes(self, scene):
+        """Device bytes of a scene's structures: dict dense_grid, box_store,
+        column_grid, render, nsdf_weights, nsdf_master."""
+        b = (C.c_uint64 * 6)()
+        _check(lib().gx_scene_bytes(self.handle, scene, b))
+        keys = ["dense_grid", "box_store", "column_grid", "render", "nsdf_weights", "nsdf_master"]
+        return {k: int(v) for k, v in zip(keys, b)}
+
+    def static_distance(self, scene, pts, store, stream=None):
+        """Trilinear static distance at device points pts [n][3] (NaN outside
+        the lattice box), node values from store 0 (dense grid) or 1 (box store)."""
+        import torch
+        out = torch.empty(pts.shape[0], dtype=torch.float32, device=pts.device)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        _check(lib().gx_static_distance(self.handle, scene, int(store), C.c_void_p(pts.data_ptr()),
+                                        int(pts.shape[0]), C.c_void_p(out.data_ptr()),
+                                        C.c_void_p(s.cuda_stream)))
+        return out
 
     # -------------------------------------------------------- neural SDF
     def nsdf_set_weights(self, scene, fourier_B, params):
@@ -339,7 +372,7 @@ class Sim:
                  seed=1, env_scene=None, small_tri_px=0, use_graph=False,
                  profile=0, sdf_mode=0, sdf_margin=0.02, heuristics=0, render_robot=False,
                  broadphase=False, raster_order=0, env_offset=0, object_boxes=False,
-                 fused_step=False, raster_warps=0, occlusion_cull=False):
+                 fused_step=False, raster_warps=0, occlusion_cull=False, static_store=0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("gx needs a CUDA device; there is no CPU fallback")
@@ -368,6 +401,7 @@ class Sim:
         cfg.fused_step = int(fused_step)
         cfg.raster_warps = int(raster_warps)
         cfg.occlusion_cull = int(occlusion_cull)
+        cfg.static_store = int(static_store)
         self.object_boxes = bool(object_boxes)
         self.robot_c = robot_struct(robot)
         self.handle = C.c_void_p()

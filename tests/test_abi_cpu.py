@@ -40,9 +40,9 @@ def test_struct_sizes_match_header(tmp_path):
     structs = {"gx_robot": gx.GxRobot, "gx_scene_desc": gx.GxSceneDesc,
                "gx_object_mesh": gx.GxObjectMesh, "gx_config": gx.GxConfig,
                "gx_outputs": gx.GxOutputs, "gx_train_params": gx.GxTrainParams,
-               "gx_tune_result": gx.GxTuneResult}
+               "gx_tune_result": gx.GxTuneResult, "gx_scene_options": gx.GxSceneOptions}
     fields = {"gx_config": ["seed", "env_scene", "profile", "sdf_mode", "sdf_margin",
-                            "broadphase", "render_robot", "heuristics"],
+                            "broadphase", "render_robot", "heuristics", "static_store"],
               "gx_outputs": ["event", "reward", "task_obs", "success"],
               "gx_train_params": ["batch", "lr", "seed"]}
     src = ["#include <stdio.h>", "#include <stddef.h>", '#include "gx.h"', "int main(void) {"]
