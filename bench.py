@@ -218,14 +218,14 @@ def reset_masks(n, period, first=0):
     return masks
 
 
-def work_counters(ss, w, acts, mask_at, steps, plan):
+def work_counters(ss, w, acts, mask_at, steps, plan, store):
     """Rasteriser work counters per view from a separate, untimed context
     running the counting variant of the kernel."""
     from paper_2306_07552_b300 import gx
     sim = gx.Sim(ss, I.fetch_like_robot(), w.n_envs, img=(w.img, w.img),
                  depth_fp16=w.depth_fp16, render_rgb=w.rgb, n_objects=w.n_objects,
                  obj_radius=w.obj_radius, seed=w.reset_seed, profile=3,
-                 env_scene=plan.env_scene, env_offset=plan.first)
+                 env_scene=plan.env_scene, env_offset=plan.first, static_store=store)
     sim.reset()
     for t in range(steps):
         sim.reset(mask_at(t))
@@ -484,6 +484,10 @@ def main():
                          "rendering)")
     ap.add_argument("--no-graph", action="store_true",
                     help="headline from the event-timed loop instead of a graph-replayed one")
+    ap.add_argument("--static-store", type=int, default=-1, choices=[-1, 0, 1],
+                    help="distance-grid nodes: 0 the dense grid, 1 the box store (recomputed "
+                         "from the scene's boxes; the scene set then holds no dense grid); "
+                         "-1: the box store for the neural form, else the dense grid")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_env()
@@ -508,8 +512,13 @@ def main():
     # environment range, the scenes those environments use, their map
     plan = shard.plan(world * n, w.n_scenes, world, rank)
     scenes = I.make_scenes(w, only=plan.scenes)
-    ss = gx.SceneSet(scenes)
     neural = w.sdf == "neural"
+    column = w.sdf == "column"
+    store = args.static_store if args.static_store >= 0 else (1 if neural else 0)
+    # with the box store the scene set holds no dense grid (nor, unless the
+    # column form needs them, column grids): what the product keeps resident
+    ss = (gx.SceneSet(scenes, dense_grid=False, column_grid=column) if store == 1
+          else gx.SceneSet(scenes))
     nsdf = None
     if neural:
         nsdf = train_scenes(ss, w, list(enumerate(plan.scenes)))
@@ -519,8 +528,7 @@ def main():
                   render_robot=args.render_robot, broadphase=args.broadphase,
                   env_scene=plan.env_scene, env_offset=plan.first,
                   object_boxes=w.objects == "boxes", fused_step=args.fused,
-                  occlusion_cull=args.occlusion)
-    column = w.sdf == "column"
+                  occlusion_cull=args.occlusion, static_store=store)
     sdf_mode = 1 if neural else (2 if column else 0)
     # per-kernel CUDA events on the launching stream (the roofline's kernel
     # time); the headline loop below replays the step as a CUDA graph on a
@@ -625,9 +633,11 @@ def main():
               "last_step_summed": shard.sum_counters(
                   (dist, dist.new_group(backend="gloo")) if dist else None, last)}
     static_form = None
-    if neural or column:
-        # the grid form of the same workload, timed the same way
-        g = gx.Sim(ss, I.fetch_like_robot(), n, profile=1, **sim_kw)
+
+    def time_form(sset, **kw):
+        """Another static form of the same batch, timed like the headline's
+        event-timed loop: env-steps/s and physics ms per launch."""
+        g = gx.Sim(sset, I.fetch_like_robot(), n, profile=1, **{**sim_kw, **kw})
         with torch.cuda.stream(stream):
             g.reset(stream=stream)
             for t in range(args.warmup):
@@ -636,6 +646,7 @@ def main():
                 g.reset(mbuf, stream=stream)
                 g.step(abuf, stream=stream)
         torch.cuda.synchronize()
+        g.phase_times()
         g0 = torch.cuda.Event(enable_timing=True)
         g1 = torch.cuda.Event(enable_timing=True)
         g0.record(stream)
@@ -647,10 +658,17 @@ def main():
                 g.step(abuf, stream=stream)
         g1.record(stream)
         torch.cuda.synchronize()
-        grid_value, _ = job_value(dist, n, args.steps, g0.elapsed_time(g1))
+        v, _ = job_value(dist, n, args.steps, g0.elapsed_time(g1))
         g_ms, g_n = g.phase_times()
-        grid_physics_ms = g_ms[0] / max(g_n[0], 1)
         g.close()
+        return v, g_ms[0] / max(g_n[0], 1)
+
+    if neural or column:
+        # the plain distance-grid form of the same workload (dense grid)
+        ss_dense = gx.SceneSet(scenes) if store == 1 else ss
+        grid_value, grid_physics_ms = time_form(ss_dense, static_store=0, sdf_mode=0)
+        if ss_dense is not ss:
+            ss_dense.close()
         grid_bytes = [int(np.prod(sc.grid_dims)) * 4 for sc in scenes]
         if column:
             cb = [ss.column_info(s)[1] for s in range(len(scenes))]
@@ -661,6 +679,15 @@ def main():
                                                "column_mean": float(np.mean(cb))},
                            "note": "release, reset and the heuristics still read the grid"}
     if neural:
+        # the method without the network but with the same small footprint:
+        # every static test on the box store
+        store_value, store_physics_ms = (time_form(ss, static_store=1, sdf_mode=0)
+                                         if store == 1 else (None, None))
+        sb = [ss.scene_bytes(s) for s in range(len(scenes))]
+        hbm = torch.cuda.get_device_properties(0).total_memory
+        render_mean = float(np.mean([b["render"] for b in sb]))
+        store_mean = float(np.mean([b["box_store"] for b in sb]))
+        static_neural = NSDF_BLOB_BYTES + (store_mean if store == 1 else np.mean(grid_bytes))
         # the neural form's decisions counted against the grid-only rule
         c = gx.Sim(ss, I.fetch_like_robot(), n, profile=4, sdf_mode=1, sdf_margin=w.sdf_margin,
                    **sim_kw)
@@ -673,6 +700,12 @@ def main():
         q_ms = phase_ms[3] / max(phase_n[3], 1)
         nsdf.update({
             "grid_form_value": grid_value, "neural_over_grid": value / grid_value,
+            "static_store": ("box store: nodes recomputed from the scene's boxes; the scene set "
+                             "holds no dense grid" if store == 1 else "dense grid"),
+            "box_store_form_value": store_value,
+            "neural_over_box_store": value / store_value if store_value else None,
+            "physics_ms": {"neural": phase_ms[0] / max(phase_n[0], 1), "grid": grid_physics_ms,
+                           "box_store": store_physics_ms},
             "query_ms_per_step": q_ms,
             "query_tflops": n * 32 * NSDF_QUERY_FLOP / (q_ms / 1e3) / 1e12 if q_ms else None,
             "query_flop_basis": f"{NSDF_QUERY_FLOP} FLOP per query, 32 query rows per env "
@@ -682,8 +715,19 @@ def main():
             "grid_consulted": cnt["grid_fallbacks"] / max(cnt["tests"], 1),
             "env_steps_differing": cnt["env_disagree"] / max(min(args.steps, 50) * n, 1),
             "bytes_per_scene": {"grid_mean": float(np.mean(grid_bytes)),
-                                "network": NSDF_BLOB_BYTES},
-            "note": "the grid stays resident: it decides every test below the margin"})
+                                "network": NSDF_BLOB_BYTES, "box_store_mean": store_mean,
+                                "render_mean": render_mean,
+                                "static_neural_form": static_neural,
+                                "static_grid_form": float(np.mean(grid_bytes))},
+            "scenes_per_gpu": {
+                "neural_form": int(hbm // (render_mean + static_neural)),
+                "grid_form": int(hbm // (render_mean + np.mean(grid_bytes))),
+                "note": f"{hbm / 2**30:.0f} GiB of HBM over one scene's render clusters and "
+                        f"static structure (environment state and framebuffers aside)"},
+            "note": ("below the margin the box store decides (the grid's node values "
+                     "recomputed from the boxes), so no dense grid is resident"
+                     if store == 1 else
+                     "the dense grid stays resident: it decides every test below the margin")})
 
     # end to end through the C ABI with host buffers (pinned), copies inside
     # the timed region: actions in, the step's result (reward, success,
@@ -738,7 +782,7 @@ def main():
                            "note": "every output (images included) copied back each step"}}
     counters = None
     if rank == 0 and not args.no_counters:
-        counters = work_counters(ss, w, acts, mask_at, min(args.warmup, 5), plan)
+        counters = work_counters(ss, w, acts, mask_at, min(args.warmup, 5), plan, store)
     sim.close()
     if rank != 0:
         ss.close()
