@@ -19,6 +19,14 @@ constexpr int kWarps = kThreads / 32;
 constexpr long kWaitLimit = 1L << 22;  // bounded waits
 constexpr int kListCap = 2048;          // clusters culled per pass
 constexpr int kSpan = 4;                // adjacent pixels of a row per expansion slot
+#ifndef GX_RASTER_DIRECT_W
+#define GX_RASTER_DIRECT_W 2
+#endif
+#ifndef GX_RASTER_DIRECT_H
+#define GX_RASTER_DIRECT_H 2
+#endif
+// bounding boxes up to this size are tested by their set-up lane (no slots)
+constexpr int kDirectW = GX_RASTER_DIRECT_W, kDirectH = GX_RASTER_DIRECT_H;
 constexpr float kClassPx = 64.f;        // screen radius (pixels) of the costliest cluster class
 
 // The box objects' instance mesh: the unit cube's twelve triangles (corner k
@@ -418,18 +426,42 @@ __device__ void raster_cluster(const View& vw, const Cam& cm, WarpSmem& ws, int 
                   }
                   float A, B, C;
                   depth_plane(cm, nx, ny, nz, h, A, B, C);
-                  // the record in four 16-byte stores (the round's slot offset follows later)
-                  int4* r4 = reinterpret_cast<int4*>(&ws.q[lane]);
-                  r4[0] = make_int4(e[0], e[1], e[2], ix0 | (iy0 << 16));
-                  r4[1] = make_int4(sx[0], sx[1], sx[2], bw);
-                  r4[2] = make_int4(sy[0], sy[1], sy[2], (int)ws.cbuf[buf][t]);
-                  r4[3] = make_int4(__float_as_int(A), __float_as_int(B), __float_as_int(C), 0);
-                  ws.q[lane].inv_bp = rcp_approx((float)((bw + kSpan - 1) / kSpan));
-                  npx = ((bw + kSpan - 1) / kSpan) * bh;  // expansion slots: pixel runs
-                  if (kCount) {
-                    cn.v[kCntTrisSmall]++;
-                    cn.v[kCntSmallPixels] += bw * bh;
-                    cn.v[kCntExpandSlots] += npx;
+                  if (bw <= kDirectW && bh <= kDirectH) {
+                    // a box of at most kDirectW x kDirectH pixels (most
+                    // triangles of a view) is tested by its own set-up lane:
+                    // the same edge values, plane and key as an expansion
+                    // slot would compute, without a slot
+                    const float u0 = (float)ix0 + 0.5f - cm.cx;
+                    const uint32_t rgb = ws.cbuf[buf][t];
+#pragma unroll
+                    for (int dy = 0; dy < kDirectH; ++dy) {
+                      const float row = fmaf(B, (float)(iy0 + dy) + 0.5f - cm.cy, C);
+                      unsigned long long* fbp = vw.fb + (iy0 + dy) * vw.W + ix0;
+#pragma unroll
+                      for (int dx = 0; dx < kDirectW; ++dx)
+                        if (dx < bw && dy < bh &&
+                            ((e[0] + dx * sx[0] + dy * sy[0]) | (e[1] + dx * sx[1] + dy * sy[1]) |
+                             (e[2] + dx * sx[2] + dy * sy[2])) >= 0)
+                          frag_key<kCount>(vw, fbp + dx, fmaf(A, u0 + (float)dx, row), rgb, cn);
+                    }
+                    if (kCount) {
+                      cn.v[kCntTrisSmall]++;
+                      cn.v[kCntSmallPixels] += bw * bh;
+                    }
+                  } else {
+                    // the record in four 16-byte stores (the round's slot offset follows later)
+                    int4* r4 = reinterpret_cast<int4*>(&ws.q[lane]);
+                    r4[0] = make_int4(e[0], e[1], e[2], ix0 | (iy0 << 16));
+                    r4[1] = make_int4(sx[0], sx[1], sx[2], bw);
+                    r4[2] = make_int4(sy[0], sy[1], sy[2], (int)ws.cbuf[buf][t]);
+                    r4[3] = make_int4(__float_as_int(A), __float_as_int(B), __float_as_int(C), 0);
+                    ws.q[lane].inv_bp = rcp_approx((float)((bw + kSpan - 1) / kSpan));
+                    npx = ((bw + kSpan - 1) / kSpan) * bh;  // expansion slots: pixel runs
+                    if (kCount) {
+                      cn.v[kCntTrisSmall]++;
+                      cn.v[kCntSmallPixels] += bw * bh;
+                      cn.v[kCntExpandSlots] += npx;
+                    }
                   }
                 } else {
                   big = true;
