@@ -130,30 +130,27 @@ __device__ float run_tile(QuerySmem& sm, int g, const Centred& d, uint32_t& mma_
     // epilogue: this warp's 32 rows, 32 columns at a time
 #pragma unroll 1
     for (int c = 0; c < kNsdfWidth / 32; ++c) {
-      float v[32];
+      float v[32], bias[32];
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
-      {
-        float bias[32];
-        lds32(&sm.tail.b[layer][c * 32], bias);
-#pragma unroll
-        for (int u = 0; u < 32; ++u) v[u] = fmaxf(v[u] + bias[u], 0.f);
-      }
+      lds32(&sm.tail.b[layer][c * 32], bias);
       if (layer < 3) {
-        // store_chunk rounds to BF16 on the way into the next operand
+        // bias, ReLU and the BF16 rounding into the next operand, two
+        // columns per instruction
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          float ch[8];
+          uint32_t pk[4];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) ch[u] = v[q * 8 + u];
-          store_chunk(act, warp * 32 + lane, c * 32 + q * 8, kTile, ch);
+          for (int i = 0; i < 4; ++i)
+            pk[i] = add_relu_bf16x2(v[q * 8 + 2 * i], v[q * 8 + 2 * i + 1], bias[q * 8 + 2 * i],
+                                    bias[q * 8 + 2 * i + 1]);
+          store_chunk_bits(act, warp * 32 + lane, c * 32 + q * 8, kTile, pk[0], pk[1], pk[2],
+                           pk[3]);
         }
       } else {
-        {
-          float w5[32];
-          lds32(&sm.tail.w5[c * 32], w5);
+        float w5[32];
+        lds32(&sm.tail.w5[c * 32], w5);
 #pragma unroll
-          for (int u = 0; u < 32; ++u) dot = fmaf(bf16_round(v[u]), w5[u], dot);
-        }
+        for (int u = 0; u < 32; ++u) dot = fmaf(bf16_round(fmaxf(v[u] + bias[u], 0.f)), w5[u], dot);
       }
     }
     fence_proxy_async();

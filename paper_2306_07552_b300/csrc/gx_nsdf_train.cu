@@ -268,14 +268,20 @@ __global__ void __launch_bounds__(kTrainThreads, 1) nsdf_fwd_bwd_kernel(const Fw
         float v[32], bias[32];
         tmem_ld32(trow + col, v);
         lds32(&sm.tail.b[L][col], bias);
-        uint32_t bits = 0;
+        // bias, ReLU and BF16 rounding two columns per instruction; a
+        // column's ReLU mask bit is set where its BF16 value is above zero
+        uint32_t bits = 0, pk[16];
 #pragma unroll
-        for (int u = 0; u < 32; ++u) {
-          v[u] = bf16_round(fmaxf(v[u] + bias[u], 0.f));
-          bits |= (v[u] > 0.f ? 1u : 0u) << u;
+        for (int i = 0; i < 16; ++i) {
+          pk[i] = add_relu_bf16x2(v[2 * i], v[2 * i + 1], bias[2 * i], bias[2 * i + 1]);
+          bits |= ((pk[i] & 0x7FFFu) != 0u ? 1u : 0u) << (2 * i);
+          bits |= ((pk[i] & 0x7FFF0000u) != 0u ? 1u : 0u) << (2 * i + 1);
         }
         sm.mask[L][c][tid] = bits;
-        store_row32(out_img, row, col, v);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          store_chunk_bits(out_img, row, col + q * 8, kTile, pk[4 * q], pk[4 * q + 1],
+                           pk[4 * q + 2], pk[4 * q + 3]);
       }
       fence_proxy_async();
       tc_fence_before();

@@ -146,6 +146,27 @@ __device__ __forceinline__ void store_chunk(unsigned char* tile, int row, int k8
   *reinterpret_cast<uint4*>(tile + sw128_offset(row, k8, rows)) = *reinterpret_cast<uint4*>(p);
 }
 
+// relu(a + b) rounded to BF16 for two neighbouring values, packed (a0 in the
+// low half): one packed FP32 add and the converter's ReLU.  Equals
+// round_bf16(max(a + b, 0)) for finite values (a negative sum clamps to 0).
+__device__ __forceinline__ uint32_t add_relu_bf16x2(float a0, float a1, float b0, float b1) {
+  unsigned long long a, b, s;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(a) : "f"(a0), "f"(a1));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(b) : "f"(b0), "f"(b1));
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(s) : "l"(a), "l"(b));
+  float s0, s1;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(s0), "=f"(s1) : "l"(s));
+  uint32_t r;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(s1), "f"(s0));
+  return r;
+}
+// Four packed BF16 pairs (8 consecutive K values of one row) into the swizzled tile.
+__device__ __forceinline__ void store_chunk_bits(unsigned char* tile, int row, int k8, int rows,
+                                                 uint32_t p0, uint32_t p1, uint32_t p2,
+                                                 uint32_t p3) {
+  *reinterpret_cast<uint4*>(tile + sw128_offset(row, k8, rows)) = make_uint4(p0, p1, p2, p3);
+}
+
 // 32 consecutive floats of shared memory (16-byte aligned) in eight 16-byte loads.
 __device__ __forceinline__ void lds32(const float* p, float (&v)[32]) {
   const float4* p4 = reinterpret_cast<const float4*>(p);
