@@ -301,6 +301,19 @@ gx_status gx_scene_set_create_ex(const gx_scene_desc* scenes, int32_t n_scenes,
  * neural-SDF FP32 master copy kept for training (0 when none). */
 gx_status gx_scene_bytes(const gx_scene_set* set, int32_t scene, uint64_t bytes[6]);
 
+/* The box store's candidate lists of one scene (gx_config.static_store 1),
+ * built on the host exactly as gx_scene_set_create builds them; no device is
+ * touched.  The lattice's node intervals are grouped 16 per axis into cells,
+ * dims[0..2] of them along x, y, z; cell (cx, cy, cz) has index
+ * (cz * dims[1] + cy) * dims[0] + cx and lists, as box indices
+ * ids[offsets[c] .. offsets[c + 1]), every box that can be the nearest one
+ * at some node of the cell (nodes 16c .. 16c + 16 per axis).  Call once with
+ * offsets and ids NULL for dims and *n_ids, then with offsets [cells + 1] and
+ * ids [*n_ids] (host buffers).  GX_EINVAL for a scene without boxes or with a
+ * bad lattice. */
+gx_status gx_box_store_lists(const gx_scene_desc* scene, int32_t dims[3], uint32_t* offsets,
+                             uint16_t* ids, uint64_t* n_ids);
+
 /* Static distance at n points (device pts [n][3]) into dist (device [n]):
  * the trilinear interpolation of the scene's distance grid whose nodes come
  * from `store` (0 dense grid, 1 box store; see gx_config.static_store); NaN

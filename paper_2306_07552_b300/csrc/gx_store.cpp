@@ -109,3 +109,23 @@ bool build_box_store(const gx_scene_desc& d, StoreHost& out) {
 }
 
 }  // namespace gx
+
+// Host-only view of the candidate lists (the same build gx_scene_set_create
+// uploads); touches no device.
+extern "C" gx_status gx_box_store_lists(const gx_scene_desc* scene, int32_t dims[3],
+                                        uint32_t* offsets, uint16_t* ids, uint64_t* n_ids) {
+  if (!scene || !dims || !n_ids || scene->n_boxes < 1 || scene->n_boxes > 4096 ||
+      !scene->boxes || !(scene->grid_h > 0.f) || scene->grid_dims[0] < 2 ||
+      scene->grid_dims[1] < 2 || scene->grid_dims[2] < 2)
+    return gx::set_last_error(GX_EINVAL, "gx_box_store_lists: bad scene");
+  gx::StoreHost sh;
+  if (!gx::build_box_store(*scene, sh))
+    return gx::set_last_error(GX_EINVAL, "gx_box_store_lists: box store too large");
+  dims[0] = sh.sbx;
+  dims[1] = sh.sby;
+  dims[2] = sh.sbz;
+  *n_ids = sh.ids.size();
+  if (offsets) std::copy(sh.off.begin(), sh.off.end(), offsets);
+  if (ids) std::copy(sh.ids.begin(), sh.ids.end(), ids);
+  return GX_OK;
+}

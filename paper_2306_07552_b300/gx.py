@@ -36,7 +36,8 @@ SYMBOLS = ["gx_scene_set_create", "gx_scene_set_destroy", "gx_create", "gx_destr
            "gx_nsdf_grad",
            "gx_nsdf_train", "gx_nsdf_counters", "gx_nsdf_step_predictions", "gx_autotune",
            "gx_column_info", "gx_column_spans", "gx_device_outputs", "gx_last_error",
-           "gx_scene_set_create_ex", "gx_scene_bytes", "gx_static_distance"]
+           "gx_scene_set_create_ex", "gx_scene_bytes", "gx_static_distance",
+           "gx_box_store_lists"]
 NSDF_PARAMS = 57985
 NSDF_FREQ = 32
 RASTER_COUNTERS = ["clusters_tested", "clusters_drawn", "tris_seen", "tris_front", "tris_expand",
@@ -134,6 +135,8 @@ def lib():
                                              P(GxSceneOptions), P(vp)]
         L.gx_scene_bytes.argtypes = [vp, C.c_int32, C.POINTER(C.c_uint64)]
         L.gx_static_distance.argtypes = [vp, C.c_int32, C.c_int32, vp, C.c_int32, vp, vp]
+        L.gx_box_store_lists.argtypes = [P(GxSceneDesc), C.POINTER(C.c_int32), vp, vp,
+                                         C.POINTER(C.c_uint64)]
         L.gx_scene_set_destroy.argtypes = [vp]
         L.gx_create.argtypes = [vp, P(GxRobot), P(GxConfig), P(vp)]
         L.gx_destroy.argtypes = [vp]
@@ -204,6 +207,41 @@ def robot_struct(r: _inputs.Robot) -> GxRobot:
     return g
 
 
+def scene_desc(s, keep):
+    """The C description of one scene (arrays kept alive in `keep`)."""
+    arrs = [np.ascontiguousarray(s.boxes, np.float32), np.ascontiguousarray(s.verts, np.float32),
+            np.ascontiguousarray(s.tris, np.int32), np.ascontiguousarray(s.tri_rgb, np.uint32),
+            np.ascontiguousarray(s.supports, np.float32)]
+    keep += arrs
+    b, v, t, c, sp = arrs
+    d = GxSceneDesc()
+    d.n_boxes, d.boxes = len(b), b.ctypes.data_as(f32p)
+    d.n_verts, d.verts = len(v), v.ctypes.data_as(f32p)
+    d.n_tris, d.tris, d.tri_rgb = len(t), t.ctypes.data_as(i32p), c.ctypes.data_as(u32p)
+    d.n_supports, d.supports = len(sp), sp.ctypes.data_as(f32p)
+    d.grid_origin[:] = [float(x) for x in s.grid_origin]
+    d.grid_h = float(s.grid_h)
+    d.grid_dims[:] = [int(x) for x in s.grid_dims]
+    d.spawn[:] = [float(x) for x in s.spawn]
+    return d
+
+
+def box_store_lists(scene):
+    """The box store's candidate lists of one scene, built on the host (no
+    device needed): (dims [3], offsets [cells + 1], box ids)."""
+    keep = []
+    d = scene_desc(scene, keep)
+    dims = (C.c_int32 * 3)()
+    n = C.c_uint64()
+    _check(lib().gx_box_store_lists(C.byref(d), dims, None, None, C.byref(n)))
+    cells = dims[0] * dims[1] * dims[2]
+    off = np.zeros(cells + 1, np.uint32)
+    ids = np.zeros(max(n.value, 1), np.uint16)
+    _check(lib().gx_box_store_lists(C.byref(d), dims, off.ctypes.data, ids.ctypes.data,
+                                    C.byref(n)))
+    return np.array(list(dims)), off, ids[:n.value]
+
+
 class SceneSet:
     """Device copies of a list of scenes (grid, clusters, supports)."""
 
@@ -213,20 +251,7 @@ class SceneSet:
         n = len(scenes)
         descs = (GxSceneDesc * n)()
         for i, s in enumerate(scenes):
-            arrs = [np.ascontiguousarray(s.boxes, np.float32), np.ascontiguousarray(s.verts, np.float32),
-                    np.ascontiguousarray(s.tris, np.int32), np.ascontiguousarray(s.tri_rgb, np.uint32),
-                    np.ascontiguousarray(s.supports, np.float32)]
-            self._keep += arrs
-            b, v, t, c, sp = arrs
-            d = descs[i]
-            d.n_boxes, d.boxes = len(b), b.ctypes.data_as(f32p)
-            d.n_verts, d.verts = len(v), v.ctypes.data_as(f32p)
-            d.n_tris, d.tris, d.tri_rgb = len(t), t.ctypes.data_as(i32p), c.ctypes.data_as(u32p)
-            d.n_supports, d.supports = len(sp), sp.ctypes.data_as(f32p)
-            d.grid_origin[:] = [float(x) for x in s.grid_origin]
-            d.grid_h = float(s.grid_h)
-            d.grid_dims[:] = [int(x) for x in s.grid_dims]
-            d.spawn[:] = [float(x) for x in s.spawn]
+            descs[i] = scene_desc(s, self._keep)
         mv, mt = obj_mesh if obj_mesh is not None else _inputs.icosahedron()
         mv = np.ascontiguousarray(mv, np.float32)
         mt = np.ascontiguousarray(mt, np.int32)
