@@ -237,7 +237,8 @@ typedef struct {
                               FP64 node value for coordinates up to 20 m;
                               about 0.1% of the dense grid's bytes, so a scene
                               set created without dense grids
-                              (gx_scene_set_create_ex) can serve it           */
+                              (gx_scene_set_create_ex) can serve it; not with
+                              fused_step (GX_EINVAL)                          */
 } gx_config;
 
 /* Outputs of one step, device memory owned by the caller (e.g. torch

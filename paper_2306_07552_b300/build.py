@@ -7,7 +7,7 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 SO = os.path.join(HERE, "libgx.so")
-SOURCES = ["gx_api.cu", "gx_physics.cu", "gx_physics_store.cu", "gx_boxes.cu", "gx_raster.cu", "gx_fused.cu", "gx_grid.cu", "gx_nsdf.cu",
+SOURCES = ["gx_api.cu", "gx_physics.cu", "gx_physics_store.cu", "gx_boxes.cu", "gx_boxes_store.cu", "gx_raster.cu", "gx_fused.cu", "gx_grid.cu", "gx_nsdf.cu",
            "gx_nsdf_train.cu", "gx_meshlets.cpp", "gx_store.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -610,10 +610,9 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
                 "(no heuristics, broad-phase, robot-body rendering or other static test)");
   if (c.static_store < 0 || c.static_store > 1)
     return fail(nullptr, GX_EINVAL, "static_store must be 0 or 1");
-  if (c.static_store == 1 && (c.fused_step || c.object_boxes))
+  if (c.static_store == 1 && c.fused_step)
     return fail(nullptr, GX_EINVAL,
-                "static_store 1: not with fused_step or object_boxes (their kernels read the "
-                "dense grid)");
+                "static_store 1: not with fused_step (its kernel reads the dense grid)");
   if (c.static_store == 0 && !set->dense)
     return fail(nullptr, GX_EINVAL,
                 "static_store 0 needs the dense grid, which this scene set was created without");

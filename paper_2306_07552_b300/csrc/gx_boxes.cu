@@ -24,6 +24,17 @@
 //     no box placed before it; then the robot base as in the sphere model.
 #include <math_constants.h>
 
+// Compiled twice: as itself (dense grid) and, through gx_boxes_store.cu, with
+// GX_STATIC_STORE 1 (box store), whose launchers carry the suffix _store.
+#ifndef GX_STATIC_STORE
+#define GX_STATIC_STORE 0
+#endif
+#if GX_STATIC_STORE == 1
+#define GX_BOX_LAUNCHER(name) name##_store
+#else
+#define GX_BOX_LAUNCHER(name) name
+#endif
+
 #include "gx_internal.h"
 #include "gx_device.cuh"
 #include "gx_kin.cuh"
@@ -529,12 +540,24 @@ __global__ void __launch_bounds__(32 * kBoxEnvsPerBlock) reset_box_kernel(const 
 
 }  // namespace
 
-void launch_physics_boxes(const PhysicsParams& p, cudaStream_t s) {
+void GX_BOX_LAUNCHER(launch_physics_boxes)(const PhysicsParams& p, cudaStream_t s) {
+#if GX_STATIC_STORE == 0
+  if (p.store) {
+    launch_physics_boxes_store(p, s);
+    return;
+  }
+#endif
   const int blocks = (p.n + kBoxEnvsPerBlock - 1) / kBoxEnvsPerBlock;
   physics_box_kernel<<<blocks, 32 * kBoxEnvsPerBlock, 0, s>>>(p);
 }
 
-void launch_reset_boxes(const ResetParams& p, cudaStream_t s) {
+void GX_BOX_LAUNCHER(launch_reset_boxes)(const ResetParams& p, cudaStream_t s) {
+#if GX_STATIC_STORE == 0
+  if (p.store) {
+    launch_reset_boxes_store(p, s);
+    return;
+  }
+#endif
   if (p.n <= 0) return;
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);

@@ -258,7 +258,9 @@ struct FusedParams {
 cudaError_t fused_configure();
 cudaError_t fused_max_ctas(int* ctas);
 cudaError_t launch_fused_step(const FusedParams& f, int ctas, cudaStream_t s);
-void launch_reset_boxes(const ResetParams& p, cudaStream_t s);
+void launch_reset_boxes(const ResetParams& p, cudaStream_t s);         // dispatches on p.store
+void launch_physics_boxes_store(const PhysicsParams& p, cudaStream_t s);  // box-store kernels
+void launch_reset_boxes_store(const ResetParams& p, cudaStream_t s);
 cudaError_t reset_configure();
 void launch_raster(const RasterParams& p, cudaStream_t s);
 // ---------------------------------------------------------------------------

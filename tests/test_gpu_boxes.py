@@ -3,7 +3,8 @@ Details") against the FP64 oracle, lockstep: resets that place boxes on
 support tops, steps whose robot spheres meet boxes, grasps that carry a box
 as eight spheres turning with the tool, releases that stand it upright on the
 highest landing of its bottom spheres or restore it, and the images of boxes
-resting and carried.  Same tolerances as the sphere model."""
+resting and carried.  Same tolerances as the sphere model.  Run on the dense
+grid and on the box store (a scene set without its dense grid)."""
 import math
 
 import numpy as np
@@ -25,9 +26,12 @@ def room():
     build.build()
     scene = I.room_scene(1000, 2000)
     ss = gx.SceneSet([scene])
+    # the same scene without its dense grid: the box store serves every static test
+    lean = gx.SceneSet([scene], dense_grid=False, column_grid=False)
     orc = O.Oracle(ROBOT, scene, I.unit_cube(), I.object_colors(256))
-    yield gx, scene, ss, orc
+    yield gx, scene, {0: ss, 1: lean}, orc
     ss.close()
+    lean.close()
 
 
 def _check_resets(sim, orc, before, M, seed, rho):
@@ -65,12 +69,13 @@ def _lockstep(sim, orc, acts, M, W, tally, image_envs):
             check_image(orc, after, out, e, W, W, M, tally, boxes=True)
 
 
-def test_box_resets_and_random_steps(room):
-    gx, scene, ss, orc = room
+@pytest.mark.parametrize("store", [0, 1])
+def test_box_resets_and_random_steps(room, store):
+    gx, scene, sets, orc = room
     n, M, W = 48, 12, 64
     rho = (0.03, 0.06)
-    sim = gx.Sim(ss, ROBOT, n, img=(W, W), n_objects=M, obj_radius=rho, seed=5,
-                 object_boxes=True)
+    sim = gx.Sim(sets[store], ROBOT, n, img=(W, W), n_objects=M, obj_radius=rho, seed=5,
+                 object_boxes=True, static_store=store)
     before = {k: v.copy() for k, v in sim.state_arrays().items()}
     sim.reset()
     torch.cuda.synchronize()
@@ -117,11 +122,12 @@ def _box_at_tip(sim, orc, M):
     sim.load_state(buf)
 
 
-def test_box_grasp_carry_release(room):
-    gx, scene, ss, orc = room
+@pytest.mark.parametrize("store", [0, 1])
+def test_box_grasp_carry_release(room, store):
+    gx, scene, sets, orc = room
     n, M, W = 32, 8, 64
-    sim = gx.Sim(ss, ROBOT, n, img=(W, W), n_objects=M, obj_radius=(0.03, 0.06), seed=9,
-                 object_boxes=True)
+    sim = gx.Sim(sets[store], ROBOT, n, img=(W, W), n_objects=M, obj_radius=(0.03, 0.06),
+                 seed=9, object_boxes=True, static_store=store)
     sim.reset()
     torch.cuda.synchronize()
     _box_at_tip(sim, orc, M)
@@ -144,7 +150,8 @@ def test_box_grasp_carry_release(room):
 
 
 def test_box_configurations_refused(room):
-    gx, scene, ss, orc = room
+    gx, scene, sets, orc = room
+    ss = sets[0]
     for kw in (dict(heuristics=1), dict(broadphase=True), dict(render_robot=True),
                dict(sdf_mode=2)):
         with pytest.raises(gx.GxError):
