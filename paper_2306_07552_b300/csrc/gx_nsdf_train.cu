@@ -535,11 +535,15 @@ struct AdamParams {
   float* loss_out;     // optional
 };
 
-// A block of 8 warps takes 32 consecutive parameters: warp w sums the
-// partials c = w, w + 8, ... (coalesced rows), then warp 0 adds the eight sums
-// in order and applies Adam; the order is fixed, so the result is deterministic.
+// A block of 8 warps takes 32 consecutive parameters of a hidden layer: warp
+// w sums the partials c = w, w + 8, ... (coalesced rows), then warp 0 adds the
+// eight sums in order and applies Adam; the output row's blocks take 8
+// parameters each (below).  Every order is fixed, so the result is
+// deterministic.
 constexpr int kAdamParamsPerBlock = 32;
 constexpr int kAdamWarps = 8;
+constexpr int kAdamHiddenBlocks = kOffW5 / kAdamParamsPerBlock;  // W1..W4, b1..b4
+constexpr int kAdamOutBlocks = (kNsdfParams - kOffW5 + 7) / 8;      // W5, b5: 8 per block
 static_assert(off_w(1) % kAdamParamsPerBlock == 0 && off_w(2) % kAdamParamsPerBlock == 0 &&
                   off_w(3) % kAdamParamsPerBlock == 0 && kOffW5 % kAdamParamsPerBlock == 0,
               "a block of parameters lies in one layer");
@@ -547,32 +551,61 @@ static_assert(off_w(1) % kAdamParamsPerBlock == 0 && off_w(2) % kAdamParamsPerBl
 __global__ void __launch_bounds__(32 * kAdamWarps) nsdf_adam_kernel(const AdamParams p) {
   __shared__ float sums[kAdamWarps][kAdamParamsPerBlock];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i = blockIdx.x * kAdamParamsPerBlock + lane;
-  if (blockIdx.x == 0 && threadIdx.x == 0 && p.loss_out) {
+  if (blockIdx.x == 0 && p.loss_out) {
+    // the loss over all partials: each thread a fixed strided share, then a
+    // fixed-order tree in shared memory (one thread walking the partials
+    // serially took most of the kernel's time)
+    __shared__ float lsum[32 * kAdamWarps];
     float s = 0.f;
-    for (int c = 0; c < p.n_part5; ++c) s += p.part5[(size_t)c * kPart5 + 129];
-    *p.loss_out = s * p.inv_n;
+    for (int c = threadIdx.x; c < p.n_part5; c += 32 * kAdamWarps)
+      s += p.part5[(size_t)c * kPart5 + 129];
+    lsum[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 16 * kAdamWarps; w > 0; w >>= 1) {
+      if (threadIdx.x < w) lsum[threadIdx.x] += lsum[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) *p.loss_out = lsum[0] * p.inv_n;
   }
-  // unrolled so that several rows' loads are in flight before their sums
-  float part = 0.f;
-  if (i < kOffW5) {
+  float g = 0.f;
+  int i = blockIdx.x * kAdamParamsPerBlock + lane;
+  if (blockIdx.x < kAdamHiddenBlocks) {
+    // unrolled so that several rows' loads are in flight before their sums;
     // the layer of this block's 32 parameters (layer offsets are multiples of 32)
+    float part = 0.f;
     int l = 3;
     while (l > 0 && blockIdx.x * kAdamParamsPerBlock < off_w(l)) --l;
 #pragma unroll 8
     for (int c = p.groups.first[l] + warp; c < p.groups.first[l + 1]; c += kAdamWarps)
       part += p.part[(size_t)c * kPartStride + i];
-  } else if (i < kNsdfParams) {
-#pragma unroll 8
-    for (int c = warp; c < p.n_part5; c += kAdamWarps)
-      part += p.part5[(size_t)c * kPart5 + (i - kOffW5)];
-  }
-  sums[warp][lane] = part;
-  __syncthreads();
-  if (warp != 0 || i >= kNsdfParams) return;
-  float g = 0.f;
+    sums[warp][lane] = part;
+    __syncthreads();
+    if (warp != 0) return;
 #pragma unroll
-  for (int w = 0; w < kAdamWarps; ++w) g += sums[w][lane];
+    for (int w = 0; w < kAdamWarps; ++w) g += sums[w][lane];
+  } else {
+    // output row and b5: every CTA of the forward kernel left 4 partials, so
+    // a block takes 8 parameters and 32 threads share each one's partials
+    // (thread t: parameter t % 8, partials t / 8, t / 8 + 32, ...), then a
+    // fixed-order tree over the 32 shares
+    __shared__ float red[32 * kAdamWarps];
+    const int k = threadIdx.x & 7;
+    i = kOffW5 + (blockIdx.x - kAdamHiddenBlocks) * 8 + k;
+    float part = 0.f;
+    if (i < kNsdfParams) {
+#pragma unroll 4
+      for (int c = threadIdx.x >> 3; c < p.n_part5; c += 4 * kAdamWarps)
+        part += p.part5[(size_t)c * kPart5 + (i - kOffW5)];
+    }
+    red[threadIdx.x] = part;
+    __syncthreads();
+    for (int w = 16 * kAdamWarps; w >= 8; w >>= 1) {
+      if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x >= 8 || i >= kNsdfParams) return;
+    g = red[threadIdx.x];
+  }
   if (p.grad_out) p.grad_out[i] = g;
   if (!p.master) return;
   const float m = p.beta1 * p.m[i] + (1.f - p.beta1) * g;
@@ -689,8 +722,7 @@ cudaError_t grad_and_update(unsigned char* blob, const float* pts, const float* 
   ap.n_part5 = w.g1 * 4;
   ap.inv_n = 1.f / (float)n;
   ap.blob = blob;
-  nsdf_adam_kernel<<<(kNsdfParams + kAdamParamsPerBlock - 1) / kAdamParamsPerBlock,
-                     32 * kAdamWarps, 0, s>>>(ap);
+  nsdf_adam_kernel<<<kAdamHiddenBlocks + kAdamOutBlocks, 32 * kAdamWarps, 0, s>>>(ap);
   return cudaGetLastError();
 }
 
