@@ -583,6 +583,18 @@ gx_status gx_render_noalloc(const gx_scene_set* set, int32_t n, const int32_t* e
 #define GX_NOALLOC_BAD_SCENE 0x200u
 gx_status gx_render_noalloc_error(uint32_t* bits);
 
+/* Caps the device memory this library allocates -- scene sets, contexts,
+ * training workspaces, on every device, for the whole process -- at `bytes`
+ * (0: no cap, the default).  An allocation that would pass the cap fails as
+ * an exhausted device would: the call returns GX_ENOMEM and releases what it
+ * had allocated.  Memory already held keeps counting.  For embedders that
+ * give the library a memory budget, and to exercise the out-of-memory paths
+ * without exhausting a shared GPU.  Thread-safe; touches no device. */
+void gx_set_device_memory_cap(uint64_t bytes);
+/* Device bytes the library holds now (every allocation it made and has not
+ * freed).  Thread-safe; touches no device. */
+uint64_t gx_device_memory_in_use(void);
+
 const char* gx_last_error(const gx_ctx* ctx);
 
 #ifdef __cplusplus

@@ -4,7 +4,9 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <mutex>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "gx_internal.h"
@@ -14,6 +16,11 @@ using namespace gx;
 namespace {
 
 thread_local std::string g_last_error;
+
+// Device bytes the library holds, per allocation, and the optional cap.
+std::mutex g_mem_mu;
+std::unordered_map<void*, size_t> g_mem_sizes;
+uint64_t g_mem_in_use = 0, g_mem_cap = 0;
 
 struct DevBuf {
   void* p = nullptr;
@@ -111,11 +118,52 @@ gx_status fail(gx_ctx* c, gx_status s, const char* fmt, ...) {
                   #call, cudaGetErrorString(e_));                                         \
   } while (0)
 
+}  // namespace
+
+cudaError_t gx::dev_malloc_bytes(void** p, size_t bytes) {
+  *p = nullptr;
+  std::lock_guard<std::mutex> lock(g_mem_mu);
+  if (g_mem_cap && g_mem_in_use + bytes > g_mem_cap) return cudaErrorMemoryAllocation;
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return e;
+  }
+  g_mem_sizes[*p] = bytes;
+  g_mem_in_use += bytes;
+  return cudaSuccess;
+}
+
+void gx::dev_free(void* p) {
+  if (!p) return;
+  {
+    std::lock_guard<std::mutex> lock(g_mem_mu);
+    auto it = g_mem_sizes.find(p);
+    if (it != g_mem_sizes.end()) {
+      g_mem_in_use -= it->second;
+      g_mem_sizes.erase(it);
+    }
+  }
+  cudaFree(p);
+}
+
+extern "C" void gx_set_device_memory_cap(uint64_t bytes) {
+  std::lock_guard<std::mutex> lock(g_mem_mu);
+  g_mem_cap = bytes;
+}
+
+extern "C" uint64_t gx_device_memory_in_use(void) {
+  std::lock_guard<std::mutex> lock(g_mem_mu);
+  return g_mem_in_use;
+}
+
+namespace {
+
 template <class T>
 cudaError_t upload(gx_scene_set* s, T** dst, const T* src, size_t count) {
   *dst = nullptr;
   if (count == 0) return cudaSuccess;
-  cudaError_t e = cudaMalloc((void**)dst, count * sizeof(T));
+  cudaError_t e = dev_malloc((void**)dst, count * sizeof(T));
   if (e != cudaSuccess) return e;
   s->allocs.push_back(*dst);
   return cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice);
@@ -123,7 +171,7 @@ cudaError_t upload(gx_scene_set* s, T** dst, const T* src, size_t count) {
 
 void free_set(gx_scene_set* s) {
   if (!s) return;
-  for (void* p : s->allocs) cudaFree(p);
+  for (void* p : s->allocs) dev_free(p);
   nsdf_free(s);
   delete s;
 }
@@ -427,7 +475,7 @@ extern "C" gx_status gx_scene_set_create_ex(const gx_scene_desc* scenes, int32_t
     ds.grid = nullptr;
     if (s->dense) {
       float* grid = nullptr;
-      if ((e = cudaMalloc(&grid, nodes * sizeof(float))) != cudaSuccess) return bail(e, "grid");
+      if ((e = dev_malloc(&grid, nodes * sizeof(float))) != cudaSuccess) return bail(e, "grid");
       s->allocs.push_back(grid);
       launch_grid_build(grid, dboxes, d.n_boxes, ds.ox, ds.oy, ds.oz, ds.h, ds.nx, ds.ny, ds.nz, 0);
       if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "grid kernel");
@@ -475,9 +523,9 @@ extern "C" gx_status gx_scene_set_create_ex(const gx_scene_desc* scenes, int32_t
       uint32_t *cnt = nullptr, *off = nullptr;
       unsigned* ovf = nullptr;
       float2* spans = nullptr;
-      if ((e = cudaMalloc(&cnt, ncol * 4)) != cudaSuccess) return bail(e, "columns");
+      if ((e = dev_malloc(&cnt, ncol * 4)) != cudaSuccess) return bail(e, "columns");
       s->allocs.push_back(cnt);
-      if ((e = cudaMalloc(&ovf, 4)) != cudaSuccess) return bail(e, "columns");
+      if ((e = dev_malloc(&ovf, 4)) != cudaSuccess) return bail(e, "columns");
       s->allocs.push_back(ovf);
       cudaMemset(ovf, 0, 4);
       launch_column_build(dboxes, d.n_boxes, (double)ds.ox, (double)ds.oz, ylo, yhi, ds.ncx, ds.ncz,
@@ -497,7 +545,7 @@ extern "C" gx_status gx_scene_set_create_ex(const gx_scene_desc* scenes, int32_t
         return fail(nullptr, GX_EINVAL, "scene %d: too many column spans", i);
       }
       if ((e = upload(s, &off, ho.data(), ho.size())) != cudaSuccess) return bail(e, "columns");
-      if ((e = cudaMalloc(&spans, (acc ? acc : 1) * sizeof(float2))) != cudaSuccess)
+      if ((e = dev_malloc(&spans, (acc ? acc : 1) * sizeof(float2))) != cudaSuccess)
         return bail(e, "column spans");
       s->allocs.push_back(spans);
       launch_column_build(dboxes, d.n_boxes, (double)ds.ox, (double)ds.oz, ylo, yhi, ds.ncx, ds.ncz,
@@ -655,23 +703,23 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
   {
     // one framebuffer slot per resident rasteriser CTA, all keys "empty"
     const size_t fb_bytes = (size_t)x->n_slots * c.img_w * c.img_h * 8;
-    if ((e = cudaMalloc(&x->d_fb, fb_bytes)) != cudaSuccess) return bail(e, "fb slots");
+    if ((e = dev_malloc(&x->d_fb, fb_bytes)) != cudaSuccess) return bail(e, "fb slots");
     if ((e = cudaMemset(x->d_fb, 0xff, fb_bytes)) != cudaSuccess) return bail(e, "fb slots");
-    if ((e = cudaMalloc(&x->d_fb_epoch, x->n_slots * sizeof(uint32_t))) != cudaSuccess ||
+    if ((e = dev_malloc(&x->d_fb_epoch, x->n_slots * sizeof(uint32_t))) != cudaSuccess ||
         (e = cudaMemset(x->d_fb_epoch, 0, x->n_slots * sizeof(uint32_t))) != cudaSuccess)
       return bail(e, "fb epochs");
-    if ((e = cudaMalloc(&x->d_raster_work, sizeof(int))) != cudaSuccess) return bail(e, "work");
+    if ((e = dev_malloc(&x->d_raster_work, sizeof(int))) != cudaSuccess) return bail(e, "work");
     if ((e = cudaMemset(x->d_raster_work, 0, sizeof(int))) != cudaSuccess) return bail(e, "work");
   }
   Robot hr;
   hr.r = *robot;
-  if ((e = cudaMalloc(&x->d_robot, sizeof(Robot))) != cudaSuccess) return bail(e, "robot");
+  if ((e = dev_malloc(&x->d_robot, sizeof(Robot))) != cudaSuccess) return bail(e, "robot");
   if ((e = cudaMemcpy(x->d_robot, &hr, sizeof(Robot), cudaMemcpyHostToDevice)) != cudaSuccess)
     return bail(e, "robot");
   std::vector<int> es(x->n);
   for (int i = 0; i < x->n; ++i)
     es[i] = c.env_scene ? c.env_scene[i] : (int)((long long)i * set->n / x->n);
-  if ((e = cudaMalloc(&x->d_env_scene, x->n * sizeof(int))) != cudaSuccess) return bail(e, "map");
+  if ((e = dev_malloc(&x->d_env_scene, x->n * sizeof(int))) != cudaSuccess) return bail(e, "map");
   if ((e = cudaMemcpy(x->d_env_scene, es.data(), x->n * sizeof(int), cudaMemcpyHostToDevice)) !=
       cudaSuccess)
     return bail(e, "map");
@@ -686,7 +734,7 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
     off += (sizes[k] + 255) & ~(size_t)255;
   }
   x->state_bytes = off;
-  if ((e = cudaMalloc(&x->d_state, off)) != cudaSuccess) return bail(e, "state");
+  if ((e = dev_malloc(&x->d_state, off)) != cudaSuccess) return bail(e, "state");
   if ((e = cudaMemset(x->d_state, 0, off)) != cudaSuccess) return bail(e, "state");
   char* b = (char*)x->d_state;
   x->st.bx = (float*)(b + x->off[0]);
@@ -703,7 +751,7 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
   x->st.obox = (float4*)(b + x->off[11]);
   x->st.roff = (float*)(b + x->off[12]);
   if (c.object_boxes &&
-      ((e = cudaMalloc(&x->d_held_M, n * 3 * sizeof(float4))) != cudaSuccess ||
+      ((e = dev_malloc(&x->d_held_M, n * 3 * sizeof(float4))) != cudaSuccess ||
        (e = cudaMemset(x->d_held_M, 0, n * 3 * sizeof(float4))) != cudaSuccess))
     return bail(e, "held box rotation");
   if (c.occlusion_cull) {
@@ -711,7 +759,7 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
     for (int sc = 0; sc < set->n; ++sc) mmax = std::max(mmax, set->meshlets_per_scene[sc]);
     x->vis_words = (mmax + 31) / 32;
     const size_t bytes = n * (size_t)x->vis_words * sizeof(uint32_t);
-    if ((e = cudaMalloc(&x->d_vis, bytes)) != cudaSuccess ||
+    if ((e = dev_malloc(&x->d_vis, bytes)) != cudaSuccess ||
         (e = cudaMemset(x->d_vis, 0, bytes)) != cudaSuccess)
       return bail(e, "visibility bits");
     x->occlusion = true;
@@ -721,31 +769,31 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
   if (c.fused_step) {
     if ((e = fused_max_ctas(&x->fused_ctas)) != cudaSuccess) return bail(e, "fused config");
     const size_t ctas = (size_t)std::max(x->fused_ctas, x->n_slots);
-    if ((e = cudaMalloc(&x->d_fused_scratch, ctas * kFusedResetScratch * sizeof(float4))) !=
+    if ((e = dev_malloc(&x->d_fused_scratch, ctas * kFusedResetScratch * sizeof(float4))) !=
             cudaSuccess ||
-        (e = cudaMalloc(&x->d_fused_obj, ctas * 8 * GX_MAX_OBJECTS * sizeof(float4))) !=
+        (e = dev_malloc(&x->d_fused_obj, ctas * 8 * GX_MAX_OBJECTS * sizeof(float4))) !=
             cudaSuccess ||
-        (e = cudaMalloc(&x->d_barrier, 2 * sizeof(unsigned))) != cudaSuccess ||
+        (e = dev_malloc(&x->d_barrier, 2 * sizeof(unsigned))) != cudaSuccess ||
         (e = cudaMemset(x->d_barrier, 0, 2 * sizeof(unsigned))) != cudaSuccess)
       return bail(e, "fused step scratch");
   }
   if ((e = cudaMemset(x->st.held, 0xff, n * 4)) != cudaSuccess) return bail(e, "state");
-  if ((e = cudaMalloc(&x->d_cam, n * 12 * sizeof(float))) != cudaSuccess) return bail(e, "cam");
+  if ((e = dev_malloc(&x->d_cam, n * 12 * sizeof(float))) != cudaSuccess) return bail(e, "cam");
   if ((e = cudaMemset(x->d_cam, 0, n * 12 * sizeof(float))) != cudaSuccess) return bail(e, "cam");
   if (c.broadphase) {
     for (int sc = 0; sc < set->n; ++sc)
       x->bp_cells = std::max(x->bp_cells, set->host[sc].bp_nx * set->host[sc].bp_nz);
     const size_t bytes = n * 4 * (size_t)x->bp_cells * sizeof(BpCell);
-    if ((e = cudaMalloc(&x->d_bp, bytes)) != cudaSuccess ||
+    if ((e = dev_malloc(&x->d_bp, bytes)) != cudaSuccess ||
         (e = cudaMemset(x->d_bp, 0, bytes)) != cudaSuccess)
       return bail(e, "broad-phase");
   }
   if (c.render_robot) {
-    if ((e = cudaMalloc(&x->d_robot_sph, n * 32 * sizeof(float4))) != cudaSuccess ||
+    if ((e = dev_malloc(&x->d_robot_sph, n * 32 * sizeof(float4))) != cudaSuccess ||
         (e = cudaMemset(x->d_robot_sph, 0, n * 32 * sizeof(float4))) != cudaSuccess)
       return bail(e, "robot spheres");
   }
-  if ((e = cudaMalloc(&x->d_err, sizeof(unsigned))) != cudaSuccess) return bail(e, "err");
+  if ((e = dev_malloc(&x->d_err, sizeof(unsigned))) != cudaSuccess) return bail(e, "err");
   if ((e = cudaMemset(x->d_err, 0, sizeof(unsigned))) != cudaSuccess) return bail(e, "err");
   if ((e = cudaMallocHost(&x->h_err, sizeof(unsigned))) != cudaSuccess) return bail(e, "err");
   *x->h_err = 0;
@@ -765,7 +813,7 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
       hi = std::max(hi, ms[es[i]]);
     }
     x->order_mode = c.raster_order ? c.raster_order - 1 : (hi > 1.5 * lo ? 1 : 0);
-    if ((e = cudaMalloc(&x->d_order, n * sizeof(int))) != cudaSuccess ||
+    if ((e = dev_malloc(&x->d_order, n * sizeof(int))) != cudaSuccess ||
         (e = cudaMemcpy(x->d_order, ord.data(), n * sizeof(int), cudaMemcpyHostToDevice)) !=
             cudaSuccess)
       return bail(e, "work order");
@@ -790,12 +838,12 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
     std::vector<const unsigned char*> blobs(set->n, nullptr);
     for (int sc = 0; sc < set->n && sc < (int)set->nsdf.size(); ++sc) blobs[sc] = set->nsdf[sc].blob;
     x->n_nsdf_tiles = (int)tiles.size();
-    if ((e = cudaMalloc(&x->d_nsdf_pts, n * 32 * sizeof(float4))) != cudaSuccess ||
-        (e = cudaMalloc(&x->d_nsdf_d, n * 32 * sizeof(float))) != cudaSuccess ||
+    if ((e = dev_malloc(&x->d_nsdf_pts, n * 32 * sizeof(float4))) != cudaSuccess ||
+        (e = dev_malloc(&x->d_nsdf_d, n * 32 * sizeof(float))) != cudaSuccess ||
         (e = cudaMemset(x->d_nsdf_d, 0xff, n * 32 * sizeof(float))) != cudaSuccess ||  // NaN
-        (e = cudaMalloc(&x->d_nsdf_tiles, tiles.size() * sizeof(int4))) != cudaSuccess ||
-        (e = cudaMalloc(&x->d_nsdf_perm, n * sizeof(int))) != cudaSuccess ||
-        (e = cudaMalloc(&x->d_nsdf_blobs, set->n * sizeof(void*))) != cudaSuccess ||
+        (e = dev_malloc(&x->d_nsdf_tiles, tiles.size() * sizeof(int4))) != cudaSuccess ||
+        (e = dev_malloc(&x->d_nsdf_perm, n * sizeof(int))) != cudaSuccess ||
+        (e = dev_malloc(&x->d_nsdf_blobs, set->n * sizeof(void*))) != cudaSuccess ||
         (e = cudaMemcpy(x->d_nsdf_tiles, tiles.data(), tiles.size() * sizeof(int4),
                         cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(x->d_nsdf_perm, perm.data(), n * sizeof(int), cudaMemcpyHostToDevice)) !=
@@ -804,13 +852,13 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
                         cudaMemcpyHostToDevice)) != cudaSuccess)
       return bail(e, "neural SDF buffers");
     if (c.profile & 4) {
-      if ((e = cudaMalloc(&x->d_nsdf_counters, kNsdfCounters * 8)) != cudaSuccess ||
+      if ((e = dev_malloc(&x->d_nsdf_counters, kNsdfCounters * 8)) != cudaSuccess ||
           (e = cudaMemset(x->d_nsdf_counters, 0, kNsdfCounters * 8)) != cudaSuccess)
         return bail(e, "neural SDF counters");
     }
   }
   if (c.profile & 2) {
-    if ((e = cudaMalloc(&x->d_counters, kRasterCounters * 8)) != cudaSuccess)
+    if ((e = dev_malloc(&x->d_counters, kRasterCounters * 8)) != cudaSuccess)
       return bail(e, "counters");
     if ((e = cudaMemset(x->d_counters, 0, kRasterCounters * 8)) != cudaSuccess)
       return bail(e, "counters");
@@ -823,33 +871,33 @@ extern "C" void gx_destroy(gx_ctx* x) {
   if (!x) return;
   cudaDeviceSynchronize();
   if (x->gexec) cudaGraphExecDestroy(x->gexec);
-  cudaFree(x->d_robot);
-  cudaFree(x->d_env_scene);
-  cudaFree(x->d_held_M);
-  cudaFree(x->d_vis);
-  cudaFree(x->d_fused_scratch);
-  cudaFree(x->d_fused_obj);
-  cudaFree(x->d_barrier);
-  cudaFree(x->d_state);
-  cudaFree(x->d_cam);
-  cudaFree(x->d_fb);
-  cudaFree(x->d_fb_epoch);
-  cudaFree(x->d_raster_work);
-  cudaFree(x->d_err);
+  dev_free(x->d_robot);
+  dev_free(x->d_env_scene);
+  dev_free(x->d_held_M);
+  dev_free(x->d_vis);
+  dev_free(x->d_fused_scratch);
+  dev_free(x->d_fused_obj);
+  dev_free(x->d_barrier);
+  dev_free(x->d_state);
+  dev_free(x->d_cam);
+  dev_free(x->d_fb);
+  dev_free(x->d_fb_epoch);
+  dev_free(x->d_raster_work);
+  dev_free(x->d_err);
   if (x->h_err) cudaFreeHost(x->h_err);
   for (cudaEvent_t e : x->prof_ev) cudaEventDestroy(e);
-  cudaFree(x->d_counters);
-  cudaFree(x->d_order);
-  cudaFree(x->d_robot_sph);
-  cudaFree(x->d_bp);
-  cudaFree(x->d_nsdf_pts);
-  cudaFree(x->d_nsdf_d);
-  cudaFree(x->d_nsdf_tiles);
-  cudaFree(x->d_nsdf_perm);
-  cudaFree((void*)x->d_nsdf_blobs);
-  cudaFree(x->d_nsdf_counters);
+  dev_free(x->d_counters);
+  dev_free(x->d_order);
+  dev_free(x->d_robot_sph);
+  dev_free(x->d_bp);
+  dev_free(x->d_nsdf_pts);
+  dev_free(x->d_nsdf_d);
+  dev_free(x->d_nsdf_tiles);
+  dev_free(x->d_nsdf_perm);
+  dev_free((void*)x->d_nsdf_blobs);
+  dev_free(x->d_nsdf_counters);
   if (x->ev_err) cudaEventDestroy(x->ev_err);
-  for (void* p : x->host_step_allocs) cudaFree(p);
+  for (void* p : x->host_step_allocs) dev_free(p);
   delete x;
 }
 
@@ -945,7 +993,7 @@ extern "C" gx_status gx_step_host(gx_ctx* x, const float* actions_host, const gx
   const size_t dbytes = n * px * (x->cfg.depth_fp16 ? 2 : 4);
   if (!x->h2d_actions) {
     auto alloc = [&](void** p, size_t bytes) {
-      cudaError_t e = cudaMalloc(p, bytes);
+      cudaError_t e = dev_malloc(p, bytes);
       if (e == cudaSuccess) x->host_step_allocs.push_back(*p);
       return e;
     };
@@ -1099,8 +1147,8 @@ extern "C" gx_status gx_autotune(gx_ctx* x, const float* actions, const gx_outpu
   cudaStream_t s = (cudaStream_t)stream;
   // the candidates run from the same state, restored after each one
   void* saved = nullptr;
-  CK(x, cudaMalloc(&saved, x->state_bytes));
-  auto release = [&] { cudaFree(saved); };
+  CK(x, dev_malloc(&saved, x->state_bytes));
+  auto release = [&] { dev_free(saved); };
   if (cudaMemcpyAsync(saved, x->d_state, x->state_bytes, cudaMemcpyDeviceToDevice, s) !=
       cudaSuccess) {
     release();

@@ -359,6 +359,17 @@ void launch_grid_build(float* grid, const float* boxes, int n_boxes, float ox, f
 cudaError_t launch_static_distance(const DScene* scenes, int scene, const float* pts, int n,
                                    float* dist, cudaStream_t s);
 
+// Device allocations of the library: cudaMalloc / cudaFree with the bytes
+// counted against the optional cap of gx_set_device_memory_cap (an
+// allocation past it fails with cudaErrorMemoryAllocation, which every
+// caller maps to GX_ENOMEM).
+cudaError_t dev_malloc_bytes(void** p, size_t bytes);
+void dev_free(void* p);
+template <class T>
+cudaError_t dev_malloc(T** p, size_t bytes) {
+  return dev_malloc_bytes(reinterpret_cast<void**>(p), bytes);
+}
+
 // device error bits beyond the public ones
 constexpr unsigned kErrWaitTimeout = 0x100u;  // a bounded mbarrier wait gave up
 constexpr unsigned kErrBadScene = 0x200u;     // a scene index outside the set (env drawn empty)

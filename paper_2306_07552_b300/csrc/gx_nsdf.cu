@@ -331,8 +331,8 @@ size_t query_smem_bytes() { return sizeof(QuerySmem) + 1024; }
 
 void nsdf_free(gx_scene_set* s) {
   for (NsdfScene& ns : s->nsdf) {
-    cudaFree(ns.blob);
-    cudaFree(ns.master);
+    dev_free(ns.blob);
+    dev_free(ns.master);
     ns = NsdfScene();
   }
 }
@@ -389,9 +389,9 @@ extern "C" gx_status gx_nsdf_set_weights(gx_scene_set* set, int32_t scene, const
   if (scene < 0 || scene >= set->n) return set_last_error(GX_EINVAL, "gx_nsdf_set_weights: scene");
   if ((int)set->nsdf.size() != set->n) set->nsdf.resize(set->n);
   NsdfScene& ns = set->nsdf[scene];
-  if (!ns.blob && cudaMalloc(&ns.blob, kNsdfBlobBytes) != cudaSuccess)
+  if (!ns.blob && dev_malloc(&ns.blob, kNsdfBlobBytes) != cudaSuccess)
     return set_last_error(GX_ENOMEM, "gx_nsdf_set_weights: allocation failed");
-  if (!ns.master && cudaMalloc(&ns.master, (size_t)kNsdfParams * 4) != cudaSuccess)
+  if (!ns.master && dev_malloc(&ns.master, (size_t)kNsdfParams * 4) != cudaSuccess)
     return set_last_error(GX_ENOMEM, "gx_nsdf_set_weights: allocation failed");
   if (cudaMemcpy(ns.master, params, (size_t)kNsdfParams * 4, cudaMemcpyHostToDevice) != cudaSuccess)
     return set_last_error(GX_ECUDA, "gx_nsdf_set_weights: copy failed");

@@ -674,22 +674,22 @@ struct Work {
     g2 = 4 * tiles < sms ? 4 * tiles : sms;  // at least one CTA per layer
     void* a = nullptr;
     cudaError_t e;
-    if ((e = cudaMalloc(&a, (size_t)tiles * kActTile)) != cudaSuccess) return e;
+    if ((e = dev_malloc(&a, (size_t)tiles * kActTile)) != cudaSuccess) return e;
     owned.push_back(a);
     act = (unsigned char*)a;
-    if ((e = cudaMalloc(&a, (size_t)g2 * kPartStride * 4)) != cudaSuccess) return e;
+    if ((e = dev_malloc(&a, (size_t)g2 * kPartStride * 4)) != cudaSuccess) return e;
     owned.push_back(a);
     part = (float*)a;
-    if ((e = cudaMalloc(&a, (size_t)g1 * 4 * kPart5 * 4)) != cudaSuccess) return e;
+    if ((e = dev_malloc(&a, (size_t)g1 * 4 * kPart5 * 4)) != cudaSuccess) return e;
     owned.push_back(a);
     part5 = (float*)a;
-    if ((e = cudaMalloc(&a, 16)) != cudaSuccess) return e;
+    if ((e = dev_malloc(&a, 16)) != cudaSuccess) return e;
     owned.push_back(a);
     err = (unsigned*)a;
     return cudaMemset(err, 0, 16);
   }
   ~Work() {
-    for (void* a : owned) cudaFree(a);
+    for (void* a : owned) dev_free(a);
   }
 };
 
@@ -808,16 +808,16 @@ extern "C" gx_status gx_nsdf_train(gx_scene_set* set, int32_t scene, const gx_tr
     return set_last_error(GX_ENOMEM, "gx_nsdf_train: allocation");
   float *pts = nullptr, *labels = nullptr, *mv = nullptr, *loss = nullptr;
   auto release = [&] {
-    cudaFree(pts);
-    cudaFree(labels);
-    cudaFree(mv);
-    cudaFree(loss);
+    dev_free(pts);
+    dev_free(labels);
+    dev_free(mv);
+    dev_free(loss);
   };
   const long long N = tp->n_samples;
-  if (cudaMalloc(&pts, (size_t)N * 12) != cudaSuccess ||
-      cudaMalloc(&labels, (size_t)N * 4) != cudaSuccess ||
-      cudaMalloc(&mv, (size_t)2 * kNsdfParams * 4) != cudaSuccess ||
-      cudaMalloc(&loss, (size_t)(tp->steps > 0 ? tp->steps : 1) * 4) != cudaSuccess) {
+  if (dev_malloc(&pts, (size_t)N * 12) != cudaSuccess ||
+      dev_malloc(&labels, (size_t)N * 4) != cudaSuccess ||
+      dev_malloc(&mv, (size_t)2 * kNsdfParams * 4) != cudaSuccess ||
+      dev_malloc(&loss, (size_t)(tp->steps > 0 ? tp->steps : 1) * 4) != cudaSuccess) {
     release();
     return set_last_error(GX_ENOMEM, "gx_nsdf_train: allocation");
   }

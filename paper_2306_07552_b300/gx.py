@@ -37,7 +37,7 @@ SYMBOLS = ["gx_scene_set_create", "gx_scene_set_destroy", "gx_create", "gx_destr
            "gx_nsdf_train", "gx_nsdf_counters", "gx_nsdf_step_predictions", "gx_autotune",
            "gx_column_info", "gx_column_spans", "gx_device_outputs", "gx_last_error",
            "gx_scene_set_create_ex", "gx_scene_bytes", "gx_static_distance",
-           "gx_box_store_lists"]
+           "gx_box_store_lists", "gx_set_device_memory_cap", "gx_device_memory_in_use"]
 NSDF_PARAMS = 57985
 NSDF_FREQ = 32
 RASTER_COUNTERS = ["clusters_tested", "clusters_drawn", "tris_seen", "tris_front", "tris_expand",
@@ -174,6 +174,10 @@ def lib():
         L.gx_column_spans.restype = C.c_int32
         L.gx_autotune.argtypes = [vp, vp, P(GxOutputs), C.c_int32, P(GxTuneResult), vp]
         L.gx_nsdf_train.argtypes = [vp, C.c_int32, C.POINTER(GxTrainParams), vp, vp]
+        L.gx_set_device_memory_cap.argtypes = [C.c_uint64]
+        L.gx_set_device_memory_cap.restype = None
+        L.gx_device_memory_in_use.argtypes = []
+        L.gx_device_memory_in_use.restype = C.c_uint64
         L.gx_last_error.argtypes = [vp]
         L.gx_last_error.restype = C.c_char_p
         _lib = L
@@ -224,6 +228,16 @@ def scene_desc(s, keep):
     d.grid_dims[:] = [int(x) for x in s.grid_dims]
     d.spawn[:] = [float(x) for x in s.spawn]
     return d
+
+
+def set_device_memory_cap(nbytes):
+    """Caps the device bytes the library may hold (0: no cap)."""
+    lib().gx_set_device_memory_cap(int(nbytes))
+
+
+def device_memory_in_use():
+    """Device bytes the library holds now."""
+    return int(lib().gx_device_memory_in_use())
 
 
 def box_store_lists(scene):
