@@ -432,6 +432,16 @@ typedef struct {
 gx_status gx_autotune(gx_ctx* ctx, const float* actions, const gx_outputs* out, int32_t steps,
                       gx_tune_result* best, void* stream);
 
+/* Applies a rasteriser setting found earlier by gx_autotune (for example one
+ * kept in a cache keyed by the configuration and the GPU) without timing
+ * anything: small_tri_px, order_costliest_first, raster_warps, raster_ctas
+ * and occlusion_cull are used, ms_per_step is ignored.  Images do not depend
+ * on the setting.  GX_EINVAL when the setting does not fit this context (a
+ * CTA shape it cannot use, more CTAs than that shape keeps resident, occlusion
+ * culling without the context's visibility bits).  Touches no device memory;
+ * a captured step graph is rebuilt at the next replay. */
+gx_status gx_apply_tune(gx_ctx* ctx, const gx_tune_result* setting);
+
 /* Neural-SDF decision counters accumulated since the previous call (profile
  * bit 2):
  * out[0] static tests made, out[1] of which the grid decided, out[2]

@@ -1230,6 +1230,33 @@ extern "C" gx_status gx_autotune(gx_ctx* x, const float* actions, const gx_outpu
   return poll_device_error(x, true);
 }
 
+extern "C" gx_status gx_apply_tune(gx_ctx* x, const gx_tune_result* t) {
+  if (!x || !t) return fail(x, GX_EINVAL, "gx_apply_tune: NULL argument");
+  const bool eight_only = x->cfg.fused_step || x->cfg.object_boxes;
+  if (t->small_tri_px < 0 || (t->order_costliest_first != 0 && t->order_costliest_first != 1) ||
+      (t->raster_warps != 8 && t->raster_warps != 12) || (eight_only && t->raster_warps != 8) ||
+      (t->occlusion_cull != 0 && t->occlusion_cull != 1) ||
+      (t->occlusion_cull && (!x->d_vis || t->raster_warps != 8)))
+    return fail(x, GX_EINVAL, "gx_apply_tune: setting not valid for this context");
+  int per_sm = x->n_slots / std::max(1, x->sms);
+  if (t->raster_warps == 12) CK(x, raster_ctas_per_sm(12, &per_sm));
+  const int most = std::min(x->n_slots, std::max(1, per_sm) * x->sms);
+  if (t->raster_ctas < 1 || t->raster_ctas > most)
+    return fail(x, GX_EINVAL, "gx_apply_tune: raster_ctas must be in [1, %d] for this shape",
+                most);
+  x->big_px = t->small_tri_px > 0 ? t->small_tri_px : (1 << 30);
+  x->order_mode = t->order_costliest_first;
+  x->raster_ctas = t->raster_ctas;
+  x->raster_warps = t->raster_warps;
+  x->occlusion = t->occlusion_cull != 0;
+  x->cfg.small_tri_px = t->small_tri_px;
+  if (x->gexec) {  // a captured step holds the old settings
+    cudaGraphExecDestroy(x->gexec);
+    x->gexec = nullptr;
+  }
+  return GX_OK;
+}
+
 extern "C" gx_status gx_nsdf_counters(gx_ctx* x, int64_t out[4]) {
   if (!x || !out) return fail(x, GX_EINVAL, "gx_nsdf_counters: bad argument");
   if (!x->d_nsdf_counters) return fail(x, GX_ESTATE, "gx_nsdf_counters: context does not count");

@@ -9,6 +9,8 @@ constructors raise.
 from __future__ import annotations
 
 import ctypes as C
+import hashlib
+import json
 import os
 
 import numpy as np
@@ -37,7 +39,8 @@ SYMBOLS = ["gx_scene_set_create", "gx_scene_set_destroy", "gx_create", "gx_destr
            "gx_nsdf_train", "gx_nsdf_counters", "gx_nsdf_step_predictions", "gx_autotune",
            "gx_column_info", "gx_column_spans", "gx_device_outputs", "gx_last_error",
            "gx_scene_set_create_ex", "gx_scene_bytes", "gx_static_distance",
-           "gx_box_store_lists", "gx_set_device_memory_cap", "gx_device_memory_in_use"]
+           "gx_box_store_lists", "gx_set_device_memory_cap", "gx_device_memory_in_use",
+           "gx_apply_tune"]
 NSDF_PARAMS = 57985
 NSDF_FREQ = 32
 RASTER_COUNTERS = ["clusters_tested", "clusters_drawn", "tris_seen", "tris_front", "tris_expand",
@@ -173,6 +176,7 @@ def lib():
         L.gx_column_spans.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, vp, C.c_int32]
         L.gx_column_spans.restype = C.c_int32
         L.gx_autotune.argtypes = [vp, vp, P(GxOutputs), C.c_int32, P(GxTuneResult), vp]
+        L.gx_apply_tune.argtypes = [vp, P(GxTuneResult)]
         L.gx_nsdf_train.argtypes = [vp, C.c_int32, C.POINTER(GxTrainParams), vp, vp]
         L.gx_set_device_memory_cap.argtypes = [C.c_uint64]
         L.gx_set_device_memory_cap.restype = None
@@ -264,8 +268,12 @@ class SceneSet:
         self._keep = []
         n = len(scenes)
         descs = (GxSceneDesc * n)()
+        sig = hashlib.sha1()
         for i, s in enumerate(scenes):
             descs[i] = scene_desc(s, self._keep)
+            for a in (s.boxes, s.verts, s.tris, s.grid_dims):
+                sig.update(np.ascontiguousarray(a).tobytes())
+        self.signature = sig.hexdigest()   # identifies the scenes (tuning cache keys)
         mv, mt = obj_mesh if obj_mesh is not None else _inputs.icosahedron()
         mv = np.ascontiguousarray(mv, np.float32)
         mt = np.ascontiguousarray(mt, np.int32)
@@ -442,6 +450,15 @@ class Sim:
         cfg.occlusion_cull = int(occlusion_cull)
         cfg.static_store = int(static_store)
         self.object_boxes = bool(object_boxes)
+        self._key_fields = dict(
+            n_envs=n_envs, img=list(img), depth_fp16=bool(depth_fp16), render_rgb=bool(render_rgb),
+            n_objects=n_objects, obj_radius=[float(x) for x in obj_radius],
+            env_scene=(hashlib.sha1(es.tobytes()).hexdigest() if es is not None else None),
+            sdf_mode=int(sdf_mode), static_store=int(static_store), heuristics=int(heuristics),
+            render_robot=bool(render_robot), broadphase=bool(broadphase),
+            object_boxes=bool(object_boxes), fused_step=bool(fused_step),
+            raster_warps=int(raster_warps), occlusion_cull=bool(occlusion_cull),
+            scenes=scene_set.signature)
         self.robot_c = robot_struct(robot)
         self.handle = C.c_void_p()
         _check(lib().gx_create(scene_set.handle, C.byref(self.robot_c), C.byref(cfg),
@@ -536,17 +553,51 @@ class Sim:
         _check(lib().gx_raster_counters(self.handle, v, len(RASTER_COUNTERS)), self.handle)
         return dict(zip(RASTER_COUNTERS, list(v)))
 
-    def autotune(self, actions, steps=5, stream=None):
+    def tune_key(self):
+        """The autotuning cache key of this context: its configuration, its
+        scene set's scenes and the GPU (name and SM count)."""
+        props = self.torch.cuda.get_device_properties(self.torch.cuda.current_device())
+        return json.dumps(dict(self._key_fields, gpu=props.name,
+                               sms=props.multi_processor_count), sort_keys=True)
+
+    def apply_tune(self, setting):
+        """Applies a setting returned by autotune (no timing)."""
+        r = GxTuneResult(int(setting["small_tri_px"]), int(setting["order_costliest_first"]),
+                         int(setting["raster_ctas"]), float(setting.get("ms_per_step", 0.0)),
+                         int(setting["raster_warps"]), int(setting["occlusion_cull"]))
+        _check(lib().gx_apply_tune(self.handle, C.byref(r)), self.handle)
+
+    def autotune(self, actions, steps=5, stream=None, cache=None):
         """Picks the fastest rasteriser setting on this batch's own state
-        (state restored afterwards); returns the chosen setting."""
+        (state restored afterwards); returns the chosen setting.  cache: path
+        of a JSON file of earlier results keyed by tune_key(); a hit applies
+        the stored setting without timing (returned with "cached": True), a
+        miss tunes and adds its result to the file."""
+        key = self.tune_key() if cache is not None else None
+        if key is not None and os.path.exists(cache):
+            with open(cache) as f:
+                table = json.load(f)
+            if key in table:
+                self.apply_tune(table[key])
+                return dict(table[key], cached=True)
         r = GxTuneResult()
         _check(lib().gx_autotune(self.handle, C.c_void_p(actions.data_ptr()),
                                  C.byref(self._outs), int(steps), C.byref(r),
                                  self._stream(stream)), self.handle)
-        return {"small_tri_px": r.small_tri_px, "order_costliest_first": r.order_costliest_first,
+        best = {"small_tri_px": r.small_tri_px, "order_costliest_first": r.order_costliest_first,
                 "raster_ctas": r.raster_ctas, "raster_warps": r.raster_warps,
-                "occlusion_cull": r.occlusion_cull,
-                "ms_per_step": r.ms_per_step}
+                "occlusion_cull": r.occlusion_cull, "ms_per_step": r.ms_per_step}
+        if key is not None:
+            table = {}
+            if os.path.exists(cache):
+                with open(cache) as f:
+                    table = json.load(f)
+            table[key] = best
+            tmp = f"{cache}.{os.getpid()}.tmp"
+            with open(tmp, "w") as f:
+                json.dump(table, f, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
+        return best
 
     def nsdf_counters(self):
         """Neural-SDF decision counters since the last call (profile bit 2 only)."""
