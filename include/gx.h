@@ -140,7 +140,10 @@ typedef struct {
                               caller's stream (disables graph replay);
                               bit 1: also count rasteriser work (slower);
                               bit 2: count neural-SDF decisions against the
-                              grid-only rule (evaluates both; slower)         */
+                              grid-only rule (evaluates both; slower);
+                              bit 3: NVTX ranges around gx_reset, gx_step,
+                              gx_step_reset and each kernel's enqueue (for
+                              timelines and ncu --nvtx filters)              */
   int32_t sdf_mode;        /* 0: static test on the distance grid;
                               2: on the column grid (appendix "Additional
                               Collision-Detection Details"): per working-set

@@ -9,6 +9,8 @@
 #include <unordered_map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gx_internal.h"
 
 using namespace gx;
@@ -16,6 +18,18 @@ using namespace gx;
 namespace {
 
 thread_local std::string g_last_error;
+
+// An NVTX range over the rest of the scope when `on` (profile bit 3): marks a
+// call's host enqueue for timeline and ncu --nvtx filtering.
+struct NvtxRange {
+  bool on;
+  NvtxRange(bool o, const char* name) : on(o) {
+    if (on) nvtxRangePushA(name);
+  }
+  ~NvtxRange() {
+    if (on) nvtxRangePop();
+  }
+};
 
 // Device bytes the library holds, per allocation, and the optional cap.
 std::mutex g_mem_mu;
@@ -322,6 +336,7 @@ ResetParams reset_params(gx_ctx* x, const uint8_t* env_mask) {
 }
 
 void enqueue_step(gx_ctx* c, const float* actions, const gx_outputs& out, cudaStream_t s) {
+  const bool nvtx = (c->cfg.profile & 8) != 0;
   const bool neural = c->cfg.sdf_mode == 1;
   cudaEvent_t* ev = (c->cfg.profile & 1) ? prof_slot(c, neural ? 2 : 0) : nullptr;
   if (ev) cudaEventRecord(ev[0], s);
@@ -332,7 +347,10 @@ void enqueue_step(gx_ctx* c, const float* actions, const gx_outputs& out, cudaSt
     pp.nsdf_margin = c->cfg.sdf_margin;
     pp.nsdf_counters = (c->cfg.profile & 4) ? c->d_nsdf_counters : nullptr;
     pp.nsdf_pass = 1;
-    launch_physics(pp, s);
+    {
+      NvtxRange r(nvtx, "gx physics pass 1");
+      launch_physics(pp, s);
+    }
     if (ev) cudaEventRecord(ev[1], s);
     NsdfStepParams np{};
     np.blobs = c->d_nsdf_blobs;
@@ -342,18 +360,27 @@ void enqueue_step(gx_ctx* c, const float* actions, const gx_outputs& out, cudaSt
     np.pts = c->d_nsdf_pts;
     np.out = c->d_nsdf_d;
     np.err = c->d_err;
-    nsdf_launch_step(np, s);
+    {
+      NvtxRange r(nvtx, "gx neural-SDF queries");
+      nsdf_launch_step(np, s);
+    }
     if (ev) cudaEventRecord(ev[2], s);
     pp.nsdf_pass = 2;
   }
-  if (c->cfg.object_boxes) {
-    pp.held_M = c->d_held_M;
-    launch_physics_boxes(pp, s);
-  } else {
-    launch_physics(pp, s);
+  {
+    NvtxRange r(nvtx, "gx physics");
+    if (c->cfg.object_boxes) {
+      pp.held_M = c->d_held_M;
+      launch_physics_boxes(pp, s);
+    } else {
+      launch_physics(pp, s);
+    }
   }
   if (ev) cudaEventRecord(ev[3], s);
-  launch_raster(raster_params(c, out), s);
+  {
+    NvtxRange r(nvtx, "gx raster");
+    launch_raster(raster_params(c, out), s);
+  }
   if (ev) cudaEventRecord(ev[4], s);
 }
 
@@ -903,6 +930,7 @@ extern "C" void gx_destroy(gx_ctx* x) {
 
 extern "C" gx_status gx_reset(gx_ctx* x, const uint8_t* env_mask, void* stream) {
   if (!x) return fail(nullptr, GX_EINVAL, "gx_reset: ctx is NULL");
+  NvtxRange r(x->cfg.profile & 8, "gx_reset");
   gx_status st = poll_device_error(x, false);
   if (st != GX_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
@@ -977,11 +1005,13 @@ gx_status run_step(gx_ctx* x, const uint8_t* mask, const float* actions, const g
 
 extern "C" gx_status gx_step(gx_ctx* x, const float* actions, const gx_outputs* out,
                              void* stream) {
+  NvtxRange r(x && (x->cfg.profile & 8), "gx_step");
   return run_step(x, nullptr, actions, out, stream, "gx_step");
 }
 
 extern "C" gx_status gx_step_reset(gx_ctx* x, const uint8_t* env_mask, const float* actions,
                                    const gx_outputs* out, void* stream) {
+  NvtxRange r(x && (x->cfg.profile & 8), "gx_step_reset");
   return run_step(x, env_mask, actions, out, stream, "gx_step_reset");
 }
 
