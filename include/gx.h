@@ -542,6 +542,22 @@ typedef struct {
 gx_status gx_nsdf_train(gx_scene_set* set, int32_t scene, const gx_train_params* params,
                         float* loss_host, void* stream);
 
+/* Steps first_step .. first_step + n_steps - 1 of the training run `params`
+ * defines (its cosine rate over params->steps, bias corrections and batches
+ * of those step numbers), from the scene's current FP32 master parameters and
+ * the Adam moments in moments_in (host [2][GX_NSDF_PARAMS], first moments
+ * then second; NULL: zero, as at step 0); the moments after the last step go
+ * to moments_out (host, may be NULL).  A run split into consecutive ranges,
+ * the moments carried from one to the next, gives the same parameters bit
+ * for bit as gx_nsdf_train over the whole run, also across processes (keep
+ * gx_nsdf_get_master and the moments; restore them with gx_nsdf_set_weights
+ * and moments_in): training checkpoints.  loss_host: [n_steps] or NULL.
+ * GX_EINVAL when the range leaves [0, params->steps); allocation and errors
+ * as gx_nsdf_train. */
+gx_status gx_nsdf_train_steps(gx_scene_set* set, int32_t scene, const gx_train_params* params,
+                              int32_t first_step, int32_t n_steps, const float* moments_in,
+                              float* moments_out, float* loss_host, void* stream);
+
 /* Column grid of a scene (built with the scene set; see sdf_mode 2): columns
  * per axis (dims[0] along x, dims[1] along z) and its size in device bytes
  * (bytes may be NULL). */

@@ -791,13 +791,20 @@ extern "C" gx_status gx_nsdf_grad(gx_scene_set* set, int32_t scene, const float*
   return GX_OK;
 }
 
-extern "C" gx_status gx_nsdf_train(gx_scene_set* set, int32_t scene, const gx_train_params* tp,
-                                   float* loss_host, void* stream) {
-  gx_status st = check_scene(set, scene, "gx_nsdf_train: NULL");
+// Adam steps first .. first + count - 1 of the schedule tp defines (cosine
+// rate over tp->steps, bias corrections of step t + 1, batch t = samples
+// t * batch ..), from the scene's current master parameters and the given
+// moments (host [2][kNsdfParams]: m then v; NULL: zero), returning the
+// moments when m_out is not NULL.
+static gx_status train_range(gx_scene_set* set, int32_t scene, const gx_train_params* tp,
+                             int32_t first, int32_t count, const float* m_in, float* m_out,
+                             float* loss_host, void* stream, const char* who) {
+  gx_status st = check_scene(set, scene, who);
   if (st != GX_OK) return st;
   if (!tp || tp->n_samples <= 0 || tp->n_samples > ((int64_t)1 << 32) || tp->batch <= 0 ||
       tp->batch > tp->n_samples || tp->batch > (1 << 24) || tp->steps < 0 ||
-      !(tp->clamp_lo < tp->clamp_hi) || !(tp->near_band > 0.f) || !(tp->lr >= 0.f))
+      !(tp->clamp_lo < tp->clamp_hi) || !(tp->near_band > 0.f) || !(tp->lr >= 0.f) ||
+      first < 0 || count < 0 || (int64_t)first + count > tp->steps)
     return set_last_error(GX_EINVAL, "gx_nsdf_train: bad parameters");
   if (train_configure() != cudaSuccess)
     return set_last_error(GX_ECUDA, "gx_nsdf_train: kernel configuration failed");
@@ -817,13 +824,15 @@ extern "C" gx_status gx_nsdf_train(gx_scene_set* set, int32_t scene, const gx_tr
   if (dev_malloc(&pts, (size_t)N * 12) != cudaSuccess ||
       dev_malloc(&labels, (size_t)N * 4) != cudaSuccess ||
       dev_malloc(&mv, (size_t)2 * kNsdfParams * 4) != cudaSuccess ||
-      dev_malloc(&loss, (size_t)(tp->steps > 0 ? tp->steps : 1) * 4) != cudaSuccess) {
+      dev_malloc(&loss, (size_t)(count > 0 ? count : 1) * 4) != cudaSuccess) {
     release();
     return set_last_error(GX_ENOMEM, "gx_nsdf_train: allocation");
   }
   SceneSetView v;
   scene_set_view(set, &v);
-  cudaError_t e = cudaMemsetAsync(mv, 0, (size_t)2 * kNsdfParams * 4, s);
+  cudaError_t e = m_in ? cudaMemcpyAsync(mv, m_in, (size_t)2 * kNsdfParams * 4,
+                                         cudaMemcpyHostToDevice, s)
+                       : cudaMemsetAsync(mv, 0, (size_t)2 * kNsdfParams * 4, s);
   if (e == cudaSuccess)
     e = launch_samples(v.scenes, scene, tp->seed, 0, N, tp->near_band, pts, labels, s);
   AdamParams ap;
@@ -834,22 +843,39 @@ extern "C" gx_status gx_nsdf_train(gx_scene_set* set, int32_t scene, const gx_tr
   ap.beta1 = tp->beta1;
   ap.beta2 = tp->beta2;
   ap.eps = tp->eps;
-  for (int t = 0; t < tp->steps && e == cudaSuccess; ++t) {
+  for (int k = 0; k < count && e == cudaSuccess; ++k) {
+    const int t = first + k;
     const long long start = ((long long)t * tp->batch) % N;
     ap.lr = (float)(tp->lr * 0.5 * (1.0 + std::cos(CUDART_PI * t / tp->steps)));
     ap.bc1 = (float)(1.0 - std::pow((double)tp->beta1, t + 1));
     ap.bc2 = (float)(1.0 - std::pow((double)tp->beta2, t + 1));
-    ap.loss_out = loss + t;
+    ap.loss_out = loss + k;
     e = grad_and_update(ns.blob, pts, labels, N, start, tp->batch, tp->clamp_lo, tp->clamp_hi, w,
                         ap, s);
   }
   unsigned herr = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, w.err, 4, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess && loss_host && tp->steps > 0)
-    e = cudaMemcpyAsync(loss_host, loss, (size_t)tp->steps * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && loss_host && count > 0)
+    e = cudaMemcpyAsync(loss_host, loss, (size_t)count * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && m_out)
+    e = cudaMemcpyAsync(m_out, mv, (size_t)2 * kNsdfParams * 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   release();
   if (e != cudaSuccess) return set_last_error(GX_ECUDA, "gx_nsdf_train: CUDA error");
   if (herr) return set_last_error(GX_EDEVICE, "gx_nsdf_train: a bounded wait gave up");
   return GX_OK;
+}
+
+extern "C" gx_status gx_nsdf_train(gx_scene_set* set, int32_t scene, const gx_train_params* tp,
+                                   float* loss_host, void* stream) {
+  return train_range(set, scene, tp, 0, tp ? tp->steps : 0, nullptr, nullptr, loss_host, stream,
+                     "gx_nsdf_train: NULL");
+}
+
+extern "C" gx_status gx_nsdf_train_steps(gx_scene_set* set, int32_t scene,
+                                         const gx_train_params* tp, int32_t first_step,
+                                         int32_t n_steps, const float* moments_in,
+                                         float* moments_out, float* loss_host, void* stream) {
+  return train_range(set, scene, tp, first_step, n_steps, moments_in, moments_out, loss_host,
+                     stream, "gx_nsdf_train_steps: NULL");
 }

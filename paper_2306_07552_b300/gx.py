@@ -40,7 +40,7 @@ SYMBOLS = ["gx_scene_set_create", "gx_scene_set_destroy", "gx_create", "gx_destr
            "gx_column_info", "gx_column_spans", "gx_device_outputs", "gx_last_error",
            "gx_scene_set_create_ex", "gx_scene_bytes", "gx_static_distance",
            "gx_box_store_lists", "gx_set_device_memory_cap", "gx_device_memory_in_use",
-           "gx_apply_tune"]
+           "gx_apply_tune", "gx_nsdf_train_steps"]
 NSDF_PARAMS = 57985
 NSDF_FREQ = 32
 RASTER_COUNTERS = ["clusters_tested", "clusters_drawn", "tris_seen", "tris_front", "tris_expand",
@@ -178,6 +178,8 @@ def lib():
         L.gx_autotune.argtypes = [vp, vp, P(GxOutputs), C.c_int32, P(GxTuneResult), vp]
         L.gx_apply_tune.argtypes = [vp, P(GxTuneResult)]
         L.gx_nsdf_train.argtypes = [vp, C.c_int32, C.POINTER(GxTrainParams), vp, vp]
+        L.gx_nsdf_train_steps.argtypes = [vp, C.c_int32, C.POINTER(GxTrainParams), C.c_int32,
+                                          C.c_int32, vp, vp, vp, vp]
         L.gx_set_device_memory_cap.argtypes = [C.c_uint64]
         L.gx_set_device_memory_cap.restype = None
         L.gx_device_memory_in_use.argtypes = []
@@ -395,6 +397,26 @@ class SceneSet:
         _check(lib().gx_nsdf_train(self.handle, scene, C.byref(tp), losses.ctypes.data,
                                    C.c_void_p(s.cuda_stream)))
         return losses[:steps]
+
+    def nsdf_train_steps(self, scene, first_step, n_steps, moments=None, n_samples=10_000_000,
+                         batch=65536, steps=1000, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+                         clamp_lo=-0.2, clamp_hi=1.0, near_band=0.1, seed=7, stream=None):
+        """Steps first_step .. first_step + n_steps - 1 of the run of `steps`
+        steps, from the current weights and `moments` ([2][GX_NSDF_PARAMS]
+        float32, None: zero); returns (losses, moments after the last step)."""
+        import torch
+        tp = GxTrainParams(n_samples, batch, steps, lr, beta1, beta2, eps, clamp_lo, clamp_hi,
+                           near_band, seed)
+        losses = np.zeros(max(n_steps, 1), np.float32)
+        m_out = np.zeros((2, NSDF_PARAMS), np.float32)
+        m_in = None if moments is None else np.ascontiguousarray(moments, np.float32)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        _check(lib().gx_nsdf_train_steps(self.handle, scene, C.byref(tp), int(first_step),
+                                         int(n_steps),
+                                         m_in.ctypes.data if m_in is not None else None,
+                                         m_out.ctypes.data, losses.ctypes.data,
+                                         C.c_void_p(s.cuda_stream)))
+        return losses[:n_steps], m_out
 
     def close(self):
         if self.handle:

@@ -159,3 +159,29 @@ def test_training_fits_the_grid(setup):
           f"{err[near].mean():.4f} m, p99 {np.quantile(err, 0.99):.4f} m")
     # far better than the best constant (the median label)
     assert err.mean() < 0.3 * np.abs(ref - np.median(ref)).mean()
+
+
+def test_training_resumes_bit_exactly(setup):
+    """A training run split in two, its FP32 master parameters and Adam
+    moments checkpointed to the host in between and restored (as another
+    process would), ends with the same parameters bit for bit as the run in
+    one call, and the same per-step losses."""
+    gx, scene, ss, orc, B, P0 = setup
+    kw = dict(n_samples=300_000, batch=16384, steps=30, lr=1e-3, seed=5)
+    ss.nsdf_set_weights(0, B, P0)
+    full = ss.nsdf_train(0, **kw)
+    m_full = ss.nsdf_get_master(0)
+    ss.nsdf_set_weights(0, B, P0)
+    l1, mom = ss.nsdf_train_steps(0, 0, 12, None, **kw)
+    ckpt_params, ckpt_moments = ss.nsdf_get_master(0).copy(), mom.copy()
+    # "another process": fresh weights, then the checkpoint restored
+    ss.nsdf_set_weights(0, B, I.nsdf_init(11))
+    ss.nsdf_set_weights(0, B, ckpt_params)
+    l2, mom2 = ss.nsdf_train_steps(0, 12, 18, ckpt_moments, **kw)
+    m_split = ss.nsdf_get_master(0)
+    assert np.array_equal(m_split, m_full)
+    assert np.array_equal(np.concatenate([l1, l2]), full)
+    assert np.all(np.isfinite(mom2)) and np.any(mom2[1] > 0)
+    with pytest.raises(gx.GxError):
+        ss.nsdf_train_steps(0, 25, 10, None, **kw)        # past the run's 30 steps
+    ss.nsdf_set_weights(0, B, P0)
