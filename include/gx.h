@@ -143,7 +143,9 @@ typedef struct {
                               grid-only rule (evaluates both; slower);
                               bit 3: NVTX ranges around gx_reset, gx_step,
                               gx_step_reset and each kernel's enqueue (for
-                              timelines and ncu --nvtx filters)              */
+                              timelines and ncu --nvtx filters);
+                              bit 4: count step events (gx_step_counters;
+                              not with object_boxes)                          */
   int32_t sdf_mode;        /* 0: static test on the distance grid;
                               2: on the column grid (appendix "Additional
                               Collision-Detection Details"): per working-set
@@ -408,6 +410,16 @@ gx_status gx_phase_times(gx_ctx* ctx, double ms[4], int64_t launches[4]);
  * Fills out[0..n-1]; waits for the device.
  * GX_ESTATE when the context does not count. */
 gx_status gx_raster_counters(gx_ctx* ctx, int64_t* out, int32_t n);
+
+/* Step event counters accumulated since the previous call (contexts created
+ * with profile bit 4), then cleared: env-steps with a contact (contact mask
+ * non-zero), grasps, missed grasps, releases that landed (also after placing
+ * jitters), releases restored, static tests and object-pair tests within
+ * 1e-4 m of their threshold (the near band of the parity tests; the static
+ * ones on the distance grid or box store, whatever the context decides with),
+ * sliding moves.  Fills out[0..n-1]; waits for the device.  GX_ESTATE when
+ * the context does not count. */
+gx_status gx_step_counters(gx_ctx* ctx, int64_t* out, int32_t n);
 
 /* Rasteriser settings chosen by gx_autotune. */
 typedef struct {

@@ -80,6 +80,7 @@ struct gx_ctx {
   BpCell* d_bp = nullptr;              // object broad-phase cells
   int bp_cells = 0;
   unsigned* d_err = nullptr;
+  unsigned long long* d_step_counters = nullptr;  // profile bit 4: step event counters
   unsigned* h_err = nullptr;
   cudaEvent_t ev_err = nullptr;
   bool err_pending = false;
@@ -269,6 +270,7 @@ PhysicsParams physics_params(gx_ctx* c, const float* actions, const gx_outputs& 
   pp.env_offset = c->cfg.env_offset;
   pp.column = c->cfg.sdf_mode == 2;
   pp.store = c->cfg.static_store;
+  pp.step_counters = c->d_step_counters;
   return pp;
 }
 
@@ -683,6 +685,9 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
     return fail(nullptr, GX_EINVAL,
                 "object_boxes: the box model runs the plain step on the distance grid "
                 "(no heuristics, broad-phase, robot-body rendering or other static test)");
+  if ((c.profile & 16) && c.object_boxes)
+    return fail(nullptr, GX_EINVAL,
+                "profile bit 4 (step counters): not with object_boxes (its kernels do not count)");
   if (c.static_store < 0 || c.static_store > 1)
     return fail(nullptr, GX_EINVAL, "static_store must be 0 or 1");
   if (c.static_store == 1 && c.fused_step)
@@ -890,6 +895,11 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
     if ((e = cudaMemset(x->d_counters, 0, kRasterCounters * 8)) != cudaSuccess)
       return bail(e, "counters");
   }
+  if (c.profile & 16) {
+    if ((e = dev_malloc(&x->d_step_counters, kStepCounters * 8)) != cudaSuccess ||
+        (e = cudaMemset(x->d_step_counters, 0, kStepCounters * 8)) != cudaSuccess)
+      return bail(e, "step counters");
+  }
   *out = x;
   return GX_OK;
 }
@@ -914,6 +924,7 @@ extern "C" void gx_destroy(gx_ctx* x) {
   if (x->h_err) cudaFreeHost(x->h_err);
   for (cudaEvent_t e : x->prof_ev) cudaEventDestroy(e);
   dev_free(x->d_counters);
+  dev_free(x->d_step_counters);
   dev_free(x->d_order);
   dev_free(x->d_robot_sph);
   dev_free(x->d_bp);
@@ -1164,6 +1175,17 @@ extern "C" gx_status gx_raster_counters(gx_ctx* x, int64_t* out, int32_t n) {
   CK(x, cudaMemcpy(h, x->d_counters, sizeof(h), cudaMemcpyDeviceToHost));
   CK(x, cudaMemset(x->d_counters, 0, sizeof(h)));
   for (int k = 0; k < n; ++k) out[k] = k < kRasterCounters ? (int64_t)h[k] : 0;
+  return GX_OK;
+}
+
+extern "C" gx_status gx_step_counters(gx_ctx* x, int64_t* out, int32_t n) {
+  if (!x || !out || n < 1) return fail(x, GX_EINVAL, "gx_step_counters: bad argument");
+  if (!x->d_step_counters) return fail(x, GX_ESTATE, "gx_step_counters: context does not count");
+  CK(x, cudaDeviceSynchronize());
+  unsigned long long h[kStepCounters];
+  CK(x, cudaMemcpy(h, x->d_step_counters, sizeof(h), cudaMemcpyDeviceToHost));
+  CK(x, cudaMemset(x->d_step_counters, 0, sizeof(h)));
+  for (int k = 0; k < n; ++k) out[k] = k < kStepCounters ? (int64_t)h[k] : 0;
   return GX_OK;
 }
 

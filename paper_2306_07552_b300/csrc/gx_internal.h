@@ -146,11 +146,29 @@ struct PhysicsParams {
   const float* nsdf_d;                  // [n][32]
   float nsdf_margin;
   unsigned long long* nsdf_counters;    // optional [kNsdfCounters]
+  unsigned long long* step_counters;    // optional [kStepCounters] (profile bit 4)
   int env_offset;                       // global index of environment 0 (Philox counters)
   float4* held_M;                       // box objects: [n][3] rows of the held box's world
                                         // rotation times its half extents (rasteriser)
   int store;                            // 1: scenes use the box store (kernels compiled for it)
 };
+
+// Step event counters (profile bit 4): env-steps with a contact, grasps,
+// missed grasps, releases landed (also after placing jitters), releases
+// restored, static and object-pair tests within kNearBand of their
+// threshold, sliding moves.
+enum StepCounter {
+  kStepContacts = 0,
+  kStepGrasps,
+  kStepGraspMisses,
+  kStepLanded,
+  kStepRestored,
+  kStepNearStatic,
+  kStepNearPairs,
+  kStepSlides,
+  kStepCounters
+};
+constexpr float kNearBand = 1e-4f;  // metres
 
 // Neural-SDF decision counters (profiling only).
 enum NsdfCounter {

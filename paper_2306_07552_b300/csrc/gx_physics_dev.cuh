@@ -123,6 +123,24 @@ __device__ __forceinline__ void physics_env(const PhysicsParams& P, int env, int
     const unsigned mask_grid = __ballot_sync(kFull, active && (cs_grid || co));
     if (lane == 0 && mask_grid != mask) atomicAdd(P.nsdf_counters + kNsdfEnvDisagree, 1ull);
   }
+  if (P.step_counters) {
+    // tests within kNearBand of their threshold (the grid or box store, and
+    // the object pairs), counted apart from the decisions above
+    bool near_s = false, near_o = false;
+    if (active && !P.column) {
+      float d;
+      if (grid_query(S, c[0], c[1], c[2], d)) near_s = fabsf(d - r) < kNearBand;
+      for (int j = 0; j < M; ++j) {
+        if (j == held) continue;
+        const float4 o = so[j];
+        const float dx = c[0] - o.x, dy = c[1] - o.y, dz = c[2] - o.z;
+        near_o |= fabsf(sqrtf(dx * dx + dy * dy + dz * dz) - (r + o.w)) < kNearBand;
+      }
+    }
+    const unsigned bs = __ballot_sync(kFull, near_s), bo = __ballot_sync(kFull, near_o);
+    if (lane == 0 && bs) atomicAdd(P.step_counters + kStepNearStatic, (unsigned long long)__popc(bs));
+    if (lane == 0 && bo) atomicAdd(P.step_counters + kStepNearPairs, (unsigned long long)__popc(bo));
+  }
   const unsigned ms = __ballot_sync(kFull, active && cs);
   const unsigned mo = __ballot_sync(kFull, active && co);
   uint8_t flags = (ms ? 1 : 0) | (mo ? 2 : 0) | ((mask >> 30) & 1u ? 4 : 0);
@@ -402,6 +420,15 @@ __device__ __forceinline__ void physics_env(const PhysicsParams& P, int env, int
     if (P.out.contact_mask) P.out.contact_mask[env] = mask;
     if (P.out.contact_flags) P.out.contact_flags[env] = flags;
     if (P.out.event) P.out.event[env] = event;
+    if (P.step_counters) {
+      unsigned long long* sc = P.step_counters;
+      if (mask) atomicAdd(sc + kStepContacts, 1ull);
+      if (event == 1) atomicAdd(sc + kStepGrasps, 1ull);
+      if (event == 2) atomicAdd(sc + kStepGraspMisses, 1ull);
+      if (event == 3 || event == 5) atomicAdd(sc + kStepLanded, 1ull);
+      if (event == 4) atomicAdd(sc + kStepRestored, 1ull);
+      if (flags & 8) atomicAdd(sc + kStepSlides, 1ull);
+    }
   }
   // rearrangement task (App. "Additional Task Details"): object 0 is the
   // target; r = 10 success + 5 pick + (d' - d) + (e' - e) - 0.001 C, d the

@@ -40,8 +40,10 @@ SYMBOLS = ["gx_scene_set_create", "gx_scene_set_destroy", "gx_create", "gx_destr
            "gx_column_info", "gx_column_spans", "gx_device_outputs", "gx_last_error",
            "gx_scene_set_create_ex", "gx_scene_bytes", "gx_static_distance",
            "gx_box_store_lists", "gx_set_device_memory_cap", "gx_device_memory_in_use",
-           "gx_apply_tune", "gx_nsdf_train_steps"]
+           "gx_apply_tune", "gx_nsdf_train_steps", "gx_step_counters"]
 NSDF_PARAMS = 57985
+STEP_COUNTERS = ["contacts", "grasps", "grasp_misses", "landed", "restored", "near_static",
+                 "near_pairs", "slides"]
 NSDF_FREQ = 32
 RASTER_COUNTERS = ["clusters_tested", "clusters_drawn", "tris_seen", "tris_front", "tris_expand",
                    "expand_pixels", "tris_warp", "warp_blocks", "tris_clipped", "fragments", "wait_polls",
@@ -158,6 +160,7 @@ def lib():
         L.gx_state_layout.argtypes = [vp, P(C.c_size_t)]
         L.gx_phase_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
         L.gx_raster_counters.argtypes = [vp, C.POINTER(C.c_int64), C.c_int32]
+        L.gx_step_counters.argtypes = [vp, C.POINTER(C.c_int64), C.c_int32]
         L.gx_render_noalloc.argtypes = [vp, C.c_int32, vp, vp, vp, C.c_int32, C.c_int32,
                                         C.c_int32, C.c_float, vp, C.c_int32, vp, vp]
         L.gx_render_noalloc_error.argtypes = [C.POINTER(C.c_uint32)]
@@ -620,6 +623,12 @@ class Sim:
                 json.dump(table, f, indent=1, sort_keys=True)
             os.replace(tmp, cache)
         return best
+
+    def step_counters(self):
+        """Step event counters since the last call (profile bit 4 only)."""
+        v = (C.c_int64 * len(STEP_COUNTERS))()
+        _check(lib().gx_step_counters(self.handle, v, len(STEP_COUNTERS)), self.handle)
+        return dict(zip(STEP_COUNTERS, list(v)))
 
     def nsdf_counters(self):
         """Neural-SDF decision counters since the last call (profile bit 2 only)."""
