@@ -80,3 +80,22 @@ def test_bad_scene_is_rejected_before_device_work(L):
     with pytest.raises(gx.GxError) as e:
         gx.SceneSet([s])
     assert e.value.status == gx.GX_EINVAL
+
+
+def test_added_entry_points_validate_on_the_host(L):
+    """The entry points added beside the step reject NULL or out-of-range
+    arguments with GX_EINVAL before touching a device; the memory cap's
+    counters are host state (no device needed)."""
+    out = (C.c_int64 * 8)()
+    assert L.gx_step_counters(None, out, 8) == gx.GX_EINVAL
+    assert L.gx_apply_tune(None, None) == gx.GX_EINVAL
+    assert L.gx_nsdf_train_steps(None, 0, None, 0, 1, None, None, None, None) == gx.GX_EINVAL
+    assert L.gx_static_distance(None, 0, 0, None, 0, None, None) == gx.GX_EINVAL
+    assert L.gx_scene_bytes(None, 0, None) == gx.GX_EINVAL
+    opt = gx.GxSceneOptions(2, 1)           # options other than 0 / 1
+    handle = C.c_void_p()
+    assert L.gx_scene_set_create_ex(None, 1, None, C.byref(opt), C.byref(handle)) == gx.GX_EINVAL
+    before = gx.device_memory_in_use()
+    gx.set_device_memory_cap(1 << 20)
+    assert gx.device_memory_in_use() == before
+    gx.set_device_memory_cap(0)
