@@ -285,7 +285,8 @@ gx_status gx_scene_set_create(const gx_scene_desc* scenes, int32_t n_scenes,
 gx_status gx_scene_set_destroy(gx_scene_set* set);
 
 /* Which static structures gx_scene_set_create_ex builds (gx_scene_set_create
- * builds all).  The box store (gx_config.static_store 1) is always built; it
+ * builds all); the paper builds its static collision structure offline from
+ * the scene (appendix "Additional Collision-Detection Details").  The box store (gx_config.static_store 1) is always built; it
  * is the distance grid's definition evaluated on demand, so a set without
  * dense grids keeps every static test of the step, and a set without column
  * grids only loses sdf_mode 2.  Training samples (gx_nsdf_samples,
@@ -300,14 +301,16 @@ gx_status gx_scene_set_create_ex(const gx_scene_desc* scenes, int32_t n_scenes,
                                  const gx_object_mesh* mesh, const gx_scene_options* options,
                                  gx_scene_set** out);
 
-/* Device bytes of one scene's structures: bytes[0] dense distance grid (0
+/* (No counterpart in the paper: memory accounting.)  Device bytes of one
+ * scene's structures, written to the host array bytes: bytes[0] dense distance grid (0
  * when not built), [1] box store (boxes and candidate lists), [2] column grid
  * (0 when not built), [3] render clusters (headers, vertices, triangles,
  * colours), [4] neural-SDF weights (0 before gx_nsdf_set_weights), [5]
  * neural-SDF FP32 master copy kept for training (0 when none). */
 gx_status gx_scene_bytes(const gx_scene_set* set, int32_t scene, uint64_t bytes[6]);
 
-/* The box store's candidate lists of one scene (gx_config.static_store 1),
+/* (No counterpart in the paper: inspection of the box store.)
+ * The box store's candidate lists of one scene (gx_config.static_store 1),
  * built on the host exactly as gx_scene_set_create builds them; no device is
  * touched.  The lattice's node intervals are grouped 16 per axis into cells,
  * dims[0..2] of them along x, y, z; cell (cx, cy, cz) has index
@@ -320,7 +323,9 @@ gx_status gx_scene_bytes(const gx_scene_set* set, int32_t scene, uint64_t bytes[
 gx_status gx_box_store_lists(const gx_scene_desc* scene, int32_t dims[3], uint32_t* offsets,
                              uint16_t* ids, uint64_t* n_ids);
 
-/* Static distance at n points (device pts [n][3]) into dist (device [n]):
+/* The static scene's distance query of the step (appendix "Additional
+ * Collision-Detection Details"; the grid's trilinear value) on its own.
+ * Static distance at n points (device pts [n][3]) into dist (device [n]):
  * the trilinear interpolation of the scene's distance grid whose nodes come
  * from `store` (0 dense grid, 1 box store; see gx_config.static_store); NaN
  * where a point lies outside the lattice box (contact for the step).
@@ -411,7 +416,8 @@ gx_status gx_phase_times(gx_ctx* ctx, double ms[4], int64_t launches[4]);
  * GX_ESTATE when the context does not count. */
 gx_status gx_raster_counters(gx_ctx* ctx, int64_t* out, int32_t n);
 
-/* Step event counters accumulated since the previous call (contexts created
+/* (No counterpart in the paper: profiling of the step of Sec. 3.2.)
+ * Step event counters accumulated since the previous call (contexts created
  * with profile bit 4), then cleared: env-steps with a contact (contact mask
  * non-zero), grasps, missed grasps, releases that landed (also after placing
  * jitters), releases restored, static tests and object-pair tests within
@@ -447,7 +453,8 @@ typedef struct {
 gx_status gx_autotune(gx_ctx* ctx, const float* actions, const gx_outputs* out, int32_t steps,
                       gx_tune_result* best, void* stream);
 
-/* Applies a rasteriser setting found earlier by gx_autotune (for example one
+/* (No counterpart in the paper: the autotuner is this library's.)
+ * Applies a rasteriser setting found earlier by gx_autotune (for example one
  * kept in a cache keyed by the configuration and the GPU) without timing
  * anything: small_tri_px, order_costliest_first, raster_warps, raster_ctas
  * and occlusion_cull are used, ms_per_step is ignored.  Images do not depend
@@ -554,7 +561,8 @@ typedef struct {
 gx_status gx_nsdf_train(gx_scene_set* set, int32_t scene, const gx_train_params* params,
                         float* loss_host, void* stream);
 
-/* Steps first_step .. first_step + n_steps - 1 of the training run `params`
+/* (Not in the paper: the learned part's training, as gx_nsdf_train.)
+ * Steps first_step .. first_step + n_steps - 1 of the training run `params`
  * defines (its cosine rate over params->steps, bias corrections and batches
  * of those step numbers), from the scene's current FP32 master parameters and
  * the Adam moments in moments_in (host [2][GX_NSDF_PARAMS], first moments
@@ -624,7 +632,8 @@ gx_status gx_render_noalloc(const gx_scene_set* set, int32_t n, const int32_t* e
 #define GX_NOALLOC_BAD_SCENE 0x200u
 gx_status gx_render_noalloc_error(uint32_t* bits);
 
-/* Caps the device memory this library allocates -- scene sets, contexts,
+/* (No counterpart in the paper: memory budgeting.)
+ * Caps the device memory this library allocates -- scene sets, contexts,
  * training workspaces, on every device, for the whole process -- at `bytes`
  * (0: no cap, the default).  An allocation that would pass the cap fails as
  * an exhausted device would: the call returns GX_ENOMEM and releases what it
