@@ -1,6 +1,7 @@
 """The full-stack workload at full size against the FP64 oracle: 16384 envs
 over 64 apartments with log-uniform 5k-150k triangles, the neural SDF in the
-step (2 cm margin), FP16 depth + RGB8, Bernoulli(0.005) per-env resets and the
+step (2 cm margin) with the box store below it on a scene set that holds no
+dense grid, FP16 depth + RGB8, Bernoulli(0.005) per-env resets and the
 graph-replayed step, in the launch configuration the bench times.
 
 Sampled checks, every step: the masked reset of the sampled envs that reset
@@ -52,7 +53,7 @@ def test_full_stack_16384_sampled():
     build.build()
     w = I.WORKLOADS["uneven16384_nsdf"]
     scenes = I.make_scenes(w)
-    ss = gx.SceneSet(scenes)
+    ss = gx.SceneSet(scenes, dense_grid=False, column_grid=False)
     n, M, W = w.n_envs, w.n_objects, w.img
     B = I.fourier_matrix(7)
     Ps = []
@@ -63,7 +64,7 @@ def test_full_stack_16384_sampled():
         Ps.append(P)
     sim = gx.Sim(ss, ROBOT, n, img=(W, W), depth_fp16=True, render_rgb=True, n_objects=M,
                  obj_radius=w.obj_radius, seed=w.reset_seed, use_graph=True, sdf_mode=1,
-                 sdf_margin=w.sdf_margin)
+                 sdf_margin=w.sdf_margin, static_store=1)
     sim.reset()
     assert sim.device_error() == 0
 
