@@ -484,6 +484,9 @@ def main():
                          "rendering)")
     ap.add_argument("--no-graph", action="store_true",
                     help="headline from the event-timed loop instead of a graph-replayed one")
+    ap.add_argument("--raster-warps", type=int, default=0, choices=[0, 6, 8, 12],
+                    help="warps per rasteriser CTA before autotuning (0: 8); with "
+                         "--no-autotune the shape timed (profiling runs)")
     ap.add_argument("--static-store", type=int, default=-1, choices=[-1, 0, 1],
                     help="distance-grid nodes: 0 the dense grid, 1 the box store (recomputed "
                          "from the scene's boxes; the scene set then holds no dense grid); "
@@ -528,7 +531,8 @@ def main():
                   render_robot=args.render_robot, broadphase=args.broadphase,
                   env_scene=plan.env_scene, env_offset=plan.first,
                   object_boxes=w.objects == "boxes", fused_step=args.fused,
-                  occlusion_cull=args.occlusion, static_store=store)
+                  occlusion_cull=args.occlusion, static_store=store,
+                  raster_warps=args.raster_warps)
     sdf_mode = 1 if neural else (2 if column else 0)
     # per-kernel CUDA events on the launching stream (the roofline's kernel
     # time); the headline loop below replays the step as a CUDA graph on a

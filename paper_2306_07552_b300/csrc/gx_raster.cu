@@ -59,7 +59,7 @@ using namespace rast;
 // kW warps per CTA: 8 (three CTAs per SM) or 12 (two), a rasteriser
 // setting the autotuner chooses.
 template <bool kCount, int kW, bool kBoxes = false, bool kOcc = false>
-__global__ void __launch_bounds__(kW * 32, kW == 8 ? kRasterMinBlocks : 2)
+__global__ void __launch_bounds__(kW * 32, kW == 8 ? kRasterMinBlocks : (kW == 6 ? 4 : 2))
     raster_kernel(const RasterParams P) {
   extern __shared__ __align__(128) unsigned char smem[];
   RasterCta<kCount> C;
@@ -102,6 +102,10 @@ cudaError_t raster_configure(int* slots) {
                                 b12)) != cudaSuccess ||
       (e = cudaFuncSetAttribute(raster_kernel<true, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 b12)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(raster_kernel<false, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)raster_smem_bytes(6))) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(raster_kernel<true, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)raster_smem_bytes(6))) != cudaSuccess ||
       (e = cudaFuncSetAttribute(raster_kernel<false, 8, true>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, b8)) != cudaSuccess ||
       (e = cudaFuncSetAttribute(raster_kernel<true, 8, true>,
@@ -123,6 +127,9 @@ cudaError_t raster_configure(int* slots) {
 }
 
 cudaError_t raster_ctas_per_sm(int warps, int* per_sm) {
+  if (warps == 6)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, raster_kernel<false, 6>, 192,
+                                                         raster_smem_bytes(6));
   return warps == 12
              ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, raster_kernel<false, 12>, 384,
                                                              raster_smem_bytes(12))
@@ -144,6 +151,12 @@ void launch_raster(const RasterParams& p, cudaStream_t s) {
       raster_kernel<true, 8, true><<<grid, 256, smem, s>>>(p);
     else
       raster_kernel<false, 8, true><<<grid, 256, smem, s>>>(p);
+  } else if (p.warps == 6) {
+    const size_t smem = raster_smem_bytes(6);
+    if (p.counters)
+      raster_kernel<true, 6><<<grid, 192, smem, s>>>(p);
+    else
+      raster_kernel<false, 6><<<grid, 192, smem, s>>>(p);
   } else if (p.warps == 12) {
     const size_t smem = raster_smem_bytes(12);
     if (p.counters)

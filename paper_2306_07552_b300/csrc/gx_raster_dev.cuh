@@ -3,6 +3,8 @@
 // Each including translation unit gets its own internal copy.
 #pragma once
 
+#include <type_traits>
+
 #include <math_constants.h>
 #include <cuda_fp16.h>
 
@@ -803,8 +805,11 @@ __device__ __forceinline__ void render_env(const RasterParams& P, const int env,
     // 1. the whole CTA culls the clusters of this pass; a visible one gets a
     //    3-bit code per loop trip (1 + its cost class) and is counted in its class
     const int end = min(base + kListCap, S.n_meshlets);
-    static_assert((kListCap + kW * 32 - 1) / (kW * 32) <= 10, "codes of one pass in 30 bits");
-    uint32_t codes = 0;
+    // 3 bits per trip: a 32-bit word holds 10 trips, more need 64 bits
+    constexpr int kTrips = (kListCap + kW * 32 - 1) / (kW * 32);
+    static_assert(kTrips <= 21, "codes of one pass in 63 bits");
+    using Codes = typename std::conditional<(kTrips > 10), unsigned long long, uint32_t>::type;
+    Codes codes = 0;
     int trip = 0;
     if (kOcc) {
       for (int m = base + tid; m < end; m += kW * 32, ++trip) {
@@ -820,7 +825,7 @@ __device__ __forceinline__ void render_env(const RasterParams& P, const int env,
           if (kCount) cn.v[kCntClustersOccluded]++;
           continue;
         }
-        codes |= (1u + cls) << (3 * trip);
+        codes |= (Codes)(1u + cls) << (3 * trip);
         atomicAdd(&ctr[4 + cls], 1);
       }
     } else
@@ -849,7 +854,7 @@ __device__ __forceinline__ void render_env(const RasterParams& P, const int env,
         if (vis) vis = box_visible(cm, vw, h3, h4);
         if (vis) {
           const uint32_t cls = cluster_class(cm, h0);
-          codes |= (1u + cls) << (3 * trip);
+          codes |= (Codes)(1u + cls) << (3 * trip);
           atomicAdd(&ctr[4 + cls], 1);
         }
       }
@@ -858,7 +863,7 @@ __device__ __forceinline__ void render_env(const RasterParams& P, const int env,
     // 2. the list in class order (a counting sort): each thread places the
     //    entries of its visible clusters, read again from their headers
     for (int m = base + tid, t = 0; (codes >> (3 * t)) != 0u; m += kW * 32, ++t) {
-      const uint32_t code = (codes >> (3 * t)) & 7u;
+      const uint32_t code = (uint32_t)(codes >> (3 * t)) & 7u;
       if (code == 0u) continue;
       const int at = (code > 1u ? ctr[4] : 0) + (code > 2u ? ctr[5] : 0) +
                      (code > 3u ? ctr[6] : 0) + atomicAdd(&ctr[7 + code], 1);
