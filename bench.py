@@ -642,6 +642,8 @@ def main():
         """Another static form of the same batch, timed like the headline's
         event-timed loop: env-steps/s and physics ms per launch."""
         g = gx.Sim(sset, I.fetch_like_robot(), n, profile=1, **{**sim_kw, **kw})
+        if tune:  # the headline's rasteriser setting, so only the static form differs
+            g.apply_tune(tune)
         with torch.cuda.stream(stream):
             g.reset(stream=stream)
             for t in range(args.warmup):
