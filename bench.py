@@ -614,7 +614,8 @@ def main():
     if not args.no_graph:
         gsim = gx.Sim(ss, I.fetch_like_robot(), n, use_graph=True, sdf_mode=sdf_mode,
                       sdf_margin=w.sdf_margin, **sim_kw)
-        warm(gsim)
+        _, gtune = warm(gsim)
+        tune = gtune or tune
         ms, clk = timed(gsim, True)
         dev_err = gsim.device_error()
         out_ctx = gsim
@@ -740,7 +741,8 @@ def main():
     # events) back; observations stay on the device for a GPU policy (the
     # paper's zero-copy hand-off).  Also timed: every output back to the host.
     # A user's context: the step replayed as a CUDA graph, no per-kernel
-    # timing events, the rasteriser setting the autotuner picks for it.
+    # timing events, the rasteriser setting the autotuner picked for the
+    # headline context (re-tuning here on three steps adds selection noise).
     sim.close()
     if gsim is not None:
         gsim.close()
@@ -753,8 +755,8 @@ def main():
             mbuf.copy_(mask_at(t))
             sim.reset(mbuf, stream=stream)
             sim.step(abuf, stream=stream)
-        if not args.no_autotune:
-            sim.autotune(abuf, steps=3, stream=stream)
+    if tune:
+        sim.apply_tune(tune)
     torch.cuda.synchronize()
     full = sim.host_outputs(pinned=True)
     result = {k: (v if k in ("reward", "success", "event") else None) for k, v in full.items()}
