@@ -484,8 +484,8 @@ def main():
                          "rendering)")
     ap.add_argument("--no-graph", action="store_true",
                     help="headline from the event-timed loop instead of a graph-replayed one")
-    ap.add_argument("--raster-warps", type=int, default=0, choices=[0, 6, 8, 12],
-                    help="warps per rasteriser CTA before autotuning (0: 8); with "
+    ap.add_argument("--raster-warps", type=int, default=0, choices=[0, 6, 7, 8, 12],
+                    help="warps per rasteriser CTA before autotuning (0: 7 where offered, else 8); with "
                          "--no-autotune the shape timed (profiling runs)")
     ap.add_argument("--static-store", type=int, default=-1, choices=[-1, 0, 1],
                     help="distance-grid nodes: 0 the dense grid, 1 the box store (recomputed "

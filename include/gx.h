@@ -206,10 +206,11 @@ typedef struct {
                               by rotation x half extents.  Only with sdf_mode 0
                               and without heuristics, broad-phase or robot-body
                               rendering (GX_EINVAL otherwise)                 */
-  int32_t raster_warps;    /* warps per rasteriser CTA: 0 or 8 (three CTAs per
-                              SM), 12 (two per SM), 6 (four per SM; not with
-                              fused_step, object_boxes or occlusion_cull);
-                              gx_autotune may change it                       */
+  int32_t raster_warps;    /* warps per rasteriser CTA: 8 (three CTAs per SM),
+                              12 (two per SM), 6 or 7 (four per SM; not with
+                              fused_step, object_boxes or occlusion_cull); 0:
+                              7 where offered, else 8; gx_autotune may change
+                              it                                              */
   int32_t occlusion_cull;  /* 1: the rasteriser culls clusters by occlusion in
                               two phases per environment: first the clusters
                               it showed in its previous image (one bit per
@@ -436,7 +437,7 @@ typedef struct {
                                      triangle clusters are rendered first       */
   int32_t raster_ctas;            /* persistent CTAs launched                    */
   float ms_per_step;              /* measured step time with these settings      */
-  int32_t raster_warps;           /* warps per rasteriser CTA (6, 8 or 12)       */
+  int32_t raster_warps;           /* warps per rasteriser CTA (6, 7, 8 or 12)    */
   int32_t occlusion_cull;         /* 1: clusters culled by occlusion             */
 } gx_tune_result;
 
@@ -444,8 +445,8 @@ typedef struct {
  * setting -- expansion limit small_tri_px in {0, 256, 96, 48}, work order
  * {index, costliest scene first}, CTA shape {8 warps at the occupancy (three
  * CTAs per SM), 8 warps one CTA per SM fewer, 12 warps at its occupancy (two
- * per SM), 6 warps at its occupancy (four per SM; not offered with occlusion
- * culling); the fused step and box objects keep 8 warps} -- for `steps` steps each (plus one
+ * per SM), 6 and 7 warps at their occupancy (four per SM; not offered with
+ * occlusion culling); the fused step and box objects keep 8 warps} -- for `steps` steps each (plus one
  * warm-up), restoring the
  * state after every candidate, and keeps the fastest (written to *best when
  * not NULL).  The outputs are overwritten; the state is left as before the

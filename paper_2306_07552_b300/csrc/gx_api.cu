@@ -50,9 +50,10 @@ struct gx_ctx {
   gx_config cfg{};
   int n = 0, M = 0, big_px = 0, n_slots = 0;
   int raster_ctas = 0;                 // CTAs launched (<= n_slots), set by the autotuner
-  int raster_warps = 8;                // warps per rasteriser CTA (6, 8 or 12)
+  int raster_warps = 8;                // warps per rasteriser CTA (6, 7, 8 or 12)
   int slots8 = 0;                      // resident 8-warp rasteriser CTAs (<= n_slots)
   int per_sm6 = 0;                     // resident 6-warp CTAs per SM (0: shape not offered)
+  int per_sm7 = 0;                     // resident 7-warp CTAs per SM (0: shape not offered)
   int order_mode = 0;                  // 0: index order, 1: costliest scene first
   int* d_order = nullptr;              // environments, costliest scene first
   int sms = 0;
@@ -673,10 +674,12 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
     return fail(nullptr, GX_EINVAL, "occlusion_cull must be 0 or 1");
   if (c.occlusion_cull && (c.fused_step || c.object_boxes))
     return fail(nullptr, GX_EINVAL, "occlusion_cull: not with fused_step or object_boxes");
-  if (c.raster_warps != 0 && c.raster_warps != 6 && c.raster_warps != 8 && c.raster_warps != 12)
-    return fail(nullptr, GX_EINVAL, "raster_warps must be 0, 6, 8 or 12");
-  if (c.raster_warps == 6 && (c.fused_step || c.object_boxes || c.occlusion_cull))
-    return fail(nullptr, GX_EINVAL, "raster_warps 6: not with fused_step, object_boxes or "
+  if (c.raster_warps != 0 && c.raster_warps != 6 && c.raster_warps != 7 && c.raster_warps != 8 &&
+      c.raster_warps != 12)
+    return fail(nullptr, GX_EINVAL, "raster_warps must be 0, 6, 7, 8 or 12");
+  if ((c.raster_warps == 6 || c.raster_warps == 7) &&
+      (c.fused_step || c.object_boxes || c.occlusion_cull))
+    return fail(nullptr, GX_EINVAL, "raster_warps 6 and 7: not with fused_step, object_boxes or "
                                     "occlusion_cull");
   if (c.fused_step < 0 || c.fused_step > 1)
     return fail(nullptr, GX_EINVAL, "fused_step must be 0 or 1");
@@ -723,23 +726,31 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
   if ((e = reset_configure()) != cudaSuccess) return bail(e, "reset config");
   {
     // framebuffer slots for the most CTAs a shape this context may use keeps
-    // resident: the 6-warp shape (offered unless the fused step, box objects
-    // or occlusion culling hold the rasteriser at 8 warps) fits more per SM
+    // resident: the 6- and 7-warp shapes (offered unless the fused step, box
+    // objects or occlusion culling hold the rasteriser at 8 warps) fit more
+    // per SM
     int sms0 = 0, dev0 = 0;
     cudaGetDevice(&dev0);
     cudaDeviceGetAttribute(&sms0, cudaDevAttrMultiProcessorCount, dev0);
+    x->sms = sms0;
     x->n_slots = x->slots8;
     if (!c.fused_step && !c.object_boxes && !c.occlusion_cull) {
-      if ((e = raster_ctas_per_sm(6, &x->per_sm6)) != cudaSuccess) return bail(e, "raster config");
-      x->n_slots = std::max(x->n_slots, std::max(1, x->per_sm6) * sms0);
+      if ((e = raster_ctas_per_sm(6, &x->per_sm6)) != cudaSuccess ||
+          (e = raster_ctas_per_sm(7, &x->per_sm7)) != cudaSuccess)
+        return bail(e, "raster config");
+      x->n_slots = std::max(x->n_slots, std::max(1, std::max(x->per_sm6, x->per_sm7)) * sms0);
     }
   }
   if (x->n_slots > x->n) x->n_slots = x->n;
   if (x->slots8 > x->n) x->slots8 = x->n;
   x->raster_ctas = x->slots8;
-  if (c.raster_warps == 6) {
-    x->raster_warps = 6;
-    x->raster_ctas = x->n_slots;
+  // the default shape: 7 warps, four CTAs per SM (28 warps at 72
+  // registers) where the context offers it, else 8 warps, three per SM
+  const int warps0 = c.raster_warps == 0 && x->per_sm7 > 0 ? 7 : c.raster_warps;
+  if (warps0 == 6 || warps0 == 7) {
+    x->raster_warps = warps0;
+    x->raster_ctas =
+        std::min(x->n_slots, std::max(1, warps0 == 6 ? x->per_sm6 : x->per_sm7) * x->sms);
   }
   if (c.raster_warps == 12 && !c.fused_step) {
     int per_sm12 = 0;
@@ -1244,17 +1255,21 @@ extern "C" gx_status gx_autotune(gx_ctx* x, const float* actions, const gx_outpu
   // at its occupancy (the fused step keeps 8 warps)
   // (occlusion culling, when the context has its visibility bits, as a CTA
   // shape of its own: 8 warps at the occupancy)
-  // and 6 warps at its occupancy (four CTAs per SM) where the context offers it
-  const int shapes = (x->cfg.fused_step || x->cfg.object_boxes) ? 2 : (x->per_sm6 > 0 ? 4 : 3);
+  // and 6 and 7 warps at their occupancy (four CTAs per SM) where the
+  // context offers them
+  const int shapes = (x->cfg.fused_step || x->cfg.object_boxes) ? 2 : (x->per_sm6 > 0 ? 5 : 3);
   const int occ_shape = x->d_vis ? shapes : -1;
   for (int ci = 0; ci < 4 && err == cudaSuccess; ++ci)
     for (int order = 0; order < 2 && err == cudaSuccess; ++order)
       for (int k = 0; k < shapes + (x->d_vis ? 1 : 0) && err == cudaSuccess; ++k) {
         const bool occ = k == occ_shape;
         x->occlusion = occ;
-        const int warps = occ ? 8 : (k == 2 ? 12 : (k == 3 ? 6 : 8));
-        const int per_sm = std::max(1, warps == 12 ? per_sm12
-                                       : (warps == 6 ? x->per_sm6 : x->slots8 / std::max(1, x->sms)));
+        const int warps = occ ? 8 : (k == 2 ? 12 : (k == 3 ? 6 : (k == 4 ? 7 : 8)));
+        const int per_sm = std::max(1, warps == 12  ? per_sm12
+                                       : warps == 6 ? x->per_sm6
+                                       : warps == 7 ? x->per_sm7
+                                                    : x->slots8 / std::max(1, x->sms));
+        if (warps == 7 && x->per_sm7 <= 0) continue;
         if (k == 1 && per_sm == 1) continue;
         const int ctas = std::min(x->n, std::max(1, per_sm - (k == 1 ? 1 : 0)) * x->sms);
         x->big_px = px[ci] > 0 ? px[ci] : (1 << 30);
@@ -1311,12 +1326,16 @@ extern "C" gx_status gx_apply_tune(gx_ctx* x, const gx_tune_result* t) {
   if (!x || !t) return fail(x, GX_EINVAL, "gx_apply_tune: NULL argument");
   const bool eight_only = x->cfg.fused_step || x->cfg.object_boxes;
   if (t->small_tri_px < 0 || (t->order_costliest_first != 0 && t->order_costliest_first != 1) ||
-      (t->raster_warps != 6 && t->raster_warps != 8 && t->raster_warps != 12) ||
+      (t->raster_warps != 6 && t->raster_warps != 7 && t->raster_warps != 8 &&
+       t->raster_warps != 12) ||
       (eight_only && t->raster_warps != 8) || (t->raster_warps == 6 && x->per_sm6 <= 0) ||
+      (t->raster_warps == 7 && x->per_sm7 <= 0) ||
       (t->occlusion_cull != 0 && t->occlusion_cull != 1) ||
       (t->occlusion_cull && (!x->d_vis || t->raster_warps != 8)))
     return fail(x, GX_EINVAL, "gx_apply_tune: setting not valid for this context");
-  int per_sm = t->raster_warps == 6 ? x->per_sm6 : x->slots8 / std::max(1, x->sms);
+  int per_sm = t->raster_warps == 6   ? x->per_sm6
+               : t->raster_warps == 7 ? x->per_sm7
+                                      : x->slots8 / std::max(1, x->sms);
   if (t->raster_warps == 12) CK(x, raster_ctas_per_sm(12, &per_sm));
   const int most = std::min(x->n_slots, std::max(1, per_sm) * x->sms);
   if (t->raster_ctas < 1 || t->raster_ctas > most)

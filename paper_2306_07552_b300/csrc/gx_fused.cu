@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(kThreads, kRasterMinBlocks) fused_step_kernel(
   // rendering phase is zeroed here, before the barrier that orders them
   if (blockIdx.x == 0 && C.tid == 0) *F.rp.work = 0;
   {
-    float4* so = M * kWarps <= (int)(kListCap * sizeof(uint2) / sizeof(float4))
+    float4* so = M * kWarps <= (int)(kListBytes / sizeof(float4))
                      ? reinterpret_cast<float4*>(C.list) + (size_t)C.warp * M
                      : F.obj_scratch + ((size_t)blockIdx.x * kWarps + C.warp) * GX_MAX_OBJECTS;
     for (int env = blockIdx.x * kWarps + C.warp; env < n; env += gridDim.x * kWarps) {

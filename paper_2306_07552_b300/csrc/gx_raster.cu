@@ -56,10 +56,15 @@ namespace {
 
 using namespace rast;
 
-// kW warps per CTA: 8 (three CTAs per SM) or 12 (two), a rasteriser
-// setting the autotuner chooses.
+// kW warps per CTA: 6 or 7 (four CTAs per SM), 8 (three) or 12 (two), a
+// rasteriser setting the autotuner chooses.  At the kernel's 72 registers
+// four 7-warp CTAs keep 28 warps per SM resident (the register file holds
+// 28.4), the most of any shape; the 7-warp bound asks ptxas for three CTAs
+// so that it keeps the 72 registers (a bound of four caps it at 64, which
+// measured 25% slower with no spills), and the occupancy query confirms four.
 template <bool kCount, int kW, bool kBoxes = false, bool kOcc = false>
-__global__ void __launch_bounds__(kW * 32, kW == 8 ? kRasterMinBlocks : (kW == 6 ? 4 : 2))
+__global__ void __launch_bounds__(kW * 32,
+                                  kW == 8 || kW == 7 ? kRasterMinBlocks : (kW == 6 ? 4 : 2))
     raster_kernel(const RasterParams P) {
   extern __shared__ __align__(128) unsigned char smem[];
   RasterCta<kCount> C;
@@ -82,7 +87,7 @@ __global__ void __launch_bounds__(kW * 32, kW == 8 ? kRasterMinBlocks : (kW == 6
 }  // namespace
 
 size_t raster_smem_bytes(int warps, int hiz_tiles) {
-  return 128 + kListCap * sizeof(uint2) + (size_t)(warps > 0 ? warps : kWarps) * sizeof(WarpSmem) +
+  return 128 + kListBytes + (size_t)(warps > 0 ? warps : kWarps) * sizeof(WarpSmem) +
          (size_t)hiz_tiles * sizeof(uint32_t);
 }
 
@@ -106,6 +111,10 @@ cudaError_t raster_configure(int* slots) {
                                 (int)raster_smem_bytes(6))) != cudaSuccess ||
       (e = cudaFuncSetAttribute(raster_kernel<true, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)raster_smem_bytes(6))) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(raster_kernel<false, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)raster_smem_bytes(7))) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(raster_kernel<true, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)raster_smem_bytes(7))) != cudaSuccess ||
       (e = cudaFuncSetAttribute(raster_kernel<false, 8, true>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, b8)) != cudaSuccess ||
       (e = cudaFuncSetAttribute(raster_kernel<true, 8, true>,
@@ -130,6 +139,9 @@ cudaError_t raster_ctas_per_sm(int warps, int* per_sm) {
   if (warps == 6)
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, raster_kernel<false, 6>, 192,
                                                          raster_smem_bytes(6));
+  if (warps == 7)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, raster_kernel<false, 7>, 224,
+                                                         raster_smem_bytes(7));
   return warps == 12
              ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, raster_kernel<false, 12>, 384,
                                                              raster_smem_bytes(12))
@@ -157,6 +169,12 @@ void launch_raster(const RasterParams& p, cudaStream_t s) {
       raster_kernel<true, 6><<<grid, 192, smem, s>>>(p);
     else
       raster_kernel<false, 6><<<grid, 192, smem, s>>>(p);
+  } else if (p.warps == 7) {
+    const size_t smem = raster_smem_bytes(7);
+    if (p.counters)
+      raster_kernel<true, 7><<<grid, 224, smem, s>>>(p);
+    else
+      raster_kernel<false, 7><<<grid, 224, smem, s>>>(p);
   } else if (p.warps == 12) {
     const size_t smem = raster_smem_bytes(12);
     if (p.counters)

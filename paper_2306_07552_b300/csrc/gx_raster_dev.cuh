@@ -20,6 +20,9 @@ constexpr int kThreads = kRasterThreads;
 constexpr int kWarps = kThreads / 32;
 constexpr long kWaitLimit = 1L << 22;  // bounded waits
 constexpr int kListCap = 2048;          // clusters culled per pass
+// bytes of the CTA's cluster list: one cluster index per entry (the copy
+// offsets and counts are read from the cluster's header when it is issued)
+constexpr size_t kListBytes = kListCap * sizeof(uint32_t);
 constexpr int kSpan = 4;                // adjacent pixels of a row per expansion slot
 #ifndef GX_RASTER_DIRECT_W
 #define GX_RASTER_DIRECT_W 2
@@ -63,6 +66,7 @@ struct __align__(16) WarpSmem {
   uint8_t voc[kMeshletMaxVerts];        // frustum outcode
   uint8_t qlane[32];                    // lanes whose triangles have pixels, in order
   unsigned long long bar[2];            // mbarriers of the two buffers
+  uint2 ent[2];                         // the clusters issued into them (cluster_entry)
 };
 
 // Per-lane work counters, summed into RasterParams::counters when counting.
@@ -544,6 +548,15 @@ __device__ void raster_cluster(const View& vw, const Cam& cm, WarpSmem& ws, int 
   __syncwarp();
 }
 
+// Offsets and counts of cluster m's vertices and triangles, from its header:
+// x = vertex offset | vertex count << 24, y = triangle offset | count << 24.
+__device__ __forceinline__ uint2 cluster_entry(const DScene& S, uint32_t m) {
+  const float4 h2 = __ldg(S.mhdr + (size_t)kMeshletHdr * m + 2);
+  const uint32_t cnt = __float_as_uint(h2.w);
+  return make_uint2(__float_as_uint(h2.y) | ((cnt & 0xffu) << 24),
+                    __float_as_uint(h2.z) | (((cnt >> 8) & 0xffu) << 24));
+}
+
 __device__ __forceinline__ void issue_cluster(WarpSmem& ws, int buf, const DScene& S, uint2 e) {
   const uint32_t voff = e.x & 0xffffffu, nv = e.x >> 24;
   const uint32_t toff = e.y & 0xffffffu, nt = e.y >> 24;
@@ -651,7 +664,7 @@ __device__ __forceinline__ uint32_t cluster_class(const Cam& cm, float4 h0) {
 // passes.
 __device__ __forceinline__ bool cluster_in_view(const DScene& S, int m, const Cam& cm,
                                                 const View& vw, float4& lo, float4& hi,
-                                                uint2& entry, uint32_t& cls) {
+                                                uint32_t& cls) {
   const float4* hd = S.mhdr + (size_t)kMeshletHdr * m;
   const float4 h0 = __ldg(hd);
   if (!sphere_visible(cm, vw, h0.x, h0.y, h0.z, h0.w)) return false;
@@ -669,11 +682,7 @@ __device__ __forceinline__ bool cluster_in_view(const DScene& S, int m, const Ca
   if (hi.w > 0.5f && h1.x * cm.ex + h1.y * cm.ey + h1.z * cm.ez <
                          lo.w - 1e-4f - 1e-5f * (fabsf(cm.ex) + fabsf(cm.ey) + fabsf(cm.ez)))
     return false;
-  if (!box_visible(cm, vw, lo, hi)) return false;
-  const uint32_t cnt = __float_as_uint(h2.w);
-  entry = make_uint2(__float_as_uint(h2.y) | ((cnt & 0xffu) << 24),
-                     __float_as_uint(h2.z) | (((cnt >> 8) & 0xffu) << 24));
-  return true;
+  return box_visible(cm, vw, lo, hi);
 }
 
 __device__ __forceinline__ int pop_item(int* ctr, int lane) {
@@ -691,7 +700,7 @@ template <bool kCount>
 struct RasterCta {
   int* ctr;         // [0] environment, [2] clusters handed out, [3] objects handed out,
                     // [4..7] clusters listed per cost class, [8..11] their list fill
-  uint2* list;
+  uint32_t* list;  // cluster indices of the current pass, in cost-class order
   WarpSmem* ws;
   int tid, lane, warp;
   View vw;
@@ -704,8 +713,8 @@ __device__ __forceinline__ void raster_cta_begin(const RasterParams& P, unsigned
                                                  RasterCta<kCount>& C, uint32_t phase[2],
                                                  Cnt& cn) {
   C.ctr = reinterpret_cast<int*>(smem);
-  C.list = reinterpret_cast<uint2*>(smem + 128);
-  WarpSmem* wsm = reinterpret_cast<WarpSmem*>(smem + 128 + kListCap * sizeof(uint2));
+  C.list = reinterpret_cast<uint32_t*>(smem + 128);
+  WarpSmem* wsm = reinterpret_cast<WarpSmem*>(smem + 128 + kListBytes);
   C.tid = threadIdx.x;
   C.lane = C.tid & 31;
   C.warp = C.tid >> 5;
@@ -741,7 +750,7 @@ template <bool kCount, int kW, bool kBoxes = false, bool kOcc = false>
 __device__ __forceinline__ void render_env(const RasterParams& P, const int env,
                                            RasterCta<kCount>& C, uint32_t phase[2], Cnt& cn) {
   int* ctr = C.ctr;
-  uint2* list = C.list;
+  uint32_t* list = C.list;
   WarpSmem& ws = *C.ws;
   const int tid = C.tid, lane = C.lane;
   View& vw = C.vw;
@@ -794,7 +803,7 @@ __device__ __forceinline__ void render_env(const RasterParams& P, const int env,
   // occlusion culling: tile depth bounds after the bytes of the warps' buffers;
   // the environment's visibility bits (one per cluster)
   uint32_t* hiz = reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(ctr) + 128 +
-                                              kListCap * sizeof(uint2) + kW * sizeof(WarpSmem));
+                                              kListBytes + kW * sizeof(WarpSmem));
   uint32_t* visw = kOcc ? P.vis + (size_t)env * P.vis_words : nullptr;
   constexpr int kPhases = kOcc ? 2 : 1;
 #pragma unroll 1
@@ -818,9 +827,8 @@ __device__ __forceinline__ void render_env(const RasterParams& P, const int env,
         if (ph == 0 && !prev) continue;
         if (ph == 1 && prev) continue;  // drawn in the first phase
         float4 lo, hi;
-        uint2 entry;
         uint32_t cls;
-        if (!cluster_in_view(S, m, cm, vw, lo, hi, entry, cls)) continue;
+        if (!cluster_in_view(S, m, cm, vw, lo, hi, cls)) continue;
         if (ph == 1 && hiz_occluded(cm, vw, lo.x, lo.y, lo.z, hi.x, hi.y, hi.z, hiz)) {
           if (kCount) cn.v[kCntClustersOccluded]++;
           continue;
@@ -861,26 +869,32 @@ __device__ __forceinline__ void render_env(const RasterParams& P, const int env,
     }
     __syncthreads();
     // 2. the list in class order (a counting sort): each thread places the
-    //    entries of its visible clusters, read again from their headers
+    //    indices of its visible clusters
     for (int m = base + tid, t = 0; (codes >> (3 * t)) != 0u; m += kW * 32, ++t) {
       const uint32_t code = (uint32_t)(codes >> (3 * t)) & 7u;
       if (code == 0u) continue;
       const int at = (code > 1u ? ctr[4] : 0) + (code > 2u ? ctr[5] : 0) +
                      (code > 3u ? ctr[6] : 0) + atomicAdd(&ctr[7 + code], 1);
-      const float4 h2 = __ldg(S.mhdr + (size_t)kMeshletHdr * m + 2);
-      const uint32_t cnt = __float_as_uint(h2.w);
-      list[at] = make_uint2(__float_as_uint(h2.y) | ((cnt & 0xffu) << 24),
-                            __float_as_uint(h2.z) | (((cnt >> 8) & 0xffu) << 24));
+      list[at] = (uint32_t)m;
     }
     __syncthreads();
     const int count = ctr[4] + ctr[5] + ctr[6] + ctr[7];
     // 3. warps take one cluster at a time; the next streams in meanwhile
     int cur = dead ? count : pop_item(&ctr[2], lane);
     int buf = 0;
-    if (cur < count && lane == 0) issue_cluster(ws, 0, S, list[cur]);
+    if (cur < count && lane == 0) {
+      ws.ent[0] = cluster_entry(S, list[cur]);
+      issue_cluster(ws, 0, S, ws.ent[0]);
+    }
+    __syncwarp();
     while (cur < count) {
       const int nxt = pop_item(&ctr[2], lane);
-      if (nxt < count && lane == 0) issue_cluster(ws, buf ^ 1, S, list[nxt]);
+      if (nxt < count && lane == 0) {
+        // the other buffer's entry is free: its cluster was drawn, and the
+        // draw ended with a warp synchronisation
+        ws.ent[buf ^ 1] = cluster_entry(S, list[nxt]);
+        issue_cluster(ws, buf ^ 1, S, ws.ent[buf ^ 1]);
+      }
       const bool ok = mbar_wait(&ws.bar[buf], phase[buf],
                                 (kCount && lane == 0) ? &cn.v[kCntWaitIters] : nullptr);
       phase[buf] ^= 1u;
@@ -891,7 +905,7 @@ __device__ __forceinline__ void render_env(const RasterParams& P, const int env,
         dead = true;
         break;
       }
-      const uint2 e = list[cur];
+      const uint2 e = ws.ent[buf];
       raster_cluster<kCount>(vw, cm, ws, buf, (int)(e.x >> 24), (int)(e.y >> 24), P.big_px,
                              lane, cn);
       cur = nxt;
@@ -1047,9 +1061,8 @@ __device__ __forceinline__ void render_env(const RasterParams& P, const int env,
       bool v = false;
       if (m < S.n_meshlets) {
         float4 lo, hi;
-        uint2 entry;
         uint32_t cls;
-        v = cluster_in_view(S, m, cm, vw, lo, hi, entry, cls) &&
+        v = cluster_in_view(S, m, cm, vw, lo, hi, cls) &&
             !hiz_occluded(cm, vw, lo.x, lo.y, lo.z, hi.x, hi.y, hi.z, hiz);
       }
       const unsigned b = __ballot_sync(kFull, v);

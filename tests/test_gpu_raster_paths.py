@@ -4,8 +4,8 @@ The autotuner chooses among expansion limits small_tri_px in {0, 256, 96, 48}
 (triangles whose clipped bounding box exceeds the limit are scanned by a whole
 warp over 8x4 blocks with int64 edge functions instead of being expanded
 pixel by pixel), two work orders (index order, costliest scene first) and
-three CTA shapes (8 warps, three CTAs per SM; 12 warps, two per SM; 6 warps,
-four per SM).
+four CTA shapes (8 warps, three CTAs per SM; 12 warps, two per SM; 6 or 7
+warps, four per SM).
 Each candidate is checked against the FP64 oracle's images of the same
 state, pixel by pixel, on views forced close to walls so that the block-scan
 path draws many large triangles per view (coarsely tessellated walls a
@@ -87,6 +87,7 @@ def test_every_autotune_candidate_renders_the_oracle_images():
     cands = [(px, order, 8) for px in (0, 256, 96, 48) for order in (1, 2)]
     cands += [(px, 2, 12) for px in (0, 48)]     # the 12-warp CTA shape
     cands += [(px, o, 6) for px in (0, 48) for o in (1, 2)]   # the 6-warp CTA shape
+    cands += [(px, o, 7) for px in (0, 48) for o in (1, 2)]   # the 7-warp CTA shape
     for px, order, warps in cands:
         sim = gx.Sim(ss, ROBOT, n, small_tri_px=px, raster_order=order, raster_warps=warps,
                      **kw)

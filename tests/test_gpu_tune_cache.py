@@ -49,7 +49,7 @@ def test_tuning_cache_hit_miss_and_refusals(tmp_path):
     assert "cached" not in rc
     assert len(json.load(open(cache))) == 2
     # settings that do not fit the context
-    for bad in (dict(ra, raster_warps=7), dict(ra, raster_ctas=10**6), dict(ra, raster_ctas=0),
+    for bad in (dict(ra, raster_warps=5), dict(ra, raster_ctas=10**6), dict(ra, raster_ctas=0),
                 dict(ra, occlusion_cull=1), dict(ra, order_costliest_first=2),
                 dict(ra, small_tri_px=-1)):
         with pytest.raises(gx.GxError) as ei:
