@@ -149,10 +149,11 @@ def raster_work(workload):
     return golden(f"raster_work_{SAME_VIEWS.get(base, base)}.json")
 
 
-def kernel_capture(workload):
+def kernel_capture(workload, warps=None):
     """Per-launch figures of the rasteriser (DRAM bytes, warp instructions)
     scaled to the full workload from an ncu capture of a smaller case; None
-    once the rasteriser source changed since the capture."""
+    once the rasteriser source changed since the capture, or when the CTA
+    shape timed (warps) is not the one captured."""
     p = os.path.join(ROOT, "profiles", f"raster_{workload}_traffic.json")
     if not os.path.exists(p):
         p = os.path.join(ROOT, "profiles",
@@ -161,6 +162,8 @@ def kernel_capture(workload):
         return None
     d = json.load(open(p))
     if d.get("source_sha1") != raster_source_sha1():
+        return None
+    if warps is not None and d.get("raster_warps") not in (None, warps):
         return None
     return d
 
@@ -174,8 +177,8 @@ def raster_source_sha1():
     return h.hexdigest()
 
 
-def kernel_traffic(workload):
-    d = kernel_capture(workload)
+def kernel_traffic(workload, warps=None):
+    d = kernel_capture(workload, warps)
     return d.get("bytes_per_launch_full") if d else None
 
 
@@ -610,12 +613,12 @@ def main():
     phase_ms, phase_n = sim.phase_times()
     # the headline: the same steps of the same batch on a context that
     # replays each step as a captured CUDA graph (how a user runs it)
+    gtune = None
     gsim = None
     if not args.no_graph:
         gsim = gx.Sim(ss, I.fetch_like_robot(), n, use_graph=True, sdf_mode=sdf_mode,
                       sdf_margin=w.sdf_margin, **sim_kw)
         _, gtune = warm(gsim)
-        tune = gtune or tune
         ms, clk = timed(gsim, True)
         dev_err = gsim.device_error()
         out_ctx = gsim
@@ -643,7 +646,7 @@ def main():
         """Another static form of the same batch, timed like the headline's
         event-timed loop: env-steps/s and physics ms per launch."""
         g = gx.Sim(sset, I.fetch_like_robot(), n, profile=1, **{**sim_kw, **kw})
-        if tune:  # the headline's rasteriser setting, so only the static form differs
+        if tune:  # the event-timed loop's rasteriser setting: only the static form differs
             g.apply_tune(tune)
         with torch.cuda.stream(stream):
             g.reset(stream=stream)
@@ -679,7 +682,8 @@ def main():
         grid_bytes = [int(np.prod(sc.grid_dims)) * 4 for sc in scenes]
         if column:
             cb = [ss.column_info(s)[1] for s in range(len(scenes))]
-            static_form = {"grid_form_value": grid_value, "column_over_grid": value / grid_value,
+            static_form = {"grid_form_value": grid_value,
+                           "column_over_grid": value_events / grid_value,
                            "physics_ms": {"column": phase_ms[0] / max(phase_n[0], 1),
                                           "grid": grid_physics_ms},
                            "bytes_per_scene": {"grid_mean": float(np.mean(grid_bytes)),
@@ -706,11 +710,11 @@ def main():
         c.close()
         q_ms = phase_ms[3] / max(phase_n[3], 1)
         nsdf.update({
-            "grid_form_value": grid_value, "neural_over_grid": value / grid_value,
+            "grid_form_value": grid_value, "neural_over_grid": value_events / grid_value,
             "static_store": ("box store: nodes recomputed from the scene's boxes; the scene set "
                              "holds no dense grid" if store == 1 else "dense grid"),
             "box_store_form_value": store_value,
-            "neural_over_box_store": value / store_value if store_value else None,
+            "neural_over_box_store": value_events / store_value if store_value else None,
             "physics_ms": {"neural": phase_ms[0] / max(phase_n[0], 1), "grid": grid_physics_ms,
                            "box_store": store_physics_ms},
             "query_ms_per_step": q_ms,
@@ -755,8 +759,8 @@ def main():
             mbuf.copy_(mask_at(t))
             sim.reset(mbuf, stream=stream)
             sim.step(abuf, stream=stream)
-    if tune:
-        sim.apply_tune(tune)
+    if gtune or tune:
+        sim.apply_tune(gtune or tune)
     torch.cuda.synchronize()
     full = sim.host_outputs(pinned=True)
     result = {k: (v if k in ("reward", "success", "event") else None) for k, v in full.items()}
@@ -829,7 +833,11 @@ def main():
                                  "(MEASURED_PEAKS.json); this run's own clocks are in 'clocks'"}
         # the rasteriser is instruction-bound: warp instructions issued per
         # second against 4 schedulers x 1 instruction per cycle per SM
-        cap = kernel_capture(w.name)
+        # the CTA shape timed: the tuned one, the one asked for, else the
+        # library's default (7 warps, or 8 where the context needs them)
+        shape = (tune["raster_warps"] if tune else args.raster_warps or
+                 (8 if (args.fused or args.occlusion or w.objects == "boxes") else 7))
+        cap = kernel_capture(w.name, shape)
         issue = None
         if cap and cap.get("warp_inst_per_launch_full"):
             rate = cap["warp_inst_per_launch_full"] / (launch_ms / 1e3) / 1e9
@@ -842,7 +850,8 @@ def main():
         roof = {"bound": "alu", "kernel": "raster_kernel", "achieved": achieved, "peak": peak,
                 "unit": "Tops/s (FP32/INT32 lane ops)",
                 "frac": (achieved / peak) if achieved else None,
-                "traffic": kernel_traffic(w.name), "launch_ms": launch_ms,
+                "traffic": kernel_traffic(w.name, shape), "launch_ms": launch_ms,
+                "raster_warps": shape,
                 "peak_basis": f"{sms} SMs x {LANES} lanes x {sm_mhz:.0f} MHz ({peak_src} max "
                               f"clock)",
                 "at_loaded_clock": at_loaded, "no_culling_bound": no_cull,
@@ -872,13 +881,14 @@ def main():
                    "per-kernel CUDA events, no graph"),
         "event_timed": {"value": value_events, "ms_per_step": ms_events / args.steps,
                         "note": "the same steps on a context timing each kernel with CUDA "
-                                "events (no graph); phases and the roofline come from it"},
+                                "events (no graph); phases, the roofline and the static-form "
+                                "ratios come from it"},
         "phases_ms_per_launch": {k: phase_ms[i] / max(phase_n[i], 1)
                                  for i, k in enumerate(["physics", "raster", "reset",
                                                         "nsdf_query"])},
         "nsdf": nsdf,
         "column_grid": static_form,
-        "autotune": tune,
+        "autotune": gtune or tune, "autotune_event_timed": tune,
         "shards": shards,
         "raster_counters_per_view": counters,
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
