@@ -207,10 +207,11 @@ typedef struct {
                               and without heuristics, broad-phase or robot-body
                               rendering (GX_EINVAL otherwise)                 */
   int32_t raster_warps;    /* warps per rasteriser CTA: 8 (three CTAs per SM),
-                              12 (two per SM), 6 or 7 (four per SM; not with
-                              fused_step, object_boxes or occlusion_cull); 0:
-                              7 where offered, else 8; gx_autotune may change
-                              it                                              */
+                              12 (two per SM; not with object_boxes), 6 (four
+                              per SM; not with fused_step, object_boxes or
+                              occlusion_cull), 7 (four per SM; not with
+                              fused_step or occlusion_cull); 0: 7 where
+                              offered, else 8; gx_autotune may change it      */
   int32_t occlusion_cull;  /* 1: the rasteriser culls clusters by occlusion in
                               two phases per environment: first the clusters
                               it showed in its previous image (one bit per
@@ -446,7 +447,7 @@ typedef struct {
  * {index, costliest scene first}, CTA shape {8 warps at the occupancy (three
  * CTAs per SM), 8 warps one CTA per SM fewer, 12 warps at its occupancy (two
  * per SM), 6 and 7 warps at their occupancy (four per SM; not offered with
- * occlusion culling); the fused step and box objects keep 8 warps} -- for `steps` steps each (plus one
+ * occlusion culling); the fused step keeps 8 warps, box objects take 8 or 7} -- for `steps` steps each (plus one
  * warm-up), restoring the
  * state after every candidate, and keeps the fastest (written to *best when
  * not NULL).  The outputs are overwritten; the state is left as before the

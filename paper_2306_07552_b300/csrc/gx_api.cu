@@ -283,7 +283,7 @@ RasterParams raster_params(gx_ctx* c, const gx_outputs& out) {
   rp.M = c->M;
   rp.W = c->cfg.img_w;
   rp.H = c->cfg.img_h;
-  rp.warps = (c->cfg.fused_step || c->cfg.object_boxes) ? 8 : c->raster_warps;
+  rp.warps = c->cfg.fused_step ? 8 : c->raster_warps;
   rp.big_px = c->big_px;
   rp.fb_slots = c->d_fb;
   rp.fb_epoch = c->d_fb_epoch;
@@ -677,10 +677,13 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
   if (c.raster_warps != 0 && c.raster_warps != 6 && c.raster_warps != 7 && c.raster_warps != 8 &&
       c.raster_warps != 12)
     return fail(nullptr, GX_EINVAL, "raster_warps must be 0, 6, 7, 8 or 12");
-  if ((c.raster_warps == 6 || c.raster_warps == 7) &&
-      (c.fused_step || c.object_boxes || c.occlusion_cull))
-    return fail(nullptr, GX_EINVAL, "raster_warps 6 and 7: not with fused_step, object_boxes or "
+  if (c.raster_warps == 6 && (c.fused_step || c.object_boxes || c.occlusion_cull))
+    return fail(nullptr, GX_EINVAL, "raster_warps 6: not with fused_step, object_boxes or "
                                     "occlusion_cull");
+  if (c.raster_warps == 7 && (c.fused_step || c.occlusion_cull))
+    return fail(nullptr, GX_EINVAL, "raster_warps 7: not with fused_step or occlusion_cull");
+  if (c.raster_warps == 12 && c.object_boxes)
+    return fail(nullptr, GX_EINVAL, "raster_warps 12: not with object_boxes");
   if (c.fused_step < 0 || c.fused_step > 1)
     return fail(nullptr, GX_EINVAL, "fused_step must be 0 or 1");
   if (c.fused_step && (c.sdf_mode == 1 || c.object_boxes))
@@ -726,17 +729,17 @@ extern "C" gx_status gx_create(const gx_scene_set* set, const gx_robot* robot,
   if ((e = reset_configure()) != cudaSuccess) return bail(e, "reset config");
   {
     // framebuffer slots for the most CTAs a shape this context may use keeps
-    // resident: the 6- and 7-warp shapes (offered unless the fused step, box
-    // objects or occlusion culling hold the rasteriser at 8 warps) fit more
-    // per SM
+    // resident: the 6- and 7-warp shapes fit more per SM (7 warps is offered
+    // unless the fused step or occlusion culling hold the rasteriser at 8
+    // warps, 6 warps not with box objects either)
     int sms0 = 0, dev0 = 0;
     cudaGetDevice(&dev0);
     cudaDeviceGetAttribute(&sms0, cudaDevAttrMultiProcessorCount, dev0);
     x->sms = sms0;
     x->n_slots = x->slots8;
-    if (!c.fused_step && !c.object_boxes && !c.occlusion_cull) {
-      if ((e = raster_ctas_per_sm(6, &x->per_sm6)) != cudaSuccess ||
-          (e = raster_ctas_per_sm(7, &x->per_sm7)) != cudaSuccess)
+    if (!c.fused_step && !c.occlusion_cull) {
+      if ((!c.object_boxes && (e = raster_ctas_per_sm(6, &x->per_sm6)) != cudaSuccess) ||
+          (e = raster_ctas_per_sm(7, &x->per_sm7, c.object_boxes != 0)) != cudaSuccess)
         return bail(e, "raster config");
       x->n_slots = std::max(x->n_slots, std::max(1, std::max(x->per_sm6, x->per_sm7)) * sms0);
     }
@@ -1256,22 +1259,30 @@ extern "C" gx_status gx_autotune(gx_ctx* x, const float* actions, const gx_outpu
   // (occlusion culling, when the context has its visibility bits, as a CTA
   // shape of its own: 8 warps at the occupancy)
   // and 6 and 7 warps at their occupancy (four CTAs per SM) where the
-  // context offers them
-  const int shapes = (x->cfg.fused_step || x->cfg.object_boxes) ? 2 : (x->per_sm6 > 0 ? 5 : 3);
-  const int occ_shape = x->d_vis ? shapes : -1;
+  // context offers them (box objects: 8 and 7 warps)
+  struct Shape {
+    int warps;
+    bool fewer, occ;  // one CTA per SM fewer; occlusion culling
+  } shape[6];
+  int n_shapes = 0;
+  shape[n_shapes++] = {8, false, false};
+  shape[n_shapes++] = {8, true, false};
+  if (!x->cfg.fused_step && !x->cfg.object_boxes) shape[n_shapes++] = {12, false, false};
+  if (x->per_sm6 > 0) shape[n_shapes++] = {6, false, false};
+  if (x->per_sm7 > 0) shape[n_shapes++] = {7, false, false};
+  if (x->d_vis) shape[n_shapes++] = {8, false, true};
   for (int ci = 0; ci < 4 && err == cudaSuccess; ++ci)
     for (int order = 0; order < 2 && err == cudaSuccess; ++order)
-      for (int k = 0; k < shapes + (x->d_vis ? 1 : 0) && err == cudaSuccess; ++k) {
-        const bool occ = k == occ_shape;
+      for (int k = 0; k < n_shapes && err == cudaSuccess; ++k) {
+        const bool occ = shape[k].occ;
         x->occlusion = occ;
-        const int warps = occ ? 8 : (k == 2 ? 12 : (k == 3 ? 6 : (k == 4 ? 7 : 8)));
+        const int warps = shape[k].warps;
         const int per_sm = std::max(1, warps == 12  ? per_sm12
                                        : warps == 6 ? x->per_sm6
                                        : warps == 7 ? x->per_sm7
                                                     : x->slots8 / std::max(1, x->sms));
-        if (warps == 7 && x->per_sm7 <= 0) continue;
-        if (k == 1 && per_sm == 1) continue;
-        const int ctas = std::min(x->n, std::max(1, per_sm - (k == 1 ? 1 : 0)) * x->sms);
+        if (shape[k].fewer && per_sm == 1) continue;
+        const int ctas = std::min(x->n, std::max(1, per_sm - (shape[k].fewer ? 1 : 0)) * x->sms);
         x->big_px = px[ci] > 0 ? px[ci] : (1 << 30);
         x->order_mode = order;
         x->raster_warps = warps;
@@ -1324,11 +1335,12 @@ extern "C" gx_status gx_autotune(gx_ctx* x, const float* actions, const gx_outpu
 
 extern "C" gx_status gx_apply_tune(gx_ctx* x, const gx_tune_result* t) {
   if (!x || !t) return fail(x, GX_EINVAL, "gx_apply_tune: NULL argument");
-  const bool eight_only = x->cfg.fused_step || x->cfg.object_boxes;
+  const bool eight_only = x->cfg.fused_step;
   if (t->small_tri_px < 0 || (t->order_costliest_first != 0 && t->order_costliest_first != 1) ||
       (t->raster_warps != 6 && t->raster_warps != 7 && t->raster_warps != 8 &&
        t->raster_warps != 12) ||
       (eight_only && t->raster_warps != 8) || (t->raster_warps == 6 && x->per_sm6 <= 0) ||
+      (x->cfg.object_boxes && t->raster_warps == 12) ||
       (t->raster_warps == 7 && x->per_sm7 <= 0) ||
       (t->occlusion_cull != 0 && t->occlusion_cull != 1) ||
       (t->occlusion_cull && (!x->d_vis || t->raster_warps != 8)))

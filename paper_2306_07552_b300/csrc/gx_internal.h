@@ -370,7 +370,8 @@ void launch_column_build(const float* boxes, int n_boxes, double ox, double oz, 
 
 size_t raster_smem_bytes(int warps = 8, int hiz_tiles = 0);
 cudaError_t raster_configure(int* slots);
-cudaError_t raster_ctas_per_sm(int warps, int* per_sm);
+// resident rasteriser CTAs per SM of a shape (boxes: the box-object kernel)
+cudaError_t raster_ctas_per_sm(int warps, int* per_sm, bool boxes = false);
 void launch_grid_build(float* grid, const float* boxes, int n_boxes, float ox, float oy, float oz,
                        float h, int nx, int ny, int nz, cudaStream_t s);
 // Trilinear static distance of scene `scene` at n points (NaN outside the box).

@@ -117,6 +117,12 @@ cudaError_t raster_configure(int* slots) {
                                 (int)raster_smem_bytes(7))) != cudaSuccess ||
       (e = cudaFuncSetAttribute(raster_kernel<false, 8, true>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, b8)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(raster_kernel<false, 7, true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)raster_smem_bytes(7))) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(raster_kernel<true, 7, true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)raster_smem_bytes(7))) != cudaSuccess ||
       (e = cudaFuncSetAttribute(raster_kernel<true, 8, true>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, b8)) != cudaSuccess ||
       (e = cudaFuncSetAttribute(raster_kernel<false, 8, false, true>,
@@ -135,7 +141,10 @@ cudaError_t raster_configure(int* slots) {
   return cudaSuccess;
 }
 
-cudaError_t raster_ctas_per_sm(int warps, int* per_sm) {
+cudaError_t raster_ctas_per_sm(int warps, int* per_sm, bool boxes) {
+  if (warps == 7 && boxes)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, raster_kernel<false, 7, true>, 224,
+                                                         raster_smem_bytes(7));
   if (warps == 6)
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, raster_kernel<false, 6>, 192,
                                                          raster_smem_bytes(6));
@@ -157,7 +166,13 @@ void launch_raster(const RasterParams& p, cudaStream_t s) {
       raster_kernel<true, 8, false, true><<<grid, 256, smem, s>>>(p);
     else
       raster_kernel<false, 8, false, true><<<grid, 256, smem, s>>>(p);
-  } else if (p.obox) {  // box objects: 8 warps
+  } else if (p.obox && p.warps == 7) {  // box objects: 7 warps or 8
+    const size_t smem = raster_smem_bytes(7);
+    if (p.counters)
+      raster_kernel<true, 7, true><<<grid, 224, smem, s>>>(p);
+    else
+      raster_kernel<false, 7, true><<<grid, 224, smem, s>>>(p);
+  } else if (p.obox) {
     const size_t smem = raster_smem_bytes(8);
     if (p.counters)
       raster_kernel<true, 8, true><<<grid, 256, smem, s>>>(p);

@@ -69,13 +69,14 @@ def _lockstep(sim, orc, acts, M, W, tally, image_envs):
             check_image(orc, after, out, e, W, W, M, tally, boxes=True)
 
 
-@pytest.mark.parametrize("store", [0, 1])
-def test_box_resets_and_random_steps(room, store):
+# warps 0: the default rasteriser shape for box objects (7 warps per CTA); 8: the other one
+@pytest.mark.parametrize("store,warps", [(0, 0), (1, 0), (0, 8)])
+def test_box_resets_and_random_steps(room, store, warps):
     gx, scene, sets, orc = room
     n, M, W = 48, 12, 64
     rho = (0.03, 0.06)
     sim = gx.Sim(sets[store], ROBOT, n, img=(W, W), n_objects=M, obj_radius=rho, seed=5,
-                 object_boxes=True, static_store=store)
+                 object_boxes=True, static_store=store, raster_warps=warps)
     before = {k: v.copy() for k, v in sim.state_arrays().items()}
     sim.reset()
     torch.cuda.synchronize()
@@ -153,6 +154,6 @@ def test_box_configurations_refused(room):
     gx, scene, sets, orc = room
     ss = sets[0]
     for kw in (dict(heuristics=1), dict(broadphase=True), dict(render_robot=True),
-               dict(sdf_mode=2)):
+               dict(sdf_mode=2), dict(raster_warps=6), dict(raster_warps=12)):
         with pytest.raises(gx.GxError):
             gx.Sim(ss, ROBOT, 4, img=(32, 32), n_objects=4, object_boxes=True, **kw)
