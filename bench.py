@@ -764,22 +764,22 @@ def main():
     torch.cuda.synchronize()
     full = sim.host_outputs(pinned=True)
     result = {k: (v if k in ("reward", "success", "event") else None) for k, v in full.items()}
-    acts_h = torch.empty((n, 11), dtype=torch.float32, pin_memory=True)
-    mask_h = torch.empty((n,), dtype=torch.uint8, pin_memory=True)
     ne = max(1, args.e2e_steps)
-    acts_np = I.make_actions(2 * ne, n, w.action_dist, seed=w.action_seed + 99 + rank)
+    # each step's actions and reset mask wait in pinned host memory, where a
+    # host-side policy would write them
+    acts_h = torch.from_numpy(I.make_actions(2 * ne, n, w.action_dist,
+                                             seed=w.action_seed + 99 + rank)).pin_memory()
+    mask_h = torch.from_numpy(np.stack([host_mask(t) for t in range(2 * ne)])).pin_memory()
 
     def e2e_run(host, k0):
-        sim.step_host(acts_h, host, stream=stream)  # warm the path once
+        sim.step_host(acts_h[k0], host, stream=stream)  # warm the path once
         t0 = time.perf_counter()
         for t in range(ne):
             # the workload's resets, their mask copied in from the host too
-            mask_h.numpy()[:] = host_mask(k0 + t)
             with torch.cuda.stream(stream):
-                mbuf.copy_(mask_h, non_blocking=True)
+                mbuf.copy_(mask_h[k0 + t], non_blocking=True)
             sim.reset(mbuf, stream=stream)
-            acts_h.numpy()[:] = acts_np[k0 + t]
-            sim.step_host(acts_h, host, stream=stream)
+            sim.step_host(acts_h[k0 + t], host, stream=stream)
         v, _ = job_value(dist, n, ne, (time.perf_counter() - t0) * 1e3)
         return v, int(sum(x.numel() * x.element_size() for x in host.values() if x is not None))
 
