@@ -650,6 +650,10 @@ __device__ void reset_env(const ResetParams& P, int env, float4 (*s_cand)[kTryWi
     }
     __syncthreads();
     const unsigned freew = ~s_bad & ((1u << kTryWindow) - 1u);
+    // every thread reads this window's word before thread 0 clears it for
+    // the next window (without this barrier a late warp could read the
+    // cleared word, leave the loop, and miss its share of the next window)
+    __syncthreads();
     if (freew) {
       if (tid == 0) s_robot_try = t0 + __ffs(freew) - 1;
       break;

@@ -84,6 +84,55 @@ def test_reset_matches_oracle(room):
     sim.close()
 
 
+def test_masked_reset_many_environments(room):
+    """Masked resets at 20,000 environments (more than the reset kernel's
+    resident CTAs, which stride over them; a ragged tail): a mask of all ones
+    equals the unmasked reset bit for bit; with sparse, dense (CTAs holding
+    several resetting environments) and edge masks exactly the masked
+    environments start a new episode, the others keep every byte, and
+    sampled ones match the oracle's placement."""
+    gx, scene, ss, orc = room
+    n, M, rho = 20000, 6, (0.03, 0.06)
+    kw = dict(img=(32, 32), n_objects=M, obj_radius=rho, seed=3)
+    a = gx.Sim(ss, ROBOT, n, **kw)
+    b = gx.Sim(ss, ROBOT, n, **kw)
+    a.reset()
+    b.reset()
+    a.reset(torch.ones(n, dtype=torch.uint8, device="cuda"))
+    b.reset()
+    sa, sb = a.state_arrays(), b.state_arrays()
+    for k in sa:
+        assert np.array_equal(sa[k], sb[k]), k
+    rng = np.random.default_rng(12)
+    edge = np.zeros(n, bool)
+    edge[[0, 255, 256, 16383, 16384, n - 1]] = True
+    checked = 0
+    for m in (rng.random(n) < 0.01, rng.random(n) < 0.6, edge):
+        before = a.state_arrays()
+        a.reset(torch.from_numpy(m.astype(np.uint8)).cuda())
+        after = a.state_arrays()
+        keep, new = np.flatnonzero(~m), np.flatnonzero(m)
+        assert (after["episode"][new] == before["episode"][new] + 1).all()
+        for k in after:
+            x, y = after[k], before[k]
+            axis = 0 if x.shape[0] == n else 1   # q, c_off, p_pre, r_off are stored [k][n]
+            assert np.array_equal(np.take(x, keep, axis=axis), np.take(y, keep, axis=axis)), k
+        for e in list(new[:4]) + list(new[-4:]):
+            st = O.Oracle.make_state((0, 0, 0), np.zeros(7), episode=int(before["episode"][e]))
+            r = orc.reset(st, 3, int(e), M, *rho)
+            if r.near_band:
+                continue
+            assert after["episode"][e] == st.episode
+            assert np.allclose(after["obj"][e, :M], O.Oracle.state_objs(st), atol=1e-5), e
+            assert abs(after["base_x"][e] - st.base[0]) < 1e-5
+            assert abs(after["base_z"][e] - st.base[1]) < 1e-5
+            checked += 1
+    assert checked >= 12
+    assert a.device_error() & ~0x2 == 0
+    a.close()
+    b.close()
+
+
 def test_room16_trajectory_lockstep(room):
     """16 envs sharing one room, 64x64 camera, 10 objects, 20 uniform-random
     steps: every env's physics and every image at every step."""
